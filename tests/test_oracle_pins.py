@@ -1,0 +1,322 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: a closed
+form, an independent quadrature, a geometric definition, a special state with
+a known residual, the linear Jacobian printed in Appendix B, or a symmetry.
+No GPU is needed.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate
+from scipy.interpolate import CubicSpline
+
+import oracle as O
+from paper_1403_5044_b300 import workloads as W
+
+
+def _mesh(spec):
+    return O.Mesh(spec.N, spec.M, spec.x1, spec.dx, spec.dy, spec.n_rad)
+
+
+TINY = W.MeshSpec(9, 5, -2.0, 0.5, 0.4)
+SMALL = W.MeshSpec(7, 4, -1.5, 0.5, 0.3)
+
+
+# ---------------------------------------------------------------- Eq. IS2
+def _corner_polar(A, B, C, a, b):
+    """Unsigned int over the rectangle with corners (0, 0) and (a, b) of
+    (A s^2 + B s t + C t^2)^(-1/2), by polar coordinates about the singular
+    corner: with Q = r^2 q(theta) the radial integral is exact and the
+    remaining angular integrand is smooth on each side of the diagonal."""
+    if a == 0.0 or b == 0.0:
+        return 0.0
+    ta = 0.0 if a > 0 else (math.pi if b > 0 else -math.pi)
+    tb = math.pi / 2 if b > 0 else -math.pi / 2
+    lo, hi = min(ta, tb), max(ta, tb)
+    tc = math.atan2(b, a)
+    q = lambda th: A * math.cos(th) ** 2 + B * math.cos(th) * math.sin(th) + C * math.sin(th) ** 2
+    R = lambda th: min(abs(a) / max(abs(math.cos(th)), 1e-300), abs(b) / max(abs(math.sin(th)), 1e-300))
+    f = lambda th: R(th) / math.sqrt(q(th))
+    v1 = integrate.quad(f, lo, tc, epsabs=1e-15, epsrel=1e-13, limit=200)[0]
+    v2 = integrate.quad(f, tc, hi, epsabs=1e-15, epsrel=1e-13, limit=200)[0]
+    return v1 + v2
+
+
+def _rect_polar(A, B, C, s1, s2, t1, t2):
+    W_ = lambda a, b: math.copysign(1.0, a) * math.copysign(1.0, b) * _corner_polar(A, B, C, a, b)
+    return W_(s2, t2) - W_(s1, t2) - W_(s2, t1) + W_(s1, t1)
+
+
+@pytest.mark.parametrize("A,B,C", [(1.0, 0.0, 1.0), (1.3, 0.4, 1.1), (1.02, -0.3, 1.6), (2.5, 1.9, 1.7)])
+@pytest.mark.parametrize("box", [(-3.0, 4.0, -2.0, 5.0), (-0.25, 7.75, 0.0, 2.4), (-5.1, -0.1, 0.3, 2.0),
+                                 (0.5, 3.0, -4.0, -1.0), (-1.0, 1.0, -1.0, 1.0)])
+def test_I_closed_form_matches_polar_quadrature(A, B, C, box):
+    s1, s2, t1, t2 = box
+    got = float(O.rect_integral(A, B, C, s1, s2, t1, t2))
+    ref = _rect_polar(A, B, C, s1, s2, t1, t2)
+    assert abs(got - ref) <= 1e-11 * max(1.0, abs(ref)), (got, ref)
+
+
+def test_I_closed_form_matches_2d_quadrature_off_singularity():
+    A, B, C = 1.4, 0.7, 1.2
+    s1, s2, t1, t2 = 0.5, 2.0, -1.0, 1.5
+    ref = integrate.dblquad(lambda t, s: (A * s * s + B * s * t + C * t * t) ** -0.5, s1, s2, t1, t2,
+                            epsabs=1e-13, epsrel=1e-13)[0]
+    assert abs(float(O.rect_integral(A, B, C, s1, s2, t1, t2)) - ref) < 1e-10
+
+
+def test_I_image_part_is_mirror_of_direct():
+    """I over the half domain with the image term equals the direct term alone
+    over the mirrored full domain [x1, xN] x [-yM, yM] (Eq. S2, Eq. IS2)."""
+    mesh = _mesh(TINY)
+    yM = (mesh.M - 1) * mesh.dy
+    xN = mesh.x1 + (mesh.N - 1) * mesh.dx
+    rng = np.random.default_rng(3)
+    for _ in range(10):
+        A, C = 1 + rng.uniform(0, 0.5, 2)
+        B = rng.uniform(-0.5, 0.5)
+        xt = mesh.x1 + mesh.dx * (rng.integers(0, mesh.N - 1) + 0.5)
+        yt = mesh.dy * rng.integers(0, mesh.M)
+        half = float(O.I_S2(mesh, A, B, C, xt, yt))
+        full = float(O.rect_integral(A, B, C, mesh.x1 - xt, xN - xt, -yM - yt, yM - yt))
+        assert abs(half - full) < 1e-12 * abs(full)
+
+
+# ---------------------------------------------------------------- kernels
+def _grad_inv_r(P, Q, h=1e-5):
+    """Central-difference gradient of 1/|P - Q| with respect to P."""
+    g = np.zeros(3)
+    for d in range(3):
+        e = np.zeros(3)
+        e[d] = h
+        g[d] = (1 / np.linalg.norm(P + e - Q) - 1 / np.linalg.norm(P - e - Q)) / (2 * h)
+    return g
+
+
+def test_K1_is_normal_derivative_of_green_function_with_image():
+    """K1 dA is the derivative of 1/r along the (unnormalised) upward normal
+    N = (-zeta_x, -zeta_y, 1) of the integration surface, with sign such
+    that K1 = -N . grad_P (1/|P - P*|); the image point is the source mirrored
+    in y = 0, whose surface slope in y flips (R1, R2)."""
+    rng = np.random.default_rng(11)
+    for _ in range(20):
+        xs, ys, zs, zx, zy = rng.uniform(-2, 2), rng.uniform(0, 2), rng.uniform(-.3, .3), rng.uniform(-.5, .5), rng.uniform(-.5, .5)
+        xt, yt, zt = rng.uniform(-2, 2), rng.uniform(0, 2), rng.uniform(-.3, .3)
+        P, Pm, T = np.array([xs, ys, zs]), np.array([xs, -ys, zs]), np.array([xt, yt, zt])
+        N1, Nm = np.array([-zx, -zy, 1.0]), np.array([-zx, zy, 1.0])
+        K1_ref = -N1 @ _grad_inv_r(P, T) - Nm @ _grad_inv_r(Pm, T)
+        K2_ref = 1 / np.linalg.norm(P - T) + 1 / np.linalg.norm(Pm - T)
+        K1, K2, _ = O.pair_kernels(xs - xt, ys - yt, ys + yt, zs - zt, zx, zy, 1.0, 0.0, 1.0)
+        assert abs(K1 - K1_ref) < 1e-7 * max(1, abs(K1_ref))
+        assert abs(K2 - K2_ref) < 1e-13 * K2_ref
+
+
+def test_S2_equals_K2_on_the_tangent_plane():
+    """S2 is K2 with the surface replaced by the target's tangent plane
+    (Eq. S2 with A, B, C of the target).  For a source on y = 0 the direct and
+    the image point both lie on that plane when dz = zx* dx - zy* y*, and
+    then S2 = K2 exactly."""
+    rng = np.random.default_rng(5)
+    for _ in range(20):
+        zxt, zyt = rng.uniform(-.6, .6, 2)
+        A, B, C = 1 + zxt ** 2, 2 * zxt * zyt, 1 + zyt ** 2
+        dx, yt = rng.uniform(-3, 3), rng.uniform(0.1, 2)
+        dz = zxt * dx - zyt * yt
+        K1, K2, S2 = O.pair_kernels(dx, -yt, yt, dz, 0.0, 0.0, A, B, C)
+        assert abs(S2 - K2) < 1e-13 * K2
+
+
+# ---------------------------------------------------------------- mesh step
+def test_trapezoid_exact_for_linear_slope():
+    mesh = _mesh(TINY)
+    x = mesh.x()
+    a, b = 0.3, -0.7
+    fx = np.tile(a + b * x, (mesh.M, 1))
+    f1 = np.full(mesh.M, 0.25)
+    f = O.trapezoid_x(mesh, f1, fx)
+    exact = 0.25 + a * (x - x[0]) + 0.5 * b * (x ** 2 - x[0] ** 2)
+    assert np.allclose(f, exact[None, :], rtol=0, atol=1e-14)
+
+
+def test_spline_reproduces_even_cubics_and_is_clamped():
+    mesh = _mesh(W.MeshSpec(9, 7, -2.0, 0.5, 0.35))
+    y = mesh.y()
+    c0, c2, c3 = 0.4, -1.3, 0.8
+    f = np.tile((c0 + c2 * y ** 2 + c3 * y ** 3)[:, None], (1, mesh.N))
+    fy = O.spline_slope_y(mesh, f)
+    assert np.allclose(fy, (2 * c2 * y + 3 * c3 * y ** 2)[:, None], rtol=0, atol=1e-12)
+    lin = np.tile(y[:, None], (1, mesh.N))
+    assert np.all(O.spline_slope_y(mesh, lin)[0] == 0.0)
+
+
+def test_spline_equals_full_domain_spline_of_even_extension():
+    """R5: the half-domain spline with zero slope at y = 0 and not-a-knot at
+    y_M is the full mirrored-domain not-a-knot spline of the even data."""
+    mesh = _mesh(W.MeshSpec(5, 8, -1.0, 0.5, 0.25))
+    rng = np.random.default_rng(2)
+    f = rng.normal(size=(mesh.M, mesh.N))
+    y = mesh.y()
+    yf = np.concatenate([-y[:0:-1], y])
+    ff = np.concatenate([f[:0:-1], f], axis=0)
+    full = CubicSpline(yf, ff, axis=0, bc_type="not-a-knot")(yf, 1)[mesh.M - 1:]
+    assert np.allclose(O.spline_slope_y(mesh, f), full, rtol=0, atol=1e-12)
+
+
+# ---------------------------------------------------------------- residual
+def test_E1_is_bernoulli_with_kinematic_condition():
+    """Eq. freeSurfCond is Eq. NondimDyn after eliminating Phi_z with
+    Eq. NondimKin: rebuild (Phi_x, Phi_y, Phi_z) from phi_x = Phi_x + Phi_z zeta_x,
+    phi_y = Phi_y + Phi_z zeta_y and the kinematic condition."""
+    rng = np.random.default_rng(7)
+    F = 0.8
+    for _ in range(20):
+        px, py, zx, zy, z = rng.uniform(-1, 2), rng.uniform(-1, 1), rng.uniform(-.7, .7), rng.uniform(-.7, .7), rng.uniform(-.3, .3)
+        Mx = np.array([[1, 0, zx], [0, 1, zy], [zx, zy, -1.0]])
+        V = np.linalg.solve(Mx, [px, py, 0.0])
+        ref = 0.5 * V @ V + z / F ** 2 - 0.5
+        assert abs(O.free_surface_E1(F, px, py, zx, zy, z) - ref) < 1e-13
+
+
+@pytest.mark.parametrize("spec", [TINY, SMALL])
+def test_flat_state_residual_is_source_term_only(spec):
+    """At the flat state (Section 4.1) zeta = 0 and phi = x, so every row
+    vanishes except E2 = eps / sqrt(x*^2 + y*^2 + 1) (Eq. IntegroEqn)."""
+    mesh = _mesh(spec)
+    u0 = O.flat_guess(mesh)
+    assert np.all(O.residual(mesh, 0.7, 0.0, u0) == 0.0)
+    eps = 0.37
+    p = O.residual_parts(mesh, 0.7, eps, u0)
+    src = eps / np.sqrt(mesh.x_star()[None, :] ** 2 + mesh.y()[:, None] ** 2 + 1)
+    assert np.abs(p["E2"] - src).max() < 1e-15
+    for k in ("E1", "E3", "E4", "E5", "E6"):
+        assert np.all(p[k] == 0.0)
+
+
+@pytest.mark.parametrize("spec", [TINY, SMALL])
+def test_linear_jacobian_of_appendix_B_equals_fd_jacobian_at_flat_state(spec):
+    """At u0 with eps = 0 the nonlinear Jacobian is the linear one: K1
+    multiplies g - g* = 0, K2 = S2 = K3 on z = 0, and only the source term
+    depends on eps.  The dense matrix built from Eqs. PreA-PreD (Appendix B)
+    must therefore equal the central-difference Jacobian of the oracle."""
+    mesh = _mesh(spec)
+    J_lin = O.jacobian_linear(mesh, 0.7)
+    J_fd = O.jacobian_fd(mesh, 0.7, 0.0, O.flat_guess(mesh), h=1e-5)
+    assert np.abs(J_lin - J_fd).max() < 1e-8 * np.abs(J_lin).max()
+
+
+def test_banded_linear_jacobian_keeps_only_block_band():
+    mesh = _mesh(TINY)
+    full = O.jacobian_linear(mesh, 0.7)
+    b3 = O.jacobian_linear(mesh, 0.7, b=3)
+    H, N1 = (mesh.N + 1) * mesh.M, mesh.N + 1
+    for l in range(mesh.M):
+        for m in range(mesh.M):
+            blk = (slice(H + l * N1, H + (l + 1) * N1), slice(H + m * N1, H + (m + 1) * N1))
+            if abs(l - m) <= 1:
+                assert np.array_equal(b3[blk], full[blk])
+            else:
+                assert np.all(b3[blk] == 0.0)
+    assert np.array_equal(b3[:H], full[:H]) and np.array_equal(b3[H:, :H], full[H:, :H])
+
+
+def test_integral_sum_with_images_equals_full_mirrored_mesh():
+    """The y-symmetry construction (R1, R2, R6): the half-domain sum with
+    image terms equals the sum over the explicit mirrored mesh j = -(M-1)..M-1
+    with direct terms only, zeta_y odd and trapezoid weights on the full
+    domain."""
+    spec = TINY
+    mesh = _mesh(spec)
+    u = W.random_state(spec, seed=4, amp=0.15)
+    st = O.surface(mesh, u)
+    S_half, _ = O.integral_sum(mesh, st)
+    N, M = mesh.N, mesh.M
+    x, y = mesh.x(), mesh.y()
+    jj = np.arange(-(M - 1), M)
+    cx = np.ones(N); cx[[0, -1]] = 0.5
+    cyf = np.ones(jj.size); cyf[[0, -1]] = 0.5
+    far = 1e30   # pushes the image point of the oracle's kernel to infinity
+    S_full = np.zeros((M, N - 1))
+    for l in range(M):
+        for k in range(N - 1):
+            xt, yt = mesh.x_star()[k], y[l]
+            zt, zxt, zyt, gt = st["zeta_t"][l, k], st["zetax_t"][l, k], st["zetay_t"][l, k], st["g_t"][l, k]
+            A, B, C = 1 + zxt ** 2, 2 * zxt * zyt, 1 + zyt ** 2
+            acc = 0.0
+            for a, j in enumerate(jj):
+                r = abs(j)
+                sgn = -1.0 if j < 0 else 1.0
+                for i in range(N):
+                    K1, K2, S2 = O.pair_kernels(x[i] - xt, sgn * y[r] - yt, far, st["zeta"][r, i] - zt,
+                                                st["zetax"][r, i], sgn * st["zetay"][r, i], A, B, C)
+                    w = mesh.dx * mesh.dy * cx[i] * cyf[a]
+                    acc += w * ((st["g"][r, i] - gt) * K1 + st["zetax"][r, i] * K2 - zxt * S2)
+            S_full[l, k] = acc
+    assert np.abs(S_half - S_full).max() < 1e-12 * np.abs(S_full).max()
+
+
+# ---------------------------------------------------------------- JVP, solves
+def test_fd_jvp_is_first_order():
+    """Eq. JvApprox is a first-order difference quotient: halving h halves
+    its error against a fourth-order central difference."""
+    spec = TINY
+    mesh = _mesh(spec)
+    u = W.random_state(spec, seed=8, amp=0.1)
+    v = np.random.default_rng(9).normal(size=u.size)
+    F, eps = 0.7, 0.3
+    E = lambda w: O.residual(mesh, F, eps, w)
+    h = 1e-3
+    ref = (8 * (E(u + h * v) - E(u - h * v)) - (E(u + 2 * h * v) - E(u - 2 * h * v))) / (12 * h)
+    Eu = E(u)
+    e1 = np.abs(O.jvp_fd(mesh, F, eps, u, v, Eu, h=2e-4) - ref).max()
+    e2 = np.abs(O.jvp_fd(mesh, F, eps, u, v, Eu, h=1e-4) - ref).max()
+    assert 1.8 < e1 / e2 < 2.2
+
+
+def test_dense_newton_and_newton_gmres_reach_the_same_root():
+    spec = TINY
+    mesh = _mesh(spec)
+    u0 = O.flat_guess(mesh)
+    ua, _ = O.newton_dense(mesh, 0.7, 0.1, u0, tol=1e-11)
+    ub, _ = O.newton_gmres(mesh, 0.7, 0.1, u0, tol=1e-11, eta=1e-8)
+    assert np.abs(ua - ub).max() < 1e-8
+    assert np.abs(O.residual(mesh, 0.7, 0.1, ub)).max() < 1e-11
+
+
+def test_weak_source_limit_is_the_linear_solution():
+    """Section 2.3: as eps -> 0 the nonlinear root approaches the linear one,
+    u_L = u0 - J_lin^{-1} E(u0), with an O(eps^2) difference."""
+    spec = W.MeshSpec(11, 5, -2.5, 0.5, 0.5)
+    mesh = _mesh(spec)
+    F = 0.7
+    u0 = O.flat_guess(mesh)
+    J = O.jacobian_linear(mesh, F)
+    errs = []
+    for eps in (0.04, 0.02, 0.01):
+        u, _ = O.newton_dense(mesh, F, eps, u0, tol=1e-13)
+        uL = u0 - np.linalg.solve(J, O.residual(mesh, F, eps, u0))
+        errs.append(np.abs(u - uL).max())
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 3.6 < r1 < 4.4 and 3.8 < r2 < 4.2, errs
+
+
+def test_converged_crest_below_limiting_height():
+    """The highest crest stays below the limiting height F^2/2 (Section 6)."""
+    spec = TINY
+    mesh = _mesh(spec)
+    F = 0.7
+    u, _ = O.newton_gmres(mesh, F, 0.3, O.flat_guess(mesh), tol=1e-10, eta=1e-6)
+    zeta, _ = O.zeta_phi(mesh, u)
+    assert zeta.max() < F ** 2 / 2
+
+
+def test_oracle_matches_its_stored_regression_values():
+    """Guards the oracle against unintended change: the stored values were
+    written by tests/golden/make_golden.py from the oracle alone."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "oracle_residual_9x5.txt")
+    ref = np.loadtxt(path)
+    mesh = _mesh(TINY)
+    E = O.residual(mesh, 0.7, 0.3, W.random_state(TINY, seed=4, amp=0.15))
+    assert np.abs(E - ref).max() < 1e-13 * max(1.0, np.abs(ref).max())
