@@ -80,6 +80,10 @@ def _lib():
         lib.oracle_pairsum.restype = None
         lib.oracle_pair_kernels.argtypes = [ctypes.c_double] * 9 + [dp]
         lib.oracle_pair_kernels.restype = None
+        lib.oracle_pairsum_targets.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                               ctypes.c_double, ctypes.c_double] + [dp] * 8 + \
+            [ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp, dp]
+        lib.oracle_pairsum_targets.restype = None
         _LIB = lib
     return _LIB
 
@@ -180,18 +184,24 @@ def surface(mesh: Mesh, u):
 
     Node arrays have shape [M, N], target arrays [M, N-1]."""
     phi1, phix, zeta1, zetax = unpack(mesh, u)
-    phi = trapezoid_x(mesh, phi1, phix)
     zeta = trapezoid_x(mesh, zeta1, zetax)
-    phiy = spline_slope_y(mesh, phi)
+    # Eq. zetaapprox applied to g = phi - x: the trapezoidal rule integrates
+    # the constant slope 1 of x exactly, so integrating phi_x - 1 from
+    # phi_1 - x1 gives phi - x at every node.  E(u) depends on phi only
+    # through phi - x (Eq. IntegroEqn: phi - phi* - x + x*, phi* - x*) and
+    # through phi_x, phi_y, so g avoids carrying the O(|x|) part of phi
+    # through the sums and the spline.
+    g = trapezoid_x(mesh, phi1 - mesh.x1, phix - 1.0)
+    phi = g + mesh.x()[None, :]
+    phiy = spline_slope_y(mesh, g)
     zetay = spline_slope_y(mesh, zeta)
-    g = phi - mesh.x()[None, :]
     st = {
         "phi1": phi1, "phix": phix, "zeta1": zeta1, "zetax": zetax,
         "phi": phi, "zeta": zeta, "phiy": phiy, "zetay": zetay, "g": g,
     }
-    for name in ("phi", "zeta", "phix", "phiy", "zetax", "zetay"):
+    for name in ("g", "zeta", "phix", "phiy", "zetax", "zetay"):
         st[name + "_t"] = half_mesh(st[name])
-    st["g_t"] = st["phi_t"] - mesh.x_star()[None, :]
+    st["phi_t"] = st["g_t"] + mesh.x_star()[None, :]
     return st
 
 
@@ -254,9 +264,37 @@ def integral_sum(mesh: Mesh, st):
     return s, a
 
 
-def residual_parts(mesh: Mesh, F: float, eps: float, u):
+def residual_E2_at(mesh: Mesh, F: float, eps: float, u, targets):
+    """E2 and its tolerance scale at the listed targets only (flat indices
+    t = l (N-1) + k into the [M, N-1] target array); for sampled checks on
+    meshes too large for a full evaluation."""
+    st = surface(mesh, u)
+    tidx = np.ascontiguousarray(np.asarray(targets, dtype=np.int32))
+    k, l = tidx % (mesh.N - 1), tidx // (mesh.N - 1)
+    c = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+    s = np.zeros(tidx.size)
+    a = np.zeros(tidx.size)
+    _lib().oracle_pairsum_targets(mesh.N, mesh.M, mesh.x1, mesh.dx, mesh.dy,
+                                  _p(c(st["zeta"])), _p(c(st["zetax"])), _p(c(st["zetay"])), _p(c(st["g"])),
+                                  _p(c(st["zeta_t"])), _p(c(st["zetax_t"])), _p(c(st["zetay_t"])),
+                                  _p(c(st["g_t"])), int(tidx.size),
+                                  tidx.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _p(s), _p(a))
+    xt = mesh.x_star()[k]
+    yt = mesh.y()[l]
+    zxt, zyt = st["zetax_t"][l, k], st["zetay_t"][l, k]
+    I = I_S2(mesh, 1 + zxt ** 2, 2 * zxt * zyt, 1 + zyt ** 2, xt, yt)
+    src = eps / np.sqrt(xt ** 2 + yt ** 2 + (st["zeta_t"][l, k] + 1) ** 2)
+    gt = st["g_t"][l, k]
+    E2 = 2 * math.pi * gt + src - s - zxt * I
+    scale = a + np.abs(2 * math.pi * gt) + np.abs(src) + np.abs(zxt * I)
+    return E2, scale
+
+
+def residual_parts(mesh: Mesh, F: float, eps: float, u, pairs: bool = True):
     """Every row family of E(u) before ordering, plus the tolerance scale of
-    each E2 row (sum of absolute values of its terms)."""
+    each E2 row (sum of absolute values of its terms).  With pairs=False the
+    all-pairs sum is skipped and E2 / scale2 are left as NaN (for sampled
+    checks on large meshes, see residual_E2_at)."""
     st = surface(mesh, u)
     xt = mesh.x_star()[None, :]
     yt = mesh.y()[:, None]
@@ -266,7 +304,10 @@ def residual_parts(mesh: Mesh, F: float, eps: float, u):
     C = 1 + zyt ** 2
     I = I_S2(mesh, A, B, C, xt, yt)
     src = eps / np.sqrt(xt ** 2 + yt ** 2 + (st["zeta_t"] + 1) ** 2)
-    S, Sabs = integral_sum(mesh, st)
+    if pairs:
+        S, Sabs = integral_sum(mesh, st)
+    else:
+        S = Sabs = np.full(st["g_t"].shape, np.nan)
     E1 = free_surface_E1(F, st["phix_t"], st["phiy_t"], zxt, zyt, st["zeta_t"])
     # Eq. IntegroEqn with every term moved to one side, the second integral
     # split per the singularity subtraction (Section 3):

@@ -320,3 +320,16 @@ def test_oracle_matches_its_stored_regression_values():
     mesh = _mesh(TINY)
     E = O.residual(mesh, 0.7, 0.3, W.random_state(TINY, seed=4, amp=0.15))
     assert np.abs(E - ref).max() < 1e-13 * max(1.0, np.abs(ref).max())
+
+
+def test_integrating_phi_minus_x_equals_integrating_phi():
+    """Eq. zetaapprox integrates the constant 1 exactly, so the oracle's g =
+    phi - x (integrated from phi_x - 1) equals trapezoid(phi_x) - x up to
+    rounding of the O(|x|) values."""
+    spec = W.MeshSpec(61, 7, -16.0, 0.6, 0.5)
+    mesh = _mesh(spec)
+    u = W.random_state(spec, seed=13, amp=0.2)
+    st = O.surface(mesh, u)
+    phi1, phix, _, _ = O.unpack(mesh, u)
+    phi = O.trapezoid_x(mesh, phi1, phix)
+    assert np.abs((phi - mesh.x()[None, :]) - st["g"]).max() < 64 * np.finfo(float).eps * 20.0 * spec.N
