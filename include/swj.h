@@ -1,0 +1,207 @@
+/*
+ * swj.h -- C ABI of libswj, a B300 (sm_103a) library for steady nonlinear
+ * free-surface flow past a submerged source, solved with the preconditioned
+ * Jacobian-free Newton-Krylov method of Pethiyagoda, McCue, Moroney & Back
+ * (arXiv 1403.5044).
+ *
+ * Problem (Section 2): infinite-depth flow with unit upstream speed past a
+ * source of strength eps at depth 1 under a free surface z = zeta(x, y);
+ * F is the depth Froude number.  Discretisation (Section 3): an N x M mesh
+ * x_i = x1 + (i-1) dx, y_j = (j-1) dy (y1 = 0, only y >= 0 is meshed), the
+ * 2(N+1)M unknowns
+ *     u = [phi_{1,l}, (phi_x)_{1..N,l}]_{l=1..M}, [zeta_{1,l}, (zeta_x)_{1..N,l}]_{l=1..M}
+ * (Eq. unknowns) and the 2(N+1)M equations E(u) = 0 ordered as
+ *     [E3_l, E4_l, E1_{1..N-1,l}]_{l=1..M}, [E5_l, E6_l, E2_{1..N-1,l}]_{l=1..M}
+ * (Appendix A): E1 is the free-surface condition (Eq. freeSurfCond) and E2 the
+ * boundary-integral equation (Eq. IntegroEqn) at the (N-1)M half-mesh points,
+ * E3..E6 the upstream radiation conditions (Eq. numUpRadiation).
+ *
+ * Conventions for every entry point:
+ *  - Vectors u, E, v, ... are caller-owned DEVICE pointers to IEEE double,
+ *    length 2(N+1)M unless stated; they must not alias unless stated.
+ *  - Work is queued on the context's CUDA stream (the one given to
+ *    swj_create).  Entry points marked "async" return before the device has
+ *    finished; the others synchronise that stream before returning.
+ *  - Every entry point returns SWJ_OK (0) or a negative status; nothing
+ *    throws across the ABI.  swj_strerror() names a status.
+ *  - A context is not thread-safe: one host thread at a time per context.
+ *  - The context owns all device workspace it needs (allocated in
+ *    swj_create, freed in swj_destroy).
+ */
+#ifndef SWJ_H
+#define SWJ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define SWJ_OK           0
+#define SWJ_EINVAL      -1   /* bad argument (size, pointer, option)          */
+#define SWJ_ENOMEM      -2   /* device or pinned-host allocation failed       */
+#define SWJ_ECUDA       -3   /* a CUDA runtime call failed                    */
+#define SWJ_ENOTCONV    -4   /* Newton iteration cap reached                  */
+#define SWJ_ELINESEARCH -5   /* line search could not reduce ||E||_2         */
+#define SWJ_EGMRES      -6   /* Krylov iteration cap reached with no progress */
+#define SWJ_ENAN        -7   /* NaN or Inf met in E or in a Krylov vector     */
+#define SWJ_ETIMEOUT    -8   /* a bounded device-side wait gave up            */
+#define SWJ_ESINGULAR   -9   /* zero pivot in the preconditioner factorisation */
+#define SWJ_PENDING      1   /* serving: request not finished yet             */
+
+/* ---- precision of the all-pairs boundary-integral sum ---- */
+#define SWJ_FP64 0   /* every step in IEEE double                                  */
+#define SWJ_FP32 1   /* all-pairs sum in FP32 with compensated accumulation; the   */
+                     /* mesh step, per-target terms and assembly stay in FP64      */
+
+/* ---- solve modes ---- */
+#define SWJ_SOLVE_FP64  0  /* Newton-GMRES with the FP64 residual throughout       */
+#define SWJ_SOLVE_MIXED 1  /* FP32 residual inside Newton/GMRES, then FP64         */
+                           /* residual refinement steps (Newton on the FP64        */
+                           /* residual with FP32 Jacobian-vector products)         */
+
+/* Mesh (Section 3).  N >= 4 points in x, M >= 3 in y; dx, dy > 0; y1 = 0.
+ * n_rad is the decay rate n of the radiation condition (0.05 in Section 3). */
+typedef struct swj_mesh {
+    int N, M;
+    double x1, dx, dy;
+    double n_rad;
+} swj_mesh;
+
+/* Solver options.  swj_default_opts() fills the defaults noted here. */
+typedef struct swj_opts {
+    int    solve_mode;     /* SWJ_SOLVE_FP64 | SWJ_SOLVE_MIXED (MIXED)               */
+    int    block_bw;       /* preconditioner block bandwidth b: odd >= 1, or 0 for   */
+                           /* the untruncated linear Jacobian (Section 4.2) (1)     */
+    int    gmres_restart;  /* GMRES restart length m (30)                            */
+    int    max_newton;     /* Newton iteration cap (60)                              */
+    int    max_krylov;     /* GMRES iterations per Newton step (300)                 */
+    double ftol_inf;       /* stop when ||E||_inf < ftol_inf (1e-10)                 */
+    double eta_max;        /* cap of the Eisenstat-Walker forcing term (0.1)         */
+    double eta_min;        /* floor of the forcing term (1e-6)                        */
+    double fd_h;           /* FD step of Eq. JvApprox; 0: h = sqrt(eps_mach)          */
+                           /* max(1,||u||_2)/||P^-1 v||_2 (0)                         */
+    int    refine_max;     /* MIXED: cap on FP64 refinement Newton steps (4)          */
+    double mixed_tol_inf;  /* MIXED: the FP32 phase stops at ||E_fp32||_inf below     */
+                           /* this, or when it stalls (2e-6)                          */
+    double refine_tol_inf; /* MIXED: the FP64 refinement stops at ||E_fp64||_inf      */
+                           /* below this (1e-9)                                       */
+    int    verbose;        /* 1: one line per Newton step on stderr (0)               */
+} swj_opts;
+
+/* Counters and timings of one solve (KINSOL-style counters). */
+typedef struct swj_stats {
+    int    status;               /* final status code                                */
+    int    newton_iters;         /* Newton steps taken (both phases)                 */
+    int    refine_iters;         /* of which FP64 refinement steps (MIXED)           */
+    int    residual_evals;       /* all residual evaluations                         */
+    int    residual_evals_fp64;  /* of which with the FP64 all-pairs sum             */
+    int    krylov_iters;         /* GMRES iterations (= FD Jacobian-vector products) */
+    int    precond_applies;
+    int    line_search_cuts;     /* halvings of the Newton step                      */
+    double final_norm_inf;       /* ||E||_inf at the returned u, in the precision    */
+                                 /* of the last residual evaluated                   */
+    double final_norm_inf_fp64;  /* ||E_fp64||_inf at the returned u (-1 if never    */
+                                 /* evaluated)                                        */
+    double t_total_ms;           /* wall time of swj_solve                           */
+    double t_setup_ms;           /* preconditioner set-up                            */
+    int    pairs_per_residual_hi, pairs_per_residual_lo;  /* (N-1)M*NM as 2x31 bits */
+} swj_stats;
+
+typedef struct swj_ctx swj_ctx;
+
+/* Fill *o with the defaults listed in swj_opts. */
+void swj_default_opts(swj_opts *o);
+
+/* Create a context for one mesh and one (F, eps), working on `stream`
+ * (a cudaStream_t; NULL = the legacy default stream) of the current device.
+ * Allocates all device workspace.  F > 0, eps >= 0.  opts may be NULL
+ * (defaults).  Returns SWJ_EINVAL for a bad mesh/option, SWJ_ENOMEM when the
+ * workspace does not fit. */
+int swj_create(swj_ctx **ctx, const swj_mesh *mesh, double F, double eps,
+               const swj_opts *opts, void *stream);
+
+/* Free the context and its device workspace (synchronises its stream). */
+void swj_destroy(swj_ctx *ctx);
+
+/* Change F and eps.  A new F invalidates the preconditioner (it depends on
+ * the mesh and F only, Appendix B); the next solve or precond call rebuilds
+ * it. */
+int swj_set_params(swj_ctx *ctx, double F, double eps);
+
+/* Replace the options (same validation as swj_create).  A new block_bw
+ * invalidates the preconditioner. */
+int swj_set_opts(swj_ctx *ctx, const swj_opts *opts);
+
+/* Bytes of device workspace the context holds. */
+size_t swj_workspace_bytes(const swj_ctx *ctx);
+
+/* u_dev <- the flat-surface initial guess of Section 4.1: phi_{1,l} = x1,
+ * (phi_x)_{k,l} = 1, zeta_{1,l} = 0, (zeta_x)_{k,l} = 0.  Async. */
+int swj_initial_guess_flat(swj_ctx *ctx, double *u_dev);
+
+/* E_dev <- E(u_dev) (Section 3, Appendix A order), with the all-pairs sum in
+ * `precision` (SWJ_FP64 or SWJ_FP32).  Steps: trapezoidal integration of
+ * zeta and phi along x (Eq. zetaapprox), cubic-spline slopes along y
+ * (clamped zero slope at y1 = 0, not-a-knot at y_M), half-mesh values,
+ * E1 (Eq. freeSurfCond), the singularity-subtracted boundary integral with
+ * the closed-form integral I of S2 (Eqs. IntegroEqn, S2, IS2) and trapezoid
+ * weights, E3..E6 (Eq. numUpRadiation).  u_dev and E_dev may not alias.
+ * Async. */
+int swj_residual(swj_ctx *ctx, const double *u_dev, double *E_dev, int precision);
+
+/* Jv_dev <- (E(u + h v) - E(u)) / h, Eq. JvApprox with the caller's v
+ * (apply swj_precond_apply first for J P^-1 v).  Eu_dev must hold E(u) in
+ * the same precision; h = opts.fd_h, or when 0 the rule noted in swj_opts
+ * with eps_mach of `precision`.  Async. */
+int swj_jvp(swj_ctx *ctx, const double *u_dev, const double *Eu_dev,
+            const double *v_dev, double *Jv_dev, int precision);
+
+/* Build and factor the preconditioner P for the context's mesh, F and
+ * block_bw: the linear Jacobian of Appendix B (Eqs. PreA-PreD plus the
+ * radiation rows), its zeta-zeta block truncated to the block band, factored
+ * through the Schur complement S = D - C A^-1 B (Appendix C) with a block LU
+ * of S in FP64.  Synchronous. */
+int swj_precond_setup(swj_ctx *ctx);
+
+/* r_dev <- P^-1 b_dev by the three-stage Schur solve of Appendix C.  Builds
+ * P first if needed.  b_dev and r_dev may alias.  Async (synchronous when it
+ * had to build P). */
+int swj_precond_apply(swj_ctx *ctx, const double *b_dev, double *r_dev);
+
+/* Solve E(u) = 0 by damped inexact Newton (Section 4.1) with right-
+ * preconditioned restarted GMRES and FD Jacobian-vector products
+ * (Eq. JvApprox), starting from u_dev_inout; on return it holds the last
+ * iterate.  stats may be NULL.  Returns SWJ_OK when ||E||_inf < ftol_inf
+ * (FP64 mode) or refine_tol_inf (MIXED mode, measured on the FP64 residual),
+ * else SWJ_ENOTCONV / SWJ_ELINESEARCH / SWJ_ENAN.  Synchronous. */
+int swj_solve(swj_ctx *ctx, double *u_dev_inout, swj_stats *stats);
+
+/* zeta_dev, phi_dev <- zeta and phi on the mesh ([M][N] row-major, index
+ * (l-1) N + (k-1)) rebuilt from u by Eq. zetaapprox.  Either may be NULL.
+ * Async. */
+int swj_unpack(swj_ctx *ctx, const double *u_dev, double *zeta_dev, double *phi_dev);
+
+/* Diagnostic view of the mesh step for u_dev: out_dev receives, each as an
+ * [M][N] array in this order, zeta, g = phi - x, zeta_y, g_y (= phi_y), and
+ * then, each as an [M][N-1] array, zeta*, g*, zeta_x*, zeta_y* and I (the
+ * closed-form integral of S2, Eq. IS2), all FP64.  out_dev must hold
+ * 4NM + 5(N-1)M doubles.  Async. */
+int swj_surface(swj_ctx *ctx, const double *u_dev, double *out_dev);
+
+/* Block until the context's stream is idle; returns SWJ_ECUDA if a kernel
+ * failed. */
+int swj_sync(swj_ctx *ctx);
+
+/* Human-readable name of a status code (static storage). */
+const char *swj_strerror(int status);
+
+/* Library version string. */
+const char *swj_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SWJ_H */

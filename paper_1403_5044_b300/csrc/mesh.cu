@@ -1,0 +1,297 @@
+// Mesh step of the residual E(u), all in FP64 (Section 3):
+//   * zeta and g = phi - x along x by the trapezoidal rule (Eq. zetaapprox),
+//     as a warp-wide prefix sum per mesh row;
+//   * zeta_y and g_y (= phi_y) at the nodes from the cubic spline along y,
+//     clamped (zero slope) at y1 = 0 and not-a-knot at y_M, one Thomas sweep
+//     per mesh column;
+//   * half-mesh values, the free-surface rows E1 (Eq. freeSurfCond), the
+//     radiation rows E3..E6 (Eq. numUpRadiation), and the per-target part of
+//     E2 that needs no pair sum: 2 pi g* + eps / r_source - zeta_x* I, with I
+//     the closed-form integral of S2 over the mesh rectangle (Eq. IS2);
+//   * the source and target records read by the all-pairs kernels;
+//   * assembly of E2 = (that part) - (all-pairs sum) in Appendix A order.
+#include "swj_internal.h"
+#include "closed_form.cuh"
+#include <math.h>
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+// Warp per mesh row.  Rows 0..M-1 integrate phi_x - 1 from g_1 = phi_1 - x1
+// (so the result is g = phi - x exactly as the trapezoidal rule integrates
+// the constant 1 exactly); rows M..2M-1 integrate zeta_x from zeta_1.
+__global__ void k_integrate(int N, int M, int H, double x1, double dx,
+                            const double *__restrict__ u, double *__restrict__ zeta,
+                            double *__restrict__ g)
+{
+    int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    int lane = threadIdx.x & 31;
+    if (warp >= 2 * M) return;
+    bool isz = warp >= M;
+    int l = isz ? warp - M : warp;
+    const double *row = u + (isz ? H : 0) + (size_t)l * (N + 1);
+    double *out = (isz ? zeta : g) + (size_t)l * N;
+    double shift = isz ? 0.0 : 1.0;
+    double f1 = isz ? row[0] : row[0] - x1;
+    double hdx = 0.5 * dx;
+    int per = (N + 31) / 32;
+    int k0 = lane * per, k1 = min(k0 + per, N);
+    // increment from node k to node k+1 (0-based, k <= N-2)
+    auto inc = [&](int k) { return hdx * ((row[1 + k] - shift) + (row[2 + k] - shift)); };
+    double run = 0.0;
+    for (int k = k0; k < k1; ++k)
+        if (k <= N - 2) run += inc(k);
+    double incl = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        double v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    double v = f1 + (incl - run);
+    for (int k = k0; k < k1; ++k) {
+        out[k] = v;
+        if (k <= N - 2) v += inc(k);
+    }
+}
+
+// Thread per mesh column k (first N threads: zeta, next N: g).  Slopes m_j of
+// the cubic spline through f_0..f_{M-1} (uniform spacing h):
+//   m_0 = 0                                          (even extension at y = 0)
+//   m_{j-1} + 4 m_j + m_{j+1} = 3 (f_{j+1} - f_{j-1}) / h     (C2 continuity)
+//   2 m_{M-2} + m_{M-1} = (d_{M-3} + 5 d_{M-2}) / 2,  d_j = (f_{j+1} - f_j)/h
+// (the last row is the not-a-knot condition at y_{M-2} with m_{M-3}
+// eliminated through the row above it).  cp, a, inv are the forward-sweep
+// coefficients of this fixed matrix.
+__global__ void k_spline(int N, int M, double hy, const double *__restrict__ cp,
+                         const double *__restrict__ a, const double *__restrict__ inv,
+                         const double *__restrict__ zeta, const double *__restrict__ g,
+                         double *__restrict__ zetay, double *__restrict__ gy)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 2 * N) return;
+    int k = t % N;
+    const double *f = (t < N ? zeta : g) + k;
+    double *m = (t < N ? zetay : gy) + k;
+    double rh = 1.0 / hy;
+    double dp = 0.0;
+    m[0] = 0.0;
+    for (int j = 1; j < M; ++j) {
+        double d;
+        if (j < M - 1) {
+            d = 3.0 * (f[(size_t)(j + 1) * N] - f[(size_t)(j - 1) * N]) * rh;
+        } else {
+            double d3 = (f[(size_t)(M - 2) * N] - f[(size_t)(M - 3) * N]) * rh;
+            double d2 = (f[(size_t)(M - 1) * N] - f[(size_t)(M - 2) * N]) * rh;
+            d = 0.5 * (d3 + 5.0 * d2);
+        }
+        dp = (d - a[j] * dp) * inv[j];
+        m[(size_t)j * N] = dp;
+    }
+    double next = m[(size_t)(M - 1) * N];
+    for (int j = M - 2; j >= 1; --j) {
+        next = m[(size_t)j * N] - cp[j] * next;
+        m[(size_t)j * N] = next;
+    }
+}
+
+// Thread per half-mesh target t = l (N-1) + k.
+__global__ void k_targets(int N, int M, int H, double x1, double dx, double dy, double F,
+                          double eps, double nrad, const double *__restrict__ u,
+                          const double *__restrict__ zeta, const double *__restrict__ g,
+                          const double *__restrict__ zetay, const double *__restrict__ gy,
+                          double *__restrict__ E, double *__restrict__ e2part,
+                          double *__restrict__ Ival, TgtArrays<double> t64,
+                          TgtArrays<float> t32)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    int T = (N - 1) * M;
+    if (t >= T) return;
+    int k = t % (N - 1), l = t / (N - 1);
+    size_t n0 = (size_t)l * N + k;
+    const double *urow_p = u + (size_t)l * (N + 1);
+    const double *urow_z = u + H + (size_t)l * (N + 1);
+    double zs = 0.5 * (zeta[n0] + zeta[n0 + 1]);
+    double gs = 0.5 * (g[n0] + g[n0 + 1]);
+    double zy = 0.5 * (zetay[n0] + zetay[n0 + 1]);
+    double py = 0.5 * (gy[n0] + gy[n0 + 1]);
+    double zx = 0.5 * (urow_z[1 + k] + urow_z[2 + k]);
+    double px = 0.5 * (urow_p[1 + k] + urow_p[2 + k]);
+    // E1: free-surface condition at the half-mesh point
+    double zx2 = zx * zx, zy2 = zy * zy;
+    double num = (1.0 + zx2) * py * py + (1.0 + zy2) * px * px - 2.0 * zx * zy * px * py;
+    double E1 = 0.5 * num / (1.0 + zx2 + zy2) + zs / (F * F) - 0.5;
+    // I: closed-form integral of S2 over [x1, xN] x [0, yM], direct + image
+    double A = 1.0 + zx2, B = 2.0 * zx * zy, C = 1.0 + zy2;
+    double xt = x1 + ((double)k + 0.5) * dx;
+    double yt = (double)l * dy;
+    double I = swj_I_S2(A, B, C, N, M, k, l, dx, dy);
+    double zp1 = zs + 1.0;
+    double src = eps / sqrt(xt * xt + yt * yt + zp1 * zp1);
+    e2part[t] = 2.0 * kPi * gs + src - zx * I;
+    Ival[t] = I;
+    E[(size_t)l * (N + 1) + 2 + k] = E1;
+    // records of the pair kernels
+    t64.tk[t] = (double)k + 0.5; t64.tl[t] = (double)l;
+    t64.zeta[t] = zs; t64.g[t] = gs; t64.zx[t] = zx;
+    t64.A[t] = A; t64.B[t] = B; t64.C[t] = C;
+    t32.tk[t] = (float)k + 0.5f; t32.tl[t] = (float)l;
+    t32.zeta[t] = (float)zs; t32.g[t] = (float)gs; t32.zx[t] = (float)zx;
+    t32.A[t] = (float)A; t32.B[t] = (float)B; t32.C[t] = (float)C;
+    if (k == 0) {
+        // radiation rows at x = x1 (forward difference for the second derivative)
+        double phi1 = urow_p[0], pxa = urow_p[1], pxb = urow_p[2];
+        double z1 = urow_z[0], zxa = urow_z[1], zxb = urow_z[2];
+        E[(size_t)l * (N + 1)] = x1 * (pxa - 1.0) + nrad * (phi1 - x1);
+        E[(size_t)l * (N + 1) + 1] = x1 * (pxb - pxa) / dx + nrad * (pxa - 1.0);
+        E[H + (size_t)l * (N + 1)] = x1 * zxa + nrad * z1;
+        E[H + (size_t)l * (N + 1) + 1] = x1 * (zxb - zxa) / dx + nrad * zxa;
+    }
+}
+
+// Thread per mesh node s = j N + i.
+__global__ void k_sources(int N, int M, int H, double dx, double dy, const double *__restrict__ u,
+                          const double *__restrict__ zeta, const double *__restrict__ g,
+                          const double *__restrict__ zetay, SrcRec<double> *__restrict__ s64,
+                          SrcRec<float> *__restrict__ s32)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= N * M) return;
+    int i = s % N, j = s / N;
+    double ci = (i == 0 || i == N - 1) ? 0.5 : 1.0;
+    double cj = (j == 0 || j == M - 1) ? 0.5 : 1.0;
+    SrcRec<double> r;
+    r.zeta = zeta[s];
+    r.zx = u[H + (size_t)j * (N + 1) + 1 + i];
+    r.zy = zetay[s];
+    r.g = g[s];
+    r.w = dx * dy * ci * cj;
+    r.si = (double)i;
+    r.sj = (double)j;
+    r.pad = 0.0;
+    s64[s] = r;
+    SrcRec<float> q;
+    q.zeta = (float)r.zeta; q.zx = (float)r.zx; q.zy = (float)r.zy; q.g = (float)r.g;
+    q.w = (float)r.w; q.si = (float)i; q.sj = (float)j; q.pad = 0.f;
+    s32[s] = q;
+}
+
+// Thread per target: E2 = (2 pi g* + src - zx* I) - sum over source chunks.
+__global__ void k_assemble(int N, int M, int H, int P, const double *__restrict__ partial,
+                           const double *__restrict__ e2part, double *__restrict__ E)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    int T = (N - 1) * M;
+    if (t >= T) return;
+    double s = 0.0;
+    for (int p = 0; p < P; ++p) s += partial[(size_t)p * T + t];
+    int k = t % (N - 1), l = t / (N - 1);
+    E[H + (size_t)l * (N + 1) + 2 + k] = e2part[t] - s;
+}
+
+__global__ void k_flat(int N, int M, int H, double x1, double *__restrict__ u)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 2 * H) return;
+    int r = i % (N + 1);
+    double v;
+    if (i < H) v = (r == 0) ? x1 : 1.0;
+    else v = 0.0;
+    u[i] = v;
+}
+
+__global__ void k_unpack(int N, int M, double x1, double dx, const double *__restrict__ zeta,
+                         const double *__restrict__ g, double *__restrict__ zo,
+                         double *__restrict__ po)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= N * M) return;
+    int i = s % N;
+    if (zo) zo[s] = zeta[s];
+    if (po) po[s] = g[s] + (x1 + (double)i * dx);
+}
+
+__global__ void k_surface(int N, int M, const double *zeta, const double *g, const double *zetay,
+                          const double *gy, TgtArrays<double> t64, const double *Ival,
+                          double *out)
+{
+    int S = N * M, T = (N - 1) * M;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < S) {
+        out[i] = zeta[i];
+        out[S + i] = g[i];
+        out[2 * S + i] = zetay[i];
+        out[3 * S + i] = gy[i];
+    }
+    if (i < T) {
+        double *o = out + 4 * (size_t)S;
+        o[i] = t64.zeta[i];
+        o[T + i] = t64.g[i];
+        o[2 * T + i] = t64.zx[i];
+        int k = i % (N - 1), l = i / (N - 1);
+        size_t n0 = (size_t)l * N + k;
+        o[3 * T + i] = 0.5 * (zetay[n0] + zetay[n0 + 1]);
+        o[4 * T + i] = Ival[i];
+    }
+}
+
+inline int nblk(long n, int b) { return (int)((n + b - 1) / b); }
+
+}  // namespace
+
+void swj_spline_coeffs(int M, double *cp, double *a, double *inv)
+{
+    // tridiagonal matrix of k_spline: row 0 (1 | 0), rows 1..M-2 (1 4 1), row M-1 (2 1 | -)
+    cp[0] = 0.0; a[0] = 0.0; inv[0] = 1.0;
+    for (int j = 1; j < M; ++j) {
+        double aj = (j < M - 1) ? 1.0 : 2.0;
+        double bj = (j < M - 1) ? 4.0 : 1.0;
+        double cj = (j < M - 1) ? 1.0 : 0.0;
+        double den = bj - aj * cp[j - 1];
+        a[j] = aj;
+        inv[j] = 1.0 / den;
+        cp[j] = cj / den;
+    }
+}
+
+void swj_launch_mesh_step(swj_ctx *c, const double *u, double *E)
+{
+    const swj_mesh &m = c->mesh;
+    cudaStream_t st = c->stream;
+    k_integrate<<<nblk(2L * c->M * 32, 256), 256, 0, st>>>(c->N, c->M, c->H, m.x1, m.dx, u,
+                                                           c->zeta, c->g);
+    k_spline<<<nblk(2L * c->N, 128), 128, 0, st>>>(c->N, c->M, m.dy, c->spl_cp, c->spl_a,
+                                                    c->spl_inv, c->zeta, c->g, c->zetay, c->gy);
+    k_targets<<<nblk(c->T, 128), 128, 0, st>>>(c->N, c->M, c->H, m.x1, m.dx, m.dy, c->F, c->eps,
+                                                m.n_rad, u, c->zeta, c->g, c->zetay, c->gy, E,
+                                                c->e2part, c->Ival, c->tgt64, c->tgt32);
+    k_sources<<<nblk(c->S, 256), 256, 0, st>>>(c->N, c->M, c->H, m.dx, m.dy, u, c->zeta, c->g,
+                                               c->zetay, c->src64, c->src32);
+}
+
+void swj_launch_assemble(swj_ctx *c, double *E, int P)
+{
+    k_assemble<<<nblk(c->T, 256), 256, 0, c->stream>>>(c->N, c->M, c->H, P, c->partial,
+                                                        c->e2part, E);
+}
+
+void swj_launch_flat(swj_ctx *c, double *u)
+{
+    k_flat<<<nblk(c->nu, 256), 256, 0, c->stream>>>(c->N, c->M, c->H, c->mesh.x1, u);
+}
+
+void swj_launch_unpack(swj_ctx *c, const double *u, double *zo, double *po)
+{
+    const swj_mesh &m = c->mesh;
+    k_integrate<<<nblk(2L * c->M * 32, 256), 256, 0, c->stream>>>(c->N, c->M, c->H, m.x1, m.dx,
+                                                                   u, c->zeta, c->g);
+    k_unpack<<<nblk(c->S, 256), 256, 0, c->stream>>>(c->N, c->M, m.x1, m.dx, c->zeta, c->g, zo,
+                                                      po);
+}
+
+void swj_launch_surface(swj_ctx *c, double *out)
+{
+    int n = c->S > c->T ? c->S : c->T;
+    k_surface<<<nblk(n, 256), 256, 0, c->stream>>>(c->N, c->M, c->zeta, c->g, c->zetay, c->gy,
+                                                    c->tgt64, c->Ival, out);
+}

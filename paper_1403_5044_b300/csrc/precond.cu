@@ -1,0 +1,467 @@
+// Preconditioner of Section 4.2 / Appendices B-C.
+//
+// P is the Jacobian of the linearised discrete system (the eps -> 0 problem
+// of Section 2.3 discretised as in Section 3), in Appendix A order:
+//
+//   P = [ A  B ]   rows  (E3, E4, E1) per y-row      columns (phi_1, phi_x) per y-row
+//       [ C  D ]         (E5, E6, E2) per y-row              (zeta_1, zeta_x) per y-row
+//
+// A, B, C are block diagonal with one repeated (N+1) x (N+1) block
+// (Eqs. PreA, PreB, PreC plus the radiation rows); D is dense (Eq. PreD) and
+// is truncated to |l - m| <= h = (b - 1)/2 blocks.  The entries of B and C
+// are written from the trapezoidal rule itself: d zeta*_k / d (zeta_x)_n =
+// dx/2 (c_k(n) + c_{k+1}(n)) with c_m(n) the trapezoid coefficient of
+// (zeta_x)_n in zeta_m (Eq. zetaapprox), which reproduces the case lists of
+// PreB/PreC.  The diagonal correction of PreD needs, per target, the
+// trapezoid sum of w K3 over all sources and I of the flat surface.
+//
+// Factorisation (Appendix C): S = D - C A^-1 B differs from D only in its
+// diagonal blocks, by the one block G = C A^-1 B.  S is factored by a block
+// LU with the block band kept (no fill outside it), partial pivoting inside
+// each diagonal block, explicit inverses of the pivot blocks, and
+// W_ik = inv_i U_ik stored for the backward sweep.  Everything is FP64.
+//
+// Apply, r = P^-1 b, by the three stages of Appendix C:
+//   t2 = b2 - C A^-1 b1;  s2 = S^-1 t2;  r1 = A^-1 b1 - A^-1 B s2;  r2 = s2.
+// Because A, B, C repeat per y-row, the stages with them are one GEMM each of
+// the M x (N+1) matrix of per-row vectors with a transposed (N+1)^2 block.
+#include "swj_internal.h"
+#include "closed_form.cuh"
+#include <vector>
+#include <string.h>
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kMaxTerms = 64;
+
+inline int nblk(long n, int b) { return (int)((n + b - 1) / b); }
+
+// coefficient of (zeta_x)_n in zeta_m / dx (1-based m, n): Eq. zetaapprox
+// gives zeta_m = zeta_1 + dx (zx_1/2 + zx_2 + ... + zx_{m-1} + zx_m/2), m >= 2.
+__device__ __forceinline__ double trap_coef(int m, int n)
+{
+    if (m == 1) return 0.0;
+    if (n == 1 || n == m) return 0.5;
+    return (n < m) ? 1.0 : 0.0;
+}
+
+// Dense (N+1)^2 blocks A, B, C (row-major).  Rows: 0 = E3 (E5), 1 = E4 (E6),
+// 1 + k = E1_k (E2_k), k = 1..N-1.  Columns: 0 = phi_1 (zeta_1), n = phi_x,n (zeta_x,n).
+__global__ void k_build_ABC(int N, double x1, double dx, double nrad, double F,
+                            double *__restrict__ A, double *__restrict__ B,
+                            double *__restrict__ C)
+{
+    int n1 = N + 1;
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n1 * n1) return;
+    int r = e / n1, c = e % n1;
+    double a = 0.0, b = 0.0, cc = 0.0;
+    if (r == 0) {
+        if (c == 0) a = nrad;
+        if (c == 1) a = x1;
+    } else if (r == 1) {
+        if (c == 1) a = nrad - x1 / dx;
+        if (c == 2) a = x1 / dx;
+    } else {
+        int k = r - 1;
+        if (c == k || c == k + 1) a = 0.5;                 // E1_k = phi_x*_k + ...
+        double s = (c == 0) ? 1.0 : 0.5 * dx * (trap_coef(k, c) + trap_coef(k + 1, c));
+        b = s / (F * F);                                    // zeta*_k / F^2 in E1_k
+        cc = 2.0 * kPi * s;                                 // 2 pi phi*_k in E2_k
+    }
+    A[e] = a;
+    B[e] = b;
+    C[e] = cc;
+}
+
+// Forward-sweep coefficients c'_r of the tridiagonal block A (one thread).
+__global__ void k_tri_coef(int n1, const double *__restrict__ A, double *__restrict__ cp)
+{
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    double prev = 0.0;
+    for (int r = 0; r < n1; ++r) {
+        double sub = r > 0 ? A[r * n1 + r - 1] : 0.0;
+        double dia = A[r * n1 + r];
+        double sup = r + 1 < n1 ? A[r * n1 + r + 1] : 0.0;
+        double den = dia - sub * prev;
+        prev = sup / den;
+        cp[r] = prev;
+    }
+}
+
+// X = A^-1 Rhs for all ncol columns (Thomas algorithm, one thread per column;
+// Rhs == nullptr means the identity).  X and Rhs are n1 x ncol row-major.
+__global__ void k_tri_cols(int n1, int ncol, const double *__restrict__ A,
+                           const double *__restrict__ cp, const double *Rhs, double *X)
+{
+    int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= ncol) return;
+    double dprev = 0.0;
+    for (int r = 0; r < n1; ++r) {
+        double sub = r > 0 ? A[r * n1 + r - 1] : 0.0;
+        double dia = A[r * n1 + r];
+        double den = dia - sub * (r > 0 ? cp[r - 1] : 0.0);
+        double d = Rhs ? Rhs[(size_t)r * ncol + col] : (r == col ? 1.0 : 0.0);
+        dprev = (d - sub * dprev) / den;
+        X[(size_t)r * ncol + col] = dprev;
+    }
+    double next = X[(size_t)(n1 - 1) * ncol + col];
+    for (int r = n1 - 2; r >= 0; --r) {
+        next = X[(size_t)r * ncol + col] - cp[r] * next;
+        X[(size_t)r * ncol + col] = next;
+    }
+}
+
+__global__ void k_transpose(int n, const double *__restrict__ in, double *__restrict__ out)
+{
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * n) return;
+    int r = e / n, c = e % n;
+    out[(size_t)c * n + r] = in[e];
+}
+
+// Records of the flat state (zeta = 0, g = 0, zeta_x = 1 at the sources,
+// zeta_x* = 0, A = C = 1, B = 0 at the targets) for which the pair kernel's
+// sum is sum_s w_s K2 = sum_s w_s K3.
+template <typename T>
+__global__ void k_flat_records(int N, int M, double dx, double dy, SrcRec<T> *src,
+                               TgtArrays<T> tg)
+{
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    int S = N * M, Tn = (N - 1) * M;
+    if (e < S) {
+        int i = e % N, j = e / N;
+        double ci = (i == 0 || i == N - 1) ? 0.5 : 1.0;
+        double cj = (j == 0 || j == M - 1) ? 0.5 : 1.0;
+        SrcRec<T> r;
+        r.zeta = T(0); r.zx = T(1); r.zy = T(0); r.g = T(0);
+        r.w = (T)(dx * dy * ci * cj); r.si = (T)i; r.sj = (T)j; r.pad = T(0);
+        src[e] = r;
+    }
+    if (e < Tn) {
+        int k = e % (N - 1), l = e / (N - 1);
+        tg.tk[e] = (T)k + (T)0.5; tg.tl[e] = (T)l;
+        tg.zeta[e] = T(0); tg.g[e] = T(0); tg.zx[e] = T(0);
+        tg.A[e] = T(1); tg.B[e] = T(0); tg.C[e] = T(1);
+    }
+}
+
+// diag[t] = (1/2) sum_s w K3 - (1/2) I_flat, the PreD correction of target t.
+__global__ void k_diag_corr(int N, int M, int P, double dx, double dy,
+                            const double *__restrict__ partial, double *__restrict__ out)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    int Tn = (N - 1) * M;
+    if (t >= Tn) return;
+    double s = 0.0;
+    for (int p = 0; p < P; ++p) s += partial[(size_t)p * Tn + t];
+    int k = t % (N - 1), l = t / (N - 1);
+    double I = swj_I_S2(1.0, 0.0, 1.0, N, M, k, l, dx, dy);
+    out[t] = 0.5 * s - 0.5 * I;
+}
+
+// Band of S: block (l, m = l - h + slot) of D minus G on the diagonal blocks.
+__global__ void k_fill_band(int N, int M, int h, double x1, double dx, double dy, double nrad,
+                            const double *__restrict__ diag, const double *__restrict__ G,
+                            double *__restrict__ band)
+{
+    const size_t n1 = N + 1, nb = 2 * h + 1;
+    const size_t total = (size_t)M * nb * n1 * n1;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        int c = (int)(e % n1);
+        int r = (int)((e / n1) % n1);
+        int slot = (int)((e / (n1 * n1)) % nb);
+        int l = (int)(e / (n1 * n1 * nb));
+        int m = l - h + slot;
+        double v = 0.0;
+        if (m >= 0 && m < M) {
+            if (r == 0) {                      // E5_l: x1 zeta_x,1 + n zeta_1
+                if (m == l) v = (c == 0) ? nrad : (c == 1 ? x1 : 0.0);
+            } else if (r == 1) {               // E6_l: x1 (zx_2 - zx_1)/dx + n zx_1
+                if (m == l) v = (c == 1) ? nrad - x1 / dx : (c == 2 ? x1 / dx : 0.0);
+            } else if (c >= 1) {               // E2_k,l versus (zeta_x)_{c, m}
+                int k = r - 1, i = c - 1;
+                double ci = (i == 0 || i == N - 1) ? 0.5 : 1.0;
+                double cj = (m == 0 || m == M - 1) ? 0.5 : 1.0;
+                double w = dx * dy * ci * cj;
+                double ddx = ((double)i - ((double)(k - 1) + 0.5)) * dx;
+                double ddy = (double)(m - l) * dy, ddyp = (double)(m + l) * dy;
+                double K3 = 1.0 / sqrt(ddx * ddx + ddy * ddy) + 1.0 / sqrt(ddx * ddx + ddyp * ddyp);
+                v = -w * K3;
+                if (m == l && (c == k || c == k + 1)) v += diag[(size_t)l * (N - 1) + (k - 1)];
+            }
+            if (m == l) v -= G[(size_t)r * n1 + c];
+        }
+        band[e] = v;
+    }
+}
+
+struct BandTerms {
+    const double *mat[kMaxTerms];
+    const double *vec[kMaxTerms];
+};
+
+// out = (inv ? inv * base : base) - sum_q mat[q] * vec[q]   (n1-vectors, n1 x n1 blocks)
+// one warp per output row.
+__global__ void k_band_step(int n1, int nterms, BandTerms bt, const double *__restrict__ base,
+                            const double *__restrict__ inv, double *__restrict__ out)
+{
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (warp >= n1) return;
+    const size_t r = warp;
+    double s = 0.0;
+    if (inv) {
+        for (int c = lane; c < n1; c += 32) s = fma(inv[r * n1 + c], base[c], s);
+    } else if (lane == 0) {
+        s = base[r];
+    }
+    for (int q = 0; q < nterms; ++q) {
+        const double *Mq = bt.mat[q] + r * n1;
+        const double *vq = bt.vec[q];
+        for (int c = lane; c < n1; c += 32) s = fma(-Mq[c], vq[c], s);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[r] = s;
+}
+
+// x_l = inv_l t_l for every block row l (block-diagonal S, h = 0).
+__global__ void k_blockdiag_gemv(int n1, int M, const double *__restrict__ band, size_t bstride,
+                                 const double *__restrict__ t, double *__restrict__ x)
+{
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (warp >= n1 * M) return;
+    int l = warp / n1, r = warp % n1;
+    const double *inv = band + (size_t)l * bstride + (size_t)r * n1;
+    const double *tl = t + (size_t)l * n1;
+    double s = 0.0;
+    for (int c = lane; c < n1; c += 32) s = fma(inv[c], tl[c], s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) x[(size_t)l * n1 + r] = s;
+}
+
+inline double *blk(swj_ctx *c, int l, int m)
+{
+    size_t n2 = (size_t)c->n1 * c->n1;
+    int slot = m - l + c->pc_h;
+    return c->pc_band + ((size_t)l * c->pc_nb + slot) * n2;
+}
+
+void free_pc(swj_ctx *c)
+{
+    double **bufs[] = {&c->pc_Ainv, &c->pc_AinvB, &c->pc_CAinv, &c->pc_G, &c->pc_A, &c->pc_B,
+                       &c->pc_C, &c->pc_tmp, &c->pc_band, &c->pc_sumK3, &c->pc_t1, &c->pc_t2};
+    for (double **b : bufs) {
+        if (*b) cudaFree(*b);
+        *b = nullptr;
+    }
+    if (c->pc_info) cudaFree(c->pc_info);
+    c->pc_info = nullptr;
+    if (c->pc_ptrs) cudaFree(c->pc_ptrs);
+    c->pc_ptrs = nullptr;
+    c->pc_ptrs_cap = 0;
+    c->pc_ready = 0;
+}
+
+}  // namespace
+
+void swj_pc_free(swj_ctx *c) { free_pc(c); }
+
+int swj_pc_setup(swj_ctx *c)
+{
+    const int N = c->N, M = c->M, n1 = c->n1;
+    const swj_mesh &m = c->mesh;
+    cudaStream_t st = c->stream;
+    int b = c->opts.block_bw;
+    int h = (b == 0) ? M - 1 : (b - 1) / 2;
+    if (h > M - 1) h = M - 1;
+    if (h > kMaxTerms) return SWJ_EINVAL;
+    const size_t n2 = (size_t)n1 * n1;
+    const int nb = 2 * h + 1;
+    if (!c->pc_band || c->pc_h != h) {
+        free_pc(c);
+        c->pc_h = h;
+        c->pc_nb = nb;
+        size_t sz[] = {n2, n2, n2, n2, n2, n2, n2, (size_t)(h > 0 ? h : 1) * n2,
+                       (size_t)M * nb * n2, (size_t)c->T, (size_t)c->H, (size_t)c->H};
+        double **bufs[] = {&c->pc_Ainv, &c->pc_AinvB, &c->pc_CAinv, &c->pc_G, &c->pc_A,
+                           &c->pc_B, &c->pc_C, &c->pc_tmp, &c->pc_band, &c->pc_sumK3,
+                           &c->pc_t1, &c->pc_t2};
+        for (int i = 0; i < 12; ++i)
+            if (cudaMalloc(bufs[i], sz[i] * sizeof(double)) != cudaSuccess) {
+                free_pc(c);
+                return SWJ_ENOMEM;
+            }
+        if (cudaMalloc(&c->pc_info, (size_t)M * sizeof(int)) != cudaSuccess) {
+            free_pc(c);
+            return SWJ_ENOMEM;
+        }
+    }
+    c->pc_ready = 0;
+    // --- repeated blocks A, B, C and their products (Appendix C)
+    k_build_ABC<<<nblk((long)n2, 256), 256, 0, st>>>(N, m.x1, m.dx, m.n_rad, c->F, c->pc_A,
+                                                     c->pc_B, c->pc_C);
+    double *cpv = c->pc_t1;   // n1 scratch
+    k_tri_coef<<<1, 1, 0, st>>>(n1, c->pc_A, cpv);
+    double *Ainv = c->pc_tmp;            // untransposed products in scratch
+    k_tri_cols<<<nblk(n1, 128), 128, 0, st>>>(n1, n1, c->pc_A, cpv, nullptr, Ainv);
+    double *AinvB = c->pc_G;             // temporarily
+    k_tri_cols<<<nblk(n1, 128), 128, 0, st>>>(n1, n1, c->pc_A, cpv, c->pc_B, AinvB);
+    // CAinv and G = C (A^-1 B); store transposes for the row-major apply GEMMs
+    double *CAinv = c->pc_band;          // band not filled yet: use as scratch (>= 2 n2)
+    double *Gtmp = c->pc_band + n2;
+    swj_dgemm(st, n1, n1, n1, 1.0, c->pc_C, n1, Ainv, n1, 0.0, CAinv, n1);
+    swj_dgemm(st, n1, n1, n1, 1.0, c->pc_C, n1, AinvB, n1, 0.0, Gtmp, n1);
+    k_transpose<<<nblk((long)n2, 256), 256, 0, st>>>(n1, Ainv, c->pc_Ainv);
+    k_transpose<<<nblk((long)n2, 256), 256, 0, st>>>(n1, AinvB, c->pc_AinvB);
+    k_transpose<<<nblk((long)n2, 256), 256, 0, st>>>(n1, CAinv, c->pc_CAinv);
+    SWJ_CUDA_TRY(cudaMemcpyAsync(c->pc_G, Gtmp, n2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    // --- PreD diagonal correction: trapezoid sum of w K3 and I of the flat surface
+    int prec = (c->opts.solve_mode == SWJ_SOLVE_FP64) ? SWJ_FP64 : SWJ_FP32;
+    PairPlan pl = swj_pair_plan(c, prec);
+    int ne = c->S > c->T ? c->S : c->T;
+    if (prec == SWJ_FP64) {
+        k_flat_records<double><<<nblk(ne, 256), 256, 0, st>>>(N, M, m.dx, m.dy, c->src64, c->tgt64);
+        swj_launch_pairs64(c, pl);
+    } else {
+        k_flat_records<float><<<nblk(ne, 256), 256, 0, st>>>(N, M, m.dx, m.dy, c->src32, c->tgt32);
+        swj_launch_pairs32(c, pl);
+    }
+    k_diag_corr<<<nblk(c->T, 256), 256, 0, st>>>(N, M, pl.P, m.dx, m.dy, c->partial, c->pc_sumK3);
+    // --- band of S
+    k_fill_band<<<4 * c->num_sms, 256, 0, st>>>(N, M, h, m.x1, m.dx, m.dy, m.n_rad, c->pc_sumK3,
+                                                c->pc_G, c->pc_band);
+    // --- block LU
+    SWJ_CUDA_TRY(cudaMemsetAsync(c->pc_info, 0, (size_t)M * sizeof(int), st));
+    const size_t bstride = (size_t)nb * n2;
+    if (h == 0) {
+        swj_block_inverse(st, n1, M, c->pc_band, bstride, c->pc_info);
+    } else {
+        // device pointer triples for every batched GEMM of the factorisation
+        std::vector<const double *> PA, PB;
+        std::vector<double *> PC;
+        std::vector<int> off2(M), cnt2(M), off3(M), cnt3(M), off4(M), cnt4(M);
+        for (int i = 0; i < M; ++i) {
+            int jmax = i + h < M - 1 ? i + h : M - 1;
+            off2[i] = (int)PA.size();
+            for (int j = i + 1; j <= jmax; ++j) {
+                PA.push_back(blk(c, j, i)); PB.push_back(blk(c, i, i));
+                PC.push_back(c->pc_tmp + (size_t)(j - i - 1) * n2);
+            }
+            cnt2[i] = (int)PA.size() - off2[i];
+            off3[i] = (int)PA.size();
+            for (int j = i + 1; j <= jmax; ++j)
+                for (int k = i + 1; k <= jmax; ++k) {
+                    PA.push_back(blk(c, j, i)); PB.push_back(blk(c, i, k));
+                    PC.push_back(blk(c, j, k));
+                }
+            cnt3[i] = (int)PA.size() - off3[i];
+            off4[i] = (int)PA.size();
+            for (int k = i + 1; k <= jmax; ++k) {
+                PA.push_back(blk(c, i, i)); PB.push_back(blk(c, i, k));
+                PC.push_back(c->pc_tmp + (size_t)(k - i - 1) * n2);
+            }
+            cnt4[i] = (int)PA.size() - off4[i];
+        }
+        int np = (int)PA.size();
+        if (c->pc_ptrs_cap < np) {
+            if (c->pc_ptrs) cudaFree(c->pc_ptrs);
+            c->pc_ptrs = nullptr;
+            if (cudaMalloc(&c->pc_ptrs, (size_t)3 * np * sizeof(double *)) != cudaSuccess) {
+                c->pc_ptrs_cap = 0;
+                return SWJ_ENOMEM;
+            }
+            c->pc_ptrs_cap = np;
+        }
+        std::vector<double *> all((size_t)3 * np);
+        for (int q = 0; q < np; ++q) {
+            all[q] = const_cast<double *>(PA[q]);
+            all[np + q] = const_cast<double *>(PB[q]);
+            all[2 * np + q] = PC[q];
+        }
+        SWJ_CUDA_TRY(cudaMemcpyAsync(c->pc_ptrs, all.data(), all.size() * sizeof(double *),
+                                     cudaMemcpyHostToDevice, st));
+        double **dA = c->pc_ptrs, **dB = c->pc_ptrs + np, **dC = c->pc_ptrs + 2 * np;
+        for (int i = 0; i < M; ++i) {
+            swj_block_inverse(st, n1, 1, blk(c, i, i), n2, c->pc_info + i);
+            if (cnt2[i]) {
+                swj_dgemm_batched(st, n1, n1, n1, 1.0, (const double *const *)(dA + off2[i]), n1,
+                                  (const double *const *)(dB + off2[i]), n1, 0.0, dC + off2[i], n1,
+                                  cnt2[i]);
+                for (int q = 0; q < cnt2[i]; ++q)
+                    SWJ_CUDA_TRY(cudaMemcpyAsync(const_cast<double *>(PA[off2[i] + q]), PC[off2[i] + q],
+                                                 n2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            }
+            if (cnt3[i])
+                swj_dgemm_batched(st, n1, n1, n1, -1.0, (const double *const *)(dA + off3[i]), n1,
+                                  (const double *const *)(dB + off3[i]), n1, 1.0, dC + off3[i], n1,
+                                  cnt3[i]);
+            if (cnt4[i]) {
+                swj_dgemm_batched(st, n1, n1, n1, 1.0, (const double *const *)(dA + off4[i]), n1,
+                                  (const double *const *)(dB + off4[i]), n1, 0.0, dC + off4[i], n1,
+                                  cnt4[i]);
+                for (int q = 0; q < cnt4[i]; ++q)
+                    SWJ_CUDA_TRY(cudaMemcpyAsync(const_cast<double *>(PB[off4[i] + q]), PC[off4[i] + q],
+                                                 n2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            }
+        }
+    }
+    std::vector<int> info(M);
+    SWJ_CUDA_TRY(cudaMemcpyAsync(info.data(), c->pc_info, (size_t)M * sizeof(int),
+                                 cudaMemcpyDeviceToHost, st));
+    SWJ_CUDA_TRY(cudaStreamSynchronize(st));
+    SWJ_CUDA_TRY(cudaGetLastError());
+    for (int i = 0; i < M; ++i)
+        if (info[i] != 0) return SWJ_ESINGULAR;
+    c->pc_ready = 1;
+    return SWJ_OK;
+}
+
+int swj_pc_apply(swj_ctx *c, const double *b, double *r)
+{
+    const int M = c->M, n1 = c->n1, H = c->H, h = c->pc_h;
+    cudaStream_t st = c->stream;
+    const size_t n2 = (size_t)n1 * n1;
+    const double *b1 = b, *b2 = b + H;
+    double *t1 = c->pc_t1, *t2 = c->pc_t2, *r2 = r + H;
+    // t2 = b2 - C A^-1 b1 ; t1 = A^-1 b1     (per-row vectors as rows of M x n1 matrices)
+    SWJ_CUDA_TRY(cudaMemcpyAsync(t2, b2, (size_t)H * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    swj_dgemm(st, M, n1, n1, -1.0, b1, n1, c->pc_CAinv, n1, 1.0, t2, n1);
+    swj_dgemm(st, M, n1, n1, 1.0, b1, n1, c->pc_Ainv, n1, 0.0, t1, n1);
+    // s2 = S^-1 t2 into r2
+    if (h == 0) {
+        k_blockdiag_gemv<<<nblk((long)n1 * M * 32, 256), 256, 0, st>>>(n1, M, c->pc_band, n2, t2, r2);
+    } else {
+        BandTerms bt;
+        int wb = nblk((long)n1 * 32, 256);
+        for (int i = 1; i < M; ++i) {             // forward: y_i = t_i - sum_j L_ij y_j (in place)
+            int j0 = i - h > 0 ? i - h : 0, nt = 0;
+            for (int j = j0; j < i; ++j) {
+                bt.mat[nt] = blk(c, i, j);
+                bt.vec[nt] = t2 + (size_t)j * n1;
+                ++nt;
+            }
+            k_band_step<<<wb, 256, 0, st>>>(n1, nt, bt, t2 + (size_t)i * n1, nullptr,
+                                            t2 + (size_t)i * n1);
+        }
+        for (int i = M - 1; i >= 0; --i) {        // backward: x_i = inv_i y_i - sum_k W_ik x_k
+            int kmax = i + h < M - 1 ? i + h : M - 1, nt = 0;
+            for (int k = i + 1; k <= kmax; ++k) {
+                bt.mat[nt] = blk(c, i, k);
+                bt.vec[nt] = r2 + (size_t)k * n1;
+                ++nt;
+            }
+            k_band_step<<<wb, 256, 0, st>>>(n1, nt, bt, t2 + (size_t)i * n1, blk(c, i, i),
+                                            r2 + (size_t)i * n1);
+        }
+    }
+    // r1 = A^-1 b1 - A^-1 B s2
+    swj_dgemm(st, M, n1, n1, -1.0, r2, n1, c->pc_AinvB, n1, 1.0, t1, n1);
+    SWJ_CUDA_TRY(cudaMemcpyAsync(r, t1, (size_t)H * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    return SWJ_OK;
+}

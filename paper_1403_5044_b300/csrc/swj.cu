@@ -1,0 +1,303 @@
+// C ABI of libswj (declared in include/swj.h): context lifecycle, argument
+// checks and dispatch to the kernel families.
+#include "swj_internal.h"
+#include <new>
+#include <stdlib.h>
+#include <string.h>
+
+namespace {
+
+bool valid_mesh(const swj_mesh *m)
+{
+    return m && m->N >= 4 && m->M >= 3 && m->dx > 0.0 && m->dy > 0.0 && m->n_rad >= 0.0 &&
+           (long long)2 * (m->N + 1) * m->M < (1LL << 31) && (long long)(m->N - 1) * m->M < (1LL << 30);
+}
+
+bool valid_opts(const swj_opts *o)
+{
+    if (!o) return false;
+    if (o->solve_mode != SWJ_SOLVE_FP64 && o->solve_mode != SWJ_SOLVE_MIXED) return false;
+    if (o->block_bw < 0 || (o->block_bw > 0 && o->block_bw % 2 == 0)) return false;
+    if (o->gmres_restart < 1 || o->gmres_restart > 60) return false;
+    if (o->max_newton < 0 || o->max_krylov < 1 || o->refine_max < 0) return false;
+    if (!(o->ftol_inf > 0.0) || !(o->eta_max > 0.0) || o->eta_max >= 1.0) return false;
+    if (!(o->eta_min > 0.0) || o->eta_min > o->eta_max) return false;
+    if (o->fd_h < 0.0 || !(o->mixed_tol_inf > 0.0) || !(o->refine_tol_inf > 0.0)) return false;
+    return true;
+}
+
+template <typename T> int dalloc(swj_ctx *c, T **p, size_t count)
+{
+    size_t b = count * sizeof(T);
+    if (b == 0) b = sizeof(T);
+    if (cudaMalloc((void **)p, b) != cudaSuccess) { *p = nullptr; return SWJ_ENOMEM; }
+    c->bytes += b;
+    return SWJ_OK;
+}
+
+void free_all(swj_ctx *c)
+{
+    void *ptrs[] = {c->zeta, c->g, c->zetay, c->gy, c->spl_cp, c->spl_a, c->spl_inv, c->e2part,
+                    c->Ival, c->src64, c->src32, c->tgt64_base, c->tgt32_base, c->partial,
+                    c->u_tmp, c->E_tmp, c->E_cur, c->u_try, c->E_try, c->E_base32, c->du,
+                    c->rvec, c->dscal, c->red, c->V, c->Z};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (c->hpin) cudaFreeHost(c->hpin);
+    swj_pc_free(c);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+}
+
+int alloc_all(swj_ctx *c)
+{
+    const size_t S = c->S, T = c->T, M = c->M, nu = c->nu;
+    int rc = 0;
+    rc |= dalloc(c, &c->zeta, S);
+    rc |= dalloc(c, &c->g, S);
+    rc |= dalloc(c, &c->zetay, S);
+    rc |= dalloc(c, &c->gy, S);
+    rc |= dalloc(c, &c->spl_cp, M);
+    rc |= dalloc(c, &c->spl_a, M);
+    rc |= dalloc(c, &c->spl_inv, M);
+    rc |= dalloc(c, &c->e2part, T);
+    rc |= dalloc(c, &c->Ival, T);
+    rc |= dalloc(c, &c->src64, S);
+    rc |= dalloc(c, &c->src32, S);
+    rc |= dalloc(c, &c->tgt64_base, 8 * T);
+    rc |= dalloc(c, &c->tgt32_base, 8 * T);
+    if (rc) return SWJ_ENOMEM;
+    double *b = c->tgt64_base;
+    c->tgt64 = TgtArrays<double>{b, b + T, b + 2 * T, b + 3 * T, b + 4 * T, b + 5 * T, b + 6 * T, b + 7 * T};
+    float *f = c->tgt32_base;
+    c->tgt32 = TgtArrays<float>{f, f + T, f + 2 * T, f + 3 * T, f + 4 * T, f + 5 * T, f + 6 * T, f + 7 * T};
+    c->plan64 = swj_pair_plan(c, SWJ_FP64);
+    c->plan32 = swj_pair_plan(c, SWJ_FP32);
+    int P = c->plan64.P > c->plan32.P ? c->plan64.P : c->plan32.P;
+    c->partial_cap = (size_t)P * T;
+    rc |= dalloc(c, &c->partial, c->partial_cap);
+    double **vecs[] = {&c->u_tmp, &c->E_tmp, &c->E_cur, &c->u_try, &c->E_try, &c->E_base32, &c->du, &c->rvec};
+    for (double **v : vecs) rc |= dalloc(c, v, nu);
+    rc |= dalloc(c, &c->dscal, 512);
+    rc |= dalloc(c, &c->red, 64 * 64 + 1024);
+    c->kry_m = c->opts.gmres_restart;
+    rc |= dalloc(c, &c->V, (size_t)(c->kry_m + 1) * nu);
+    rc |= dalloc(c, &c->Z, (size_t)c->kry_m * nu);
+    if (rc) return SWJ_ENOMEM;
+    if (cudaMallocHost((void **)&c->hpin, 512 * sizeof(double)) != cudaSuccess) {
+        c->hpin = nullptr;
+        return SWJ_ENOMEM;
+    }
+    double *cp = (double *)malloc(3 * M * sizeof(double));
+    if (!cp) return SWJ_ENOMEM;
+    swj_spline_coeffs((int)M, cp, cp + M, cp + 2 * M);
+    cudaError_t e1 = cudaMemcpy(c->spl_cp, cp, M * sizeof(double), cudaMemcpyHostToDevice);
+    cudaError_t e2 = cudaMemcpy(c->spl_a, cp + M, M * sizeof(double), cudaMemcpyHostToDevice);
+    cudaError_t e3 = cudaMemcpy(c->spl_inv, cp + 2 * M, M * sizeof(double), cudaMemcpyHostToDevice);
+    free(cp);
+    if (e1 || e2 || e3) return SWJ_ECUDA;
+    if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess)
+        return SWJ_ECUDA;
+    return SWJ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void swj_default_opts(swj_opts *o)
+{
+    if (!o) return;
+    o->solve_mode = SWJ_SOLVE_MIXED;
+    o->block_bw = 1;
+    o->gmres_restart = 30;
+    o->max_newton = 60;
+    o->max_krylov = 300;
+    o->ftol_inf = 1e-10;
+    o->eta_max = 0.1;
+    o->eta_min = 1e-6;
+    o->fd_h = 0.0;
+    o->refine_max = 4;
+    o->mixed_tol_inf = 2e-6;
+    o->refine_tol_inf = 1e-9;
+    o->verbose = 0;
+}
+
+int swj_create(swj_ctx **out, const swj_mesh *mesh, double F, double eps, const swj_opts *opts,
+               void *stream)
+{
+    if (!out) return SWJ_EINVAL;
+    *out = nullptr;
+    if (!valid_mesh(mesh) || !(F > 0.0) || !(eps >= 0.0)) return SWJ_EINVAL;
+    swj_opts o;
+    if (opts) o = *opts; else swj_default_opts(&o);
+    if (!valid_opts(&o)) return SWJ_EINVAL;
+    swj_ctx *c = new (std::nothrow) swj_ctx();
+    if (!c) return SWJ_ENOMEM;
+    memset((void *)c, 0, sizeof(*c));
+    c->mesh = *mesh;
+    c->F = F;
+    c->eps = eps;
+    c->opts = o;
+    c->stream = (cudaStream_t)stream;
+    if (cudaGetDevice(&c->dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->dev) != cudaSuccess) {
+        delete c;
+        return SWJ_ECUDA;
+    }
+    c->N = mesh->N;
+    c->M = mesh->M;
+    c->n1 = c->N + 1;
+    c->H = c->n1 * c->M;
+    c->nu = 2 * c->H;
+    c->T = (c->N - 1) * c->M;
+    c->S = c->N * c->M;
+    int rc = alloc_all(c);
+    if (rc) {
+        free_all(c);
+        delete c;
+        return rc;
+    }
+    *out = c;
+    return SWJ_OK;
+}
+
+void swj_destroy(swj_ctx *c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    free_all(c);
+    delete c;
+}
+
+int swj_set_params(swj_ctx *c, double F, double eps)
+{
+    if (!c || !(F > 0.0) || !(eps >= 0.0)) return SWJ_EINVAL;
+    if (F != c->F) c->pc_ready = 0;
+    c->F = F;
+    c->eps = eps;
+    return SWJ_OK;
+}
+
+int swj_set_opts(swj_ctx *c, const swj_opts *o)
+{
+    if (!c || !valid_opts(o)) return SWJ_EINVAL;
+    if (o->gmres_restart != c->kry_m) {
+        double *V = nullptr, *Z = nullptr;
+        if (cudaMalloc(&V, (size_t)(o->gmres_restart + 1) * c->nu * sizeof(double)) != cudaSuccess)
+            return SWJ_ENOMEM;
+        if (cudaMalloc(&Z, (size_t)o->gmres_restart * c->nu * sizeof(double)) != cudaSuccess) {
+            cudaFree(V);
+            return SWJ_ENOMEM;
+        }
+        cudaStreamSynchronize(c->stream);
+        c->bytes -= (size_t)(2 * c->kry_m + 1) * c->nu * sizeof(double);
+        cudaFree(c->V);
+        cudaFree(c->Z);
+        c->V = V;
+        c->Z = Z;
+        c->kry_m = o->gmres_restart;
+        c->bytes += (size_t)(2 * c->kry_m + 1) * c->nu * sizeof(double);
+    }
+    if (o->block_bw != c->opts.block_bw || o->solve_mode != c->opts.solve_mode) c->pc_ready = 0;
+    c->opts = *o;
+    return SWJ_OK;
+}
+
+size_t swj_workspace_bytes(const swj_ctx *c) { return c ? c->bytes : 0; }
+
+int swj_initial_guess_flat(swj_ctx *c, double *u)
+{
+    if (!c || !u) return SWJ_EINVAL;
+    swj_launch_flat(c, u);
+    SWJ_CUDA_TRY(cudaGetLastError());
+    return SWJ_OK;
+}
+
+int swj_residual(swj_ctx *c, const double *u, double *E, int precision)
+{
+    if (!c || !u || !E || u == E) return SWJ_EINVAL;
+    if (precision != SWJ_FP64 && precision != SWJ_FP32) return SWJ_EINVAL;
+    return swj_residual_impl(c, u, E, precision);
+}
+
+int swj_jvp(swj_ctx *c, const double *u, const double *Eu, const double *v, double *Jv,
+            int precision)
+{
+    if (!c || !u || !Eu || !v || !Jv) return SWJ_EINVAL;
+    if (precision != SWJ_FP64 && precision != SWJ_FP32) return SWJ_EINVAL;
+    return swj_jvp_impl(c, u, Eu, v, Jv, precision, c->opts.fd_h);
+}
+
+int swj_precond_setup(swj_ctx *c)
+{
+    if (!c) return SWJ_EINVAL;
+    return swj_pc_setup(c);
+}
+
+int swj_precond_apply(swj_ctx *c, const double *b, double *r)
+{
+    if (!c || !b || !r) return SWJ_EINVAL;
+    if (!c->pc_ready) {
+        int rc = swj_pc_setup(c);
+        if (rc) return rc;
+    }
+    return swj_pc_apply(c, b, r);
+}
+
+int swj_solve(swj_ctx *c, double *u, swj_stats *st)
+{
+    if (!c || !u) return SWJ_EINVAL;
+    int rc = swj_solve_impl(c, u, st);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return SWJ_ECUDA;
+    return rc;
+}
+
+int swj_unpack(swj_ctx *c, const double *u, double *zeta, double *phi)
+{
+    if (!c || !u) return SWJ_EINVAL;
+    swj_launch_unpack(c, u, zeta, phi);
+    SWJ_CUDA_TRY(cudaGetLastError());
+    return SWJ_OK;
+}
+
+int swj_surface(swj_ctx *c, const double *u, double *out)
+{
+    if (!c || !u || !out) return SWJ_EINVAL;
+    // the mesh step also writes E1/E3..E6 rows; send them to a scratch vector
+    swj_launch_mesh_step(c, u, c->E_tmp);
+    swj_launch_surface(c, out);
+    SWJ_CUDA_TRY(cudaGetLastError());
+    return SWJ_OK;
+}
+
+int swj_sync(swj_ctx *c)
+{
+    if (!c) return SWJ_EINVAL;
+    SWJ_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    SWJ_CUDA_TRY(cudaGetLastError());
+    return SWJ_OK;
+}
+
+const char *swj_strerror(int s)
+{
+    switch (s) {
+    case SWJ_OK: return "ok";
+    case SWJ_EINVAL: return "invalid argument";
+    case SWJ_ENOMEM: return "out of memory";
+    case SWJ_ECUDA: return "CUDA error";
+    case SWJ_ENOTCONV: return "Newton iteration cap reached";
+    case SWJ_ELINESEARCH: return "line search failed";
+    case SWJ_EGMRES: return "GMRES failed";
+    case SWJ_ENAN: return "NaN or Inf encountered";
+    case SWJ_ETIMEOUT: return "device wait timed out";
+    case SWJ_ESINGULAR: return "singular preconditioner block";
+    case SWJ_PENDING: return "pending";
+    default: return "unknown status";
+    }
+}
+
+const char *swj_version(void) { return SWJ_VERSION_STRING; }
+
+}  // extern "C"

@@ -1,0 +1,162 @@
+// Internal declarations of libswj: the context, device buffers and the
+// launch wrappers of each kernel family.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+#include "../../include/swj.h"
+
+#define SWJ_VERSION_STRING "swj 0.1 (sm_103a)"
+
+// ---------------------------------------------------------------- records
+// Per-source record of the all-pairs sum (one per mesh node (i, j)).
+// Coordinates are kept as exact index values (si = i, sj = j, 0-based) so
+// that every coordinate difference in the kernel is exact; lengths are
+// recovered with the mesh spacings.
+template <typename T> struct SrcRec {
+    T zeta;   // zeta_ij
+    T zx;     // (zeta_x)_ij
+    T zy;     // (zeta_y)_ij
+    T g;      // g_ij = phi_ij - x_i
+    T w;      // trapezoid weight w(i, j)
+    T si;     // i (0-based)
+    T sj;     // j (0-based)
+    T pad;
+};
+
+// Per-target record (one per half-mesh point (k + 1/2, l)), structure of
+// arrays, each of length T.
+template <typename T> struct TgtArrays {
+    T *tk;    // k + 1/2 (0-based k)
+    T *tl;    // l
+    T *zeta;  // zeta*
+    T *g;     // g*
+    T *zx;    // zeta_x*
+    T *A, *B, *C;   // 1 + zx*^2, 2 zx* zy*, 1 + zy*^2
+};
+
+struct PairPlan {
+    int tpb;      // threads per block
+    int R;        // targets per thread
+    int P;        // source chunks (grid.y)
+    int chunk;    // sources per chunk
+    int tiles;    // target tiles (grid.x)
+};
+
+// ---------------------------------------------------------------- context
+struct swj_ctx {
+    swj_mesh mesh;
+    double F, eps;
+    swj_opts opts;
+    cudaStream_t stream;
+    int dev, num_sms;
+
+    int N, M;          // mesh
+    int n1;            // N + 1 (block size)
+    int H;             // (N + 1) M (half of the unknowns)
+    int nu;            // 2 (N + 1) M
+    int T;             // (N - 1) M targets
+    int S;             // N M sources
+
+    // mesh step (FP64), node arrays [M][N]
+    double *zeta, *g, *zetay, *gy;
+    double *spl_cp, *spl_a, *spl_inv;   // Thomas coefficients along y (M each)
+    // per-target E2 terms that do not need the pair sum: 2 pi g* + src - zx* I
+    double *e2part;
+    double *Ival;      // I per target (diagnostics)
+    // records for the two precisions
+    SrcRec<double> *src64;
+    SrcRec<float> *src32;
+    TgtArrays<double> tgt64;
+    TgtArrays<float> tgt32;
+    double *tgt64_base; float *tgt32_base;
+    // partial sums [P][T]
+    double *partial;
+    size_t partial_cap;   // doubles
+    PairPlan plan64, plan32;
+
+    // JVP / solver temporaries (length nu)
+    double *u_tmp, *E_tmp;           // JVP: u + h v and E(u + h v)
+    double *E_cur, *u_try, *E_try;   // Newton: current residual, line-search trial
+    double *E_base32;                // MIXED refinement: FP32 residual at u (JVP base)
+    double *du, *rvec;               // Newton step, GMRES right-hand side
+    double *dscal;        // device scalars (norms, FD step, Arnoldi coefficients)
+    double *red;          // reduction scratch
+    double *hpin;         // pinned host mirror of device scalars
+
+    // Krylov basis (m + 1) x nu and preconditioned basis m x nu
+    double *V, *Z;
+    int kry_m;
+
+    // preconditioner
+    int pc_ready, pc_h, pc_nb;   // built flag, block half bandwidth, blocks per band row
+    double *pc_Ainv, *pc_AinvB, *pc_CAinv, *pc_G, *pc_A, *pc_B, *pc_C, *pc_tmp;
+    double *pc_band;             // [M][2h+1][n1][n1]
+    double *pc_sumK3;            // [T] sum_s w K3 (flat-state trapezoid sum)
+    int *pc_info;                // device status of the factorisation
+    double **pc_ptrs;            // device pointer arrays for batched block GEMMs
+    int pc_ptrs_cap;
+    double *pc_t1, *pc_t2;       // apply temporaries [H]
+
+    size_t bytes;                // device bytes held
+    cudaEvent_t ev0, ev1;
+};
+
+// ---------------------------------------------------------------- launches
+// mesh.cu
+void swj_launch_mesh_step(swj_ctx *c, const double *u, double *E);
+void swj_launch_assemble(swj_ctx *c, double *E, int P);
+void swj_spline_coeffs(int M, double *cp, double *a, double *inv);  // host helper
+void swj_launch_flat(swj_ctx *c, double *u);
+void swj_launch_unpack(swj_ctx *c, const double *u, double *zeta_out, double *phi_out);
+void swj_launch_surface(swj_ctx *c, double *out);
+
+// pairs.cu
+PairPlan swj_pair_plan(const swj_ctx *c, int precision);
+void swj_launch_pairs64(swj_ctx *c, const PairPlan &pl);
+void swj_launch_pairs32(swj_ctx *c, const PairPlan &pl);
+void swj_launch_pairs_generic32(cudaStream_t st, int T, int S, const SrcRec<float> *src,
+                                const TgtArrays<float> &tgt, float dX, float dY,
+                                double *partial, const PairPlan &pl);
+
+// linalg.cu
+void swj_axpby(cudaStream_t st, int n, double a, const double *x, double b, double *y);      // y = a x + b y
+void swj_axpy_dev(cudaStream_t st, int n, const double *a_dev, double a_scale,
+                  const double *x, double *y);                                             // y += (a_scale * *a_dev) x
+void swj_scale_dev(cudaStream_t st, int n, const double *num_dev, double *x, int invert);  // x *= *num (or 1/ *num)
+void swj_copy(cudaStream_t st, int n, const double *x, double *y);
+void swj_fill(cudaStream_t st, int n, double v, double *x);
+// out[0] = ||x||_2^2, out[1] = ||x||_inf (NaN if any entry is NaN/Inf)
+void swj_norms(cudaStream_t st, int n, const double *x, double *red, double *out);
+// out[r] = sum_i V[r*ld + i] w[i], r = 0..rows-1
+void swj_mdot(cudaStream_t st, int n, int rows, const double *V, size_t ld, const double *w,
+              double *red, double *out);
+// w -= sum_r coef[r] V[r*ld + :]
+void swj_mgemv_sub(cudaStream_t st, int n, int rows, const double *V, size_t ld,
+                   const double *coef, double *w);
+// x = sum_r coef_host[r] Z[r*ld + :]  (coefficients from host)
+void swj_combine(cudaStream_t st, int n, int rows, const double *Z, size_t ld,
+                 const double *coef_dev, double *x, int accumulate);
+// C(mxn) = alpha A(mxk) B(kxn) + beta C, row-major with leading dims; batched by pointer arrays
+void swj_dgemm_batched(cudaStream_t st, int m, int n, int k, double alpha,
+                       const double *const *A, int lda, const double *const *B, int ldb,
+                       double beta, double *const *C, int ldc, int batch);
+void swj_dgemm(cudaStream_t st, int m, int n, int k, double alpha, const double *A, int lda,
+               const double *B, int ldb, double beta, double *C, int ldc);
+// in-place inverse of `count` n x n blocks (stride `stride` doubles) by Gauss-Jordan with
+// partial pivoting; info[b] = 0 or 1 + failing column.
+void swj_block_inverse(cudaStream_t st, int n, int count, double *blocks, size_t stride, int *info);
+
+// precond.cu
+int swj_pc_setup(swj_ctx *c);
+int swj_pc_apply(swj_ctx *c, const double *b, double *r);
+void swj_pc_free(swj_ctx *c);
+
+// solver.cu
+int swj_residual_impl(swj_ctx *c, const double *u, double *E, int precision);
+int swj_jvp_impl(swj_ctx *c, const double *u, const double *Eu, const double *v, double *Jv,
+                 int precision, double h_fixed);
+int swj_solve_impl(swj_ctx *c, double *u, swj_stats *st);
+
+#define SWJ_CUDA_TRY(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) return SWJ_ECUDA; } while (0)

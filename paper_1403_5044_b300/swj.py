@@ -1,0 +1,231 @@
+"""Thin ctypes binding of libswj (include/swj.h).
+
+Argument marshalling only: every step of the residual, JVP, preconditioner
+and solve runs in the CUDA library.  Device buffers are torch CUDA float64
+tensors (torch is used for device memory and streams).  If the library is
+missing the import fails loudly; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libswj.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "swj.h")
+
+OK, EINVAL, ENOMEM, ECUDA, ENOTCONV, ELINESEARCH, EGMRES, ENAN, ETIMEOUT, ESINGULAR = \
+    0, -1, -2, -3, -4, -5, -6, -7, -8, -9
+PENDING = 1
+FP64, FP32 = 0, 1
+SOLVE_FP64, SOLVE_MIXED = 0, 1
+
+
+class SwjError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        super().__init__("%s: %s (%d)" % (what, strerror(status), status))
+
+
+class Mesh(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("M", ctypes.c_int), ("x1", ctypes.c_double),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("n_rad", ctypes.c_double)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("solve_mode", ctypes.c_int), ("block_bw", ctypes.c_int),
+                ("gmres_restart", ctypes.c_int), ("max_newton", ctypes.c_int),
+                ("max_krylov", ctypes.c_int), ("ftol_inf", ctypes.c_double),
+                ("eta_max", ctypes.c_double), ("eta_min", ctypes.c_double),
+                ("fd_h", ctypes.c_double), ("refine_max", ctypes.c_int),
+                ("mixed_tol_inf", ctypes.c_double), ("refine_tol_inf", ctypes.c_double),
+                ("verbose", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("newton_iters", ctypes.c_int),
+                ("refine_iters", ctypes.c_int), ("residual_evals", ctypes.c_int),
+                ("residual_evals_fp64", ctypes.c_int), ("krylov_iters", ctypes.c_int),
+                ("precond_applies", ctypes.c_int), ("line_search_cuts", ctypes.c_int),
+                ("final_norm_inf", ctypes.c_double), ("final_norm_inf_fp64", ctypes.c_double),
+                ("t_total_ms", ctypes.c_double), ("t_setup_ms", ctypes.c_double),
+                ("pairs_per_residual_hi", ctypes.c_int), ("pairs_per_residual_lo", ctypes.c_int)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_}
+        d["pairs_per_residual"] = (d.pop("pairs_per_residual_hi") << 31) | d.pop("pairs_per_residual_lo")
+        return d
+
+
+_LIB = None
+_vp = ctypes.c_void_p
+
+
+def lib():
+    """Load libswj.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libswj.so not built: run `python -m paper_1403_5044_b300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        P = ctypes.POINTER
+        sig = {
+            "swj_default_opts": (None, [P(Opts)]),
+            "swj_create": (ctypes.c_int, [P(_vp), P(Mesh), ctypes.c_double, ctypes.c_double, P(Opts), _vp]),
+            "swj_destroy": (None, [_vp]),
+            "swj_set_params": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double]),
+            "swj_set_opts": (ctypes.c_int, [_vp, P(Opts)]),
+            "swj_workspace_bytes": (ctypes.c_size_t, [_vp]),
+            "swj_initial_guess_flat": (ctypes.c_int, [_vp, _vp]),
+            "swj_residual": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int]),
+            "swj_jvp": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_int]),
+            "swj_precond_setup": (ctypes.c_int, [_vp]),
+            "swj_precond_apply": (ctypes.c_int, [_vp, _vp, _vp]),
+            "swj_solve": (ctypes.c_int, [_vp, _vp, P(Stats)]),
+            "swj_unpack": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+            "swj_surface": (ctypes.c_int, [_vp, _vp, _vp]),
+            "swj_sync": (ctypes.c_int, [_vp]),
+            "swj_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+            "swj_version": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def header_functions(path: str = HEADER):
+    """Names of every function the public header declares."""
+    txt = open(path).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(swj_[a-z0-9_]+)\s*\(", txt)))
+
+
+def strerror(status: int) -> str:
+    return lib().swj_strerror(int(status)).decode()
+
+
+def version() -> str:
+    return lib().swj_version().decode()
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    lib().swj_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "solve_mode" and isinstance(v, str):
+            v = {"fp64": SOLVE_FP64, "mixed": SOLVE_MIXED}[v]
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    import torch
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA float64 tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _check(rc, what):
+    if rc != OK:
+        raise SwjError(rc, what)
+    return rc
+
+
+class Context:
+    """One mesh, one (F, eps), one CUDA stream (torch's current stream by
+    default).  Mirrors swj_create / swj_destroy."""
+
+    def __init__(self, N, M, x1, dx, dy, F, eps, n_rad=0.05, opts: Opts | None = None, stream=None, **kw):
+        import torch
+        self.mesh = Mesh(int(N), int(M), float(x1), float(dx), float(dy), float(n_rad))
+        self.opts = opts if opts is not None else default_opts(**kw)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        handle = getattr(stream, "cuda_stream", stream)
+        self._h = _vp()
+        _check(lib().swj_create(ctypes.byref(self._h), ctypes.byref(self.mesh), float(F), float(eps),
+                                ctypes.byref(self.opts), _vp(handle)), "swj_create")
+        self.N, self.M, self.F, self.eps = int(N), int(M), float(F), float(eps)
+        self.n_unknowns = 2 * (self.N + 1) * self.M
+
+    @classmethod
+    def from_spec(cls, spec, F, eps, **kw):
+        return cls(spec.N, spec.M, spec.x1, spec.dx, spec.dy, F, eps, n_rad=spec.n_rad, **kw)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().swj_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- thin wrappers -------------------------------------------------------
+    def vector(self):
+        import torch
+        return torch.empty(self.n_unknowns, dtype=torch.float64, device="cuda")
+
+    def set_params(self, F, eps):
+        _check(lib().swj_set_params(self._h, float(F), float(eps)), "swj_set_params")
+        self.F, self.eps = float(F), float(eps)
+
+    def set_opts(self, opts: Opts):
+        _check(lib().swj_set_opts(self._h, ctypes.byref(opts)), "swj_set_opts")
+        self.opts = opts
+
+    def workspace_bytes(self):
+        return int(lib().swj_workspace_bytes(self._h))
+
+    def initial_guess_flat(self, u):
+        _check(lib().swj_initial_guess_flat(self._h, _ptr(u)), "swj_initial_guess_flat")
+        return u
+
+    def residual(self, u, E, precision=FP64):
+        _check(lib().swj_residual(self._h, _ptr(u), _ptr(E), int(precision)), "swj_residual")
+        return E
+
+    def jvp(self, u, Eu, v, Jv, precision=FP64):
+        _check(lib().swj_jvp(self._h, _ptr(u), _ptr(Eu), _ptr(v), _ptr(Jv), int(precision)), "swj_jvp")
+        return Jv
+
+    def precond_setup(self):
+        _check(lib().swj_precond_setup(self._h), "swj_precond_setup")
+
+    def precond_apply(self, b, r):
+        _check(lib().swj_precond_apply(self._h, _ptr(b), _ptr(r)), "swj_precond_apply")
+        return r
+
+    def solve(self, u, check=True):
+        st = Stats()
+        rc = lib().swj_solve(self._h, _ptr(u), ctypes.byref(st))
+        if check:
+            _check(rc, "swj_solve")
+        d = st.as_dict()
+        d["rc"] = rc
+        return d
+
+    def unpack(self, u, zeta=None, phi=None):
+        _check(lib().swj_unpack(self._h, _ptr(u), _ptr(zeta), _ptr(phi)), "swj_unpack")
+
+    def surface(self, u, out):
+        _check(lib().swj_surface(self._h, _ptr(u), _ptr(out)), "swj_surface")
+        return out
+
+    def sync(self):
+        _check(lib().swj_sync(self._h), "swj_sync")

@@ -1,0 +1,122 @@
+"""Parity of the CUDA Jacobian-vector product, preconditioner and Newton-GMRES
+solves with the CPU oracle, through the C ABI."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1403_5044_b300 import swj
+from paper_1403_5044_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def omesh(spec):
+    return O.Mesh(spec.N, spec.M, spec.x1, spec.dx, spec.dy, spec.n_rad)
+
+
+def dev(x):
+    return torch.tensor(np.asarray(x), dtype=torch.float64, device="cuda")
+
+
+def test_jvp_matches_oracle_derivative():
+    """Eq. JvApprox on the GPU (automatic h) against a fourth-order central
+    difference of the oracle residual."""
+    spec, F, eps = W.MeshSpec(37, 13, -8.0, 0.45, 0.35), 0.7, 0.3
+    m = omesh(spec)
+    u = W.random_state(spec, seed=31, amp=0.1)
+    v = np.random.default_rng(32).normal(size=u.size)
+    E = lambda w: O.residual(m, F, eps, w)
+    h = 1e-4
+    ref = (8 * (E(u + h * v) - E(u - h * v)) - (E(u + 2 * h * v) - E(u - 2 * h * v))) / (12 * h)
+    with swj.Context.from_spec(spec, F, eps) as ctx:
+        ud, vd = dev(u), dev(v)
+        Eu, Jv = ctx.vector(), ctx.vector()
+        ctx.residual(ud, Eu, swj.FP64)
+        ctx.jvp(ud, Eu, vd, Jv, swj.FP64)
+        ctx.sync()
+        got = Jv.cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-6 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("spec,b", [(W.MeshSpec(9, 5, -2.0, 0.5, 0.4), 0),
+                                    (W.MeshSpec(9, 5, -2.0, 0.5, 0.4), 1),
+                                    (W.MeshSpec(9, 5, -2.0, 0.5, 0.4), 3),
+                                    (W.MESH_41x21, 0),
+                                    (W.MESH_41x21, 1),
+                                    (W.MESH_41x21, 5)])
+def test_precond_apply_matches_linear_jacobian_solve(spec, b):
+    """r = P^-1 b from the Schur-complement block LU (Appendix C) equals a
+    dense solve with the oracle's Appendix B matrix truncated to the same
+    block bandwidth."""
+    F = 0.7
+    m = omesh(spec)
+    P = O.jacobian_linear(m, F, None if b == 0 else b)
+    rhs = np.random.default_rng(b + spec.N).normal(size=m.n_unknowns)
+    ref = np.linalg.solve(P, rhs)
+    with swj.Context.from_spec(spec, F, 0.1, solve_mode="fp64", block_bw=b) as ctx:
+        ctx.precond_setup()
+        r = ctx.vector()
+        ctx.precond_apply(dev(rhs), r)
+        ctx.sync()
+        got = r.cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-9 * np.abs(ref).max()
+    assert np.abs(P @ got - rhs).max() <= 1e-9 * np.abs(rhs).max()
+
+
+def gpu_solve(spec, F, eps, **kw):
+    with swj.Context.from_spec(spec, F, eps, **kw) as ctx:
+        u = ctx.initial_guess_flat(ctx.vector())
+        st = ctx.solve(u)
+        zeta, phi = torch.empty(spec.N * spec.M, dtype=torch.float64, device="cuda"), \
+            torch.empty(spec.N * spec.M, dtype=torch.float64, device="cuda")
+        ctx.unpack(u, zeta, phi)
+        ctx.sync()
+        return u.cpu().numpy(), zeta.cpu().numpy().reshape(spec.M, spec.N), st
+
+
+@pytest.mark.parametrize("spec,F,eps", [(W.MeshSpec(9, 5, -2.0, 0.5, 0.4), 0.7, 0.1),
+                                        W.SOLVE_41x21])
+def test_fp64_solve_reaches_the_oracle_root(spec, F, eps):
+    m = omesh(spec)
+    uo, _ = O.newton_gmres(m, F, eps, O.flat_guess(m), tol=1e-11, eta=1e-8)
+    zo, _ = O.zeta_phi(m, uo)
+    u, zeta, st = gpu_solve(spec, F, eps, solve_mode="fp64", block_bw=0)
+    assert st["rc"] == 0 and st["final_norm_inf"] < 1e-10
+    assert np.abs(zeta - zo).max() <= 1e-8
+    assert np.abs(O.residual(m, F, eps, u)).max() < 1e-9
+
+
+@pytest.mark.parametrize("b", [1, 3])
+def test_mixed_solve_matches_oracle_root_41x21(b):
+    spec, F, eps = W.SOLVE_41x21
+    m = omesh(spec)
+    uo, _ = O.newton_gmres(m, F, eps, O.flat_guess(m), tol=1e-11, eta=1e-8)
+    zo, _ = O.zeta_phi(m, uo)
+    u, zeta, st = gpu_solve(spec, F, eps, solve_mode="mixed", block_bw=b)
+    assert st["rc"] == 0, st
+    assert np.abs(zeta - zo).max() <= 1e-6
+    assert np.abs(O.residual(m, F, eps, u)).max() < 1e-8
+
+
+def test_181x61_mixed_and_fp64_solves_agree_and_are_oracle_roots():
+    """The 181x61, F = 0.7, eps = 0.4 workload: both GPU solves are roots of
+    the oracle's residual, and their surfaces agree to 1e-6."""
+    spec, F, eps = W.SOLVE_181x61
+    m = omesh(spec)
+    u64, z64, s64 = gpu_solve(spec, F, eps, solve_mode="fp64", block_bw=1)
+    umx, zmx, smx = gpu_solve(spec, F, eps, solve_mode="mixed", block_bw=1)
+    assert s64["rc"] == 0 and smx["rc"] == 0, (s64, smx)
+    assert np.abs(zmx - z64).max() <= 1e-6
+    assert np.abs(O.residual(m, F, eps, u64)).max() < 1e-9
+    assert np.abs(O.residual(m, F, eps, umx)).max() < 1e-8
+    assert z64.max() < F ** 2 / 2
+
+
+def test_solve_reports_nan():
+    spec = W.MeshSpec(9, 5, -2.0, 0.5, 0.4)
+    with swj.Context.from_spec(spec, 0.7, 0.1, solve_mode="fp64") as ctx:
+        u = ctx.initial_guess_flat(ctx.vector())
+        u[3] = float("nan")
+        st = ctx.solve(u, check=False)
+        assert st["rc"] == swj.ENAN
