@@ -62,6 +62,44 @@ void oracle_pair_kernels(double dx, double dy, double dyp, double dz,
  *   asum[t] = sum over sources of |w (g-g*) K1| + |w zx K2| + |w zx* S2|
  *             (the scale that the parity tolerance is measured against).
  */
+static void one_target(int t, int N, int M, double x1, double dxm, double dym,
+                       const double *zeta, const double *zetax,
+                       const double *zetay, const double *g,
+                       const double *zeta_t, const double *zetax_t,
+                       const double *zetay_t, const double *g_t,
+                       double *sum_out, double *asum_out)
+{
+    int k = t % (N - 1);
+    int l = t / (N - 1);
+    double xt = x1 + ((double)k + 0.5) * dxm;
+    double yt = (double)l * dym;
+    double zt = zeta_t[t], zxt = zetax_t[t], zyt = zetay_t[t], gt = g_t[t];
+    double A = 1.0 + zxt * zxt;
+    double B = 2.0 * zxt * zyt;
+    double C = 1.0 + zyt * zyt;
+    double s = 0.0, a = 0.0;
+    for (int j = 0; j < M; ++j) {
+        double yj = (double)j * dym;
+        double cj = (j == 0 || j == M - 1) ? 0.5 : 1.0;
+        for (int i = 0; i < N; ++i) {
+            double xi = x1 + (double)i * dxm;
+            double ci = (i == 0 || i == N - 1) ? 0.5 : 1.0;
+            double w = dxm * dym * ci * cj;
+            int p = j * N + i;
+            double kv[3];
+            oracle_pair_kernels(xi - xt, yj - yt, yj + yt, zeta[p] - zt,
+                                zetax[p], zetay[p], A, B, C, kv);
+            double t1 = w * (g[p] - gt) * kv[0];
+            double t2 = w * zetax[p] * kv[1];
+            double t3 = w * zxt * kv[2];
+            s += t1 + t2 - t3;
+            a += fabs(t1) + fabs(t2) + fabs(t3);
+        }
+    }
+    *sum_out = s;
+    *asum_out = a;
+}
+
 void oracle_pairsum(int N, int M, double x1, double dxm, double dym,
                     const double *zeta, const double *zetax,
                     const double *zetay, const double *g,
@@ -71,35 +109,22 @@ void oracle_pairsum(int N, int M, double x1, double dxm, double dym,
 {
     int T = (N - 1) * M;
 #pragma omp parallel for schedule(dynamic, 16)
-    for (int t = 0; t < T; ++t) {
-        int k = t % (N - 1);
-        int l = t / (N - 1);
-        double xt = x1 + ((double)k + 0.5) * dxm;
-        double yt = (double)l * dym;
-        double zt = zeta_t[t], zxt = zetax_t[t], zyt = zetay_t[t], gt = g_t[t];
-        double A = 1.0 + zxt * zxt;
-        double B = 2.0 * zxt * zyt;
-        double C = 1.0 + zyt * zyt;
-        double s = 0.0, a = 0.0;
-        for (int j = 0; j < M; ++j) {
-            double yj = (double)j * dym;
-            double cj = (j == 0 || j == M - 1) ? 0.5 : 1.0;
-            for (int i = 0; i < N; ++i) {
-                double xi = x1 + (double)i * dxm;
-                double ci = (i == 0 || i == N - 1) ? 0.5 : 1.0;
-                double w = dxm * dym * ci * cj;
-                int p = j * N + i;
-                double kv[3];
-                oracle_pair_kernels(xi - xt, yj - yt, yj + yt, zeta[p] - zt,
-                                    zetax[p], zetay[p], A, B, C, kv);
-                double t1 = w * (g[p] - gt) * kv[0];
-                double t2 = w * zetax[p] * kv[1];
-                double t3 = w * zxt * kv[2];
-                s += t1 + t2 - t3;
-                a += fabs(t1) + fabs(t2) + fabs(t3);
-            }
-        }
-        sum[t] = s;
-        asum[t] = a;
-    }
+    for (int t = 0; t < T; ++t)
+        one_target(t, N, M, x1, dxm, dym, zeta, zetax, zetay, g, zeta_t, zetax_t,
+                   zetay_t, g_t, &sum[t], &asum[t]);
+}
+
+/* The same sum for the listed targets only (tidx[q], q < nt); outputs are
+ * indexed by q. */
+void oracle_pairsum_targets(int N, int M, double x1, double dxm, double dym,
+                            const double *zeta, const double *zetax,
+                            const double *zetay, const double *g,
+                            const double *zeta_t, const double *zetax_t,
+                            const double *zetay_t, const double *g_t,
+                            int nt, const int *tidx, double *sum, double *asum)
+{
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int q = 0; q < nt; ++q)
+        one_target(tidx[q], N, M, x1, dxm, dym, zeta, zetax, zetay, g, zeta_t,
+                   zetax_t, zetay_t, g_t, &sum[q], &asum[q]);
 }
