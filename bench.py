@@ -1,0 +1,353 @@
+"""Benchmark: steady nonlinear ship-wave solves on the 181x61 mesh.
+
+Workload: 181 x 61 half-mesh on x in [-16, 20], y in [0, 12] (dx = dy = 0.2),
+F = 0.7, eps = 0.4, flat initial guess, GMRES restart 30.  One step is one
+complete solve: preconditioner set-up, Newton-GMRES with the FP32 all-pairs
+residual, and the FP64 residual refinement down to ||E_fp64||_inf < 1e-9
+(the mixed-precision solve).  The plain FP64 solve of the same workload is
+timed beside it and every mixed result is compared with it (max |d zeta|).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank runs its
+own replica of the workload (independent solves; there is no data exchange)
+and the time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "ship-wave solve 181x61, F=0.7, eps=0.4 (x in [-16,20], y in [0,12], dx=dy=0.2)"
+METRIC = "solves/s (mixed FP32-residual solve refined to FP64, max|dzeta| vs FP64 solve <= 1e-6)"
+FLOP_PER_PAIR = 44          # FP32 operations per (source, target) pair, FFMA counted as 2
+FP32_LANES_PER_SM = 128
+SM_COUNT_B300 = 148
+SM_MAX_MHZ = 2032.0
+# residual evaluations of one FP64 Newton-GMRES solve of this workload with the
+# default options (measured on the GPU path); the reference arm converts the
+# oracle's residual time into solves/s with it
+RESIDUALS_PER_SOLVE = 21
+BLOCK_BW = 15
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--block-bw", type=int, default=BLOCK_BW)
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--residual-only", action="store_true",
+                    help="only evaluate the FP32 and FP64 residual of the workload `steps` times "
+                         "(a small, fixed launch sequence for profilers)")
+    return ap.parse_args()
+
+
+def dist_init(n):
+    import torch
+    if n <= 1 or "RANK" not in os.environ:
+        return 0, 1, None
+    import torch.distributed as dist
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl")
+    return dist.get_rank(), dist.get_world_size(), dist
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples while the timed region runs."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_residual_rate(seconds):
+    """Time the oracle's full FP64 residual of the workload on the host cores;
+    returns (seconds per residual, evaluations, cores)."""
+    import oracle as O
+    from paper_1403_5044_b300 import workloads as W
+    spec, F, eps = W.SOLVE_181x61
+    m = O.Mesh(spec.N, spec.M, spec.x1, spec.dx, spec.dy, spec.n_rad)
+    u = W.random_state(spec, seed=3, amp=0.05)
+    O.residual(m, F, eps, u)  # compile / warm
+    n, t0 = 0, time.perf_counter()
+    while True:
+        O.residual(m, F, eps, u)
+        n += 1
+        if time.perf_counter() - t0 >= seconds or n >= 50:
+            break
+    dt = (time.perf_counter() - t0) / n
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return dt, n, cores
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_1403_5044_b300 import workloads as W
+    spec = W.SOLVE_181x61[0]
+    per = []
+    for _ in range(args.warmup + args.steps):
+        dt, n, cores = cpu_oracle_residual_rate(0.0)
+        per.append(dt)
+    per = per[args.warmup:]
+    t_res = sum(per) / len(per)
+    solves_s = 1.0 / (t_res * RESIDUALS_PER_SOLVE)
+    sample = ("each step: one full oracle FP64 residual of the 181x61 workload (%d pairs) on %d host "
+              "threads; solves/s = 1 / (t_residual x %d residual evaluations per solve)"
+              % (spec.pairs, cores, RESIDUALS_PER_SOLVE))
+    out = {"impl": "reference", "metric": METRIC, "value": solves_s, "unit": "solves/s",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": t_res * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "impl": "CPU oracle (numpy + plain C, OpenMP)"},
+           "cpu_baseline": {"value": solves_s, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": solves_s, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "residual_pairs_per_s": spec.pairs / t_res}
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    from paper_1403_5044_b300 import swj
+    from paper_1403_5044_b300 import workloads as W
+
+    rank, world, dist = dist_init(args.gpus)
+    if world == 1:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    spec, F, eps = W.SOLVE_181x61
+    stream = torch.cuda.current_stream()
+    ctx = swj.Context.from_spec(spec, F, eps, solve_mode="mixed", block_bw=args.block_bw, stream=stream)
+    u = ctx.vector()
+    zeta = torch.empty(spec.N * spec.M, dtype=torch.float64, device="cuda")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+
+    def solve_once():
+        # a whole solve: preconditioner set-up (it depends on the mesh and F only, but
+        # every step rebuilds it) + Newton-GMRES + FP64 refinement
+        ctx.initial_guess_flat(u)
+        ctx.precond_setup()
+        return ctx.solve(u)
+
+    for _ in range(args.warmup):
+        solve_once()
+    ctx.sync()
+
+    # ---- timed region: K mixed solves (L2 flushed before each, outside the step time)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stats = []
+    ctx.set_kernel_timing(True)
+    launches0 = swj.kernel_launches()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            stats.append(solve_once())
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    launches = swj.kernel_launches() - launches0
+    pair_ms, pair_n = ctx.pair_timing(swj.FP32)
+    pair64_ms, pair64_n = ctx.pair_timing(swj.FP64)
+    ctx.set_kernel_timing(False)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ctx.unpack(u, zeta, None)
+    ctx.sync()
+    zeta_mixed = zeta.cpu().numpy()
+
+    # ---- plain FP64 solve of the same workload (reference for max|dzeta| and its own rate)
+    ctx64 = swj.Context.from_spec(spec, F, eps, solve_mode="fp64", block_bw=args.block_bw, stream=stream)
+    u64 = ctx64.vector()
+    t64 = []
+    st64 = None
+    for k in range(max(1, args.fp64_steps)):
+        flush.fill_(-1.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx64.initial_guess_flat(u64)
+        ctx64.precond_setup()
+        st64 = ctx64.solve(u64)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t64.append(a.elapsed_time(b))
+    ctx64.unpack(u64, zeta, None)
+    ctx64.sync()
+    dzeta = float(np.abs(zeta_mixed - zeta.cpu().numpy()).max())
+
+    # ---- end to end through the public API with host buffers
+    u_host = torch.empty(ctx.n_unknowns, dtype=torch.float64).pin_memory()
+    u_host.copy_(torch.from_numpy(W.flat_state(spec)))
+    z_host = torch.empty(spec.N * spec.M, dtype=torch.float64).pin_memory()
+    e2e_ms = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        u.copy_(u_host, non_blocking=True)
+        ctx.precond_setup()
+        ctx.solve(u)
+        ctx.unpack(u, zeta, None)
+        z_host.copy_(zeta, non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+
+    if rank != 0:
+        return
+    n_solves = world * args.steps
+    value = n_solves / (total_ms / 1e3)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    pairs = spec.pairs
+    avg_pair_ms = pair_ms / max(1, pair_n)
+    achieved = FLOP_PER_PAIR * pairs / (avg_pair_ms * 1e-3) / 1e12
+    peak = sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    cs = clk.summary()
+    mean = lambda xs: sum(xs) / len(xs)
+    s0 = stats[-1]
+    cpu = None
+    if world == 1:
+        dt, n, cores = cpu_oracle_residual_rate(args.cpu_seconds)
+        res_per_solve = mean([s["residual_evals"] for s in stats])
+        cpu = {"value": 1.0 / (dt * st64["residual_evals"]), "unit": "solves/s", "cores": cores, "kind": "oracle",
+               "sample": "%d full oracle FP64 residuals of the 181x61 workload (%.2f s each, %.3e pairs/s); "
+                         "solves/s = 1 / (t_residual x %d residual evaluations of the FP64 solve)"
+                         % (n, dt, pairs / dt, st64["residual_evals"]),
+               "residual_pairs_per_s": pairs / dt}
+    out = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 all-pairs sum + f64 (mesh step, Krylov, LU, refinement)",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "mesh": [spec.N, spec.M], "F": F, "eps": eps,
+                   "block_bw": args.block_bw, "gmres_restart": 30, "solve": "mixed",
+                   "refine_tol_inf": 1e-9, "l2": "flushed (256 MB write) before every step, outside the step time",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "latency_ms": {"p50": statistics.median(step_ms), "p99": float(np.percentile(step_ms, 99)),
+                       "mean": mean(step_ms)},
+        "solve_stats": {k: s0[k] for k in ("newton_iters", "refine_iters", "residual_evals", "residual_evals_fp64",
+                                           "krylov_iters", "precond_applies", "final_norm_inf_fp64", "t_setup_ms")},
+        "fp64_solve": {"value": 1e3 / mean(t64), "unit": "solves/s", "ms": mean(t64),
+                       "residual_evals": st64["residual_evals"], "krylov_iters": st64["krylov_iters"],
+                       "final_norm_inf": st64["final_norm_inf"]},
+        "max_abs_dzeta_mixed_vs_fp64": dzeta,
+        "speedup_mixed_vs_fp64": value / (1e3 / mean(t64)),
+        "residual_pairs_per_s": {"fp32_kernel": pairs / (avg_pair_ms * 1e-3),
+                                 "fp64_kernel": pairs / (pair64_ms / max(1, pair64_n) * 1e-3) if pair64_n else None},
+        "roofline": {"bound": "alu", "kernel": "k_pairs<float> (all-pairs boundary-integral sum)",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "peak_note": "derived: %d SMs x %d FP32 lanes x 2 flop x %.0f MHz (MEASURED_PEAKS.json has no FP32 figure)"
+                                  % (sms, FP32_LANES_PER_SM, SM_MAX_MHZ),
+                     "flop_per_pair": FLOP_PER_PAIR, "pairs_per_launch": pairs,
+                     "avg_launch_ms": avg_pair_ms, "launches_timed": pair_n,
+                     "frac_at_measured_clock": (achieved / (sms * FP32_LANES_PER_SM * 2 * cs["sm_mhz"] * 1e6 / 1e12)
+                                                if cs["sm_mhz"] else None),
+                     "traffic": None},
+        "cpu_baseline": cpu,
+        "e2e": {"value": n_solves / (sum(e2e_ms) / 1e3) if world == 1 else args.steps / (sum(e2e_ms) / 1e3),
+                "unit": "solves/s", "h2d_bytes_per_step": ctx.n_unknowns * 8,
+                "d2h_bytes_per_step": spec.N * spec.M * 8},
+        "gpu_launches": int(launches),
+        "clocks": {"sm_mhz": cs["sm_mhz"], "sm_max_mhz": cs["sm_max_mhz"], "reasons": cs["reasons"]},
+        "wall_s_timed": wall,
+    }
+    print(json.dumps(out), flush=True)
+
+
+def run_residual_only(args):
+    import torch
+    from paper_1403_5044_b300 import swj
+    from paper_1403_5044_b300 import workloads as W
+    spec, F, eps = W.SOLVE_181x61
+    with swj.Context.from_spec(spec, F, eps) as ctx:
+        u = torch.tensor(W.random_state(spec, seed=1, amp=0.05), device="cuda")
+        E = ctx.vector()
+        for _ in range(args.steps):
+            ctx.residual(u, E, swj.FP32)
+        ctx.residual(u, E, swj.FP64)
+        ctx.sync()
+    print(json.dumps({"residual_only": True, "steps": args.steps}))
+
+
+def main():
+    args = parse()
+    if args.residual_only:
+        run_residual_only(args)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -104,8 +104,8 @@ def test_181x61_mixed_and_fp64_solves_agree_and_are_oracle_roots():
     the oracle's residual, and their surfaces agree to 1e-6."""
     spec, F, eps = W.SOLVE_181x61
     m = omesh(spec)
-    u64, z64, s64 = gpu_solve(spec, F, eps, solve_mode="fp64", block_bw=1)
-    umx, zmx, smx = gpu_solve(spec, F, eps, solve_mode="mixed", block_bw=1)
+    u64, z64, s64 = gpu_solve(spec, F, eps, solve_mode="fp64", block_bw=15)
+    umx, zmx, smx = gpu_solve(spec, F, eps, solve_mode="mixed", block_bw=15)
     assert s64["rc"] == 0 and smx["rc"] == 0, (s64, smx)
     assert np.abs(zmx - z64).max() <= 1e-6
     assert np.abs(O.residual(m, F, eps, u64)).max() < 1e-9
