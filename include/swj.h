@@ -201,6 +201,27 @@ const char *swj_strerror(int status);
 /* Library version string. */
 const char *swj_version(void);
 
+/* ---- instrumentation ---- */
+
+/* Kernel launches the library has issued since it was loaded (all
+ * contexts; a plain counter, not synchronised across host threads). */
+unsigned long long swj_kernel_launches(void);
+
+/* enable != 0: record a CUDA event pair around every launch of the all-pairs
+ * kernel on the context's stream (up to 2048 launches until the next reset),
+ * so its device time can be read back; 0: stop recording.  Either way the
+ * record is cleared.  Returns SWJ_ENOMEM / SWJ_ECUDA if the events cannot be
+ * created. */
+int swj_set_kernel_timing(swj_ctx *ctx, int enable);
+
+/* Synchronise the stream and report the summed device time (ms) and count of
+ * the recorded all-pairs launches of the given precision since the last
+ * reset. */
+int swj_pair_timing(swj_ctx *ctx, int precision, double *total_ms, int *launches);
+
+/* Clear the record of timed launches (synchronises the stream). */
+int swj_reset_pair_timing(swj_ctx *ctx);
+
 #ifdef __cplusplus
 }
 #endif

@@ -310,22 +310,27 @@ k_gj_inverse(int n, double *blocks, size_t stride, int *info)
 
 void swj_axpby(cudaStream_t st, int n, double a, const double *x, double b, double *y)
 {
+    SWJ_COUNT_LAUNCH();
     k_axpby<<<nblk(n, 256), 256, 0, st>>>(n, a, x, b, y);
 }
 void swj_axpy_dev(cudaStream_t st, int n, const double *a, double s, const double *x, double *y)
 {
+    SWJ_COUNT_LAUNCH();
     k_axpy_dev<<<nblk(n, 256), 256, 0, st>>>(n, a, s, x, y);
 }
 void swj_scale_dev(cudaStream_t st, int n, const double *num, double *x, int invert)
 {
+    SWJ_COUNT_LAUNCH();
     k_scale_dev<<<nblk(n, 256), 256, 0, st>>>(n, num, x, invert);
 }
 void swj_copy(cudaStream_t st, int n, const double *x, double *y)
 {
+    SWJ_COUNT_LAUNCH();
     k_copy<<<nblk(n, 256), 256, 0, st>>>(n, x, y);
 }
 void swj_fill(cudaStream_t st, int n, double v, double *x)
 {
+    SWJ_COUNT_LAUNCH();
     k_fill<<<nblk(n, 256), 256, 0, st>>>(n, v, x);
 }
 void swj_norms(cudaStream_t st, int n, const double *x, double *red, double *out)
@@ -333,7 +338,9 @@ void swj_norms(cudaStream_t st, int n, const double *x, double *red, double *out
     int G = nblk(n, kRedThreads);
     if (G > kRedBlocks) G = kRedBlocks;
     if (G < 1) G = 1;
+    SWJ_COUNT_LAUNCH();
     k_norms1<<<G, kRedThreads, 0, st>>>(n, x, red);
+    SWJ_COUNT_LAUNCH();
     k_norms2<<<1, kRedThreads, 0, st>>>(G, red, out);
 }
 void swj_mdot(cudaStream_t st, int n, int rows, const double *V, size_t ld, const double *w,
@@ -342,17 +349,21 @@ void swj_mdot(cudaStream_t st, int n, int rows, const double *V, size_t ld, cons
     int G = nblk(n, kRedThreads);
     if (G > 64) G = 64;
     if (G < 1) G = 1;
+    SWJ_COUNT_LAUNCH();
     k_mdot1<<<dim3(G, rows), kRedThreads, 0, st>>>(n, V, ld, w, red);
+    SWJ_COUNT_LAUNCH();
     k_mdot2<<<rows, 64, 0, st>>>(G, red, out);
 }
 void swj_mgemv_sub(cudaStream_t st, int n, int rows, const double *V, size_t ld,
                    const double *coef, double *w)
 {
+    SWJ_COUNT_LAUNCH();
     k_mgemv_sub<<<nblk(n, 256), 256, 0, st>>>(n, rows, V, ld, coef, w);
 }
 void swj_combine(cudaStream_t st, int n, int rows, const double *Z, size_t ld,
                  const double *coef, double *x, int acc)
 {
+    SWJ_COUNT_LAUNCH();
     k_combine<<<nblk(n, 256), 256, 0, st>>>(n, rows, Z, ld, coef, x, acc);
 }
 void swj_dgemm_batched(cudaStream_t st, int m, int n, int k, double alpha,
@@ -361,6 +372,7 @@ void swj_dgemm_batched(cudaStream_t st, int m, int n, int k, double alpha,
 {
     if (batch <= 0 || m <= 0 || n <= 0) return;
     dim3 grid(nblk(n, GT), nblk(m, GT), batch);
+    SWJ_COUNT_LAUNCH();
     k_dgemm<<<grid, 256, 0, st>>>(m, n, k, alpha, A, nullptr, lda, B, nullptr, ldb, beta, C,
                                   nullptr, ldc);
 }
@@ -369,6 +381,7 @@ void swj_dgemm(cudaStream_t st, int m, int n, int k, double alpha, const double 
 {
     if (m <= 0 || n <= 0) return;
     dim3 grid(nblk(n, GT), nblk(m, GT), 1);
+    SWJ_COUNT_LAUNCH();
     k_dgemm<<<grid, 256, 0, st>>>(m, n, k, alpha, nullptr, A, lda, nullptr, B, ldb, beta,
                                   nullptr, C, ldc);
 }
@@ -376,5 +389,6 @@ void swj_block_inverse(cudaStream_t st, int n, int count, double *blocks, size_t
                        int *info)
 {
     size_t sh = (size_t)n * (2 * sizeof(double) + sizeof(int));
+    SWJ_COUNT_LAUNCH();
     k_gj_inverse<<<count, 1024, sh, st>>>(n, blocks, stride, info);
 }

@@ -102,7 +102,7 @@ __global__ void k_targets(int N, int M, int H, double x1, double dx, double dy, 
                           const double *__restrict__ zetay, const double *__restrict__ gy,
                           double *__restrict__ E, double *__restrict__ e2part,
                           double *__restrict__ Ival, TgtArrays<double> t64,
-                          TgtArrays<float> t32)
+                          TgtArrays32 t32)
 {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     int T = (N - 1) * M;
@@ -135,8 +135,8 @@ __global__ void k_targets(int N, int M, int H, double x1, double dx, double dy, 
     t64.tk[t] = (double)k + 0.5; t64.tl[t] = (double)l;
     t64.zeta[t] = zs; t64.g[t] = gs; t64.zx[t] = zx;
     t64.A[t] = A; t64.B[t] = B; t64.C[t] = C;
-    t32.tk[t] = (float)k + 0.5f; t32.tl[t] = (float)l;
-    t32.zeta[t] = (float)zs; t32.g[t] = (float)gs; t32.zx[t] = (float)zx;
+    t32.x[t] = (float)(((double)k + 0.5) * (dx / dy)); t32.y[t] = (float)l;
+    t32.zeta[t] = (float)(zs / dy); t32.g[t] = (float)gs; t32.zxw[t] = (float)(zx * dy);
     t32.A[t] = (float)A; t32.B[t] = (float)B; t32.C[t] = (float)C;
     if (k == 0) {
         // radiation rows at x = x1 (forward difference for the second derivative)
@@ -153,7 +153,7 @@ __global__ void k_targets(int N, int M, int H, double x1, double dx, double dy, 
 __global__ void k_sources(int N, int M, int H, double dx, double dy, const double *__restrict__ u,
                           const double *__restrict__ zeta, const double *__restrict__ g,
                           const double *__restrict__ zetay, SrcRec<double> *__restrict__ s64,
-                          SrcRec<float> *__restrict__ s32)
+                          SrcRec32 *__restrict__ s32)
 {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= N * M) return;
@@ -170,9 +170,10 @@ __global__ void k_sources(int N, int M, int H, double dx, double dy, const doubl
     r.sj = (double)j;
     r.pad = 0.0;
     s64[s] = r;
-    SrcRec<float> q;
-    q.zeta = (float)r.zeta; q.zx = (float)r.zx; q.zy = (float)r.zy; q.g = (float)r.g;
-    q.w = (float)r.w; q.si = (float)i; q.sj = (float)j; q.pad = 0.f;
+    SrcRec32 q;
+    q.x = (float)((double)i * (dx / dy)); q.y = (float)j;
+    q.zeta = (float)(r.zeta / dy); q.zx = (float)r.zx; q.zy = (float)r.zy; q.g = (float)r.g;
+    q.w = (float)((dx / dy) * ci * cj); q.zxw = (float)(r.zx * dy);
     s32[s] = q;
 }
 
@@ -258,33 +259,41 @@ void swj_launch_mesh_step(swj_ctx *c, const double *u, double *E)
 {
     const swj_mesh &m = c->mesh;
     cudaStream_t st = c->stream;
+    SWJ_COUNT_LAUNCH();
     k_integrate<<<nblk(2L * c->M * 32, 256), 256, 0, st>>>(c->N, c->M, c->H, m.x1, m.dx, u,
                                                            c->zeta, c->g);
+    SWJ_COUNT_LAUNCH();
     k_spline<<<nblk(2L * c->N, 128), 128, 0, st>>>(c->N, c->M, m.dy, c->spl_cp, c->spl_a,
                                                     c->spl_inv, c->zeta, c->g, c->zetay, c->gy);
+    SWJ_COUNT_LAUNCH();
     k_targets<<<nblk(c->T, 128), 128, 0, st>>>(c->N, c->M, c->H, m.x1, m.dx, m.dy, c->F, c->eps,
                                                 m.n_rad, u, c->zeta, c->g, c->zetay, c->gy, E,
                                                 c->e2part, c->Ival, c->tgt64, c->tgt32);
+    SWJ_COUNT_LAUNCH();
     k_sources<<<nblk(c->S, 256), 256, 0, st>>>(c->N, c->M, c->H, m.dx, m.dy, u, c->zeta, c->g,
                                                c->zetay, c->src64, c->src32);
 }
 
 void swj_launch_assemble(swj_ctx *c, double *E, int P)
 {
+    SWJ_COUNT_LAUNCH();
     k_assemble<<<nblk(c->T, 256), 256, 0, c->stream>>>(c->N, c->M, c->H, P, c->partial,
                                                         c->e2part, E);
 }
 
 void swj_launch_flat(swj_ctx *c, double *u)
 {
+    SWJ_COUNT_LAUNCH();
     k_flat<<<nblk(c->nu, 256), 256, 0, c->stream>>>(c->N, c->M, c->H, c->mesh.x1, u);
 }
 
 void swj_launch_unpack(swj_ctx *c, const double *u, double *zo, double *po)
 {
     const swj_mesh &m = c->mesh;
+    SWJ_COUNT_LAUNCH();
     k_integrate<<<nblk(2L * c->M * 32, 256), 256, 0, c->stream>>>(c->N, c->M, c->H, m.x1, m.dx,
                                                                    u, c->zeta, c->g);
+    SWJ_COUNT_LAUNCH();
     k_unpack<<<nblk(c->S, 256), 256, 0, c->stream>>>(c->N, c->M, m.x1, m.dx, c->zeta, c->g, zo,
                                                       po);
 }
@@ -292,6 +301,7 @@ void swj_launch_unpack(swj_ctx *c, const double *u, double *zo, double *po)
 void swj_launch_surface(swj_ctx *c, double *out)
 {
     int n = c->S > c->T ? c->S : c->T;
+    SWJ_COUNT_LAUNCH();
     k_surface<<<nblk(n, 256), 256, 0, c->stream>>>(c->N, c->M, c->zeta, c->g, c->zetay, c->gy,
                                                     c->tgt64, c->Ival, out);
 }

@@ -25,18 +25,23 @@
 // Coordinates are exact index values: dx = (i - (k + 1/2)) dx_mesh, etc., so
 // the only rounding in a coordinate difference is the one product.
 //
-// FP32 variant: plain FP32 within sub-tiles of 32 sources, Kahan
-// compensation when a sub-tile total is added to the running sum.
+// FP32 variant (k_pairs32): lengths in units of dy with exact index
+// coordinates (see SrcRec32), the reciprocal square roots as single
+// rsqrt.approx.ftz.f32 instructions (every argument is at least (dx/2)^2, so
+// never denormal), plain FP32 within sub-tiles of 64 sources and Kahan
+// compensation when a sub-tile total is added to the running sum.  Stated
+// work: 7 FADD + 9 FMUL + 14 FFMA + 4 MUFU = 44 flop per pair.
+//
+// Launch plan: the number of source chunks is chosen so that
+// (target tiles) x (chunks) fills whole waves of resident blocks.
 #include "swj_internal.h"
 
 namespace {
 
 template <typename T> __device__ __forceinline__ T rsq(T x);
-template <> __device__ __forceinline__ float rsq<float>(float x) { return rsqrtf(x); }
 template <> __device__ __forceinline__ double rsq<double>(double x) { return rsqrt(x); }
 
 template <typename T> struct TileCfg;
-template <> struct TileCfg<float> { static constexpr int tile = 512; };
 template <> struct TileCfg<double> { static constexpr int tile = 256; };
 
 constexpr int kSub = 32;   // sources per compensated sub-tile
@@ -126,36 +131,140 @@ k_pairs(int T_, int S_, int chunk, const SrcRec<T> *__restrict__ src, TgtArrays<
     }
 }
 
+__device__ __forceinline__ float rsqrt_ftz(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+constexpr int kTile32 = 512;
+constexpr int kSub32 = 64;
+
+template <int R>
+__global__ void __launch_bounds__(128)
+k_pairs32(int T_, int S_, int chunk, const SrcRec32 *__restrict__ src, TgtArrays32 tg,
+          double *__restrict__ partial)
+{
+    __shared__ SrcRec32 sh[kTile32];
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int s0 = blockIdx.y * chunk;
+    const int s1 = min(S_, s0 + chunk);
+    float tx[R], ty[R], tz[R], tgv[R], tzw[R], A[R], B[R], C[R], sum[R], comp[R];
+    const int tb = blockIdx.x * R * nth + tid;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        int t = min(tb + r * nth, T_ - 1);
+        tx[r] = tg.x[t]; ty[r] = tg.y[t]; tz[r] = tg.zeta[t]; tgv[r] = tg.g[t];
+        tzw[r] = tg.zxw[t]; A[r] = tg.A[t]; B[r] = tg.B[t]; C[r] = tg.C[t];
+        sum[r] = 0.f; comp[r] = 0.f;
+    }
+    for (int base = s0; base < s1; base += kTile32) {
+        const int nt = min(kTile32, s1 - base);
+        __syncthreads();
+        for (int i = tid; i < nt; i += nth) sh[i] = src[base + i];
+        __syncthreads();
+        for (int sb = 0; sb < nt; sb += kSub32) {
+            const int se = min(sb + kSub32, nt);
+            float loc[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) loc[r] = 0.f;
+#pragma unroll 2
+            for (int s = sb; s < se; ++s) {
+                const SrcRec32 q = sh[s];
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    float p = q.x - tx[r];
+                    float qq = q.y - ty[r];
+                    float qp = q.y + ty[r];
+                    float dz = q.zeta - tz[r];
+                    float p2 = p * p;
+                    float bs = fmaf(dz, dz, p2);
+                    float r1s = fmaf(qq, qq, bs);
+                    float r2s = fmaf(qp, qp, bs);
+                    float nc = fmaf(-p, q.zx, dz);
+                    float n1 = fmaf(-qq, q.zy, nc);
+                    float n2 = fmaf(-qp, q.zy, nc);
+                    float i1 = rsqrt_ftz(r1s), i2 = rsqrt_ftz(r2s);
+                    float i1c = i1 * i1 * i1, i2c = i2 * i2 * i2;
+                    float K1 = fmaf(n1, i1c, n2 * i2c);
+                    float K2 = i1 + i2;
+                    float Ap2 = A[r] * p2;
+                    float Bp = B[r] * p;
+                    float Q1 = fmaf(fmaf(C[r], qq, Bp), qq, Ap2);
+                    float Q2 = fmaf(fmaf(C[r], qp, -Bp), qp, Ap2);
+                    float S2 = rsqrt_ftz(Q1) + rsqrt_ftz(Q2);
+                    float f = q.g - tgv[r];
+                    float inner = fmaf(q.zxw, K2, fmaf(f, K1, -tzw[r] * S2));
+                    loc[r] = fmaf(q.w, inner, loc[r]);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                float y = loc[r] - comp[r];
+                float t2 = sum[r] + y;
+                comp[r] = (t2 - sum[r]) - y;
+                sum[r] = t2;
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        int t = tb + r * nth;
+        if (t < T_) partial[(size_t)blockIdx.y * T_ + t] = (double)sum[r] - (double)comp[r];
+    }
+}
+
 constexpr int kTPB = 128;
 constexpr int kR = 4;
 
-PairPlan make_plan(int T, int S, int num_sms)
+// Source-chunk count P for (tiles) target tiles: (tiles x P) blocks should fill
+// whole waves of `slots` resident blocks; chunks keep at least 64 sources.
+PairPlan make_plan(int T, int S, int slots)
 {
     PairPlan p;
     p.tpb = kTPB;
     p.R = kR;
     p.tiles = (T + kTPB * kR - 1) / (kTPB * kR);
-    int want = 4 * num_sms;
-    int P = (want + p.tiles - 1) / p.tiles;
     int maxP = S / 64 > 1 ? S / 64 : 1;
-    if (P > maxP) P = maxP;
-    if (P < 1) P = 1;
-    p.chunk = (S + P - 1) / P;
+    if (maxP > 4096) maxP = 4096;
+    int bestP = 1;
+    double best = -1.0;
+    for (int P = 1; P <= maxP; ++P) {
+        long items = (long)p.tiles * P;
+        long waves = (items + slots - 1) / slots;
+        double eff = (double)items / (double)(waves * slots);
+        // prefer a fuller last wave; among equals, fewer chunks
+        if (eff > best + 0.02) { best = eff; bestP = P; }
+        if (items >= 8L * slots) break;
+    }
+    p.chunk = (S + bestP - 1) / bestP;
     p.P = (S + p.chunk - 1) / p.chunk;
     return p;
+}
+
+int resident_blocks(const void *kernel, int threads)
+{
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, 0) != cudaSuccess || nb < 1)
+        nb = 1;
+    return nb;
 }
 
 }  // namespace
 
 PairPlan swj_pair_plan(const swj_ctx *c, int precision)
 {
-    (void)precision;
-    return make_plan(c->T, c->S, c->num_sms);
+    const void *k = (precision == SWJ_FP64) ? (const void *)k_pairs<double, kR, false>
+                                             : (const void *)k_pairs32<kR>;
+    int slots = c->num_sms * resident_blocks(k, kTPB);
+    return make_plan(c->T, c->S, slots);
 }
 
 void swj_launch_pairs64(swj_ctx *c, const PairPlan &pl)
 {
     dim3 grid(pl.tiles, pl.P);
+    SWJ_COUNT_LAUNCH();
     k_pairs<double, kR, false><<<grid, kTPB, 0, c->stream>>>(
         c->T, c->S, pl.chunk, c->src64, c->tgt64, c->mesh.dx, c->mesh.dy, c->partial);
 }
@@ -163,15 +272,15 @@ void swj_launch_pairs64(swj_ctx *c, const PairPlan &pl)
 void swj_launch_pairs32(swj_ctx *c, const PairPlan &pl)
 {
     dim3 grid(pl.tiles, pl.P);
-    k_pairs<float, kR, true><<<grid, kTPB, 0, c->stream>>>(
-        c->T, c->S, pl.chunk, c->src32, c->tgt32, (float)c->mesh.dx, (float)c->mesh.dy,
-        c->partial);
+    SWJ_COUNT_LAUNCH();
+    k_pairs32<kR><<<grid, kTPB, 0, c->stream>>>(c->T, c->S, pl.chunk, c->src32, c->tgt32,
+                                                c->partial);
 }
 
-void swj_launch_pairs_generic32(cudaStream_t st, int T, int S, const SrcRec<float> *src,
-                                const TgtArrays<float> &tgt, float dX, float dY,
-                                double *partial, const PairPlan &pl)
+void swj_launch_pairs_generic32(cudaStream_t st, int T, int S, const SrcRec32 *src,
+                                const TgtArrays32 &tgt, double *partial, const PairPlan &pl)
 {
     dim3 grid(pl.tiles, pl.P);
-    k_pairs<float, kR, true><<<grid, kTPB, 0, st>>>(T, S, pl.chunk, src, tgt, dX, dY, partial);
+    SWJ_COUNT_LAUNCH();
+    k_pairs32<kR><<<grid, kTPB, 0, st>>>(T, S, pl.chunk, src, tgt, partial);
 }

@@ -33,7 +33,6 @@
 namespace {
 
 constexpr double kPi = 3.14159265358979323846;
-constexpr int kMaxTerms = 64;
 
 inline int nblk(long n, int b) { return (int)((n + b - 1) / b); }
 
@@ -126,7 +125,7 @@ __global__ void k_transpose(int n, const double *__restrict__ in, double *__rest
 // sum is sum_s w_s K2 = sum_s w_s K3.
 template <typename T>
 __global__ void k_flat_records(int N, int M, double dx, double dy, SrcRec<T> *src,
-                               TgtArrays<T> tg)
+                               TgtArrays<T> tg)  // FP64 records
 {
     int e = blockIdx.x * blockDim.x + threadIdx.x;
     int S = N * M, Tn = (N - 1) * M;
@@ -144,6 +143,29 @@ __global__ void k_flat_records(int N, int M, double dx, double dy, SrcRec<T> *sr
         tg.tk[e] = (T)k + (T)0.5; tg.tl[e] = (T)l;
         tg.zeta[e] = T(0); tg.g[e] = T(0); tg.zx[e] = T(0);
         tg.A[e] = T(1); tg.B[e] = T(0); tg.C[e] = T(1);
+    }
+}
+
+// The same flat-state records in the scaled FP32 units (see SrcRec32).
+__global__ void k_flat_records32(int N, int M, double dx, double dy, SrcRec32 *src, TgtArrays32 tg)
+{
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    int S = N * M, Tn = (N - 1) * M;
+    double rho = dx / dy;
+    if (e < S) {
+        int i = e % N, j = e / N;
+        double ci = (i == 0 || i == N - 1) ? 0.5 : 1.0;
+        double cj = (j == 0 || j == M - 1) ? 0.5 : 1.0;
+        SrcRec32 r;
+        r.x = (float)(i * rho); r.y = (float)j; r.zeta = 0.f; r.zx = 1.f; r.zy = 0.f; r.g = 0.f;
+        r.w = (float)(rho * ci * cj); r.zxw = (float)dy;
+        src[e] = r;
+    }
+    if (e < Tn) {
+        int k = e % (N - 1), l = e / (N - 1);
+        tg.x[e] = (float)((k + 0.5) * rho); tg.y[e] = (float)l;
+        tg.zeta[e] = 0.f; tg.g[e] = 0.f; tg.zxw[e] = 0.f;
+        tg.A[e] = 1.f; tg.B[e] = 0.f; tg.C[e] = 1.f;
     }
 }
 
@@ -198,36 +220,6 @@ __global__ void k_fill_band(int N, int M, int h, double x1, double dx, double dy
     }
 }
 
-struct BandTerms {
-    const double *mat[kMaxTerms];
-    const double *vec[kMaxTerms];
-};
-
-// out = (inv ? inv * base : base) - sum_q mat[q] * vec[q]   (n1-vectors, n1 x n1 blocks)
-// one warp per output row.
-__global__ void k_band_step(int n1, int nterms, BandTerms bt, const double *__restrict__ base,
-                            const double *__restrict__ inv, double *__restrict__ out)
-{
-    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    if (warp >= n1) return;
-    const size_t r = warp;
-    double s = 0.0;
-    if (inv) {
-        for (int c = lane; c < n1; c += 32) s = fma(inv[r * n1 + c], base[c], s);
-    } else if (lane == 0) {
-        s = base[r];
-    }
-    for (int q = 0; q < nterms; ++q) {
-        const double *Mq = bt.mat[q] + r * n1;
-        const double *vq = bt.vec[q];
-        for (int c = lane; c < n1; c += 32) s = fma(-Mq[c], vq[c], s);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) out[r] = s;
-}
-
 // x_l = inv_l t_l for every block row l (block-diagonal S, h = 0).
 __global__ void k_blockdiag_gemv(int n1, int M, const double *__restrict__ band, size_t bstride,
                                  const double *__restrict__ t, double *__restrict__ x)
@@ -255,7 +247,8 @@ inline double *blk(swj_ctx *c, int l, int m)
 void free_pc(swj_ctx *c)
 {
     double **bufs[] = {&c->pc_Ainv, &c->pc_AinvB, &c->pc_CAinv, &c->pc_G, &c->pc_A, &c->pc_B,
-                       &c->pc_C, &c->pc_tmp, &c->pc_band, &c->pc_sumK3, &c->pc_t1, &c->pc_t2};
+                       &c->pc_C, &c->pc_tmp, &c->pc_band, &c->pc_sumK3, &c->pc_t1, &c->pc_t2,
+                       &c->pc_work};
     for (double **b : bufs) {
         if (*b) cudaFree(*b);
         *b = nullptr;
@@ -280,7 +273,8 @@ int swj_pc_setup(swj_ctx *c)
     int b = c->opts.block_bw;
     int h = (b == 0) ? M - 1 : (b - 1) / 2;
     if (h > M - 1) h = M - 1;
-    if (h > kMaxTerms) return SWJ_EINVAL;
+    // the band sweep stages h + 1 block vectors in shared memory
+    if ((size_t)(h + 1) * n1 * sizeof(double) > 200 * 1024) return SWJ_EINVAL;
     const size_t n2 = (size_t)n1 * n1;
     const int nb = 2 * h + 1;
     if (!c->pc_band || c->pc_h != h) {
@@ -288,11 +282,12 @@ int swj_pc_setup(swj_ctx *c)
         c->pc_h = h;
         c->pc_nb = nb;
         size_t sz[] = {n2, n2, n2, n2, n2, n2, n2, (size_t)(h > 0 ? h : 1) * n2,
-                       (size_t)M * nb * n2, (size_t)c->T, (size_t)c->H, (size_t)c->H};
+                       (size_t)M * nb * n2, (size_t)c->T, (size_t)c->H, (size_t)c->H,
+                       (size_t)(h == 0 ? M : 1) * n2};
         double **bufs[] = {&c->pc_Ainv, &c->pc_AinvB, &c->pc_CAinv, &c->pc_G, &c->pc_A,
                            &c->pc_B, &c->pc_C, &c->pc_tmp, &c->pc_band, &c->pc_sumK3,
-                           &c->pc_t1, &c->pc_t2};
-        for (int i = 0; i < 12; ++i)
+                           &c->pc_t1, &c->pc_t2, &c->pc_work};
+        for (int i = 0; i < 13; ++i)
             if (cudaMalloc(bufs[i], sz[i] * sizeof(double)) != cudaSuccess) {
                 free_pc(c);
                 return SWJ_ENOMEM;
@@ -304,21 +299,28 @@ int swj_pc_setup(swj_ctx *c)
     }
     c->pc_ready = 0;
     // --- repeated blocks A, B, C and their products (Appendix C)
+    SWJ_COUNT_LAUNCH();
     k_build_ABC<<<nblk((long)n2, 256), 256, 0, st>>>(N, m.x1, m.dx, m.n_rad, c->F, c->pc_A,
                                                      c->pc_B, c->pc_C);
     double *cpv = c->pc_t1;   // n1 scratch
+    SWJ_COUNT_LAUNCH();
     k_tri_coef<<<1, 1, 0, st>>>(n1, c->pc_A, cpv);
     double *Ainv = c->pc_tmp;            // untransposed products in scratch
+    SWJ_COUNT_LAUNCH();
     k_tri_cols<<<nblk(n1, 128), 128, 0, st>>>(n1, n1, c->pc_A, cpv, nullptr, Ainv);
     double *AinvB = c->pc_G;             // temporarily
+    SWJ_COUNT_LAUNCH();
     k_tri_cols<<<nblk(n1, 128), 128, 0, st>>>(n1, n1, c->pc_A, cpv, c->pc_B, AinvB);
     // CAinv and G = C (A^-1 B); store transposes for the row-major apply GEMMs
     double *CAinv = c->pc_band;          // band not filled yet: use as scratch (>= 2 n2)
     double *Gtmp = c->pc_band + n2;
     swj_dgemm(st, n1, n1, n1, 1.0, c->pc_C, n1, Ainv, n1, 0.0, CAinv, n1);
     swj_dgemm(st, n1, n1, n1, 1.0, c->pc_C, n1, AinvB, n1, 0.0, Gtmp, n1);
+    SWJ_COUNT_LAUNCH();
     k_transpose<<<nblk((long)n2, 256), 256, 0, st>>>(n1, Ainv, c->pc_Ainv);
+    SWJ_COUNT_LAUNCH();
     k_transpose<<<nblk((long)n2, 256), 256, 0, st>>>(n1, AinvB, c->pc_AinvB);
+    SWJ_COUNT_LAUNCH();
     k_transpose<<<nblk((long)n2, 256), 256, 0, st>>>(n1, CAinv, c->pc_CAinv);
     SWJ_CUDA_TRY(cudaMemcpyAsync(c->pc_G, Gtmp, n2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
     // --- PreD diagonal correction: trapezoid sum of w K3 and I of the flat surface
@@ -326,21 +328,29 @@ int swj_pc_setup(swj_ctx *c)
     PairPlan pl = swj_pair_plan(c, prec);
     int ne = c->S > c->T ? c->S : c->T;
     if (prec == SWJ_FP64) {
+        SWJ_COUNT_LAUNCH();
         k_flat_records<double><<<nblk(ne, 256), 256, 0, st>>>(N, M, m.dx, m.dy, c->src64, c->tgt64);
         swj_launch_pairs64(c, pl);
     } else {
-        k_flat_records<float><<<nblk(ne, 256), 256, 0, st>>>(N, M, m.dx, m.dy, c->src32, c->tgt32);
+        SWJ_COUNT_LAUNCH();
+        k_flat_records32<<<nblk(ne, 256), 256, 0, st>>>(N, M, m.dx, m.dy, c->src32, c->tgt32);
         swj_launch_pairs32(c, pl);
     }
+    SWJ_COUNT_LAUNCH();
     k_diag_corr<<<nblk(c->T, 256), 256, 0, st>>>(N, M, pl.P, m.dx, m.dy, c->partial, c->pc_sumK3);
     // --- band of S
+    SWJ_COUNT_LAUNCH();
     k_fill_band<<<4 * c->num_sms, 256, 0, st>>>(N, M, h, m.x1, m.dx, m.dy, m.n_rad, c->pc_sumK3,
                                                 c->pc_G, c->pc_band);
     // --- block LU
     SWJ_CUDA_TRY(cudaMemsetAsync(c->pc_info, 0, (size_t)M * sizeof(int), st));
     const size_t bstride = (size_t)nb * n2;
+    int rc;
     if (h == 0) {
-        swj_block_inverse(st, n1, M, c->pc_band, bstride, c->pc_info);
+        SWJ_CUDA_TRY(cudaMemcpyAsync(c->pc_work, c->pc_band, (size_t)M * n2 * sizeof(double),
+                                     cudaMemcpyDeviceToDevice, st));
+        rc = swj_gj_inverse_cluster(st, n1, M, c->pc_work, n2, c->pc_band, bstride, c->pc_info);
+        if (rc) return rc;
     } else {
         // device pointer triples for every batched GEMM of the factorisation
         std::vector<const double *> PA, PB;
@@ -388,7 +398,10 @@ int swj_pc_setup(swj_ctx *c)
                                      cudaMemcpyHostToDevice, st));
         double **dA = c->pc_ptrs, **dB = c->pc_ptrs + np, **dC = c->pc_ptrs + 2 * np;
         for (int i = 0; i < M; ++i) {
-            swj_block_inverse(st, n1, 1, blk(c, i, i), n2, c->pc_info + i);
+            SWJ_CUDA_TRY(cudaMemcpyAsync(c->pc_work, blk(c, i, i), n2 * sizeof(double),
+                                         cudaMemcpyDeviceToDevice, st));
+            rc = swj_gj_inverse_cluster(st, n1, 1, c->pc_work, n2, blk(c, i, i), n2, c->pc_info + i);
+            if (rc) return rc;
             if (cnt2[i]) {
                 swj_dgemm_batched(st, n1, n1, n1, 1.0, (const double *const *)(dA + off2[i]), n1,
                                   (const double *const *)(dB + off2[i]), n1, 0.0, dC + off2[i], n1,
@@ -435,30 +448,11 @@ int swj_pc_apply(swj_ctx *c, const double *b, double *r)
     swj_dgemm(st, M, n1, n1, 1.0, b1, n1, c->pc_Ainv, n1, 0.0, t1, n1);
     // s2 = S^-1 t2 into r2
     if (h == 0) {
+        SWJ_COUNT_LAUNCH();
         k_blockdiag_gemv<<<nblk((long)n1 * M * 32, 256), 256, 0, st>>>(n1, M, c->pc_band, n2, t2, r2);
     } else {
-        BandTerms bt;
-        int wb = nblk((long)n1 * 32, 256);
-        for (int i = 1; i < M; ++i) {             // forward: y_i = t_i - sum_j L_ij y_j (in place)
-            int j0 = i - h > 0 ? i - h : 0, nt = 0;
-            for (int j = j0; j < i; ++j) {
-                bt.mat[nt] = blk(c, i, j);
-                bt.vec[nt] = t2 + (size_t)j * n1;
-                ++nt;
-            }
-            k_band_step<<<wb, 256, 0, st>>>(n1, nt, bt, t2 + (size_t)i * n1, nullptr,
-                                            t2 + (size_t)i * n1);
-        }
-        for (int i = M - 1; i >= 0; --i) {        // backward: x_i = inv_i y_i - sum_k W_ik x_k
-            int kmax = i + h < M - 1 ? i + h : M - 1, nt = 0;
-            for (int k = i + 1; k <= kmax; ++k) {
-                bt.mat[nt] = blk(c, i, k);
-                bt.vec[nt] = r2 + (size_t)k * n1;
-                ++nt;
-            }
-            k_band_step<<<wb, 256, 0, st>>>(n1, nt, bt, t2 + (size_t)i * n1, blk(c, i, i),
-                                            r2 + (size_t)i * n1);
-        }
+        int rc = swj_band_sweep_cluster(st, n1, M, h, c->pc_band, t2, r2);
+        if (rc) return rc;
     }
     // r1 = A^-1 b1 - A^-1 B s2
     swj_dgemm(st, M, n1, n1, -1.0, r2, n1, c->pc_AinvB, n1, 1.0, t1, n1);

@@ -124,6 +124,7 @@ int gmres(swj_ctx *c, const double *u, const double *Ebase, int prec, const doub
     swj_fill(s, n, 0.0, x);
     if (!isfinite(nb.two)) return SWJ_ENAN;
     if (nb.two == 0.0) return SWJ_OK;
+    SWJ_COUNT_LAUNCH();
     k_scale_to<<<nblk(n, 256), 256, 0, s>>>(n, 1.0 / nb.two, rhs, c->V);
     double beta = nb.two;
     const double target = rtol * nb.two;
@@ -149,6 +150,7 @@ int gmres(swj_ctx *c, const double *u, const double *Ebase, int prec, const doub
             swj_mgemv_sub(s, n, j + 1, c->V, ld, c->dscal + DS_H1, w);
             swj_mdot(s, n, j + 1, c->V, ld, w, c->red, c->dscal + DS_H2);
             swj_mgemv_sub(s, n, j + 1, c->V, ld, c->dscal + DS_H2, w);
+            SWJ_COUNT_LAUNCH();
             k_add_rows<<<1, 64, 0, s>>>(j + 1, c->dscal + DS_H1, c->dscal + DS_H2);
             swj_norms(s, n, w, c->red, c->dscal + DS_NW);
             SWJ_CUDA_TRY(cudaMemcpyAsync(c->hpin + DS_H1, c->dscal + DS_H1, (size_t)(j + 1) * sizeof(double),
@@ -181,7 +183,10 @@ int gmres(swj_ctx *c, const double *u, const double *Ebase, int prec, const doub
             est = fabs(gv[j + 1]);
             ++total;
             k = j + 1;
-            if (hn > 0.0) k_scale_to<<<nblk(n, 256), 256, 0, s>>>(n, 1.0 / hn, w, w);
+            if (hn > 0.0) {
+                SWJ_COUNT_LAUNCH();
+                k_scale_to<<<nblk(n, 256), 256, 0, s>>>(n, 1.0 / hn, w, w);
+            }
             if (est <= target || hn == 0.0 || total >= maxit) { done = true; break; }
         }
         // y = R^-1 g (upper triangular k x k)
@@ -214,6 +219,7 @@ int gmres(swj_ctx *c, const double *u, const double *Ebase, int prec, const doub
         if (!isfinite(nr.two)) return SWJ_ENAN;
         beta = nr.two;
         if (beta <= target) break;
+        SWJ_COUNT_LAUNCH();
         k_scale_to<<<nblk(n, 256), 256, 0, s>>>(n, 1.0 / beta, c->rvec, c->V);
     }
     SWJ_CUDA_TRY(cudaGetLastError());
@@ -234,6 +240,7 @@ int newton_phase(swj_ctx *c, double *u, int prec, double tol, int max_it, PhaseR
     for (int it = 0; it < max_it; ++it) {
         if (!isfinite(ph->finf)) { ph->status = SWJ_ENAN; return SWJ_ENAN; }
         if (ph->finf < tol) { ph->status = SWJ_OK; return SWJ_OK; }
+        SWJ_COUNT_LAUNCH();
         k_scale_to<<<nblk(n, 256), 256, 0, s>>>(n, -1.0, c->E_cur, c->rvec);
         GmresResult gr;
         int rc = gmres(c, u, c->E_cur, prec, c->rvec, c->du, eta, o.max_krylov, &gr, st);
@@ -283,13 +290,15 @@ int newton_phase(swj_ctx *c, double *u, int prec, double tol, int max_it, PhaseR
 int swj_residual_impl(swj_ctx *c, const double *u, double *E, int precision)
 {
     swj_launch_mesh_step(c, u, E);
-    if (precision == SWJ_FP64) {
-        swj_launch_pairs64(c, c->plan64);
-        swj_launch_assemble(c, E, c->plan64.P);
-    } else {
-        swj_launch_pairs32(c, c->plan32);
-        swj_launch_assemble(c, E, c->plan32.P);
+    const bool rec = c->time_pairs && c->tev && c->n_timed < SWJ_MAX_TIMED;
+    if (rec) cudaEventRecord(c->tev[2 * c->n_timed], c->stream);
+    if (precision == SWJ_FP64) swj_launch_pairs64(c, c->plan64);
+    else swj_launch_pairs32(c, c->plan32);
+    if (rec) {
+        cudaEventRecord(c->tev[2 * c->n_timed + 1], c->stream);
+        c->tev_prec[c->n_timed++] = precision;
     }
+    swj_launch_assemble(c, E, precision == SWJ_FP64 ? c->plan64.P : c->plan32.P);
     SWJ_CUDA_TRY(cudaGetLastError());
     return SWJ_OK;
 }
@@ -304,10 +313,13 @@ int swj_jvp_impl(swj_ctx *c, const double *u, const double *Eu, const double *v,
         swj_norms(s, n, v, c->red, c->dscal + DS_NV);
     }
     double epsm = (precision == SWJ_FP64) ? 2.220446049250313e-16 : 1.1920928955078125e-07;
+    SWJ_COUNT_LAUNCH();
     k_fd_h<<<1, 1, 0, s>>>(c->dscal + DS_NU, c->dscal + DS_NV, epsm, h_fixed, c->dscal + DS_H);
+    SWJ_COUNT_LAUNCH();
     k_perturb<<<nblk(n, 256), 256, 0, s>>>(n, u, v, c->dscal + DS_H, c->u_tmp);
     int rc = swj_residual_impl(c, c->u_tmp, c->E_tmp, precision);
     if (rc) return rc;
+    SWJ_COUNT_LAUNCH();
     k_fd_diff<<<nblk(n, 256), 256, 0, s>>>(n, c->E_tmp, Eu, c->dscal + DS_H, Jv);
     SWJ_CUDA_TRY(cudaGetLastError());
     return SWJ_OK;
@@ -367,6 +379,7 @@ int swj_solve_impl(swj_ctx *c, double *u, swj_stats *stats)
         if (r == o.refine_max) break;
         rc = residual_counted(c, u, c->E_base32, SWJ_FP32, st);
         if (rc) { status = rc; break; }
+        SWJ_COUNT_LAUNCH();
         k_scale_to<<<nblk(n, 256), 256, 0, s>>>(n, -1.0, c->E_cur, c->rvec);
         GmresResult gr;
         rc = gmres(c, u, c->E_base32, SWJ_FP32, c->rvec, c->du, 1e-3, o.max_krylov, &gr, st);

@@ -5,6 +5,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+unsigned long long g_swj_launches = 0;
+
 namespace {
 
 bool valid_mesh(const swj_mesh *m)
@@ -47,6 +49,11 @@ void free_all(swj_ctx *c)
     swj_pc_free(c);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
+    if (c->tev) {
+        for (int i = 0; i < 2 * SWJ_MAX_TIMED; ++i) cudaEventDestroy(c->tev[i]);
+        free(c->tev);
+        free(c->tev_prec);
+    }
 }
 
 int alloc_all(swj_ctx *c)
@@ -70,7 +77,7 @@ int alloc_all(swj_ctx *c)
     double *b = c->tgt64_base;
     c->tgt64 = TgtArrays<double>{b, b + T, b + 2 * T, b + 3 * T, b + 4 * T, b + 5 * T, b + 6 * T, b + 7 * T};
     float *f = c->tgt32_base;
-    c->tgt32 = TgtArrays<float>{f, f + T, f + 2 * T, f + 3 * T, f + 4 * T, f + 5 * T, f + 6 * T, f + 7 * T};
+    c->tgt32 = TgtArrays32{f, f + T, f + 2 * T, f + 3 * T, f + 4 * T, f + 5 * T, f + 6 * T, f + 7 * T};
     c->plan64 = swj_pair_plan(c, SWJ_FP64);
     c->plan32 = swj_pair_plan(c, SWJ_FP32);
     int P = c->plan64.P > c->plan32.P ? c->plan64.P : c->plan32.P;
@@ -299,5 +306,46 @@ const char *swj_strerror(int s)
 }
 
 const char *swj_version(void) { return SWJ_VERSION_STRING; }
+
+unsigned long long swj_kernel_launches(void) { return g_swj_launches; }
+
+int swj_set_kernel_timing(swj_ctx *c, int enable)
+{
+    if (!c) return SWJ_EINVAL;
+    if (enable && !c->tev) {
+        c->tev = (cudaEvent_t *)calloc(2 * SWJ_MAX_TIMED, sizeof(cudaEvent_t));
+        c->tev_prec = (int *)calloc(SWJ_MAX_TIMED, sizeof(int));
+        if (!c->tev || !c->tev_prec) return SWJ_ENOMEM;
+        for (int i = 0; i < 2 * SWJ_MAX_TIMED; ++i)
+            if (cudaEventCreate(&c->tev[i]) != cudaSuccess) return SWJ_ECUDA;
+    }
+    c->time_pairs = enable ? 1 : 0;
+    c->n_timed = 0;
+    return SWJ_OK;
+}
+
+int swj_pair_timing(swj_ctx *c, int precision, double *total_ms, int *launches)
+{
+    if (!c || !total_ms || !launches) return SWJ_EINVAL;
+    *total_ms = 0.0;
+    *launches = 0;
+    SWJ_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    for (int i = 0; i < c->n_timed; ++i) {
+        if (c->tev_prec[i] != precision) continue;
+        float ms = 0.f;
+        SWJ_CUDA_TRY(cudaEventElapsedTime(&ms, c->tev[2 * i], c->tev[2 * i + 1]));
+        *total_ms += ms;
+        ++*launches;
+    }
+    return SWJ_OK;
+}
+
+int swj_reset_pair_timing(swj_ctx *c)
+{
+    if (!c) return SWJ_EINVAL;
+    SWJ_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    c->n_timed = 0;
+    return SWJ_OK;
+}
 
 }  // extern "C"

@@ -25,6 +25,23 @@ template <typename T> struct SrcRec {
     T pad;
 };
 
+// FP32 source record, lengths in units of L = dy (rho = dx / dy):
+//   x = i rho, y = j (exact when rho is a short binary fraction, e.g. 1),
+//   zeta = zeta_ij / L, zx, zy = slopes, g = g_ij, w = rho c_i c_j (= w(i,j) / L^2),
+//   zxw = L (zeta_x)_ij.
+// With r' = r / L the pair term w [(g - g*) K1 + zx K2 - zx* S2] equals
+// w' [(g - g*) K1' + zxw K2' - zxw* S2'] where K1', K2', S2' are the kernels
+// evaluated in these units, so no coordinate needs rescaling per pair.
+struct SrcRec32 {
+    float x, y, zeta, zx, zy, g, w, zxw;
+};
+
+// FP32 target arrays in the same units: x = (k + 1/2) rho, y = l, zeta* / L,
+// g*, L zeta_x*, and the dimensionless A, B, C.
+struct TgtArrays32 {
+    float *x, *y, *zeta, *g, *zxw, *A, *B, *C;
+};
+
 // Per-target record (one per half-mesh point (k + 1/2, l)), structure of
 // arrays, each of length T.
 template <typename T> struct TgtArrays {
@@ -67,9 +84,9 @@ struct swj_ctx {
     double *Ival;      // I per target (diagnostics)
     // records for the two precisions
     SrcRec<double> *src64;
-    SrcRec<float> *src32;
+    SrcRec32 *src32;
     TgtArrays<double> tgt64;
-    TgtArrays<float> tgt32;
+    TgtArrays32 tgt32;
     double *tgt64_base; float *tgt32_base;
     // partial sums [P][T]
     double *partial;
@@ -98,9 +115,15 @@ struct swj_ctx {
     double **pc_ptrs;            // device pointer arrays for batched block GEMMs
     int pc_ptrs_cap;
     double *pc_t1, *pc_t2;       // apply temporaries [H]
+    double *pc_work;             // Gauss-Jordan work copy: M blocks (h = 0) or one block
 
     size_t bytes;                // device bytes held
     cudaEvent_t ev0, ev1;
+    // optional timing of every all-pairs launch (events on the context's stream)
+    int time_pairs;
+    int n_timed;
+    cudaEvent_t *tev;            // 2 * SWJ_MAX_TIMED events, created on first enable
+    int *tev_prec;               // precision of each timed launch (host array)
 };
 
 // ---------------------------------------------------------------- launches
@@ -116,9 +139,8 @@ void swj_launch_surface(swj_ctx *c, double *out);
 PairPlan swj_pair_plan(const swj_ctx *c, int precision);
 void swj_launch_pairs64(swj_ctx *c, const PairPlan &pl);
 void swj_launch_pairs32(swj_ctx *c, const PairPlan &pl);
-void swj_launch_pairs_generic32(cudaStream_t st, int T, int S, const SrcRec<float> *src,
-                                const TgtArrays<float> &tgt, float dX, float dY,
-                                double *partial, const PairPlan &pl);
+void swj_launch_pairs_generic32(cudaStream_t st, int T, int S, const SrcRec32 *src,
+                                const TgtArrays32 &tgt, double *partial, const PairPlan &pl);
 
 // linalg.cu
 void swj_axpby(cudaStream_t st, int n, double a, const double *x, double b, double *y);      // y = a x + b y
@@ -148,6 +170,12 @@ void swj_dgemm(cudaStream_t st, int m, int n, int k, double alpha, const double 
 // partial pivoting; info[b] = 0 or 1 + failing column.
 void swj_block_inverse(cudaStream_t st, int n, int count, double *blocks, size_t stride, int *info);
 
+// cluster.cu
+int swj_gj_inverse_cluster(cudaStream_t st, int n, int count, double *work, size_t wstride,
+                           double *out, size_t ostride, int *info);
+int swj_band_sweep_cluster(cudaStream_t st, int n1, int M, int h, const double *band, double *y,
+                           double *x);
+
 // precond.cu
 int swj_pc_setup(swj_ctx *c);
 int swj_pc_apply(swj_ctx *c, const double *b, double *r);
@@ -158,5 +186,12 @@ int swj_residual_impl(swj_ctx *c, const double *u, double *E, int precision);
 int swj_jvp_impl(swj_ctx *c, const double *u, const double *Eu, const double *v, double *Jv,
                  int precision, double h_fixed);
 int swj_solve_impl(swj_ctx *c, double *u, swj_stats *st);
+
+// Running count of kernel launches issued by the library (all contexts;
+// not synchronised across host threads).
+extern unsigned long long g_swj_launches;
+#define SWJ_COUNT_LAUNCH() (++g_swj_launches)
+
+#define SWJ_MAX_TIMED 2048   // pair-kernel launches whose duration can be recorded
 
 #define SWJ_CUDA_TRY(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) return SWJ_ECUDA; } while (0)

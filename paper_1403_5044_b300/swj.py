@@ -88,6 +88,10 @@ def lib():
             "swj_sync": (ctypes.c_int, [_vp]),
             "swj_strerror": (ctypes.c_char_p, [ctypes.c_int]),
             "swj_version": (ctypes.c_char_p, []),
+            "swj_kernel_launches": (ctypes.c_ulonglong, []),
+            "swj_set_kernel_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
+            "swj_pair_timing": (ctypes.c_int, [_vp, ctypes.c_int, P(ctypes.c_double), P(ctypes.c_int)]),
+            "swj_reset_pair_timing": (ctypes.c_int, [_vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -110,6 +114,11 @@ def strerror(status: int) -> str:
 
 def version() -> str:
     return lib().swj_version().decode()
+
+
+def kernel_launches() -> int:
+    """Kernel launches issued by the library since it was loaded."""
+    return int(lib().swj_kernel_launches())
 
 
 def default_opts(**kw) -> Opts:
@@ -229,3 +238,16 @@ class Context:
 
     def sync(self):
         _check(lib().swj_sync(self._h), "swj_sync")
+
+    def set_kernel_timing(self, enable=True):
+        _check(lib().swj_set_kernel_timing(self._h, int(bool(enable))), "swj_set_kernel_timing")
+
+    def reset_pair_timing(self):
+        _check(lib().swj_reset_pair_timing(self._h), "swj_reset_pair_timing")
+
+    def pair_timing(self, precision):
+        """(total device ms, launches) of the timed all-pairs launches."""
+        ms, n = ctypes.c_double(), ctypes.c_int()
+        _check(lib().swj_pair_timing(self._h, int(precision), ctypes.byref(ms), ctypes.byref(n)),
+               "swj_pair_timing")
+        return ms.value, n.value

@@ -61,7 +61,9 @@ def test_precond_apply_matches_linear_jacobian_solve(spec, b):
         ctx.sync()
         got = r.cpu().numpy()
     assert np.abs(got - ref).max() <= 1e-9 * np.abs(ref).max()
-    assert np.abs(P @ got - rhs).max() <= 1e-9 * np.abs(rhs).max()
+    # normwise backward error, |P r - b| against |P| |r| (P is ill-conditioned: the
+    # radiation rows have n = 0.05 on the diagonal next to x1 / dx)
+    assert np.abs(P @ got - rhs).max() <= 1e-10 * (np.abs(P) @ np.abs(got)).max()
 
 
 def gpu_solve(spec, F, eps, **kw):
