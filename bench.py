@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--block-bw", type=int, default=BLOCK_BW)
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--precond-only", action="store_true",
+                    help="build the preconditioner, apply it 10 times and solve once "
+                         "(a small, fixed launch sequence for profilers)")
     ap.add_argument("--residual-only", action="store_true",
                     help="only evaluate the FP32 and FP64 residual of the workload `steps` times "
                          "(a small, fixed launch sequence for profilers)")
@@ -339,9 +342,34 @@ def run_residual_only(args):
     print(json.dumps({"residual_only": True, "steps": args.steps}))
 
 
+def run_precond_only(args):
+    import torch
+    from paper_1403_5044_b300 import swj
+    from paper_1403_5044_b300 import workloads as W
+    spec, F, eps = W.SOLVE_181x61
+    with swj.Context.from_spec(spec, F, eps, solve_mode="mixed", block_bw=args.block_bw) as ctx:
+        t0 = time.perf_counter()
+        ctx.precond_setup()
+        ctx.sync()
+        t1 = time.perf_counter()
+        u = ctx.initial_guess_flat(ctx.vector())
+        r = ctx.vector()
+        for _ in range(10):
+            ctx.precond_apply(u, r)
+        ctx.sync()
+        t2 = time.perf_counter()
+        st = ctx.solve(u)
+        t3 = time.perf_counter()
+    print(json.dumps({"precond_only": True, "block_bw": args.block_bw, "setup_ms": (t1 - t0) * 1e3,
+                      "apply_ms": (t2 - t1) * 1e2, "solve_ms": (t3 - t2) * 1e3,
+                      "krylov_iters": st["krylov_iters"], "residual_evals": st["residual_evals"]}))
+
+
 def main():
     args = parse()
-    if args.residual_only:
+    if args.precond_only:
+        run_precond_only(args)
+    elif args.residual_only:
         run_residual_only(args)
     elif args.impl == "reference":
         run_reference(args)
