@@ -49,6 +49,7 @@ extern "C" {
 #define SWJ_ENAN        -7   /* NaN or Inf met in E or in a Krylov vector     */
 #define SWJ_ETIMEOUT    -8   /* a bounded device-side wait gave up            */
 #define SWJ_ESINGULAR   -9   /* zero pivot in the preconditioner factorisation */
+#define SWJ_ESIZE      -10   /* the mesh does not fit the no-allocation scratch */
 #define SWJ_PENDING      1   /* serving: request not finished yet             */
 
 /* ---- precision of the all-pairs boundary-integral sum ---- */
@@ -200,6 +201,35 @@ const char *swj_strerror(int status);
 
 /* Library version string. */
 const char *swj_version(void);
+
+/* ---- residual without allocation ---- */
+
+/* Bytes of the device array that swj_residual_noalloc works in. */
+#define SWJ_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* E_dev <- E(u_dev) exactly as swj_residual computes it (same kernels,
+ * precision SWJ_FP64 or SWJ_FP32), for callers that cannot allocate device
+ * memory: no context, no cudaMalloc, cudaFree or allocating library call.
+ * The paper has no counterpart; it exists for hosts such as a serving loop
+ * with a fixed latency budget (cudaMalloc/cudaFree synchronise the whole
+ * device) or a framework that budgets all device memory up front.
+ *
+ * Work is queued on `stream` (a cudaStream_t, NULL = legacy default) of the
+ * current device; the call returns before it finishes.  u_dev and E_dev are
+ * caller-owned device buffers of 2(N+1)M doubles and may not alias.
+ *
+ * Scratch: one file-scope device array of SWJ_NOALLOC_SCRATCH_BYTES (16 MiB)
+ * per GPU that loads the library, held until the process exits.  A mesh
+ * needs about 128 NM + 112 (N-1)M bytes plus 8 (N-1)M per source chunk
+ * (meshes up to about 361 x 121 fit); larger meshes return SWJ_ESIZE before
+ * any work is queued.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress, with that device current): make that
+ * first call before any stream capture.  All calls on a device share the
+ * array and leave their data in it; nothing needs clearing between calls, but
+ * calls that overlap on the GPU race on it, so serialise them.
+ * Returns SWJ_OK, SWJ_EINVAL (bad argument), SWJ_ESIZE or SWJ_ECUDA. */
+int swj_residual_noalloc(const swj_mesh *mesh, double F, double eps, const double *u_dev,
+                         double *E_dev, int precision, void *stream);
 
 /* ---- instrumentation ---- */
 

@@ -300,6 +300,7 @@ const char *swj_strerror(int s)
     case SWJ_ENAN: return "NaN or Inf encountered";
     case SWJ_ETIMEOUT: return "device wait timed out";
     case SWJ_ESINGULAR: return "singular preconditioner block";
+    case SWJ_ESIZE: return "mesh exceeds the no-allocation scratch";
     case SWJ_PENDING: return "pending";
     default: return "unknown status";
     }

@@ -15,8 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libswj.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "swj.h")
 
-OK, EINVAL, ENOMEM, ECUDA, ENOTCONV, ELINESEARCH, EGMRES, ENAN, ETIMEOUT, ESINGULAR = \
-    0, -1, -2, -3, -4, -5, -6, -7, -8, -9
+OK, EINVAL, ENOMEM, ECUDA, ENOTCONV, ELINESEARCH, EGMRES, ENAN, ETIMEOUT, ESINGULAR, ESIZE = \
+    0, -1, -2, -3, -4, -5, -6, -7, -8, -9, -10
 PENDING = 1
 FP64, FP32 = 0, 1
 SOLVE_FP64, SOLVE_MIXED = 0, 1
