@@ -14,7 +14,7 @@ namespace cg = cooperative_groups;
 namespace {
 
 constexpr int kGJThreads = 256;
-constexpr int kSweepThreads = 256;
+constexpr int kSweepThreads = 512;
 
 // Gauss-Jordan inverse with partial (row) pivoting of one n x n row-major
 // block per cluster.  `work` holds the matrix and is overwritten; the inverse
@@ -141,16 +141,199 @@ k_gj_cluster(int n, double *work_base, size_t wstride, double *out_base, size_t 
     cl.sync();
 }
 
-// One cluster solves S x = t with the block-banded LU factors of S stored in
-// `band` ([M][2h+1][n1][n1]; slot h of row i holds inv_i, slots < h hold L_ij,
-// slots > h hold W_ik = inv_i U_ik):
-//   forward   y_i = t_i - sum_{j=i-h}^{i-1} L_ij y_j      (y overwrites t)
-//   backward  x_i = inv_i y_i - sum_{k=i+1}^{i+h} W_ik x_k
+// The same Gauss-Jordan inverse with each CTA's column slice held in shared
+// memory (n x w doubles) for the whole elimination.  Every CTA loads its
+// slice before the first cluster barrier and writes the permuted result after
+// the last one, so `in` and `out` may be the same block.
+__global__ void __launch_bounds__(kGJThreads)
+k_gj_cluster_smem(int n, const double *in_base, size_t istride, double *out_base, size_t ostride,
+                  int *info)
+{
+    cg::cluster_group cl = cg::this_cluster();
+    const int ncta = (int)cl.num_blocks();
+    const int rank = (int)cl.block_rank();
+    const int mat = blockIdx.x / ncta;
+    const double *in = in_base + (size_t)mat * istride;
+    double *out = out_base + (size_t)mat * ostride;
+    const int w = (n + ncta - 1) / ncta;
+    const int c0 = rank * w, c1 = min(n, c0 + w), nc = max(0, c1 - c0);
+    extern __shared__ double sm[];
+    double *colf = sm;                          // 2 x n, double buffered
+    double *rowk = sm + 2 * n;                  // w
+    double *A = rowk + w;                       // n x w slice (row-major, stride w)
+    int *piv = (int *)(A + (size_t)n * w);      // n
+    int *ctl = piv + n;                         // [p, fail] x 2 buffers
+    int *sigma = ctl + 4;                       // n
+    __shared__ double red_v[kGJThreads / 32];
+    __shared__ int red_i[kGJThreads / 32];
+    const int tid = threadIdx.x, nth = blockDim.x;
+    for (int e = tid; e < n * nc; e += nth) {
+        int i = e / nc, jj = e % nc;
+        A[(size_t)i * w + jj] = in[(size_t)i * n + c0 + jj];
+    }
+    __syncthreads();
+    int fail = 0;
+    for (int k = 0; k < n; ++k) {
+        const int buf = k & 1;
+        const int owner = k / w;
+        if (rank == owner) {
+            const int kk = k - c0;
+            double bv = -1.0;
+            int bi = n;
+            for (int i = k + tid; i < n; i += nth) {
+                double v = fabs(A[(size_t)i * w + kk]);
+                if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+            }
+            if ((tid & 31) == 0) { red_v[tid >> 5] = bv; red_i[tid >> 5] = bi; }
+            __syncthreads();
+            if (tid < 32) {
+                double v = (tid < nth / 32) ? red_v[tid] : -1.0;
+                int ii = (tid < nth / 32) ? red_i[tid] : n;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    double ov = __shfl_xor_sync(0xffffffffu, v, o);
+                    int oi = __shfl_xor_sync(0xffffffffu, ii, o);
+                    if (ov > v || (ov == v && oi < ii)) { v = ov; ii = oi; }
+                }
+                if (tid == 0) {
+                    red_i[0] = ii;
+                    red_v[0] = (v > 0.0 && isfinite(v)) ? 0.0 : 1.0;
+                }
+            }
+            __syncthreads();
+            const int p = red_i[0];
+            const int f = red_v[0] != 0.0 ? k + 1 : 0;
+            for (int e = tid; e < n * ncta; e += nth) {
+                int q = e / n, i = e % n;
+                int src = (i == k) ? p : ((i == p) ? k : i);
+                double v = (f || p >= n) ? 0.0 : A[(size_t)src * w + kk];
+                double *rc = cl.map_shared_rank(colf + buf * n, q);
+                rc[i] = v;
+            }
+            if (tid < ncta) {
+                int *rq = cl.map_shared_rank(ctl + 2 * buf, tid);
+                rq[0] = p;
+                rq[1] = f;
+            }
+        }
+        cl.sync();
+        const int p = ctl[2 * buf];
+        fail = ctl[2 * buf + 1];
+        if (fail) break;
+        if (tid == 0) piv[k] = p;
+        if (p != k) {
+            for (int jj = tid; jj < nc; jj += nth) {
+                double t = A[(size_t)k * w + jj];
+                A[(size_t)k * w + jj] = A[(size_t)p * w + jj];
+                A[(size_t)p * w + jj] = t;
+            }
+        }
+        __syncthreads();
+        const double *cf = colf + buf * n;
+        const double rp = 1.0 / cf[k];
+        for (int jj = tid; jj < nc; jj += nth)
+            rowk[jj] = (c0 + jj == k) ? rp : A[(size_t)k * w + jj] * rp;
+        __syncthreads();
+        for (int e = tid; e < n * nc; e += nth) {
+            int i = e / nc, jj = e % nc;
+            size_t ij = (size_t)i * w + jj;
+            if (i == k) {
+                A[ij] = rowk[jj];
+            } else {
+                double base = (c0 + jj == k) ? 0.0 : A[ij];
+                A[ij] = fma(-cf[i], rowk[jj], base);
+            }
+        }
+        __syncthreads();
+    }
+    if (!fail) {
+        if (tid == 0) {
+            for (int j = 0; j < n; ++j) sigma[j] = j;
+            for (int k = n - 1; k >= 0; --k) {
+                int p = piv[k];
+                int t = sigma[k]; sigma[k] = sigma[p]; sigma[p] = t;
+            }
+            for (int j = 0; j < n; ++j) piv[sigma[j]] = j;
+        }
+        __syncthreads();
+        for (int e = tid; e < n * nc; e += nth) {
+            int i = e / nc, jj = e % nc;
+            out[(size_t)i * n + piv[c0 + jj]] = A[(size_t)i * w + jj];
+        }
+    }
+    if (rank == 0 && tid == 0) info[mat] = fail;
+    cl.sync();
+}
+
+// Dot products of one row of up to `nt` n1 x n1 blocks with staged vectors,
+// one warp per row.  KC = ceil(n1 / 32) column chunks per lane are loaded
+// with independent, fully unrolled loads (two blocks per pass) so that the
+// warp keeps 2 KC loads in flight instead of one dependent load at a time.
+template <int KC>
+__device__ __forceinline__ double row_dots(const double *__restrict__ base, size_t bstride,
+                                           const double *__restrict__ vs, int nt, int n1, int lane)
+{
+    double a0 = 0.0, a1 = 0.0;
+    int q = 0;
+    for (; q + 1 < nt; q += 2) {
+        const double *L0 = base + (size_t)q * bstride, *L1 = L0 + bstride;
+        const double *v0 = vs + (size_t)q * n1, *v1 = v0 + n1;
+        double x0[KC], x1[KC];
+#pragma unroll
+        for (int k = 0; k < KC; ++k) {
+            int c = lane + 32 * k;
+            x0[k] = (c < n1) ? __ldg(L0 + c) : 0.0;
+            x1[k] = (c < n1) ? __ldg(L1 + c) : 0.0;
+        }
+#pragma unroll
+        for (int k = 0; k < KC; ++k) {
+            int c = lane + 32 * k;
+            if (c < n1) {
+                a0 = fma(x0[k], v0[c], a0);
+                a1 = fma(x1[k], v1[c], a1);
+            }
+        }
+    }
+    if (q < nt) {
+        const double *L0 = base + (size_t)q * bstride;
+        const double *v0 = vs + (size_t)q * n1;
+        double x0[KC];
+#pragma unroll
+        for (int k = 0; k < KC; ++k) {
+            int c = lane + 32 * k;
+            x0[k] = (c < n1) ? __ldg(L0 + c) : 0.0;
+        }
+#pragma unroll
+        for (int k = 0; k < KC; ++k) {
+            int c = lane + 32 * k;
+            if (c < n1) a0 = fma(x0[k], v0[c], a0);
+        }
+    }
+    double s = a0 + a1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+// One cluster solves S x = t with the block-banded LU factors of S:
+// `band` ([M][2h+1][n1][n1]) holds inv_i in slot h of row i and the blocks
+// S_ij (j < i, as they were at step j) in the slots left of it; `W`
+// ([M][h][n1][n1]) holds W_ik = inv_i S_ik (k > i).
+//   forward   y_i = t_i - sum_{j=i-h}^{i-1} S_ij z_j  (y overwrites t),  z_i = inv_i y_i
+//   backward  x_i = z_i - sum_{k=i+1}^{i+h} W_ik x_k
 // Each CTA computes a slice of the rows of every block step (a warp per
 // row); the vectors a step reads are staged in shared memory after the
-// cluster barrier that ends the previous step.
+// cluster barrier that ends the previous phase.
+template <int KC>
 __global__ void __launch_bounds__(kSweepThreads)
-k_band_sweep(int n1, int M, int h, const double *__restrict__ band, double *y, double *x)
+k_band_sweep(int n1, int M, int h, const double *__restrict__ band, const double *__restrict__ W,
+             double *y, double *z, double *x)
 {
     cg::cluster_group cl = cg::this_cluster();
     const int ncta = (int)cl.num_blocks();
@@ -160,62 +343,92 @@ k_band_sweep(int n1, int M, int h, const double *__restrict__ band, double *y, d
     const int rows = (n1 + ncta - 1) / ncta;
     const int r0 = rank * rows, r1 = min(n1, r0 + rows);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    extern __shared__ double vs[];   // (h + 1) x n1 staged vectors
-    for (int i = 1; i < M; ++i) {
+    extern __shared__ double vs[];   // up to max(h, 1) x n1 staged vectors
+    for (int i = 0; i < M; ++i) {
         const int j0 = max(0, i - h), nt = i - j0;
-        for (int e = threadIdx.x; e < nt * n1; e += blockDim.x)
-            vs[e] = y[(size_t)(j0 + e / n1) * n1 + e % n1];
+        if (nt > 0) {
+            for (int e = threadIdx.x; e < nt * n1; e += blockDim.x)
+                vs[e] = z[(size_t)(j0 + e / n1) * n1 + e % n1];
+            __syncthreads();
+            for (int r = r0 + warp; r < r1; r += nw) {
+                const double *L = band + ((size_t)i * nb + (j0 - i + h)) * n2 + (size_t)r * n1;
+                double s = row_dots<KC>(L, n2, vs, nt, n1, lane);
+                if (lane == 0) y[(size_t)i * n1 + r] -= s;
+            }
+            cl.sync();
+        }
+        for (int e = threadIdx.x; e < n1; e += blockDim.x) vs[e] = y[(size_t)i * n1 + e];
         __syncthreads();
         for (int r = r0 + warp; r < r1; r += nw) {
-            double s = 0.0;
-            for (int q = 0; q < nt; ++q) {
-                const double *L = band + ((size_t)i * nb + (j0 + q - i + h)) * n2 + (size_t)r * n1;
-                const double *v = vs + (size_t)q * n1;
-                for (int c = lane; c < n1; c += 32) s = fma(L[c], v[c], s);
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) y[(size_t)i * n1 + r] -= s;
+            const double *Inv = band + ((size_t)i * nb + h) * n2 + (size_t)r * n1;
+            double s = row_dots<KC>(Inv, n2, vs, 1, n1, lane);
+            if (lane == 0) z[(size_t)i * n1 + r] = s;
         }
         cl.sync();
     }
     for (int i = M - 1; i >= 0; --i) {
         const int k1 = min(M - 1, i + h), nt = k1 - i;
-        for (int e = threadIdx.x; e < n1; e += blockDim.x) vs[e] = y[(size_t)i * n1 + e];
         for (int e = threadIdx.x; e < nt * n1; e += blockDim.x)
-            vs[n1 + e] = x[(size_t)(i + 1 + e / n1) * n1 + e % n1];
+            vs[e] = x[(size_t)(i + 1 + e / n1) * n1 + e % n1];
         __syncthreads();
         for (int r = r0 + warp; r < r1; r += nw) {
-            const double *Inv = band + ((size_t)i * nb + h) * n2 + (size_t)r * n1;
-            double s = 0.0;
-            for (int c = lane; c < n1; c += 32) s = fma(Inv[c], vs[c], s);
-            for (int q = 0; q < nt; ++q) {
-                const double *Wm = band + ((size_t)i * nb + (q + 1 + h)) * n2 + (size_t)r * n1;
-                const double *v = vs + (size_t)(q + 1) * n1;
-                for (int c = lane; c < n1; c += 32) s = fma(-Wm[c], v[c], s);
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) x[(size_t)i * n1 + r] = s;
+            const double *Wm = W + ((size_t)i * h) * n2 + (size_t)r * n1;
+            double s = row_dots<KC>(Wm, n2, vs, nt, n1, lane);
+            if (lane == 0) x[(size_t)i * n1 + r] = z[(size_t)i * n1 + r] - s;
         }
         cl.sync();
     }
 }
 
-int cluster_size_for(int n)
+// 16 CTAs per cluster where the device runs such clusters (a non-portable
+// size), else the portable 8.
+int cluster_ctas(const void *kernel, int threads, size_t smem)
 {
-    (void)n;
-    return 8;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+        return 8;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(16);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 16;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, kernel, &cfg) != cudaSuccess || n < 1) {
+        cudaGetLastError();
+        return 8;
+    }
+    return 16;
 }
 
 }  // namespace
 
+size_t gj_smem_bytes(int n, int cs)
+{
+    const int w = (n + cs - 1) / cs;
+    return (size_t)(2 * n + w + (size_t)n * w) * sizeof(double) + (size_t)(2 * n + 4) * sizeof(int);
+}
+
 int swj_gj_inverse_cluster(cudaStream_t st, int n, int count, double *work, size_t wstride,
                            double *out, size_t ostride, int *info)
 {
-    const int cs = cluster_size_for(n);
+    static int cs_g = 0, cs_s = 0;
+    if (!cs_s) cs_s = cluster_ctas((const void *)k_gj_cluster_smem, kGJThreads, 64 * 1024);
+    const bool use_smem = gj_smem_bytes(n, cs_s) <= 200 * 1024;
+    if (!use_smem && !cs_g) cs_g = cluster_ctas((const void *)k_gj_cluster, kGJThreads, 64 * 1024);
+    const int cs = use_smem ? cs_s : cs_g;
     const int w = (n + cs - 1) / cs;
-    size_t smem = (size_t)(2 * n + w) * sizeof(double) + (size_t)(2 * n + 4) * sizeof(int);
+    size_t smem = use_smem ? gj_smem_bytes(n, cs)
+                           : (size_t)(2 * n + w) * sizeof(double) + (size_t)(2 * n + 4) * sizeof(int);
+    const void *kern = use_smem ? (const void *)k_gj_cluster_smem : (const void *)k_gj_cluster;
+    if (smem > 48 * 1024)
+        SWJ_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cs * count);
     cfg.blockDim = dim3(kGJThreads);
@@ -229,23 +442,24 @@ int swj_gj_inverse_cluster(cudaStream_t st, int n, int count, double *work, size
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     SWJ_COUNT_LAUNCH();
-    SWJ_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_gj_cluster, n, work, wstride, out, ostride, info));
+    if (use_smem)
+        SWJ_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_gj_cluster_smem, n, (const double *)work, wstride, out,
+                                        ostride, info));
+    else
+        SWJ_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_gj_cluster, n, work, wstride, out, ostride, info));
     return SWJ_OK;
 }
 
-int swj_band_sweep_cluster(cudaStream_t st, int n1, int M, int h, const double *band, double *y,
-                           double *x)
+template <int KC>
+int launch_sweep(cudaStream_t st, int n1, int M, int h, const double *band, const double *W,
+                 double *y, double *z, double *x)
 {
-    const int cs = 8;
-    size_t smem = (size_t)(h + 1) * n1 * sizeof(double);
-    if (smem > 48 * 1024) {
-        static thread_local size_t set_to = 0;
-        if (set_to < smem) {
-            SWJ_CUDA_TRY(cudaFuncSetAttribute(k_band_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)smem));
-            set_to = smem;
-        }
-    }
+    static int cs_cached = 0;
+    if (!cs_cached) cs_cached = cluster_ctas((const void *)k_band_sweep<KC>, kSweepThreads, 64 * 1024);
+    const int cs = cs_cached;
+    size_t smem = (size_t)(h > 0 ? h : 1) * n1 * sizeof(double);
+    if (smem > 48 * 1024)
+        SWJ_CUDA_TRY(cudaFuncSetAttribute(k_band_sweep<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cs);
     cfg.blockDim = dim3(kSweepThreads);
@@ -259,6 +473,20 @@ int swj_band_sweep_cluster(cudaStream_t st, int n1, int M, int h, const double *
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     SWJ_COUNT_LAUNCH();
-    SWJ_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_band_sweep, n1, M, h, band, y, x));
+    SWJ_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_band_sweep<KC>, n1, M, h, band, W, y, z, x));
     return SWJ_OK;
+}
+
+int swj_band_sweep_cluster(cudaStream_t st, int n1, int M, int h, const double *band,
+                           const double *W, double *y, double *z, double *x)
+{
+    const int kc = (n1 + 31) / 32;
+    if (kc <= 2) return launch_sweep<2>(st, n1, M, h, band, W, y, z, x);
+    if (kc <= 4) return launch_sweep<4>(st, n1, M, h, band, W, y, z, x);
+    if (kc <= 6) return launch_sweep<6>(st, n1, M, h, band, W, y, z, x);
+    if (kc <= 8) return launch_sweep<8>(st, n1, M, h, band, W, y, z, x);
+    if (kc <= 12) return launch_sweep<12>(st, n1, M, h, band, W, y, z, x);
+    if (kc <= 16) return launch_sweep<16>(st, n1, M, h, band, W, y, z, x);
+    if (kc <= 24) return launch_sweep<24>(st, n1, M, h, band, W, y, z, x);
+    return launch_sweep<32>(st, n1, M, h, band, W, y, z, x);
 }

@@ -101,8 +101,7 @@ __global__ void k_targets(int N, int M, int H, double x1, double dx, double dy, 
                           const double *__restrict__ zeta, const double *__restrict__ g,
                           const double *__restrict__ zetay, const double *__restrict__ gy,
                           double *__restrict__ E, double *__restrict__ e2part,
-                          double *__restrict__ Ival, TgtArrays<double> t64,
-                          TgtArrays32 t32)
+                          double *__restrict__ Ival, TgtArrays64 t64, TgtArrays32 t32)
 {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     int T = (N - 1) * M;
@@ -131,13 +130,12 @@ __global__ void k_targets(int N, int M, int H, double x1, double dx, double dy, 
     e2part[t] = 2.0 * kPi * gs + src - zx * I;
     Ival[t] = I;
     E[(size_t)l * (N + 1) + 2 + k] = E1;
-    // records of the pair kernels
-    t64.tk[t] = (double)k + 0.5; t64.tl[t] = (double)l;
-    t64.zeta[t] = zs; t64.g[t] = gs; t64.zx[t] = zx;
+    // records of the pair kernels (units of L = dy, see SrcRecS)
+    const double xs = ((double)k + 0.5) * (dx / dy);
+    t64.x[t] = xs; t64.y[t] = (double)l; t64.zeta[t] = zs / dy; t64.g[t] = gs; t64.zxw[t] = zx * dy;
     t64.A[t] = A; t64.B[t] = B; t64.C[t] = C;
-    t32.x[t] = (float)(((double)k + 0.5) * (dx / dy)); t32.y[t] = (float)l;
-    t32.zeta[t] = (float)(zs / dy); t32.g[t] = (float)gs; t32.zxw[t] = (float)(zx * dy);
-    t32.A[t] = (float)A; t32.B[t] = (float)B; t32.C[t] = (float)C;
+    t32.x[t] = (float)xs; t32.y[t] = (float)l; t32.zeta[t] = (float)(zs / dy); t32.g[t] = (float)gs;
+    t32.zxw[t] = (float)(zx * dy); t32.A[t] = (float)A; t32.B[t] = (float)B; t32.C[t] = (float)C;
     if (k == 0) {
         // radiation rows at x = x1 (forward difference for the second derivative)
         double phi1 = urow_p[0], pxa = urow_p[1], pxb = urow_p[2];
@@ -152,7 +150,7 @@ __global__ void k_targets(int N, int M, int H, double x1, double dx, double dy, 
 // Thread per mesh node s = j N + i.
 __global__ void k_sources(int N, int M, int H, double dx, double dy, const double *__restrict__ u,
                           const double *__restrict__ zeta, const double *__restrict__ g,
-                          const double *__restrict__ zetay, SrcRec<double> *__restrict__ s64,
+                          const double *__restrict__ zetay, SrcRec64 *__restrict__ s64,
                           SrcRec32 *__restrict__ s32)
 {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -160,20 +158,19 @@ __global__ void k_sources(int N, int M, int H, double dx, double dy, const doubl
     int i = s % N, j = s / N;
     double ci = (i == 0 || i == N - 1) ? 0.5 : 1.0;
     double cj = (j == 0 || j == M - 1) ? 0.5 : 1.0;
-    SrcRec<double> r;
-    r.zeta = zeta[s];
+    SrcRec64 r;
+    r.x = (double)i * (dx / dy);
+    r.y = (double)j;
+    r.zeta = zeta[s] / dy;
     r.zx = u[H + (size_t)j * (N + 1) + 1 + i];
     r.zy = zetay[s];
     r.g = g[s];
-    r.w = dx * dy * ci * cj;
-    r.si = (double)i;
-    r.sj = (double)j;
-    r.pad = 0.0;
+    r.w = (dx / dy) * ci * cj;
+    r.zxw = r.zx * dy;
     s64[s] = r;
     SrcRec32 q;
-    q.x = (float)((double)i * (dx / dy)); q.y = (float)j;
-    q.zeta = (float)(r.zeta / dy); q.zx = (float)r.zx; q.zy = (float)r.zy; q.g = (float)r.g;
-    q.w = (float)((dx / dy) * ci * cj); q.zxw = (float)(r.zx * dy);
+    q.x = (float)r.x; q.y = (float)j; q.zeta = (float)r.zeta; q.zx = (float)r.zx;
+    q.zy = (float)r.zy; q.g = (float)r.g; q.w = (float)r.w; q.zxw = (float)r.zxw;
     s32[s] = q;
 }
 
@@ -212,9 +209,9 @@ __global__ void k_unpack(int N, int M, double x1, double dx, const double *__res
     if (po) po[s] = g[s] + (x1 + (double)i * dx);
 }
 
-__global__ void k_surface(int N, int M, const double *zeta, const double *g, const double *zetay,
-                          const double *gy, TgtArrays<double> t64, const double *Ival,
-                          double *out)
+__global__ void k_surface(int N, int M, double dy, const double *zeta, const double *g,
+                          const double *zetay, const double *gy, TgtArrays64 t64,
+                          const double *Ival, double *out)
 {
     int S = N * M, T = (N - 1) * M;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -226,9 +223,9 @@ __global__ void k_surface(int N, int M, const double *zeta, const double *g, con
     }
     if (i < T) {
         double *o = out + 4 * (size_t)S;
-        o[i] = t64.zeta[i];
+        o[i] = t64.zeta[i] * dy;
         o[T + i] = t64.g[i];
-        o[2 * T + i] = t64.zx[i];
+        o[2 * T + i] = t64.zxw[i] / dy;
         int k = i % (N - 1), l = i / (N - 1);
         size_t n0 = (size_t)l * N + k;
         o[3 * T + i] = 0.5 * (zetay[n0] + zetay[n0 + 1]);
@@ -302,6 +299,6 @@ void swj_launch_surface(swj_ctx *c, double *out)
 {
     int n = c->S > c->T ? c->S : c->T;
     SWJ_COUNT_LAUNCH();
-    k_surface<<<nblk(n, 256), 256, 0, c->stream>>>(c->N, c->M, c->zeta, c->g, c->zetay, c->gy,
-                                                    c->tgt64, c->Ival, out);
+    k_surface<<<nblk(n, 256), 256, 0, c->stream>>>(c->N, c->M, c->mesh.dy, c->zeta, c->g, c->zetay,
+                                                    c->gy, c->tgt64, c->Ival, out);
 }

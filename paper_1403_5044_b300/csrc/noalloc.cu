@@ -88,7 +88,7 @@ extern "C" int swj_residual_noalloc(const swj_mesh *mesh, double F, double eps, 
     if (precision != SWJ_FP64 && precision != SWJ_FP32) return SWJ_EINVAL;
     const long long S = (long long)mesh->N * mesh->M, T = (long long)(mesh->N - 1) * mesh->M;
     // fixed part of the scratch; the partial sums need at least one chunk (P = 1)
-    const long long need = 4 * S * 8 + 3LL * mesh->M * 8 + 2 * T * 8 + S * (long long)sizeof(SrcRec<double>) +
+    const long long need = 4 * S * 8 + 3LL * mesh->M * 8 + 2 * T * 8 + S * (long long)sizeof(SrcRec64) +
                            S * (long long)sizeof(SrcRec32) + 8 * T * 8 + 8 * T * 4 + T * 8 + 13 * 256;
     if (need > (long long)SWJ_NOALLOC_SCRATCH_BYTES) return SWJ_ESIZE;
 
@@ -123,12 +123,12 @@ extern "C" int swj_residual_noalloc(const swj_mesh *mesh, double F, double eps, 
     c.spl_inv = (double *)cv.take((size_t)c.M * 8);
     c.e2part = (double *)cv.take(T * 8);
     c.Ival = (double *)cv.take(T * 8);
-    c.src64 = (SrcRec<double> *)cv.take(S * sizeof(SrcRec<double>));
+    c.src64 = (SrcRec64 *)cv.take(S * sizeof(SrcRec64));
     c.src32 = (SrcRec32 *)cv.take(S * sizeof(SrcRec32));
     double *t64 = (double *)cv.take(8 * T * 8);
     float *t32 = (float *)cv.take(8 * T * 4);
     if (!t32) return SWJ_ESIZE;
-    c.tgt64 = TgtArrays<double>{t64, t64 + T, t64 + 2 * T, t64 + 3 * T, t64 + 4 * T, t64 + 5 * T,
+    c.tgt64 = TgtArrays64{t64, t64 + T, t64 + 2 * T, t64 + 3 * T, t64 + 4 * T, t64 + 5 * T,
                                 t64 + 6 * T, t64 + 7 * T};
     c.tgt32 = TgtArrays32{t32, t32 + T, t32 + 2 * T, t32 + 3 * T, t32 + 4 * T, t32 + 5 * T,
                           t32 + 6 * T, t32 + 7 * T};

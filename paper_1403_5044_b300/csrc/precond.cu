@@ -17,14 +17,20 @@
 //
 // Factorisation (Appendix C): S = D - C A^-1 B differs from D only in its
 // diagonal blocks, by the one block G = C A^-1 B.  S is factored by a block
-// LU with the block band kept (no fill outside it), partial pivoting inside
-// each diagonal block, explicit inverses of the pivot blocks, and
-// W_ik = inv_i U_ik stored for the backward sweep.  Everything is FP64.
+// LU that keeps the block band (no fill outside it), with partial pivoting
+// inside each diagonal block.  Step i inverts the updated pivot block
+// (inv_i), forms W_ik = inv_i S_ik for the blocks right of it, and updates
+// S_jk -= S_ji W_ik below it.  The blocks S_ji left of the diagonal are kept
+// as they are at their step, so the solve is
+//   forward   y_i = t_i - sum_{j<i} S_ij z_j,  z_i = inv_i y_i
+//   backward  x_i = z_i - sum_{k>i} W_ik x_k
+// (the L factor is S_ij inv_j, never formed).  Everything is FP64.
 //
 // Apply, r = P^-1 b, by the three stages of Appendix C:
 //   t2 = b2 - C A^-1 b1;  s2 = S^-1 t2;  r1 = A^-1 b1 - A^-1 B s2;  r2 = s2.
-// Because A, B, C repeat per y-row, the stages with them are one GEMM each of
-// the M x (N+1) matrix of per-row vectors with a transposed (N+1)^2 block.
+// Because A, B, C repeat per y-row, each stage with them is a product of the
+// M x (N+1) matrix of per-row vectors with one (N+1)^2 block, computed as
+// row-by-row dot products (one warp per output) so that all SMs share it.
 #include "swj_internal.h"
 #include "closed_form.cuh"
 #include <vector>
@@ -112,42 +118,11 @@ __global__ void k_tri_cols(int n1, int ncol, const double *__restrict__ A,
     }
 }
 
-__global__ void k_transpose(int n, const double *__restrict__ in, double *__restrict__ out)
-{
-    int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n * n) return;
-    int r = e / n, c = e % n;
-    out[(size_t)c * n + r] = in[e];
-}
-
 // Records of the flat state (zeta = 0, g = 0, zeta_x = 1 at the sources,
-// zeta_x* = 0, A = C = 1, B = 0 at the targets) for which the pair kernel's
-// sum is sum_s w_s K2 = sum_s w_s K3.
+// zeta_x* = 0, A = C = 1, B = 0 at the targets) in the units of SrcRecS, for
+// which the pair kernel's sum is sum_s w_s K2 = sum_s w_s K3.
 template <typename T>
-__global__ void k_flat_records(int N, int M, double dx, double dy, SrcRec<T> *src,
-                               TgtArrays<T> tg)  // FP64 records
-{
-    int e = blockIdx.x * blockDim.x + threadIdx.x;
-    int S = N * M, Tn = (N - 1) * M;
-    if (e < S) {
-        int i = e % N, j = e / N;
-        double ci = (i == 0 || i == N - 1) ? 0.5 : 1.0;
-        double cj = (j == 0 || j == M - 1) ? 0.5 : 1.0;
-        SrcRec<T> r;
-        r.zeta = T(0); r.zx = T(1); r.zy = T(0); r.g = T(0);
-        r.w = (T)(dx * dy * ci * cj); r.si = (T)i; r.sj = (T)j; r.pad = T(0);
-        src[e] = r;
-    }
-    if (e < Tn) {
-        int k = e % (N - 1), l = e / (N - 1);
-        tg.tk[e] = (T)k + (T)0.5; tg.tl[e] = (T)l;
-        tg.zeta[e] = T(0); tg.g[e] = T(0); tg.zx[e] = T(0);
-        tg.A[e] = T(1); tg.B[e] = T(0); tg.C[e] = T(1);
-    }
-}
-
-// The same flat-state records in the scaled FP32 units (see SrcRec32).
-__global__ void k_flat_records32(int N, int M, double dx, double dy, SrcRec32 *src, TgtArrays32 tg)
+__global__ void k_flat_records(int N, int M, double dx, double dy, SrcRecS<T> *src, TgtArraysS<T> tg)
 {
     int e = blockIdx.x * blockDim.x + threadIdx.x;
     int S = N * M, Tn = (N - 1) * M;
@@ -156,16 +131,16 @@ __global__ void k_flat_records32(int N, int M, double dx, double dy, SrcRec32 *s
         int i = e % N, j = e / N;
         double ci = (i == 0 || i == N - 1) ? 0.5 : 1.0;
         double cj = (j == 0 || j == M - 1) ? 0.5 : 1.0;
-        SrcRec32 r;
-        r.x = (float)(i * rho); r.y = (float)j; r.zeta = 0.f; r.zx = 1.f; r.zy = 0.f; r.g = 0.f;
-        r.w = (float)(rho * ci * cj); r.zxw = (float)dy;
+        SrcRecS<T> r;
+        r.x = (T)(i * rho); r.y = (T)j; r.zeta = T(0); r.zx = T(1); r.zy = T(0); r.g = T(0);
+        r.w = (T)(rho * ci * cj); r.zxw = (T)dy;
         src[e] = r;
     }
     if (e < Tn) {
         int k = e % (N - 1), l = e / (N - 1);
-        tg.x[e] = (float)((k + 0.5) * rho); tg.y[e] = (float)l;
-        tg.zeta[e] = 0.f; tg.g[e] = 0.f; tg.zxw[e] = 0.f;
-        tg.A[e] = 1.f; tg.B[e] = 0.f; tg.C[e] = 1.f;
+        tg.x[e] = (T)((k + 0.5) * rho); tg.y[e] = (T)l;
+        tg.zeta[e] = T(0); tg.g[e] = T(0); tg.zxw[e] = T(0);
+        tg.A[e] = T(1); tg.B[e] = T(0); tg.C[e] = T(1);
     }
 }
 
@@ -237,6 +212,38 @@ __global__ void k_blockdiag_gemv(int n1, int M, const double *__restrict__ band,
     if (lane == 0) x[(size_t)l * n1 + r] = s;
 }
 
+// Y[l][c] = alpha * dot(X[l, :], Mat[c, :]) + beta * Y[l][c]   (X: M x n, Mat: n x n)
+__global__ void k_rowdot(int M, int n, const double *__restrict__ X, const double *__restrict__ Mat,
+                         double alpha, double beta, double *__restrict__ Y)
+{
+    int warp = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    int lane = threadIdx.x & 31;
+    if (warp >= M * n) return;
+    int l = warp / n, c = warp % n;
+    const double *x = X + (size_t)l * n, *mr = Mat + (size_t)c * n;
+    double s = 0.0;
+    for (int k = lane; k < n; k += 32) s = fma(x[k], mr[k], s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+        double *y = Y + (size_t)l * n + c;
+        *y = (beta == 0.0) ? alpha * s : fma(alpha, s, beta * *y);
+    }
+}
+
+inline void rowdot(cudaStream_t st, int M, int n, const double *X, const double *Mat, double alpha,
+                   double beta, double *Y)
+{
+    SWJ_COUNT_LAUNCH();
+    k_rowdot<<<nblk((long)M * n * 32, 256), 256, 0, st>>>(M, n, X, Mat, alpha, beta, Y);
+}
+
+inline double *wblk(swj_ctx *c, int i, int k)
+{
+    size_t n2 = (size_t)c->n1 * c->n1;
+    return c->pc_W + ((size_t)i * c->pc_h + (k - i - 1)) * n2;
+}
+
 inline double *blk(swj_ctx *c, int l, int m)
 {
     size_t n2 = (size_t)c->n1 * c->n1;
@@ -248,7 +255,7 @@ void free_pc(swj_ctx *c)
 {
     double **bufs[] = {&c->pc_Ainv, &c->pc_AinvB, &c->pc_CAinv, &c->pc_G, &c->pc_A, &c->pc_B,
                        &c->pc_C, &c->pc_tmp, &c->pc_band, &c->pc_sumK3, &c->pc_t1, &c->pc_t2,
-                       &c->pc_work};
+                       &c->pc_work, &c->pc_W, &c->pc_z};
     for (double **b : bufs) {
         if (*b) cudaFree(*b);
         *b = nullptr;
@@ -281,13 +288,14 @@ int swj_pc_setup(swj_ctx *c)
         free_pc(c);
         c->pc_h = h;
         c->pc_nb = nb;
-        size_t sz[] = {n2, n2, n2, n2, n2, n2, n2, (size_t)(h > 0 ? h : 1) * n2,
+        size_t sz[] = {n2, n2, n2, n2, n2, n2, n2, n2,
                        (size_t)M * nb * n2, (size_t)c->T, (size_t)c->H, (size_t)c->H,
-                       (size_t)(h == 0 ? M : 1) * n2};
+                       (size_t)(h == 0 ? M : 1) * n2, (size_t)M * (h > 0 ? h : 1) * n2,
+                       (size_t)c->H};
         double **bufs[] = {&c->pc_Ainv, &c->pc_AinvB, &c->pc_CAinv, &c->pc_G, &c->pc_A,
                            &c->pc_B, &c->pc_C, &c->pc_tmp, &c->pc_band, &c->pc_sumK3,
-                           &c->pc_t1, &c->pc_t2, &c->pc_work};
-        for (int i = 0; i < 13; ++i)
+                           &c->pc_t1, &c->pc_t2, &c->pc_work, &c->pc_W, &c->pc_z};
+        for (int i = 0; i < 15; ++i)
             if (cudaMalloc(bufs[i], sz[i] * sizeof(double)) != cudaSuccess) {
                 free_pc(c);
                 return SWJ_ENOMEM;
@@ -305,24 +313,12 @@ int swj_pc_setup(swj_ctx *c)
     double *cpv = c->pc_t1;   // n1 scratch
     SWJ_COUNT_LAUNCH();
     k_tri_coef<<<1, 1, 0, st>>>(n1, c->pc_A, cpv);
-    double *Ainv = c->pc_tmp;            // untransposed products in scratch
     SWJ_COUNT_LAUNCH();
-    k_tri_cols<<<nblk(n1, 128), 128, 0, st>>>(n1, n1, c->pc_A, cpv, nullptr, Ainv);
-    double *AinvB = c->pc_G;             // temporarily
+    k_tri_cols<<<nblk(n1, 128), 128, 0, st>>>(n1, n1, c->pc_A, cpv, nullptr, c->pc_Ainv);
     SWJ_COUNT_LAUNCH();
-    k_tri_cols<<<nblk(n1, 128), 128, 0, st>>>(n1, n1, c->pc_A, cpv, c->pc_B, AinvB);
-    // CAinv and G = C (A^-1 B); store transposes for the row-major apply GEMMs
-    double *CAinv = c->pc_band;          // band not filled yet: use as scratch (>= 2 n2)
-    double *Gtmp = c->pc_band + n2;
-    swj_dgemm(st, n1, n1, n1, 1.0, c->pc_C, n1, Ainv, n1, 0.0, CAinv, n1);
-    swj_dgemm(st, n1, n1, n1, 1.0, c->pc_C, n1, AinvB, n1, 0.0, Gtmp, n1);
-    SWJ_COUNT_LAUNCH();
-    k_transpose<<<nblk((long)n2, 256), 256, 0, st>>>(n1, Ainv, c->pc_Ainv);
-    SWJ_COUNT_LAUNCH();
-    k_transpose<<<nblk((long)n2, 256), 256, 0, st>>>(n1, AinvB, c->pc_AinvB);
-    SWJ_COUNT_LAUNCH();
-    k_transpose<<<nblk((long)n2, 256), 256, 0, st>>>(n1, CAinv, c->pc_CAinv);
-    SWJ_CUDA_TRY(cudaMemcpyAsync(c->pc_G, Gtmp, n2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    k_tri_cols<<<nblk(n1, 128), 128, 0, st>>>(n1, n1, c->pc_A, cpv, c->pc_B, c->pc_AinvB);
+    swj_dgemm(st, n1, n1, n1, 1.0, c->pc_C, n1, c->pc_Ainv, n1, 0.0, c->pc_CAinv, n1);
+    swj_dgemm(st, n1, n1, n1, 1.0, c->pc_C, n1, c->pc_AinvB, n1, 0.0, c->pc_G, n1);
     // --- PreD diagonal correction: trapezoid sum of w K3 and I of the flat surface
     int prec = (c->opts.solve_mode == SWJ_SOLVE_FP64) ? SWJ_FP64 : SWJ_FP32;
     PairPlan pl = swj_pair_plan(c, prec);
@@ -333,7 +329,7 @@ int swj_pc_setup(swj_ctx *c)
         swj_launch_pairs64(c, pl);
     } else {
         SWJ_COUNT_LAUNCH();
-        k_flat_records32<<<nblk(ne, 256), 256, 0, st>>>(N, M, m.dx, m.dy, c->src32, c->tgt32);
+        k_flat_records<float><<<nblk(ne, 256), 256, 0, st>>>(N, M, m.dx, m.dy, c->src32, c->tgt32);
         swj_launch_pairs32(c, pl);
     }
     SWJ_COUNT_LAUNCH();
@@ -352,31 +348,24 @@ int swj_pc_setup(swj_ctx *c)
         rc = swj_gj_inverse_cluster(st, n1, M, c->pc_work, n2, c->pc_band, bstride, c->pc_info);
         if (rc) return rc;
     } else {
-        // device pointer triples for every batched GEMM of the factorisation
+        // device pointer triples of the batched GEMMs of every step:
+        //   W_ik = inv_i S_ik (k = i+1..i+h), then S_jk -= S_ji W_ik (j, k = i+1..i+h)
         std::vector<const double *> PA, PB;
         std::vector<double *> PC;
-        std::vector<int> off2(M), cnt2(M), off3(M), cnt3(M), off4(M), cnt4(M);
+        std::vector<int> offW(M), cntW(M), offU(M), cntU(M);
         for (int i = 0; i < M; ++i) {
-            int jmax = i + h < M - 1 ? i + h : M - 1;
-            off2[i] = (int)PA.size();
-            for (int j = i + 1; j <= jmax; ++j) {
-                PA.push_back(blk(c, j, i)); PB.push_back(blk(c, i, i));
-                PC.push_back(c->pc_tmp + (size_t)(j - i - 1) * n2);
+            int kmax = i + h < M - 1 ? i + h : M - 1;
+            offW[i] = (int)PA.size();
+            for (int k = i + 1; k <= kmax; ++k) {
+                PA.push_back(blk(c, i, i)); PB.push_back(blk(c, i, k)); PC.push_back(wblk(c, i, k));
             }
-            cnt2[i] = (int)PA.size() - off2[i];
-            off3[i] = (int)PA.size();
-            for (int j = i + 1; j <= jmax; ++j)
-                for (int k = i + 1; k <= jmax; ++k) {
-                    PA.push_back(blk(c, j, i)); PB.push_back(blk(c, i, k));
-                    PC.push_back(blk(c, j, k));
+            cntW[i] = (int)PA.size() - offW[i];
+            offU[i] = (int)PA.size();
+            for (int j = i + 1; j <= kmax; ++j)
+                for (int k = i + 1; k <= kmax; ++k) {
+                    PA.push_back(blk(c, j, i)); PB.push_back(wblk(c, i, k)); PC.push_back(blk(c, j, k));
                 }
-            cnt3[i] = (int)PA.size() - off3[i];
-            off4[i] = (int)PA.size();
-            for (int k = i + 1; k <= jmax; ++k) {
-                PA.push_back(blk(c, i, i)); PB.push_back(blk(c, i, k));
-                PC.push_back(c->pc_tmp + (size_t)(k - i - 1) * n2);
-            }
-            cnt4[i] = (int)PA.size() - off4[i];
+            cntU[i] = (int)PA.size() - offU[i];
         }
         int np = (int)PA.size();
         if (c->pc_ptrs_cap < np) {
@@ -402,26 +391,14 @@ int swj_pc_setup(swj_ctx *c)
                                          cudaMemcpyDeviceToDevice, st));
             rc = swj_gj_inverse_cluster(st, n1, 1, c->pc_work, n2, blk(c, i, i), n2, c->pc_info + i);
             if (rc) return rc;
-            if (cnt2[i]) {
-                swj_dgemm_batched(st, n1, n1, n1, 1.0, (const double *const *)(dA + off2[i]), n1,
-                                  (const double *const *)(dB + off2[i]), n1, 0.0, dC + off2[i], n1,
-                                  cnt2[i]);
-                for (int q = 0; q < cnt2[i]; ++q)
-                    SWJ_CUDA_TRY(cudaMemcpyAsync(const_cast<double *>(PA[off2[i] + q]), PC[off2[i] + q],
-                                                 n2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
-            }
-            if (cnt3[i])
-                swj_dgemm_batched(st, n1, n1, n1, -1.0, (const double *const *)(dA + off3[i]), n1,
-                                  (const double *const *)(dB + off3[i]), n1, 1.0, dC + off3[i], n1,
-                                  cnt3[i]);
-            if (cnt4[i]) {
-                swj_dgemm_batched(st, n1, n1, n1, 1.0, (const double *const *)(dA + off4[i]), n1,
-                                  (const double *const *)(dB + off4[i]), n1, 0.0, dC + off4[i], n1,
-                                  cnt4[i]);
-                for (int q = 0; q < cnt4[i]; ++q)
-                    SWJ_CUDA_TRY(cudaMemcpyAsync(const_cast<double *>(PB[off4[i] + q]), PC[off4[i] + q],
-                                                 n2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
-            }
+            if (cntW[i])
+                swj_dgemm_batched(st, n1, n1, n1, 1.0, (const double *const *)(dA + offW[i]), n1,
+                                  (const double *const *)(dB + offW[i]), n1, 0.0, dC + offW[i], n1,
+                                  cntW[i]);
+            if (cntU[i])
+                swj_dgemm_batched(st, n1, n1, n1, -1.0, (const double *const *)(dA + offU[i]), n1,
+                                  (const double *const *)(dB + offU[i]), n1, 1.0, dC + offU[i], n1,
+                                  cntU[i]);
         }
     }
     std::vector<int> info(M);
@@ -442,20 +419,20 @@ int swj_pc_apply(swj_ctx *c, const double *b, double *r)
     const size_t n2 = (size_t)n1 * n1;
     const double *b1 = b, *b2 = b + H;
     double *t1 = c->pc_t1, *t2 = c->pc_t2, *r2 = r + H;
-    // t2 = b2 - C A^-1 b1 ; t1 = A^-1 b1     (per-row vectors as rows of M x n1 matrices)
+    // t2 = b2 - C A^-1 b1 ; t1 = A^-1 b1   (per-row vectors are the rows of M x n1 matrices)
     SWJ_CUDA_TRY(cudaMemcpyAsync(t2, b2, (size_t)H * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    swj_dgemm(st, M, n1, n1, -1.0, b1, n1, c->pc_CAinv, n1, 1.0, t2, n1);
-    swj_dgemm(st, M, n1, n1, 1.0, b1, n1, c->pc_Ainv, n1, 0.0, t1, n1);
+    rowdot(st, M, n1, b1, c->pc_CAinv, -1.0, 1.0, t2);
+    rowdot(st, M, n1, b1, c->pc_Ainv, 1.0, 0.0, t1);
     // s2 = S^-1 t2 into r2
     if (h == 0) {
         SWJ_COUNT_LAUNCH();
         k_blockdiag_gemv<<<nblk((long)n1 * M * 32, 256), 256, 0, st>>>(n1, M, c->pc_band, n2, t2, r2);
     } else {
-        int rc = swj_band_sweep_cluster(st, n1, M, h, c->pc_band, t2, r2);
+        int rc = swj_band_sweep_cluster(st, n1, M, h, c->pc_band, c->pc_W, t2, c->pc_z, r2);
         if (rc) return rc;
     }
     // r1 = A^-1 b1 - A^-1 B s2
-    swj_dgemm(st, M, n1, n1, -1.0, r2, n1, c->pc_AinvB, n1, 1.0, t1, n1);
+    rowdot(st, M, n1, r2, c->pc_AinvB, -1.0, 1.0, t1);
     SWJ_CUDA_TRY(cudaMemcpyAsync(r, t1, (size_t)H * sizeof(double), cudaMemcpyDeviceToDevice, st));
     return SWJ_OK;
 }

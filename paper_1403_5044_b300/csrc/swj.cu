@@ -75,7 +75,7 @@ int alloc_all(swj_ctx *c)
     rc |= dalloc(c, &c->tgt32_base, 8 * T);
     if (rc) return SWJ_ENOMEM;
     double *b = c->tgt64_base;
-    c->tgt64 = TgtArrays<double>{b, b + T, b + 2 * T, b + 3 * T, b + 4 * T, b + 5 * T, b + 6 * T, b + 7 * T};
+    c->tgt64 = TgtArrays64{b, b + T, b + 2 * T, b + 3 * T, b + 4 * T, b + 5 * T, b + 6 * T, b + 7 * T};
     float *f = c->tgt32_base;
     c->tgt32 = TgtArrays32{f, f + T, f + 2 * T, f + 3 * T, f + 4 * T, f + 5 * T, f + 6 * T, f + 7 * T};
     c->plan64 = swj_pair_plan(c, SWJ_FP64);

@@ -10,48 +10,30 @@
 #define SWJ_VERSION_STRING "swj 0.1 (sm_103a)"
 
 // ---------------------------------------------------------------- records
-// Per-source record of the all-pairs sum (one per mesh node (i, j)).
-// Coordinates are kept as exact index values (si = i, sj = j, 0-based) so
-// that every coordinate difference in the kernel is exact; lengths are
-// recovered with the mesh spacings.
-template <typename T> struct SrcRec {
-    T zeta;   // zeta_ij
-    T zx;     // (zeta_x)_ij
-    T zy;     // (zeta_y)_ij
-    T g;      // g_ij = phi_ij - x_i
-    T w;      // trapezoid weight w(i, j)
-    T si;     // i (0-based)
-    T sj;     // j (0-based)
-    T pad;
-};
-
-// FP32 source record, lengths in units of L = dy (rho = dx / dy):
+// Source record of the all-pairs sum (one per mesh node (i, j)), lengths in
+// units of L = dy (rho = dx / dy):
 //   x = i rho, y = j (exact when rho is a short binary fraction, e.g. 1),
 //   zeta = zeta_ij / L, zx, zy = slopes, g = g_ij, w = rho c_i c_j (= w(i,j) / L^2),
 //   zxw = L (zeta_x)_ij.
 // With r' = r / L the pair term w [(g - g*) K1 + zx K2 - zx* S2] equals
 // w' [(g - g*) K1' + zxw K2' - zxw* S2'] where K1', K2', S2' are the kernels
-// evaluated in these units, so no coordinate needs rescaling per pair.
-struct SrcRec32 {
-    float x, y, zeta, zx, zy, g, w, zxw;
+// evaluated in these units, so no coordinate is rescaled per pair and every
+// coordinate difference is exact.
+template <typename T> struct SrcRecS {
+    T x, y, zeta, zx, zy, g, w, zxw;
 };
 
-// FP32 target arrays in the same units: x = (k + 1/2) rho, y = l, zeta* / L,
-// g*, L zeta_x*, and the dimensionless A, B, C.
-struct TgtArrays32 {
-    float *x, *y, *zeta, *g, *zxw, *A, *B, *C;
+// Target arrays in the same units, structure of arrays of length T each:
+// x = (k + 1/2) rho, y = l, zeta* / L, g*, L zeta_x*, and the dimensionless
+// A = 1 + zx*^2, B = 2 zx* zy*, C = 1 + zy*^2.
+template <typename T> struct TgtArraysS {
+    T *x, *y, *zeta, *g, *zxw, *A, *B, *C;
 };
 
-// Per-target record (one per half-mesh point (k + 1/2, l)), structure of
-// arrays, each of length T.
-template <typename T> struct TgtArrays {
-    T *tk;    // k + 1/2 (0-based k)
-    T *tl;    // l
-    T *zeta;  // zeta*
-    T *g;     // g*
-    T *zx;    // zeta_x*
-    T *A, *B, *C;   // 1 + zx*^2, 2 zx* zy*, 1 + zy*^2
-};
+typedef SrcRecS<float> SrcRec32;
+typedef TgtArraysS<float> TgtArrays32;
+typedef SrcRecS<double> SrcRec64;
+typedef TgtArraysS<double> TgtArrays64;
 
 struct PairPlan {
     int tpb;      // threads per block
@@ -83,9 +65,9 @@ struct swj_ctx {
     double *e2part;
     double *Ival;      // I per target (diagnostics)
     // records for the two precisions
-    SrcRec<double> *src64;
+    SrcRec64 *src64;
     SrcRec32 *src32;
-    TgtArrays<double> tgt64;
+    TgtArrays64 tgt64;
     TgtArrays32 tgt32;
     double *tgt64_base; float *tgt32_base;
     // partial sums [P][T]
@@ -116,6 +98,8 @@ struct swj_ctx {
     int pc_ptrs_cap;
     double *pc_t1, *pc_t2;       // apply temporaries [H]
     double *pc_work;             // Gauss-Jordan work copy: M blocks (h = 0) or one block
+    double *pc_W;                // W_ik = inv_i S_ik, [M][h][n1][n1]
+    double *pc_z;                // z_i = inv_i y_i of the forward sweep [H]
 
     size_t bytes;                // device bytes held
     cudaEvent_t ev0, ev1;
@@ -139,8 +123,6 @@ void swj_launch_surface(swj_ctx *c, double *out);
 PairPlan swj_pair_plan(const swj_ctx *c, int precision);
 void swj_launch_pairs64(swj_ctx *c, const PairPlan &pl);
 void swj_launch_pairs32(swj_ctx *c, const PairPlan &pl);
-void swj_launch_pairs_generic32(cudaStream_t st, int T, int S, const SrcRec32 *src,
-                                const TgtArrays32 &tgt, double *partial, const PairPlan &pl);
 
 // linalg.cu
 void swj_axpby(cudaStream_t st, int n, double a, const double *x, double b, double *y);      // y = a x + b y
@@ -173,8 +155,8 @@ void swj_block_inverse(cudaStream_t st, int n, int count, double *blocks, size_t
 // cluster.cu
 int swj_gj_inverse_cluster(cudaStream_t st, int n, int count, double *work, size_t wstride,
                            double *out, size_t ostride, int *info);
-int swj_band_sweep_cluster(cudaStream_t st, int n1, int M, int h, const double *band, double *y,
-                           double *x);
+int swj_band_sweep_cluster(cudaStream_t st, int n1, int M, int h, const double *band,
+                           const double *W, double *y, double *z, double *x);
 
 // precond.cu
 int swj_pc_setup(swj_ctx *c);
