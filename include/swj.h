@@ -124,10 +124,32 @@ void swj_default_opts(swj_opts *o);
 int swj_create(swj_ctx **ctx, const swj_mesh *mesh, double F, double eps,
                const swj_opts *opts, void *stream);
 
+/* ---- batches of instances on one mesh ----
+ * A batch context holds `count` >= 1 independent problems on the same mesh,
+ * instance i with its own F[i] > 0 and eps[i] >= 0 (copied).  Every vector
+ * argument of the entry points below is then `count` consecutive vectors of
+ * the single-instance length (u, E, v: count * 2(N+1)M doubles; zeta/phi of
+ * swj_unpack: count * NM).  All instances advance together in the same
+ * kernel launches (the instance index is a grid dimension), so one launch
+ * sequence serves the whole batch; instances that have converged are masked
+ * out on the device.  swj_solve takes `stats` as an array of `count`
+ * entries (or NULL), fills one per instance and returns SWJ_OK when every
+ * instance converged, else the status of the first instance that did not.
+ * swj_surface reports instance 0 only.  swj_create is swj_batch_create with
+ * count = 1. */
+int swj_batch_create(swj_ctx **ctx, const swj_mesh *mesh, int count, const double *F,
+                     const double *eps, const swj_opts *opts, void *stream);
+
+/* Number of instances of the context (0 for NULL). */
+int swj_batch_count(const swj_ctx *ctx);
+
+/* Per-instance F[count], eps[count] (see swj_set_params). */
+int swj_batch_set_params(swj_ctx *ctx, const double *F, const double *eps);
+
 /* Free the context and its device workspace (synchronises its stream). */
 void swj_destroy(swj_ctx *ctx);
 
-/* Change F and eps.  A new F invalidates the preconditioner (it depends on
+/* Change F and eps (of every instance of a batch).  A new F invalidates the preconditioner (it depends on
  * the mesh and F only, Appendix B); the next solve or precond call rebuilds
  * it. */
 int swj_set_params(swj_ctx *ctx, double F, double eps);

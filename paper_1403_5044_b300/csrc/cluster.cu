@@ -332,12 +332,20 @@ __device__ __forceinline__ double row_dots(const double *__restrict__ base, size
 // cluster barrier that ends the previous phase.
 template <int KC>
 __global__ void __launch_bounds__(kSweepThreads)
-k_band_sweep(int n1, int M, int h, const double *__restrict__ band, const double *__restrict__ W,
-             double *y, double *z, double *x)
+k_band_sweep(int n1, int M, int h, const double *__restrict__ band, size_t band_stride,
+             const double *__restrict__ W, size_t w_stride, double *y, double *z, double *x,
+             size_t vec_stride, const int *__restrict__ act)
 {
     cg::cluster_group cl = cg::this_cluster();
     const int ncta = (int)cl.num_blocks();
     const int rank = (int)cl.block_rank();
+    const int inst = blockIdx.x / ncta;
+    if (!SWJ_INST_ACTIVE(act, inst)) return;   // the whole cluster leaves together
+    band += (size_t)inst * band_stride;
+    W += (size_t)inst * w_stride;
+    y += (size_t)inst * vec_stride;
+    z += (size_t)inst * vec_stride;
+    x += (size_t)inst * vec_stride;
     const int nb = 2 * h + 1;
     const size_t n2 = (size_t)n1 * n1;
     const int rows = (n1 + ncta - 1) / ncta;
@@ -415,12 +423,22 @@ size_t gj_smem_bytes(int n, int cs)
     return (size_t)(2 * n + w + (size_t)n * w) * sizeof(double) + (size_t)(2 * n + 4) * sizeof(int);
 }
 
+static int g_cs_smem = 0;
+
+// true when the shared-memory Gauss-Jordan variant applies to n x n blocks
+// (then input and output may be the same block)
+bool swj_gj_inplace(int n)
+{
+    if (!g_cs_smem) g_cs_smem = cluster_ctas((const void *)k_gj_cluster_smem, kGJThreads, 64 * 1024);
+    return gj_smem_bytes(n, g_cs_smem) <= 200 * 1024;
+}
+
 int swj_gj_inverse_cluster(cudaStream_t st, int n, int count, double *work, size_t wstride,
                            double *out, size_t ostride, int *info)
 {
-    static int cs_g = 0, cs_s = 0;
-    if (!cs_s) cs_s = cluster_ctas((const void *)k_gj_cluster_smem, kGJThreads, 64 * 1024);
-    const bool use_smem = gj_smem_bytes(n, cs_s) <= 200 * 1024;
+    static int cs_g = 0;
+    const bool use_smem = swj_gj_inplace(n);
+    const int cs_s = g_cs_smem;
     if (!use_smem && !cs_g) cs_g = cluster_ctas((const void *)k_gj_cluster, kGJThreads, 64 * 1024);
     const int cs = use_smem ? cs_s : cs_g;
     const int w = (n + cs - 1) / cs;
@@ -450,18 +468,26 @@ int swj_gj_inverse_cluster(cudaStream_t st, int n, int count, double *work, size
     return SWJ_OK;
 }
 
+// Cluster size and shared-memory limit of the sweep kernel are settled on the
+// first call with prepare = true (from the preconditioner set-up), so that a
+// launch recorded into a CUDA graph makes no attribute call.
 template <int KC>
-int launch_sweep(cudaStream_t st, int n1, int M, int h, const double *band, const double *W,
-                 double *y, double *z, double *x)
+int launch_sweep(cudaStream_t st, int nb, int n1, int M, int h, const double *band, size_t bs,
+                 const double *W, size_t ws, double *y, double *z, double *x, size_t vs, const int *act,
+                 bool prepare)
 {
     static int cs_cached = 0;
+    static size_t smem_set = 48 * 1024;
     if (!cs_cached) cs_cached = cluster_ctas((const void *)k_band_sweep<KC>, kSweepThreads, 64 * 1024);
     const int cs = cs_cached;
     size_t smem = (size_t)(h > 0 ? h : 1) * n1 * sizeof(double);
-    if (smem > 48 * 1024)
+    if (smem > smem_set) {
         SWJ_CUDA_TRY(cudaFuncSetAttribute(k_band_sweep<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        smem_set = smem;
+    }
+    if (prepare) return SWJ_OK;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(cs);
+    cfg.gridDim = dim3(cs * nb);
     cfg.blockDim = dim3(kSweepThreads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
@@ -473,20 +499,23 @@ int launch_sweep(cudaStream_t st, int n1, int M, int h, const double *band, cons
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     SWJ_COUNT_LAUNCH();
-    SWJ_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_band_sweep<KC>, n1, M, h, band, W, y, z, x));
+    SWJ_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_band_sweep<KC>, n1, M, h, band, bs, W, ws, y, z, x, vs, act));
     return SWJ_OK;
 }
 
-int swj_band_sweep_cluster(cudaStream_t st, int n1, int M, int h, const double *band,
-                           const double *W, double *y, double *z, double *x)
+int swj_band_sweep_cluster(cudaStream_t st, int nb, int n1, int M, int h, const double *band,
+                           size_t bs, const double *W, size_t ws, double *y, double *z, double *x,
+                           size_t vs, const int *act, bool prepare)
 {
     const int kc = (n1 + 31) / 32;
-    if (kc <= 2) return launch_sweep<2>(st, n1, M, h, band, W, y, z, x);
-    if (kc <= 4) return launch_sweep<4>(st, n1, M, h, band, W, y, z, x);
-    if (kc <= 6) return launch_sweep<6>(st, n1, M, h, band, W, y, z, x);
-    if (kc <= 8) return launch_sweep<8>(st, n1, M, h, band, W, y, z, x);
-    if (kc <= 12) return launch_sweep<12>(st, n1, M, h, band, W, y, z, x);
-    if (kc <= 16) return launch_sweep<16>(st, n1, M, h, band, W, y, z, x);
-    if (kc <= 24) return launch_sweep<24>(st, n1, M, h, band, W, y, z, x);
-    return launch_sweep<32>(st, n1, M, h, band, W, y, z, x);
+#define SWJ_SWEEP(K) return launch_sweep<K>(st, nb, n1, M, h, band, bs, W, ws, y, z, x, vs, act, prepare)
+    if (kc <= 2) SWJ_SWEEP(2);
+    if (kc <= 4) SWJ_SWEEP(4);
+    if (kc <= 6) SWJ_SWEEP(6);
+    if (kc <= 8) SWJ_SWEEP(8);
+    if (kc <= 12) SWJ_SWEEP(12);
+    if (kc <= 16) SWJ_SWEEP(16);
+    if (kc <= 24) SWJ_SWEEP(24);
+    SWJ_SWEEP(32);
+#undef SWJ_SWEEP
 }

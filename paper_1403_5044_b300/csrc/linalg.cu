@@ -11,38 +11,44 @@ constexpr int kRedThreads = 256;
 
 inline int nblk(long n, int b) { return (int)((n + b - 1) / b); }
 
-__global__ void k_axpby(int n, double a, const double *__restrict__ x, double b,
-                        double *__restrict__ y)
+__global__ void k_bcopy(int n, const double *__restrict__ x, double *__restrict__ y, size_t ld,
+                        const int *__restrict__ act)
 {
+    const int inst = blockIdx.y;
+    if (!SWJ_INST_ACTIVE(act, inst)) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) y[i] = a * x[i] + b * y[i];
+    if (i < n) y[inst * ld + i] = x[inst * ld + i];
 }
 
-__global__ void k_axpy_dev(int n, const double *__restrict__ a, double s,
-                           const double *__restrict__ x, double *__restrict__ y)
+__global__ void k_bfill(int n, double v, double *__restrict__ x, size_t ld, const int *__restrict__ act)
 {
+    const int inst = blockIdx.y;
+    if (!SWJ_INST_ACTIVE(act, inst)) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) y[i] += (s * a[0]) * x[i];
+    if (i < n) x[inst * ld + i] = v;
 }
 
-__global__ void k_scale_dev(int n, const double *__restrict__ num, double *__restrict__ x,
-                            int invert)
+__global__ void k_baxpy(int n, const double *__restrict__ a_dev, size_t sstride, double a_scale,
+                        const double *__restrict__ x, double *__restrict__ y, size_t ld,
+                        const int *__restrict__ act)
 {
+    const int inst = blockIdx.y;
+    if (!SWJ_INST_ACTIVE(act, inst)) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    double f = invert ? 1.0 / num[0] : num[0];
-    if (i < n) x[i] *= f;
+    double a = a_dev ? a_scale * a_dev[inst * sstride] : a_scale;
+    if (i < n) y[inst * ld + i] = fma(a, x[inst * ld + i], y[inst * ld + i]);
 }
 
-__global__ void k_copy(int n, const double *__restrict__ x, double *__restrict__ y)
+__global__ void k_bscale(int n, const double *__restrict__ s_dev, size_t sstride, double s_scale,
+                         int invert, const double *__restrict__ x, double *__restrict__ y, size_t ld,
+                         const int *__restrict__ act)
 {
+    const int inst = blockIdx.y;
+    if (!SWJ_INST_ACTIVE(act, inst)) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) y[i] = x[i];
-}
-
-__global__ void k_fill(int n, double v, double *__restrict__ x)
-{
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) x[i] = v;
+    double f = s_dev ? s_scale * s_dev[inst * sstride] : s_scale;
+    if (invert) f = 1.0 / f;
+    if (i < n) y[inst * ld + i] = f * x[inst * ld + i];
 }
 
 __device__ __forceinline__ double warp_sum(double v)
@@ -90,9 +96,15 @@ __device__ double block_max(double v)
     return sh[0];
 }
 
-// stage 1: red[b] = sum of squares, red[G + b] = max |x| or +Inf if non-finite
-__global__ void k_norms1(int n, const double *__restrict__ x, double *__restrict__ red)
+// stage 1 of the norms: per instance, red[b] = sum of squares of block b's
+// range, red[G + b] = max |x| there (+Inf if any entry is not finite)
+__global__ void k_bnorms1(int n, const double *__restrict__ x, size_t ld, double *__restrict__ red,
+                          const int *__restrict__ act)
 {
+    const int inst = blockIdx.y;
+    if (!SWJ_INST_ACTIVE(act, inst)) return;
+    x += inst * ld;
+    red += (size_t)inst * SWJ_RED;
     double s = 0.0, m = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         double v = x[i];
@@ -105,55 +117,79 @@ __global__ void k_norms1(int n, const double *__restrict__ x, double *__restrict
     if (threadIdx.x == 0) { red[blockIdx.x] = s; red[gridDim.x + blockIdx.x] = m; }
 }
 
-__global__ void k_norms2(int G, const double *__restrict__ red, double *__restrict__ out)
+__global__ void k_bnorms2(int G, const double *__restrict__ red, double *__restrict__ out,
+                          size_t sstride, const int *__restrict__ act)
 {
+    const int inst = blockIdx.x;
+    if (!SWJ_INST_ACTIVE(act, inst)) return;
+    red += (size_t)inst * SWJ_RED;
     double s = 0.0, m = 0.0;
     for (int i = threadIdx.x; i < G; i += blockDim.x) { s += red[i]; m = fmax(m, red[G + i]); }
     s = block_sum(s);
     m = block_max(m);
-    if (threadIdx.x == 0) { out[0] = isinf(m) ? NAN : s; out[1] = isinf(m) ? NAN : m; }
+    if (threadIdx.x == 0) {
+        out[inst * sstride] = isinf(m) ? NAN : s;
+        out[inst * sstride + 1] = isinf(m) ? NAN : m;
+    }
 }
 
-// stage 1 of multi-dot: red[r * G + b] = partial of row r over block b's range
-__global__ void k_mdot1(int n, const double *__restrict__ V, size_t ld,
-                        const double *__restrict__ w, double *__restrict__ red)
+// stage 1 of the multi-dot: red[r * G + b] = partial of row r over block b's range
+__global__ void k_bmdot1(int n, const double *__restrict__ V, size_t ld, size_t vstride,
+                         const double *__restrict__ w, size_t wstride, double *__restrict__ red,
+                         const int *__restrict__ act)
 {
-    int r = blockIdx.y;
-    const double *v = V + (size_t)r * ld;
+    const int inst = blockIdx.z;
+    if (!SWJ_INST_ACTIVE(act, inst)) return;
+    const int r = blockIdx.y;
+    const double *v = V + inst * vstride + (size_t)r * ld;
+    w += inst * wstride;
     double s = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         s = fma(v[i], w[i], s);
     s = block_sum(s);
-    if (threadIdx.x == 0) red[(size_t)r * gridDim.x + blockIdx.x] = s;
+    if (threadIdx.x == 0) red[(size_t)inst * SWJ_RED + (size_t)r * gridDim.x + blockIdx.x] = s;
 }
 
-__global__ void k_mdot2(int G, const double *__restrict__ red, double *__restrict__ out)
+__global__ void k_bmdot2(int G, const double *__restrict__ red, double *__restrict__ out,
+                         size_t sstride, const int *__restrict__ act)
 {
-    int r = blockIdx.x;
+    const int inst = blockIdx.y;
+    if (!SWJ_INST_ACTIVE(act, inst)) return;
+    const int r = blockIdx.x;
     double s = 0.0;
-    for (int i = threadIdx.x; i < G; i += blockDim.x) s += red[(size_t)r * G + i];
+    for (int i = threadIdx.x; i < G; i += blockDim.x) s += red[(size_t)inst * SWJ_RED + (size_t)r * G + i];
     s = block_sum(s);
-    if (threadIdx.x == 0) out[r] = s;
+    if (threadIdx.x == 0) out[inst * sstride + r] = s;
 }
 
-__global__ void k_mgemv_sub(int n, int rows, const double *__restrict__ V, size_t ld,
-                            const double *__restrict__ coef, double *__restrict__ w)
+__global__ void k_bmgemv_sub(int n, int rows, const double *__restrict__ V, size_t ld, size_t vstride,
+                             const double *__restrict__ coef, size_t sstride, double *__restrict__ w,
+                             size_t wstride, const int *__restrict__ act)
 {
+    const int inst = blockIdx.y;
+    if (!SWJ_INST_ACTIVE(act, inst)) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    double s = w[i];
-    for (int r = 0; r < rows; ++r) s = fma(-coef[r], V[(size_t)r * ld + i], s);
-    w[i] = s;
+    const double *v = V + inst * vstride;
+    const double *cf = coef + inst * sstride;
+    double s = w[inst * wstride + i];
+    for (int r = 0; r < rows; ++r) s = fma(-cf[r], v[(size_t)r * ld + i], s);
+    w[inst * wstride + i] = s;
 }
 
-__global__ void k_combine(int n, int rows, const double *__restrict__ Z, size_t ld,
-                          const double *__restrict__ coef, double *__restrict__ x, int acc)
+__global__ void k_bcombine(int n, int rows, const double *__restrict__ Z, size_t ld, size_t zstride,
+                           const double *__restrict__ coef, size_t sstride, double *__restrict__ x,
+                           size_t xstride, int acc, const int *__restrict__ act)
 {
+    const int inst = blockIdx.y;
+    if (!SWJ_INST_ACTIVE(act, inst)) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    double s = acc ? x[i] : 0.0;
-    for (int r = 0; r < rows; ++r) s = fma(coef[r], Z[(size_t)r * ld + i], s);
-    x[i] = s;
+    const double *z = Z + inst * zstride;
+    const double *cf = coef + inst * sstride;
+    double s = acc ? x[inst * xstride + i] : 0.0;
+    for (int r = 0; r < rows; ++r) s = fma(cf[r], z[(size_t)r * ld + i], s);
+    x[inst * xstride + i] = s;
 }
 
 // C = alpha A B + beta C (row-major), 64x64 output tile per block, 256 threads
@@ -210,161 +246,67 @@ k_dgemm(int m, int n, int k, double alpha, const double *const *Ap, const double
     }
 }
 
-// In-place inverse of one n x n row-major block per CTA by Gauss-Jordan
-// elimination with partial (row) pivoting; the row interchanges are undone
-// at the end as column interchanges in reverse order.  info[b] = 0 on
-// success, 1 + k when column k has no non-zero pivot.
-__global__ void __launch_bounds__(1024)
-k_gj_inverse(int n, double *blocks, size_t stride, int *info)
-{
-    extern __shared__ double shm[];
-    double *rowk = shm;             // n
-    double *colf = shm + n;         // n
-    int *piv = (int *)(shm + 2 * n);  // n
-    __shared__ double bestv[32];
-    __shared__ int besti[32];
-    __shared__ int pivot_row;
-    __shared__ int fail;
-    double *a = blocks + (size_t)blockIdx.x * stride;
-    const int tid = threadIdx.x, nth = blockDim.x;
-    if (tid == 0) fail = 0;
-    for (int k = 0; k < n; ++k) {
-        // pivot search in column k, rows k..n-1 (ties: smallest row index)
-        double bv = -1.0; int bi = n;
-        for (int i = k + tid; i < n; i += nth) {
-            double v = fabs(a[(size_t)i * n + k]);
-            if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-            int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
-        }
-        __syncthreads();
-        if ((tid & 31) == 0) { bestv[tid >> 5] = bv; besti[tid >> 5] = bi; }
-        __syncthreads();
-        if (tid < 32) {
-            int nw = nth >> 5;
-            double v = (tid < nw) ? bestv[tid] : -1.0;
-            int ii = (tid < nw) ? besti[tid] : n;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                double ov = __shfl_xor_sync(0xffffffffu, v, o);
-                int oi = __shfl_xor_sync(0xffffffffu, ii, o);
-                if (ov > v || (ov == v && oi < ii)) { v = ov; ii = oi; }
-            }
-            if (tid == 0) {
-                pivot_row = ii;
-                if (!(v > 0.0) || !isfinite(v)) fail = k + 1;
-            }
-        }
-        __syncthreads();
-        if (fail) break;
-        int p = pivot_row;
-        if (tid == 0) piv[k] = p;
-        if (p != k) {
-            for (int j = tid; j < n; j += nth) {
-                double t = a[(size_t)k * n + j];
-                a[(size_t)k * n + j] = a[(size_t)p * n + j];
-                a[(size_t)p * n + j] = t;
-            }
-        }
-        __syncthreads();
-        double pv = a[(size_t)k * n + k];
-        double rp = 1.0 / pv;
-        for (int j = tid; j < n; j += nth) {
-            double v = (j == k) ? rp : a[(size_t)k * n + j] * rp;
-            rowk[j] = v;
-        }
-        for (int i = tid; i < n; i += nth) colf[i] = (i == k) ? 0.0 : a[(size_t)i * n + k];
-        __syncthreads();
-        for (int j = tid; j < n; j += nth) a[(size_t)k * n + j] = rowk[j];
-        for (size_t e = tid; e < (size_t)n * n; e += nth) {
-            int i = (int)(e / n), j = (int)(e % n);
-            if (i == k) continue;
-            double base = (j == k) ? 0.0 : a[e];
-            a[e] = fma(-colf[i], rowk[j], base);
-        }
-        __syncthreads();
-    }
-    if (fail) {
-        if (tid == 0) info[blockIdx.x] = fail;
-        return;
-    }
-    for (int k = n - 1; k >= 0; --k) {
-        int p = piv[k];
-        if (p != k) {
-            for (int i = tid; i < n; i += nth) {
-                double t = a[(size_t)i * n + k];
-                a[(size_t)i * n + k] = a[(size_t)i * n + p];
-                a[(size_t)i * n + p] = t;
-            }
-        }
-        __syncthreads();
-    }
-    if (tid == 0) info[blockIdx.x] = 0;
-}
-
 }  // namespace
 
-void swj_axpby(cudaStream_t st, int n, double a, const double *x, double b, double *y)
+void swj_bcopy(cudaStream_t st, int nb, int n, const double *x, double *y, size_t ld, const int *act)
 {
     SWJ_COUNT_LAUNCH();
-    k_axpby<<<nblk(n, 256), 256, 0, st>>>(n, a, x, b, y);
+    k_bcopy<<<dim3(nblk(n, 256), nb), 256, 0, st>>>(n, x, y, ld, act);
 }
-void swj_axpy_dev(cudaStream_t st, int n, const double *a, double s, const double *x, double *y)
+void swj_bfill(cudaStream_t st, int nb, int n, double v, double *x, size_t ld, const int *act)
 {
     SWJ_COUNT_LAUNCH();
-    k_axpy_dev<<<nblk(n, 256), 256, 0, st>>>(n, a, s, x, y);
+    k_bfill<<<dim3(nblk(n, 256), nb), 256, 0, st>>>(n, v, x, ld, act);
 }
-void swj_scale_dev(cudaStream_t st, int n, const double *num, double *x, int invert)
+void swj_baxpy(cudaStream_t st, int nb, int n, const double *a_dev, size_t sstride, double a_scale,
+               const double *x, double *y, size_t ld, const int *act)
 {
     SWJ_COUNT_LAUNCH();
-    k_scale_dev<<<nblk(n, 256), 256, 0, st>>>(n, num, x, invert);
+    k_baxpy<<<dim3(nblk(n, 256), nb), 256, 0, st>>>(n, a_dev, sstride, a_scale, x, y, ld, act);
 }
-void swj_copy(cudaStream_t st, int n, const double *x, double *y)
+void swj_bscale(cudaStream_t st, int nb, int n, const double *s_dev, size_t sstride, double s_scale,
+                int invert, const double *x, double *y, size_t ld, const int *act)
 {
     SWJ_COUNT_LAUNCH();
-    k_copy<<<nblk(n, 256), 256, 0, st>>>(n, x, y);
+    k_bscale<<<dim3(nblk(n, 256), nb), 256, 0, st>>>(n, s_dev, sstride, s_scale, invert, x, y, ld, act);
 }
-void swj_fill(cudaStream_t st, int n, double v, double *x)
-{
-    SWJ_COUNT_LAUNCH();
-    k_fill<<<nblk(n, 256), 256, 0, st>>>(n, v, x);
-}
-void swj_norms(cudaStream_t st, int n, const double *x, double *red, double *out)
+void swj_bnorms(cudaStream_t st, int nb, int n, const double *x, size_t ld, double *red,
+                double *out, size_t sstride, const int *act)
 {
     int G = nblk(n, kRedThreads);
     if (G > kRedBlocks) G = kRedBlocks;
     if (G < 1) G = 1;
     SWJ_COUNT_LAUNCH();
-    k_norms1<<<G, kRedThreads, 0, st>>>(n, x, red);
+    k_bnorms1<<<dim3(G, nb), kRedThreads, 0, st>>>(n, x, ld, red, act);
     SWJ_COUNT_LAUNCH();
-    k_norms2<<<1, kRedThreads, 0, st>>>(G, red, out);
+    k_bnorms2<<<nb, kRedThreads, 0, st>>>(G, red, out, sstride, act);
 }
-void swj_mdot(cudaStream_t st, int n, int rows, const double *V, size_t ld, const double *w,
-              double *red, double *out)
+void swj_bmdot(cudaStream_t st, int nb, int n, int rows, const double *V, size_t ld, size_t vstride,
+               const double *w, size_t wstride, double *red, double *out, size_t sstride, const int *act)
 {
     int G = nblk(n, kRedThreads);
     if (G > 64) G = 64;
     if (G < 1) G = 1;
     SWJ_COUNT_LAUNCH();
-    k_mdot1<<<dim3(G, rows), kRedThreads, 0, st>>>(n, V, ld, w, red);
+    k_bmdot1<<<dim3(G, rows, nb), kRedThreads, 0, st>>>(n, V, ld, vstride, w, wstride, red, act);
     SWJ_COUNT_LAUNCH();
-    k_mdot2<<<rows, 64, 0, st>>>(G, red, out);
+    k_bmdot2<<<dim3(rows, nb), 64, 0, st>>>(G, red, out, sstride, act);
 }
-void swj_mgemv_sub(cudaStream_t st, int n, int rows, const double *V, size_t ld,
-                   const double *coef, double *w)
+void swj_bmgemv_sub(cudaStream_t st, int nb, int n, int rows, const double *V, size_t ld,
+                    size_t vstride, const double *coef, size_t sstride, double *w, size_t wstride,
+                    const int *act)
 {
     SWJ_COUNT_LAUNCH();
-    k_mgemv_sub<<<nblk(n, 256), 256, 0, st>>>(n, rows, V, ld, coef, w);
+    k_bmgemv_sub<<<dim3(nblk(n, 256), nb), 256, 0, st>>>(n, rows, V, ld, vstride, coef, sstride, w,
+                                                        wstride, act);
 }
-void swj_combine(cudaStream_t st, int n, int rows, const double *Z, size_t ld,
-                 const double *coef, double *x, int acc)
+void swj_bcombine(cudaStream_t st, int nb, int n, int rows, const double *Z, size_t ld,
+                  size_t zstride, const double *coef, size_t sstride, double *x, size_t xstride,
+                  int accumulate, const int *act)
 {
     SWJ_COUNT_LAUNCH();
-    k_combine<<<nblk(n, 256), 256, 0, st>>>(n, rows, Z, ld, coef, x, acc);
+    k_bcombine<<<dim3(nblk(n, 256), nb), 256, 0, st>>>(n, rows, Z, ld, zstride, coef, sstride, x,
+                                                      xstride, accumulate, act);
 }
 void swj_dgemm_batched(cudaStream_t st, int m, int n, int k, double alpha,
                        const double *const *A, int lda, const double *const *B, int ldb,
@@ -384,11 +326,4 @@ void swj_dgemm(cudaStream_t st, int m, int n, int k, double alpha, const double 
     SWJ_COUNT_LAUNCH();
     k_dgemm<<<grid, 256, 0, st>>>(m, n, k, alpha, nullptr, A, lda, nullptr, B, ldb, beta,
                                   nullptr, C, ldc);
-}
-void swj_block_inverse(cudaStream_t st, int n, int count, double *blocks, size_t stride,
-                       int *info)
-{
-    size_t sh = (size_t)n * (2 * sizeof(double) + sizeof(int));
-    SWJ_COUNT_LAUNCH();
-    k_gj_inverse<<<count, 1024, sh, st>>>(n, blocks, stride, info);
 }

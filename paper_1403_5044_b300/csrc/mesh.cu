@@ -23,8 +23,13 @@ constexpr double kPi = 3.14159265358979323846;
 // the constant 1 exactly); rows M..2M-1 integrate zeta_x from zeta_1.
 __global__ void k_integrate(int N, int M, int H, double x1, double dx,
                             const double *__restrict__ u, double *__restrict__ zeta,
-                            double *__restrict__ g)
+                            double *__restrict__ g, const int *__restrict__ act)
 {
+    const int inst = blockIdx.y;
+    if (!SWJ_INST_ACTIVE(act, inst)) return;
+    u += (size_t)inst * 2 * H;
+    zeta += (size_t)inst * N * M;
+    g += (size_t)inst * N * M;
     int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     int lane = threadIdx.x & 31;
     if (warp >= 2 * M) return;
@@ -66,8 +71,13 @@ __global__ void k_integrate(int N, int M, int H, double x1, double dx,
 __global__ void k_spline(int N, int M, double hy, const double *__restrict__ cp,
                          const double *__restrict__ a, const double *__restrict__ inv,
                          const double *__restrict__ zeta, const double *__restrict__ g,
-                         double *__restrict__ zetay, double *__restrict__ gy)
+                         double *__restrict__ zetay, double *__restrict__ gy,
+                         const int *__restrict__ act)
 {
+    const int inst = blockIdx.y;
+    if (!SWJ_INST_ACTIVE(act, inst)) return;
+    const size_t off = (size_t)inst * N * M;
+    zeta += off; g += off; zetay += off; gy += off;
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 2 * N) return;
     int k = t % N;
@@ -96,16 +106,27 @@ __global__ void k_spline(int N, int M, double hy, const double *__restrict__ cp,
 }
 
 // Thread per half-mesh target t = l (N-1) + k.
-__global__ void k_targets(int N, int M, int H, double x1, double dx, double dy, double F,
-                          double eps, double nrad, const double *__restrict__ u,
+__global__ void k_targets(int N, int M, int H, double x1, double dx, double dy,
+                          const double *__restrict__ Fv, const double *__restrict__ epsv,
+                          double nrad, const double *__restrict__ u,
                           const double *__restrict__ zeta, const double *__restrict__ g,
                           const double *__restrict__ zetay, const double *__restrict__ gy,
                           double *__restrict__ E, double *__restrict__ e2part,
-                          double *__restrict__ Ival, TgtArrays64 t64, TgtArrays32 t32)
+                          double *__restrict__ Ival, TgtArrays64 t64, TgtArrays32 t32,
+                          const int *__restrict__ act)
 {
+    const int inst = blockIdx.y;
+    if (!SWJ_INST_ACTIVE(act, inst)) return;
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     int T = (N - 1) * M;
     if (t >= T) return;
+    const double F = Fv[inst], eps = epsv[inst];
+    {
+        const size_t on = (size_t)inst * N * M, ov = (size_t)inst * 2 * H, ot = (size_t)inst * T;
+        u += ov; E += ov; zeta += on; g += on; zetay += on; gy += on; e2part += ot; Ival += ot;
+        t64.x += ot; t64.y += ot; t64.zeta += ot; t64.g += ot; t64.zxw += ot; t64.A += ot; t64.B += ot; t64.C += ot;
+        t32.x += ot; t32.y += ot; t32.zeta += ot; t32.g += ot; t32.zxw += ot; t32.A += ot; t32.B += ot; t32.C += ot;
+    }
     int k = t % (N - 1), l = t / (N - 1);
     size_t n0 = (size_t)l * N + k;
     const double *urow_p = u + (size_t)l * (N + 1);
@@ -151,10 +172,16 @@ __global__ void k_targets(int N, int M, int H, double x1, double dx, double dy, 
 __global__ void k_sources(int N, int M, int H, double dx, double dy, const double *__restrict__ u,
                           const double *__restrict__ zeta, const double *__restrict__ g,
                           const double *__restrict__ zetay, SrcRec64 *__restrict__ s64,
-                          SrcRec32 *__restrict__ s32)
+                          SrcRec32 *__restrict__ s32, const int *__restrict__ act)
 {
+    const int inst = blockIdx.y;
+    if (!SWJ_INST_ACTIVE(act, inst)) return;
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= N * M) return;
+    {
+        const size_t on = (size_t)inst * N * M;
+        u += (size_t)inst * 2 * H; zeta += on; g += on; zetay += on; s64 += on; s32 += on;
+    }
     int i = s % N, j = s / N;
     double ci = (i == 0 || i == N - 1) ? 0.5 : 1.0;
     double cj = (j == 0 || j == M - 1) ? 0.5 : 1.0;
@@ -176,11 +203,17 @@ __global__ void k_sources(int N, int M, int H, double dx, double dy, const doubl
 
 // Thread per target: E2 = (2 pi g* + src - zx* I) - sum over source chunks.
 __global__ void k_assemble(int N, int M, int H, int P, const double *__restrict__ partial,
-                           const double *__restrict__ e2part, double *__restrict__ E)
+                           const double *__restrict__ e2part, double *__restrict__ E,
+                           const int *__restrict__ act)
 {
+    const int inst = blockIdx.y;
+    if (!SWJ_INST_ACTIVE(act, inst)) return;
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     int T = (N - 1) * M;
     if (t >= T) return;
+    partial += (size_t)inst * P * T;
+    e2part += (size_t)inst * T;
+    E += (size_t)inst * 2 * H;
     double s = 0.0;
     for (int p = 0; p < P; ++p) s += partial[(size_t)p * T + t];
     int k = t % (N - 1), l = t / (N - 1);
@@ -191,6 +224,7 @@ __global__ void k_flat(int N, int M, int H, double x1, double *__restrict__ u)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= 2 * H) return;
+    u += (size_t)blockIdx.y * 2 * H;
     int r = i % (N + 1);
     double v;
     if (i < H) v = (r == 0) ? x1 : 1.0;
@@ -204,6 +238,10 @@ __global__ void k_unpack(int N, int M, double x1, double dx, const double *__res
 {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= N * M) return;
+    const size_t on = (size_t)blockIdx.y * N * M;
+    zeta += on; g += on;
+    if (zo) zo += on;
+    if (po) po += on;
     int i = s % N;
     if (zo) zo[s] = zeta[s];
     if (po) po[s] = g[s] + (x1 + (double)i * dx);
@@ -252,47 +290,50 @@ void swj_spline_coeffs(int M, double *cp, double *a, double *inv)
     }
 }
 
-void swj_launch_mesh_step(swj_ctx *c, const double *u, double *E)
+void swj_launch_mesh_step(swj_ctx *c, const double *u, double *E, const int *act)
 {
     const swj_mesh &m = c->mesh;
     cudaStream_t st = c->stream;
+    const int nb = c->nb;
     SWJ_COUNT_LAUNCH();
-    k_integrate<<<nblk(2L * c->M * 32, 256), 256, 0, st>>>(c->N, c->M, c->H, m.x1, m.dx, u,
-                                                           c->zeta, c->g);
+    k_integrate<<<dim3(nblk(2L * c->M * 32, 256), nb), 256, 0, st>>>(c->N, c->M, c->H, m.x1, m.dx, u,
+                                                                     c->zeta, c->g, act);
     SWJ_COUNT_LAUNCH();
-    k_spline<<<nblk(2L * c->N, 128), 128, 0, st>>>(c->N, c->M, m.dy, c->spl_cp, c->spl_a,
-                                                    c->spl_inv, c->zeta, c->g, c->zetay, c->gy);
+    k_spline<<<dim3(nblk(2L * c->N, 128), nb), 128, 0, st>>>(c->N, c->M, m.dy, c->spl_cp, c->spl_a,
+                                                              c->spl_inv, c->zeta, c->g, c->zetay,
+                                                              c->gy, act);
     SWJ_COUNT_LAUNCH();
-    k_targets<<<nblk(c->T, 128), 128, 0, st>>>(c->N, c->M, c->H, m.x1, m.dx, m.dy, c->F, c->eps,
-                                                m.n_rad, u, c->zeta, c->g, c->zetay, c->gy, E,
-                                                c->e2part, c->Ival, c->tgt64, c->tgt32);
+    k_targets<<<dim3(nblk(c->T, 128), nb), 128, 0, st>>>(c->N, c->M, c->H, m.x1, m.dx, m.dy, c->Fd,
+                                                          c->epsd, m.n_rad, u, c->zeta, c->g,
+                                                          c->zetay, c->gy, E, c->e2part, c->Ival,
+                                                          c->tgt64, c->tgt32, act);
     SWJ_COUNT_LAUNCH();
-    k_sources<<<nblk(c->S, 256), 256, 0, st>>>(c->N, c->M, c->H, m.dx, m.dy, u, c->zeta, c->g,
-                                               c->zetay, c->src64, c->src32);
+    k_sources<<<dim3(nblk(c->S, 256), nb), 256, 0, st>>>(c->N, c->M, c->H, m.dx, m.dy, u, c->zeta,
+                                                         c->g, c->zetay, c->src64, c->src32, act);
 }
 
-void swj_launch_assemble(swj_ctx *c, double *E, int P)
+void swj_launch_assemble(swj_ctx *c, double *E, int P, const int *act)
 {
     SWJ_COUNT_LAUNCH();
-    k_assemble<<<nblk(c->T, 256), 256, 0, c->stream>>>(c->N, c->M, c->H, P, c->partial,
-                                                        c->e2part, E);
+    k_assemble<<<dim3(nblk(c->T, 256), c->nb), 256, 0, c->stream>>>(c->N, c->M, c->H, P, c->partial,
+                                                                     c->e2part, E, act);
 }
 
 void swj_launch_flat(swj_ctx *c, double *u)
 {
     SWJ_COUNT_LAUNCH();
-    k_flat<<<nblk(c->nu, 256), 256, 0, c->stream>>>(c->N, c->M, c->H, c->mesh.x1, u);
+    k_flat<<<dim3(nblk(c->nu, 256), c->nb), 256, 0, c->stream>>>(c->N, c->M, c->H, c->mesh.x1, u);
 }
 
 void swj_launch_unpack(swj_ctx *c, const double *u, double *zo, double *po)
 {
     const swj_mesh &m = c->mesh;
     SWJ_COUNT_LAUNCH();
-    k_integrate<<<nblk(2L * c->M * 32, 256), 256, 0, c->stream>>>(c->N, c->M, c->H, m.x1, m.dx,
-                                                                   u, c->zeta, c->g);
+    k_integrate<<<dim3(nblk(2L * c->M * 32, 256), c->nb), 256, 0, c->stream>>>(
+        c->N, c->M, c->H, m.x1, m.dx, u, c->zeta, c->g, nullptr);
     SWJ_COUNT_LAUNCH();
-    k_unpack<<<nblk(c->S, 256), 256, 0, c->stream>>>(c->N, c->M, m.x1, m.dx, c->zeta, c->g, zo,
-                                                      po);
+    k_unpack<<<dim3(nblk(c->S, 256), c->nb), 256, 0, c->stream>>>(c->N, c->M, m.x1, m.dx, c->zeta,
+                                                                  c->g, zo, po);
 }
 
 void swj_launch_surface(swj_ctx *c, double *out)

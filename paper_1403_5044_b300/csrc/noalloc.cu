@@ -49,10 +49,14 @@ int na_base(void **out)
 }
 
 // Forward-sweep coefficients of the spline system (same matrix as the
-// context path builds on the host), written straight into the scratch.
-__global__ void k_na_spline_coeffs(int M, double *cp, double *a, double *inv)
+// context path builds on the host) and F, eps, written straight into the
+// scratch.
+__global__ void k_na_setup(int M, double *cp, double *a, double *inv, double *Fd, double *epsd,
+                           double F, double eps)
 {
     if (blockIdx.x || threadIdx.x) return;
+    Fd[0] = F;
+    epsd[0] = eps;
     cp[0] = 0.0; a[0] = 0.0; inv[0] = 1.0;
     for (int j = 1; j < M; ++j) {
         double aj = (j < M - 1) ? 1.0 : 2.0;
@@ -89,7 +93,7 @@ extern "C" int swj_residual_noalloc(const swj_mesh *mesh, double F, double eps, 
     const long long S = (long long)mesh->N * mesh->M, T = (long long)(mesh->N - 1) * mesh->M;
     // fixed part of the scratch; the partial sums need at least one chunk (P = 1)
     const long long need = 4 * S * 8 + 3LL * mesh->M * 8 + 2 * T * 8 + S * (long long)sizeof(SrcRec64) +
-                           S * (long long)sizeof(SrcRec32) + 8 * T * 8 + 8 * T * 4 + T * 8 + 13 * 256;
+                           S * (long long)sizeof(SrcRec32) + 8 * T * 8 + 8 * T * 4 + T * 8 + 15 * 256;
     if (need > (long long)SWJ_NOALLOC_SCRATCH_BYTES) return SWJ_ESIZE;
 
     void *base = nullptr;
@@ -99,8 +103,7 @@ extern "C" int swj_residual_noalloc(const swj_mesh *mesh, double F, double eps, 
     swj_ctx c;
     memset((void *)&c, 0, sizeof(c));
     c.mesh = *mesh;
-    c.F = F;
-    c.eps = eps;
+    c.nb = 1;
     c.stream = (cudaStream_t)stream;
     if (cudaGetDevice(&c.dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, c.dev) != cudaSuccess)
@@ -142,14 +145,16 @@ extern "C" int swj_residual_noalloc(const swj_mesh *mesh, double F, double eps, 
         pl.P = (int)((S + pl.chunk - 1) / pl.chunk);
     }
     c.partial = (double *)cv.take((size_t)pl.P * T * 8);
-    if (!c.partial) return SWJ_ESIZE;
+    c.Fd = (double *)cv.take(8);
+    c.epsd = (double *)cv.take(8);
+    if (!c.partial || !c.epsd) return SWJ_ESIZE;
 
     SWJ_COUNT_LAUNCH();
-    k_na_spline_coeffs<<<1, 1, 0, c.stream>>>(c.M, c.spl_cp, c.spl_a, c.spl_inv);
-    swj_launch_mesh_step(&c, u_dev, E_dev);
-    if (precision == SWJ_FP64) swj_launch_pairs64(&c, pl);
-    else swj_launch_pairs32(&c, pl);
-    swj_launch_assemble(&c, E_dev, pl.P);
+    k_na_setup<<<1, 1, 0, c.stream>>>(c.M, c.spl_cp, c.spl_a, c.spl_inv, c.Fd, c.epsd, F, eps);
+    swj_launch_mesh_step(&c, u_dev, E_dev, nullptr);
+    if (precision == SWJ_FP64) swj_launch_pairs64(&c, pl, nullptr);
+    else swj_launch_pairs32(&c, pl, nullptr);
+    swj_launch_assemble(&c, E_dev, pl.P, nullptr);
     SWJ_CUDA_TRY(cudaGetLastError());
     return SWJ_OK;
 }

@@ -74,9 +74,17 @@ constexpr int kSub = 64;   // sources per compensated sub-tile
 template <typename T, int R>
 __global__ void __launch_bounds__(128)
 k_pairs_s(int T_, int S_, int chunk, const SrcRecS<T> *__restrict__ src, TgtArraysS<T> tg,
-          double *__restrict__ partial)
+          double *__restrict__ partial, const int *__restrict__ act)
 {
     constexpr int TILE = Cfg<T>::tile;
+    const int inst = blockIdx.z;
+    if (!SWJ_INST_ACTIVE(act, inst)) return;
+    {
+        const size_t ot = (size_t)inst * T_;
+        src += (size_t)inst * S_;
+        tg.x += ot; tg.y += ot; tg.zeta += ot; tg.g += ot; tg.zxw += ot; tg.A += ot; tg.B += ot; tg.C += ot;
+        partial += (size_t)inst * gridDim.y * T_;
+    }
     __shared__ SrcRecS<T> sh[TILE];
     const int tid = threadIdx.x, nth = blockDim.x;
     const int s0 = blockIdx.y * chunk;
@@ -196,18 +204,20 @@ PairPlan swj_pair_plan(const swj_ctx *c, int precision)
     return make_plan(c->T, c->S, slots);
 }
 
-void swj_launch_pairs64(swj_ctx *c, const PairPlan &pl)
+// One launch covers every instance (grid.z); each instance uses the chunking
+// of the single-instance plan, so its result does not depend on the batch.
+void swj_launch_pairs64(swj_ctx *c, const PairPlan &pl, const int *act)
 {
-    dim3 grid(pl.tiles, pl.P);
+    dim3 grid(pl.tiles, pl.P, c->nb);
     SWJ_COUNT_LAUNCH();
     k_pairs_s<double, kR><<<grid, kTPB, 0, c->stream>>>(c->T, c->S, pl.chunk, c->src64, c->tgt64,
-                                                        c->partial);
+                                                        c->partial, act);
 }
 
-void swj_launch_pairs32(swj_ctx *c, const PairPlan &pl)
+void swj_launch_pairs32(swj_ctx *c, const PairPlan &pl, const int *act)
 {
-    dim3 grid(pl.tiles, pl.P);
+    dim3 grid(pl.tiles, pl.P, c->nb);
     SWJ_COUNT_LAUNCH();
     k_pairs_s<float, kR><<<grid, kTPB, 0, c->stream>>>(c->T, c->S, pl.chunk, c->src32, c->tgt32,
-                                                       c->partial);
+                                                       c->partial, act);
 }

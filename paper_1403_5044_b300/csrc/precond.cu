@@ -158,10 +158,10 @@ __global__ void k_diag_corr(int N, int M, int P, double dx, double dy,
     out[t] = 0.5 * s - 0.5 * I;
 }
 
-// Band of S: block (l, m = l - h + slot) of D minus G on the diagonal blocks.
-__global__ void k_fill_band(int N, int M, int h, double x1, double dx, double dy, double nrad,
-                            const double *__restrict__ diag, const double *__restrict__ G,
-                            double *__restrict__ band)
+// D of one instance (the band of the zeta-zeta block of P; it does not depend
+// on F): block (l, m = l - h + slot).
+__global__ void k_fill_D(int N, int M, int h, double x1, double dx, double dy, double nrad,
+                         const double *__restrict__ diag, double *__restrict__ band)
 {
     const size_t n1 = N + 1, nb = 2 * h + 1;
     const size_t total = (size_t)M * nb * n1 * n1;
@@ -189,73 +189,130 @@ __global__ void k_fill_band(int N, int M, int h, double x1, double dx, double dy
                 v = -w * K3;
                 if (m == l && (c == k || c == k + 1)) v += diag[(size_t)l * (N - 1) + (k - 1)];
             }
-            if (m == l) v -= G[(size_t)r * n1 + c];
         }
         band[e] = v;
     }
 }
 
-// x_l = inv_l t_l for every block row l (block-diagonal S, h = 0).
-__global__ void k_blockdiag_gemv(int n1, int M, const double *__restrict__ band, size_t bstride,
-                                 const double *__restrict__ t, double *__restrict__ x)
+// dst[b] = src for instances b = 1..nb-1 (src is instance 0's band)
+__global__ void k_replicate(size_t n, const double *__restrict__ src, double *__restrict__ base,
+                            size_t stride)
 {
+    const int inst = blockIdx.y + 1;
+    double *dst = base + (size_t)inst * stride;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+        dst[e] = src[e];
+}
+
+// S = D - G / F^2 on every diagonal block of every instance (G = C A^-1 B at F = 1)
+__global__ void k_sub_G(int n1, int M, int h, const double *__restrict__ G1,
+                        const double *__restrict__ invF2, double *__restrict__ band, size_t stride)
+{
+    const int inst = blockIdx.y;
+    const size_t n2 = (size_t)n1 * n1, nb = 2 * h + 1;
+    const double f = invF2[inst];
+    double *b0 = band + (size_t)inst * stride;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)M * n2;
+         e += (size_t)gridDim.x * blockDim.x) {
+        size_t l = e / n2, rc = e % n2;
+        b0[(l * nb + h) * n2 + rc] -= f * G1[rc];
+    }
+}
+
+// copy `count` blocks of n doubles between strided locations
+__global__ void k_copy_blocks(size_t n, const double *__restrict__ src, size_t sstride,
+                              double *__restrict__ dst, size_t dstride)
+{
+    const int b = blockIdx.y;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+        dst[(size_t)b * dstride + e] = src[(size_t)b * sstride + e];
+}
+
+// x_l = inv_l t_l for every block row l of every instance (block-diagonal S, h = 0)
+__global__ void k_blockdiag_gemv(int n1, int M, const double *__restrict__ band, size_t bstride,
+                                 const double *__restrict__ t, double *__restrict__ x,
+                                 size_t vstride, const int *__restrict__ act)
+{
+    const int inst = blockIdx.y;
+    if (!SWJ_INST_ACTIVE(act, inst)) return;
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     if (warp >= n1 * M) return;
     int l = warp / n1, r = warp % n1;
-    const double *inv = band + (size_t)l * bstride + (size_t)r * n1;
-    const double *tl = t + (size_t)l * n1;
+    const double *inv = band + (size_t)inst * bstride * M + (size_t)l * bstride + (size_t)r * n1;
+    const double *tl = t + (size_t)inst * vstride + (size_t)l * n1;
     double s = 0.0;
     for (int c = lane; c < n1; c += 32) s = fma(inv[c], tl[c], s);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) x[(size_t)l * n1 + r] = s;
+    if (lane == 0) x[(size_t)inst * vstride + (size_t)l * n1 + r] = s;
 }
 
-// Y[l][c] = alpha * dot(X[l, :], Mat[c, :]) + beta * Y[l][c]   (X: M x n, Mat: n x n)
-__global__ void k_rowdot(int M, int n, const double *__restrict__ X, const double *__restrict__ Mat,
-                         double alpha, double beta, double *__restrict__ Y)
+// Y[l][c] = alpha f dot(X[l, :], Mat[c, :]) + beta Y[l][c] for the M rows of
+// every instance (X, Y at instance strides xs, ys; f = scale[inst] or 1)
+__global__ void k_rowdot(int M, int n, const double *__restrict__ X, size_t xs,
+                         const double *__restrict__ Mat, double alpha, const double *__restrict__ scale,
+                         double beta, double *__restrict__ Y, size_t ys, const int *__restrict__ act)
 {
+    const int inst = blockIdx.y;
+    if (!SWJ_INST_ACTIVE(act, inst)) return;
     int warp = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
     int lane = threadIdx.x & 31;
     if (warp >= M * n) return;
     int l = warp / n, c = warp % n;
-    const double *x = X + (size_t)l * n, *mr = Mat + (size_t)c * n;
+    const double *x = X + (size_t)inst * xs + (size_t)l * n, *mr = Mat + (size_t)c * n;
     double s = 0.0;
     for (int k = lane; k < n; k += 32) s = fma(x[k], mr[k], s);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) {
-        double *y = Y + (size_t)l * n + c;
-        *y = (beta == 0.0) ? alpha * s : fma(alpha, s, beta * *y);
+        double a = scale ? alpha * scale[inst] : alpha;
+        double *y = Y + (size_t)inst * ys + (size_t)l * n + c;
+        *y = (beta == 0.0) ? a * s : fma(a, s, beta * *y);
     }
 }
 
-inline void rowdot(cudaStream_t st, int M, int n, const double *X, const double *Mat, double alpha,
-                   double beta, double *Y)
+// y_inst = x_inst for vectors at different instance strides
+__global__ void k_copy_vec(int n, const double *__restrict__ x, size_t xs, double *__restrict__ y,
+                           size_t ys, const int *__restrict__ act)
+{
+    const int inst = blockIdx.y;
+    if (!SWJ_INST_ACTIVE(act, inst)) return;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[(size_t)inst * ys + i] = x[(size_t)inst * xs + i];
+}
+
+inline void rowdot(swj_ctx *c, const double *X, size_t xs, const double *Mat, double alpha,
+                   const double *scale, double beta, double *Y, size_t ys, const int *act)
 {
     SWJ_COUNT_LAUNCH();
-    k_rowdot<<<nblk((long)M * n * 32, 256), 256, 0, st>>>(M, n, X, Mat, alpha, beta, Y);
+    k_rowdot<<<dim3(nblk((long)c->M * c->n1 * 32, 256), c->nb), 256, 0, c->stream>>>(
+        c->M, c->n1, X, xs, Mat, alpha, scale, beta, Y, ys, act);
 }
 
-inline double *wblk(swj_ctx *c, int i, int k)
+inline size_t band_stride(const swj_ctx *c)
 {
-    size_t n2 = (size_t)c->n1 * c->n1;
-    return c->pc_W + ((size_t)i * c->pc_h + (k - i - 1)) * n2;
+    return (size_t)c->M * c->pc_nb * c->n1 * c->n1;
 }
 
-inline double *blk(swj_ctx *c, int l, int m)
+inline double *blk(swj_ctx *c, int inst, int l, int m)
 {
     size_t n2 = (size_t)c->n1 * c->n1;
     int slot = m - l + c->pc_h;
-    return c->pc_band + ((size_t)l * c->pc_nb + slot) * n2;
+    return c->pc_band + inst * band_stride(c) + ((size_t)l * c->pc_nb + slot) * n2;
+}
+
+inline double *wblk(swj_ctx *c, int inst, int i, int k)
+{
+    size_t n2 = (size_t)c->n1 * c->n1;
+    return c->pc_W + ((size_t)inst * c->M * c->pc_h + (size_t)i * c->pc_h + (k - i - 1)) * n2;
 }
 
 void free_pc(swj_ctx *c)
 {
-    double **bufs[] = {&c->pc_Ainv, &c->pc_AinvB, &c->pc_CAinv, &c->pc_G, &c->pc_A, &c->pc_B,
-                       &c->pc_C, &c->pc_tmp, &c->pc_band, &c->pc_sumK3, &c->pc_t1, &c->pc_t2,
-                       &c->pc_work, &c->pc_W, &c->pc_z};
+    double **bufs[] = {&c->pc_Ainv, &c->pc_AinvB1, &c->pc_CAinv, &c->pc_G1, &c->pc_A, &c->pc_B1,
+                       &c->pc_C, &c->pc_invF2, &c->pc_band, &c->pc_W, &c->pc_sumK3, &c->pc_t1,
+                       &c->pc_t2, &c->pc_z, &c->pc_work};
     for (double **b : bufs) {
         if (*b) cudaFree(*b);
         *b = nullptr;
@@ -274,81 +331,104 @@ void swj_pc_free(swj_ctx *c) { free_pc(c); }
 
 int swj_pc_setup(swj_ctx *c)
 {
-    const int N = c->N, M = c->M, n1 = c->n1;
+    const int N = c->N, M = c->M, n1 = c->n1, nb = c->nb;
     const swj_mesh &m = c->mesh;
     cudaStream_t st = c->stream;
     int b = c->opts.block_bw;
     int h = (b == 0) ? M - 1 : (b - 1) / 2;
     if (h > M - 1) h = M - 1;
-    // the band sweep stages h + 1 block vectors in shared memory
+    // the band sweep stages h vectors of n1 doubles in shared memory
     if ((size_t)(h + 1) * n1 * sizeof(double) > 200 * 1024) return SWJ_EINVAL;
     const size_t n2 = (size_t)n1 * n1;
-    const int nb = 2 * h + 1;
+    const int nbs = 2 * h + 1;
+    const bool gj_inplace = swj_gj_inplace(n1);
     if (!c->pc_band || c->pc_h != h) {
         free_pc(c);
         c->pc_h = h;
-        c->pc_nb = nb;
-        size_t sz[] = {n2, n2, n2, n2, n2, n2, n2, n2,
-                       (size_t)M * nb * n2, (size_t)c->T, (size_t)c->H, (size_t)c->H,
-                       (size_t)(h == 0 ? M : 1) * n2, (size_t)M * (h > 0 ? h : 1) * n2,
-                       (size_t)c->H};
-        double **bufs[] = {&c->pc_Ainv, &c->pc_AinvB, &c->pc_CAinv, &c->pc_G, &c->pc_A,
-                           &c->pc_B, &c->pc_C, &c->pc_tmp, &c->pc_band, &c->pc_sumK3,
-                           &c->pc_t1, &c->pc_t2, &c->pc_work, &c->pc_W, &c->pc_z};
+        c->pc_nb = nbs;
+        size_t work_blocks = gj_inplace ? 1 : (size_t)nb * (h == 0 ? M : 1);
+        size_t sz[] = {n2, n2, n2, n2, n2, n2, n2, (size_t)nb,
+                       (size_t)nb * M * nbs * n2, (size_t)nb * M * (h > 0 ? h : 1) * n2,
+                       (size_t)c->T, (size_t)nb * c->H, (size_t)nb * c->H, (size_t)nb * c->H,
+                       work_blocks * n2};
+        double **bufs[] = {&c->pc_Ainv, &c->pc_AinvB1, &c->pc_CAinv, &c->pc_G1, &c->pc_A,
+                           &c->pc_B1, &c->pc_C, &c->pc_invF2, &c->pc_band, &c->pc_W,
+                           &c->pc_sumK3, &c->pc_t1, &c->pc_t2, &c->pc_z, &c->pc_work};
         for (int i = 0; i < 15; ++i)
             if (cudaMalloc(bufs[i], sz[i] * sizeof(double)) != cudaSuccess) {
                 free_pc(c);
                 return SWJ_ENOMEM;
             }
-        if (cudaMalloc(&c->pc_info, (size_t)M * sizeof(int)) != cudaSuccess) {
+        if (cudaMalloc(&c->pc_info, (size_t)nb * M * sizeof(int)) != cudaSuccess) {
             free_pc(c);
             return SWJ_ENOMEM;
         }
     }
     c->pc_ready = 0;
-    // --- repeated blocks A, B, C and their products (Appendix C)
+    std::vector<double> invF2(nb);
+    for (int i = 0; i < nb; ++i) invF2[i] = 1.0 / (c->F[i] * c->F[i]);
+    SWJ_CUDA_TRY(cudaMemcpyAsync(c->pc_invF2, invF2.data(), nb * sizeof(double), cudaMemcpyHostToDevice, st));
+    // --- repeated blocks A, B (at F = 1), C and their products (Appendix C)
     SWJ_COUNT_LAUNCH();
-    k_build_ABC<<<nblk((long)n2, 256), 256, 0, st>>>(N, m.x1, m.dx, m.n_rad, c->F, c->pc_A,
-                                                     c->pc_B, c->pc_C);
+    k_build_ABC<<<nblk((long)n2, 256), 256, 0, st>>>(N, m.x1, m.dx, m.n_rad, 1.0, c->pc_A,
+                                                     c->pc_B1, c->pc_C);
     double *cpv = c->pc_t1;   // n1 scratch
     SWJ_COUNT_LAUNCH();
     k_tri_coef<<<1, 1, 0, st>>>(n1, c->pc_A, cpv);
     SWJ_COUNT_LAUNCH();
     k_tri_cols<<<nblk(n1, 128), 128, 0, st>>>(n1, n1, c->pc_A, cpv, nullptr, c->pc_Ainv);
     SWJ_COUNT_LAUNCH();
-    k_tri_cols<<<nblk(n1, 128), 128, 0, st>>>(n1, n1, c->pc_A, cpv, c->pc_B, c->pc_AinvB);
+    k_tri_cols<<<nblk(n1, 128), 128, 0, st>>>(n1, n1, c->pc_A, cpv, c->pc_B1, c->pc_AinvB1);
     swj_dgemm(st, n1, n1, n1, 1.0, c->pc_C, n1, c->pc_Ainv, n1, 0.0, c->pc_CAinv, n1);
-    swj_dgemm(st, n1, n1, n1, 1.0, c->pc_C, n1, c->pc_AinvB, n1, 0.0, c->pc_G, n1);
+    swj_dgemm(st, n1, n1, n1, 1.0, c->pc_C, n1, c->pc_AinvB1, n1, 0.0, c->pc_G1, n1);
     // --- PreD diagonal correction: trapezoid sum of w K3 and I of the flat surface
+    //     (instance 0's record buffers serve as scratch; every residual rewrites them)
     int prec = (c->opts.solve_mode == SWJ_SOLVE_FP64) ? SWJ_FP64 : SWJ_FP32;
     PairPlan pl = swj_pair_plan(c, prec);
     int ne = c->S > c->T ? c->S : c->T;
+    std::vector<int> only0(nb, 0);
+    only0[0] = 1;
+    int *act0 = c->act_d;
+    for (int i = 0; i < nb; ++i) c->act_h[i] = only0[i];
+    SWJ_CUDA_TRY(cudaMemcpyAsync(act0, c->act_h, nb * sizeof(int), cudaMemcpyHostToDevice, st));
     if (prec == SWJ_FP64) {
         SWJ_COUNT_LAUNCH();
         k_flat_records<double><<<nblk(ne, 256), 256, 0, st>>>(N, M, m.dx, m.dy, c->src64, c->tgt64);
-        swj_launch_pairs64(c, pl);
+        swj_launch_pairs64(c, pl, act0);
     } else {
         SWJ_COUNT_LAUNCH();
         k_flat_records<float><<<nblk(ne, 256), 256, 0, st>>>(N, M, m.dx, m.dy, c->src32, c->tgt32);
-        swj_launch_pairs32(c, pl);
+        swj_launch_pairs32(c, pl, act0);
     }
     SWJ_COUNT_LAUNCH();
     k_diag_corr<<<nblk(c->T, 256), 256, 0, st>>>(N, M, pl.P, m.dx, m.dy, c->partial, c->pc_sumK3);
-    // --- band of S
+    // --- band of S for every instance: D (shared) minus G / F^2 on the diagonal blocks
+    const size_t bst = band_stride(c);
     SWJ_COUNT_LAUNCH();
-    k_fill_band<<<4 * c->num_sms, 256, 0, st>>>(N, M, h, m.x1, m.dx, m.dy, m.n_rad, c->pc_sumK3,
-                                                c->pc_G, c->pc_band);
-    // --- block LU
-    SWJ_CUDA_TRY(cudaMemsetAsync(c->pc_info, 0, (size_t)M * sizeof(int), st));
-    const size_t bstride = (size_t)nb * n2;
+    k_fill_D<<<4 * c->num_sms, 256, 0, st>>>(N, M, h, m.x1, m.dx, m.dy, m.n_rad, c->pc_sumK3,
+                                             c->pc_band);
+    if (nb > 1) {
+        SWJ_COUNT_LAUNCH();
+        k_replicate<<<dim3(2 * c->num_sms, nb - 1), 256, 0, st>>>(bst, c->pc_band, c->pc_band, bst);
+    }
+    SWJ_COUNT_LAUNCH();
+    k_sub_G<<<dim3(nblk((long)M * n2, 256) < 4096 ? nblk((long)M * n2, 256) : 4096, nb), 256, 0, st>>>(
+        n1, M, h, c->pc_G1, c->pc_invF2, c->pc_band, bst);
+    // --- block LU of every instance, step by step
+    SWJ_CUDA_TRY(cudaMemsetAsync(c->pc_info, 0, (size_t)nb * M * sizeof(int), st));
     int rc;
     if (h == 0) {
-        SWJ_CUDA_TRY(cudaMemcpyAsync(c->pc_work, c->pc_band, (size_t)M * n2 * sizeof(double),
-                                     cudaMemcpyDeviceToDevice, st));
-        rc = swj_gj_inverse_cluster(st, n1, M, c->pc_work, n2, c->pc_band, bstride, c->pc_info);
+        // all M diagonal blocks of all instances are independent
+        if (gj_inplace) {
+            rc = swj_gj_inverse_cluster(st, n1, nb * M, c->pc_band, n2, c->pc_band, n2, c->pc_info);
+        } else {
+            SWJ_CUDA_TRY(cudaMemcpyAsync(c->pc_work, c->pc_band, (size_t)nb * M * n2 * sizeof(double),
+                                         cudaMemcpyDeviceToDevice, st));
+            rc = swj_gj_inverse_cluster(st, n1, nb * M, c->pc_work, n2, c->pc_band, n2, c->pc_info);
+        }
         if (rc) return rc;
     } else {
-        // device pointer triples of the batched GEMMs of every step:
+        // device pointer triples of the batched GEMMs of every step, all instances:
         //   W_ik = inv_i S_ik (k = i+1..i+h), then S_jk -= S_ji W_ik (j, k = i+1..i+h)
         std::vector<const double *> PA, PB;
         std::vector<double *> PC;
@@ -356,15 +436,19 @@ int swj_pc_setup(swj_ctx *c)
         for (int i = 0; i < M; ++i) {
             int kmax = i + h < M - 1 ? i + h : M - 1;
             offW[i] = (int)PA.size();
-            for (int k = i + 1; k <= kmax; ++k) {
-                PA.push_back(blk(c, i, i)); PB.push_back(blk(c, i, k)); PC.push_back(wblk(c, i, k));
-            }
+            for (int q = 0; q < nb; ++q)
+                for (int k = i + 1; k <= kmax; ++k) {
+                    PA.push_back(blk(c, q, i, i)); PB.push_back(blk(c, q, i, k));
+                    PC.push_back(wblk(c, q, i, k));
+                }
             cntW[i] = (int)PA.size() - offW[i];
             offU[i] = (int)PA.size();
-            for (int j = i + 1; j <= kmax; ++j)
-                for (int k = i + 1; k <= kmax; ++k) {
-                    PA.push_back(blk(c, j, i)); PB.push_back(wblk(c, i, k)); PC.push_back(blk(c, j, k));
-                }
+            for (int q = 0; q < nb; ++q)
+                for (int j = i + 1; j <= kmax; ++j)
+                    for (int k = i + 1; k <= kmax; ++k) {
+                        PA.push_back(blk(c, q, j, i)); PB.push_back(wblk(c, q, i, k));
+                        PC.push_back(blk(c, q, j, k));
+                    }
             cntU[i] = (int)PA.size() - offU[i];
         }
         int np = (int)PA.size();
@@ -385,11 +469,17 @@ int swj_pc_setup(swj_ctx *c)
         }
         SWJ_CUDA_TRY(cudaMemcpyAsync(c->pc_ptrs, all.data(), all.size() * sizeof(double *),
                                      cudaMemcpyHostToDevice, st));
+        SWJ_CUDA_TRY(cudaStreamSynchronize(st));   // `all` must outlive the copy
         double **dA = c->pc_ptrs, **dB = c->pc_ptrs + np, **dC = c->pc_ptrs + 2 * np;
         for (int i = 0; i < M; ++i) {
-            SWJ_CUDA_TRY(cudaMemcpyAsync(c->pc_work, blk(c, i, i), n2 * sizeof(double),
-                                         cudaMemcpyDeviceToDevice, st));
-            rc = swj_gj_inverse_cluster(st, n1, 1, c->pc_work, n2, blk(c, i, i), n2, c->pc_info + i);
+            double *diag0 = blk(c, 0, i, i);
+            if (gj_inplace) {
+                rc = swj_gj_inverse_cluster(st, n1, nb, diag0, bst, diag0, bst, c->pc_info + (size_t)i * nb);
+            } else {
+                SWJ_COUNT_LAUNCH();
+                k_copy_blocks<<<dim3(64, nb), 256, 0, st>>>(n2, diag0, bst, c->pc_work, n2);
+                rc = swj_gj_inverse_cluster(st, n1, nb, c->pc_work, n2, diag0, bst, c->pc_info + (size_t)i * nb);
+            }
             if (rc) return rc;
             if (cntW[i])
                 swj_dgemm_batched(st, n1, n1, n1, 1.0, (const double *const *)(dA + offW[i]), n1,
@@ -401,38 +491,53 @@ int swj_pc_setup(swj_ctx *c)
                                   cntU[i]);
         }
     }
-    std::vector<int> info(M);
-    SWJ_CUDA_TRY(cudaMemcpyAsync(info.data(), c->pc_info, (size_t)M * sizeof(int),
+    std::vector<int> info((size_t)nb * M);
+    SWJ_CUDA_TRY(cudaMemcpyAsync(info.data(), c->pc_info, info.size() * sizeof(int),
                                  cudaMemcpyDeviceToHost, st));
     SWJ_CUDA_TRY(cudaStreamSynchronize(st));
     SWJ_CUDA_TRY(cudaGetLastError());
-    for (int i = 0; i < M; ++i)
+    for (size_t i = 0; i < info.size(); ++i)
         if (info[i] != 0) return SWJ_ESINGULAR;
+    if (h > 0) {
+        int rc = swj_band_sweep_cluster(st, nb, n1, M, h, c->pc_band, band_stride(c), c->pc_W,
+                                        (size_t)M * h * n1 * n1, c->pc_t2, c->pc_z, c->pc_t2, (size_t)c->H,
+                                        nullptr, true);
+        if (rc) return rc;
+    }
     c->pc_ready = 1;
     return SWJ_OK;
 }
 
-int swj_pc_apply(swj_ctx *c, const double *b, double *r)
+int swj_pc_apply(swj_ctx *c, const double *b, double *r, const int *act)
 {
-    const int M = c->M, n1 = c->n1, H = c->H, h = c->pc_h;
+    const int M = c->M, n1 = c->n1, H = c->H, h = c->pc_h, nb = c->nb;
+    const size_t nu = c->nu;
     cudaStream_t st = c->stream;
     const size_t n2 = (size_t)n1 * n1;
-    const double *b1 = b, *b2 = b + H;
-    double *t1 = c->pc_t1, *t2 = c->pc_t2, *r2 = r + H;
+    double *t1 = c->pc_t1, *t2 = c->pc_t2;
     // t2 = b2 - C A^-1 b1 ; t1 = A^-1 b1   (per-row vectors are the rows of M x n1 matrices)
-    SWJ_CUDA_TRY(cudaMemcpyAsync(t2, b2, (size_t)H * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    rowdot(st, M, n1, b1, c->pc_CAinv, -1.0, 1.0, t2);
-    rowdot(st, M, n1, b1, c->pc_Ainv, 1.0, 0.0, t1);
-    // s2 = S^-1 t2 into r2
+    SWJ_COUNT_LAUNCH();
+    k_copy_vec<<<dim3(nblk(H, 256), nb), 256, 0, st>>>(H, b + H, nu, t2, H, act);
+    rowdot(c, b, nu, c->pc_CAinv, -1.0, nullptr, 1.0, t2, H, act);
+    rowdot(c, b, nu, c->pc_Ainv, 1.0, nullptr, 0.0, t1, H, act);
+    // s2 = S^-1 t2 into r2 (= r + H of every instance)
     if (h == 0) {
         SWJ_COUNT_LAUNCH();
-        k_blockdiag_gemv<<<nblk((long)n1 * M * 32, 256), 256, 0, st>>>(n1, M, c->pc_band, n2, t2, r2);
+        k_blockdiag_gemv<<<dim3(nblk((long)n1 * M * 32, 256), nb), 256, 0, st>>>(
+            n1, M, c->pc_band, n2, t2, c->pc_z, H, act);
+        SWJ_COUNT_LAUNCH();
+        k_copy_vec<<<dim3(nblk(H, 256), nb), 256, 0, st>>>(H, c->pc_z, H, r + H, nu, act);
     } else {
-        int rc = swj_band_sweep_cluster(st, n1, M, h, c->pc_band, c->pc_W, t2, c->pc_z, r2);
+        int rc = swj_band_sweep_cluster(st, nb, n1, M, h, c->pc_band, band_stride(c), c->pc_W,
+                                        (size_t)M * h * n2, t2, c->pc_z, c->pc_t2, H, act);
         if (rc) return rc;
+        // the sweep leaves x in pc_t2 (y is dead after the forward phase)
+        SWJ_COUNT_LAUNCH();
+        k_copy_vec<<<dim3(nblk(H, 256), nb), 256, 0, st>>>(H, c->pc_t2, H, r + H, nu, act);
     }
-    // r1 = A^-1 b1 - A^-1 B s2
-    rowdot(st, M, n1, r2, c->pc_AinvB, -1.0, 1.0, t1);
-    SWJ_CUDA_TRY(cudaMemcpyAsync(r, t1, (size_t)H * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    // r1 = A^-1 b1 - (A^-1 B) s2, A^-1 B = (A^-1 B at F = 1) / F^2
+    rowdot(c, r + H, nu, c->pc_AinvB1, -1.0, c->pc_invF2, 1.0, t1, H, act);
+    SWJ_COUNT_LAUNCH();
+    k_copy_vec<<<dim3(nblk(H, 256), nb), 256, 0, st>>>(H, t1, H, r, nu, act);
     return SWJ_OK;
 }

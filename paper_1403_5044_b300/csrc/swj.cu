@@ -42,10 +42,14 @@ void free_all(swj_ctx *c)
     void *ptrs[] = {c->zeta, c->g, c->zetay, c->gy, c->spl_cp, c->spl_a, c->spl_inv, c->e2part,
                     c->Ival, c->src64, c->src32, c->tgt64_base, c->tgt32_base, c->partial,
                     c->u_tmp, c->E_tmp, c->E_cur, c->u_try, c->E_try, c->E_base32, c->du,
-                    c->rvec, c->dscal, c->red, c->V, c->Z};
+                    c->rvec, c->dscal, c->red, c->V, c->Z, c->Fd, c->epsd, c->act_d};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->hpin) cudaFreeHost(c->hpin);
+    if (c->act_h) cudaFreeHost(c->act_h);
+    free(c->F);
+    free(c->eps);
+    swj_graphs_free(c);
     swj_pc_free(c);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
@@ -58,43 +62,53 @@ void free_all(swj_ctx *c)
 
 int alloc_all(swj_ctx *c)
 {
-    const size_t S = c->S, T = c->T, M = c->M, nu = c->nu;
+    const size_t S = c->S, T = c->T, M = c->M, nu = c->nu, nb = c->nb;
     int rc = 0;
-    rc |= dalloc(c, &c->zeta, S);
-    rc |= dalloc(c, &c->g, S);
-    rc |= dalloc(c, &c->zetay, S);
-    rc |= dalloc(c, &c->gy, S);
+    rc |= dalloc(c, &c->zeta, nb * S);
+    rc |= dalloc(c, &c->g, nb * S);
+    rc |= dalloc(c, &c->zetay, nb * S);
+    rc |= dalloc(c, &c->gy, nb * S);
     rc |= dalloc(c, &c->spl_cp, M);
     rc |= dalloc(c, &c->spl_a, M);
     rc |= dalloc(c, &c->spl_inv, M);
-    rc |= dalloc(c, &c->e2part, T);
-    rc |= dalloc(c, &c->Ival, T);
-    rc |= dalloc(c, &c->src64, S);
-    rc |= dalloc(c, &c->src32, S);
-    rc |= dalloc(c, &c->tgt64_base, 8 * T);
-    rc |= dalloc(c, &c->tgt32_base, 8 * T);
+    rc |= dalloc(c, &c->e2part, nb * T);
+    rc |= dalloc(c, &c->Ival, nb * T);
+    rc |= dalloc(c, &c->src64, nb * S);
+    rc |= dalloc(c, &c->src32, nb * S);
+    rc |= dalloc(c, &c->tgt64_base, 8 * nb * T);
+    rc |= dalloc(c, &c->tgt32_base, 8 * nb * T);
+    rc |= dalloc(c, &c->Fd, nb);
+    rc |= dalloc(c, &c->epsd, nb);
+    rc |= dalloc(c, &c->act_d, nb);
     if (rc) return SWJ_ENOMEM;
+    // each field of the target arrays holds nb blocks of T values
+    const size_t NT = nb * T;
     double *b = c->tgt64_base;
-    c->tgt64 = TgtArrays64{b, b + T, b + 2 * T, b + 3 * T, b + 4 * T, b + 5 * T, b + 6 * T, b + 7 * T};
+    c->tgt64 = TgtArrays64{b, b + NT, b + 2 * NT, b + 3 * NT, b + 4 * NT, b + 5 * NT, b + 6 * NT, b + 7 * NT};
     float *f = c->tgt32_base;
-    c->tgt32 = TgtArrays32{f, f + T, f + 2 * T, f + 3 * T, f + 4 * T, f + 5 * T, f + 6 * T, f + 7 * T};
+    c->tgt32 = TgtArrays32{f, f + NT, f + 2 * NT, f + 3 * NT, f + 4 * NT, f + 5 * NT, f + 6 * NT, f + 7 * NT};
     c->plan64 = swj_pair_plan(c, SWJ_FP64);
     c->plan32 = swj_pair_plan(c, SWJ_FP32);
     int P = c->plan64.P > c->plan32.P ? c->plan64.P : c->plan32.P;
-    c->partial_cap = (size_t)P * T;
+    c->partial_cap = (size_t)P * T * nb;
     rc |= dalloc(c, &c->partial, c->partial_cap);
     double **vecs[] = {&c->u_tmp, &c->E_tmp, &c->E_cur, &c->u_try, &c->E_try, &c->E_base32, &c->du, &c->rvec};
-    for (double **v : vecs) rc |= dalloc(c, v, nu);
-    rc |= dalloc(c, &c->dscal, 512);
-    rc |= dalloc(c, &c->red, 64 * 64 + 1024);
+    for (double **v : vecs) rc |= dalloc(c, v, nb * nu);
+    rc |= dalloc(c, &c->dscal, nb * SWJ_DS);
+    rc |= dalloc(c, &c->red, nb * SWJ_RED);
     c->kry_m = c->opts.gmres_restart;
-    rc |= dalloc(c, &c->V, (size_t)(c->kry_m + 1) * nu);
-    rc |= dalloc(c, &c->Z, (size_t)c->kry_m * nu);
+    rc |= dalloc(c, &c->V, nb * (c->kry_m + 1) * nu);
+    rc |= dalloc(c, &c->Z, nb * c->kry_m * nu);
     if (rc) return SWJ_ENOMEM;
-    if (cudaMallocHost((void **)&c->hpin, 512 * sizeof(double)) != cudaSuccess) {
+    if (cudaMallocHost((void **)&c->hpin, nb * SWJ_DS * sizeof(double)) != cudaSuccess) {
         c->hpin = nullptr;
         return SWJ_ENOMEM;
     }
+    if (cudaMallocHost((void **)&c->act_h, nb * sizeof(int)) != cudaSuccess) {
+        c->act_h = nullptr;
+        return SWJ_ENOMEM;
+    }
+    for (size_t i = 0; i < nb; ++i) c->act_h[i] = 1;
     double *cp = (double *)malloc(3 * M * sizeof(double));
     if (!cp) return SWJ_ENOMEM;
     swj_spline_coeffs((int)M, cp, cp + M, cp + 2 * M);
@@ -103,8 +117,65 @@ int alloc_all(swj_ctx *c)
     cudaError_t e3 = cudaMemcpy(c->spl_inv, cp + 2 * M, M * sizeof(double), cudaMemcpyHostToDevice);
     free(cp);
     if (e1 || e2 || e3) return SWJ_ECUDA;
+    if (cudaMemcpy(c->Fd, c->F, nb * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->epsd, c->eps, nb * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->act_d, c->act_h, nb * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+        return SWJ_ECUDA;
     if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess)
         return SWJ_ECUDA;
+    c->graphs_enabled = 1;
+    return SWJ_OK;
+}
+
+int create_ctx(swj_ctx **out, const swj_mesh *mesh, int nb, const double *F, const double *eps,
+               const swj_opts *opts, void *stream)
+{
+    if (!out) return SWJ_EINVAL;
+    *out = nullptr;
+    if (!valid_mesh(mesh) || nb < 1 || !F || !eps) return SWJ_EINVAL;
+    for (int i = 0; i < nb; ++i)
+        if (!(F[i] > 0.0) || !(eps[i] >= 0.0)) return SWJ_EINVAL;
+    swj_opts o;
+    if (opts) o = *opts; else swj_default_opts(&o);
+    if (!valid_opts(&o)) return SWJ_EINVAL;
+    swj_ctx *c = new (std::nothrow) swj_ctx();
+    if (!c) return SWJ_ENOMEM;
+    memset((void *)c, 0, sizeof(*c));
+    c->mesh = *mesh;
+    c->opts = o;
+    c->stream = (cudaStream_t)stream;
+    c->nb = nb;
+    c->F = (double *)malloc(nb * sizeof(double));
+    c->eps = (double *)malloc(nb * sizeof(double));
+    if (!c->F || !c->eps) {
+        free(c->F);
+        free(c->eps);
+        delete c;
+        return SWJ_ENOMEM;
+    }
+    memcpy(c->F, F, nb * sizeof(double));
+    memcpy(c->eps, eps, nb * sizeof(double));
+    if (cudaGetDevice(&c->dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->dev) != cudaSuccess) {
+        free(c->F);
+        free(c->eps);
+        delete c;
+        return SWJ_ECUDA;
+    }
+    c->N = mesh->N;
+    c->M = mesh->M;
+    c->n1 = c->N + 1;
+    c->H = c->n1 * c->M;
+    c->nu = 2 * c->H;
+    c->T = (c->N - 1) * c->M;
+    c->S = c->N * c->M;
+    int rc = alloc_all(c);
+    if (rc) {
+        free_all(c);
+        delete c;
+        return rc;
+    }
+    *out = c;
     return SWJ_OK;
 }
 
@@ -133,41 +204,16 @@ void swj_default_opts(swj_opts *o)
 int swj_create(swj_ctx **out, const swj_mesh *mesh, double F, double eps, const swj_opts *opts,
                void *stream)
 {
-    if (!out) return SWJ_EINVAL;
-    *out = nullptr;
-    if (!valid_mesh(mesh) || !(F > 0.0) || !(eps >= 0.0)) return SWJ_EINVAL;
-    swj_opts o;
-    if (opts) o = *opts; else swj_default_opts(&o);
-    if (!valid_opts(&o)) return SWJ_EINVAL;
-    swj_ctx *c = new (std::nothrow) swj_ctx();
-    if (!c) return SWJ_ENOMEM;
-    memset((void *)c, 0, sizeof(*c));
-    c->mesh = *mesh;
-    c->F = F;
-    c->eps = eps;
-    c->opts = o;
-    c->stream = (cudaStream_t)stream;
-    if (cudaGetDevice(&c->dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->dev) != cudaSuccess) {
-        delete c;
-        return SWJ_ECUDA;
-    }
-    c->N = mesh->N;
-    c->M = mesh->M;
-    c->n1 = c->N + 1;
-    c->H = c->n1 * c->M;
-    c->nu = 2 * c->H;
-    c->T = (c->N - 1) * c->M;
-    c->S = c->N * c->M;
-    int rc = alloc_all(c);
-    if (rc) {
-        free_all(c);
-        delete c;
-        return rc;
-    }
-    *out = c;
-    return SWJ_OK;
+    return create_ctx(out, mesh, 1, &F, &eps, opts, stream);
 }
+
+int swj_batch_create(swj_ctx **out, const swj_mesh *mesh, int count, const double *F,
+                     const double *eps, const swj_opts *opts, void *stream)
+{
+    return create_ctx(out, mesh, count, F, eps, opts, stream);
+}
+
+int swj_batch_count(const swj_ctx *c) { return c ? c->nb : 0; }
 
 void swj_destroy(swj_ctx *c)
 {
@@ -180,9 +226,30 @@ void swj_destroy(swj_ctx *c)
 int swj_set_params(swj_ctx *c, double F, double eps)
 {
     if (!c || !(F > 0.0) || !(eps >= 0.0)) return SWJ_EINVAL;
-    if (F != c->F) c->pc_ready = 0;
-    c->F = F;
-    c->eps = eps;
+    for (int i = 0; i < c->nb; ++i) {
+        if (F != c->F[i]) c->pc_ready = 0;
+        c->F[i] = F;
+        c->eps[i] = eps;
+    }
+    SWJ_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    SWJ_CUDA_TRY(cudaMemcpy(c->Fd, c->F, c->nb * sizeof(double), cudaMemcpyHostToDevice));
+    SWJ_CUDA_TRY(cudaMemcpy(c->epsd, c->eps, c->nb * sizeof(double), cudaMemcpyHostToDevice));
+    return SWJ_OK;
+}
+
+int swj_batch_set_params(swj_ctx *c, const double *F, const double *eps)
+{
+    if (!c || !F || !eps) return SWJ_EINVAL;
+    for (int i = 0; i < c->nb; ++i)
+        if (!(F[i] > 0.0) || !(eps[i] >= 0.0)) return SWJ_EINVAL;
+    for (int i = 0; i < c->nb; ++i) {
+        if (F[i] != c->F[i]) c->pc_ready = 0;
+        c->F[i] = F[i];
+        c->eps[i] = eps[i];
+    }
+    SWJ_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    SWJ_CUDA_TRY(cudaMemcpy(c->Fd, c->F, c->nb * sizeof(double), cudaMemcpyHostToDevice));
+    SWJ_CUDA_TRY(cudaMemcpy(c->epsd, c->eps, c->nb * sizeof(double), cudaMemcpyHostToDevice));
     return SWJ_OK;
 }
 
@@ -191,21 +258,23 @@ int swj_set_opts(swj_ctx *c, const swj_opts *o)
     if (!c || !valid_opts(o)) return SWJ_EINVAL;
     if (o->gmres_restart != c->kry_m) {
         double *V = nullptr, *Z = nullptr;
-        if (cudaMalloc(&V, (size_t)(o->gmres_restart + 1) * c->nu * sizeof(double)) != cudaSuccess)
+        if (cudaMalloc(&V, (size_t)c->nb * (o->gmres_restart + 1) * c->nu * sizeof(double)) != cudaSuccess)
             return SWJ_ENOMEM;
-        if (cudaMalloc(&Z, (size_t)o->gmres_restart * c->nu * sizeof(double)) != cudaSuccess) {
+        if (cudaMalloc(&Z, (size_t)c->nb * o->gmres_restart * c->nu * sizeof(double)) != cudaSuccess) {
             cudaFree(V);
             return SWJ_ENOMEM;
         }
         cudaStreamSynchronize(c->stream);
-        c->bytes -= (size_t)(2 * c->kry_m + 1) * c->nu * sizeof(double);
+        swj_graphs_free(c);
+        c->bytes -= (size_t)c->nb * (2 * c->kry_m + 1) * c->nu * sizeof(double);
         cudaFree(c->V);
         cudaFree(c->Z);
         c->V = V;
         c->Z = Z;
         c->kry_m = o->gmres_restart;
-        c->bytes += (size_t)(2 * c->kry_m + 1) * c->nu * sizeof(double);
+        c->bytes += (size_t)c->nb * (2 * c->kry_m + 1) * c->nu * sizeof(double);
     }
+    if (o->fd_h != c->opts.fd_h) swj_graphs_free(c);
     if (o->block_bw != c->opts.block_bw || o->solve_mode != c->opts.solve_mode) c->pc_ready = 0;
     c->opts = *o;
     return SWJ_OK;
@@ -225,7 +294,7 @@ int swj_residual(swj_ctx *c, const double *u, double *E, int precision)
 {
     if (!c || !u || !E || u == E) return SWJ_EINVAL;
     if (precision != SWJ_FP64 && precision != SWJ_FP32) return SWJ_EINVAL;
-    return swj_residual_impl(c, u, E, precision);
+    return swj_residual_impl(c, u, E, precision, nullptr);
 }
 
 int swj_jvp(swj_ctx *c, const double *u, const double *Eu, const double *v, double *Jv,
@@ -233,7 +302,7 @@ int swj_jvp(swj_ctx *c, const double *u, const double *Eu, const double *v, doub
 {
     if (!c || !u || !Eu || !v || !Jv) return SWJ_EINVAL;
     if (precision != SWJ_FP64 && precision != SWJ_FP32) return SWJ_EINVAL;
-    return swj_jvp_impl(c, u, Eu, v, Jv, precision, c->opts.fd_h);
+    return swj_jvp_impl(c, u, Eu, v, Jv, precision, c->opts.fd_h, nullptr);
 }
 
 int swj_precond_setup(swj_ctx *c)
@@ -249,7 +318,7 @@ int swj_precond_apply(swj_ctx *c, const double *b, double *r)
         int rc = swj_pc_setup(c);
         if (rc) return rc;
     }
-    return swj_pc_apply(c, b, r);
+    return swj_pc_apply(c, b, r, nullptr);
 }
 
 int swj_solve(swj_ctx *c, double *u, swj_stats *st)
@@ -273,7 +342,7 @@ int swj_surface(swj_ctx *c, const double *u, double *out)
 {
     if (!c || !u || !out) return SWJ_EINVAL;
     // the mesh step also writes E1/E3..E6 rows; send them to a scratch vector
-    swj_launch_mesh_step(c, u, c->E_tmp);
+    swj_launch_mesh_step(c, u, c->E_tmp, nullptr);
     swj_launch_surface(c, out);
     SWJ_CUDA_TRY(cudaGetLastError());
     return SWJ_OK;

@@ -1,5 +1,13 @@
 // Internal declarations of libswj: the context, device buffers and the
 // launch wrappers of each kernel family.  Not part of the public ABI.
+//
+// A context holds nb >= 1 instances of one mesh, each with its own (F, eps)
+// and its own unknowns, residual, Krylov space and preconditioner factors.
+// Every per-instance buffer is nb consecutive copies with a fixed stride, and
+// every kernel runs over all instances at once (the instance index is a grid
+// dimension).  A device array of per-instance flags (`act`, nullable = all)
+// lets converged instances drop out without changing any launch shape, so a
+// captured CUDA graph stays valid whatever the mix of active instances.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -7,7 +15,7 @@
 #include <stddef.h>
 #include "../../include/swj.h"
 
-#define SWJ_VERSION_STRING "swj 0.1 (sm_103a)"
+#define SWJ_VERSION_STRING "swj 0.2 (sm_103a)"
 
 // ---------------------------------------------------------------- records
 // Source record of the all-pairs sum (one per mesh node (i, j)), lengths in
@@ -23,9 +31,9 @@ template <typename T> struct SrcRecS {
     T x, y, zeta, zx, zy, g, w, zxw;
 };
 
-// Target arrays in the same units, structure of arrays of length T each:
-// x = (k + 1/2) rho, y = l, zeta* / L, g*, L zeta_x*, and the dimensionless
-// A = 1 + zx*^2, B = 2 zx* zy*, C = 1 + zy*^2.
+// Target arrays in the same units, structure of arrays (each field holds nb
+// blocks of T values): x = (k + 1/2) rho, y = l, zeta* / L, g*, L zeta_x*, and
+// the dimensionless A = 1 + zx*^2, B = 2 zx* zy*, C = 1 + zy*^2.
 template <typename T> struct TgtArraysS {
     T *x, *y, *zeta, *g, *zxw, *A, *B, *C;
 };
@@ -43,13 +51,21 @@ struct PairPlan {
     int tiles;    // target tiles (grid.x)
 };
 
+// is instance `inst` active (act = device flags, or nullptr for all)
+#define SWJ_INST_ACTIVE(act, inst) ((act) == nullptr || (act)[inst] != 0)
+
 // ---------------------------------------------------------------- context
 struct swj_ctx {
     swj_mesh mesh;
-    double F, eps;
     swj_opts opts;
     cudaStream_t stream;
     int dev, num_sms;
+
+    int nb;            // instances
+    double *F, *eps;   // host, per instance
+    double *Fd, *epsd; // device copies
+    int *act_d;        // device per-instance flags (1 = active)
+    int *act_h;        // pinned host mirror
 
     int N, M;          // mesh
     int n1;            // N + 1 (block size)
@@ -58,48 +74,53 @@ struct swj_ctx {
     int T;             // (N - 1) M targets
     int S;             // N M sources
 
-    // mesh step (FP64), node arrays [M][N]
+    // mesh step (FP64), node arrays [nb][M][N]
     double *zeta, *g, *zetay, *gy;
-    double *spl_cp, *spl_a, *spl_inv;   // Thomas coefficients along y (M each)
-    // per-target E2 terms that do not need the pair sum: 2 pi g* + src - zx* I
+    double *spl_cp, *spl_a, *spl_inv;   // Thomas coefficients along y (M each, shared)
+    // per-target E2 terms that do not need the pair sum: 2 pi g* + src - zx* I  [nb][T]
     double *e2part;
-    double *Ival;      // I per target (diagnostics)
-    // records for the two precisions
+    double *Ival;      // I per target (diagnostics)  [nb][T]
+    // records for the two precisions, [nb][S] / fields of [nb][T]
     SrcRec64 *src64;
     SrcRec32 *src32;
     TgtArrays64 tgt64;
     TgtArrays32 tgt32;
     double *tgt64_base; float *tgt32_base;
-    // partial sums [P][T]
+    // partial sums [nb][P][T]
     double *partial;
     size_t partial_cap;   // doubles
     PairPlan plan64, plan32;
 
-    // JVP / solver temporaries (length nu)
+    // JVP / solver temporaries, [nb][nu]
     double *u_tmp, *E_tmp;           // JVP: u + h v and E(u + h v)
     double *E_cur, *u_try, *E_try;   // Newton: current residual, line-search trial
     double *E_base32;                // MIXED refinement: FP32 residual at u (JVP base)
     double *du, *rvec;               // Newton step, GMRES right-hand side
-    double *dscal;        // device scalars (norms, FD step, Arnoldi coefficients)
-    double *red;          // reduction scratch
-    double *hpin;         // pinned host mirror of device scalars
+    double *dscal;        // device scalars [nb][SWJ_DS]
+    double *red;          // reduction scratch [nb][SWJ_RED]
+    double *hpin;         // pinned host mirror of dscal
 
-    // Krylov basis (m + 1) x nu and preconditioned basis m x nu
+    // Krylov bases [nb][m + 1][nu] and preconditioned [nb][m][nu]
     double *V, *Z;
     int kry_m;
+    // captured Arnoldi steps, one per Krylov index and per kind of linear solve
+    // (FP64 Newton, FP32 Newton, FP32-JVP refinement), valid for one address of u
+    cudaGraphExec_t *arn_graph;   // [3][kry_m], null until captured
+    const double *arn_u;          // the u the graphs were captured with
+    int graphs_enabled;
 
-    // preconditioner
+    // preconditioner: blocks that do not depend on F are shared, the factors are per instance
     int pc_ready, pc_h, pc_nb;   // built flag, block half bandwidth, blocks per band row
-    double *pc_Ainv, *pc_AinvB, *pc_CAinv, *pc_G, *pc_A, *pc_B, *pc_C, *pc_tmp;
-    double *pc_band;             // [M][2h+1][n1][n1]
-    double *pc_sumK3;            // [T] sum_s w K3 (flat-state trapezoid sum)
-    int *pc_info;                // device status of the factorisation
+    double *pc_Ainv, *pc_AinvB1, *pc_CAinv, *pc_G1, *pc_A, *pc_B1, *pc_C;   // (n1 x n1), "1" = at F = 1
+    double *pc_invF2;            // [nb] 1 / F^2 (scales B, G, A^-1 B)
+    double *pc_band;             // [nb][M][2h+1][n1][n1]
+    double *pc_W;                // [nb][M][h][n1][n1]  W_ik = inv_i S_ik
+    double *pc_sumK3;            // [T] PreD correction (flat-state sums; F-independent)
+    int *pc_info;                // [nb][M] status of the block inverses
     double **pc_ptrs;            // device pointer arrays for batched block GEMMs
     int pc_ptrs_cap;
-    double *pc_t1, *pc_t2;       // apply temporaries [H]
-    double *pc_work;             // Gauss-Jordan work copy: M blocks (h = 0) or one block
-    double *pc_W;                // W_ik = inv_i S_ik, [M][h][n1][n1]
-    double *pc_z;                // z_i = inv_i y_i of the forward sweep [H]
+    double *pc_t1, *pc_t2, *pc_z;   // apply temporaries [nb][H]
+    double *pc_work;             // Gauss-Jordan work copies [nb][(h == 0 ? M : 1)][n1][n1]
 
     size_t bytes;                // device bytes held
     cudaEvent_t ev0, ev1;
@@ -110,10 +131,12 @@ struct swj_ctx {
     int *tev_prec;               // precision of each timed launch (host array)
 };
 
+enum { SWJ_DS = 512, SWJ_RED = 64 * 64 + 1024 };
+
 // ---------------------------------------------------------------- launches
-// mesh.cu
-void swj_launch_mesh_step(swj_ctx *c, const double *u, double *E);
-void swj_launch_assemble(swj_ctx *c, double *E, int P);
+// mesh.cu (act: device per-instance flags or nullptr for all)
+void swj_launch_mesh_step(swj_ctx *c, const double *u, double *E, const int *act);
+void swj_launch_assemble(swj_ctx *c, double *E, int P, const int *act);
 void swj_spline_coeffs(int M, double *cp, double *a, double *inv);  // host helper
 void swj_launch_flat(swj_ctx *c, double *u);
 void swj_launch_unpack(swj_ctx *c, const double *u, double *zeta_out, double *phi_out);
@@ -121,53 +144,63 @@ void swj_launch_surface(swj_ctx *c, double *out);
 
 // pairs.cu
 PairPlan swj_pair_plan(const swj_ctx *c, int precision);
-void swj_launch_pairs64(swj_ctx *c, const PairPlan &pl);
-void swj_launch_pairs32(swj_ctx *c, const PairPlan &pl);
+void swj_launch_pairs64(swj_ctx *c, const PairPlan &pl, const int *act);
+void swj_launch_pairs32(swj_ctx *c, const PairPlan &pl, const int *act);
 
-// linalg.cu
-void swj_axpby(cudaStream_t st, int n, double a, const double *x, double b, double *y);      // y = a x + b y
-void swj_axpy_dev(cudaStream_t st, int n, const double *a_dev, double a_scale,
-                  const double *x, double *y);                                             // y += (a_scale * *a_dev) x
-void swj_scale_dev(cudaStream_t st, int n, const double *num_dev, double *x, int invert);  // x *= *num (or 1/ *num)
-void swj_copy(cudaStream_t st, int n, const double *x, double *y);
-void swj_fill(cudaStream_t st, int n, double v, double *x);
-// out[0] = ||x||_2^2, out[1] = ||x||_inf (NaN if any entry is NaN/Inf)
-void swj_norms(cudaStream_t st, int n, const double *x, double *red, double *out);
-// out[r] = sum_i V[r*ld + i] w[i], r = 0..rows-1
-void swj_mdot(cudaStream_t st, int n, int rows, const double *V, size_t ld, const double *w,
-              double *red, double *out);
-// w -= sum_r coef[r] V[r*ld + :]
-void swj_mgemv_sub(cudaStream_t st, int n, int rows, const double *V, size_t ld,
-                   const double *coef, double *w);
-// x = sum_r coef_host[r] Z[r*ld + :]  (coefficients from host)
-void swj_combine(cudaStream_t st, int n, int rows, const double *Z, size_t ld,
-                 const double *coef_dev, double *x, int accumulate);
+// linalg.cu: batched vector operations on nb vectors of length n at stride ld
+// (one instance per grid row; act: per-instance flags or nullptr), with
+// per-instance scalars in device arrays at stride sstride.
+void swj_bcopy(cudaStream_t st, int nb, int n, const double *x, double *y, size_t ld, const int *act);
+void swj_bfill(cudaStream_t st, int nb, int n, double v, double *x, size_t ld, const int *act);
+// y = a x + y with a = a_scale * a_dev[inst * sstride] (a_dev may be null: a = a_scale)
+void swj_baxpy(cudaStream_t st, int nb, int n, const double *a_dev, size_t sstride, double a_scale,
+               const double *x, double *y, size_t ld, const int *act);
+// y = s x with s = s_scale * s_dev[inst * sstride] (or 1 / that if invert; s_dev null: s_scale)
+void swj_bscale(cudaStream_t st, int nb, int n, const double *s_dev, size_t sstride, double s_scale,
+                int invert, const double *x, double *y, size_t ld, const int *act);
+// out[inst*sstride + 0] = ||x||_2^2, [1] = ||x||_inf (NaN if any entry is NaN/Inf)
+void swj_bnorms(cudaStream_t st, int nb, int n, const double *x, size_t ld, double *red,
+                double *out, size_t sstride, const int *act);
+// out[inst*sstride + r] = <V_inst[r], w_inst>, r < rows; rows of V_inst at ld, V_inst at vstride
+void swj_bmdot(cudaStream_t st, int nb, int n, int rows, const double *V, size_t ld, size_t vstride,
+               const double *w, size_t wstride, double *red, double *out, size_t sstride, const int *act);
+// w_inst -= sum_r coef[inst*sstride + r] V_inst[r]
+void swj_bmgemv_sub(cudaStream_t st, int nb, int n, int rows, const double *V, size_t ld,
+                    size_t vstride, const double *coef, size_t sstride, double *w, size_t wstride,
+                    const int *act);
+// x_inst (+)= sum_r coef[inst*sstride + r] Z_inst[r]
+void swj_bcombine(cudaStream_t st, int nb, int n, int rows, const double *Z, size_t ld,
+                  size_t zstride, const double *coef, size_t sstride, double *x, size_t xstride,
+                  int accumulate, const int *act);
 // C(mxn) = alpha A(mxk) B(kxn) + beta C, row-major with leading dims; batched by pointer arrays
 void swj_dgemm_batched(cudaStream_t st, int m, int n, int k, double alpha,
                        const double *const *A, int lda, const double *const *B, int ldb,
                        double beta, double *const *C, int ldc, int batch);
 void swj_dgemm(cudaStream_t st, int m, int n, int k, double alpha, const double *A, int lda,
                const double *B, int ldb, double beta, double *C, int ldc);
-// in-place inverse of `count` n x n blocks (stride `stride` doubles) by Gauss-Jordan with
-// partial pivoting; info[b] = 0 or 1 + failing column.
-void swj_block_inverse(cudaStream_t st, int n, int count, double *blocks, size_t stride, int *info);
 
 // cluster.cu
+bool swj_gj_inplace(int n);
 int swj_gj_inverse_cluster(cudaStream_t st, int n, int count, double *work, size_t wstride,
                            double *out, size_t ostride, int *info);
-int swj_band_sweep_cluster(cudaStream_t st, int n1, int M, int h, const double *band,
-                           const double *W, double *y, double *z, double *x);
+// prepare = true: only settle the kernel's attributes (no launch); call it
+// once before any launch that may be captured into a graph
+int swj_band_sweep_cluster(cudaStream_t st, int nb, int n1, int M, int h, const double *band,
+                           size_t band_stride, const double *W, size_t w_stride, double *y,
+                           double *z, double *x, size_t vec_stride, const int *act,
+                           bool prepare = false);
 
 // precond.cu
 int swj_pc_setup(swj_ctx *c);
-int swj_pc_apply(swj_ctx *c, const double *b, double *r);
+int swj_pc_apply(swj_ctx *c, const double *b, double *r, const int *act);
 void swj_pc_free(swj_ctx *c);
 
 // solver.cu
-int swj_residual_impl(swj_ctx *c, const double *u, double *E, int precision);
+int swj_residual_impl(swj_ctx *c, const double *u, double *E, int precision, const int *act);
 int swj_jvp_impl(swj_ctx *c, const double *u, const double *Eu, const double *v, double *Jv,
-                 int precision, double h_fixed);
+                 int precision, double h_fixed, const int *act);
 int swj_solve_impl(swj_ctx *c, double *u, swj_stats *st);
+void swj_graphs_free(swj_ctx *c);
 
 // Running count of kernel launches issued by the library (all contexts;
 // not synchronised across host threads).

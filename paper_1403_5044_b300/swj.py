@@ -73,6 +73,10 @@ def lib():
         sig = {
             "swj_default_opts": (None, [P(Opts)]),
             "swj_create": (ctypes.c_int, [P(_vp), P(Mesh), ctypes.c_double, ctypes.c_double, P(Opts), _vp]),
+            "swj_batch_create": (ctypes.c_int, [P(_vp), P(Mesh), ctypes.c_int, P(ctypes.c_double),
+                                                 P(ctypes.c_double), P(Opts), _vp]),
+            "swj_batch_count": (ctypes.c_int, [_vp]),
+            "swj_batch_set_params": (ctypes.c_int, [_vp, P(ctypes.c_double), P(ctypes.c_double)]),
             "swj_destroy": (None, [_vp]),
             "swj_set_params": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double]),
             "swj_set_opts": (ctypes.c_int, [_vp, P(Opts)]),
@@ -82,7 +86,7 @@ def lib():
             "swj_jvp": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_int]),
             "swj_precond_setup": (ctypes.c_int, [_vp]),
             "swj_precond_apply": (ctypes.c_int, [_vp, _vp, _vp]),
-            "swj_solve": (ctypes.c_int, [_vp, _vp, P(Stats)]),
+            "swj_solve": (ctypes.c_int, [_vp, _vp, _vp]),
             "swj_unpack": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
             "swj_surface": (ctypes.c_int, [_vp, _vp, _vp]),
             "swj_sync": (ctypes.c_int, [_vp]),
@@ -222,7 +226,7 @@ class Context:
 
     def solve(self, u, check=True):
         st = Stats()
-        rc = lib().swj_solve(self._h, _ptr(u), ctypes.byref(st))
+        rc = lib().swj_solve(self._h, _ptr(u), ctypes.cast(ctypes.byref(st), _vp))
         if check:
             _check(rc, "swj_solve")
         d = st.as_dict()
@@ -251,3 +255,61 @@ class Context:
         _check(lib().swj_pair_timing(self._h, int(precision), ctypes.byref(ms), ctypes.byref(n)),
                "swj_pair_timing")
         return ms.value, n.value
+
+
+class BatchContext(Context):
+    """`count` instances on one mesh, instance i with (F[i], eps[i]); mirrors
+    swj_batch_create.  Vectors hold the instances back to back: a vector()
+    is count * n_unknowns doubles, and `view(x)` shows it as [count, n]."""
+
+    def __init__(self, N, M, x1, dx, dy, F, eps, n_rad=0.05, opts: Opts | None = None, stream=None, **kw):
+        import torch
+        F = [float(f) for f in F]
+        eps = [float(e) for e in eps]
+        if len(F) != len(eps) or not F:
+            raise ValueError("F and eps must be non-empty and of equal length")
+        self.mesh = Mesh(int(N), int(M), float(x1), float(dx), float(dy), float(n_rad))
+        self.opts = opts if opts is not None else default_opts(**kw)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        handle = getattr(stream, "cuda_stream", stream)
+        self.count = len(F)
+        Fa = (ctypes.c_double * self.count)(*F)
+        ea = (ctypes.c_double * self.count)(*eps)
+        self._h = _vp()
+        _check(lib().swj_batch_create(ctypes.byref(self._h), ctypes.byref(self.mesh), self.count, Fa, ea,
+                                      ctypes.byref(self.opts), _vp(handle)), "swj_batch_create")
+        self.N, self.M, self.F, self.eps = int(N), int(M), F, eps
+        self.n_unknowns = 2 * (self.N + 1) * self.M
+
+    @classmethod
+    def from_spec(cls, spec, F, eps, **kw):
+        return cls(spec.N, spec.M, spec.x1, spec.dx, spec.dy, F, eps, n_rad=spec.n_rad, **kw)
+
+    def vector(self):
+        import torch
+        return torch.empty(self.count * self.n_unknowns, dtype=torch.float64, device="cuda")
+
+    def view(self, x):
+        return x.view(self.count, -1)
+
+    def set_params(self, F, eps):
+        F = [float(f) for f in F]
+        eps = [float(e) for e in eps]
+        _check(lib().swj_batch_set_params(self._h, (ctypes.c_double * self.count)(*F),
+                                          (ctypes.c_double * self.count)(*eps)), "swj_batch_set_params")
+        self.F, self.eps = F, eps
+
+    def solve(self, u, check=True):
+        """Solve every instance; returns (rc, [stats dict per instance])."""
+        st = (Stats * self.count)()
+        rc = lib().swj_solve(self._h, _ptr(u), ctypes.cast(st, _vp))
+        if check:
+            _check(rc, "swj_solve")
+        out = []
+        for i in range(self.count):
+            d = st[i].as_dict()
+            d["rc"] = st[i].status
+            out.append(d)
+        return rc, out
