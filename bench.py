@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--block-bw", type=int, default=BLOCK_BW)
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--batch-steps", type=int, default=2,
+                    help="timed steps of the 64 x 121x41 batched workload (0 = skip it)")
     ap.add_argument("--precond-only", action="store_true",
                     help="build the preconditioner, apply it 10 times and solve once "
                          "(a small, fixed launch sequence for profilers)")
@@ -266,6 +268,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         e2e_ms.append(a.elapsed_time(b))
 
+    batch = run_batch(args, stream, flush) if args.batch_steps > 0 else None
+
     if rank != 0:
         return
     n_solves = world * args.steps
@@ -321,10 +325,63 @@ def run_ours(args):
                 "unit": "solves/s", "h2d_bytes_per_step": ctx.n_unknowns * 8,
                 "d2h_bytes_per_step": spec.N * spec.M * 8},
         "gpu_launches": int(launches),
+        "batch": batch,
         "clocks": {"sm_mhz": cs["sm_mhz"], "sm_max_mhz": cs["sm_max_mhz"], "reasons": cs["reasons"]},
         "wall_s_timed": wall,
     }
     print(json.dumps(out), flush=True)
+
+
+def run_batch(args, stream, flush):
+    """The batched workload: 64 instances of 121x41 (x in [-16, 20], y in [0, 12],
+    dx = dy = 0.3), F ~ U[0.5, 1], eps ~ U[0.05, 0.6] from seed 1403_5044.  One
+    step solves the whole batch from the flat guess (preconditioner set-up
+    included), mixed precision; the FP64 batch is timed beside it and every
+    instance's surface is compared with its FP64 one."""
+    import numpy as np
+    import torch
+    from paper_1403_5044_b300 import swj
+    from paper_1403_5044_b300 import workloads as W
+    spec = W.MESH_121x41
+    params = W.batch_params()
+    F = [p[0] for p in params]
+    eps = [p[1] for p in params]
+    out = {"workload": "64 x 121x41, F ~ U[0.5,1], eps ~ U[0.05,0.6] (seed 1403_5044), block_bw 15",
+           "instances": len(F)}
+    zeta = {}
+    for mode, steps in (("mixed", args.batch_steps), ("fp64", 1)):
+        ctx = swj.BatchContext.from_spec(spec, F, eps, solve_mode=mode, block_bw=BLOCK_BW, stream=stream)
+        u = ctx.vector()
+
+        def once():
+            ctx.initial_guess_flat(u)
+            ctx.precond_setup()
+            return ctx.solve(u, check=False)
+        once()                          # warm-up: captures the Arnoldi graphs
+        ctx.sync()
+        ms = []
+        for k in range(steps):
+            flush.fill_(float(k))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            rc, st = once()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        z = torch.empty(ctx.count * spec.N * spec.M, dtype=torch.float64, device="cuda")
+        ctx.unpack(u, z, None)
+        ctx.sync()
+        zeta[mode] = z.view(ctx.count, -1).cpu().numpy()
+        conv = sum(1 for s in st if s["status"] == swj.OK)
+        res = [s["residual_evals"] for s in st]
+        out[mode] = {"solves_per_s": len(F) * 1e3 / (sum(ms) / len(ms)), "ms_per_batch": sum(ms) / len(ms),
+                     "steps": steps, "converged": conv, "rc": rc,
+                     "residual_evals_max": max(res), "residual_evals_mean": sum(res) / len(res),
+                     "effective_pairs_per_s": sum(res) * spec.pairs / (sum(ms) / len(ms) / 1e3)}
+        ctx.close()
+    out["max_abs_dzeta_mixed_vs_fp64"] = float(np.abs(zeta["mixed"] - zeta["fp64"]).max())
+    out["speedup_mixed_vs_fp64"] = out["mixed"]["solves_per_s"] / out["fp64"]["solves_per_s"]
+    return out
 
 
 def run_residual_only(args):
