@@ -158,8 +158,15 @@ int swj_set_params(swj_ctx *ctx, double F, double eps);
  * invalidates the preconditioner. */
 int swj_set_opts(swj_ctx *ctx, const swj_opts *opts);
 
-/* Bytes of device workspace the context holds. */
+/* Bytes of device workspace the context holds (its buffers and, once built,
+ * the preconditioner's). */
 size_t swj_workspace_bytes(const swj_ctx *ctx);
+
+/* Device bytes a context of `count` instances of `mesh` with `opts` (NULL =
+ * defaults) holds after its preconditioner is built, i.e. what
+ * swj_workspace_bytes reports for it then (allocator rounding not included).
+ * Uses the current device's SM count.  0 for an invalid mesh or option. */
+size_t swj_footprint_bytes(const swj_mesh *mesh, int count, const swj_opts *opts);
 
 /* u_dev <- the flat-surface initial guess of Section 4.1: phi_{1,l} = x1,
  * (phi_x)_{k,l} = 1, zeta_{1,l} = 0, (zeta_x)_{k,l} = 0.  Async. */
@@ -213,6 +220,71 @@ int swj_unpack(swj_ctx *ctx, const double *u_dev, double *zeta_dev, double *phi_
  * closed-form integral of S2, Eq. IS2), all FP64.  out_dev must hold
  * 4NM + 5(N-1)M doubles.  Async. */
 int swj_surface(swj_ctx *ctx, const double *u_dev, double *out_dev);
+
+/* ---- serving: a request loop over concurrent solves ----
+ * A server owns worker threads, one CUDA stream per running group, and the
+ * contexts it creates, all on the device current at swj_server_create.
+ * Requests (mesh, F, eps; flat initial guess, the server's swj_opts) queue
+ * in FIFO order.  A request is admitted when one of max_active worker slots
+ * is free and the footprint of its context (swj_footprint_bytes) fits the
+ * memory budget; later queued requests on the same mesh are admitted with it
+ * as one batch context (a power of two of them, at most max_group).  Groups
+ * on different streams run concurrently on the device; each finished group
+ * frees its slot for the next admission at once.  Finished contexts are kept
+ * for reuse by later groups of the same mesh and size when keep_contexts is
+ * set (evicted least recently used when memory is needed).  A result is the
+ * same whether its request ran alone or in a group.  All server entry points
+ * are thread-safe. */
+typedef struct swj_server swj_server;
+
+typedef struct {
+    size_t   hbm_budget_bytes; /* device bytes for contexts (0: 80% of free memory)   */
+    int      max_active;       /* groups running at once, 1..256 (default 4)          */
+    int      max_group;        /* requests per batch context, 1..1024 (default 8)     */
+    int      keep_contexts;    /* reuse finished contexts (default 1)                 */
+    swj_opts opts;             /* solve options of every request                      */
+} swj_server_opts;
+
+typedef struct {
+    long long submitted, completed, failed;
+    int       queued, active, peak_active;
+    size_t    bytes_held, peak_bytes_held, budget_bytes;
+    long long contexts_created, contexts_reused, contexts_evicted;
+} swj_server_info;
+
+typedef struct {
+    double queue_ms;     /* submit -> admission                      */
+    double run_ms;       /* admission -> result copied to the host   */
+    double latency_ms;   /* submit -> result copied to the host      */
+    int    group_size;   /* requests in the batch context it ran in  */
+} swj_request_times;
+
+void swj_server_default_opts(swj_server_opts *opts);
+
+/* Start a server (threads and budget; no context is created yet).  opts may
+ * be NULL.  SWJ_EINVAL for bad options. */
+int swj_server_create(swj_server **srv, const swj_server_opts *opts);
+
+/* Queue one solve; *id receives its handle.  SWJ_ENOMEM if its context could
+ * never fit the budget, SWJ_EINVAL for a bad mesh or parameter. */
+int swj_server_submit(swj_server *srv, const swj_mesh *mesh, double F, double eps, long long *id);
+
+/* SWJ_PENDING while request `id` runs or waits (wait = 0); with wait = 1
+ * block until it is done.  When done: fill stats, zeta_host (N*M doubles,
+ * [M][N] as swj_unpack), times (each may be NULL), forget the request and
+ * return its status (SWJ_OK or the solver's error).  SWJ_EINVAL for an
+ * unknown or already collected id. */
+int swj_server_poll(swj_server *srv, long long id, int wait, swj_stats *stats,
+                    double *zeta_host, swj_request_times *times);
+
+/* Counters and memory of the server. */
+int swj_server_get_info(swj_server *srv, swj_server_info *info);
+
+/* Block until no request is queued or running. */
+int swj_server_drain(swj_server *srv);
+
+/* Drop queued requests, wait for running groups, free everything. */
+void swj_server_destroy(swj_server *srv);
 
 /* Block until the context's stream is idle; returns SWJ_ECUDA if a kernel
  * failed. */

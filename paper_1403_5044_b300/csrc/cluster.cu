@@ -7,6 +7,7 @@
 // row) through distributed shared memory, with the hardware cluster barrier
 // as the only synchronisation.  No kernel here spins on a flag.
 #include "swj_internal.h"
+#include <mutex>
 #include <cooperative_groups.h>
 
 namespace cg = cooperative_groups;
@@ -423,30 +424,46 @@ size_t gj_smem_bytes(int n, int cs)
     return (size_t)(2 * n + w + (size_t)n * w) * sizeof(double) + (size_t)(2 * n + 4) * sizeof(int);
 }
 
+// Lazily settled launch attributes, shared by every context and host thread.
+static std::mutex g_attr_mutex;
 static int g_cs_smem = 0;
 
 // true when the shared-memory Gauss-Jordan variant applies to n x n blocks
 // (then input and output may be the same block)
+static int gj_smem_cluster()
+{
+    std::lock_guard<std::mutex> lock(g_attr_mutex);
+    if (!g_cs_smem) g_cs_smem = cluster_ctas((const void *)k_gj_cluster_smem, kGJThreads, 64 * 1024);
+    return g_cs_smem;
+}
+
 bool swj_gj_inplace(int n)
 {
-    if (!g_cs_smem) g_cs_smem = cluster_ctas((const void *)k_gj_cluster_smem, kGJThreads, 64 * 1024);
-    return gj_smem_bytes(n, g_cs_smem) <= 200 * 1024;
+    return gj_smem_bytes(n, gj_smem_cluster()) <= 200 * 1024;
 }
 
 int swj_gj_inverse_cluster(cudaStream_t st, int n, int count, double *work, size_t wstride,
                            double *out, size_t ostride, int *info)
 {
     static int cs_g = 0;
+    static size_t set_s = 48 * 1024, set_g = 48 * 1024;
     const bool use_smem = swj_gj_inplace(n);
-    const int cs_s = g_cs_smem;
-    if (!use_smem && !cs_g) cs_g = cluster_ctas((const void *)k_gj_cluster, kGJThreads, 64 * 1024);
-    const int cs = use_smem ? cs_s : cs_g;
-    const int w = (n + cs - 1) / cs;
-    size_t smem = use_smem ? gj_smem_bytes(n, cs)
-                           : (size_t)(2 * n + w) * sizeof(double) + (size_t)(2 * n + 4) * sizeof(int);
     const void *kern = use_smem ? (const void *)k_gj_cluster_smem : (const void *)k_gj_cluster;
-    if (smem > 48 * 1024)
-        SWJ_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int cs;
+    size_t smem;
+    {
+        std::lock_guard<std::mutex> lock(g_attr_mutex);
+        if (!use_smem && !cs_g) cs_g = cluster_ctas((const void *)k_gj_cluster, kGJThreads, 64 * 1024);
+        cs = use_smem ? g_cs_smem : cs_g;
+        const int w = (n + cs - 1) / cs;
+        smem = use_smem ? gj_smem_bytes(n, cs)
+                        : (size_t)(2 * n + w) * sizeof(double) + (size_t)(2 * n + 4) * sizeof(int);
+        size_t &set = use_smem ? set_s : set_g;
+        if (smem > set) {
+            SWJ_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            set = smem;
+        }
+    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cs * count);
     cfg.blockDim = dim3(kGJThreads);
@@ -478,12 +495,16 @@ int launch_sweep(cudaStream_t st, int nb, int n1, int M, int h, const double *ba
 {
     static int cs_cached = 0;
     static size_t smem_set = 48 * 1024;
-    if (!cs_cached) cs_cached = cluster_ctas((const void *)k_band_sweep<KC>, kSweepThreads, 64 * 1024);
-    const int cs = cs_cached;
-    size_t smem = (size_t)(h > 0 ? h : 1) * n1 * sizeof(double);
-    if (smem > smem_set) {
-        SWJ_CUDA_TRY(cudaFuncSetAttribute(k_band_sweep<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        smem_set = smem;
+    const size_t smem = (size_t)(h > 0 ? h : 1) * n1 * sizeof(double);
+    int cs;
+    {
+        std::lock_guard<std::mutex> lock(g_attr_mutex);
+        if (!cs_cached) cs_cached = cluster_ctas((const void *)k_band_sweep<KC>, kSweepThreads, 64 * 1024);
+        cs = cs_cached;
+        if (smem > smem_set) {
+            SWJ_CUDA_TRY(cudaFuncSetAttribute(k_band_sweep<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            smem_set = smem;
+        }
     }
     if (prepare) return SWJ_OK;
     cudaLaunchConfig_t cfg = {};

@@ -323,20 +323,61 @@ void free_pc(swj_ctx *c)
     c->pc_ptrs = nullptr;
     c->pc_ptrs_cap = 0;
     c->pc_ready = 0;
+    c->bytes -= c->pc_bytes;
+    c->pc_bytes = 0;
+}
+
+// block half bandwidth of the option block_bw (0 = the whole matrix)
+int half_band(int block_bw, int M)
+{
+    int h = (block_bw == 0) ? M - 1 : (block_bw - 1) / 2;
+    return h > M - 1 ? M - 1 : h;
+}
+
+// doubles of each preconditioner buffer, in the order of free_pc's list
+void pc_sizes(int n1, int M, int T, int H, int nb, int h, bool gj_inplace, size_t sz[15])
+{
+    const size_t n2 = (size_t)n1 * n1;
+    const size_t work_blocks = gj_inplace ? 1 : (size_t)nb * (h == 0 ? M : 1);
+    const size_t v[15] = {n2, n2, n2, n2, n2, n2, n2, (size_t)nb,
+                          (size_t)nb * M * (2 * h + 1) * n2, (size_t)nb * M * (h > 0 ? h : 1) * n2,
+                          (size_t)T, (size_t)nb * H, (size_t)nb * H, (size_t)nb * H, work_blocks * n2};
+    for (int i = 0; i < 15; ++i) sz[i] = v[i];
+}
+
+// block products of the band LU (pointer triples of the batched GEMMs)
+size_t pc_gemm_count(int M, int nb, int h)
+{
+    if (h == 0) return 0;
+    size_t np = 0;
+    for (int i = 0; i < M; ++i) {
+        size_t k = (size_t)(i + h < M - 1 ? h : M - 1 - i);
+        np += (size_t)nb * (k + k * k);
+    }
+    return np;
 }
 
 }  // namespace
 
 void swj_pc_free(swj_ctx *c) { free_pc(c); }
 
+size_t swj_pc_bytes(int N, int M, int nb, int block_bw)
+{
+    const int n1 = N + 1, h = half_band(block_bw, M);
+    size_t sz[15], tot = 0;
+    pc_sizes(n1, M, (N - 1) * M, n1 * M, nb, h, swj_gj_inplace(n1), sz);
+    for (size_t v : sz) tot += v * sizeof(double);
+    tot += (size_t)nb * M * sizeof(int);
+    tot += 3 * pc_gemm_count(M, nb, h) * sizeof(double *);
+    return tot;
+}
+
 int swj_pc_setup(swj_ctx *c)
 {
     const int N = c->N, M = c->M, n1 = c->n1, nb = c->nb;
     const swj_mesh &m = c->mesh;
     cudaStream_t st = c->stream;
-    int b = c->opts.block_bw;
-    int h = (b == 0) ? M - 1 : (b - 1) / 2;
-    if (h > M - 1) h = M - 1;
+    const int h = half_band(c->opts.block_bw, M);
     // the band sweep stages h vectors of n1 doubles in shared memory
     if ((size_t)(h + 1) * n1 * sizeof(double) > 200 * 1024) return SWJ_EINVAL;
     const size_t n2 = (size_t)n1 * n1;
@@ -346,23 +387,25 @@ int swj_pc_setup(swj_ctx *c)
         free_pc(c);
         c->pc_h = h;
         c->pc_nb = nbs;
-        size_t work_blocks = gj_inplace ? 1 : (size_t)nb * (h == 0 ? M : 1);
-        size_t sz[] = {n2, n2, n2, n2, n2, n2, n2, (size_t)nb,
-                       (size_t)nb * M * nbs * n2, (size_t)nb * M * (h > 0 ? h : 1) * n2,
-                       (size_t)c->T, (size_t)nb * c->H, (size_t)nb * c->H, (size_t)nb * c->H,
-                       work_blocks * n2};
+        size_t sz[15];
+        pc_sizes(n1, M, c->T, c->H, nb, h, gj_inplace, sz);
         double **bufs[] = {&c->pc_Ainv, &c->pc_AinvB1, &c->pc_CAinv, &c->pc_G1, &c->pc_A,
                            &c->pc_B1, &c->pc_C, &c->pc_invF2, &c->pc_band, &c->pc_W,
                            &c->pc_sumK3, &c->pc_t1, &c->pc_t2, &c->pc_z, &c->pc_work};
-        for (int i = 0; i < 15; ++i)
+        for (int i = 0; i < 15; ++i) {
             if (cudaMalloc(bufs[i], sz[i] * sizeof(double)) != cudaSuccess) {
                 free_pc(c);
                 return SWJ_ENOMEM;
             }
+            c->pc_bytes += sz[i] * sizeof(double);
+            c->bytes += sz[i] * sizeof(double);
+        }
         if (cudaMalloc(&c->pc_info, (size_t)nb * M * sizeof(int)) != cudaSuccess) {
             free_pc(c);
             return SWJ_ENOMEM;
         }
+        c->pc_bytes += (size_t)nb * M * sizeof(int);
+        c->bytes += (size_t)nb * M * sizeof(int);
     }
     c->pc_ready = 0;
     std::vector<double> invF2(nb);
@@ -453,13 +496,19 @@ int swj_pc_setup(swj_ctx *c)
         }
         int np = (int)PA.size();
         if (c->pc_ptrs_cap < np) {
-            if (c->pc_ptrs) cudaFree(c->pc_ptrs);
+            if (c->pc_ptrs) {
+                cudaFree(c->pc_ptrs);
+                c->pc_bytes -= (size_t)3 * c->pc_ptrs_cap * sizeof(double *);
+                c->bytes -= (size_t)3 * c->pc_ptrs_cap * sizeof(double *);
+            }
             c->pc_ptrs = nullptr;
             if (cudaMalloc(&c->pc_ptrs, (size_t)3 * np * sizeof(double *)) != cudaSuccess) {
                 c->pc_ptrs_cap = 0;
                 return SWJ_ENOMEM;
             }
             c->pc_ptrs_cap = np;
+            c->pc_bytes += (size_t)3 * np * sizeof(double *);
+            c->bytes += (size_t)3 * np * sizeof(double *);
         }
         std::vector<double *> all((size_t)3 * np);
         for (int q = 0; q < np; ++q) {

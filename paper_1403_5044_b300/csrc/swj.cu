@@ -5,7 +5,7 @@
 #include <stdlib.h>
 #include <string.h>
 
-unsigned long long g_swj_launches = 0;
+std::atomic<unsigned long long> g_swj_launches{0};
 
 namespace {
 
@@ -124,6 +124,31 @@ int alloc_all(swj_ctx *c)
     if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess)
         return SWJ_ECUDA;
     c->graphs_enabled = 1;
+    return SWJ_OK;
+}
+
+// device bytes alloc_all() requests for nb instances (plan from the current device)
+int ctx_bytes(const swj_mesh *mesh, int nb, int kry_m, size_t *out)
+{
+    swj_ctx c;
+    memset((void *)&c, 0, sizeof(c));
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return SWJ_ECUDA;
+    c.N = mesh->N;
+    c.M = mesh->M;
+    c.T = (c.N - 1) * c.M;
+    c.S = c.N * c.M;
+    c.nu = 2 * (c.N + 1) * c.M;
+    const size_t S = c.S, T = c.T, M = c.M, nu = c.nu, n = nb, d = sizeof(double);
+    PairPlan p64 = swj_pair_plan(&c, SWJ_FP64), p32 = swj_pair_plan(&c, SWJ_FP32);
+    const size_t P = (size_t)(p64.P > p32.P ? p64.P : p32.P);
+    size_t b = 4 * n * S * d + 3 * M * d + 2 * n * T * d + n * S * sizeof(SrcRec64) +
+               n * S * sizeof(SrcRec32) + 8 * n * T * d + 8 * n * T * sizeof(float) + 2 * n * d +
+               n * sizeof(int) + P * T * n * d + 8 * n * nu * d + n * SWJ_DS * d + n * SWJ_RED * d +
+               n * (size_t)(2 * kry_m + 1) * nu * d;
+    *out = b;
     return SWJ_OK;
 }
 
@@ -282,6 +307,16 @@ int swj_set_opts(swj_ctx *c, const swj_opts *o)
 
 size_t swj_workspace_bytes(const swj_ctx *c) { return c ? c->bytes : 0; }
 
+size_t swj_footprint_bytes(const swj_mesh *mesh, int count, const swj_opts *opts)
+{
+    swj_opts o;
+    if (opts) o = *opts; else swj_default_opts(&o);
+    if (!valid_mesh(mesh) || count < 1 || !valid_opts(&o)) return 0;
+    size_t b = 0;
+    if (ctx_bytes(mesh, count, o.gmres_restart, &b) != SWJ_OK) return 0;
+    return b + swj_pc_bytes(mesh->N, mesh->M, count, o.block_bw);
+}
+
 int swj_initial_guess_flat(swj_ctx *c, double *u)
 {
     if (!c || !u) return SWJ_EINVAL;
@@ -377,7 +412,7 @@ const char *swj_strerror(int s)
 
 const char *swj_version(void) { return SWJ_VERSION_STRING; }
 
-unsigned long long swj_kernel_launches(void) { return g_swj_launches; }
+unsigned long long swj_kernel_launches(void) { return g_swj_launches.load(); }
 
 int swj_set_kernel_timing(swj_ctx *c, int enable)
 {

@@ -11,6 +11,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <atomic>
 #include <stdint.h>
 #include <stddef.h>
 #include "../../include/swj.h"
@@ -122,7 +123,8 @@ struct swj_ctx {
     double *pc_t1, *pc_t2, *pc_z;   // apply temporaries [nb][H]
     double *pc_work;             // Gauss-Jordan work copies [nb][(h == 0 ? M : 1)][n1][n1]
 
-    size_t bytes;                // device bytes held
+    size_t pc_bytes;             // device bytes of the preconditioner buffers
+    size_t bytes;                // device bytes held (workspace + preconditioner)
     cudaEvent_t ev0, ev1;
     // optional timing of every all-pairs launch (events on the context's stream)
     int time_pairs;
@@ -194,6 +196,8 @@ int swj_band_sweep_cluster(cudaStream_t st, int nb, int n1, int M, int h, const 
 int swj_pc_setup(swj_ctx *c);
 int swj_pc_apply(swj_ctx *c, const double *b, double *r, const int *act);
 void swj_pc_free(swj_ctx *c);
+// device bytes the preconditioner of an nb-instance context holds after set-up
+size_t swj_pc_bytes(int N, int M, int nb, int block_bw);
 
 // solver.cu
 int swj_residual_impl(swj_ctx *c, const double *u, double *E, int precision, const int *act);
@@ -202,10 +206,10 @@ int swj_jvp_impl(swj_ctx *c, const double *u, const double *Eu, const double *v,
 int swj_solve_impl(swj_ctx *c, double *u, swj_stats *st);
 void swj_graphs_free(swj_ctx *c);
 
-// Running count of kernel launches issued by the library (all contexts;
-// not synchronised across host threads).
-extern unsigned long long g_swj_launches;
-#define SWJ_COUNT_LAUNCH() (++g_swj_launches)
+// Running count of kernel launches issued by the library (all contexts and
+// host threads).
+extern std::atomic<unsigned long long> g_swj_launches;
+#define SWJ_COUNT_LAUNCH() (g_swj_launches.fetch_add(1, std::memory_order_relaxed))
 
 #define SWJ_MAX_TIMED 2048   // pair-kernel launches whose duration can be recorded
 

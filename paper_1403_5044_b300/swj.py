@@ -43,6 +43,28 @@ class Opts(ctypes.Structure):
                 ("verbose", ctypes.c_int)]
 
 
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_active", ctypes.c_int),
+                ("max_group", ctypes.c_int), ("keep_contexts", ctypes.c_int), ("opts", Opts)]
+
+
+class ServerInfo(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong),
+                ("failed", ctypes.c_longlong), ("queued", ctypes.c_int), ("active", ctypes.c_int),
+                ("peak_active", ctypes.c_int), ("bytes_held", ctypes.c_size_t),
+                ("peak_bytes_held", ctypes.c_size_t), ("budget_bytes", ctypes.c_size_t),
+                ("contexts_created", ctypes.c_longlong), ("contexts_reused", ctypes.c_longlong),
+                ("contexts_evicted", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class RequestTimes(ctypes.Structure):
+    _fields_ = [("queue_ms", ctypes.c_double), ("run_ms", ctypes.c_double),
+                ("latency_ms", ctypes.c_double), ("group_size", ctypes.c_int)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("newton_iters", ctypes.c_int),
                 ("refine_iters", ctypes.c_int), ("residual_evals", ctypes.c_int),
@@ -78,6 +100,16 @@ def lib():
             "swj_batch_count": (ctypes.c_int, [_vp]),
             "swj_batch_set_params": (ctypes.c_int, [_vp, P(ctypes.c_double), P(ctypes.c_double)]),
             "swj_destroy": (None, [_vp]),
+            "swj_footprint_bytes": (ctypes.c_size_t, [P(Mesh), ctypes.c_int, P(Opts)]),
+            "swj_server_default_opts": (None, [P(ServerOpts)]),
+            "swj_server_create": (ctypes.c_int, [P(_vp), P(ServerOpts)]),
+            "swj_server_submit": (ctypes.c_int, [_vp, P(Mesh), ctypes.c_double, ctypes.c_double,
+                                                 P(ctypes.c_longlong)]),
+            "swj_server_poll": (ctypes.c_int, [_vp, ctypes.c_longlong, ctypes.c_int, P(Stats), _vp,
+                                               P(RequestTimes)]),
+            "swj_server_get_info": (ctypes.c_int, [_vp, P(ServerInfo)]),
+            "swj_server_drain": (ctypes.c_int, [_vp]),
+            "swj_server_destroy": (None, [_vp]),
             "swj_set_params": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double]),
             "swj_set_opts": (ctypes.c_int, [_vp, P(Opts)]),
             "swj_workspace_bytes": (ctypes.c_size_t, [_vp]),
@@ -313,3 +345,80 @@ class BatchContext(Context):
             d["rc"] = st[i].status
             out.append(d)
         return rc, out
+
+
+def footprint_bytes(spec, count=1, opts: Opts | None = None, **kw):
+    """Device bytes a context of `count` instances of mesh `spec` holds once its
+    preconditioner is built (swj_footprint_bytes)."""
+    m = Mesh(spec.N, spec.M, spec.x1, spec.dx, spec.dy, spec.n_rad)
+    o = opts if opts is not None else default_opts(**kw)
+    return int(lib().swj_footprint_bytes(ctypes.byref(m), int(count), ctypes.byref(o)))
+
+
+class Server:
+    """The serving loop of swj_server_*: submit() queues a solve and returns
+    its id; poll(id, wait) returns None while it is pending, else a dict with
+    the status, solver counters, zeta ([M, N] numpy array) and times."""
+
+    def __init__(self, hbm_budget_bytes=0, max_active=4, max_group=8, keep_contexts=True,
+                 opts: Opts | None = None, **kw):
+        so = ServerOpts()
+        lib().swj_server_default_opts(ctypes.byref(so))
+        so.hbm_budget_bytes = int(hbm_budget_bytes)
+        so.max_active = int(max_active)
+        so.max_group = int(max_group)
+        so.keep_contexts = int(bool(keep_contexts))
+        so.opts = opts if opts is not None else default_opts(**kw)
+        self._h = _vp()
+        _check(lib().swj_server_create(ctypes.byref(self._h), ctypes.byref(so)), "swj_server_create")
+        self._shape = {}
+
+    def submit(self, spec, F, eps):
+        m = Mesh(spec.N, spec.M, spec.x1, spec.dx, spec.dy, spec.n_rad)
+        rid = ctypes.c_longlong()
+        _check(lib().swj_server_submit(self._h, ctypes.byref(m), float(F), float(eps), ctypes.byref(rid)),
+               "swj_server_submit")
+        self._shape[rid.value] = (spec.M, spec.N)
+        return rid.value
+
+    def poll(self, rid, wait=False):
+        import numpy as np
+        M, N = self._shape[rid]
+        z = np.empty((M, N), dtype=np.float64)
+        st, tm = Stats(), RequestTimes()
+        rc = lib().swj_server_poll(self._h, int(rid), int(bool(wait)), ctypes.byref(st),
+                                   z.ctypes.data_as(_vp), ctypes.byref(tm))
+        if rc == PENDING:
+            return None
+        del self._shape[rid]
+        if rc == EINVAL:
+            raise SwjError(rc, "swj_server_poll")
+        d = st.as_dict()
+        d.update(rc=rc, zeta=z, queue_ms=tm.queue_ms, run_ms=tm.run_ms, latency_ms=tm.latency_ms,
+                 group_size=tm.group_size)
+        return d
+
+    def info(self):
+        i = ServerInfo()
+        _check(lib().swj_server_get_info(self._h, ctypes.byref(i)), "swj_server_get_info")
+        return i.as_dict()
+
+    def drain(self):
+        _check(lib().swj_server_drain(self._h), "swj_server_drain")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().swj_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
