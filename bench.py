@@ -49,6 +49,12 @@ def parse():
     ap.add_argument("--block-bw", type=int, default=BLOCK_BW)
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--serve-requests", type=int, default=64,
+                    help="requests of the serving sample in the default run (0 = skip it)")
+    ap.add_argument("--serve", action="store_true",
+                    help="only the serving workload: 2000 Poisson requests per rate, rates swept over "
+                         "{0.25, 0.5, 0.75, 1.0, 1.25} x the measured saturated rate, mixed and FP64")
+    ap.add_argument("--serve-rates", default="0.25,0.5,0.75,1.0,1.25")
     ap.add_argument("--batch-steps", type=int, default=2,
                     help="timed steps of the 64 x 121x41 batched workload (0 = skip it)")
     ap.add_argument("--precond-only", action="store_true",
@@ -269,6 +275,9 @@ def run_ours(args):
         e2e_ms.append(a.elapsed_time(b))
 
     batch = run_batch(args, stream, flush) if args.batch_steps > 0 else None
+    serve = None
+    if args.serve_requests > 0 and rank == 0:
+        serve = {"mixed": serve_point("mixed", args.serve_requests, 1.0)}
 
     if rank != 0:
         return
@@ -326,6 +335,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": spec.N * spec.M * 8},
         "gpu_launches": int(launches),
         "batch": batch,
+        "serve": serve,
         "clocks": {"sm_mhz": cs["sm_mhz"], "sm_max_mhz": cs["sm_max_mhz"], "reasons": cs["reasons"]},
         "wall_s_timed": wall,
     }
@@ -384,19 +394,116 @@ def run_batch(args, stream, flush):
     return out
 
 
+SERVE_WORKLOAD = ("requests on meshes drawn uniformly from {61x21, 121x41, 181x61, 361x121} over "
+                  "x in [-16,20], y in [0,12]; F ~ U[0.5,1], eps ~ U[0.05,0.5]; Poisson arrivals (seed 1403_5045)")
+
+
+def serve_point(mode, count, rate_factor, sat=None):
+    """One point of the serving workload: measure the saturated rate (all
+    `count` requests submitted at once) unless given, then replay `count`
+    Poisson arrivals at rate_factor x that rate.  Latency is submit -> result
+    on the host, measured inside the server."""
+    import numpy as np
+    from paper_1403_5044_b300 import swj
+    from paper_1403_5044_b300 import workloads as W
+    reqs = W.serve_requests(count=count)
+    kw = dict(max_active=4, max_group=8, block_bw=BLOCK_BW, solve_mode=mode)
+    with swj.Server(**kw) as srv:
+        # warm-up: one request per mesh (creates the kept contexts' first graphs)
+        for m in W.SERVE_MESHES:
+            srv.poll(srv.submit(m, 0.75, 0.25), wait=True)
+        if sat is None:
+            t0 = time.perf_counter()
+            ids = [srv.submit(m, F, eps) for _, m, F, eps in reqs]
+            srv.drain()
+            sat = count / (time.perf_counter() - t0)
+            for i in ids:
+                srv.poll(i, wait=True)
+        rate = rate_factor * sat
+        arrivals = np.array([t for t, *_ in reqs])
+        arrivals = arrivals / arrivals[-1] * (count / rate)      # rescale the stream to `rate`
+        ids = []
+        t0 = time.perf_counter()
+        for (t, m, F, eps), ta in zip(reqs, arrivals):
+            dt = ta - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            ids.append(srv.submit(m, F, eps))
+        srv.drain()
+        span = time.perf_counter() - t0
+        res = [srv.poll(i, wait=True) for i in ids]
+        info = srv.info()
+    lat = np.array([r["latency_ms"] for r in res])
+    ok = sum(1 for r in res if r["rc"] == swj.OK)
+    by_mesh = {}
+    for (t, m, F, eps), r in zip(reqs, res):
+        by_mesh.setdefault("%dx%d" % (m.N, m.M), []).append(r["latency_ms"])
+    return {"requests": count, "rate_factor": rate_factor, "saturated_solves_per_s": sat,
+            "offered_solves_per_s": rate, "solves_per_s": count / span, "converged": ok,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "mean": float(lat.mean())},
+            "p50_ms_by_mesh": {k: float(np.median(v)) for k, v in sorted(by_mesh.items())},
+            "mean_group": float(np.mean([r["group_size"] for r in res])),
+            "peak_active": info["peak_active"], "peak_bytes_held": info["peak_bytes_held"],
+            "contexts_created": info["contexts_created"], "contexts_reused": info["contexts_reused"]}
+
+
+def run_serve(args):
+    import torch
+    torch.cuda.set_device(0)
+    rates = [float(r) for r in args.serve_rates.split(",")]
+    out = {"serve": True, "workload": SERVE_WORKLOAD, "points": {}}
+    for mode in ("mixed", "fp64"):
+        sat = None
+        pts = []
+        for f in rates:
+            p = serve_point(mode, args.serve_requests, f, sat)
+            sat = p["saturated_solves_per_s"]
+            pts.append(p)
+            print(json.dumps({"mode": mode, **p}), flush=True)
+        out["points"][mode] = pts
+    print(json.dumps(out), flush=True)
+
+
 def run_residual_only(args):
+    """Residuals of the 181x61 workload only: every compiled tile shape of the
+    all-pairs kernel pinned in turn, `steps` timed launches each (plus the
+    autotuner's choice), a short fixed launch sequence for profilers."""
     import torch
     from paper_1403_5044_b300 import swj
     from paper_1403_5044_b300 import workloads as W
     spec, F, eps = W.SOLVE_181x61
+    out = {"residual_only": True, "steps": args.steps, "workload": WORKLOAD, "pairs": spec.pairs, "shapes": []}
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    peak = sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     with swj.Context.from_spec(spec, F, eps) as ctx:
         u = torch.tensor(W.random_state(spec, seed=1, amp=0.05), device="cuda")
         E = ctx.vector()
-        for _ in range(args.steps):
-            ctx.residual(u, E, swj.FP32)
+        ctx.residual(u, E, swj.FP32)
         ctx.residual(u, E, swj.FP64)
         ctx.sync()
-    print(json.dumps({"residual_only": True, "steps": args.steps}))
+        out["tuned"] = {"fp32": ctx.pair_config(swj.FP32), "fp64": ctx.pair_config(swj.FP64)}
+        for prec in (swj.FP32, swj.FP64):
+            for v in range(swj.pair_variants(prec)):
+                ctx.set_pair_config(prec, v)
+                ctx.residual(u, E, prec)
+                ctx.sync()
+                ctx.set_kernel_timing(True)
+                ctx.reset_pair_timing()
+                for _ in range(args.steps if prec == swj.FP32 else max(1, args.steps // 10)):
+                    ctx.residual(u, E, prec)
+                ctx.sync()
+                ms, n = ctx.pair_timing(prec)
+                ctx.set_kernel_timing(False)
+                _, tpb, r, packed = ctx.pair_config(prec)
+                avg = ms / max(1, n)
+                row = {"precision": "fp32" if prec == swj.FP32 else "fp64", "variant": v, "threads": tpb,
+                       "targets_per_thread": r, "packed": packed, "avg_ms": avg,
+                       "pairs_per_s": spec.pairs / (avg * 1e-3)}
+                if prec == swj.FP32:
+                    row["frac_fp32_peak"] = FLOP_PER_PAIR * spec.pairs / (avg * 1e-3) / 1e12 / peak
+                out["shapes"].append(row)
+    print(json.dumps(out))
 
 
 def run_precond_only(args):
@@ -424,7 +531,11 @@ def run_precond_only(args):
 
 def main():
     args = parse()
-    if args.precond_only:
+    if args.serve:
+        if args.serve_requests == 64:
+            args.serve_requests = 2000
+        run_serve(args)
+    elif args.precond_only:
         run_precond_only(args)
     elif args.residual_only:
         run_residual_only(args)

@@ -90,6 +90,9 @@ typedef struct swj_opts {
     double refine_tol_inf; /* MIXED: the FP64 refinement stops at ||E_fp64||_inf      */
                            /* below this (1e-9)                                       */
     int    verbose;        /* 1: one line per Newton step on stderr (0)               */
+    int    autotune;       /* 1: on the first residual of a mesh size, time every     */
+                           /* compiled tile shape of the all-pairs kernel and keep    */
+                           /* the fastest for the process (1)                         */
 } swj_opts;
 
 /* Counters and timings of one solve (KINSOL-style counters). */
@@ -220,6 +223,25 @@ int swj_unpack(swj_ctx *ctx, const double *u_dev, double *zeta_dev, double *phi_
  * closed-form integral of S2, Eq. IS2), all FP64.  out_dev must hold
  * 4NM + 5(N-1)M doubles.  Async. */
 int swj_surface(swj_ctx *ctx, const double *u_dev, double *out_dev);
+
+/* ---- tile shapes of the all-pairs kernel ----
+ * Several tile shapes (threads per block, targets per thread, FP32 packed
+ * pair instructions or not) are compiled per precision; index 0 is the
+ * default.  With opts.autotune the first residual of each mesh size times
+ * them all and every context of that size in the process uses the fastest. */
+
+/* Number of compiled shapes for `precision`. */
+int swj_pair_variants(int precision);
+
+/* The shape the context uses for `precision`: its index, threads per block,
+ * targets per thread and whether it uses packed FP32 pair instructions (any
+ * pointer may be NULL). */
+int swj_pair_config(const swj_ctx *ctx, int precision, int *variant, int *threads,
+                    int *targets_per_thread, int *packed);
+
+/* Pin shape `variant` for `precision` on this context (synchronises its
+ * stream; drops captured graphs).  SWJ_EINVAL for an unknown index. */
+int swj_set_pair_config(swj_ctx *ctx, int precision, int variant);
 
 /* ---- serving: a request loop over concurrent solves ----
  * A server owns worker threads, one CUDA stream per running group, and the

@@ -33,9 +33,22 @@
 // FP64 (the parity path and the refinement residual): the same FP32 seed
 // refined by one Halley step; plain FP64 accumulation.
 //
+// FP32 packed variant: Blackwell's paired FP32 instructions (FFMA2, FADD2,
+// FMUL2) evaluate the same formulas for two targets per instruction, halving
+// the FP32 issue slots per pair; the four reciprocal square roots stay scalar
+// (MUFU), which then bounds the kernel.  Every operation and its rounding is
+// the one of the scalar kernel, so both give bitwise equal sums for the same
+// launch plan.
+//
 // Launch plan: the number of source chunks is chosen so that
-// (target tiles) x (chunks) fills whole waves of resident blocks.
+// (target tiles) x (chunks) fills whole waves of resident blocks.  Several
+// tile shapes (threads per block, targets per thread, packed or not) are
+// compiled; the first residual of a mesh size times each one and keeps the
+// fastest for every later launch in the process (the autotuner).
 #include "swj_internal.h"
+#include <map>
+#include <mutex>
+#include <tuple>
 
 namespace {
 
@@ -158,17 +171,132 @@ k_pairs_s(int T_, int S_, int chunk, const SrcRecS<T> *__restrict__ src, TgtArra
     }
 }
 
-constexpr int kTPB = 128;
-constexpr int kR = 4;
+
+// Source record of the packed kernel in shared memory: each field in both
+// halves of a float2 (a broadcast operand of the paired instructions), with
+// the negated copies the formulas need: my = -y, nzx = -zeta_x, nzy = -zeta_y.
+struct __align__(16) SrcX2 {
+    float2 x, y, my, z, nzx, zy, nzy, g, w, zxw;
+};
+
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 rsq2(float2 v) { return make_float2(rsqrt_ftz(v.x), rsqrt_ftz(v.y)); }
+
+// RP packed pairs of targets per thread (2 RP targets): target 2m + h of the
+// thread is tb + (2m + h) TPB, in lane h of pair m.  MINB = resident blocks per
+// SM asked of the register allocator.
+template <int RP, int TPB, int MINB>
+__global__ void __launch_bounds__(TPB, MINB)
+k_pairs_x2(int T_, int S_, int chunk, const SrcRec32 *__restrict__ src, TgtArrays32 tg,
+           double *__restrict__ partial, const int *__restrict__ act)
+{
+    constexpr int TILE = 256;
+    const int inst = blockIdx.z;
+    if (!SWJ_INST_ACTIVE(act, inst)) return;
+    {
+        const size_t ot = (size_t)inst * T_;
+        src += (size_t)inst * S_;
+        tg.x += ot; tg.y += ot; tg.zeta += ot; tg.g += ot; tg.zxw += ot; tg.A += ot; tg.B += ot; tg.C += ot;
+        partial += (size_t)inst * gridDim.y * T_;
+    }
+    __shared__ SrcX2 sh[TILE];
+    const int tid = threadIdx.x;
+    const int s0 = blockIdx.y * chunk;
+    const int s1 = min(S_, s0 + chunk);
+    float2 ntx[RP], nty[RP], ntz[RP], ntg[RP], ntzw[RP], A[RP], B[RP], C[RP], sum[RP], comp[RP];
+    const int tb = blockIdx.x * 2 * RP * TPB + tid;
+#pragma unroll
+    for (int m = 0; m < RP; ++m) {
+        const int ta = min(tb + 2 * m * TPB, T_ - 1), tc = min(tb + (2 * m + 1) * TPB, T_ - 1);
+        ntx[m] = make_float2(-tg.x[ta], -tg.x[tc]);
+        nty[m] = make_float2(-tg.y[ta], -tg.y[tc]);
+        ntz[m] = make_float2(-tg.zeta[ta], -tg.zeta[tc]);
+        ntg[m] = make_float2(-tg.g[ta], -tg.g[tc]);
+        ntzw[m] = make_float2(-tg.zxw[ta], -tg.zxw[tc]);
+        A[m] = make_float2(tg.A[ta], tg.A[tc]);
+        B[m] = make_float2(tg.B[ta], tg.B[tc]);
+        C[m] = make_float2(tg.C[ta], tg.C[tc]);
+        sum[m] = f2(0.f);
+        comp[m] = f2(0.f);
+    }
+    for (int base = s0; base < s1; base += TILE) {
+        const int nt = min(TILE, s1 - base);
+        __syncthreads();
+        for (int i = tid; i < nt; i += TPB) {
+            const SrcRec32 q = src[base + i];
+            SrcX2 r;
+            r.x = f2(q.x); r.y = f2(q.y); r.my = f2(-q.y); r.z = f2(q.zeta);
+            r.nzx = f2(-q.zx); r.zy = f2(q.zy); r.nzy = f2(-q.zy);
+            r.g = f2(q.g); r.w = f2(q.w); r.zxw = f2(q.zxw);
+            sh[i] = r;
+        }
+        __syncthreads();
+        for (int sb = 0; sb < nt; sb += kSub) {
+            const int se = min(sb + kSub, nt);
+            float2 loc[RP];
+#pragma unroll
+            for (int m = 0; m < RP; ++m) loc[m] = f2(0.f);
+#pragma unroll 1
+            for (int s = sb; s < se; ++s) {
+                const SrcX2 q = sh[s];
+#pragma unroll
+                for (int m = 0; m < RP; ++m) {
+                    const float2 p = __fadd2_rn(q.x, ntx[m]);
+                    const float2 qq = __fadd2_rn(q.y, nty[m]);
+                    const float2 mqp = __fadd2_rn(q.my, nty[m]);      // -(y + y*)
+                    const float2 dz = __fadd2_rn(q.z, ntz[m]);
+                    const float2 p2 = __fmul2_rn(p, p);
+                    const float2 bs = __ffma2_rn(dz, dz, p2);
+                    const float2 r1s = __ffma2_rn(qq, qq, bs);
+                    const float2 r2s = __ffma2_rn(mqp, mqp, bs);
+                    const float2 nc = __ffma2_rn(p, q.nzx, dz);
+                    const float2 n1 = __ffma2_rn(qq, q.nzy, nc);
+                    const float2 n2 = __ffma2_rn(mqp, q.zy, nc);
+                    const float2 i1 = rsq2(r1s), i2 = rsq2(r2s);
+                    const float2 i1c = __fmul2_rn(__fmul2_rn(i1, i1), i1);
+                    const float2 i2c = __fmul2_rn(__fmul2_rn(i2, i2), i2);
+                    const float2 K1 = __ffma2_rn(n1, i1c, __fmul2_rn(n2, i2c));
+                    const float2 K2 = __fadd2_rn(i1, i2);
+                    const float2 Ap2 = __fmul2_rn(A[m], p2);
+                    const float2 Bp = __fmul2_rn(B[m], p);
+                    const float2 Q1 = __ffma2_rn(__ffma2_rn(C[m], qq, Bp), qq, Ap2);
+                    const float2 Q2 = __ffma2_rn(__ffma2_rn(C[m], mqp, Bp), mqp, Ap2);
+                    const float2 S2 = __fadd2_rn(rsq2(Q1), rsq2(Q2));
+                    const float2 f = __fadd2_rn(q.g, ntg[m]);
+                    const float2 inner = __ffma2_rn(q.zxw, K2, __ffma2_rn(f, K1, __fmul2_rn(ntzw[m], S2)));
+                    loc[m] = __ffma2_rn(q.w, inner, loc[m]);
+                }
+            }
+#pragma unroll
+            for (int m = 0; m < RP; ++m) {
+                float y = loc[m].x - comp[m].x, t2 = sum[m].x + y;
+                comp[m].x = (t2 - sum[m].x) - y;
+                sum[m].x = t2;
+                y = loc[m].y - comp[m].y;
+                t2 = sum[m].y + y;
+                comp[m].y = (t2 - sum[m].y) - y;
+                sum[m].y = t2;
+            }
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < RP; ++m) {
+        const int ta = tb + 2 * m * TPB, tc = tb + (2 * m + 1) * TPB;
+        if (ta < T_) partial[(size_t)blockIdx.y * T_ + ta] = (double)sum[m].x - (double)comp[m].x;
+        if (tc < T_) partial[(size_t)blockIdx.y * T_ + tc] = (double)sum[m].y - (double)comp[m].y;
+    }
+}
+
 
 // Source-chunk count P for (tiles) target tiles: (tiles x P) blocks should fill
 // whole waves of `slots` resident blocks; chunks keep at least 64 sources.
-PairPlan make_plan(int T, int S, int slots)
+PairPlan make_plan(int T, int S, int slots, int tpb, int R, int v)
 {
     PairPlan p;
-    p.tpb = kTPB;
-    p.R = kR;
-    p.tiles = (T + kTPB * kR - 1) / (kTPB * kR);
+    p.tpb = tpb;
+    p.R = R;
+    p.v = v;
+    p.tiles = (T + tpb * R - 1) / (tpb * R);
     int maxP = S / 64 > 1 ? S / 64 : 1;
     if (maxP > 4096) maxP = 4096;
     int bestP = 1;
@@ -194,30 +322,170 @@ int resident_blocks(const void *kernel, int threads)
     return nb;
 }
 
+typedef void (*PairLaunch)(dim3, cudaStream_t, int, int, int, const void *, const void *, double *,
+                           const int *);
+
+struct PairVariant {
+    const void *kernel;
+    int tpb, R;
+    PairLaunch launch;
+};
+
+template <typename T, int R, int TPB> struct ScalarLaunch;
+template <typename T, int R> struct ScalarLaunch<T, R, 128> {
+    static void go(dim3 g, cudaStream_t st, int T_, int S_, int chunk, const void *src, const void *tg,
+                   double *partial, const int *act)
+    {
+        k_pairs_s<T, R><<<g, 128, 0, st>>>(T_, S_, chunk, (const SrcRecS<T> *)src,
+                                           *(const TgtArraysS<T> *)tg, partial, act);
+    }
+};
+
+template <int RP, int TPB, int MINB>
+void launch_x2(dim3 g, cudaStream_t st, int T_, int S_, int chunk, const void *src, const void *tg,
+               double *partial, const int *act)
+{
+    k_pairs_x2<RP, TPB, MINB><<<g, TPB, 0, st>>>(T_, S_, chunk, (const SrcRec32 *)src,
+                                          *(const TgtArrays32 *)tg, partial, act);
+}
+
+// Compiled tile shapes; index 0 of each table is the untuned default.
+const PairVariant kVar32[] = {
+    {(const void *)k_pairs_s<float, 4>, 128, 4, ScalarLaunch<float, 4, 128>::go},
+    {(const void *)k_pairs_x2<2, 128, 1>, 128, 4, launch_x2<2, 128, 1>},
+    {(const void *)k_pairs_x2<3, 128, 1>, 128, 6, launch_x2<3, 128, 1>},
+    {(const void *)k_pairs_x2<4, 128, 1>, 128, 8, launch_x2<4, 128, 1>},
+    {(const void *)k_pairs_x2<2, 256, 1>, 256, 4, launch_x2<2, 256, 1>},
+    {(const void *)k_pairs_x2<4, 64, 1>, 64, 8, launch_x2<4, 64, 1>},
+    {(const void *)k_pairs_x2<2, 256, 3>, 256, 4, launch_x2<2, 256, 3>},
+    {(const void *)k_pairs_x2<2, 128, 5>, 128, 4, launch_x2<2, 128, 5>},
+    {(const void *)k_pairs_x2<2, 128, 6>, 128, 4, launch_x2<2, 128, 6>},
+    {(const void *)k_pairs_x2<3, 256, 2>, 256, 6, launch_x2<3, 256, 2>},
+    {(const void *)k_pairs_x2<1, 256, 4>, 256, 2, launch_x2<1, 256, 4>},
+};
+const PairVariant kVar64[] = {
+    {(const void *)k_pairs_s<double, 4>, 128, 4, ScalarLaunch<double, 4, 128>::go},
+    {(const void *)k_pairs_s<double, 2>, 128, 2, ScalarLaunch<double, 2, 128>::go},
+    {(const void *)k_pairs_s<double, 8>, 128, 8, ScalarLaunch<double, 8, 128>::go},
+};
+constexpr int kNVar32 = sizeof(kVar32) / sizeof(kVar32[0]);
+constexpr int kNVar64 = sizeof(kVar64) / sizeof(kVar64[0]);
+
+const PairVariant &variant(int precision, int v)
+{
+    return precision == SWJ_FP64 ? kVar64[v] : kVar32[v];
+}
+
+int n_variants(int precision) { return precision == SWJ_FP64 ? kNVar64 : kNVar32; }
+
+// tuned variant per (T, S, precision, SM count), shared by every context
+std::mutex g_tune_mutex;
+std::map<std::tuple<int, int, int, int>, int> g_tuned;
+
+int tuned_variant(const swj_ctx *c, int precision)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tuned.find(std::make_tuple(c->T, c->S, precision, c->num_sms));
+    return it == g_tuned.end() ? -1 : it->second;
+}
+
 }  // namespace
+
+PairPlan swj_pair_plan_variant(const swj_ctx *c, int precision, int v)
+{
+    const PairVariant &pv = variant(precision, v);
+    int slots = c->num_sms * resident_blocks(pv.kernel, pv.tpb);
+    return make_plan(c->T, c->S, slots, pv.tpb, pv.R, v);
+}
 
 PairPlan swj_pair_plan(const swj_ctx *c, int precision)
 {
-    const void *k = (precision == SWJ_FP64) ? (const void *)k_pairs_s<double, kR>
-                                             : (const void *)k_pairs_s<float, kR>;
-    int slots = c->num_sms * resident_blocks(k, kTPB);
-    return make_plan(c->T, c->S, slots);
+    int v = tuned_variant(c, precision);
+    return swj_pair_plan_variant(c, precision, v < 0 ? 0 : v);
+}
+
+int swj_pair_max_chunks(const swj_ctx *c)
+{
+    int P = 1;
+    for (int prec = 0; prec < 2; ++prec)
+        for (int v = 0; v < n_variants(prec); ++v) {
+            PairPlan pl = swj_pair_plan_variant(c, prec, v);
+            if (pl.P > P) P = pl.P;
+        }
+    return P;
+}
+
+static void launch_plan(swj_ctx *c, const PairPlan &pl, int precision, const int *act)
+{
+    dim3 grid(pl.tiles, pl.P, c->nb);
+    SWJ_COUNT_LAUNCH();
+    if (precision == SWJ_FP64)
+        kVar64[pl.v].launch(grid, c->stream, c->T, c->S, pl.chunk, c->src64, &c->tgt64, c->partial, act);
+    else
+        kVar32[pl.v].launch(grid, c->stream, c->T, c->S, pl.chunk, c->src32, &c->tgt32, c->partial, act);
 }
 
 // One launch covers every instance (grid.z); each instance uses the chunking
 // of the single-instance plan, so its result does not depend on the batch.
-void swj_launch_pairs64(swj_ctx *c, const PairPlan &pl, const int *act)
+void swj_launch_pairs64(swj_ctx *c, const PairPlan &pl, const int *act) { launch_plan(c, pl, SWJ_FP64, act); }
+void swj_launch_pairs32(swj_ctx *c, const PairPlan &pl, const int *act) { launch_plan(c, pl, SWJ_FP32, act); }
+
+// Pick the context's plan for `precision`: the variant already tuned for this
+// mesh size, else (autotune on, stream not capturing) time every variant on
+// the current source/target records (one warm-up launch, then the mean of
+// three) and keep the fastest for the whole process.
+int swj_pair_autotune(swj_ctx *c, int precision, const int *act)
 {
-    dim3 grid(pl.tiles, pl.P, c->nb);
-    SWJ_COUNT_LAUNCH();
-    k_pairs_s<double, kR><<<grid, kTPB, 0, c->stream>>>(c->T, c->S, pl.chunk, c->src64, c->tgt64,
-                                                        c->partial, act);
+    int &done = precision == SWJ_FP64 ? c->tuned64 : c->tuned32;
+    if (done) return SWJ_OK;
+    PairPlan &plan = precision == SWJ_FP64 ? c->plan64 : c->plan32;
+    int v = tuned_variant(c, precision);
+    if (v < 0 && c->opts.autotune) {
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(c->stream, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
+            return SWJ_OK;   // untuned for now; tried again on a later residual
+        cudaEvent_t e0, e1;
+        SWJ_CUDA_TRY(cudaEventCreate(&e0));
+        SWJ_CUDA_TRY(cudaEventCreate(&e1));
+        float best = 0.f;
+        int bv = 0;
+        for (int k = 0; k < n_variants(precision); ++k) {
+            PairPlan pl = swj_pair_plan_variant(c, precision, k);
+            if ((size_t)pl.P * c->T * c->nb > c->partial_cap) continue;
+            launch_plan(c, pl, precision, act);
+            cudaEventRecord(e0, c->stream);
+            for (int rep = 0; rep < 3; ++rep) launch_plan(c, pl, precision, act);
+            cudaEventRecord(e1, c->stream);
+            float ms = 0.f;
+            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return SWJ_ECUDA;
+            }
+            if (k == 0 || ms < best) { best = ms; bv = k; }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto key = std::make_tuple(c->T, c->S, precision, c->num_sms);
+        auto it = g_tuned.find(key);
+        if (it == g_tuned.end()) g_tuned[key] = bv;   // first finished tuning wins
+        else bv = it->second;
+        v = bv;
+    }
+    if (v < 0) v = 0;
+    plan = swj_pair_plan_variant(c, precision, v);
+    done = 1;
+    return SWJ_OK;
 }
 
-void swj_launch_pairs32(swj_ctx *c, const PairPlan &pl, const int *act)
+int swj_pair_variant_info(int precision, int v, int *tpb, int *R, int *packed)
 {
-    dim3 grid(pl.tiles, pl.P, c->nb);
-    SWJ_COUNT_LAUNCH();
-    k_pairs_s<float, kR><<<grid, kTPB, 0, c->stream>>>(c->T, c->S, pl.chunk, c->src32, c->tgt32,
-                                                       c->partial, act);
+    if (precision != SWJ_FP64 && precision != SWJ_FP32) return SWJ_EINVAL;
+    if (v < 0 || v >= n_variants(precision)) return SWJ_EINVAL;
+    const PairVariant &pv = variant(precision, v);
+    if (tpb) *tpb = pv.tpb;
+    if (R) *R = pv.R;
+    if (packed) *packed = (precision == SWJ_FP32 && v > 0) ? 1 : 0;
+    return SWJ_OK;
 }

@@ -427,7 +427,9 @@ int swj_pc_setup(swj_ctx *c)
     // --- PreD diagonal correction: trapezoid sum of w K3 and I of the flat surface
     //     (instance 0's record buffers serve as scratch; every residual rewrites them)
     int prec = (c->opts.solve_mode == SWJ_SOLVE_FP64) ? SWJ_FP64 : SWJ_FP32;
-    PairPlan pl = swj_pair_plan(c, prec);
+    // the default tile shape, whatever the autotuner picked: the preconditioner of
+    // a mesh and F must not depend on when it was built
+    PairPlan pl = swj_pair_plan_variant(c, prec, 0);
     int ne = c->S > c->T ? c->S : c->T;
     std::vector<int> only0(nb, 0);
     only0[0] = 1;

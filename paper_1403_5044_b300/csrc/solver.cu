@@ -542,6 +542,10 @@ int newton_phase(swj_ctx *c, double *u, int prec, double tol, int max_it, Phase 
 int swj_residual_impl(swj_ctx *c, const double *u, double *E, int precision, const int *act)
 {
     swj_launch_mesh_step(c, u, E, act);
+    if (!(precision == SWJ_FP64 ? c->tuned64 : c->tuned32)) {
+        int rc = swj_pair_autotune(c, precision, act);
+        if (rc) return rc;
+    }
     const bool rec = c->time_pairs && c->tev && c->n_timed < SWJ_MAX_TIMED;
     if (rec) cudaEventRecord(c->tev[2 * c->n_timed], c->stream);
     if (precision == SWJ_FP64) swj_launch_pairs64(c, c->plan64, act);

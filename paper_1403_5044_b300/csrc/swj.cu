@@ -25,6 +25,7 @@ bool valid_opts(const swj_opts *o)
     if (!(o->ftol_inf > 0.0) || !(o->eta_max > 0.0) || o->eta_max >= 1.0) return false;
     if (!(o->eta_min > 0.0) || o->eta_min > o->eta_max) return false;
     if (o->fd_h < 0.0 || !(o->mixed_tol_inf > 0.0) || !(o->refine_tol_inf > 0.0)) return false;
+    if (o->autotune != 0 && o->autotune != 1) return false;
     return true;
 }
 
@@ -89,7 +90,8 @@ int alloc_all(swj_ctx *c)
     c->tgt32 = TgtArrays32{f, f + NT, f + 2 * NT, f + 3 * NT, f + 4 * NT, f + 5 * NT, f + 6 * NT, f + 7 * NT};
     c->plan64 = swj_pair_plan(c, SWJ_FP64);
     c->plan32 = swj_pair_plan(c, SWJ_FP32);
-    int P = c->plan64.P > c->plan32.P ? c->plan64.P : c->plan32.P;
+    // room for the partial sums of every compiled tile shape (the autotuner tries them all)
+    const int P = swj_pair_max_chunks(c);
     c->partial_cap = (size_t)P * T * nb;
     rc |= dalloc(c, &c->partial, c->partial_cap);
     double **vecs[] = {&c->u_tmp, &c->E_tmp, &c->E_cur, &c->u_try, &c->E_try, &c->E_base32, &c->du, &c->rvec};
@@ -142,8 +144,7 @@ int ctx_bytes(const swj_mesh *mesh, int nb, int kry_m, size_t *out)
     c.S = c.N * c.M;
     c.nu = 2 * (c.N + 1) * c.M;
     const size_t S = c.S, T = c.T, M = c.M, nu = c.nu, n = nb, d = sizeof(double);
-    PairPlan p64 = swj_pair_plan(&c, SWJ_FP64), p32 = swj_pair_plan(&c, SWJ_FP32);
-    const size_t P = (size_t)(p64.P > p32.P ? p64.P : p32.P);
+    const size_t P = (size_t)swj_pair_max_chunks(&c);
     size_t b = 4 * n * S * d + 3 * M * d + 2 * n * T * d + n * S * sizeof(SrcRec64) +
                n * S * sizeof(SrcRec32) + 8 * n * T * d + 8 * n * T * sizeof(float) + 2 * n * d +
                n * sizeof(int) + P * T * n * d + 8 * n * nu * d + n * SWJ_DS * d + n * SWJ_RED * d +
@@ -224,6 +225,7 @@ void swj_default_opts(swj_opts *o)
     o->mixed_tol_inf = 2e-6;
     o->refine_tol_inf = 1e-9;
     o->verbose = 0;
+    o->autotune = 1;
 }
 
 int swj_create(swj_ctx **out, const swj_mesh *mesh, double F, double eps, const swj_opts *opts,
@@ -306,6 +308,35 @@ int swj_set_opts(swj_ctx *c, const swj_opts *o)
 }
 
 size_t swj_workspace_bytes(const swj_ctx *c) { return c ? c->bytes : 0; }
+
+int swj_pair_variants(int precision)
+{
+    int n = 0;
+    while (swj_pair_variant_info(precision, n, nullptr, nullptr, nullptr) == SWJ_OK) ++n;
+    return n;
+}
+
+int swj_pair_config(const swj_ctx *c, int precision, int *variant, int *threads, int *targets,
+                    int *packed)
+{
+    if (!c || (precision != SWJ_FP64 && precision != SWJ_FP32)) return SWJ_EINVAL;
+    const PairPlan &pl = precision == SWJ_FP64 ? c->plan64 : c->plan32;
+    if (variant) *variant = pl.v;
+    return swj_pair_variant_info(precision, pl.v, threads, targets, packed);
+}
+
+int swj_set_pair_config(swj_ctx *c, int precision, int variant)
+{
+    if (!c || (precision != SWJ_FP64 && precision != SWJ_FP32)) return SWJ_EINVAL;
+    if (swj_pair_variant_info(precision, variant, nullptr, nullptr, nullptr) != SWJ_OK) return SWJ_EINVAL;
+    PairPlan pl = swj_pair_plan_variant(c, precision, variant);
+    if ((size_t)pl.P * c->T * c->nb > c->partial_cap) return SWJ_EINVAL;
+    SWJ_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    swj_graphs_free(c);   // captured steps bake in the old plan
+    if (precision == SWJ_FP64) { c->plan64 = pl; c->tuned64 = 1; }
+    else { c->plan32 = pl; c->tuned32 = 1; }
+    return SWJ_OK;
+}
 
 size_t swj_footprint_bytes(const swj_mesh *mesh, int count, const swj_opts *opts)
 {

@@ -50,6 +50,7 @@ struct PairPlan {
     int P;        // source chunks (grid.y)
     int chunk;    // sources per chunk
     int tiles;    // target tiles (grid.x)
+    int v;        // compiled tile shape (index into the variant table)
 };
 
 // is instance `inst` active (act = device flags, or nullptr for all)
@@ -91,6 +92,7 @@ struct swj_ctx {
     double *partial;
     size_t partial_cap;   // doubles
     PairPlan plan64, plan32;
+    int tuned64, tuned32;   // plan settled (autotuned or taken from the process cache)
 
     // JVP / solver temporaries, [nb][nu]
     double *u_tmp, *E_tmp;           // JVP: u + h v and E(u + h v)
@@ -145,7 +147,12 @@ void swj_launch_unpack(swj_ctx *c, const double *u, double *zeta_out, double *ph
 void swj_launch_surface(swj_ctx *c, double *out);
 
 // pairs.cu
+// plan of the tuned tile shape for this mesh size (the default shape if none yet)
 PairPlan swj_pair_plan(const swj_ctx *c, int precision);
+PairPlan swj_pair_plan_variant(const swj_ctx *c, int precision, int v);
+int swj_pair_max_chunks(const swj_ctx *c);     // largest P over every compiled shape
+int swj_pair_autotune(swj_ctx *c, int precision, const int *act);
+int swj_pair_variant_info(int precision, int v, int *tpb, int *R, int *packed);
 void swj_launch_pairs64(swj_ctx *c, const PairPlan &pl, const int *act);
 void swj_launch_pairs32(swj_ctx *c, const PairPlan &pl, const int *act);
 

@@ -40,7 +40,7 @@ class Opts(ctypes.Structure):
                 ("eta_max", ctypes.c_double), ("eta_min", ctypes.c_double),
                 ("fd_h", ctypes.c_double), ("refine_max", ctypes.c_int),
                 ("mixed_tol_inf", ctypes.c_double), ("refine_tol_inf", ctypes.c_double),
-                ("verbose", ctypes.c_int)]
+                ("verbose", ctypes.c_int), ("autotune", ctypes.c_int)]
 
 
 class ServerOpts(ctypes.Structure):
@@ -100,6 +100,10 @@ def lib():
             "swj_batch_count": (ctypes.c_int, [_vp]),
             "swj_batch_set_params": (ctypes.c_int, [_vp, P(ctypes.c_double), P(ctypes.c_double)]),
             "swj_destroy": (None, [_vp]),
+            "swj_pair_variants": (ctypes.c_int, [ctypes.c_int]),
+            "swj_pair_config": (ctypes.c_int, [_vp, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_int),
+                                               P(ctypes.c_int), P(ctypes.c_int)]),
+            "swj_set_pair_config": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
             "swj_footprint_bytes": (ctypes.c_size_t, [P(Mesh), ctypes.c_int, P(Opts)]),
             "swj_server_default_opts": (None, [P(ServerOpts)]),
             "swj_server_create": (ctypes.c_int, [P(_vp), P(ServerOpts)]),
@@ -150,6 +154,10 @@ def strerror(status: int) -> str:
 
 def version() -> str:
     return lib().swj_version().decode()
+
+
+def pair_variants(precision) -> int:
+    return int(lib().swj_pair_variants(int(precision)))
 
 
 def kernel_launches() -> int:
@@ -274,6 +282,16 @@ class Context:
 
     def sync(self):
         _check(lib().swj_sync(self._h), "swj_sync")
+
+    def pair_config(self, precision):
+        """(variant, threads per block, targets per thread, packed) of the all-pairs kernel."""
+        v, t, r, p = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().swj_pair_config(self._h, int(precision), ctypes.byref(v), ctypes.byref(t),
+                                     ctypes.byref(r), ctypes.byref(p)), "swj_pair_config")
+        return v.value, t.value, r.value, bool(p.value)
+
+    def set_pair_config(self, precision, variant):
+        _check(lib().swj_set_pair_config(self._h, int(precision), int(variant)), "swj_set_pair_config")
 
     def set_kernel_timing(self, enable=True):
         _check(lib().swj_set_kernel_timing(self._h, int(bool(enable))), "swj_set_kernel_timing")

@@ -75,6 +75,40 @@ def test_residual_fp32_matches_oracle(spec, F, eps, seed, amp):
     assert err.max() <= TOL32, (err.max(), int(err.argmax()))
 
 
+@pytest.mark.parametrize("spec,F,eps,seed,amp", [CASES[2], CASES[4]])
+@pytest.mark.parametrize("prec", [swj.FP64, swj.FP32])
+def test_every_tile_shape_matches_oracle(spec, F, eps, seed, amp, prec):
+    """Each compiled tile shape of the all-pairs kernel (the autotuner's
+    candidates, packed FP32 pair instructions included), pinned in turn."""
+    u = W.random_state(spec, seed=seed, amp=amp)
+    Eo, scale, _ = oracle_E_and_scale(spec, F, eps, u)
+    n = swj.pair_variants(prec)
+    assert n >= (6 if prec == swj.FP32 else 3)
+    with swj.Context.from_spec(spec, F, eps) as ctx:
+        ud = torch.tensor(u, dtype=torch.float64, device="cuda")
+        for v in range(n):
+            ctx.set_pair_config(prec, v)
+            assert ctx.pair_config(prec)[0] == v
+            Ed = ctx.vector()
+            ctx.residual(ud, Ed, prec)
+            ctx.sync()
+            err = np.abs(Ed.cpu().numpy() - Eo) / scale
+            assert err.max() <= (TOL64 if prec == swj.FP64 else TOL32), (v, err.max())
+
+
+def test_autotuned_shape_is_shared_by_contexts_of_one_mesh_size():
+    spec, F, eps = W.SOLVE_41x21
+    u = torch.tensor(W.random_state(spec, seed=3, amp=0.05), dtype=torch.float64, device="cuda")
+    cfg = []
+    for _ in range(2):
+        with swj.Context.from_spec(spec, F, eps) as ctx:
+            E = ctx.vector()
+            ctx.residual(u, E, swj.FP32)
+            ctx.sync()
+            cfg.append(ctx.pair_config(swj.FP32))
+    assert cfg[0] == cfg[1]
+
+
 def test_residual_181x61_both_precisions():
     """The 181x61, F = 0.7, eps = 0.4 workload, every row."""
     spec, F, eps = W.SOLVE_181x61
