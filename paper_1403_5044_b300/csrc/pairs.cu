@@ -288,6 +288,152 @@ k_pairs_x2(int T_, int S_, int chunk, const SrcRec32 *__restrict__ src, TgtArray
 }
 
 
+
+// Packed kernel with the source-row terms hoisted.  Sources are ordered row
+// by row (N per row, y = j exact), so within a row dy = j - y* and
+// dy' = j + y* are constants of the target; with them
+//   r1^2 = p^2 + (dz^2 + dy^2),   Q1 = (A p + B dy) p + C dy^2
+// (and the image forms with -dy') cost 2 operations each per pair, and the
+// row constants (dy, -dy', dy^2, dy'^2, B dy, -B dy', C dy^2, C dy'^2) are
+// recomputed only when the source row changes: 26 FP32 operations per pair
+// instead of 30 (the stated algorithmic count stays 44 flop).  The sums
+// differ from the scalar kernel's in rounding only.
+struct __align__(16) SrcX2R {
+    float2 x, z, nzx, zy, nzy, g, w, zxw;
+};
+
+// LEAN: B, C and y* are not held in registers but reloaded (from L1) at each
+// row change.  UNR: unroll factor of the source loop (more independent
+// reciprocal square roots in flight per warp).
+template <int RP, int TPB, int MINB, bool LEAN, int UNR>
+__global__ void __launch_bounds__(TPB, MINB)
+k_pairs_x2r(int T_, int S_, int chunk, int N, const SrcRec32 *__restrict__ src, TgtArrays32 tg,
+            double *__restrict__ partial, const int *__restrict__ act)
+{
+    constexpr int TILE = 256;
+    const int inst = blockIdx.z;
+    if (!SWJ_INST_ACTIVE(act, inst)) return;
+    {
+        const size_t ot = (size_t)inst * T_;
+        src += (size_t)inst * S_;
+        tg.x += ot; tg.y += ot; tg.zeta += ot; tg.g += ot; tg.zxw += ot; tg.A += ot; tg.B += ot; tg.C += ot;
+        partial += (size_t)inst * gridDim.y * T_;
+    }
+    __shared__ SrcX2R sh[TILE];
+    const int tid = threadIdx.x;
+    const int s0 = blockIdx.y * chunk;
+    const int s1 = min(S_, s0 + chunk);
+    float2 ntx[RP], nty[RP], ntz[RP], ntg[RP], ntzw[RP], A[RP], B[RP], C[RP], sum[RP], comp[RP];
+    float2 dy[RP], mdyp[RP], dy2[RP], dyp2[RP], Bdy[RP], mBdyp[RP], Cdy2[RP], Cdyp2[RP];
+    const int tb = blockIdx.x * 2 * RP * TPB + tid;
+#pragma unroll
+    for (int m = 0; m < RP; ++m) {
+        const int ta = min(tb + 2 * m * TPB, T_ - 1), tc = min(tb + (2 * m + 1) * TPB, T_ - 1);
+        ntx[m] = make_float2(-tg.x[ta], -tg.x[tc]);
+        if (!LEAN) nty[m] = make_float2(-tg.y[ta], -tg.y[tc]);
+        ntz[m] = make_float2(-tg.zeta[ta], -tg.zeta[tc]);
+        ntg[m] = make_float2(-tg.g[ta], -tg.g[tc]);
+        ntzw[m] = make_float2(-tg.zxw[ta], -tg.zxw[tc]);
+        A[m] = make_float2(tg.A[ta], tg.A[tc]);
+        if (!LEAN) {
+            B[m] = make_float2(tg.B[ta], tg.B[tc]);
+            C[m] = make_float2(tg.C[ta], tg.C[tc]);
+        }
+        sum[m] = f2(0.f);
+        comp[m] = f2(0.f);
+    }
+    int row = -1;            // source row the row constants belong to
+    for (int base = s0; base < s1; base += TILE) {
+        const int nt = min(TILE, s1 - base);
+        __syncthreads();
+        for (int i = tid; i < nt; i += TPB) {
+            const SrcRec32 q = src[base + i];
+            SrcX2R r;
+            r.x = f2(q.x); r.z = f2(q.zeta); r.nzx = f2(-q.zx); r.zy = f2(q.zy); r.nzy = f2(-q.zy);
+            r.g = f2(q.g); r.w = f2(q.w); r.zxw = f2(q.zxw);
+            sh[i] = r;
+        }
+        __syncthreads();
+        int j = base / N;                      // row of source `base`
+        int row_end = (j + 1) * N - base;      // tile index where row j ends
+        for (int sb = 0; sb < nt; sb += kSub) {
+            const int se = min(sb + kSub, nt);
+            float2 loc[RP];
+#pragma unroll
+            for (int m = 0; m < RP; ++m) loc[m] = f2(0.f);
+            int s = sb;
+            while (s < se) {
+                while (s >= row_end) { ++j; row_end += N; }
+                if (j != row) {
+                    row = j;
+                    const float2 yj = f2((float)j), myj = f2(-(float)j);
+#pragma unroll
+                    for (int m = 0; m < RP; ++m) {
+                        float2 ny = nty[m], Bm = B[m], Cm = C[m];
+                        if (LEAN) {
+                            const int ta = min(tb + 2 * m * TPB, T_ - 1), tc = min(tb + (2 * m + 1) * TPB, T_ - 1);
+                            ny = make_float2(-tg.y[ta], -tg.y[tc]);
+                            Bm = make_float2(tg.B[ta], tg.B[tc]);
+                            Cm = make_float2(tg.C[ta], tg.C[tc]);
+                        }
+                        dy[m] = __fadd2_rn(yj, ny);
+                        mdyp[m] = __fadd2_rn(myj, ny);               // -(y_j + y*)
+                        dy2[m] = __fmul2_rn(dy[m], dy[m]);
+                        dyp2[m] = __fmul2_rn(mdyp[m], mdyp[m]);
+                        Bdy[m] = __fmul2_rn(Bm, dy[m]);
+                        mBdyp[m] = __fmul2_rn(Bm, mdyp[m]);
+                        Cdy2[m] = __fmul2_rn(Cm, dy2[m]);
+                        Cdyp2[m] = __fmul2_rn(Cm, dyp2[m]);
+                    }
+                }
+                const int send = min(se, row_end);
+#pragma unroll UNR
+                for (; s < send; ++s) {
+                    const SrcX2R q = sh[s];
+#pragma unroll
+                    for (int m = 0; m < RP; ++m) {
+                        const float2 p = __fadd2_rn(q.x, ntx[m]);
+                        const float2 dz = __fadd2_rn(q.z, ntz[m]);
+                        const float2 r1s = __ffma2_rn(p, p, __ffma2_rn(dz, dz, dy2[m]));
+                        const float2 r2s = __ffma2_rn(p, p, __ffma2_rn(dz, dz, dyp2[m]));
+                        const float2 nc = __ffma2_rn(p, q.nzx, dz);
+                        const float2 n1 = __ffma2_rn(dy[m], q.nzy, nc);
+                        const float2 n2 = __ffma2_rn(mdyp[m], q.zy, nc);
+                        const float2 i1 = rsq2(r1s), i2 = rsq2(r2s);
+                        const float2 i1c = __fmul2_rn(__fmul2_rn(i1, i1), i1);
+                        const float2 i2c = __fmul2_rn(__fmul2_rn(i2, i2), i2);
+                        const float2 K1 = __ffma2_rn(n1, i1c, __fmul2_rn(n2, i2c));
+                        const float2 K2 = __fadd2_rn(i1, i2);
+                        const float2 Q1 = __ffma2_rn(__ffma2_rn(A[m], p, Bdy[m]), p, Cdy2[m]);
+                        const float2 Q2 = __ffma2_rn(__ffma2_rn(A[m], p, mBdyp[m]), p, Cdyp2[m]);
+                        const float2 S2 = __fadd2_rn(rsq2(Q1), rsq2(Q2));
+                        const float2 f = __fadd2_rn(q.g, ntg[m]);
+                        const float2 inner =
+                            __ffma2_rn(q.zxw, K2, __ffma2_rn(f, K1, __fmul2_rn(ntzw[m], S2)));
+                        loc[m] = __ffma2_rn(q.w, inner, loc[m]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int m = 0; m < RP; ++m) {
+                float y = loc[m].x - comp[m].x, t2 = sum[m].x + y;
+                comp[m].x = (t2 - sum[m].x) - y;
+                sum[m].x = t2;
+                y = loc[m].y - comp[m].y;
+                t2 = sum[m].y + y;
+                comp[m].y = (t2 - sum[m].y) - y;
+                sum[m].y = t2;
+            }
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < RP; ++m) {
+        const int ta = tb + 2 * m * TPB, tc = tb + (2 * m + 1) * TPB;
+        if (ta < T_) partial[(size_t)blockIdx.y * T_ + ta] = (double)sum[m].x - (double)comp[m].x;
+        if (tc < T_) partial[(size_t)blockIdx.y * T_ + tc] = (double)sum[m].y - (double)comp[m].y;
+    }
+}
+
 // Source-chunk count P for (tiles) target tiles: (tiles x P) blocks should fill
 // whole waves of `slots` resident blocks; chunks keep at least 64 sources.
 PairPlan make_plan(int T, int S, int slots, int tpb, int R, int v)
@@ -322,8 +468,8 @@ int resident_blocks(const void *kernel, int threads)
     return nb;
 }
 
-typedef void (*PairLaunch)(dim3, cudaStream_t, int, int, int, const void *, const void *, double *,
-                           const int *);
+typedef void (*PairLaunch)(dim3, cudaStream_t, int, int, int, int, const void *, const void *,
+                           double *, const int *);
 
 struct PairVariant {
     const void *kernel;
@@ -333,16 +479,24 @@ struct PairVariant {
 
 template <typename T, int R, int TPB> struct ScalarLaunch;
 template <typename T, int R> struct ScalarLaunch<T, R, 128> {
-    static void go(dim3 g, cudaStream_t st, int T_, int S_, int chunk, const void *src, const void *tg,
-                   double *partial, const int *act)
+    static void go(dim3 g, cudaStream_t st, int T_, int S_, int chunk, int, const void *src,
+                   const void *tg, double *partial, const int *act)
     {
         k_pairs_s<T, R><<<g, 128, 0, st>>>(T_, S_, chunk, (const SrcRecS<T> *)src,
                                            *(const TgtArraysS<T> *)tg, partial, act);
     }
 };
 
+template <int RP, int TPB, int MINB, bool LEAN, int UNR>
+void launch_x2r(dim3 g, cudaStream_t st, int T_, int S_, int chunk, int N, const void *src,
+                const void *tg, double *partial, const int *act)
+{
+    k_pairs_x2r<RP, TPB, MINB, LEAN, UNR><<<g, TPB, 0, st>>>(T_, S_, chunk, N, (const SrcRec32 *)src,
+                                                  *(const TgtArrays32 *)tg, partial, act);
+}
+
 template <int RP, int TPB, int MINB>
-void launch_x2(dim3 g, cudaStream_t st, int T_, int S_, int chunk, const void *src, const void *tg,
+void launch_x2(dim3 g, cudaStream_t st, int T_, int S_, int chunk, int, const void *src, const void *tg,
                double *partial, const int *act)
 {
     k_pairs_x2<RP, TPB, MINB><<<g, TPB, 0, st>>>(T_, S_, chunk, (const SrcRec32 *)src,
@@ -362,6 +516,18 @@ const PairVariant kVar32[] = {
     {(const void *)k_pairs_x2<2, 128, 6>, 128, 4, launch_x2<2, 128, 6>},
     {(const void *)k_pairs_x2<3, 256, 2>, 256, 6, launch_x2<3, 256, 2>},
     {(const void *)k_pairs_x2<1, 256, 4>, 256, 2, launch_x2<1, 256, 4>},
+    {(const void *)k_pairs_x2r<2, 256, 2, false, 1>, 256, 4, launch_x2r<2, 256, 2, false, 1>},
+    {(const void *)k_pairs_x2r<2, 256, 2, true, 1>, 256, 4, launch_x2r<2, 256, 2, true, 1>},
+    {(const void *)k_pairs_x2r<2, 256, 3, true, 1>, 256, 4, launch_x2r<2, 256, 3, true, 1>},
+    {(const void *)k_pairs_x2r<2, 128, 4, true, 1>, 128, 4, launch_x2r<2, 128, 4, true, 1>},
+    {(const void *)k_pairs_x2r<3, 128, 2, true, 1>, 128, 6, launch_x2r<3, 128, 2, true, 1>},
+    {(const void *)k_pairs_x2r<1, 256, 4, true, 1>, 256, 2, launch_x2r<1, 256, 4, true, 1>},
+    {(const void *)k_pairs_x2r<1, 256, 5, true, 1>, 256, 2, launch_x2r<1, 256, 5, true, 1>},
+    {(const void *)k_pairs_x2r<1, 256, 4, true, 2>, 256, 2, launch_x2r<1, 256, 4, true, 2>},
+    {(const void *)k_pairs_x2r<1, 256, 3, true, 2>, 256, 2, launch_x2r<1, 256, 3, true, 2>},
+    {(const void *)k_pairs_x2r<2, 128, 4, false, 2>, 128, 4, launch_x2r<2, 128, 4, false, 2>},
+    {(const void *)k_pairs_x2r<2, 256, 2, false, 2>, 256, 4, launch_x2r<2, 256, 2, false, 2>},
+    {(const void *)k_pairs_x2r<1, 128, 8, true, 2>, 128, 2, launch_x2r<1, 128, 8, true, 2>},
 };
 const PairVariant kVar64[] = {
     {(const void *)k_pairs_s<double, 4>, 128, 4, ScalarLaunch<double, 4, 128>::go},
@@ -420,9 +586,11 @@ static void launch_plan(swj_ctx *c, const PairPlan &pl, int precision, const int
     dim3 grid(pl.tiles, pl.P, c->nb);
     SWJ_COUNT_LAUNCH();
     if (precision == SWJ_FP64)
-        kVar64[pl.v].launch(grid, c->stream, c->T, c->S, pl.chunk, c->src64, &c->tgt64, c->partial, act);
+        kVar64[pl.v].launch(grid, c->stream, c->T, c->S, pl.chunk, c->N, c->src64, &c->tgt64, c->partial,
+                            act);
     else
-        kVar32[pl.v].launch(grid, c->stream, c->T, c->S, pl.chunk, c->src32, &c->tgt32, c->partial, act);
+        kVar32[pl.v].launch(grid, c->stream, c->T, c->S, pl.chunk, c->N, c->src32, &c->tgt32, c->partial,
+                            act);
 }
 
 // One launch covers every instance (grid.z); each instance uses the chunking
