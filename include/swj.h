@@ -90,9 +90,9 @@ typedef struct swj_opts {
     double refine_tol_inf; /* MIXED: the FP64 refinement stops at ||E_fp64||_inf      */
                            /* below this (1e-9)                                       */
     int    verbose;        /* 1: one line per Newton step on stderr (0)               */
-    int    autotune;       /* 1: on the first residual of a mesh size, time every     */
-                           /* compiled tile shape of the all-pairs kernel and keep    */
-                           /* the fastest for the process (1)                         */
+    int    autotune;       /* 1: on the first FP32 residual of a mesh size, time      */
+                           /* every compiled FP32 tile shape of the all-pairs kernel  */
+                           /* and keep the fastest for the process (1)                */
 } swj_opts;
 
 /* Counters and timings of one solve (KINSOL-style counters). */
@@ -227,8 +227,9 @@ int swj_surface(swj_ctx *ctx, const double *u_dev, double *out_dev);
 /* ---- tile shapes of the all-pairs kernel ----
  * Several tile shapes (threads per block, targets per thread, FP32 packed
  * pair instructions or not) are compiled per precision; index 0 is the
- * default.  With opts.autotune the first residual of each mesh size times
- * them all and every context of that size in the process uses the fastest. */
+ * default.  With opts.autotune the first FP32 residual of each mesh size
+ * times the FP32 shapes and every context of that size in the process uses
+ * the fastest; FP64 residuals use the default shape unless one is pinned. */
 
 /* Number of compiled shapes for `precision`. */
 int swj_pair_variants(int precision);

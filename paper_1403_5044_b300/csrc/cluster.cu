@@ -7,6 +7,7 @@
 // row) through distributed shared memory, with the hardware cluster barrier
 // as the only synchronisation.  No kernel here spins on a flag.
 #include "swj_internal.h"
+#include <map>
 #include <mutex>
 #include <cooperative_groups.h>
 
@@ -142,13 +143,50 @@ k_gj_cluster(int n, double *work_base, size_t wstride, double *out_base, size_t 
     cl.sync();
 }
 
-// The same Gauss-Jordan inverse with each CTA's column slice held in shared
-// memory (n x w doubles) for the whole elimination.  Every CTA loads its
-// slice before the first cluster barrier and writes the permuted result after
-// the last one, so `in` and `out` may be the same block.
+// One elimination step on a CTA's slice (rows over threads, WM >= nc columns
+// per row held in registers): row k <- rowk, every other row i <- row i -
+// col_k[i] rowk, with the pivot column's own entry (local index kk_own, or
+// -1 if it is not in this slice) starting from zero.
+template <int WM>
+__device__ __forceinline__ void gj_eliminate(double *A, int ws, int n, int nc, int k, int kk_own,
+                                             const double *__restrict__ col_k,
+                                             const double *__restrict__ rowk, int tid, int nth)
+{
+    double r[WM];
+#pragma unroll
+    for (int jj = 0; jj < WM; ++jj) r[jj] = (jj < nc) ? rowk[jj] : 0.0;
+    for (int i = tid; i < n; i += nth) {
+        double *Ai = A + (size_t)i * ws;
+        if (i == k) {
+#pragma unroll
+            for (int jj = 0; jj < WM; ++jj)
+                if (jj < nc) Ai[jj] = r[jj];
+        } else {
+            const double m = col_k[i];
+            double v[WM];
+#pragma unroll
+            for (int jj = 0; jj < WM; ++jj) v[jj] = (jj < nc && jj != kk_own) ? Ai[jj] : 0.0;
+#pragma unroll
+            for (int jj = 0; jj < WM; ++jj)
+                if (jj < nc) Ai[jj] = fma(-m, r[jj], v[jj]);
+        }
+    }
+}
+
+// Blocked Gauss-Jordan inverse with partial (row) pivoting, one n x n block
+// per cluster, each CTA's column slice (n x w) in shared memory.  The pivots
+// are taken panel by panel, a panel being one CTA's slice: its owner runs the
+// w pivot steps on its own columns alone (pivot search, interchange,
+// scaling, elimination of every other row), keeping each step's pivot column
+// (the multipliers); after one cluster barrier the other CTAs copy those
+// columns and the pivot indices from the owner's shared memory and replay the
+// w steps on their slices.  One cluster barrier per panel instead of two per
+// pivot; the arithmetic of every step is that of the unblocked elimination.
+// Every CTA loads its slice before the first barrier and writes the
+// (column-permuted) inverse after the last, so `in` and `out` may alias.
+template <int WM>
 __global__ void __launch_bounds__(kGJThreads)
-k_gj_cluster_smem(int n, const double *in_base, size_t istride, double *out_base, size_t ostride,
-                  int *info)
+k_gj_blocked(int n, const double *in_base, size_t istride, double *out_base, size_t ostride, int *info)
 {
     cg::cluster_group cl = cg::this_cluster();
     const int ncta = (int)cl.num_blocks();
@@ -157,101 +195,118 @@ k_gj_cluster_smem(int n, const double *in_base, size_t istride, double *out_base
     const double *in = in_base + (size_t)mat * istride;
     double *out = out_base + (size_t)mat * ostride;
     const int w = (n + ncta - 1) / ncta;
+    const int ws = w | 1;                       // odd row stride: conflict-free row-per-thread access
     const int c0 = rank * w, c1 = min(n, c0 + w), nc = max(0, c1 - c0);
     extern __shared__ double sm[];
-    double *colf = sm;                          // 2 x n, double buffered
-    double *rowk = sm + 2 * n;                  // w
-    double *A = rowk + w;                       // n x w slice (row-major, stride w)
-    int *piv = (int *)(A + (size_t)n * w);      // n
-    int *ctl = piv + n;                         // [p, fail] x 2 buffers
+    double *A = sm;                             // n x w slice (row-major, stride ws)
+    double *col = A + (size_t)n * ws;           // w x n: pivot columns of the current panel
+    double *rowk = col + (size_t)n * w;         // w
+    double *rpv = rowk + w;                     // w: reciprocal pivots of the current panel
+    int *piv = (int *)(rpv + w);                // n
+    int *ctl = piv + n;                         // [fail]
     int *sigma = ctl + 4;                       // n
-    __shared__ double red_v[kGJThreads / 32];
+    __shared__ unsigned long long red_k[kGJThreads / 32];
     __shared__ int red_i[kGJThreads / 32];
     const int tid = threadIdx.x, nth = blockDim.x;
     for (int e = tid; e < n * nc; e += nth) {
-        int i = e / nc, jj = e % nc;
-        A[(size_t)i * w + jj] = in[(size_t)i * n + c0 + jj];
+        const int i = e / nc, jj = e - i * nc;
+        A[(size_t)i * ws + jj] = in[(size_t)i * n + c0 + jj];
     }
+    if (tid == 0) ctl[0] = 0;
     __syncthreads();
     int fail = 0;
-    for (int k = 0; k < n; ++k) {
-        const int buf = k & 1;
-        const int owner = k / w;
-        if (rank == owner) {
-            const int kk = k - c0;
-            double bv = -1.0;
-            int bi = n;
-            for (int i = k + tid; i < n; i += nth) {
-                double v = fabs(A[(size_t)i * w + kk]);
-                if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-                int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
-            }
-            if ((tid & 31) == 0) { red_v[tid >> 5] = bv; red_i[tid >> 5] = bi; }
-            __syncthreads();
-            if (tid < 32) {
-                double v = (tid < nth / 32) ? red_v[tid] : -1.0;
-                int ii = (tid < nth / 32) ? red_i[tid] : n;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    double ov = __shfl_xor_sync(0xffffffffu, v, o);
-                    int oi = __shfl_xor_sync(0xffffffffu, ii, o);
-                    if (ov > v || (ov == v && oi < ii)) { v = ov; ii = oi; }
+    for (int o = 0; o < ncta; ++o) {
+        const int oc0 = o * w;
+        const int onc = min(n, oc0 + w) - oc0;
+        if (onc <= 0) break;                    // the same for every CTA
+        if (rank == o) {
+            int f = 0;
+            for (int kk = 0; kk < onc; ++kk) {
+                const int k = oc0 + kk;
+                // pivot: the largest |a_ik| of column kk, rows k..n-1, first index on ties;
+                // non-negative doubles order as their bit patterns, so the search runs on
+                // integer keys (no FP64 comparisons)
+                unsigned long long bk = 0ull;
+                int bi = n;
+                for (int i = k + tid; i < n; i += nth) {
+                    const unsigned long long kv =
+                        (unsigned long long)__double_as_longlong(fabs(A[(size_t)i * ws + kk]));
+                    if (kv > bk || (kv == bk && i < bi)) { bk = kv; bi = i; }
                 }
-                if (tid == 0) {
-                    red_i[0] = ii;
-                    red_v[0] = (v > 0.0 && isfinite(v)) ? 0.0 : 1.0;
+#pragma unroll
+                for (int sft = 16; sft > 0; sft >>= 1) {
+                    const unsigned long long ok = __shfl_xor_sync(0xffffffffu, bk, sft);
+                    const int oi = __shfl_xor_sync(0xffffffffu, bi, sft);
+                    if (ok > bk || (ok == bk && oi < bi)) { bk = ok; bi = oi; }
                 }
+                if ((tid & 31) == 0) { red_k[tid >> 5] = bk; red_i[tid >> 5] = bi; }
+                __syncthreads();
+                if (tid < 32) {
+                    unsigned long long kv = (tid < nth / 32) ? red_k[tid] : 0ull;
+                    int ii = (tid < nth / 32) ? red_i[tid] : n;
+#pragma unroll
+                    for (int sft = 16; sft > 0; sft >>= 1) {
+                        const unsigned long long ok = __shfl_xor_sync(0xffffffffu, kv, sft);
+                        const int oi = __shfl_xor_sync(0xffffffffu, ii, sft);
+                        if (ok > kv || (ok == kv && oi < ii)) { kv = ok; ii = oi; }
+                    }
+                    if (tid == 0) {
+                        const double pv = (ii < n) ? A[(size_t)ii * ws + kk] : 0.0;
+                        const bool good = ii < n && pv != 0.0 && isfinite(pv);
+                        piv[k] = good ? ii : k;
+                        ctl[1] = good ? 0 : k + 1;
+                        rpv[kk] = good ? 1.0 / pv : 0.0;     // one division per step
+                        col[(size_t)kk * n + k] = pv;
+                    }
+                }
+                __syncthreads();
+                f = ctl[1];
+                if (f) break;
+                const int p = piv[k];
+                const double rp = rpv[kk];
+                // interchange rows k and p, scaled pivot row, multipliers (pre-interchange
+                // values: row k is not written in this phase, row p only by its own column)
+                for (int jj = tid; jj < nc; jj += nth) {
+                    const double v = A[(size_t)p * ws + jj];
+                    rowk[jj] = (jj == kk) ? rp : v * rp;
+                    if (p != k) A[(size_t)p * ws + jj] = A[(size_t)k * ws + jj];
+                }
+                for (int i = tid; i < n; i += nth)
+                    if (i != k) col[(size_t)kk * n + i] = (i == p) ? A[(size_t)k * ws + kk] : A[(size_t)i * ws + kk];
+                __syncthreads();
+                gj_eliminate<WM>(A, ws, n, nc, k, kk, col + (size_t)kk * n, rowk, tid, nth);
+                __syncthreads();
             }
-            __syncthreads();
-            const int p = red_i[0];
-            const int f = red_v[0] != 0.0 ? k + 1 : 0;
-            for (int e = tid; e < n * ncta; e += nth) {
-                int q = e / n, i = e % n;
-                int src = (i == k) ? p : ((i == p) ? k : i);
-                double v = (f || p >= n) ? 0.0 : A[(size_t)src * w + kk];
-                double *rc = cl.map_shared_rank(colf + buf * n, q);
-                rc[i] = v;
-            }
-            if (tid < ncta) {
-                int *rq = cl.map_shared_rank(ctl + 2 * buf, tid);
-                rq[0] = p;
-                rq[1] = f;
-            }
+            if (tid == 0) ctl[0] = f;
         }
         cl.sync();
-        const int p = ctl[2 * buf];
-        fail = ctl[2 * buf + 1];
+        fail = *cl.map_shared_rank(ctl, o);
         if (fail) break;
-        if (tid == 0) piv[k] = p;
-        if (p != k) {
-            for (int jj = tid; jj < nc; jj += nth) {
-                double t = A[(size_t)k * w + jj];
-                A[(size_t)k * w + jj] = A[(size_t)p * w + jj];
-                A[(size_t)p * w + jj] = t;
+        if (rank != o) {
+            const double *ocol = cl.map_shared_rank(col, o);
+            const double *orpv = cl.map_shared_rank(rpv, o);
+            const int *opiv = cl.map_shared_rank(piv, o);
+            for (int e = tid; e < onc * n; e += nth) col[e] = ocol[e];
+            for (int e = tid; e < onc; e += nth) {
+                piv[oc0 + e] = opiv[oc0 + e];
+                rpv[e] = orpv[e];
+            }
+            __syncthreads();
+            for (int kk = 0; kk < onc; ++kk) {
+                const int k = oc0 + kk, p = piv[k];
+                const double rp = rpv[kk];
+                for (int jj = tid; jj < nc; jj += nth) {
+                    const double v = A[(size_t)p * ws + jj];
+                    rowk[jj] = v * rp;
+                    if (p != k) A[(size_t)p * ws + jj] = A[(size_t)k * ws + jj];
+                }
+                __syncthreads();
+                gj_eliminate<WM>(A, ws, n, nc, k, -1, col + (size_t)kk * n, rowk, tid, nth);
+                __syncthreads();
             }
         }
-        __syncthreads();
-        const double *cf = colf + buf * n;
-        const double rp = 1.0 / cf[k];
-        for (int jj = tid; jj < nc; jj += nth)
-            rowk[jj] = (c0 + jj == k) ? rp : A[(size_t)k * w + jj] * rp;
-        __syncthreads();
-        for (int e = tid; e < n * nc; e += nth) {
-            int i = e / nc, jj = e % nc;
-            size_t ij = (size_t)i * w + jj;
-            if (i == k) {
-                A[ij] = rowk[jj];
-            } else {
-                double base = (c0 + jj == k) ? 0.0 : A[ij];
-                A[ij] = fma(-cf[i], rowk[jj], base);
-            }
-        }
-        __syncthreads();
+        // the owner's columns are read by the others until they reach the next barrier;
+        // the owner does not touch `col` again before that barrier
     }
     if (!fail) {
         if (tid == 0) {
@@ -264,8 +319,8 @@ k_gj_cluster_smem(int n, const double *in_base, size_t istride, double *out_base
         }
         __syncthreads();
         for (int e = tid; e < n * nc; e += nth) {
-            int i = e / nc, jj = e % nc;
-            out[(size_t)i * n + piv[c0 + jj]] = A[(size_t)i * w + jj];
+            const int i = e / nc, jj = e - i * nc;
+            out[(size_t)i * n + piv[c0 + jj]] = A[(size_t)i * ws + jj];
         }
     }
     if (rank == 0 && tid == 0) info[mat] = fail;
@@ -391,9 +446,12 @@ k_band_sweep(int n1, int M, int h, const double *__restrict__ band, size_t band_
 
 // 16 CTAs per cluster where the device runs such clusters (a non-portable
 // size), else the portable 8.
+// (The kernel's dynamic shared-memory limit is raised to `smem` first: the
+// occupancy query fails for a size above the kernel's limit.)
 int cluster_ctas(const void *kernel, int threads, size_t smem)
 {
-    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         cudaGetLastError();
         return 8;
     }
@@ -418,51 +476,87 @@ int cluster_ctas(const void *kernel, int threads, size_t smem)
 
 }  // namespace
 
+// Cluster size (16 where the device can run such clusters of this kernel with
+// `smem` bytes of dynamic shared memory per CTA, else 8) per (kernel, smem);
+// also raises the kernel's shared-memory limit to `smem`.  Call with
+// g_attr_mutex held.
+// Lazily settled launch attributes, shared by every context and host thread.
+static std::mutex g_attr_mutex;
+static std::map<std::pair<const void *, size_t>, int> g_cluster_cache;
+static std::map<const void *, size_t> g_smem_limit;
+static int cluster_for(const void *kern, int threads, size_t smem)
+{
+    auto key = std::make_pair(kern, smem);
+    auto it = g_cluster_cache.find(key);
+    if (it != g_cluster_cache.end()) return it->second;
+    // the limit only grows: a smaller size queried later must not lower it
+    int cs = cluster_ctas(kern, threads, smem);
+    size_t &lim = g_smem_limit[kern];
+    if (smem > lim) lim = smem;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim);
+    cudaGetLastError();
+    g_cluster_cache[key] = cs;
+    return cs;
+}
+
 size_t gj_smem_bytes(int n, int cs)
 {
     const int w = (n + cs - 1) / cs;
-    return (size_t)(2 * n + w + (size_t)n * w) * sizeof(double) + (size_t)(2 * n + 4) * sizeof(int);
+    return (size_t)((size_t)n * (w | 1) + (size_t)n * w + 2 * w) * sizeof(double) + (size_t)(2 * n + 4) * sizeof(int);
 }
 
-// Lazily settled launch attributes, shared by every context and host thread.
-static std::mutex g_attr_mutex;
-static int g_cs_smem = 0;
 
-// true when the shared-memory Gauss-Jordan variant applies to n x n blocks
-// (then input and output may be the same block)
-static int gj_smem_cluster()
+// Instances of the blocked Gauss-Jordan kernel by maximum slice width.
+static const void *gj_blocked_kernel(int w)
 {
+    if (w <= 8) return (const void *)k_gj_blocked<8>;
+    if (w <= 12) return (const void *)k_gj_blocked<12>;
+    if (w <= 16) return (const void *)k_gj_blocked<16>;
+    if (w <= 24) return (const void *)k_gj_blocked<24>;
+    return (const void *)k_gj_blocked<32>;
+}
+
+// Cluster size of the blocked kernel for n x n blocks (0: it does not apply).
+static int gj_blocked_cluster(int n)
+{
+    static std::map<int, int> cache;
     std::lock_guard<std::mutex> lock(g_attr_mutex);
-    if (!g_cs_smem) g_cs_smem = cluster_ctas((const void *)k_gj_cluster_smem, kGJThreads, 64 * 1024);
-    return g_cs_smem;
+    auto it = cache.find(n);
+    if (it != cache.end()) return it->second;
+    int cs = 0;
+    for (int c : {16, 8}) {
+        const int w = (n + c - 1) / c;
+        const size_t smem = gj_smem_bytes(n, c);
+        if (w > 32 || smem > 200 * 1024) continue;
+        if (cluster_for(gj_blocked_kernel(w), kGJThreads, smem) >= c) { cs = c; break; }
+    }
+    cache[n] = cs;
+    return cs;
 }
 
-bool swj_gj_inplace(int n)
-{
-    return gj_smem_bytes(n, gj_smem_cluster()) <= 200 * 1024;
-}
+// true when the shared-memory (blocked) Gauss-Jordan kernel applies to n x n
+// blocks (then input and output may be the same block)
+bool swj_gj_inplace(int n) { return gj_blocked_cluster(n) > 0; }
 
 int swj_gj_inverse_cluster(cudaStream_t st, int n, int count, double *work, size_t wstride,
                            double *out, size_t ostride, int *info)
 {
-    static int cs_g = 0;
-    static size_t set_s = 48 * 1024, set_g = 48 * 1024;
-    const bool use_smem = swj_gj_inplace(n);
-    const void *kern = use_smem ? (const void *)k_gj_cluster_smem : (const void *)k_gj_cluster;
+    const int csb = gj_blocked_cluster(n);
+    const bool use_smem = csb > 0;
     int cs;
     size_t smem;
-    {
+    const void *kern;
+    if (use_smem) {
+        cs = csb;
+        smem = gj_smem_bytes(n, cs);
+        kern = gj_blocked_kernel((n + cs - 1) / cs);
+    } else {
         std::lock_guard<std::mutex> lock(g_attr_mutex);
-        if (!use_smem && !cs_g) cs_g = cluster_ctas((const void *)k_gj_cluster, kGJThreads, 64 * 1024);
-        cs = use_smem ? g_cs_smem : cs_g;
+        kern = (const void *)k_gj_cluster;
+        cs = cluster_for(kern, kGJThreads, 64 * 1024);
         const int w = (n + cs - 1) / cs;
-        smem = use_smem ? gj_smem_bytes(n, cs)
-                        : (size_t)(2 * n + w) * sizeof(double) + (size_t)(2 * n + 4) * sizeof(int);
-        size_t &set = use_smem ? set_s : set_g;
-        if (smem > set) {
-            SWJ_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            set = smem;
-        }
+        smem = (size_t)(2 * n + w) * sizeof(double) + (size_t)(2 * n + 4) * sizeof(int);
+        cluster_for(kern, kGJThreads, smem);
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cs * count);
@@ -477,11 +571,10 @@ int swj_gj_inverse_cluster(cudaStream_t st, int n, int count, double *work, size
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     SWJ_COUNT_LAUNCH();
-    if (use_smem)
-        SWJ_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_gj_cluster_smem, n, (const double *)work, wstride, out,
-                                        ostride, info));
-    else
-        SWJ_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_gj_cluster, n, work, wstride, out, ostride, info));
+    const double *win = work;
+    void *args[] = {(void *)&n, (void *)&win, (void *)&wstride, (void *)&out, (void *)&ostride, (void *)&info};
+    if (use_smem) SWJ_CUDA_TRY(cudaLaunchKernelExC(&cfg, kern, args));
+    else SWJ_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_gj_cluster, n, work, wstride, out, ostride, info));
     return SWJ_OK;
 }
 
@@ -493,18 +586,11 @@ int launch_sweep(cudaStream_t st, int nb, int n1, int M, int h, const double *ba
                  const double *W, size_t ws, double *y, double *z, double *x, size_t vs, const int *act,
                  bool prepare)
 {
-    static int cs_cached = 0;
-    static size_t smem_set = 48 * 1024;
     const size_t smem = (size_t)(h > 0 ? h : 1) * n1 * sizeof(double);
     int cs;
     {
         std::lock_guard<std::mutex> lock(g_attr_mutex);
-        if (!cs_cached) cs_cached = cluster_ctas((const void *)k_band_sweep<KC>, kSweepThreads, 64 * 1024);
-        cs = cs_cached;
-        if (smem > smem_set) {
-            SWJ_CUDA_TRY(cudaFuncSetAttribute(k_band_sweep<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            smem_set = smem;
-        }
+        cs = cluster_for((const void *)k_band_sweep<KC>, kSweepThreads, smem);
     }
     if (prepare) return SWJ_OK;
     cudaLaunchConfig_t cfg = {};

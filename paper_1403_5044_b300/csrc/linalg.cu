@@ -192,52 +192,56 @@ __global__ void k_bcombine(int n, int rows, const double *__restrict__ Z, size_t
     x[inst * xstride + i] = s;
 }
 
-// C = alpha A B + beta C (row-major), 64x64 output tile per block, 256 threads
-// with 4x4 outputs each, k-tiles of 16 staged in shared memory.
-constexpr int GT = 64, GK = 16;
+// C = alpha A B + beta C (row-major), TILE x TILE output tile per block, 256
+// threads with (TILE/16)^2 outputs each, k-tiles of 16 staged in shared memory.
+// TILE = 64 for throughput, 32 to spread one small product over more SMs
+// (FP64 work on one SM is slow on this part).
+constexpr int GK = 16;
+template <int TILE>
 __global__ void __launch_bounds__(256)
 k_dgemm(int m, int n, int k, double alpha, const double *const *Ap, const double *A0, int lda,
         const double *const *Bp, const double *B0, int ldb, double beta, double *const *Cp,
         double *C0, int ldc)
 {
+    constexpr int R = TILE / 16;
     const double *A = Ap ? Ap[blockIdx.z] : A0;
     const double *B = Bp ? Bp[blockIdx.z] : B0;
     double *C = Cp ? Cp[blockIdx.z] : C0;
-    __shared__ double As[GK][GT + 1];
-    __shared__ double Bs[GK][GT + 1];
+    __shared__ double As[GK][TILE + 1];
+    __shared__ double Bs[GK][TILE + 1];
     int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    int row0 = blockIdx.y * GT, col0 = blockIdx.x * GT;
-    double acc[4][4] = {};
+    int row0 = blockIdx.y * TILE, col0 = blockIdx.x * TILE;
+    double acc[R][R] = {};
     for (int kk = 0; kk < k; kk += GK) {
-        for (int e = threadIdx.x; e < GT * GK; e += 256) {
+        for (int e = threadIdx.x; e < TILE * GK; e += 256) {
             int r = e / GK, q = e % GK;          // A tile: rows r, cols q
             int gr = row0 + r, gq = kk + q;
             As[q][r] = (gr < m && gq < k) ? A[(size_t)gr * lda + gq] : 0.0;
-            int q2 = e / GT, c2 = e % GT;        // B tile: rows q2, cols c2
+            int q2 = e / TILE, c2 = e % TILE;    // B tile: rows q2, cols c2
             int gq2 = kk + q2, gc = col0 + c2;
             Bs[q2][c2] = (gq2 < k && gc < n) ? B[(size_t)gq2 * ldb + gc] : 0.0;
         }
         __syncthreads();
 #pragma unroll
         for (int q = 0; q < GK; ++q) {
-            double a[4], b[4];
+            double a[R], b[R];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[q][ty + 16 * i];
+            for (int i = 0; i < R; ++i) a[i] = As[q][ty + 16 * i];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Bs[q][tx + 16 * j];
+            for (int j = 0; j < R; ++j) b[j] = Bs[q][tx + 16 * j];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < R; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+                for (int j = 0; j < R; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < R; ++i) {
         int r = row0 + ty + 16 * i;
         if (r >= m) continue;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < R; ++j) {
             int cc = col0 + tx + 16 * j;
             if (cc >= n) continue;
             double *cp = C + (size_t)r * ldc + cc;
@@ -310,20 +314,23 @@ void swj_bcombine(cudaStream_t st, int nb, int n, int rows, const double *Z, siz
 }
 void swj_dgemm_batched(cudaStream_t st, int m, int n, int k, double alpha,
                        const double *const *A, int lda, const double *const *B, int ldb,
-                       double beta, double *const *C, int ldc, int batch)
+                       double beta, double *const *C, int ldc, int batch, int tile)
 {
     if (batch <= 0 || m <= 0 || n <= 0) return;
-    dim3 grid(nblk(n, GT), nblk(m, GT), batch);
     SWJ_COUNT_LAUNCH();
-    k_dgemm<<<grid, 256, 0, st>>>(m, n, k, alpha, A, nullptr, lda, B, nullptr, ldb, beta, C,
-                                  nullptr, ldc);
+    if (tile == 32)
+        k_dgemm<32><<<dim3(nblk(n, 32), nblk(m, 32), batch), 256, 0, st>>>(
+            m, n, k, alpha, A, nullptr, lda, B, nullptr, ldb, beta, C, nullptr, ldc);
+    else
+        k_dgemm<64><<<dim3(nblk(n, 64), nblk(m, 64), batch), 256, 0, st>>>(
+            m, n, k, alpha, A, nullptr, lda, B, nullptr, ldb, beta, C, nullptr, ldc);
 }
 void swj_dgemm(cudaStream_t st, int m, int n, int k, double alpha, const double *A, int lda,
                const double *B, int ldb, double beta, double *C, int ldc)
 {
     if (m <= 0 || n <= 0) return;
-    dim3 grid(nblk(n, GT), nblk(m, GT), 1);
+    dim3 grid(nblk(n, 32), nblk(m, 32), 1);
     SWJ_COUNT_LAUNCH();
-    k_dgemm<<<grid, 256, 0, st>>>(m, n, k, alpha, nullptr, A, lda, nullptr, B, ldb, beta,
-                                  nullptr, C, ldc);
+    k_dgemm<32><<<grid, 256, 0, st>>>(m, n, k, alpha, nullptr, A, lda, nullptr, B, ldb, beta,
+                                      nullptr, C, ldc);
 }

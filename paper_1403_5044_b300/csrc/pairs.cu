@@ -530,8 +530,8 @@ const PairVariant kVar32[] = {
     {(const void *)k_pairs_x2r<1, 128, 8, true, 2>, 128, 2, launch_x2r<1, 128, 8, true, 2>},
 };
 const PairVariant kVar64[] = {
-    {(const void *)k_pairs_s<double, 4>, 128, 4, ScalarLaunch<double, 4, 128>::go},
     {(const void *)k_pairs_s<double, 2>, 128, 2, ScalarLaunch<double, 2, 128>::go},
+    {(const void *)k_pairs_s<double, 4>, 128, 4, ScalarLaunch<double, 4, 128>::go},
     {(const void *)k_pairs_s<double, 8>, 128, 8, ScalarLaunch<double, 8, 128>::go},
 };
 constexpr int kNVar32 = sizeof(kVar32) / sizeof(kVar32[0]);
@@ -599,7 +599,7 @@ void swj_launch_pairs64(swj_ctx *c, const PairPlan &pl, const int *act) { launch
 void swj_launch_pairs32(swj_ctx *c, const PairPlan &pl, const int *act) { launch_plan(c, pl, SWJ_FP32, act); }
 
 // Pick the context's plan for `precision`: the variant already tuned for this
-// mesh size, else (autotune on, stream not capturing) time every variant on
+// mesh size, else (FP32, autotune on, stream not capturing) time every variant on
 // the current source/target records (one warm-up launch, then the mean of
 // three) and keep the fastest for the whole process.
 int swj_pair_autotune(swj_ctx *c, int precision, const int *act)
@@ -608,7 +608,9 @@ int swj_pair_autotune(swj_ctx *c, int precision, const int *act)
     if (done) return SWJ_OK;
     PairPlan &plan = precision == SWJ_FP64 ? c->plan64 : c->plan32;
     int v = tuned_variant(c, precision);
-    if (v < 0 && c->opts.autotune) {
+    // FP64 shapes differ by a few percent while timing them costs a dozen FP64
+    // residuals: only the FP32 kernel is tuned, FP64 takes its default shape
+    if (v < 0 && c->opts.autotune && precision == SWJ_FP32) {
         cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
         if (cudaStreamIsCapturing(c->stream, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
             return SWJ_OK;   // untuned for now; tried again on a later residual

@@ -32,6 +32,7 @@
 // M x (N+1) matrix of per-row vectors with one (N+1)^2 block, computed as
 // row-by-row dot products (one warp per output) so that all SMs share it.
 #include "swj_internal.h"
+#include <algorithm>
 #include "closed_form.cuh"
 #include <vector>
 #include <string.h>
@@ -322,6 +323,14 @@ void free_pc(swj_ctx *c)
     if (c->pc_ptrs) cudaFree(c->pc_ptrs);
     c->pc_ptrs = nullptr;
     c->pc_ptrs_cap = 0;
+    if (c->pc_chain) {
+        cudaStreamSynchronize(c->pc_chain);
+        cudaStreamSynchronize(c->pc_bulk);
+        for (cudaEvent_t &e : c->pc_ev) cudaEventDestroy(e);
+        cudaStreamDestroy(c->pc_chain);
+        cudaStreamDestroy(c->pc_bulk);
+        c->pc_chain = c->pc_bulk = nullptr;
+    }
     c->pc_ready = 0;
     c->bytes -= c->pc_bytes;
     c->pc_bytes = 0;
@@ -474,10 +483,11 @@ int swj_pc_setup(swj_ctx *c)
         if (rc) return rc;
     } else {
         // device pointer triples of the batched GEMMs of every step, all instances:
-        //   W_ik = inv_i S_ik (k = i+1..i+h), then S_jk -= S_ji W_ik (j, k = i+1..i+h)
+        //   W_ik = inv_i S_ik (k = i+1..i+h), then S_jk -= S_ji W_ik (j, k = i+1..i+h),
+        //   the updates of block row i+1 (U1) apart from those of rows i+2.. (U2)
         std::vector<const double *> PA, PB;
         std::vector<double *> PC;
-        std::vector<int> offW(M), cntW(M), offU(M), cntU(M);
+        std::vector<int> offW(M), cntW(M), offU1(M), cntU1(M), offU2(M), cntU2(M);
         for (int i = 0; i < M; ++i) {
             int kmax = i + h < M - 1 ? i + h : M - 1;
             offW[i] = (int)PA.size();
@@ -487,14 +497,16 @@ int swj_pc_setup(swj_ctx *c)
                     PC.push_back(wblk(c, q, i, k));
                 }
             cntW[i] = (int)PA.size() - offW[i];
-            offU[i] = (int)PA.size();
-            for (int q = 0; q < nb; ++q)
-                for (int j = i + 1; j <= kmax; ++j)
-                    for (int k = i + 1; k <= kmax; ++k) {
-                        PA.push_back(blk(c, q, j, i)); PB.push_back(wblk(c, q, i, k));
-                        PC.push_back(blk(c, q, j, k));
-                    }
-            cntU[i] = (int)PA.size() - offU[i];
+            for (int part = 0; part < 2; ++part) {
+                (part ? offU2 : offU1)[i] = (int)PA.size();
+                for (int q = 0; q < nb; ++q)
+                    for (int j = (part ? i + 2 : i + 1); j <= (part ? kmax : std::min(i + 1, kmax)); ++j)
+                        for (int k = i + 1; k <= kmax; ++k) {
+                            PA.push_back(blk(c, q, j, i)); PB.push_back(wblk(c, q, i, k));
+                            PC.push_back(blk(c, q, j, k));
+                        }
+                (part ? cntU2 : cntU1)[i] = (int)PA.size() - (part ? offU2 : offU1)[i];
+            }
         }
         int np = (int)PA.size();
         if (c->pc_ptrs_cap < np) {
@@ -522,25 +534,58 @@ int swj_pc_setup(swj_ctx *c)
                                      cudaMemcpyHostToDevice, st));
         SWJ_CUDA_TRY(cudaStreamSynchronize(st));   // `all` must outlive the copy
         double **dA = c->pc_ptrs, **dB = c->pc_ptrs + np, **dC = c->pc_ptrs + 2 * np;
+        // Look-ahead factorisation.  Step i on the chain stream: wait for the bulk
+        // updates of step i-2 (the last ones block row i receives), invert S_ii,
+        // W_i = inv_i S_i*, then wait for the bulk of step i-1 (it writes block row
+        // i+1 too) and update block row i+1 (U1).  The bulk stream updates rows
+        // i+2..i+h of step i (U2) once W_i exists, while the chain inverts the
+        // next diagonal blocks.  Events ev[0..3] follow W_i, ev[4..7] the bulk of
+        // step i (rings of 4: a wait is always enqueued before its event is
+        // recorded again).
+        if (!c->pc_chain) {
+            int lo = 0, hi = 0;
+            cudaDeviceGetStreamPriorityRange(&lo, &hi);
+            SWJ_CUDA_TRY(cudaStreamCreateWithPriority(&c->pc_chain, cudaStreamNonBlocking, hi));
+            SWJ_CUDA_TRY(cudaStreamCreateWithPriority(&c->pc_bulk, cudaStreamNonBlocking, lo));
+            for (cudaEvent_t &e : c->pc_ev) SWJ_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        }
+        cudaStream_t sc = c->pc_chain, sb = c->pc_bulk;
+        cudaEvent_t *evW = c->pc_ev, *evB = c->pc_ev + 4, evStart = c->pc_ev[8], evEnd = c->pc_ev[9];
+        SWJ_CUDA_TRY(cudaEventRecord(evStart, st));
+        SWJ_CUDA_TRY(cudaStreamWaitEvent(sc, evStart, 0));
+        SWJ_CUDA_TRY(cudaStreamWaitEvent(sb, evStart, 0));
         for (int i = 0; i < M; ++i) {
+            if (i >= 2) SWJ_CUDA_TRY(cudaStreamWaitEvent(sc, evB[(i - 2) % 4], 0));
             double *diag0 = blk(c, 0, i, i);
             if (gj_inplace) {
-                rc = swj_gj_inverse_cluster(st, n1, nb, diag0, bst, diag0, bst, c->pc_info + (size_t)i * nb);
+                rc = swj_gj_inverse_cluster(sc, n1, nb, diag0, bst, diag0, bst, c->pc_info + (size_t)i * nb);
             } else {
                 SWJ_COUNT_LAUNCH();
-                k_copy_blocks<<<dim3(64, nb), 256, 0, st>>>(n2, diag0, bst, c->pc_work, n2);
-                rc = swj_gj_inverse_cluster(st, n1, nb, c->pc_work, n2, diag0, bst, c->pc_info + (size_t)i * nb);
+                k_copy_blocks<<<dim3(64, nb), 256, 0, sc>>>(n2, diag0, bst, c->pc_work, n2);
+                rc = swj_gj_inverse_cluster(sc, n1, nb, c->pc_work, n2, diag0, bst, c->pc_info + (size_t)i * nb);
             }
             if (rc) return rc;
             if (cntW[i])
-                swj_dgemm_batched(st, n1, n1, n1, 1.0, (const double *const *)(dA + offW[i]), n1,
+                swj_dgemm_batched(sc, n1, n1, n1, 1.0, (const double *const *)(dA + offW[i]), n1,
                                   (const double *const *)(dB + offW[i]), n1, 0.0, dC + offW[i], n1,
-                                  cntW[i]);
-            if (cntU[i])
-                swj_dgemm_batched(st, n1, n1, n1, -1.0, (const double *const *)(dA + offU[i]), n1,
-                                  (const double *const *)(dB + offU[i]), n1, 1.0, dC + offU[i], n1,
-                                  cntU[i]);
+                                  cntW[i], 32);
+            SWJ_CUDA_TRY(cudaEventRecord(evW[i % 4], sc));
+            if (i >= 1) SWJ_CUDA_TRY(cudaStreamWaitEvent(sc, evB[(i - 1) % 4], 0));
+            if (cntU1[i])
+                swj_dgemm_batched(sc, n1, n1, n1, -1.0, (const double *const *)(dA + offU1[i]), n1,
+                                  (const double *const *)(dB + offU1[i]), n1, 1.0, dC + offU1[i], n1,
+                                  cntU1[i], 32);
+            SWJ_CUDA_TRY(cudaStreamWaitEvent(sb, evW[i % 4], 0));
+            if (cntU2[i])
+                swj_dgemm_batched(sb, n1, n1, n1, -1.0, (const double *const *)(dA + offU2[i]), n1,
+                                  (const double *const *)(dB + offU2[i]), n1, 1.0, dC + offU2[i], n1,
+                                  cntU2[i], 64);
+            SWJ_CUDA_TRY(cudaEventRecord(evB[i % 4], sb));
         }
+        SWJ_CUDA_TRY(cudaEventRecord(evEnd, sb));
+        SWJ_CUDA_TRY(cudaStreamWaitEvent(st, evEnd, 0));
+        SWJ_CUDA_TRY(cudaEventRecord(evEnd, sc));
+        SWJ_CUDA_TRY(cudaStreamWaitEvent(st, evEnd, 0));
     }
     std::vector<int> info((size_t)nb * M);
     SWJ_CUDA_TRY(cudaMemcpyAsync(info.data(), c->pc_info, info.size() * sizeof(int),

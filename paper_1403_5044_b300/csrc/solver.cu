@@ -43,7 +43,11 @@ enum {
 
 inline int nblk(long n, int b) { return (int)((n + b - 1) / b); }
 
-__global__ void k_fd_h(double *__restrict__ ds, double epsm, double hfix, const int *__restrict__ act,
+// FD step: h = sqrt(eps_mach) max(1, ||u||_2) / ||v||_2 (||u|| is dominated by
+// the phi_x ~ 1 entries, so h ||v|| is already ~0.05 of a mesh-wide unit; a
+// larger step for the central difference would make its truncation error, not
+// the rounding, the larger term)
+__global__ void k_fd_h(double *__restrict__ ds, double rel, double hfix, const int *__restrict__ act,
                        int nb)
 {
     int inst = blockIdx.x * blockDim.x + threadIdx.x;
@@ -52,29 +56,31 @@ __global__ void k_fd_h(double *__restrict__ ds, double epsm, double hfix, const 
     if (hfix > 0.0) { d[DS_H] = hfix; return; }
     double nv = sqrt(d[DS_NV]);
     double nu = sqrt(d[DS_NU]);
-    d[DS_H] = (nv > 0.0) ? sqrt(epsm) * fmax(1.0, nu) / nv : 1.0;
+    d[DS_H] = (nv > 0.0) ? rel * fmax(1.0, nu) / nv : 1.0;
 }
 
+// out = u + sgn h v
 __global__ void k_perturb(int n, const double *__restrict__ u, const double *__restrict__ v,
-                          const double *__restrict__ ds, double *__restrict__ out,
+                          const double *__restrict__ ds, double sgn, double *__restrict__ out,
                           const int *__restrict__ act)
 {
     const int inst = blockIdx.y;
     if (!SWJ_INST_ACTIVE(act, inst)) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     const size_t o = (size_t)inst * n;
-    if (i < n) out[o + i] = fma(ds[(size_t)inst * SWJ_DS + DS_H], v[o + i], u[o + i]);
+    if (i < n) out[o + i] = fma(sgn * ds[(size_t)inst * SWJ_DS + DS_H], v[o + i], u[o + i]);
 }
 
+// out = (Ep - Eu) / (span h): span 1 forward, 2 central (Eu = E(u - h v))
 __global__ void k_fd_diff(int n, const double *__restrict__ Ep, const double *__restrict__ Eu,
-                          const double *__restrict__ ds, double *__restrict__ out,
+                          const double *__restrict__ ds, double span, double *__restrict__ out,
                           const int *__restrict__ act)
 {
     const int inst = blockIdx.y;
     if (!SWJ_INST_ACTIVE(act, inst)) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     const size_t o = (size_t)inst * n;
-    if (i < n) out[o + i] = (Ep[o + i] - Eu[o + i]) / ds[(size_t)inst * SWJ_DS + DS_H];
+    if (i < n) out[o + i] = (Ep[o + i] - Eu[o + i]) / (span * ds[(size_t)inst * SWJ_DS + DS_H]);
 }
 
 // v_{j+1} <- w / ||w||_2 (the squared norm is in slot DS_NW)
@@ -310,6 +316,7 @@ int gmres(swj_ctx *c, int kind, const double *u, const double *Ebase, int prec,
             if (rc) return rc;
             SWJ_CUDA_TRY(cudaStreamSynchronize(s));
             count_residual(st, step, prec);
+            if (!Ebase) count_residual(st, step, prec);   // central difference: two residuals
             for (int i = 0; i < nb; ++i) {
                 if (!step[i]) continue;
                 if (st) { st[i].precond_applies++; st[i].krylov_iters++; }
@@ -417,6 +424,11 @@ int gmres(swj_ctx *c, int kind, const double *u, const double *Ebase, int prec,
     return SWJ_OK;
 }
 
+// GMRES tolerance of the refinement steps: their central-difference FP32 JVPs
+// are accurate to ~1e-5 relative, so one step can contract the FP64 residual
+// by about that much
+constexpr double kRefineEta = 1e-4;
+
 struct Phase {
     std::vector<double> finf, f2;
     std::vector<int> status;     // SWJ_PENDING while iterating
@@ -432,7 +444,7 @@ int newton_phase(swj_ctx *c, double *u, int prec, double tol, int max_it, Phase 
     const size_t ld = (size_t)n;
     cudaStream_t s = c->stream;
     const swj_opts &o = c->opts;
-    std::vector<double> eta(nb, refine ? 1e-3 : o.eta_max);
+    std::vector<double> eta(nb, refine ? kRefineEta : o.eta_max);
     const int kind = refine ? 2 : (prec == SWJ_FP64 ? 0 : 1);
     int rc;
     for (int it = 0; it <= max_it; ++it) {
@@ -449,13 +461,8 @@ int newton_phase(swj_ctx *c, double *u, int prec, double tol, int max_it, Phase 
         if (!any) break;
         rc = set_mask(c, on);
         if (rc) return rc;
-        const double *Ebase = c->E_cur;
-        if (refine) {
-            rc = swj_residual_impl(c, u, c->E_base32, SWJ_FP32, c->act_d);
-            if (rc) return rc;
-            count_residual(st, on, SWJ_FP32);
-            Ebase = c->E_base32;
-        }
+        // refinement: central-difference FP32 JVPs (no FP32 base residual needed)
+        const double *Ebase = refine ? nullptr : c->E_cur;
         const int jprec = refine ? SWJ_FP32 : prec;
         swj_bscale(s, nb, n, nullptr, 0, -1.0, 0, c->E_cur, c->rvec, ld, c->act_d);
         std::vector<double> gres;
@@ -564,19 +571,27 @@ int swj_jvp_impl(swj_ctx *c, const double *u, const double *Eu, const double *v,
 {
     cudaStream_t s = c->stream;
     const int n = c->nu, nb = c->nb;
+    const bool central = (Eu == nullptr);
     if (!(h_fixed > 0.0)) {
         swj_bnorms(s, nb, n, u, n, c->red, c->dscal + DS_NU, SWJ_DS, act);
         swj_bnorms(s, nb, n, v, n, c->red, c->dscal + DS_NV, SWJ_DS, act);
     }
-    double epsm = (precision == SWJ_FP64) ? 2.220446049250313e-16 : 1.1920928955078125e-07;
+    const double epsm = (precision == SWJ_FP64) ? 2.220446049250313e-16 : 1.1920928955078125e-07;
     SWJ_COUNT_LAUNCH();
-    k_fd_h<<<nblk(nb, 64), 64, 0, s>>>(c->dscal, epsm, h_fixed, act, nb);
+    k_fd_h<<<nblk(nb, 64), 64, 0, s>>>(c->dscal, sqrt(epsm), h_fixed, act, nb);
     SWJ_COUNT_LAUNCH();
-    k_perturb<<<dim3(nblk(n, 256), nb), 256, 0, s>>>(n, u, v, c->dscal, c->u_tmp, act);
+    k_perturb<<<dim3(nblk(n, 256), nb), 256, 0, s>>>(n, u, v, c->dscal, 1.0, c->u_tmp, act);
     int rc = swj_residual_impl(c, c->u_tmp, c->E_tmp, precision, act);
     if (rc) return rc;
+    if (central) {
+        SWJ_COUNT_LAUNCH();
+        k_perturb<<<dim3(nblk(n, 256), nb), 256, 0, s>>>(n, u, v, c->dscal, -1.0, c->u_tmp2, act);
+        rc = swj_residual_impl(c, c->u_tmp2, c->E_tmp2, precision, act);
+        if (rc) return rc;
+    }
     SWJ_COUNT_LAUNCH();
-    k_fd_diff<<<dim3(nblk(n, 256), nb), 256, 0, s>>>(n, c->E_tmp, Eu, c->dscal, Jv, act);
+    k_fd_diff<<<dim3(nblk(n, 256), nb), 256, 0, s>>>(n, c->E_tmp, central ? c->E_tmp2 : Eu, c->dscal,
+                                                      central ? 2.0 : 1.0, Jv, act);
     SWJ_CUDA_TRY(cudaGetLastError());
     return SWJ_OK;
 }

@@ -42,7 +42,7 @@ void free_all(swj_ctx *c)
 {
     void *ptrs[] = {c->zeta, c->g, c->zetay, c->gy, c->spl_cp, c->spl_a, c->spl_inv, c->e2part,
                     c->Ival, c->src64, c->src32, c->tgt64_base, c->tgt32_base, c->partial,
-                    c->u_tmp, c->E_tmp, c->E_cur, c->u_try, c->E_try, c->E_base32, c->du,
+                    c->u_tmp, c->E_tmp, c->u_tmp2, c->E_tmp2, c->E_cur, c->u_try, c->E_try, c->E_base32, c->du,
                     c->rvec, c->dscal, c->red, c->V, c->Z, c->Fd, c->epsd, c->act_d};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -94,7 +94,8 @@ int alloc_all(swj_ctx *c)
     const int P = swj_pair_max_chunks(c);
     c->partial_cap = (size_t)P * T * nb;
     rc |= dalloc(c, &c->partial, c->partial_cap);
-    double **vecs[] = {&c->u_tmp, &c->E_tmp, &c->E_cur, &c->u_try, &c->E_try, &c->E_base32, &c->du, &c->rvec};
+    double **vecs[] = {&c->u_tmp, &c->E_tmp, &c->u_tmp2, &c->E_tmp2, &c->E_cur, &c->u_try, &c->E_try,
+                       &c->E_base32, &c->du, &c->rvec};
     for (double **v : vecs) rc |= dalloc(c, v, nb * nu);
     rc |= dalloc(c, &c->dscal, nb * SWJ_DS);
     rc |= dalloc(c, &c->red, nb * SWJ_RED);
@@ -147,7 +148,7 @@ int ctx_bytes(const swj_mesh *mesh, int nb, int kry_m, size_t *out)
     const size_t P = (size_t)swj_pair_max_chunks(&c);
     size_t b = 4 * n * S * d + 3 * M * d + 2 * n * T * d + n * S * sizeof(SrcRec64) +
                n * S * sizeof(SrcRec32) + 8 * n * T * d + 8 * n * T * sizeof(float) + 2 * n * d +
-               n * sizeof(int) + P * T * n * d + 8 * n * nu * d + n * SWJ_DS * d + n * SWJ_RED * d +
+               n * sizeof(int) + P * T * n * d + 10 * n * nu * d + n * SWJ_DS * d + n * SWJ_RED * d +
                n * (size_t)(2 * kry_m + 1) * nu * d;
     *out = b;
     return SWJ_OK;

@@ -96,6 +96,7 @@ struct swj_ctx {
 
     // JVP / solver temporaries, [nb][nu]
     double *u_tmp, *E_tmp;           // JVP: u + h v and E(u + h v)
+    double *u_tmp2, *E_tmp2;         // central-difference JVP: u - h v and E(u - h v)
     double *E_cur, *u_try, *E_try;   // Newton: current residual, line-search trial
     double *E_base32;                // MIXED refinement: FP32 residual at u (JVP base)
     double *du, *rvec;               // Newton step, GMRES right-hand side
@@ -124,6 +125,10 @@ struct swj_ctx {
     int pc_ptrs_cap;
     double *pc_t1, *pc_t2, *pc_z;   // apply temporaries [nb][H]
     double *pc_work;             // Gauss-Jordan work copies [nb][(h == 0 ? M : 1)][n1][n1]
+    // look-ahead factorisation: the critical chain (Gauss-Jordan, W, next block row)
+    // on a high-priority stream, the other Schur updates on a low-priority one
+    cudaStream_t pc_chain, pc_bulk;
+    cudaEvent_t pc_ev[10];
 
     size_t pc_bytes;             // device bytes of the preconditioner buffers
     size_t bytes;                // device bytes held (workspace + preconditioner)
@@ -181,10 +186,11 @@ void swj_bmgemv_sub(cudaStream_t st, int nb, int n, int rows, const double *V, s
 void swj_bcombine(cudaStream_t st, int nb, int n, int rows, const double *Z, size_t ld,
                   size_t zstride, const double *coef, size_t sstride, double *x, size_t xstride,
                   int accumulate, const int *act);
-// C(mxn) = alpha A(mxk) B(kxn) + beta C, row-major with leading dims; batched by pointer arrays
+// C(mxn) = alpha A(mxk) B(kxn) + beta C, row-major with leading dims; batched by pointer
+// arrays; output tiles of `tile` (64, or 32 for small products that must spread over SMs)
 void swj_dgemm_batched(cudaStream_t st, int m, int n, int k, double alpha,
                        const double *const *A, int lda, const double *const *B, int ldb,
-                       double beta, double *const *C, int ldc, int batch);
+                       double beta, double *const *C, int ldc, int batch, int tile = 64);
 void swj_dgemm(cudaStream_t st, int m, int n, int k, double alpha, const double *A, int lda,
                const double *B, int ldb, double beta, double *C, int ldc);
 
@@ -208,6 +214,8 @@ size_t swj_pc_bytes(int N, int M, int nb, int block_bw);
 
 // solver.cu
 int swj_residual_impl(swj_ctx *c, const double *u, double *E, int precision, const int *act);
+// Eu = E(u) in `precision`: forward difference (E(u + h v) - E(u)) / h;
+// Eu = nullptr: central difference (E(u + h v) - E(u - h v)) / (2 h)
 int swj_jvp_impl(swj_ctx *c, const double *u, const double *Eu, const double *v, double *Jv,
                  int precision, double h_fixed, const int *act);
 int swj_solve_impl(swj_ctx *c, double *u, swj_stats *st);
