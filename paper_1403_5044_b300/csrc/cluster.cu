@@ -173,20 +173,46 @@ __device__ __forceinline__ void gj_eliminate(double *A, int ws, int n, int nc, i
     }
 }
 
-// Blocked Gauss-Jordan inverse with partial (row) pivoting, one n x n block
-// per cluster, each CTA's column slice (n x w) in shared memory.  The pivots
-// are taken panel by panel, a panel being one CTA's slice: its owner runs the
-// w pivot steps on its own columns alone (pivot search, interchange,
-// scaling, elimination of every other row), keeping each step's pivot column
-// (the multipliers); after one cluster barrier the other CTAs copy those
-// columns and the pivot indices from the owner's shared memory and replay the
-// w steps on their slices.  One cluster barrier per panel instead of two per
-// pivot; the arithmetic of every step is that of the unblocked elimination.
-// Every CTA loads its slice before the first barrier and writes the
-// (column-permuted) inverse after the last, so `in` and `out` may alias.
+// Flag helpers for the pipelined Gauss-Jordan kernel: a release max-update of
+// a word in another CTA's shared memory (a max, not a store: updates from two
+// successive owners may land in either order, the flag must never go back)
+// and an acquire load of this CTA's own word.
+__device__ __forceinline__ void max_release_cluster(unsigned *local_word, int cta, unsigned v)
+{
+    unsigned a = (unsigned)__cvta_generic_to_shared(local_word), ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(cta));
+    asm volatile("red.release.cluster.shared::cluster.max.u32 [%0], %1;" ::"r"(ra), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned ld_acquire_cluster(const unsigned *local_word)
+{
+    unsigned a = (unsigned)__cvta_generic_to_shared(local_word), v;
+    asm volatile("ld.acquire.cluster.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+    return v;
+}
+
+// Iterations of a flag wait before the kernel gives up (far above any real
+// wait: a step takes a few microseconds).
+constexpr long long kGJSpinLimit = 1ll << 26;
+
+// Pipelined Gauss-Jordan inverse with partial (row) pivoting, one n x n block
+// per cluster, each CTA's column slice (n x w) in shared memory.  The pivot
+// steps k = 0..n-1 are owned by the CTA holding column k.  The owner searches
+// the pivot in its (up to date) column, records the step (pivot row, the
+// multiplier column after the interchange, the reciprocal pivot) in its own
+// shared memory, raises a release flag in every other CTA and eliminates its
+// slice; it goes on to its next step at once.  Every other CTA waits for the
+// flag of step k (acquire), reads the step from the owner's shared memory and
+// applies it to its slice.  Steps are applied in order everywhere, so the
+// arithmetic is that of the unblocked elimination; no CTA waits for the
+// slower ones except a new panel owner, which must have applied every earlier
+// step first.  A failed pivot is published as a flag above n; a flag wait that
+// runs past kGJSpinLimit ends the kernel with info = -1.  Every CTA loads its
+// slice before the first barrier and writes the (column-permuted) inverse
+// after the last, so `in` and `out` may alias.
 template <int WM>
 __global__ void __launch_bounds__(kGJThreads)
-k_gj_blocked(int n, const double *in_base, size_t istride, double *out_base, size_t ostride, int *info)
+k_gj_pipe(int n, const double *in_base, size_t istride, double *out_base, size_t ostride, int *info)
 {
     cg::cluster_group cl = cg::this_cluster();
     const int ncta = (int)cl.num_blocks();
@@ -199,12 +225,16 @@ k_gj_blocked(int n, const double *in_base, size_t istride, double *out_base, siz
     const int c0 = rank * w, c1 = min(n, c0 + w), nc = max(0, c1 - c0);
     extern __shared__ double sm[];
     double *A = sm;                             // n x w slice (row-major, stride ws)
-    double *col = A + (size_t)n * ws;           // w x n: pivot columns of the current panel
-    double *rowk = col + (size_t)n * w;         // w
-    double *rpv = rowk + w;                     // w: reciprocal pivots of the current panel
-    int *piv = (int *)(rpv + w);                // n
-    int *ctl = piv + n;                         // [fail]
-    int *sigma = ctl + 4;                       // n
+    // step records of this CTA's steps, n + 2 doubles each: the multiplier column,
+    // the reciprocal pivot and the pivot row (as a double), read by the others
+    const int rs = n + 2;
+    double *rec = A + (size_t)n * ws;           // w x rs
+    double *lrec = rec + (size_t)w * rs;        // 2 x rs: copies of other owners' records (by step parity)
+    double *rowk = lrec + 2 * (size_t)rs;       // w
+    int *piv = (int *)(rowk + w);               // n
+    int *sigma = piv + n;                       // n
+    int *ctl = sigma + n;                       // [0] step status, [2..3] prefetch counts by parity
+    unsigned *flag = (unsigned *)(ctl + 4);     // published step count (written by the owners)
     __shared__ unsigned long long red_k[kGJThreads / 32];
     __shared__ int red_i[kGJThreads / 32];
     const int tid = threadIdx.x, nth = blockDim.x;
@@ -212,58 +242,80 @@ k_gj_blocked(int n, const double *in_base, size_t istride, double *out_base, siz
         const int i = e / nc, jj = e - i * nc;
         A[(size_t)i * ws + jj] = in[(size_t)i * n + c0 + jj];
     }
-    if (tid == 0) ctl[0] = 0;
-    __syncthreads();
+    if (tid == 0) {
+        *flag = 0u;
+        ctl[0] = ctl[1] = ctl[2] = ctl[3] = 0;
+    }
+    cl.sync();                                  // flags initialised before any remote store
+    // When the rows leave the last two warps idle in the elimination (n <= nth - 64),
+    // those warps fetch the next step's record from its owner meanwhile (if this CTA
+    // does not own it); ctl[2 + parity] counts the threads whose copy succeeded, and
+    // a step whose record was not fetched in full is fetched when it starts.
+    const int npre = 64;
+    const bool prefetch = n <= nth - npre;
+    const bool pre_thread = prefetch && tid >= nth - npre;
     int fail = 0;
-    for (int o = 0; o < ncta; ++o) {
-        const int oc0 = o * w;
-        const int onc = min(n, oc0 + w) - oc0;
-        if (onc <= 0) break;                    // the same for every CTA
+    for (int k = 0; k < n && !fail; ++k) {
+        const int o = k / w, kk = k - o * w;
+        const int nk = k + 1, no = nk / w;      // the next step and its owner
+        // the prefetching warps' part of the elimination phase of step k
+        auto prefetch_next = [&]() {
+            if (!pre_thread || nk >= n || no == rank) return;
+            long long it = 0;
+            unsigned v;
+            while ((v = ld_acquire_cluster(flag)) < (unsigned)(nk + 1)) {
+                if (++it > kGJSpinLimit) break;
+            }
+            if (v < (unsigned)(nk + 1) || v > (unsigned)n) return;   // left to the next step
+            const double *orec = cl.map_shared_rank(rec + (size_t)(nk - no * w) * rs, no);
+            double *dst = lrec + (size_t)(nk & 1) * rs;
+            for (int i = tid - (nth - npre); i < rs; i += npre) dst[i] = orec[i];
+            atomicAdd(&ctl[2 + (nk & 1)], 1);
+        };
         if (rank == o) {
-            int f = 0;
-            for (int kk = 0; kk < onc; ++kk) {
-                const int k = oc0 + kk;
-                // pivot: the largest |a_ik| of column kk, rows k..n-1, first index on ties;
-                // non-negative doubles order as their bit patterns, so the search runs on
-                // integer keys (no FP64 comparisons)
-                unsigned long long bk = 0ull;
-                int bi = n;
-                for (int i = k + tid; i < n; i += nth) {
-                    const unsigned long long kv =
-                        (unsigned long long)__double_as_longlong(fabs(A[(size_t)i * ws + kk]));
-                    if (kv > bk || (kv == bk && i < bi)) { bk = kv; bi = i; }
-                }
+            // pivot: the largest |a_ik|, rows k..n-1 of local column kk, first index
+            // on ties (non-negative doubles order as their bit patterns)
+            unsigned long long bk = 0ull;
+            int bi = n;
+            for (int i = k + tid; i < n; i += nth) {
+                const unsigned long long kv =
+                    (unsigned long long)__double_as_longlong(fabs(A[(size_t)i * ws + kk]));
+                if (kv > bk || (kv == bk && i < bi)) { bk = kv; bi = i; }
+            }
+#pragma unroll
+            for (int sft = 16; sft > 0; sft >>= 1) {
+                const unsigned long long ok = __shfl_xor_sync(0xffffffffu, bk, sft);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, sft);
+                if (ok > bk || (ok == bk && oi < bi)) { bk = ok; bi = oi; }
+            }
+            if ((tid & 31) == 0) { red_k[tid >> 5] = bk; red_i[tid >> 5] = bi; }
+            __syncthreads();
+            if (tid < 32) {
+                unsigned long long kv = (tid < nth / 32) ? red_k[tid] : 0ull;
+                int ii = (tid < nth / 32) ? red_i[tid] : n;
 #pragma unroll
                 for (int sft = 16; sft > 0; sft >>= 1) {
-                    const unsigned long long ok = __shfl_xor_sync(0xffffffffu, bk, sft);
-                    const int oi = __shfl_xor_sync(0xffffffffu, bi, sft);
-                    if (ok > bk || (ok == bk && oi < bi)) { bk = ok; bi = oi; }
+                    const unsigned long long ok = __shfl_xor_sync(0xffffffffu, kv, sft);
+                    const int oi = __shfl_xor_sync(0xffffffffu, ii, sft);
+                    if (ok > kv || (ok == kv && oi < ii)) { kv = ok; ii = oi; }
                 }
-                if ((tid & 31) == 0) { red_k[tid >> 5] = bk; red_i[tid >> 5] = bi; }
-                __syncthreads();
-                if (tid < 32) {
-                    unsigned long long kv = (tid < nth / 32) ? red_k[tid] : 0ull;
-                    int ii = (tid < nth / 32) ? red_i[tid] : n;
-#pragma unroll
-                    for (int sft = 16; sft > 0; sft >>= 1) {
-                        const unsigned long long ok = __shfl_xor_sync(0xffffffffu, kv, sft);
-                        const int oi = __shfl_xor_sync(0xffffffffu, ii, sft);
-                        if (ok > kv || (ok == kv && oi < ii)) { kv = ok; ii = oi; }
-                    }
-                    if (tid == 0) {
-                        const double pv = (ii < n) ? A[(size_t)ii * ws + kk] : 0.0;
-                        const bool good = ii < n && pv != 0.0 && isfinite(pv);
-                        piv[k] = good ? ii : k;
-                        ctl[1] = good ? 0 : k + 1;
-                        rpv[kk] = good ? 1.0 / pv : 0.0;     // one division per step
-                        col[(size_t)kk * n + k] = pv;
-                    }
+                if (tid == 0) {
+                    const double pv = (ii < n) ? A[(size_t)ii * ws + kk] : 0.0;
+                    const bool good = ii < n && pv != 0.0 && isfinite(pv);
+                    piv[k] = good ? ii : k;
+                    ctl[0] = good ? 0 : k + 1;
+                    double *r = rec + (size_t)kk * rs;
+                    r[k] = pv;
+                    r[n] = good ? 1.0 / pv : 0.0;        // one division per step
+                    r[n + 1] = (double)(good ? ii : k);
                 }
-                __syncthreads();
-                f = ctl[1];
-                if (f) break;
-                const int p = piv[k];
-                const double rp = rpv[kk];
+            }
+            __syncthreads();
+            const int f = ctl[0];
+            const int p = piv[k];
+            double *r = rec + (size_t)kk * rs;
+            const double rp = r[n];
+            if (!f) {
                 // interchange rows k and p, scaled pivot row, multipliers (pre-interchange
                 // values: row k is not written in this phase, row p only by its own column)
                 for (int jj = tid; jj < nc; jj += nth) {
@@ -272,42 +324,54 @@ k_gj_blocked(int n, const double *in_base, size_t istride, double *out_base, siz
                     if (p != k) A[(size_t)p * ws + jj] = A[(size_t)k * ws + jj];
                 }
                 for (int i = tid; i < n; i += nth)
-                    if (i != k) col[(size_t)kk * n + i] = (i == p) ? A[(size_t)k * ws + kk] : A[(size_t)i * ws + kk];
-                __syncthreads();
-                gj_eliminate<WM>(A, ws, n, nc, k, kk, col + (size_t)kk * n, rowk, tid, nth);
-                __syncthreads();
-            }
-            if (tid == 0) ctl[0] = f;
-        }
-        cl.sync();
-        fail = *cl.map_shared_rank(ctl, o);
-        if (fail) break;
-        if (rank != o) {
-            const double *ocol = cl.map_shared_rank(col, o);
-            const double *orpv = cl.map_shared_rank(rpv, o);
-            const int *opiv = cl.map_shared_rank(piv, o);
-            for (int e = tid; e < onc * n; e += nth) col[e] = ocol[e];
-            for (int e = tid; e < onc; e += nth) {
-                piv[oc0 + e] = opiv[oc0 + e];
-                rpv[e] = orpv[e];
+                    if (i != k) r[i] = (i == p) ? A[(size_t)k * ws + kk] : A[(size_t)i * ws + kk];
             }
             __syncthreads();
-            for (int kk = 0; kk < onc; ++kk) {
-                const int k = oc0 + kk, p = piv[k];
-                const double rp = rpv[kk];
-                for (int jj = tid; jj < nc; jj += nth) {
-                    const double v = A[(size_t)p * ws + jj];
-                    rowk[jj] = v * rp;
-                    if (p != k) A[(size_t)p * ws + jj] = A[(size_t)k * ws + jj];
+            // publish step k (or the failure) to every other CTA
+            if (tid < ncta && tid != rank) max_release_cluster(flag, tid, f ? (unsigned)(n + f) : (unsigned)(k + 1));
+            if (f) { fail = f; break; }
+            if (pre_thread) prefetch_next();
+            else gj_eliminate<WM>(A, ws, n, nc, k, kk, r, rowk, tid, nth);
+            __syncthreads();
+        } else {
+            double *lr = lrec + (size_t)(k & 1) * rs;
+            if (!(prefetch && ctl[2 + (k & 1)] == npre)) {
+                // not prefetched: every thread waits for the flag itself (acquire), then
+                // copies its share of the owner's step record
+                long long it = 0;
+                unsigned v;
+                while ((v = ld_acquire_cluster(flag)) < (unsigned)(k + 1)) {
+                    if (++it > kGJSpinLimit) break;
                 }
-                __syncthreads();
-                gj_eliminate<WM>(A, ws, n, nc, k, -1, col + (size_t)kk * n, rowk, tid, nth);
-                __syncthreads();
+                int st = 0;
+                if (v < (unsigned)(k + 1)) st = -1;                      // timed out
+                else if (v > (unsigned)n) st = (int)(v - (unsigned)n);    // the owner's pivot failed
+                if (!st) {
+                    const double *orec = cl.map_shared_rank(rec + (size_t)kk * rs, o);
+                    for (int i = tid; i < rs; i += nth) lr[i] = orec[i];
+                }
+                // the CTA stops if any thread timed out or saw the owner's failure
+                if (__syncthreads_or(st != 0)) { fail = st ? st : -1; break; }
             }
+            const int p = (int)lr[n + 1];
+            const double rp = lr[n];
+            if (tid == 0) piv[k] = p;
+            for (int jj = tid; jj < nc; jj += nth) {
+                const double a = A[(size_t)p * ws + jj];
+                rowk[jj] = a * rp;
+                if (p != k) A[(size_t)p * ws + jj] = A[(size_t)k * ws + jj];
+            }
+            __syncthreads();
+            // every thread has read this parity's count (before the barrier above): the
+            // buffer is free again for the step after next
+            if (tid == 0) ctl[2 + (k & 1)] = 0;
+            if (pre_thread) prefetch_next();
+            else gj_eliminate<WM>(A, ws, n, nc, k, -1, lr, rowk, tid, nth);
+            __syncthreads();
         }
-        // the owner's columns are read by the others until they reach the next barrier;
-        // the owner does not touch `col` again before that barrier
     }
+    // every CTA keeps its shared memory until all have read what they need
+    cl.sync();
     if (!fail) {
         if (tid == 0) {
             for (int j = 0; j < n; ++j) sigma[j] = j;
@@ -323,6 +387,8 @@ k_gj_blocked(int n, const double *in_base, size_t istride, double *out_base, siz
             out[(size_t)i * n + piv[c0 + jj]] = A[(size_t)i * ws + jj];
         }
     }
+    // status of the block: the first failing step (+1), -1 for a timeout, 0 for success;
+    // CTAs that stopped for different reasons agree on failure, rank 0 reports
     if (rank == 0 && tid == 0) info[mat] = fail;
     cl.sync();
 }
@@ -502,18 +568,19 @@ static int cluster_for(const void *kern, int threads, size_t smem)
 size_t gj_smem_bytes(int n, int cs)
 {
     const int w = (n + cs - 1) / cs;
-    return (size_t)((size_t)n * (w | 1) + (size_t)n * w + 2 * w) * sizeof(double) + (size_t)(2 * n + 4) * sizeof(int);
+    return (size_t)((size_t)n * (w | 1) + (size_t)(w + 2) * (n + 2) + w) * sizeof(double) +
+           (size_t)(2 * n + 8) * sizeof(int);
 }
 
 
 // Instances of the blocked Gauss-Jordan kernel by maximum slice width.
 static const void *gj_blocked_kernel(int w)
 {
-    if (w <= 8) return (const void *)k_gj_blocked<8>;
-    if (w <= 12) return (const void *)k_gj_blocked<12>;
-    if (w <= 16) return (const void *)k_gj_blocked<16>;
-    if (w <= 24) return (const void *)k_gj_blocked<24>;
-    return (const void *)k_gj_blocked<32>;
+    if (w <= 8) return (const void *)k_gj_pipe<8>;
+    if (w <= 12) return (const void *)k_gj_pipe<12>;
+    if (w <= 16) return (const void *)k_gj_pipe<16>;
+    if (w <= 24) return (const void *)k_gj_pipe<24>;
+    return (const void *)k_gj_pipe<32>;
 }
 
 // Cluster size of the blocked kernel for n x n blocks (0: it does not apply).

@@ -593,7 +593,8 @@ int swj_pc_setup(swj_ctx *c)
     SWJ_CUDA_TRY(cudaStreamSynchronize(st));
     SWJ_CUDA_TRY(cudaGetLastError());
     for (size_t i = 0; i < info.size(); ++i)
-        if (info[i] != 0) return SWJ_ESINGULAR;
+        if (info[i] < 0) return SWJ_ETIMEOUT;
+        else if (info[i] != 0) return SWJ_ESINGULAR;
     if (h > 0) {
         int rc = swj_band_sweep_cluster(st, nb, n1, M, h, c->pc_band, band_stride(c), c->pc_W,
                                         (size_t)M * h * n1 * n1, c->pc_t2, c->pc_z, c->pc_t2, (size_t)c->H,
