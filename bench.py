@@ -31,12 +31,40 @@ WORKLOAD = "ship-wave solve 181x61, F=0.7, eps=0.4 (x in [-16,20], y in [0,12], 
 METRIC = "solves/s (mixed FP32-residual solve refined to FP64, max|dzeta| vs FP64 solve <= 1e-6)"
 FLOP_PER_PAIR = 44          # FP32 operations per (source, target) pair, FFMA counted as 2
 FP32_LANES_PER_SM = 128
+FP64_LANES_PER_SM = 2        # B300: FP64 at 1/64 of the FP32 rate
 SM_COUNT_B300 = 148
 SM_MAX_MHZ = 2032.0
 # residual evaluations of one FP64 Newton-GMRES solve of this workload with the
 # default options (measured on the GPU path); the reference arm converts the
 # oracle's residual time into solves/s with it
 RESIDUALS_PER_SOLVE = 21
+# DRAM bytes (read + write) per launch of a pair-kernel shape, from the ncu capture
+# summarised in profiles/k_pairs_fp32_181x61.md (null for a shape not captured)
+PROFILED_TRAFFIC = {
+    "k_pairs_s<float,4>": 727589,
+    "k_pairs_x2<1,256,4>": 721664,
+    "k_pairs_x2<2,128,1>": 724882,
+    "k_pairs_x2<2,128,5>": 740498,
+    "k_pairs_x2<2,128,6>": 722213,
+    "k_pairs_x2<2,256,1>": 716178,
+    "k_pairs_x2<2,256,3>": 719726,
+    "k_pairs_x2<3,128,1>": 731173,
+    "k_pairs_x2<3,256,2>": 723712,
+    "k_pairs_x2<4,128,1>": 724699,
+    "k_pairs_x2<4,64,1>": 724151,
+    "k_pairs_x2r<1,128,8,1,2>": 721335,
+    "k_pairs_x2r<1,256,3,1,2>": 719177,
+    "k_pairs_x2r<1,256,4,1,1>": 716983,
+    "k_pairs_x2r<1,256,4,1,2>": 716946,
+    "k_pairs_x2r<1,256,5,1,1>": 717897,
+    "k_pairs_x2r<2,128,4,0,2>": 917285,
+    "k_pairs_x2r<2,128,4,1,1>": 723127,
+    "k_pairs_x2r<2,256,2,0,1>": 723163,
+    "k_pairs_x2r<2,256,2,0,2>": 720201,
+    "k_pairs_x2r<2,256,2,1,1>": 728864,
+    "k_pairs_x2r<2,256,3,1,1>": 717751,
+    "k_pairs_x2r<3,128,2,1,1>": 723639,
+}
 BLOCK_BW = 11          # block bandwidth of the mixed solves (fastest measured at 181x61)
 FP64_BLOCK_BW = 15     # the FP64 solve's own fastest block bandwidth
 
@@ -59,6 +87,9 @@ def parse():
     ap.add_argument("--serve-rates", default="0.25,0.5,0.75,1.0,1.25")
     ap.add_argument("--batch-steps", type=int, default=2,
                     help="timed steps of the 64 x 121x41 batched workload (0 = skip it)")
+    ap.add_argument("--mesh", default="181x61",
+                    help="--precond-only: mesh NxM on x in [-16,20], y in [0,12] (F = 0.7, eps = 0.3 "
+                         "unless 181x61, the workload)")
     ap.add_argument("--precond-only", action="store_true",
                     help="build the preconditioner, apply it 10 times and solve once "
                          "(a small, fixed launch sequence for profilers)")
@@ -227,6 +258,7 @@ def run_ours(args):
         wall = time.perf_counter() - wall0
     launches = swj.kernel_launches() - launches0
     pair_ms, pair_n = ctx.pair_timing(swj.FP32)
+    pair_name = swj.pair_variant_name(swj.FP32, ctx.pair_config(swj.FP32)[0])
     pair64_ms, pair64_n = ctx.pair_timing(swj.FP64)
     ctx.set_kernel_timing(False)
     step_ms = [a.elapsed_time(b) for a, b in ev]
@@ -323,7 +355,7 @@ def run_ours(args):
         "speedup_mixed_vs_fp64": value / (1e3 / mean(t64)),
         "residual_pairs_per_s": {"fp32_kernel": pairs / (avg_pair_ms * 1e-3),
                                  "fp64_kernel": pairs / (pair64_ms / max(1, pair64_n) * 1e-3) if pair64_n else None},
-        "roofline": {"bound": "alu", "kernel": "k_pairs<float> (all-pairs boundary-integral sum)",
+        "roofline": {"bound": "alu", "kernel": pair_name + " (FP32 all-pairs boundary-integral sum)",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "peak_note": "derived: %d SMs x %d FP32 lanes x 2 flop x %.0f MHz (MEASURED_PEAKS.json has no FP32 figure)"
                                   % (sms, FP32_LANES_PER_SM, SM_MAX_MHZ),
@@ -331,7 +363,17 @@ def run_ours(args):
                      "avg_launch_ms": avg_pair_ms, "launches_timed": pair_n,
                      "frac_at_measured_clock": (achieved / (sms * FP32_LANES_PER_SM * 2 * cs["sm_mhz"] * 1e6 / 1e12)
                                                 if cs["sm_mhz"] else None),
-                     "traffic": None},
+                     "traffic": PROFILED_TRAFFIC.get(pair_name)},
+        "roofline_fp64": ({"bound": "alu", "kernel": swj.pair_variant_name(swj.FP64, ctx.pair_config(swj.FP64)[0])
+                           + " (FP64 all-pairs sum of the refinement residuals)",
+                           "achieved": FLOP_PER_PAIR * pairs / (pair64_ms / pair64_n * 1e-3) / 1e12,
+                           "peak": sms * FP64_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12, "unit": "TFLOP/s",
+                           "frac": FLOP_PER_PAIR * pairs / (pair64_ms / pair64_n * 1e-3) / 1e12
+                           / (sms * FP64_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12),
+                           "peak_note": "derived: %d SMs x %d FP64 lanes x 2 flop x %.0f MHz (B300 nominal 1.25 TFLOP/s FP64)"
+                                        % (sms, FP64_LANES_PER_SM, SM_MAX_MHZ),
+                           "avg_launch_ms": pair64_ms / pair64_n, "launches_timed": pair64_n}
+                          if pair64_n else None),
         "cpu_baseline": cpu,
         "e2e": {"value": n_solves / (sum(e2e_ms) / 1e3) if world == 1 else args.steps / (sum(e2e_ms) / 1e3),
                 "unit": "solves/s", "h2d_bytes_per_step": ctx.n_unknowns * 8,
@@ -410,7 +452,7 @@ def serve_point(mode, count, rate_factor, sat=None):
     from paper_1403_5044_b300 import swj
     from paper_1403_5044_b300 import workloads as W
     reqs = W.serve_requests(count=count)
-    kw = dict(max_active=4, max_group=8, block_bw=BLOCK_BW, solve_mode=mode)
+    kw = dict(max_active=4, max_group=8, block_bw=-1, solve_mode=mode)   # block bandwidth by mesh
     with swj.Server(**kw) as srv:
         # warm-up: one request per mesh (creates the kept contexts' first graphs)
         for m in W.SERVE_MESHES:
@@ -514,6 +556,9 @@ def run_precond_only(args):
     from paper_1403_5044_b300 import swj
     from paper_1403_5044_b300 import workloads as W
     spec, F, eps = W.SOLVE_181x61
+    if args.mesh != "181x61":
+        N, M = (int(v) for v in args.mesh.split("x"))
+        spec, F, eps = W.domain_mesh(N, M), 0.7, 0.3
     with swj.Context.from_spec(spec, F, eps, solve_mode="mixed", block_bw=args.block_bw) as ctx:
         ctx.precond_setup()             # first use: module loading and kernel attributes
         ctx.sync()
@@ -526,11 +571,14 @@ def run_precond_only(args):
         for _ in range(10):
             ctx.precond_apply(u, r)
         ctx.sync()
+        t_apply = time.perf_counter() - t1
+        st = ctx.solve(u)               # first solve: autotuning and graph capture
+        ctx.initial_guess_flat(u)
         t2 = time.perf_counter()
         st = ctx.solve(u)
         t3 = time.perf_counter()
-    print(json.dumps({"precond_only": True, "block_bw": args.block_bw, "setup_ms": (t1 - t0) * 1e3,
-                      "apply_ms": (t2 - t1) * 1e2, "solve_ms": (t3 - t2) * 1e3,
+    print(json.dumps({"precond_only": True, "mesh": args.mesh, "block_bw": args.block_bw, "setup_ms": (t1 - t0) * 1e3,
+                      "apply_ms": t_apply * 1e2, "solve_ms": (t3 - t2) * 1e3,
                       "krylov_iters": st["krylov_iters"], "residual_evals": st["residual_evals"]}))
 
 

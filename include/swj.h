@@ -74,8 +74,9 @@ typedef struct swj_mesh {
 /* Solver options.  swj_default_opts() fills the defaults noted here. */
 typedef struct swj_opts {
     int    solve_mode;     /* SWJ_SOLVE_FP64 | SWJ_SOLVE_MIXED (MIXED)               */
-    int    block_bw;       /* preconditioner block bandwidth b: odd >= 1, or 0 for   */
-                           /* the untruncated linear Jacobian (Section 4.2) (1)     */
+    int    block_bw;       /* preconditioner block bandwidth b: odd >= 1, 0 for the  */
+                           /* untruncated linear Jacobian (Section 4.2), or -1: by  */
+                           /* mesh, 11 for M <= 64 block rows, else 15 (-1)         */
     int    gmres_restart;  /* GMRES restart length m (30)                            */
     int    max_newton;     /* Newton iteration cap (60)                              */
     int    max_krylov;     /* GMRES iterations per Newton step (300)                 */
@@ -239,6 +240,10 @@ int swj_pair_variants(int precision);
  * pointer may be NULL). */
 int swj_pair_config(const swj_ctx *ctx, int precision, int *variant, int *threads,
                     int *targets_per_thread, int *packed);
+
+/* Name of compiled shape `variant` (kernel and template arguments, e.g.
+ * "k_pairs_x2r<2,256,2,0,1>"; "" for an unknown index).  Static storage. */
+const char *swj_pair_variant_name(int precision, int variant);
 
 /* Pin shape `variant` for `precision` on this context (synchronises its
  * stream; drops captured graphs).  SWJ_EINVAL for an unknown index. */

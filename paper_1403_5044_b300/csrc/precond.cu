@@ -336,9 +336,12 @@ void free_pc(swj_ctx *c)
     c->pc_bytes = 0;
 }
 
-// block half bandwidth of the option block_bw (0 = the whole matrix)
+// block half bandwidth of the option block_bw (0 = the whole matrix, -1 = by
+// mesh: b = 11 up to 64 block rows, 15 above, the fastest set-up + solve
+// measured on the 61x21, 121x41, 181x61 and 361x121 meshes)
 int half_band(int block_bw, int M)
 {
+    if (block_bw < 0) block_bw = (M <= 64) ? 11 : 15;
     int h = (block_bw == 0) ? M - 1 : (block_bw - 1) / 2;
     return h > M - 1 ? M - 1 : h;
 }

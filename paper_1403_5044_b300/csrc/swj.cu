@@ -19,7 +19,7 @@ bool valid_opts(const swj_opts *o)
 {
     if (!o) return false;
     if (o->solve_mode != SWJ_SOLVE_FP64 && o->solve_mode != SWJ_SOLVE_MIXED) return false;
-    if (o->block_bw < 0 || (o->block_bw > 0 && o->block_bw % 2 == 0)) return false;
+    if (o->block_bw < -1 || (o->block_bw > 0 && o->block_bw % 2 == 0)) return false;
     if (o->gmres_restart < 1 || o->gmres_restart > 60) return false;
     if (o->max_newton < 0 || o->max_krylov < 1 || o->refine_max < 0) return false;
     if (!(o->ftol_inf > 0.0) || !(o->eta_max > 0.0) || o->eta_max >= 1.0) return false;
@@ -214,7 +214,7 @@ void swj_default_opts(swj_opts *o)
 {
     if (!o) return;
     o->solve_mode = SWJ_SOLVE_MIXED;
-    o->block_bw = 1;
+    o->block_bw = -1;
     o->gmres_restart = 30;
     o->max_newton = 60;
     o->max_krylov = 300;

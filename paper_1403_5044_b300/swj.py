@@ -101,6 +101,7 @@ def lib():
             "swj_batch_set_params": (ctypes.c_int, [_vp, P(ctypes.c_double), P(ctypes.c_double)]),
             "swj_destroy": (None, [_vp]),
             "swj_pair_variants": (ctypes.c_int, [ctypes.c_int]),
+            "swj_pair_variant_name": (ctypes.c_char_p, [ctypes.c_int, ctypes.c_int]),
             "swj_pair_config": (ctypes.c_int, [_vp, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_int),
                                                P(ctypes.c_int), P(ctypes.c_int)]),
             "swj_set_pair_config": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
@@ -158,6 +159,10 @@ def version() -> str:
 
 def pair_variants(precision) -> int:
     return int(lib().swj_pair_variants(int(precision)))
+
+
+def pair_variant_name(precision, variant) -> str:
+    return lib().swj_pair_variant_name(int(precision), int(variant)).decode()
 
 
 def kernel_launches() -> int:
