@@ -527,22 +527,25 @@ def run_residual_only(args):
         ctx.residual(u, E, swj.FP32)
         ctx.residual(u, E, swj.FP64)
         ctx.sync()
+        ctx.residual(u, E, swj.FF)
+        ctx.sync()
         out["tuned"] = {"fp32": ctx.pair_config(swj.FP32), "fp64": ctx.pair_config(swj.FP64)}
-        for prec in (swj.FP32, swj.FP64):
+        for prec in (swj.FP32, swj.FP64, swj.FF):
             for v in range(swj.pair_variants(prec)):
                 ctx.set_pair_config(prec, v)
                 ctx.residual(u, E, prec)
                 ctx.sync()
                 ctx.set_kernel_timing(True)
                 ctx.reset_pair_timing()
-                for _ in range(args.steps if prec == swj.FP32 else max(1, args.steps // 10)):
+                for _ in range(args.steps if prec != swj.FP64 else max(1, args.steps // 10)):
                     ctx.residual(u, E, prec)
                 ctx.sync()
                 ms, n = ctx.pair_timing(prec)
                 ctx.set_kernel_timing(False)
                 _, tpb, r, packed = ctx.pair_config(prec)
                 avg = ms / max(1, n)
-                row = {"precision": "fp32" if prec == swj.FP32 else "fp64", "variant": v, "threads": tpb,
+                row = {"precision": {swj.FP32: "fp32", swj.FP64: "fp64", swj.FF: "ff"}[prec], "variant": v,
+                       "name": swj.pair_variant_name(prec, v), "threads": tpb,
                        "targets_per_thread": r, "packed": packed, "avg_ms": avg,
                        "pairs_per_s": spec.pairs / (avg * 1e-3)}
                 if prec == swj.FP32:

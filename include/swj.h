@@ -56,6 +56,9 @@ extern "C" {
 #define SWJ_FP64 0   /* every step in IEEE double                                  */
 #define SWJ_FP32 1   /* all-pairs sum in FP32 with compensated accumulation; the   */
                      /* mesh step, per-target terms and assembly stay in FP64      */
+#define SWJ_FF   2   /* all-pairs sum in float-float: FP32 arithmetic with error-  */
+                     /* free transformations (~2^-44 relative, close to FP64), at  */
+                     /* FP32 speed; residual only (not swj_jvp)                    */
 
 /* ---- solve modes ---- */
 #define SWJ_SOLVE_FP64  0  /* Newton-GMRES with the FP64 residual throughout       */
@@ -94,6 +97,9 @@ typedef struct swj_opts {
     int    autotune;       /* 1: on the first FP32 residual of a mesh size, time      */
                            /* every compiled FP32 tile shape of the all-pairs kernel  */
                            /* and keep the fastest for the process (1)                */
+    int    refine_precision; /* MIXED: all-pairs precision of the refinement          */
+                           /* residuals: SWJ_FF (float-float, as accurate as FP64 and */
+                           /* ~8x faster on this GPU) or SWJ_FP64 (SWJ_FF)            */
 } swj_opts;
 
 /* Counters and timings of one solve (KINSOL-style counters). */
@@ -108,11 +114,14 @@ typedef struct swj_stats {
     int    line_search_cuts;     /* halvings of the Newton step                      */
     double final_norm_inf;       /* ||E||_inf at the returned u, in the precision    */
                                  /* of the last residual evaluated                   */
-    double final_norm_inf_fp64;  /* ||E_fp64||_inf at the returned u (-1 if never    */
-                                 /* evaluated)                                        */
+    double final_norm_inf_fp64;  /* ||E||_inf at the returned u with an FP64-accurate */
+                                 /* all-pairs sum (FP64, or float-float in MIXED mode */
+                                 /* with refine_precision SWJ_FF); -1 if never        */
     double t_total_ms;           /* wall time of swj_solve                           */
     double t_setup_ms;           /* preconditioner set-up                            */
     int    pairs_per_residual_hi, pairs_per_residual_lo;  /* (N-1)M*NM as 2x31 bits */
+    int    residual_evals_ff;    /* of which with the float-float all-pairs sum (the */
+                                 /* right-hand side of the MIXED refinement)         */
 } swj_stats;
 
 typedef struct swj_ctx swj_ctx;
@@ -177,7 +186,7 @@ size_t swj_footprint_bytes(const swj_mesh *mesh, int count, const swj_opts *opts
 int swj_initial_guess_flat(swj_ctx *ctx, double *u_dev);
 
 /* E_dev <- E(u_dev) (Section 3, Appendix A order), with the all-pairs sum in
- * `precision` (SWJ_FP64 or SWJ_FP32).  Steps: trapezoidal integration of
+ * `precision` (SWJ_FP64, SWJ_FP32 or SWJ_FF).  Steps: trapezoidal integration of
  * zeta and phi along x (Eq. zetaapprox), cubic-spline slopes along y
  * (clamped zero slope at y1 = 0, not-a-knot at y_M), half-mesh values,
  * E1 (Eq. freeSurfCond), the singularity-subtracted boundary integral with

@@ -529,6 +529,204 @@ k_pairs_r64(int T_, int S_, int chunk, int N, const SrcRec64 *__restrict__ src, 
     }
 }
 
+
+// ------------------------------------------------------------ float-float
+// A value is an unevaluated sum hi + lo of two floats with |lo| <= ulp(hi)/2
+// (about 48 significant bits).  The sums and products below are the classic
+// error-free transformations: Knuth's two-sum, Dekker's fast two-sum (for
+// |a| >= |b|) and the FMA-based exact product; every operation is an explicit
+// round-to-nearest intrinsic so that no FMA contraction can break them.  The
+// additions are the "sloppy" float-float sum (the error is bounded by
+// ~2^-44 (|a| + |b|), not by |a + b|), which is what the all-pairs sum needs:
+// its tolerance is relative to the sum of absolute terms.
+struct ff {
+    float h, l;
+};
+
+__device__ __forceinline__ ff ff_from(double d)
+{
+    const float h = __double2float_rn(d);
+    return {h, __double2float_rn(d - (double)h)};
+}
+
+__device__ __forceinline__ ff ff_fast2(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ ff ff_two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+
+__device__ __forceinline__ ff ff_add(ff a, ff b)
+{
+    const ff s = ff_two_sum(a.h, b.h);
+    return ff_fast2(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
+}
+
+__device__ __forceinline__ ff ff_addf(ff a, float b)   // b exact
+{
+    const ff s = ff_two_sum(a.h, b);
+    return ff_fast2(s.h, __fadd_rn(s.l, a.l));
+}
+
+// the accurate sum (both halves two-summed): for the running totals
+__device__ __forceinline__ ff ff_add_acc(ff a, ff b)
+{
+    const ff s = ff_two_sum(a.h, b.h);
+    const ff t = ff_two_sum(a.l, b.l);
+    const ff u = ff_fast2(s.h, __fadd_rn(s.l, t.h));
+    return ff_fast2(u.h, __fadd_rn(u.l, t.l));
+}
+
+__device__ __forceinline__ ff ff_neg(ff a) { return {-a.h, -a.l}; }
+
+__device__ __forceinline__ ff ff_mul(ff a, ff b)
+{
+    const float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    return ff_fast2(p, e);
+}
+
+__device__ __forceinline__ ff ff_mulf(ff a, float b)   // b exact
+{
+    const float p = __fmul_rn(a.h, b);
+    float e = __fmaf_rn(a.h, b, -p);
+    e = __fmaf_rn(a.l, b, e);
+    return ff_fast2(p, e);
+}
+
+// 1/sqrt(x): the FP32 hardware approximation y (relative error ~2^-23) and one
+// Newton step y (1 + (1 - x y^2) / 2), with x y^2 formed in float-float (its
+// first difference from 1 is exact), giving ~2^-46 relative.
+__device__ __forceinline__ ff ff_rsqrt(ff x)
+{
+    const float y = rsqrt_ftz(x.h);
+    const ff t = ff_mulf(ff_mulf(x, y), y);
+    const float r = __fsub_rn(__fsub_rn(1.0f, t.h), t.l);
+    return ff_fast2(y, __fmul_rn(__fmul_rn(0.5f, y), r));
+}
+
+// Source record of the float-float kernel (converted from the FP64 record when
+// staged): coordinates and fields split into hi + lo.
+struct __align__(16) SrcFF {
+    ff x, z, zx, zy, g, w, zxw, pad;
+};
+
+// The all-pairs sum in float-float, structured as k_pairs_r64 (source-row
+// terms hoisted; dy, dy' and their squares are exact small integers in units
+// of dy).  Running totals use the accurate sum every 64 sources.
+template <int R>
+__global__ void __launch_bounds__(128)
+k_pairs_ff(int T_, int S_, int chunk, int N, const SrcRec64 *__restrict__ src, TgtArrays64 tg,
+           double *__restrict__ partial, const int *__restrict__ act)
+{
+    constexpr int TILE = 256;
+    const int inst = blockIdx.z;
+    if (!SWJ_INST_ACTIVE(act, inst)) return;
+    {
+        const size_t ot = (size_t)inst * T_;
+        src += (size_t)inst * S_;
+        tg.x += ot; tg.y += ot; tg.zeta += ot; tg.g += ot; tg.zxw += ot; tg.A += ot; tg.B += ot; tg.C += ot;
+        partial += (size_t)inst * gridDim.y * T_;
+    }
+    __shared__ SrcFF sh[TILE];
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int s0 = blockIdx.y * chunk;
+    const int s1 = min(S_, s0 + chunk);
+    ff ntx[R], ntz[R], ntg[R], ntzw[R], A[R], B[R], C[R], sum[R];
+    float ty[R], dy[R], mdyp[R], dy2[R], dyp2[R];
+    ff Bdy[R], mBdyp[R], Cdy2[R], Cdyp2[R];
+    const int tb = blockIdx.x * R * nth + tid;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int t = min(tb + r * nth, T_ - 1);
+        ntx[r] = ff_from(-tg.x[t]); ty[r] = (float)tg.y[t]; ntz[r] = ff_from(-tg.zeta[t]);
+        ntg[r] = ff_from(-tg.g[t]); ntzw[r] = ff_from(-tg.zxw[t]);
+        A[r] = ff_from(tg.A[t]); B[r] = ff_from(tg.B[t]); C[r] = ff_from(tg.C[t]);
+        sum[r] = {0.f, 0.f};
+    }
+    int row = -1;
+    for (int base = s0; base < s1; base += TILE) {
+        const int nt = min(TILE, s1 - base);
+        __syncthreads();
+        for (int i = tid; i < nt; i += nth) {
+            const SrcRec64 q = src[base + i];
+            SrcFF r;
+            r.x = ff_from(q.x); r.z = ff_from(q.zeta); r.zx = ff_from(q.zx); r.zy = ff_from(q.zy);
+            r.g = ff_from(q.g); r.w = ff_from(q.w); r.zxw = ff_from(q.zxw); r.pad = {0.f, 0.f};
+            sh[i] = r;
+        }
+        __syncthreads();
+        int j = base / N;
+        int row_end = (j + 1) * N - base;
+        for (int sb = 0; sb < nt; sb += kSub) {
+            const int se = min(sb + kSub, nt);
+            ff loc[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) loc[r] = {0.f, 0.f};
+            int s = sb;
+            while (s < se) {
+                while (s >= row_end) { ++j; row_end += N; }
+                if (j != row) {
+                    row = j;
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        dy[r] = (float)j - ty[r];              // exact (integers)
+                        mdyp[r] = -(float)j - ty[r];            // -(y_j + y*)
+                        dy2[r] = dy[r] * dy[r];
+                        dyp2[r] = mdyp[r] * mdyp[r];
+                        Bdy[r] = ff_mulf(B[r], dy[r]);
+                        mBdyp[r] = ff_mulf(B[r], mdyp[r]);
+                        Cdy2[r] = ff_mulf(C[r], dy2[r]);
+                        Cdyp2[r] = ff_mulf(C[r], dyp2[r]);
+                    }
+                }
+                const int send = min(se, row_end);
+#pragma unroll 1
+                for (; s < send; ++s) {
+                    const SrcFF q = sh[s];
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const ff p = ff_add(q.x, ntx[r]);
+                        const ff dz = ff_add(q.z, ntz[r]);
+                        const ff bs = ff_add(ff_mul(p, p), ff_mul(dz, dz));
+                        const ff r1s = ff_addf(bs, dy2[r]);
+                        const ff r2s = ff_addf(bs, dyp2[r]);
+                        const ff nc = ff_add(dz, ff_neg(ff_mul(p, q.zx)));
+                        const ff n1 = ff_add(nc, ff_neg(ff_mulf(q.zy, dy[r])));
+                        const ff n2 = ff_add(nc, ff_mulf(q.zy, mdyp[r]));
+                        const ff i1 = ff_rsqrt(r1s), i2 = ff_rsqrt(r2s);
+                        const ff i1c = ff_mul(ff_mul(i1, i1), i1), i2c = ff_mul(ff_mul(i2, i2), i2);
+                        const ff K1 = ff_add(ff_mul(n1, i1c), ff_mul(n2, i2c));
+                        const ff K2 = ff_add(i1, i2);
+                        const ff Ap = ff_mul(A[r], p);
+                        const ff Q1 = ff_add(ff_mul(ff_add(Ap, Bdy[r]), p), Cdy2[r]);
+                        const ff Q2 = ff_add(ff_mul(ff_add(Ap, mBdyp[r]), p), Cdyp2[r]);
+                        const ff S2 = ff_add(ff_rsqrt(Q1), ff_rsqrt(Q2));
+                        const ff f = ff_add(q.g, ntg[r]);
+                        const ff inner = ff_add(ff_add(ff_mul(q.zxw, K2), ff_mul(f, K1)), ff_mul(ntzw[r], S2));
+                        loc[r] = ff_add(loc[r], ff_mul(q.w, inner));
+                    }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) sum[r] = ff_add_acc(sum[r], loc[r]);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int t = tb + r * nth;
+        if (t < T_) partial[(size_t)blockIdx.y * T_ + t] = (double)sum[r].h + (double)sum[r].l;
+    }
+}
+
 // Source-chunk count P for (tiles) target tiles: (tiles x P) blocks should fill
 // whole waves of `slots` resident blocks; chunks keep at least 64 sources.
 PairPlan make_plan(int T, int S, int slots, int tpb, int R, int v)
@@ -582,6 +780,14 @@ template <typename T, int R> struct ScalarLaunch<T, R, 128> {
                                            *(const TgtArraysS<T> *)tg, partial, act);
     }
 };
+
+template <int R>
+void launch_ff(dim3 g, cudaStream_t st, int T_, int S_, int chunk, int N, const void *src,
+               const void *tg, double *partial, const int *act)
+{
+    k_pairs_ff<R><<<g, 128, 0, st>>>(T_, S_, chunk, N, (const SrcRec64 *)src, *(const TgtArrays64 *)tg,
+                                     partial, act);
+}
 
 template <int R>
 void launch_r64(dim3 g, cudaStream_t st, int T_, int S_, int chunk, int N, const void *src,
@@ -639,15 +845,21 @@ const PairVariant kVar64[] = {
     {(const void *)k_pairs_s<double, 2>, 128, 2, ScalarLaunch<double, 2, 128>::go, "k_pairs_s<double,2>"},
     {(const void *)k_pairs_s<double, 4>, 128, 4, ScalarLaunch<double, 4, 128>::go, "k_pairs_s<double,4>"},
 };
+const PairVariant kVarFF[] = {
+    {(const void *)k_pairs_ff<2>, 128, 2, launch_ff<2>, "k_pairs_ff<2>"},
+    {(const void *)k_pairs_ff<1>, 128, 1, launch_ff<1>, "k_pairs_ff<1>"},
+    {(const void *)k_pairs_ff<4>, 128, 4, launch_ff<4>, "k_pairs_ff<4>"},
+};
 constexpr int kNVar32 = sizeof(kVar32) / sizeof(kVar32[0]);
 constexpr int kNVar64 = sizeof(kVar64) / sizeof(kVar64[0]);
+constexpr int kNVarFF = sizeof(kVarFF) / sizeof(kVarFF[0]);
 
 const PairVariant &variant(int precision, int v)
 {
-    return precision == SWJ_FP64 ? kVar64[v] : kVar32[v];
+    return precision == SWJ_FP64 ? kVar64[v] : (precision == SWJ_FF ? kVarFF[v] : kVar32[v]);
 }
 
-int n_variants(int precision) { return precision == SWJ_FP64 ? kNVar64 : kNVar32; }
+int n_variants(int precision) { return precision == SWJ_FP64 ? kNVar64 : (precision == SWJ_FF ? kNVarFF : kNVar32); }
 
 // tuned variant per (T, S, precision, SM count), shared by every context
 std::mutex g_tune_mutex;
@@ -678,7 +890,7 @@ PairPlan swj_pair_plan(const swj_ctx *c, int precision)
 int swj_pair_max_chunks(const swj_ctx *c)
 {
     int P = 1;
-    for (int prec = 0; prec < 2; ++prec)
+    for (int prec = 0; prec < 3; ++prec)
         for (int v = 0; v < n_variants(prec); ++v) {
             PairPlan pl = swj_pair_plan_variant(c, prec, v);
             if (pl.P > P) P = pl.P;
@@ -693,6 +905,9 @@ static void launch_plan(swj_ctx *c, const PairPlan &pl, int precision, const int
     if (precision == SWJ_FP64)
         kVar64[pl.v].launch(grid, c->stream, c->T, c->S, pl.chunk, c->N, c->src64, &c->tgt64, c->partial,
                             act);
+    else if (precision == SWJ_FF)
+        kVarFF[pl.v].launch(grid, c->stream, c->T, c->S, pl.chunk, c->N, c->src64, &c->tgt64, c->partial,
+                            act);
     else
         kVar32[pl.v].launch(grid, c->stream, c->T, c->S, pl.chunk, c->N, c->src32, &c->tgt32, c->partial,
                             act);
@@ -702,6 +917,7 @@ static void launch_plan(swj_ctx *c, const PairPlan &pl, int precision, const int
 // of the single-instance plan, so its result does not depend on the batch.
 void swj_launch_pairs64(swj_ctx *c, const PairPlan &pl, const int *act) { launch_plan(c, pl, SWJ_FP64, act); }
 void swj_launch_pairs32(swj_ctx *c, const PairPlan &pl, const int *act) { launch_plan(c, pl, SWJ_FP32, act); }
+void swj_launch_pairs_ff(swj_ctx *c, const PairPlan &pl, const int *act) { launch_plan(c, pl, SWJ_FF, act); }
 
 // Pick the context's plan for `precision`: the variant already tuned for this
 // mesh size, else (FP32, autotune on, stream not capturing) time every variant on
@@ -709,9 +925,9 @@ void swj_launch_pairs32(swj_ctx *c, const PairPlan &pl, const int *act) { launch
 // three) and keep the fastest for the whole process.
 int swj_pair_autotune(swj_ctx *c, int precision, const int *act)
 {
-    int &done = precision == SWJ_FP64 ? c->tuned64 : c->tuned32;
+    int &done = swj_tuned_of(c, precision);
     if (done) return SWJ_OK;
-    PairPlan &plan = precision == SWJ_FP64 ? c->plan64 : c->plan32;
+    PairPlan &plan = swj_plan_of(c, precision);
     int v = tuned_variant(c, precision);
     // FP64 shapes differ by a few percent while timing them costs a dozen FP64
     // residuals: only the FP32 kernel is tuned, FP64 takes its default shape
@@ -756,13 +972,13 @@ int swj_pair_autotune(swj_ctx *c, int precision, const int *act)
 
 const char *swj_pair_variant_name(int precision, int v)
 {
-    if ((precision != SWJ_FP64 && precision != SWJ_FP32) || v < 0 || v >= n_variants(precision)) return "";
+    if (!swj_valid_precision(precision) || v < 0 || v >= n_variants(precision)) return "";
     return variant(precision, v).name;
 }
 
 int swj_pair_variant_info(int precision, int v, int *tpb, int *R, int *packed)
 {
-    if (precision != SWJ_FP64 && precision != SWJ_FP32) return SWJ_EINVAL;
+    if (!swj_valid_precision(precision)) return SWJ_EINVAL;
     if (v < 0 || v >= n_variants(precision)) return SWJ_EINVAL;
     const PairVariant &pv = variant(precision, v);
     if (tpb) *tpb = pv.tpb;

@@ -19,8 +19,9 @@
 //    the GMRES tolerance is the Eisenstat-Walker forcing term (choice 1 with
 //    its safeguard), kept in [eta_min, eta_max].
 //  * MIXED mode: Newton on the FP32-sum residual until it reaches its noise
-//    floor, then Newton steps on the FP64 residual whose linear solves use
-//    FP32 JVPs (a defect correction: the root is the FP64 one).
+//    floor, then Newton steps on an FP64-accurate residual (the float-float or
+//    the FP64 all-pairs sum) whose linear solves use FP32 JVPs (a defect
+//    correction: the root is the FP64 one).
 // Instances advance in lock step; a per-instance flag array on the device
 // masks those that have finished (or whose GMRES has converged), so every
 // launch keeps its shape.
@@ -165,6 +166,7 @@ void count_residual(swj_stats *st, const std::vector<int> &mask, int prec)
         if (mask[i]) {
             st[i].residual_evals++;
             if (prec == SWJ_FP64) st[i].residual_evals_fp64++;
+            if (prec == SWJ_FF) st[i].residual_evals_ff++;
         }
 }
 
@@ -536,7 +538,8 @@ int newton_phase(swj_ctx *c, double *u, int prec, double tol, int max_it, Phase 
             }
             if (o.verbose)
                 fprintf(stderr, "[swj] %s inst=%d it=%d |E|inf=%.3e |E|2=%.3e lam=%.3g gmres=%d eta=%.2e\n",
-                        refine ? "refine fp64" : (prec == SWJ_FP64 ? "newton fp64" : "newton fp32"),
+                        refine ? (prec == SWJ_FF ? "refine ff" : "refine fp64")
+                               : (prec == SWJ_FP64 ? "newton fp64" : "newton fp32"),
                         i, it + 1, ti[i], tn[i], lam[i], giters[i], eta[i]);
             if (stop_on_stall && ti[i] > 0.5 * prev && ti[i] < 100.0 * tol) ph.status[i] = SWJ_OK;
         }
@@ -549,19 +552,20 @@ int newton_phase(swj_ctx *c, double *u, int prec, double tol, int max_it, Phase 
 int swj_residual_impl(swj_ctx *c, const double *u, double *E, int precision, const int *act)
 {
     swj_launch_mesh_step(c, u, E, act);
-    if (!(precision == SWJ_FP64 ? c->tuned64 : c->tuned32)) {
+    if (!swj_tuned_of(c, precision)) {
         int rc = swj_pair_autotune(c, precision, act);
         if (rc) return rc;
     }
     const bool rec = c->time_pairs && c->tev && c->n_timed < SWJ_MAX_TIMED;
     if (rec) cudaEventRecord(c->tev[2 * c->n_timed], c->stream);
     if (precision == SWJ_FP64) swj_launch_pairs64(c, c->plan64, act);
+    else if (precision == SWJ_FF) swj_launch_pairs_ff(c, c->planff, act);
     else swj_launch_pairs32(c, c->plan32, act);
     if (rec) {
         cudaEventRecord(c->tev[2 * c->n_timed + 1], c->stream);
         c->tev_prec[c->n_timed++] = precision;
     }
-    swj_launch_assemble(c, E, precision == SWJ_FP64 ? c->plan64.P : c->plan32.P, act);
+    swj_launch_assemble(c, E, swj_plan_of(c, precision).P, act);
     SWJ_CUDA_TRY(cudaGetLastError());
     return SWJ_OK;
 }
@@ -683,9 +687,10 @@ int swj_solve_impl(swj_ctx *c, double *u, swj_stats *stats)
     }
     rc = set_mask(c, go);
     if (rc) return finish(rc);
-    rc = swj_residual_impl(c, u, c->E_cur, SWJ_FP64, c->act_d);
+    const int rprec = o.refine_precision;   // FP64-accurate: float-float or FP64
+    rc = swj_residual_impl(c, u, c->E_cur, rprec, c->act_d);
     if (rc) return finish(rc);
-    count_residual(st, go, SWJ_FP64);
+    count_residual(st, go, rprec);
     Norms e64;
     rc = norms_of(c, c->E_cur, DS_NE, &e64, c->act_d);
     if (rc) return finish(rc);
@@ -694,7 +699,7 @@ int swj_solve_impl(swj_ctx *c, double *u, swj_stats *stats)
         rf.finf[i] = e64.inf[i];
         rf.f2[i] = e64.two[i];
     }
-    rc = newton_phase(c, u, SWJ_FP64, o.refine_tol_inf, o.refine_max, rf, st, false, true);
+    rc = newton_phase(c, u, rprec, o.refine_tol_inf, o.refine_max, rf, st, false, true);
     if (rc) return finish(rc);
     for (int i = 0; i < nb; ++i) {
         if (go[i]) {

@@ -26,6 +26,7 @@ bool valid_opts(const swj_opts *o)
     if (!(o->eta_min > 0.0) || o->eta_min > o->eta_max) return false;
     if (o->fd_h < 0.0 || !(o->mixed_tol_inf > 0.0) || !(o->refine_tol_inf > 0.0)) return false;
     if (o->autotune != 0 && o->autotune != 1) return false;
+    if (o->refine_precision != SWJ_FF && o->refine_precision != SWJ_FP64) return false;
     return true;
 }
 
@@ -90,6 +91,7 @@ int alloc_all(swj_ctx *c)
     c->tgt32 = TgtArrays32{f, f + NT, f + 2 * NT, f + 3 * NT, f + 4 * NT, f + 5 * NT, f + 6 * NT, f + 7 * NT};
     c->plan64 = swj_pair_plan(c, SWJ_FP64);
     c->plan32 = swj_pair_plan(c, SWJ_FP32);
+    c->planff = swj_pair_plan(c, SWJ_FF);
     // room for the partial sums of every compiled tile shape (the autotuner tries them all)
     const int P = swj_pair_max_chunks(c);
     c->partial_cap = (size_t)P * T * nb;
@@ -227,6 +229,7 @@ void swj_default_opts(swj_opts *o)
     o->refine_tol_inf = 1e-9;
     o->verbose = 0;
     o->autotune = 1;
+    o->refine_precision = SWJ_FF;
 }
 
 int swj_create(swj_ctx **out, const swj_mesh *mesh, double F, double eps, const swj_opts *opts,
@@ -320,22 +323,22 @@ int swj_pair_variants(int precision)
 int swj_pair_config(const swj_ctx *c, int precision, int *variant, int *threads, int *targets,
                     int *packed)
 {
-    if (!c || (precision != SWJ_FP64 && precision != SWJ_FP32)) return SWJ_EINVAL;
-    const PairPlan &pl = precision == SWJ_FP64 ? c->plan64 : c->plan32;
+    if (!c || !swj_valid_precision(precision)) return SWJ_EINVAL;
+    const PairPlan &pl = swj_plan_of(const_cast<swj_ctx *>(c), precision);
     if (variant) *variant = pl.v;
     return swj_pair_variant_info(precision, pl.v, threads, targets, packed);
 }
 
 int swj_set_pair_config(swj_ctx *c, int precision, int variant)
 {
-    if (!c || (precision != SWJ_FP64 && precision != SWJ_FP32)) return SWJ_EINVAL;
+    if (!c || !swj_valid_precision(precision)) return SWJ_EINVAL;
     if (swj_pair_variant_info(precision, variant, nullptr, nullptr, nullptr) != SWJ_OK) return SWJ_EINVAL;
     PairPlan pl = swj_pair_plan_variant(c, precision, variant);
     if ((size_t)pl.P * c->T * c->nb > c->partial_cap) return SWJ_EINVAL;
     SWJ_CUDA_TRY(cudaStreamSynchronize(c->stream));
     swj_graphs_free(c);   // captured steps bake in the old plan
-    if (precision == SWJ_FP64) { c->plan64 = pl; c->tuned64 = 1; }
-    else { c->plan32 = pl; c->tuned32 = 1; }
+    swj_plan_of(c, precision) = pl;
+    swj_tuned_of(c, precision) = 1;
     return SWJ_OK;
 }
 
@@ -360,7 +363,7 @@ int swj_initial_guess_flat(swj_ctx *c, double *u)
 int swj_residual(swj_ctx *c, const double *u, double *E, int precision)
 {
     if (!c || !u || !E || u == E) return SWJ_EINVAL;
-    if (precision != SWJ_FP64 && precision != SWJ_FP32) return SWJ_EINVAL;
+    if (!swj_valid_precision(precision)) return SWJ_EINVAL;
     return swj_residual_impl(c, u, E, precision, nullptr);
 }
 

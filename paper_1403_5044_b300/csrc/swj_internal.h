@@ -91,8 +91,8 @@ struct swj_ctx {
     // partial sums [nb][P][T]
     double *partial;
     size_t partial_cap;   // doubles
-    PairPlan plan64, plan32;
-    int tuned64, tuned32;   // plan settled (autotuned or taken from the process cache)
+    PairPlan plan64, plan32, planff;
+    int tuned64, tuned32, tunedff;   // plan settled (autotuned or taken from the process cache)
 
     // JVP / solver temporaries, [nb][nu]
     double *u_tmp, *E_tmp;           // JVP: u + h v and E(u + h v)
@@ -142,6 +142,16 @@ struct swj_ctx {
 
 enum { SWJ_DS = 512, SWJ_RED = 64 * 64 + 1024 };
 
+inline bool swj_valid_precision(int p) { return p == SWJ_FP64 || p == SWJ_FP32 || p == SWJ_FF; }
+inline PairPlan &swj_plan_of(swj_ctx *c, int prec)
+{
+    return prec == SWJ_FP64 ? c->plan64 : (prec == SWJ_FF ? c->planff : c->plan32);
+}
+inline int &swj_tuned_of(swj_ctx *c, int prec)
+{
+    return prec == SWJ_FP64 ? c->tuned64 : (prec == SWJ_FF ? c->tunedff : c->tuned32);
+}
+
 // ---------------------------------------------------------------- launches
 // mesh.cu (act: device per-instance flags or nullptr for all)
 void swj_launch_mesh_step(swj_ctx *c, const double *u, double *E, const int *act);
@@ -160,6 +170,7 @@ int swj_pair_autotune(swj_ctx *c, int precision, const int *act);
 int swj_pair_variant_info(int precision, int v, int *tpb, int *R, int *packed);
 void swj_launch_pairs64(swj_ctx *c, const PairPlan &pl, const int *act);
 void swj_launch_pairs32(swj_ctx *c, const PairPlan &pl, const int *act);
+void swj_launch_pairs_ff(swj_ctx *c, const PairPlan &pl, const int *act);
 
 // linalg.cu: batched vector operations on nb vectors of length n at stride ld
 // (one instance per grid row; act: per-instance flags or nullptr), with

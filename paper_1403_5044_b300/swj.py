@@ -18,7 +18,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "swj.h")
 OK, EINVAL, ENOMEM, ECUDA, ENOTCONV, ELINESEARCH, EGMRES, ENAN, ETIMEOUT, ESINGULAR, ESIZE = \
     0, -1, -2, -3, -4, -5, -6, -7, -8, -9, -10
 PENDING = 1
-FP64, FP32 = 0, 1
+FP64, FP32, FF = 0, 1, 2
 SOLVE_FP64, SOLVE_MIXED = 0, 1
 
 
@@ -40,7 +40,7 @@ class Opts(ctypes.Structure):
                 ("eta_max", ctypes.c_double), ("eta_min", ctypes.c_double),
                 ("fd_h", ctypes.c_double), ("refine_max", ctypes.c_int),
                 ("mixed_tol_inf", ctypes.c_double), ("refine_tol_inf", ctypes.c_double),
-                ("verbose", ctypes.c_int), ("autotune", ctypes.c_int)]
+                ("verbose", ctypes.c_int), ("autotune", ctypes.c_int), ("refine_precision", ctypes.c_int)]
 
 
 class ServerOpts(ctypes.Structure):
@@ -72,7 +72,8 @@ class Stats(ctypes.Structure):
                 ("precond_applies", ctypes.c_int), ("line_search_cuts", ctypes.c_int),
                 ("final_norm_inf", ctypes.c_double), ("final_norm_inf_fp64", ctypes.c_double),
                 ("t_total_ms", ctypes.c_double), ("t_setup_ms", ctypes.c_double),
-                ("pairs_per_residual_hi", ctypes.c_int), ("pairs_per_residual_lo", ctypes.c_int)]
+                ("pairs_per_residual_hi", ctypes.c_int), ("pairs_per_residual_lo", ctypes.c_int),
+                ("residual_evals_ff", ctypes.c_int)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}

@@ -22,6 +22,7 @@ pytestmark = pytest.mark.gpu
 
 TOL64 = 1e-12
 TOL32 = 2e-6
+TOLFF = 1e-12   # float-float (~2^-44 per operation): the FP64 tolerance; measured 3e-15
 
 
 def omesh(spec):
@@ -76,7 +77,7 @@ def test_residual_fp32_matches_oracle(spec, F, eps, seed, amp):
 
 
 @pytest.mark.parametrize("spec,F,eps,seed,amp", [CASES[2], CASES[4]])
-@pytest.mark.parametrize("prec", [swj.FP64, swj.FP32])
+@pytest.mark.parametrize("prec", [swj.FP64, swj.FP32, swj.FF])
 def test_every_tile_shape_matches_oracle(spec, F, eps, seed, amp, prec):
     """Each compiled tile shape of the all-pairs kernel (the autotuner's
     candidates, packed FP32 pair instructions included), pinned in turn."""
@@ -93,7 +94,7 @@ def test_every_tile_shape_matches_oracle(spec, F, eps, seed, amp, prec):
             ctx.residual(ud, Ed, prec)
             ctx.sync()
             err = np.abs(Ed.cpu().numpy() - Eo) / scale
-            assert err.max() <= (TOL64 if prec == swj.FP64 else TOL32), (v, err.max())
+            assert err.max() <= {swj.FP64: TOL64, swj.FP32: TOL32, swj.FF: TOLFF}[prec], (v, err.max())
 
 
 def test_autotuned_shape_is_shared_by_contexts_of_one_mesh_size():
@@ -109,12 +110,21 @@ def test_autotuned_shape_is_shared_by_contexts_of_one_mesh_size():
     assert cfg[0] == cfg[1]
 
 
-def test_residual_181x61_both_precisions():
+@pytest.mark.parametrize("spec,F,eps,seed,amp", CASES)
+def test_residual_ff_matches_oracle(spec, F, eps, seed, amp):
+    u = W.random_state(spec, seed=seed, amp=amp)
+    Eo, scale, _ = oracle_E_and_scale(spec, F, eps, u)
+    Eg = gpu_residual(spec, F, eps, u, swj.FF)
+    err = np.abs(Eg - Eo) / scale
+    assert err.max() <= TOLFF, (err.max(), int(err.argmax()))
+
+
+def test_residual_181x61_every_precision():
     """The 181x61, F = 0.7, eps = 0.4 workload, every row."""
     spec, F, eps = W.SOLVE_181x61
     u = W.random_state(spec, seed=11, amp=0.08)
     Eo, scale, _ = oracle_E_and_scale(spec, F, eps, u)
-    for prec, tol in ((swj.FP64, TOL64), (swj.FP32, TOL32)):
+    for prec, tol in ((swj.FP64, TOL64), (swj.FP32, TOL32), (swj.FF, TOLFF)):
         err = np.abs(gpu_residual(spec, F, eps, u, prec) - Eo) / scale
         assert err.max() <= tol, (prec, err.max())
 

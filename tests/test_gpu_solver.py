@@ -115,6 +115,22 @@ def test_181x61_mixed_and_fp64_solves_agree_and_are_oracle_roots():
     assert z64.max() < F ** 2 / 2
 
 
+def test_refinement_precisions_reach_the_same_root():
+    """MIXED solves refined with float-float and with FP64 residuals: the same
+    FP64 root (the float-float sum is as accurate as FP64), both roots of the
+    oracle residual."""
+    spec, F, eps = W.SOLVE_181x61
+    m = omesh(spec)
+    uf, zf, sf = gpu_solve(spec, F, eps, solve_mode="mixed", block_bw=11, refine_precision=swj.FF)
+    u6, z6, s6 = gpu_solve(spec, F, eps, solve_mode="mixed", block_bw=11, refine_precision=swj.FP64)
+    assert sf["rc"] == 0 and s6["rc"] == 0, (sf, s6)
+    assert sf["residual_evals_ff"] >= 1 and sf["residual_evals_fp64"] == 0
+    assert s6["residual_evals_fp64"] >= 1 and s6["residual_evals_ff"] == 0
+    assert np.abs(zf - z6).max() <= 1e-8
+    assert np.abs(O.residual(m, F, eps, uf)).max() < 1e-8
+    assert np.abs(O.residual(m, F, eps, u6)).max() < 1e-8
+
+
 def test_solve_reports_nan():
     spec = W.MeshSpec(9, 5, -2.0, 0.5, 0.4)
     with swj.Context.from_spec(spec, 0.7, 0.1, solve_mode="fp64") as ctx:
