@@ -85,6 +85,9 @@ def parse():
                     help="only the serving workload: 2000 Poisson requests per rate, rates swept over "
                          "{0.25, 0.5, 0.75, 1.0, 1.25} x the measured saturated rate, mixed and FP64")
     ap.add_argument("--serve-rates", default="0.25,0.5,0.75,1.0,1.25")
+    ap.add_argument("--large", action="store_true",
+                    help="only the 721x241 workload (F = 0.7, eps = 0.8): one mixed solve from the flat "
+                         "guess, reported with its counters (minutes)")
     ap.add_argument("--batch-steps", type=int, default=2,
                     help="timed steps of the 64 x 121x41 batched workload (0 = skip it)")
     ap.add_argument("--mesh", default="181x61",
@@ -510,6 +513,47 @@ def run_serve(args):
     print(json.dumps(out), flush=True)
 
 
+def run_large(args):
+    """The 721x241 workload: F = 0.7, eps = 0.8 (a steep, near-limiting wave),
+    mixed precision with FP64 GMRES/LU and a float-float refinement, from the
+    flat guess; falls back to eps-continuation 0.2, 0.4, 0.6, 0.8 (Section 5)
+    if the direct solve fails."""
+    import torch
+    from paper_1403_5044_b300 import swj
+    from paper_1403_5044_b300 import workloads as W
+    spec, F, eps = W.SOLVE_721x241
+    out = {"large": True, "workload": "ship-wave solve 721x241, F=0.7, eps=0.8 (x in [-16,20], y in [0,12], dx=dy=0.05)",
+           "pairs_per_residual": spec.pairs, "block_bw": args.block_bw}
+    with swj.Context.from_spec(spec, F, eps, solve_mode="mixed", block_bw=args.block_bw) as ctx:
+        u = ctx.initial_guess_flat(ctx.vector())
+        out["workspace_bytes"] = ctx.workspace_bytes()
+        t0 = time.perf_counter()
+        ctx.precond_setup()
+        ctx.sync()
+        out["setup_s"] = time.perf_counter() - t0
+        path = [eps]
+        st = ctx.solve(u, check=False)
+        if st["rc"] != swj.OK:
+            path = [0.2, 0.4, 0.6, 0.8]
+            ctx.initial_guess_flat(u)
+            for e in path:
+                ctx.set_params(F, e)
+                st = ctx.solve(u, check=False)
+                if st["rc"] != swj.OK:
+                    break
+        out["total_s"] = time.perf_counter() - t0
+        out["eps_path"] = path
+        out["solve_stats"] = {k: st[k] for k in ("rc", "newton_iters", "refine_iters", "residual_evals",
+                                                 "residual_evals_ff", "krylov_iters", "final_norm_inf_fp64",
+                                                 "t_total_ms")}
+        z = torch.empty(spec.N * spec.M, dtype=torch.float64, device="cuda")
+        ctx.unpack(u, z, None)
+        ctx.sync()
+        out["max_zeta"] = float(z.max().item())
+        out["crest_bound_F2_over_2"] = F * F / 2
+    print(json.dumps(out), flush=True)
+
+
 def run_residual_only(args):
     """Residuals of the 181x61 workload only: every compiled tile shape of the
     all-pairs kernel pinned in turn, `steps` timed launches each (plus the
@@ -587,7 +631,11 @@ def run_precond_only(args):
 
 def main():
     args = parse()
-    if args.serve:
+    if args.large:
+        if args.block_bw == BLOCK_BW:
+            args.block_bw = 7
+        run_large(args)
+    elif args.serve:
         if args.serve_requests == 64:
             args.serve_requests = 2000
         run_serve(args)
