@@ -214,6 +214,12 @@ int swj_precond_setup(swj_ctx *ctx);
  * had to build P). */
 int swj_precond_apply(swj_ctx *ctx, const double *b_dev, double *r_dev);
 
+/* Clusters the block substitution of the apply runs on: h (the block half
+ * bandwidth) when a single-instance context spreads it over one critical and
+ * h - 1 helper clusters, 1 for one cluster per instance, 0 before the
+ * preconditioner is built.  Both give identical results. */
+int swj_precond_sweep_clusters(const swj_ctx *ctx);
+
 /* Solve E(u) = 0 by damped inexact Newton (Section 4.1) with right-
  * preconditioned restarted GMRES and FD Jacobian-vector products
  * (Eq. JvApprox), starting from u_dev_inout; on return it holds the last
@@ -324,7 +330,8 @@ int swj_server_drain(swj_server *srv);
 void swj_server_destroy(swj_server *srv);
 
 /* Block until the context's stream is idle; returns SWJ_ECUDA if a kernel
- * failed. */
+ * failed, SWJ_ETIMEOUT if a bounded device-side wait of the preconditioner
+ * apply gave up since the last set-up. */
 int swj_sync(swj_ctx *ctx);
 
 /* Human-readable name of a status code (static storage). */

@@ -1,11 +1,12 @@
-// Thread-block-cluster kernels of the preconditioner (FP64).
+// Gauss-Jordan inverses of the diagonal blocks of the preconditioner (FP64),
+// on thread-block clusters.
 //
 // B300 issues about two FP64 FMAs per clock per SM, so a dense block
 // operation on one CTA is slow; these kernels spread each sequential
-// factorisation / substitution over the CTAs of one cluster and exchange the
-// little data that must be shared (a pivot column, the index of the pivot
-// row) through distributed shared memory, with the hardware cluster barrier
-// as the only synchronisation.  No kernel here spins on a flag.
+// elimination over the CTAs of one cluster and exchange the little data that
+// must be shared (a pivot column, the index of the pivot row) through
+// distributed shared memory.  The pipelined kernel also spins on per-step
+// flags in shared memory, every spin with an iteration limit.
 #include "swj_internal.h"
 #include <map>
 #include <mutex>
@@ -16,7 +17,6 @@ namespace cg = cooperative_groups;
 namespace {
 
 constexpr int kGJThreads = 256;
-constexpr int kSweepThreads = 512;
 
 // Gauss-Jordan inverse with partial (row) pivoting of one n x n row-major
 // block per cluster.  `work` holds the matrix and is overwritten; the inverse
@@ -393,123 +393,6 @@ k_gj_pipe(int n, const double *in_base, size_t istride, double *out_base, size_t
     cl.sync();
 }
 
-// Dot products of one row of up to `nt` n1 x n1 blocks with staged vectors,
-// one warp per row.  KC = ceil(n1 / 32) column chunks per lane are loaded
-// with independent, fully unrolled loads (two blocks per pass) so that the
-// warp keeps 2 KC loads in flight instead of one dependent load at a time.
-template <int KC>
-__device__ __forceinline__ double row_dots(const double *__restrict__ base, size_t bstride,
-                                           const double *__restrict__ vs, int nt, int n1, int lane)
-{
-    double a0 = 0.0, a1 = 0.0;
-    int q = 0;
-    for (; q + 1 < nt; q += 2) {
-        const double *L0 = base + (size_t)q * bstride, *L1 = L0 + bstride;
-        const double *v0 = vs + (size_t)q * n1, *v1 = v0 + n1;
-        double x0[KC], x1[KC];
-#pragma unroll
-        for (int k = 0; k < KC; ++k) {
-            int c = lane + 32 * k;
-            x0[k] = (c < n1) ? __ldg(L0 + c) : 0.0;
-            x1[k] = (c < n1) ? __ldg(L1 + c) : 0.0;
-        }
-#pragma unroll
-        for (int k = 0; k < KC; ++k) {
-            int c = lane + 32 * k;
-            if (c < n1) {
-                a0 = fma(x0[k], v0[c], a0);
-                a1 = fma(x1[k], v1[c], a1);
-            }
-        }
-    }
-    if (q < nt) {
-        const double *L0 = base + (size_t)q * bstride;
-        const double *v0 = vs + (size_t)q * n1;
-        double x0[KC];
-#pragma unroll
-        for (int k = 0; k < KC; ++k) {
-            int c = lane + 32 * k;
-            x0[k] = (c < n1) ? __ldg(L0 + c) : 0.0;
-        }
-#pragma unroll
-        for (int k = 0; k < KC; ++k) {
-            int c = lane + 32 * k;
-            if (c < n1) a0 = fma(x0[k], v0[c], a0);
-        }
-    }
-    double s = a0 + a1;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    return s;
-}
-
-// One cluster solves S x = t with the block-banded LU factors of S:
-// `band` ([M][2h+1][n1][n1]) holds inv_i in slot h of row i and the blocks
-// S_ij (j < i, as they were at step j) in the slots left of it; `W`
-// ([M][h][n1][n1]) holds W_ik = inv_i S_ik (k > i).
-//   forward   y_i = t_i - sum_{j=i-h}^{i-1} S_ij z_j  (y overwrites t),  z_i = inv_i y_i
-//   backward  x_i = z_i - sum_{k=i+1}^{i+h} W_ik x_k
-// Each CTA computes a slice of the rows of every block step (a warp per
-// row); the vectors a step reads are staged in shared memory after the
-// cluster barrier that ends the previous phase.
-template <int KC>
-__global__ void __launch_bounds__(kSweepThreads)
-k_band_sweep(int n1, int M, int h, const double *__restrict__ band, size_t band_stride,
-             const double *__restrict__ W, size_t w_stride, double *y, double *z, double *x,
-             size_t vec_stride, const int *__restrict__ act)
-{
-    cg::cluster_group cl = cg::this_cluster();
-    const int ncta = (int)cl.num_blocks();
-    const int rank = (int)cl.block_rank();
-    const int inst = blockIdx.x / ncta;
-    if (!SWJ_INST_ACTIVE(act, inst)) return;   // the whole cluster leaves together
-    band += (size_t)inst * band_stride;
-    W += (size_t)inst * w_stride;
-    y += (size_t)inst * vec_stride;
-    z += (size_t)inst * vec_stride;
-    x += (size_t)inst * vec_stride;
-    const int nb = 2 * h + 1;
-    const size_t n2 = (size_t)n1 * n1;
-    const int rows = (n1 + ncta - 1) / ncta;
-    const int r0 = rank * rows, r1 = min(n1, r0 + rows);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    extern __shared__ double vs[];   // up to max(h, 1) x n1 staged vectors
-    for (int i = 0; i < M; ++i) {
-        const int j0 = max(0, i - h), nt = i - j0;
-        if (nt > 0) {
-            for (int e = threadIdx.x; e < nt * n1; e += blockDim.x)
-                vs[e] = z[(size_t)(j0 + e / n1) * n1 + e % n1];
-            __syncthreads();
-            for (int r = r0 + warp; r < r1; r += nw) {
-                const double *L = band + ((size_t)i * nb + (j0 - i + h)) * n2 + (size_t)r * n1;
-                double s = row_dots<KC>(L, n2, vs, nt, n1, lane);
-                if (lane == 0) y[(size_t)i * n1 + r] -= s;
-            }
-            cl.sync();
-        }
-        for (int e = threadIdx.x; e < n1; e += blockDim.x) vs[e] = y[(size_t)i * n1 + e];
-        __syncthreads();
-        for (int r = r0 + warp; r < r1; r += nw) {
-            const double *Inv = band + ((size_t)i * nb + h) * n2 + (size_t)r * n1;
-            double s = row_dots<KC>(Inv, n2, vs, 1, n1, lane);
-            if (lane == 0) z[(size_t)i * n1 + r] = s;
-        }
-        cl.sync();
-    }
-    for (int i = M - 1; i >= 0; --i) {
-        const int k1 = min(M - 1, i + h), nt = k1 - i;
-        for (int e = threadIdx.x; e < nt * n1; e += blockDim.x)
-            vs[e] = x[(size_t)(i + 1 + e / n1) * n1 + e % n1];
-        __syncthreads();
-        for (int r = r0 + warp; r < r1; r += nw) {
-            const double *Wm = W + ((size_t)i * h) * n2 + (size_t)r * n1;
-            double s = row_dots<KC>(Wm, n2, vs, nt, n1, lane);
-            if (lane == 0) x[(size_t)i * n1 + r] = z[(size_t)i * n1 + r] - s;
-        }
-        cl.sync();
-    }
-}
-
 // 16 CTAs per cluster where the device runs such clusters (a non-portable
 // size), else the portable 8.
 // (The kernel's dynamic shared-memory limit is raised to `smem` first: the
@@ -645,51 +528,8 @@ int swj_gj_inverse_cluster(cudaStream_t st, int n, int count, double *work, size
     return SWJ_OK;
 }
 
-// Cluster size and shared-memory limit of the sweep kernel are settled on the
-// first call with prepare = true (from the preconditioner set-up), so that a
-// launch recorded into a CUDA graph makes no attribute call.
-template <int KC>
-int launch_sweep(cudaStream_t st, int nb, int n1, int M, int h, const double *band, size_t bs,
-                 const double *W, size_t ws, double *y, double *z, double *x, size_t vs, const int *act,
-                 bool prepare)
+int swj_cluster_for(const void *kern, int threads, size_t smem)
 {
-    const size_t smem = (size_t)(h > 0 ? h : 1) * n1 * sizeof(double);
-    int cs;
-    {
-        std::lock_guard<std::mutex> lock(g_attr_mutex);
-        cs = cluster_for((const void *)k_band_sweep<KC>, kSweepThreads, smem);
-    }
-    if (prepare) return SWJ_OK;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(cs * nb);
-    cfg.blockDim = dim3(kSweepThreads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = cs;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    SWJ_COUNT_LAUNCH();
-    SWJ_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_band_sweep<KC>, n1, M, h, band, bs, W, ws, y, z, x, vs, act));
-    return SWJ_OK;
-}
-
-int swj_band_sweep_cluster(cudaStream_t st, int nb, int n1, int M, int h, const double *band,
-                           size_t bs, const double *W, size_t ws, double *y, double *z, double *x,
-                           size_t vs, const int *act, bool prepare)
-{
-    const int kc = (n1 + 31) / 32;
-#define SWJ_SWEEP(K) return launch_sweep<K>(st, nb, n1, M, h, band, bs, W, ws, y, z, x, vs, act, prepare)
-    if (kc <= 2) SWJ_SWEEP(2);
-    if (kc <= 4) SWJ_SWEEP(4);
-    if (kc <= 6) SWJ_SWEEP(6);
-    if (kc <= 8) SWJ_SWEEP(8);
-    if (kc <= 12) SWJ_SWEEP(12);
-    if (kc <= 16) SWJ_SWEEP(16);
-    if (kc <= 24) SWJ_SWEEP(24);
-    SWJ_SWEEP(32);
-#undef SWJ_SWEEP
+    std::lock_guard<std::mutex> lock(g_attr_mutex);
+    return cluster_for(kern, threads, smem);
 }

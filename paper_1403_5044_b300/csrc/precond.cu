@@ -229,26 +229,6 @@ __global__ void k_copy_blocks(size_t n, const double *__restrict__ src, size_t s
         dst[(size_t)b * dstride + e] = src[(size_t)b * sstride + e];
 }
 
-// x_l = inv_l t_l for every block row l of every instance (block-diagonal S, h = 0)
-__global__ void k_blockdiag_gemv(int n1, int M, const double *__restrict__ band, size_t bstride,
-                                 const double *__restrict__ t, double *__restrict__ x,
-                                 size_t vstride, const int *__restrict__ act)
-{
-    const int inst = blockIdx.y;
-    if (!SWJ_INST_ACTIVE(act, inst)) return;
-    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    if (warp >= n1 * M) return;
-    int l = warp / n1, r = warp % n1;
-    const double *inv = band + (size_t)inst * bstride * M + (size_t)l * bstride + (size_t)r * n1;
-    const double *tl = t + (size_t)inst * vstride + (size_t)l * n1;
-    double s = 0.0;
-    for (int c = lane; c < n1; c += 32) s = fma(inv[c], tl[c], s);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) x[(size_t)inst * vstride + (size_t)l * n1 + r] = s;
-}
-
 // Y[l][c] = alpha f dot(X[l, :], Mat[c, :]) + beta Y[l][c] for the M rows of
 // every instance (X, Y at instance strides xs, ys; f = scale[inst] or 1)
 __global__ void k_rowdot(int M, int n, const double *__restrict__ X, size_t xs,
@@ -313,7 +293,7 @@ void free_pc(swj_ctx *c)
 {
     double **bufs[] = {&c->pc_Ainv, &c->pc_AinvB1, &c->pc_CAinv, &c->pc_G1, &c->pc_A, &c->pc_B1,
                        &c->pc_C, &c->pc_invF2, &c->pc_band, &c->pc_W, &c->pc_sumK3, &c->pc_t1,
-                       &c->pc_t2, &c->pc_z, &c->pc_work};
+                       &c->pc_t2, &c->pc_z, &c->pc_work, &c->pc_lt, &c->pc_mc_buf};
     for (double **b : bufs) {
         if (*b) cudaFree(*b);
         *b = nullptr;
@@ -323,6 +303,9 @@ void free_pc(swj_ctx *c)
     if (c->pc_ptrs) cudaFree(c->pc_ptrs);
     c->pc_ptrs = nullptr;
     c->pc_ptrs_cap = 0;
+    if (c->pc_mc_err) cudaFree(c->pc_mc_err);
+    c->pc_mc_err = nullptr;
+    c->pc_mc = 0;
     if (c->pc_chain) {
         cudaStreamSynchronize(c->pc_chain);
         cudaStreamSynchronize(c->pc_bulk);
@@ -346,15 +329,26 @@ int half_band(int block_bw, int M)
     return h > M - 1 ? M - 1 : h;
 }
 
+// multi-cluster apply scratch (one instance, h >= 2): z [M][n1], then the term
+// slots cf, cb [M][h+1][n1] (0 where it does not apply)
+size_t pc_mc_doubles(int n1, int M, int nb, int h)
+{
+    return (nb == 1 && h >= 2) ? (size_t)M * n1 * (1 + 2 * (size_t)(h + 1)) : 0;
+}
+
+constexpr int kPcBufs = 17;
+
 // doubles of each preconditioner buffer, in the order of free_pc's list
-void pc_sizes(int n1, int M, int T, int H, int nb, int h, bool gj_inplace, size_t sz[15])
+// (0: not allocated)
+void pc_sizes(int n1, int M, int T, int H, int nb, int h, bool gj_inplace, size_t sz[kPcBufs])
 {
     const size_t n2 = (size_t)n1 * n1;
     const size_t work_blocks = gj_inplace ? 1 : (size_t)nb * (h == 0 ? M : 1);
-    const size_t v[15] = {n2, n2, n2, n2, n2, n2, n2, (size_t)nb,
-                          (size_t)nb * M * (2 * h + 1) * n2, (size_t)nb * M * (h > 0 ? h : 1) * n2,
-                          (size_t)T, (size_t)nb * H, (size_t)nb * H, (size_t)nb * H, work_blocks * n2};
-    for (int i = 0; i < 15; ++i) sz[i] = v[i];
+    const size_t v[kPcBufs] = {n2, n2, n2, n2, n2, n2, n2, (size_t)nb,
+                               (size_t)nb * M * (2 * h + 1) * n2, (size_t)nb * M * (h > 0 ? h : 1) * n2,
+                               (size_t)T, (size_t)nb * H, (size_t)nb * H, (size_t)nb * H, work_blocks * n2,
+                               (size_t)nb * h * n2, pc_mc_doubles(n1, M, nb, h)};
+    for (int i = 0; i < kPcBufs; ++i) sz[i] = v[i];
 }
 
 // block products of the band LU (pointer triples of the batched GEMMs)
@@ -364,7 +358,7 @@ size_t pc_gemm_count(int M, int nb, int h)
     size_t np = 0;
     for (int i = 0; i < M; ++i) {
         size_t k = (size_t)(i + h < M - 1 ? h : M - 1 - i);
-        np += (size_t)nb * (k + k * k);
+        np += (size_t)nb * (k + k * k + (size_t)std::min(i, h));
     }
     return np;
 }
@@ -376,12 +370,26 @@ void swj_pc_free(swj_ctx *c) { free_pc(c); }
 size_t swj_pc_bytes(int N, int M, int nb, int block_bw)
 {
     const int n1 = N + 1, h = half_band(block_bw, M);
-    size_t sz[15], tot = 0;
+    size_t sz[kPcBufs], tot = 0;
     pc_sizes(n1, M, (N - 1) * M, n1 * M, nb, h, swj_gj_inplace(n1), sz);
     for (size_t v : sz) tot += v * sizeof(double);
     tot += (size_t)nb * M * sizeof(int);
     tot += 3 * pc_gemm_count(M, nb, h) * sizeof(double *);
+    if (pc_mc_doubles(n1, M, nb, h)) tot += sizeof(int);
     return tot;
+}
+
+// S x = pc_t2 on h clusters into x (one instance): p into pc_z, the scratch
+// and x set to "not yet written", then the sweep
+static int mc_solve(swj_ctx *c, double *x)
+{
+    const int M = c->M, n1 = c->n1, h = c->pc_h;
+    const size_t mn = (size_t)M * n1;
+    double *z = c->pc_mc_buf, *cf = z + mn, *cb = cf + mn * (h + 1);
+    int rc = swj_block_p(c->stream, 1, n1, M, h, c->pc_band, band_stride(c), c->pc_t2, mn, c->pc_z, mn,
+                         nullptr, c->pc_mc_buf, mn * (1 + 2 * (size_t)(h + 1)), x, mn);
+    if (rc) return rc;
+    return swj_band_sweep_mc(c->stream, n1, M, h, c->pc_band, c->pc_W, c->pc_z, z, x, cf, cb, c->pc_mc_err);
 }
 
 int swj_pc_setup(swj_ctx *c)
@@ -399,12 +407,15 @@ int swj_pc_setup(swj_ctx *c)
         free_pc(c);
         c->pc_h = h;
         c->pc_nb = nbs;
-        size_t sz[15];
+        size_t sz[kPcBufs];
         pc_sizes(n1, M, c->T, c->H, nb, h, gj_inplace, sz);
         double **bufs[] = {&c->pc_Ainv, &c->pc_AinvB1, &c->pc_CAinv, &c->pc_G1, &c->pc_A,
                            &c->pc_B1, &c->pc_C, &c->pc_invF2, &c->pc_band, &c->pc_W,
-                           &c->pc_sumK3, &c->pc_t1, &c->pc_t2, &c->pc_z, &c->pc_work};
-        for (int i = 0; i < 15; ++i) {
+                           &c->pc_sumK3, &c->pc_t1, &c->pc_t2, &c->pc_z, &c->pc_work,
+                           &c->pc_lt, &c->pc_mc_buf};
+        static_assert(sizeof(bufs) / sizeof(bufs[0]) == kPcBufs, "buffer list");
+        for (int i = 0; i < kPcBufs; ++i) {
+            if (!sz[i]) continue;
             if (cudaMalloc(bufs[i], sz[i] * sizeof(double)) != cudaSuccess) {
                 free_pc(c);
                 return SWJ_ENOMEM;
@@ -418,6 +429,14 @@ int swj_pc_setup(swj_ctx *c)
         }
         c->pc_bytes += (size_t)nb * M * sizeof(int);
         c->bytes += (size_t)nb * M * sizeof(int);
+        if (c->pc_mc_buf) {
+            if (cudaMalloc(&c->pc_mc_err, sizeof(int)) != cudaSuccess) {
+                free_pc(c);
+                return SWJ_ENOMEM;
+            }
+            c->pc_bytes += sizeof(int);
+            c->bytes += sizeof(int);
+        }
     }
     c->pc_ready = 0;
     std::vector<double> invF2(nb);
@@ -487,10 +506,11 @@ int swj_pc_setup(swj_ctx *c)
     } else {
         // device pointer triples of the batched GEMMs of every step, all instances:
         //   W_ik = inv_i S_ik (k = i+1..i+h), then S_jk -= S_ji W_ik (j, k = i+1..i+h),
-        //   the updates of block row i+1 (U1) apart from those of rows i+2.. (U2)
+        //   the updates of block row i+1 (U1) apart from those of rows i+2.. (U2),
+        //   and L_ij = inv_i S_ij (j = i-h..i-1) into the scratch pc_lt (L)
         std::vector<const double *> PA, PB;
         std::vector<double *> PC;
-        std::vector<int> offW(M), cntW(M), offU1(M), cntU1(M), offU2(M), cntU2(M);
+        std::vector<int> offW(M), cntW(M), offU1(M), cntU1(M), offU2(M), cntU2(M), offL(M), cntL(M);
         for (int i = 0; i < M; ++i) {
             int kmax = i + h < M - 1 ? i + h : M - 1;
             offW[i] = (int)PA.size();
@@ -510,6 +530,14 @@ int swj_pc_setup(swj_ctx *c)
                         }
                 (part ? cntU2 : cntU1)[i] = (int)PA.size() - (part ? offU2 : offU1)[i];
             }
+            const int j0 = std::max(0, i - h);
+            offL[i] = (int)PA.size();
+            for (int q = 0; q < nb; ++q)
+                for (int j = j0; j < i; ++j) {
+                    PA.push_back(blk(c, q, i, i)); PB.push_back(blk(c, q, i, j));
+                    PC.push_back(c->pc_lt + ((size_t)q * h + (j - j0)) * n2);
+                }
+            cntL[i] = (int)PA.size() - offL[i];
         }
         int np = (int)PA.size();
         if (c->pc_ptrs_cap < np) {
@@ -544,7 +572,10 @@ int swj_pc_setup(swj_ctx *c)
         // i+2..i+h of step i (U2) once W_i exists, while the chain inverts the
         // next diagonal blocks.  Events ev[0..3] follow W_i, ev[4..7] the bulk of
         // step i (rings of 4: a wait is always enqueued before its event is
-        // recorded again).
+        // recorded again).  After the bulk updates of step i the bulk stream
+        // also replaces block row i's left blocks by L_ij = inv_i S_ij (the
+        // forward substitution's factors; nothing of the set-up reads them
+        // after step i - 1), outside the event the chain waits for.
         if (!c->pc_chain) {
             int lo = 0, hi = 0;
             cudaDeviceGetStreamPriorityRange(&lo, &hi);
@@ -584,6 +615,15 @@ int swj_pc_setup(swj_ctx *c)
                                   (const double *const *)(dB + offU2[i]), n1, 1.0, dC + offU2[i], n1,
                                   cntU2[i], 64);
             SWJ_CUDA_TRY(cudaEventRecord(evB[i % 4], sb));
+            if (cntL[i]) {
+                swj_dgemm_batched(sb, n1, n1, n1, 1.0, (const double *const *)(dA + offL[i]), n1,
+                                  (const double *const *)(dB + offL[i]), n1, 0.0, dC + offL[i], n1,
+                                  cntL[i], 64);
+                const int nt = std::min(i, h);
+                SWJ_COUNT_LAUNCH();
+                k_copy_blocks<<<dim3(64, nb), 256, 0, sb>>>((size_t)nt * n2, c->pc_lt, (size_t)h * n2,
+                                                            blk(c, 0, i, i - nt), bst);
+            }
         }
         SWJ_CUDA_TRY(cudaEventRecord(evEnd, sb));
         SWJ_CUDA_TRY(cudaStreamWaitEvent(st, evEnd, 0));
@@ -600,12 +640,41 @@ int swj_pc_setup(swj_ctx *c)
         else if (info[i] != 0) return SWJ_ESINGULAR;
     if (h > 0) {
         int rc = swj_band_sweep_cluster(st, nb, n1, M, h, c->pc_band, band_stride(c), c->pc_W,
-                                        (size_t)M * h * n1 * n1, c->pc_t2, c->pc_z, c->pc_t2, (size_t)c->H,
+                                        (size_t)M * h * n2, c->pc_z, (size_t)c->H, c->pc_t2, (size_t)c->H,
                                         nullptr, true);
         if (rc) return rc;
     }
+    // one instance: the multi-cluster apply where the device holds its h
+    // clusters, after one trial solve (of t = 0) shows that the launch forms
+    // them
+    c->pc_mc = 0;
+    if (c->pc_mc_buf && swj_band_sweep_mc(st, n1, M, h, c->pc_band, c->pc_W, nullptr, nullptr, nullptr,
+                                          nullptr, nullptr, nullptr, true) == SWJ_OK) {
+        SWJ_CUDA_TRY(cudaMemsetAsync(c->pc_t2, 0, (size_t)c->H * sizeof(double), st));
+        SWJ_CUDA_TRY(cudaMemsetAsync(c->pc_mc_err, 0, sizeof(int), st));
+        c->pc_mc = 1;
+        int rc = mc_solve(c, c->pc_t1);
+        int err = 1;
+        if (rc == SWJ_OK) {
+            SWJ_CUDA_TRY(cudaMemcpyAsync(&err, c->pc_mc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+            SWJ_CUDA_TRY(cudaStreamSynchronize(st));
+        }
+        c->pc_mc = (rc == SWJ_OK && err == 0);
+        SWJ_CUDA_TRY(cudaMemsetAsync(c->pc_mc_err, 0, sizeof(int), st));
+    }
     c->pc_ready = 1;
     return SWJ_OK;
+}
+
+// SWJ_ETIMEOUT if a wait of the multi-cluster apply gave up since the set-up
+// (synchronises the stream)
+int swj_pc_status(swj_ctx *c)
+{
+    if (!c->pc_mc) return SWJ_OK;
+    int err = 0;
+    SWJ_CUDA_TRY(cudaMemcpyAsync(&err, c->pc_mc_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    SWJ_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return err ? SWJ_ETIMEOUT : SWJ_OK;
 }
 
 int swj_pc_apply(swj_ctx *c, const double *b, double *r, const int *act)
@@ -621,19 +690,20 @@ int swj_pc_apply(swj_ctx *c, const double *b, double *r, const int *act)
     rowdot(c, b, nu, c->pc_CAinv, -1.0, nullptr, 1.0, t2, H, act);
     rowdot(c, b, nu, c->pc_Ainv, 1.0, nullptr, 0.0, t1, H, act);
     // s2 = S^-1 t2 into r2 (= r + H of every instance)
-    if (h == 0) {
-        SWJ_COUNT_LAUNCH();
-        k_blockdiag_gemv<<<dim3(nblk((long)n1 * M * 32, 256), nb), 256, 0, st>>>(
-            n1, M, c->pc_band, n2, t2, c->pc_z, H, act);
-        SWJ_COUNT_LAUNCH();
-        k_copy_vec<<<dim3(nblk(H, 256), nb), 256, 0, st>>>(H, c->pc_z, H, r + H, nu, act);
-    } else {
-        int rc = swj_band_sweep_cluster(st, nb, n1, M, h, c->pc_band, band_stride(c), c->pc_W,
-                                        (size_t)M * h * n2, t2, c->pc_z, c->pc_t2, H, act);
+    int rc = SWJ_EINVAL;
+    if (c->pc_mc) {
+        rc = mc_solve(c, r + H);
+        if (rc) c->pc_mc = 0;   // the launch was refused: one cluster from now on
+    }
+    if (rc) {
+        rc = swj_block_p(st, nb, n1, M, h, c->pc_band, band_stride(c), t2, H, h ? c->pc_z : r + H,
+                         h ? H : nu, act);
         if (rc) return rc;
-        // the sweep leaves x in pc_t2 (y is dead after the forward phase)
-        SWJ_COUNT_LAUNCH();
-        k_copy_vec<<<dim3(nblk(H, 256), nb), 256, 0, st>>>(H, c->pc_t2, H, r + H, nu, act);
+        if (h > 0) {
+            rc = swj_band_sweep_cluster(st, nb, n1, M, h, c->pc_band, band_stride(c), c->pc_W,
+                                        (size_t)M * h * n2, c->pc_z, H, r + H, nu, act);
+            if (rc) return rc;
+        }
     }
     // r1 = A^-1 b1 - (A^-1 B) s2, A^-1 B = (A^-1 B at F = 1) / F^2
     rowdot(c, r + H, nu, c->pc_AinvB1, -1.0, c->pc_invF2, 1.0, t1, H, act);

@@ -669,6 +669,8 @@ int swj_solve_impl(swj_ctx *c, double *u, swj_stats *stats)
             st[i].status = ph.status[i];
         }
         finish(0);
+        rc = swj_pc_status(c);
+        if (rc) return finish(rc);
         for (int i = 0; i < nb; ++i)
             if (st[i].status) return st[i].status;
         return SWJ_OK;
@@ -709,6 +711,8 @@ int swj_solve_impl(swj_ctx *c, double *u, swj_stats *stats)
         st[i].status = rf.status[i];
     }
     finish(0);
+    rc = swj_pc_status(c);
+    if (rc) return finish(rc);
     for (int i = 0; i < nb; ++i)
         if (st[i].status) return st[i].status;
     return SWJ_OK;

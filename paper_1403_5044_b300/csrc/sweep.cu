@@ -1,0 +1,533 @@
+// Block forward / backward substitution with the band LU factors of the
+// Schur complement S (Appendix C, middle stage of the three-stage solve), FP64.
+//
+// The set-up leaves, for block row i of S (n1 x n1 blocks, half bandwidth h):
+//   band slot h       inv_i = S_ii^-1 (after the updates of steps < i)
+//   band slot h - d   L_{i,i-d} = inv_i S_{i,i-d}          (d = 1..h)
+//   W[i][e - 1]       W_{i,i+e} = inv_i S_{i,i+e}          (e = 1..h)
+// so that S x = t is solved by
+//   p_i = inv_i t_i                                         (all i at once)
+//   z_i = p_i - sum_{d=1..h} L_{i,i-d} z_{i-d}              (forward, i = 0..M-1)
+//   x_i = z_i - sum_{e=1..h} W_{i,i+e} x_{i+e}              (backward, i = M-1..0)
+// Only the forward and backward recurrences are sequential.  Every block
+// product is a set of row dots computed by block_dot (one warp per row, one
+// fixed order of operations), and every recurrence subtracts them nearest
+// block first, so the single-cluster and the multi-cluster sweeps below
+// return identical bits.
+#include "swj_internal.h"
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <cooperative_groups.h>
+#include <cuda_pipeline.h>
+
+namespace cg = cooperative_groups;
+
+namespace {
+
+constexpr int kSweepThreads = 512;
+
+// Bit pattern written into every value the multi-cluster sweep publishes
+// before its launch: a signalling NaN, which no FP64 operation returns (a NaN
+// result is always quiet), so a consumer polls a value until it differs.
+constexpr unsigned long long kUnset = 0x7FF4DEAD7FF4DEADull;
+
+// a poll that has not seen its value after this many reads gives up (about a
+// second at L2 latency) and reports through the error word
+constexpr int kPollLimit = 1 << 21;
+
+__device__ __forceinline__ double ld_relaxed(const double *p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return __longlong_as_double((long long)v);
+}
+
+__device__ __forceinline__ void st_relaxed(double *p, double x)
+{
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"((unsigned long long)__double_as_longlong(x))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool unset(double x) { return (unsigned long long)__double_as_longlong(x) == kUnset; }
+
+__device__ __forceinline__ double warp_sum(double a)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    return a;
+}
+
+// Dot product of one n1-row with an n1-vector, one warp: lane l accumulates
+// columns l, l + 32, ... with FMAs in that order, then a butterfly sum; every
+// lane returns the result.
+template <int KC>
+__device__ __forceinline__ double block_dot(const double *row, const double *v, int n1, int lane)
+{
+    double x[KC];
+#pragma unroll
+    for (int k = 0; k < KC; ++k) {
+        const int c = lane + 32 * k;
+        x[k] = (c < n1) ? row[c] : 0.0;
+    }
+    double a = 0.0;
+#pragma unroll
+    for (int k = 0; k < KC; ++k) {
+        const int c = lane + 32 * k;
+        if (c < n1) a = fma(x[k], v[c], a);
+    }
+    return warp_sum(a);
+}
+
+// Two dots at once (the loads of both in flight together), each with exactly
+// the arithmetic of block_dot.
+template <int KC>
+__device__ __forceinline__ void block_dot2(const double *row0, const double *v0, const double *row1,
+                                           const double *v1, int n1, int lane, double &s0, double &s1)
+{
+    double x0[KC], x1[KC];
+#pragma unroll
+    for (int k = 0; k < KC; ++k) {
+        const int c = lane + 32 * k;
+        x0[k] = (c < n1) ? row0[c] : 0.0;
+        x1[k] = (c < n1) ? row1[c] : 0.0;
+    }
+    double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+    for (int k = 0; k < KC; ++k) {
+        const int c = lane + 32 * k;
+        if (c < n1) {
+            a0 = fma(x0[k], v0[c], a0);
+            a1 = fma(x1[k], v1[c], a1);
+        }
+    }
+    s0 = warp_sum(a0);
+    s1 = warp_sum(a1);
+}
+
+// v - sum_{q=0..nt-1} dot(row q, vector q), subtracted in the order q = 0, 1, ...
+// Rows at base + q bstride (global memory; bstride may be negative), vectors
+// at vs + q n1 (shared).
+template <int KC>
+__device__ __forceinline__ double sub_dots(double v, const double *base, long long bstride, const double *vs,
+                                           int nt, int n1, int lane)
+{
+    int q = 0;
+    for (; q + 1 < nt; q += 2) {
+        double s0, s1;
+        block_dot2<KC>(base + q * bstride, vs + (size_t)q * n1, base + (q + 1) * bstride,
+                       vs + (size_t)(q + 1) * n1, n1, lane, s0, s1);
+        v -= s0;
+        v -= s1;
+    }
+    if (q < nt) v -= block_dot<KC>(base + q * bstride, vs + (size_t)q * n1, n1, lane);
+    return v;
+}
+
+// p_i = inv_i t_i for every block row of every active instance (one warp per
+// row).  Optionally also sets fill1[0, n1f) and fill2[0, n2f) to kUnset (the
+// multi-cluster sweep's published values; grid-stride over blockIdx.x of
+// instance 0).
+template <int KC>
+__global__ void __launch_bounds__(256)
+k_block_p(int n1, int M, int h, const double *__restrict__ band, size_t bs, const double *__restrict__ t,
+          size_t ts, double *__restrict__ p, size_t ps, const int *__restrict__ act, double *fill1,
+          size_t n1f, double *fill2, size_t n2f)
+{
+    const int inst = blockIdx.y;
+    if (blockIdx.y == 0 && (fill1 || fill2)) {
+        const double u = __longlong_as_double((long long)kUnset);
+        const size_t stride = (size_t)gridDim.x * blockDim.x;
+        for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n1f; e += stride) fill1[e] = u;
+        for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n2f; e += stride) fill2[e] = u;
+    }
+    if (!SWJ_INST_ACTIVE(act, inst)) return;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= n1 * M) return;
+    const int l = warp / n1, r = warp % n1;
+    const size_t n2 = (size_t)n1 * n1;
+    const double *inv = band + (size_t)inst * bs + ((size_t)l * (2 * h + 1) + h) * n2 + (size_t)r * n1;
+    const double s = block_dot<KC>(inv, t + (size_t)inst * ts + (size_t)l * n1, n1, lane);
+    if (lane == 0) p[(size_t)inst * ps + (size_t)l * n1 + r] = s;
+}
+
+// One cluster per instance runs both recurrences; z holds p on entry and z
+// on exit, x receives the solution.  Each CTA computes a slice of the rows of
+// every block step (a warp per row); the vectors a step reads are staged in
+// shared memory after the cluster barrier that ends the previous step.
+template <int KC>
+__global__ void __launch_bounds__(kSweepThreads)
+k_band_sweep(int n1, int M, int h, const double *__restrict__ band, size_t band_stride,
+             const double *__restrict__ W, size_t w_stride, double *z, size_t zs, double *x, size_t xs,
+             const int *__restrict__ act)
+{
+    cg::cluster_group cl = cg::this_cluster();
+    const int ncta = (int)cl.num_blocks();
+    const int rank = (int)cl.block_rank();
+    const int inst = blockIdx.x / ncta;
+    if (!SWJ_INST_ACTIVE(act, inst)) return;   // the whole cluster leaves together
+    band += (size_t)inst * band_stride;
+    W += (size_t)inst * w_stride;
+    z += (size_t)inst * zs;
+    x += (size_t)inst * xs;
+    const int nbk = 2 * h + 1;
+    const size_t n2 = (size_t)n1 * n1;
+    const int rows = (n1 + ncta - 1) / ncta;
+    const int r0 = min(n1, rank * rows), r1 = min(n1, r0 + rows);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    extern __shared__ double vs[];   // up to h staged vectors of n1
+    for (int i = 1; i < M; ++i) {
+        const int nt = min(i, h);
+        // vs[d - 1] = z_{i-d}
+        for (int e = threadIdx.x; e < nt * n1; e += blockDim.x) vs[e] = z[(size_t)(i - 1 - e / n1) * n1 + e % n1];
+        __syncthreads();
+        for (int r = r0 + warp; r < r1; r += nw) {
+            // slots h-1, h-2, ... hold L_{i,i-1}, L_{i,i-2}, ...: stride -n2
+            const double *L = band + ((size_t)i * nbk + (h - 1)) * n2 + (size_t)r * n1;
+            const double v = sub_dots<KC>(z[(size_t)i * n1 + r], L, -(long long)n2, vs, nt, n1, lane);
+            if (lane == 0) z[(size_t)i * n1 + r] = v;
+        }
+        cl.sync();
+    }
+    for (int i = M - 1; i >= 0; --i) {
+        const int nt = min(M - 1 - i, h);
+        // vs[e - 1] = x_{i+e}
+        for (int e = threadIdx.x; e < nt * n1; e += blockDim.x) vs[e] = x[(size_t)(i + 1 + e / n1) * n1 + e % n1];
+        __syncthreads();
+        for (int r = r0 + warp; r < r1; r += nw) {
+            const double *Wr = W + ((size_t)i * h) * n2 + (size_t)r * n1;
+            const double v = sub_dots<KC>(z[(size_t)i * n1 + r], Wr, (long long)n2, vs, nt, n1, lane);
+            if (lane == 0) x[(size_t)i * n1 + r] = v;
+        }
+        cl.sync();
+    }
+}
+
+// The same recurrences for one instance on h clusters.  Cluster 0 (critical)
+// keeps only the product with the block next to the diagonal:
+//   forward   z_i = p_i - L_{i,i-1} z_{i-1} - sum_{d>=2} c_{i,d}
+//   backward  x_i = z_i - W_{i,i+1} x_{i+1} - sum_{e>=2} b_{i,e}
+// and cluster d-1 (d = 2..h) computes the older terms as soon as their
+// vector exists: c_{j+d,d} = L_{j+d,j} z_j and b_{k-d,d} = W_{k-d,k} x_k.
+// Nothing is signalled apart from the values themselves: z, x and the term
+// slots cf, cb ([M][h+1][n1], slots 2..h used) are set to kUnset before the
+// launch, producers store each value once (relaxed, 8 bytes, single-copy
+// atomic) and consumers poll it until it is set.  In cluster 0 each CTA owns
+// a slice of rows, takes the next step's block rows into shared memory with
+// cp.async while the current step runs, keeps its z rows for the backward
+// pass, and sends every new element of z_i / x_i straight into the shared
+// memory of all CTAs of the cluster (one cluster barrier per step).  The
+// helpers are independent CTAs (no barrier between them).  The launch is
+// cooperative, so all clusters are resident at once; a poll that runs out
+// sets *err = 1, and a launch whose clusters are not of cs CTAs sets
+// *err = 2 and returns at once.
+template <int KC>
+__global__ void __launch_bounds__(kSweepThreads)
+k_band_sweep_mc(int n1, int M, int h, const double *__restrict__ band, const double *__restrict__ W,
+                const double *__restrict__ p, double *z, double *x, double *cf, double *cb, int cs, int *err)
+{
+    cg::cluster_group cl = cg::this_cluster();
+    const int ncta = (int)cl.num_blocks();
+    if (ncta != cs || (int)gridDim.x != cs * h) {   // the same decision in every CTA
+        if (threadIdx.x == 0) atomicExch(err, 2);
+        return;
+    }
+    const int rank = (int)cl.block_rank();
+    const int cid = blockIdx.x / ncta;
+    const int nbk = 2 * h + 1, hs = h + 1;
+    const size_t n2 = (size_t)n1 * n1;
+    const int rows = (n1 + ncta - 1) / ncta;
+    const int r0 = min(n1, rank * rows), r1 = min(n1, r0 + rows), nr = r1 - r0;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    extern __shared__ double sm[];
+    double *rb = sm;                              // [2][rows][n1] block rows, by step parity
+    double *vz = rb + 2 * (size_t)rows * n1;      // [2][n1]: z by parity (helpers: the staged vector)
+    double *vx = vz + 2 * (size_t)n1;             // [2][n1]: x by parity
+    double *zs = vx + 2 * (size_t)n1;             // [M][rows]: this CTA's rows of z
+    __shared__ int bad;
+    if (threadIdx.x == 0) bad = 0;
+    __syncthreads();
+    // rows [r0, r1) of one block into rb[buf] (16-byte copies where aligned)
+    auto prefetch = [&](int buf, const double *blk) {
+        double *dst = rb + (size_t)buf * rows * n1;
+        const double *src = blk + (size_t)r0 * n1;
+        const int ne = nr * n1;
+        if ((n1 & 1) == 0) {
+            for (int e = 2 * threadIdx.x; e < ne; e += 2 * blockDim.x) __pipeline_memcpy_async(dst + e, src + e, 16);
+        } else {
+            for (int e = threadIdx.x; e < ne; e += blockDim.x) __pipeline_memcpy_async(dst + e, src + e, 8);
+        }
+    };
+    // finishes a poll whose first read gave v
+    auto poll = [&](const double *a, double v) {
+        if (unset(v) && !*(volatile int *)&bad) {
+            int it = 0;
+            while (unset(v = ld_relaxed(a)))
+                if (++it > kPollLimit || *(volatile int *)&bad) {
+                    bad = 1;
+                    atomicExch(err, 1);
+                    break;
+                }
+        }
+        return v;
+    };
+    if (cid == 0) {
+        // ---- forward: step i reads L_{i,i-1} from rb[i & 1] and prefetches
+        //      L_{i+1,i} into the other buffer (read at step i - 1, before the
+        //      barrier that ended it)
+        for (int i = 0; i < M; ++i) {
+            if (i + 1 < M) prefetch((i + 1) & 1, band + ((size_t)(i + 1) * nbk + (h - 1)) * n2);
+            __pipeline_commit();
+            const int nd = min(h, i);   // terms c_{i,2..nd}
+            // lane 0: p_i[r]; lane d (2..nd): first read of c_{i,d}[r]
+            auto addr = [&](int rr) { return cf + ((size_t)i * hs + lane) * n1 + r0 + rr; };
+            double mine = 0.0;
+            if (warp < nr) {
+                if (lane == 0) mine = p[(size_t)i * n1 + r0 + warp];
+                else if (lane >= 2 && lane <= nd) mine = ld_relaxed(addr(warp));
+            }
+            __pipeline_wait_prior(1);
+            __syncthreads();
+            for (int rr = warp; rr < nr; rr += nw) {
+                const int r = r0 + rr;
+                if (rr != warp) {
+                    if (lane == 0) mine = p[(size_t)i * n1 + r];
+                    else if (lane >= 2 && lane <= nd) mine = ld_relaxed(addr(rr));
+                }
+                double s = 0.0;
+                if (i > 0) s = block_dot<KC>(rb + ((size_t)(i & 1) * rows + rr) * n1, vz + (size_t)((i - 1) & 1) * n1, n1, lane);
+                if (lane >= 2 && lane <= nd) mine = poll(addr(rr), mine);
+                double v = __shfl_sync(0xffffffffu, mine, 0);
+                if (i > 0) v -= s;
+                for (int d = 2; d <= nd; ++d) v -= __shfl_sync(0xffffffffu, mine, d);
+                if (lane == 0) {
+                    st_relaxed(z + (size_t)i * n1 + r, v);
+                    zs[(size_t)i * rows + rr] = v;
+                }
+                if (lane < ncta) *cl.map_shared_rank(vz + (size_t)(i & 1) * n1 + r, lane) = v;
+            }
+            cl.sync();
+        }
+        // ---- backward: step i (t = M - 1 - i) reads W_{i,i+1} from rb[t & 1]
+        //      and prefetches W_{i-1,i} into the other buffer
+        for (int i = M - 1; i >= 0; --i) {
+            const int t = M - 1 - i;
+            if (i >= 1) prefetch((t + 1) & 1, W + ((size_t)(i - 1) * h) * n2);
+            __pipeline_commit();
+            const int ne = min(h, M - 1 - i);   // terms b_{i,2..ne}
+            auto addr = [&](int rr) { return cb + ((size_t)i * hs + lane) * n1 + r0 + rr; };
+            double mine = 0.0;
+            if (warp < nr && lane >= 2 && lane <= ne) mine = ld_relaxed(addr(warp));
+            __pipeline_wait_prior(1);
+            __syncthreads();
+            for (int rr = warp; rr < nr; rr += nw) {
+                const int r = r0 + rr;
+                if (rr != warp && lane >= 2 && lane <= ne) mine = ld_relaxed(addr(rr));
+                double s = 0.0;
+                if (i < M - 1) s = block_dot<KC>(rb + ((size_t)(t & 1) * rows + rr) * n1, vx + (size_t)((i + 1) & 1) * n1, n1, lane);
+                if (lane >= 2 && lane <= ne) mine = poll(addr(rr), mine);
+                double v = zs[(size_t)i * rows + rr];
+                if (i < M - 1) v -= s;
+                for (int e = 2; e <= ne; ++e) v -= __shfl_sync(0xffffffffu, mine, e);
+                if (lane == 0) st_relaxed(x + (size_t)i * n1 + r, v);
+                if (lane < ncta) *cl.map_shared_rank(vx + (size_t)(i & 1) * n1 + r, lane) = v;
+            }
+            cl.sync();
+        }
+        __pipeline_wait_prior(0);
+    } else {
+        const int d = cid + 1;   // 2..h
+        // forward terms c_{j+d,d} = L_{j+d,j} z_j (slot h - d of block row j + d)
+        if (d < M) prefetch(0, band + ((size_t)d * nbk + (h - d)) * n2);
+        __pipeline_commit();
+        for (int j = 0; j + d < M; ++j) {
+            const int buf = j & 1;
+            if (j + 1 + d < M) prefetch(buf ^ 1, band + ((size_t)(j + 1 + d) * nbk + (h - d)) * n2);
+            __pipeline_commit();
+            for (int e = threadIdx.x; e < n1; e += blockDim.x) vz[e] = poll(z + (size_t)j * n1 + e, ld_relaxed(z + (size_t)j * n1 + e));
+            __pipeline_wait_prior(1);
+            __syncthreads();
+            for (int rr = warp; rr < nr; rr += nw) {
+                const double s = block_dot<KC>(rb + ((size_t)buf * rows + rr) * n1, vz, n1, lane);
+                if (lane == 0) st_relaxed(cf + ((size_t)(j + d) * hs + d) * n1 + r0 + rr, s);
+            }
+            __syncthreads();
+        }
+        __pipeline_wait_prior(0);
+        __syncthreads();
+        // backward terms b_{k-d,d} = W_{k-d,k} x_k, k = M-1 down to d
+        if (M - 1 - d >= 0) prefetch(0, W + ((size_t)(M - 1 - d) * h + (d - 1)) * n2);
+        __pipeline_commit();
+        for (int k = M - 1, t = 0; k - d >= 0; --k, ++t) {
+            const int buf = t & 1;
+            if (k - 1 - d >= 0) prefetch(buf ^ 1, W + ((size_t)(k - 1 - d) * h + (d - 1)) * n2);
+            __pipeline_commit();
+            for (int e = threadIdx.x; e < n1; e += blockDim.x) vz[e] = poll(x + (size_t)k * n1 + e, ld_relaxed(x + (size_t)k * n1 + e));
+            __pipeline_wait_prior(1);
+            __syncthreads();
+            for (int rr = warp; rr < nr; rr += nw) {
+                const double s = block_dot<KC>(rb + ((size_t)buf * rows + rr) * n1, vz, n1, lane);
+                if (lane == 0) st_relaxed(cb + ((size_t)(k - d) * hs + d) * n1 + r0 + rr, s);
+            }
+            __syncthreads();
+        }
+        __pipeline_wait_prior(0);
+    }
+}
+
+size_t mc_smem_bytes(int n1, int M, int cs)
+{
+    const size_t rows = (size_t)(n1 + cs - 1) / cs;
+    return (2 * rows * n1 + 4 * (size_t)n1 + (size_t)M * rows) * sizeof(double);
+}
+
+}  // namespace
+
+// The single-cluster sweep's cluster size and shared-memory limit are settled
+// on the first call with prepare = true (from the preconditioner set-up), so
+// that a launch recorded into a CUDA graph makes no attribute call.
+template <int KC>
+static int launch_sweep(cudaStream_t st, int nb, int n1, int M, int h, const double *band, size_t bs,
+                        const double *W, size_t ws, double *z, size_t zs, double *x, size_t xs,
+                        const int *act, bool prepare)
+{
+    const size_t smem = (size_t)(h > 0 ? h : 1) * n1 * sizeof(double);
+    const int cs = swj_cluster_for((const void *)k_band_sweep<KC>, kSweepThreads, smem);
+    if (prepare) return SWJ_OK;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs * nb);
+    cfg.blockDim = dim3(kSweepThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    SWJ_COUNT_LAUNCH();
+    SWJ_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_band_sweep<KC>, n1, M, h, band, bs, W, ws, z, zs, x, xs, act));
+    return SWJ_OK;
+}
+
+// Cluster size and shared memory of the multi-cluster sweep per (kernel, n1,
+// M, h): 16 CTAs, else 8, where h such clusters fit on the device at once
+// (0: the multi-cluster sweep does not apply).
+static std::mutex g_mc_mutex;
+static std::map<std::tuple<const void *, int, int, int>, std::pair<int, size_t>> g_mc_cache;
+
+template <int KC>
+static int launch_sweep_mc(cudaStream_t st, int n1, int M, int h, const double *band, const double *W,
+                           const double *p, double *z, double *x, double *cf, double *cb, int *err,
+                           bool prepare)
+{
+    const void *kern = (const void *)k_band_sweep_mc<KC>;
+    int cs;
+    size_t smem;
+    {
+        std::lock_guard<std::mutex> lock(g_mc_mutex);
+        auto key = std::make_tuple(kern, n1, M, h);
+        auto it = g_mc_cache.find(key);
+        if (it == g_mc_cache.end()) {
+            std::pair<int, size_t> pick(0, 0);
+            for (int c : {16, 8}) {
+                const size_t sm = mc_smem_bytes(n1, M, c);
+                if (sm > 220 * 1024) continue;
+                swj_cluster_for(kern, kSweepThreads, sm);   // raises the kernel's limit to sm
+                cudaLaunchConfig_t q = {};
+                q.gridDim = dim3(c * h);
+                q.blockDim = dim3(kSweepThreads);
+                q.dynamicSmemBytes = sm;
+                cudaLaunchAttribute qa[1];
+                qa[0].id = cudaLaunchAttributeClusterDimension;
+                qa[0].val.clusterDim.x = c;
+                qa[0].val.clusterDim.y = 1;
+                qa[0].val.clusterDim.z = 1;
+                q.attrs = qa;
+                q.numAttrs = 1;
+                int ncl = 0;
+                if (cudaOccupancyMaxActiveClusters(&ncl, kern, &q) != cudaSuccess) ncl = 0;
+                cudaGetLastError();
+                if (ncl >= h) {
+                    pick = std::make_pair(c, sm);
+                    break;
+                }
+            }
+            it = g_mc_cache.emplace(key, pick).first;
+        }
+        cs = it->second.first;
+        smem = it->second.second;
+    }
+    if (!cs) return SWJ_EINVAL;
+    if (prepare) return SWJ_OK;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs * h);
+    cfg.blockDim = dim3(kSweepThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeCooperative;
+    attr[1].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 2;
+    SWJ_COUNT_LAUNCH();
+    if (cudaLaunchKernelEx(&cfg, k_band_sweep_mc<KC>, n1, M, h, band, W, p, z, x, cf, cb, cs, err) !=
+        cudaSuccess) {
+        cudaGetLastError();   // e.g. no cooperative launch with clusters: the caller falls back
+        return SWJ_EINVAL;
+    }
+    return SWJ_OK;
+}
+
+template <int KC>
+static int launch_block_p(cudaStream_t st, int nb, int n1, int M, int h, const double *band, size_t bs,
+                          const double *t, size_t ts, double *p, size_t ps, const int *act, double *fill1,
+                          size_t n1f, double *fill2, size_t n2f)
+{
+    SWJ_COUNT_LAUNCH();
+    const long nthr = (long)n1 * M * 32;
+    k_block_p<KC><<<dim3((unsigned)((nthr + 255) / 256), nb), 256, 0, st>>>(n1, M, h, band, bs, t, ts, p, ps,
+                                                                             act, fill1, n1f, fill2, n2f);
+    SWJ_CUDA_TRY(cudaGetLastError());
+    return SWJ_OK;
+}
+
+#define SWJ_KC_DISPATCH(CALL)                                                                        \
+    do {                                                                                             \
+        const int kc = (n1 + 31) / 32;                                                               \
+        if (kc <= 2) { constexpr int K = 2; return CALL; }                                           \
+        if (kc <= 4) { constexpr int K = 4; return CALL; }                                           \
+        if (kc <= 6) { constexpr int K = 6; return CALL; }                                           \
+        if (kc <= 8) { constexpr int K = 8; return CALL; }                                           \
+        if (kc <= 12) { constexpr int K = 12; return CALL; }                                         \
+        if (kc <= 16) { constexpr int K = 16; return CALL; }                                         \
+        if (kc <= 24) { constexpr int K = 24; return CALL; }                                         \
+        if (kc <= 32) { constexpr int K = 32; return CALL; }                                         \
+        return SWJ_EINVAL;                                                                           \
+    } while (0)
+
+int swj_block_p(cudaStream_t st, int nb, int n1, int M, int h, const double *band, size_t bs,
+                const double *t, size_t ts, double *p, size_t ps, const int *act, double *fill1,
+                size_t n1f, double *fill2, size_t n2f)
+{
+    SWJ_KC_DISPATCH((launch_block_p<K>(st, nb, n1, M, h, band, bs, t, ts, p, ps, act, fill1, n1f, fill2, n2f)));
+}
+
+int swj_band_sweep_cluster(cudaStream_t st, int nb, int n1, int M, int h, const double *band, size_t bs,
+                           const double *W, size_t ws, double *z, size_t zs, double *x, size_t xs,
+                           const int *act, bool prepare)
+{
+    SWJ_KC_DISPATCH((launch_sweep<K>(st, nb, n1, M, h, band, bs, W, ws, z, zs, x, xs, act, prepare)));
+}
+
+int swj_band_sweep_mc(cudaStream_t st, int n1, int M, int h, const double *band, const double *W,
+                      const double *p, double *z, double *x, double *cf, double *cb, int *err, bool prepare)
+{
+    if (h < 2 || M < 2) return SWJ_EINVAL;
+    SWJ_KC_DISPATCH((launch_sweep_mc<K>(st, n1, M, h, band, W, p, z, x, cf, cb, err, prepare)));
+}

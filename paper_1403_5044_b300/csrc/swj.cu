@@ -381,6 +381,12 @@ int swj_precond_setup(swj_ctx *c)
     return swj_pc_setup(c);
 }
 
+int swj_precond_sweep_clusters(const swj_ctx *c)
+{
+    if (!c || !c->pc_ready) return 0;
+    return c->pc_mc ? c->pc_h : 1;
+}
+
 int swj_precond_apply(swj_ctx *c, const double *b, double *r)
 {
     if (!c || !b || !r) return SWJ_EINVAL;
@@ -423,7 +429,7 @@ int swj_sync(swj_ctx *c)
     if (!c) return SWJ_EINVAL;
     SWJ_CUDA_TRY(cudaStreamSynchronize(c->stream));
     SWJ_CUDA_TRY(cudaGetLastError());
-    return SWJ_OK;
+    return swj_pc_status(c);
 }
 
 const char *swj_strerror(int s)

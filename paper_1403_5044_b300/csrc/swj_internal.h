@@ -129,6 +129,11 @@ struct swj_ctx {
     // on a high-priority stream, the other Schur updates on a low-priority one
     cudaStream_t pc_chain, pc_bulk;
     cudaEvent_t pc_ev[10];
+    // multi-cluster apply (one instance): z, then the term slots cf, cb, and the error word
+    double *pc_mc_buf;
+    int *pc_mc_err;
+    int pc_mc;                   // 1: the apply uses swj_band_sweep_mc
+    double *pc_lt;               // set-up scratch: inv_i S_ij (j < i) of one block row, every instance
 
     size_t pc_bytes;             // device bytes of the preconditioner buffers
     size_t bytes;                // device bytes held (workspace + preconditioner)
@@ -209,16 +214,36 @@ void swj_dgemm(cudaStream_t st, int m, int n, int k, double alpha, const double 
 bool swj_gj_inplace(int n);
 int swj_gj_inverse_cluster(cudaStream_t st, int n, int count, double *work, size_t wstride,
                            double *out, size_t ostride, int *info);
-// prepare = true: only settle the kernel's attributes (no launch); call it
-// once before any launch that may be captured into a graph
+// cluster size (16, else 8) for `kern` with `smem` bytes of dynamic shared
+// memory per CTA; raises the kernel's shared-memory limit to `smem`
+int swj_cluster_for(const void *kern, int threads, size_t smem);
+
+// sweep.cu: the solve S x = t with the band LU factors (see sweep.cu).
+// p_i = inv_i t_i for every block row of every active instance; fill1/fill2
+// (optional, instance 0's launch) are set to the multi-cluster sweep's
+// "not yet written" pattern.
+int swj_block_p(cudaStream_t st, int nb, int n1, int M, int h, const double *band, size_t band_stride,
+                const double *t, size_t ts, double *p, size_t ps, const int *act,
+                double *fill1 = nullptr, size_t nfill1 = 0, double *fill2 = nullptr, size_t nfill2 = 0);
+// One cluster per instance: z (p on entry) -> z, then x.  prepare = true only
+// settles the kernel's attributes (no launch); call it once before any launch
+// that may be captured into a graph.
 int swj_band_sweep_cluster(cudaStream_t st, int nb, int n1, int M, int h, const double *band,
-                           size_t band_stride, const double *W, size_t w_stride, double *y,
-                           double *z, double *x, size_t vec_stride, const int *act,
-                           bool prepare = false);
+                           size_t band_stride, const double *W, size_t w_stride, double *z, size_t zs,
+                           double *x, size_t xs, const int *act, bool prepare = false);
+// One instance on h clusters (a critical one and h - 1 helpers, cooperative
+// launch): p -> z -> x.  z, x and cf, cb ([M][h+1][n1]) must hold the "not yet
+// written" pattern (swj_block_p's fill); err: set to 1 when a poll gave up, 2
+// when the launch did not form clusters of the expected size.  SWJ_EINVAL when
+// h < 2 or the device cannot hold h clusters at once (nothing launched).
+int swj_band_sweep_mc(cudaStream_t st, int n1, int M, int h, const double *band, const double *W,
+                      const double *p, double *z, double *x, double *cf, double *cb, int *err,
+                      bool prepare = false);
 
 // precond.cu
 int swj_pc_setup(swj_ctx *c);
 int swj_pc_apply(swj_ctx *c, const double *b, double *r, const int *act);
+int swj_pc_status(swj_ctx *c);   // SWJ_ETIMEOUT if a bounded wait of the apply gave up
 void swj_pc_free(swj_ctx *c);
 // device bytes the preconditioner of an nb-instance context holds after set-up
 size_t swj_pc_bytes(int N, int M, int nb, int block_bw);

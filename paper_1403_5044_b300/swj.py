@@ -124,6 +124,7 @@ def lib():
             "swj_jvp": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_int]),
             "swj_precond_setup": (ctypes.c_int, [_vp]),
             "swj_precond_apply": (ctypes.c_int, [_vp, _vp, _vp]),
+            "swj_precond_sweep_clusters": (ctypes.c_int, [_vp]),
             "swj_solve": (ctypes.c_int, [_vp, _vp, _vp]),
             "swj_unpack": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
             "swj_surface": (ctypes.c_int, [_vp, _vp, _vp]),
@@ -269,6 +270,9 @@ class Context:
     def precond_apply(self, b, r):
         _check(lib().swj_precond_apply(self._h, _ptr(b), _ptr(r)), "swj_precond_apply")
         return r
+
+    def sweep_clusters(self):
+        return int(lib().swj_precond_sweep_clusters(self._h))
 
     def solve(self, u, check=True):
         st = Stats()

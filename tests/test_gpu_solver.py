@@ -42,9 +42,11 @@ def test_jvp_matches_oracle_derivative():
 @pytest.mark.parametrize("spec,b", [(W.MeshSpec(9, 5, -2.0, 0.5, 0.4), 0),
                                     (W.MeshSpec(9, 5, -2.0, 0.5, 0.4), 1),
                                     (W.MeshSpec(9, 5, -2.0, 0.5, 0.4), 3),
+                                    (W.MeshSpec(9, 5, -2.0, 0.5, 0.4), 5),
                                     (W.MESH_41x21, 0),
                                     (W.MESH_41x21, 1),
-                                    (W.MESH_41x21, 5)])
+                                    (W.MESH_41x21, 5),
+                                    (W.MESH_41x21, 11)])
 def test_precond_apply_matches_linear_jacobian_solve(spec, b):
     """r = P^-1 b from the Schur-complement block LU (Appendix C) equals a
     dense solve with the oracle's Appendix B matrix truncated to the same
@@ -64,6 +66,33 @@ def test_precond_apply_matches_linear_jacobian_solve(spec, b):
     # normwise backward error, |P r - b| against |P| |r| (P is ill-conditioned: the
     # radiation rows have n = 0.05 on the diagonal next to x1 / dx)
     assert np.abs(P @ got - rhs).max() <= 1e-10 * (np.abs(P) @ np.abs(got)).max()
+
+
+@pytest.mark.parametrize("spec,b", [(W.MESH_41x21, 5), (W.SERVE_MESHES[1], 11), (W.SERVE_MESHES[2], 11),
+                                    (W.MeshSpec(9, 5, -2.0, 0.5, 0.4), 0)])
+def test_multi_cluster_sweep_equals_one_cluster_sweep(spec, b):
+    """A single-instance context spreads the block substitution over h
+    clusters; a batch runs it on one cluster per instance.  Both subtract the
+    same block products in the same order, so the applies agree bit for bit."""
+    F = 0.75
+    rhs = np.random.default_rng(spec.N + b).normal(size=spec.n_unknowns)
+    with swj.Context.from_spec(spec, F, 0.2, solve_mode="fp64", block_bw=b) as one:
+        one.precond_setup()
+        h = one.sweep_clusters()
+        r1 = one.vector()
+        one.precond_apply(dev(rhs), r1)
+        one.sync()
+        r1 = r1.cpu().numpy()
+    with swj.BatchContext.from_spec(spec, [F, F], [0.2, 0.2], solve_mode="fp64", block_bw=b) as two:
+        two.precond_setup()
+        assert two.sweep_clusters() == 1
+        rb = two.vector()
+        two.precond_apply(dev(np.concatenate([rhs, rhs])), rb)
+        two.sync()
+        rb = two.view(rb).cpu().numpy()
+    hb = (spec.M - 1) if b == 0 else min((b - 1) // 2, spec.M - 1)
+    assert h == hb, (h, hb)          # the device holds these few clusters at once
+    assert np.array_equal(r1, rb[0]) and np.array_equal(r1, rb[1])
 
 
 def gpu_solve(spec, F, eps, **kw):
