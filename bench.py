@@ -632,7 +632,8 @@ def run_precond_only(args):
         t2 = time.perf_counter()
         st = ctx.solve(u)
         t3 = time.perf_counter()
-    print(json.dumps({"precond_only": True, "mesh": args.mesh, "block_bw": args.block_bw, "setup_ms": (t1 - t0) * 1e3,
+    print(json.dumps({"precond_only": True, "mesh": args.mesh, "block_bw": args.block_bw,
+                      "setup_ms": (t1 - t0) * 1e3,
                       "apply_ms": apply_ms, "sweep_clusters": clusters, "solve_ms": (t3 - t2) * 1e3,
                       "krylov_iters": st["krylov_iters"], "residual_evals": st["residual_evals"]}))
 

@@ -318,7 +318,10 @@ void swj_dgemm_batched(cudaStream_t st, int m, int n, int k, double alpha,
 {
     if (batch <= 0 || m <= 0 || n <= 0) return;
     SWJ_COUNT_LAUNCH();
-    if (tile == 32)
+    if (tile == 16)
+        k_dgemm<16><<<dim3(nblk(n, 16), nblk(m, 16), batch), 256, 0, st>>>(
+            m, n, k, alpha, A, nullptr, lda, B, nullptr, ldb, beta, C, nullptr, ldc);
+    else if (tile == 32)
         k_dgemm<32><<<dim3(nblk(n, 32), nblk(m, 32), batch), 256, 0, st>>>(
             m, n, k, alpha, A, nullptr, lda, B, nullptr, ldb, beta, C, nullptr, ldc);
     else

@@ -504,40 +504,60 @@ int swj_pc_setup(swj_ctx *c)
         }
         if (rc) return rc;
     } else {
-        // device pointer triples of the batched GEMMs of every step, all instances:
-        //   W_ik = inv_i S_ik (k = i+1..i+h), then S_jk -= S_ji W_ik (j, k = i+1..i+h),
-        //   the updates of block row i+1 (U1) apart from those of rows i+2.. (U2),
-        //   and L_ij = inv_i S_ij (j = i-h..i-1) into the scratch pc_lt (L)
+        // device pointer triples of the batched GEMMs of every step, all instances,
+        // in groups (kmax = min(i + h, M - 1)):
+        //   Wc  W_{i,i+1} = inv_i S_{i,i+1}
+        //   Uc  S_{i+1,i+1} -= S_{i+1,i} W_{i,i+1}
+        //   Wb  W_ik = inv_i S_ik, k = i+2..kmax
+        //   B1  S_jk -= S_ji W_ik for (j,k) = (i+1,i+2), (i+2,i+1), (i+2,i+2)
+        //   B2  S_jk -= S_ji W_ik for the other j, k = i+1..kmax
+        //   L   L_ij = inv_i S_ij, j = i-h..i-1, into the scratch pc_lt
+        enum { gWc, gUc, gWb, gB1, gB2, gL, kGroups };
         std::vector<const double *> PA, PB;
         std::vector<double *> PC;
-        std::vector<int> offW(M), cntW(M), offU1(M), cntU1(M), offU2(M), cntU2(M), offL(M), cntL(M);
+        std::vector<int> off((size_t)M * kGroups), cnt((size_t)M * kGroups);
+        auto begin = [&](int i, int g) { off[(size_t)i * kGroups + g] = (int)PA.size(); };
+        auto end = [&](int i, int g) {
+            cnt[(size_t)i * kGroups + g] = (int)PA.size() - off[(size_t)i * kGroups + g];
+        };
+        auto add = [&](const double *a, const double *b, double *cc) {
+            PA.push_back(a); PB.push_back(b); PC.push_back(cc);
+        };
+        auto chain_b1 = [&](int i, int j, int k) {
+            return (j == i + 1 && k == i + 1) || (j == i + 1 && k == i + 2) || (j == i + 2 && k == i + 1) ||
+                   (j == i + 2 && k == i + 2);
+        };
         for (int i = 0; i < M; ++i) {
-            int kmax = i + h < M - 1 ? i + h : M - 1;
-            offW[i] = (int)PA.size();
+            const int kmax = i + h < M - 1 ? i + h : M - 1;
+            begin(i, gWc);
             for (int q = 0; q < nb; ++q)
-                for (int k = i + 1; k <= kmax; ++k) {
-                    PA.push_back(blk(c, q, i, i)); PB.push_back(blk(c, q, i, k));
-                    PC.push_back(wblk(c, q, i, k));
-                }
-            cntW[i] = (int)PA.size() - offW[i];
-            for (int part = 0; part < 2; ++part) {
-                (part ? offU2 : offU1)[i] = (int)PA.size();
+                if (kmax >= i + 1) add(blk(c, q, i, i), blk(c, q, i, i + 1), wblk(c, q, i, i + 1));
+            end(i, gWc);
+            begin(i, gUc);
+            for (int q = 0; q < nb; ++q)
+                if (kmax >= i + 1) add(blk(c, q, i + 1, i), wblk(c, q, i, i + 1), blk(c, q, i + 1, i + 1));
+            end(i, gUc);
+            begin(i, gWb);
+            for (int q = 0; q < nb; ++q)
+                for (int k = i + 2; k <= kmax; ++k) add(blk(c, q, i, i), blk(c, q, i, k), wblk(c, q, i, k));
+            end(i, gWb);
+            for (int g : {gB1, gB2}) {
+                begin(i, g);
                 for (int q = 0; q < nb; ++q)
-                    for (int j = (part ? i + 2 : i + 1); j <= (part ? kmax : std::min(i + 1, kmax)); ++j)
+                    for (int j = i + 1; j <= kmax; ++j)
                         for (int k = i + 1; k <= kmax; ++k) {
-                            PA.push_back(blk(c, q, j, i)); PB.push_back(wblk(c, q, i, k));
-                            PC.push_back(blk(c, q, j, k));
+                            if (j == i + 1 && k == i + 1) continue;   // Uc
+                            if (chain_b1(i, j, k) != (g == gB1)) continue;
+                            add(blk(c, q, j, i), wblk(c, q, i, k), blk(c, q, j, k));
                         }
-                (part ? cntU2 : cntU1)[i] = (int)PA.size() - (part ? offU2 : offU1)[i];
+                end(i, g);
             }
             const int j0 = std::max(0, i - h);
-            offL[i] = (int)PA.size();
+            begin(i, gL);
             for (int q = 0; q < nb; ++q)
-                for (int j = j0; j < i; ++j) {
-                    PA.push_back(blk(c, q, i, i)); PB.push_back(blk(c, q, i, j));
-                    PC.push_back(c->pc_lt + ((size_t)q * h + (j - j0)) * n2);
-                }
-            cntL[i] = (int)PA.size() - offL[i];
+                for (int j = j0; j < i; ++j)
+                    add(blk(c, q, i, i), blk(c, q, i, j), c->pc_lt + ((size_t)q * h + (j - j0)) * n2);
+            end(i, gL);
         }
         int np = (int)PA.size();
         if (c->pc_ptrs_cap < np) {
@@ -565,17 +585,20 @@ int swj_pc_setup(swj_ctx *c)
                                      cudaMemcpyHostToDevice, st));
         SWJ_CUDA_TRY(cudaStreamSynchronize(st));   // `all` must outlive the copy
         double **dA = c->pc_ptrs, **dB = c->pc_ptrs + np, **dC = c->pc_ptrs + 2 * np;
-        // Look-ahead factorisation.  Step i on the chain stream: wait for the bulk
-        // updates of step i-2 (the last ones block row i receives), invert S_ii,
-        // W_i = inv_i S_i*, then wait for the bulk of step i-1 (it writes block row
-        // i+1 too) and update block row i+1 (U1).  The bulk stream updates rows
-        // i+2..i+h of step i (U2) once W_i exists, while the chain inverts the
-        // next diagonal blocks.  Events ev[0..3] follow W_i, ev[4..7] the bulk of
-        // step i (rings of 4: a wait is always enqueued before its event is
-        // recorded again).  After the bulk updates of step i the bulk stream
-        // also replaces block row i's left blocks by L_ij = inv_i S_ij (the
-        // forward substitution's factors; nothing of the set-up reads them
-        // after step i - 1), outside the event the chain waits for.
+        // Look-ahead factorisation.  The chain stream (high priority) runs only
+        // what the next diagonal block waits for: at step i it inverts S_ii,
+        // forms W_{i,i+1} and applies the one update S_{i+1,i+1} -= S_{i+1,i}
+        // W_{i,i+1}, then goes on with step i + 1.  The bulk stream forms the
+        // other W_ik, first the three updates step i + 1 of the chain reads
+        // (B1, event evB1), then all the others (B2), then replaces block row
+        // i's left blocks by L_ij = inv_i S_ij (the forward substitution's
+        // factors; nothing of the set-up reads them after step i - 1).  The
+        // chain waits for B1 of step i - 1 before W_{i,i+1}; every other
+        // update a chain product reads was enqueued on the bulk stream before
+        // that B1.  Every block receives its updates in the order of the steps,
+        // so the factors do not depend on timing.  Events: evW[i % 4] after
+        // W_{i,i+1}, evB1[i % 4] after B1 of step i (rings of 4: a wait is
+        // always enqueued before its event is recorded again).
         if (!c->pc_chain) {
             int lo = 0, hi = 0;
             cudaDeviceGetStreamPriorityRange(&lo, &hi);
@@ -584,12 +607,30 @@ int swj_pc_setup(swj_ctx *c)
             for (cudaEvent_t &e : c->pc_ev) SWJ_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         }
         cudaStream_t sc = c->pc_chain, sb = c->pc_bulk;
-        cudaEvent_t *evW = c->pc_ev, *evB = c->pc_ev + 4, evStart = c->pc_ev[8], evEnd = c->pc_ev[9];
+        cudaEvent_t *evW = c->pc_ev, *evB1 = c->pc_ev + 4, evStart = c->pc_ev[8], evEnd = c->pc_ev[9];
+        // Output tile of a batched product launch: the largest of 64, 32, 16 that
+        // still gives every SM a few CTAs.  One CTA of a 64-wide tile runs for
+        // ~0.2 ms on B300's FP64 pipe (two FMAs per clock per SM), so a launch of
+        // a few such CTAs leaves most SMs idle; the arithmetic of every output
+        // element is the same for all three tiles.
+        auto tile_for = [&](int products) {
+            const long t64 = (long)products * ((n1 + 63) / 64) * ((n1 + 63) / 64);
+            const long t32 = (long)products * ((n1 + 31) / 32) * ((n1 + 31) / 32);
+            if (t64 >= 4L * c->num_sms) return 64;
+            if (t32 >= 2L * c->num_sms) return 32;
+            return 16;
+        };
+        auto gemm = [&](cudaStream_t s, int i, int g, double alpha, double beta) {
+            const int o = off[(size_t)i * kGroups + g], n = cnt[(size_t)i * kGroups + g];
+            if (!n) return SWJ_OK;
+            swj_dgemm_batched(s, n1, n1, n1, alpha, (const double *const *)(dA + o), n1,
+                              (const double *const *)(dB + o), n1, beta, dC + o, n1, n, tile_for(n));
+            return SWJ_OK;
+        };
         SWJ_CUDA_TRY(cudaEventRecord(evStart, st));
         SWJ_CUDA_TRY(cudaStreamWaitEvent(sc, evStart, 0));
         SWJ_CUDA_TRY(cudaStreamWaitEvent(sb, evStart, 0));
         for (int i = 0; i < M; ++i) {
-            if (i >= 2) SWJ_CUDA_TRY(cudaStreamWaitEvent(sc, evB[(i - 2) % 4], 0));
             double *diag0 = blk(c, 0, i, i);
             if (gj_inplace) {
                 rc = swj_gj_inverse_cluster(sc, n1, nb, diag0, bst, diag0, bst, c->pc_info + (size_t)i * nb);
@@ -599,26 +640,17 @@ int swj_pc_setup(swj_ctx *c)
                 rc = swj_gj_inverse_cluster(sc, n1, nb, c->pc_work, n2, diag0, bst, c->pc_info + (size_t)i * nb);
             }
             if (rc) return rc;
-            if (cntW[i])
-                swj_dgemm_batched(sc, n1, n1, n1, 1.0, (const double *const *)(dA + offW[i]), n1,
-                                  (const double *const *)(dB + offW[i]), n1, 0.0, dC + offW[i], n1,
-                                  cntW[i], 32);
+            if (i >= 1) SWJ_CUDA_TRY(cudaStreamWaitEvent(sc, evB1[(i - 1) % 4], 0));
+            if ((rc = gemm(sc, i, gWc, 1.0, 0.0))) return rc;
             SWJ_CUDA_TRY(cudaEventRecord(evW[i % 4], sc));
-            if (i >= 1) SWJ_CUDA_TRY(cudaStreamWaitEvent(sc, evB[(i - 1) % 4], 0));
-            if (cntU1[i])
-                swj_dgemm_batched(sc, n1, n1, n1, -1.0, (const double *const *)(dA + offU1[i]), n1,
-                                  (const double *const *)(dB + offU1[i]), n1, 1.0, dC + offU1[i], n1,
-                                  cntU1[i], 32);
+            if ((rc = gemm(sc, i, gUc, -1.0, 1.0))) return rc;
             SWJ_CUDA_TRY(cudaStreamWaitEvent(sb, evW[i % 4], 0));
-            if (cntU2[i])
-                swj_dgemm_batched(sb, n1, n1, n1, -1.0, (const double *const *)(dA + offU2[i]), n1,
-                                  (const double *const *)(dB + offU2[i]), n1, 1.0, dC + offU2[i], n1,
-                                  cntU2[i], 64);
-            SWJ_CUDA_TRY(cudaEventRecord(evB[i % 4], sb));
-            if (cntL[i]) {
-                swj_dgemm_batched(sb, n1, n1, n1, 1.0, (const double *const *)(dA + offL[i]), n1,
-                                  (const double *const *)(dB + offL[i]), n1, 0.0, dC + offL[i], n1,
-                                  cntL[i], 64);
+            if ((rc = gemm(sb, i, gWb, 1.0, 0.0))) return rc;
+            if ((rc = gemm(sb, i, gB1, -1.0, 1.0))) return rc;
+            SWJ_CUDA_TRY(cudaEventRecord(evB1[i % 4], sb));
+            if ((rc = gemm(sb, i, gB2, -1.0, 1.0))) return rc;
+            if (cnt[(size_t)i * kGroups + gL]) {
+                if ((rc = gemm(sb, i, gL, 1.0, 0.0))) return rc;
                 const int nt = std::min(i, h);
                 SWJ_COUNT_LAUNCH();
                 k_copy_blocks<<<dim3(64, nb), 256, 0, sb>>>((size_t)nt * n2, c->pc_lt, (size_t)h * n2,

@@ -49,6 +49,45 @@ __device__ __forceinline__ void st_relaxed(double *p, double x)
                  : "memory");
 }
 
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint32_t map_rank(uint32_t a, int rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+
+// 8-byte store into the shared memory of a CTA of the cluster that completes
+// `bytes` of the transaction count of that CTA's mbarrier (both addresses
+// from map_rank)
+__device__ __forceinline__ void st_async_f64(uint32_t dst, double v, uint32_t mbar)
+{
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];"
+                 ::"r"(dst), "l"((unsigned long long)__double_as_longlong(v)), "r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *mb, int count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(mb)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect(uint64_t *mb, int bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mb)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t *mb, int parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok) : "r"(smem_addr(mb)), "r"(parity) : "memory");
+    return ok != 0;
+}
+
 __device__ __forceinline__ bool unset(double x) { return (unsigned long long)__double_as_longlong(x) == kUnset; }
 
 __device__ __forceinline__ double warp_sum(double a)
@@ -213,13 +252,15 @@ k_band_sweep(int n1, int M, int h, const double *__restrict__ band, size_t band_
 // slots cf, cb ([M][h+1][n1], slots 2..h used) are set to kUnset before the
 // launch, producers store each value once (relaxed, 8 bytes, single-copy
 // atomic) and consumers poll it until it is set.  In cluster 0 each CTA owns
-// a slice of rows, takes the next step's block rows into shared memory with
-// cp.async while the current step runs, keeps its z rows for the backward
-// pass, and sends every new element of z_i / x_i straight into the shared
-// memory of all CTAs of the cluster (one cluster barrier per step).  The
-// helpers are independent CTAs (no barrier between them).  The launch is
+// a slice of rows (at least one), takes the next step's block rows into
+// shared memory with cp.async while the current step runs, keeps p and then
+// its z rows in shared memory, reads the helpers' terms one step ahead, and
+// sends every new element of z_i / x_i into the shared memory of all CTAs of
+// the cluster by st.async, whose arrival each CTA awaits on an mbarrier (no
+// cluster barrier per step).  The helpers are independent CTAs.  The launch is
 // cooperative, so all clusters are resident at once; a poll that runs out
-// sets *err = 1, and a launch whose clusters are not of cs CTAs sets
+// sets *err = 1 (as does a barrier wait that runs out), and a launch whose
+// clusters are not of cs CTAs, each with one to two rows per warp, sets
 // *err = 2 and returns at once.
 template <int KC>
 __global__ void __launch_bounds__(kSweepThreads)
@@ -228,7 +269,8 @@ k_band_sweep_mc(int n1, int M, int h, const double *__restrict__ band, const dou
 {
     cg::cluster_group cl = cg::this_cluster();
     const int ncta = (int)cl.num_blocks();
-    if (ncta != cs || (int)gridDim.x != cs * h) {   // the same decision in every CTA
+    if (ncta != cs || (int)gridDim.x != cs * h || (cs - 1) * ((n1 + cs - 1) / cs) >= n1 ||
+        (n1 + cs - 1) / cs > 2 * (kSweepThreads / 32)) {   // the same decision in every CTA
         if (threadIdx.x == 0) atomicExch(err, 2);
         return;
     }
@@ -245,6 +287,7 @@ k_band_sweep_mc(int n1, int M, int h, const double *__restrict__ band, const dou
     double *vx = vz + 2 * (size_t)n1;             // [2][n1]: x by parity
     double *zs = vx + 2 * (size_t)n1;             // [M][rows]: this CTA's rows of z
     __shared__ int bad;
+    __shared__ __align__(8) uint64_t mbz[2], mbx[2];
     if (threadIdx.x == 0) bad = 0;
     __syncthreads();
     // rows [r0, r1) of one block into rb[buf] (16-byte copies where aligned)
@@ -272,69 +315,118 @@ k_band_sweep_mc(int n1, int M, int h, const double *__restrict__ band, const dou
         return v;
     };
     if (cid == 0) {
+        // Exchange inside the cluster: element r of z_i (x_i) goes from the CTA
+        // that owns row r to vz[i & 1][r] (vx[t & 1][r], t = M - 1 - i) of every
+        // CTA by st.async, which completes mbz[i & 1] (mbx[t & 1]) there; each
+        // CTA arms that barrier for n1 * 8 bytes at the start of the step and
+        // waits on it (the use count >> 1 gives the phase) before reading the
+        // vector.  A buffer is rewritten two steps later, only after every CTA
+        // produced its rows of the step in between, i.e. after every reader
+        // of the buffer has finished with it.
+        const int rpw = (nr + nw - 1) / nw;   // rows per warp (<= 2, checked at launch)
+        if (threadIdx.x == 0) {
+            for (int q = 0; q < 2; ++q) {
+                mbar_init(&mbz[q], 1);
+                mbar_init(&mbx[q], 1);
+            }
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        // this CTA's rows of p into zs (z overwrites them step by step)
+        for (int e = threadIdx.x; e < M * nr; e += blockDim.x)
+            zs[(size_t)(e / nr) * rows + e % nr] = p[(size_t)(e / nr) * n1 + r0 + e % nr];
+        cl.sync();
+        auto wait_bar = [&](uint64_t *mb, int parity) {
+            if (*(volatile int *)&bad) return;
+            int it = 0;
+            while (!mbar_test(mb, parity))
+                if (++it > kPollLimit) {
+                    bad = 1;
+                    atomicExch(err, 1);
+                    return;
+                }
+        };
+        auto send = [&](double *vec, uint64_t *mb, int r, double v) {
+            if (lane < ncta) st_async_f64(map_rank(smem_addr(vec + r), lane), v, map_rank(smem_addr(mb), lane));
+        };
+        // lane d (2..h) of the warp of row rr reads term d of that row (first read;
+        // poll() finishes it when the value is used)
+        double cur[2] = {0.0, 0.0};
+        auto read_terms = [&](const double *slots, int step, int nd, double &o0, double &o1) {
+            if (lane >= 2 && lane <= nd) {
+                const double *a = slots + ((size_t)step * hs + lane) * n1 + r0;
+                if (warp < nr) o0 = ld_relaxed(a + warp);
+                if (warp + nw < nr) o1 = ld_relaxed(a + warp + nw);
+            }
+        };
         // ---- forward: step i reads L_{i,i-1} from rb[i & 1] and prefetches
-        //      L_{i+1,i} into the other buffer (read at step i - 1, before the
-        //      barrier that ended it)
+        //      L_{i+1,i} into the other buffer
+        read_terms(cf, 0, 0, cur[0], cur[1]);
         for (int i = 0; i < M; ++i) {
+            const int nd = min(h, i);   // terms c_{i,2..nd}
+            __syncthreads();            // every warp is done with step i - 1 (rb, zs)
+            if (threadIdx.x == 0) mbar_expect(&mbz[i & 1], n1 * (int)sizeof(double));
             if (i + 1 < M) prefetch((i + 1) & 1, band + ((size_t)(i + 1) * nbk + (h - 1)) * n2);
             __pipeline_commit();
-            const int nd = min(h, i);   // terms c_{i,2..nd}
-            // lane 0: p_i[r]; lane d (2..nd): first read of c_{i,d}[r]
-            auto addr = [&](int rr) { return cf + ((size_t)i * hs + lane) * n1 + r0 + rr; };
-            double mine = 0.0;
-            if (warp < nr) {
-                if (lane == 0) mine = p[(size_t)i * n1 + r0 + warp];
-                else if (lane >= 2 && lane <= nd) mine = ld_relaxed(addr(warp));
-            }
             __pipeline_wait_prior(1);
             __syncthreads();
-            for (int rr = warp; rr < nr; rr += nw) {
+            if (i > 0) wait_bar(&mbz[(i - 1) & 1], ((i - 1) >> 1) & 1);
+            double nxt[2] = {0.0, 0.0};
+            if (i + 1 < M) read_terms(cf, i + 1, min(h, i + 1), nxt[0], nxt[1]);
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int rr = warp + q * nw;
+                if (q >= rpw || rr >= nr) break;
                 const int r = r0 + rr;
-                if (rr != warp) {
-                    if (lane == 0) mine = p[(size_t)i * n1 + r];
-                    else if (lane >= 2 && lane <= nd) mine = ld_relaxed(addr(rr));
-                }
-                double s = 0.0;
-                if (i > 0) s = block_dot<KC>(rb + ((size_t)(i & 1) * rows + rr) * n1, vz + (size_t)((i - 1) & 1) * n1, n1, lane);
-                if (lane >= 2 && lane <= nd) mine = poll(addr(rr), mine);
-                double v = __shfl_sync(0xffffffffu, mine, 0);
-                if (i > 0) v -= s;
-                for (int d = 2; d <= nd; ++d) v -= __shfl_sync(0xffffffffu, mine, d);
+                double v = zs[(size_t)i * rows + rr];
+                if (i > 0) v -= block_dot<KC>(rb + ((size_t)(i & 1) * rows + rr) * n1, vz + (size_t)((i - 1) & 1) * n1, n1, lane);
+                if (lane >= 2 && lane <= nd) cur[q] = poll(cf + ((size_t)i * hs + lane) * n1 + r, cur[q]);
+                for (int d = 2; d <= nd; ++d) v -= __shfl_sync(0xffffffffu, cur[q], d);
                 if (lane == 0) {
                     st_relaxed(z + (size_t)i * n1 + r, v);
                     zs[(size_t)i * rows + rr] = v;
                 }
-                if (lane < ncta) *cl.map_shared_rank(vz + (size_t)(i & 1) * n1 + r, lane) = v;
+                send(vz + (size_t)(i & 1) * n1, &mbz[i & 1], r, v);
             }
-            cl.sync();
+            cur[0] = nxt[0];
+            cur[1] = nxt[1];
         }
-        // ---- backward: step i (t = M - 1 - i) reads W_{i,i+1} from rb[t & 1]
-        //      and prefetches W_{i-1,i} into the other buffer
+        // ---- backward: step t = M - 1 - i reads W_{i,i+1} from rb[t & 1] and
+        //      prefetches W_{i-1,i} into the other buffer
+        __syncthreads();
+        read_terms(cb, M - 1, 0, cur[0], cur[1]);
         for (int i = M - 1; i >= 0; --i) {
             const int t = M - 1 - i;
+            const int ne = min(h, M - 1 - i);   // terms b_{i,2..ne}
+            __syncthreads();
+            if (threadIdx.x == 0) mbar_expect(&mbx[t & 1], n1 * (int)sizeof(double));
             if (i >= 1) prefetch((t + 1) & 1, W + ((size_t)(i - 1) * h) * n2);
             __pipeline_commit();
-            const int ne = min(h, M - 1 - i);   // terms b_{i,2..ne}
-            auto addr = [&](int rr) { return cb + ((size_t)i * hs + lane) * n1 + r0 + rr; };
-            double mine = 0.0;
-            if (warp < nr && lane >= 2 && lane <= ne) mine = ld_relaxed(addr(warp));
             __pipeline_wait_prior(1);
             __syncthreads();
-            for (int rr = warp; rr < nr; rr += nw) {
+            if (t > 0) wait_bar(&mbx[(t - 1) & 1], ((t - 1) >> 1) & 1);
+            double nxt[2] = {0.0, 0.0};
+            if (i >= 1) read_terms(cb, i - 1, min(h, M - i), nxt[0], nxt[1]);
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int rr = warp + q * nw;
+                if (q >= rpw || rr >= nr) break;
                 const int r = r0 + rr;
-                if (rr != warp && lane >= 2 && lane <= ne) mine = ld_relaxed(addr(rr));
-                double s = 0.0;
-                if (i < M - 1) s = block_dot<KC>(rb + ((size_t)(t & 1) * rows + rr) * n1, vx + (size_t)((i + 1) & 1) * n1, n1, lane);
-                if (lane >= 2 && lane <= ne) mine = poll(addr(rr), mine);
                 double v = zs[(size_t)i * rows + rr];
-                if (i < M - 1) v -= s;
-                for (int e = 2; e <= ne; ++e) v -= __shfl_sync(0xffffffffu, mine, e);
+                if (t > 0) v -= block_dot<KC>(rb + ((size_t)(t & 1) * rows + rr) * n1, vx + (size_t)((t - 1) & 1) * n1, n1, lane);
+                if (lane >= 2 && lane <= ne) cur[q] = poll(cb + ((size_t)i * hs + lane) * n1 + r, cur[q]);
+                for (int e = 2; e <= ne; ++e) v -= __shfl_sync(0xffffffffu, cur[q], e);
                 if (lane == 0) st_relaxed(x + (size_t)i * n1 + r, v);
-                if (lane < ncta) *cl.map_shared_rank(vx + (size_t)(i & 1) * n1 + r, lane) = v;
+                send(vx + (size_t)(t & 1) * n1, &mbx[t & 1], r, v);
             }
-            cl.sync();
+            cur[0] = nxt[0];
+            cur[1] = nxt[1];
         }
         __pipeline_wait_prior(0);
+        // the last vectors were sent but not read: wait for them, so that no
+        // store into this CTA's shared memory is in flight when it exits
+        wait_bar(&mbz[(M - 1) & 1], ((M - 1) >> 1) & 1);
+        wait_bar(&mbx[(M - 1) & 1], ((M - 1) >> 1) & 1);
+        cl.sync();
     } else {
         const int d = cid + 1;   // 2..h
         // forward terms c_{j+d,d} = L_{j+d,j} z_j (slot h - d of block row j + d)
@@ -431,7 +523,12 @@ static int launch_sweep_mc(cudaStream_t st, int n1, int M, int h, const double *
         auto it = g_mc_cache.find(key);
         if (it == g_mc_cache.end()) {
             std::pair<int, size_t> pick(0, 0);
-            for (int c : {16, 8}) {
+            for (int c0 : {16, 8}) {
+                // as many CTAs as it takes to give each the same number of rows
+                // (every CTA owns at least one row: the exchange relies on it),
+                // at most two rows per warp
+                const int rows = (n1 + c0 - 1) / c0, c = (n1 + rows - 1) / rows;
+                if (rows > 2 * (kSweepThreads / 32)) continue;
                 const size_t sm = mc_smem_bytes(n1, M, c);
                 if (sm > 220 * 1024) continue;
                 swj_cluster_for(kern, kSweepThreads, sm);   // raises the kernel's limit to sm

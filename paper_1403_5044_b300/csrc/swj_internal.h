@@ -206,7 +206,7 @@ void swj_bcombine(cudaStream_t st, int nb, int n, int rows, const double *Z, siz
 // arrays; output tiles of `tile` (64, or 32 for small products that must spread over SMs)
 void swj_dgemm_batched(cudaStream_t st, int m, int n, int k, double alpha,
                        const double *const *A, int lda, const double *const *B, int ldb,
-                       double beta, double *const *C, int ldc, int batch, int tile = 64);
+                       double beta, double *const *C, int ldc, int batch, int tile = 64);   // tile 16, 32 or 64
 void swj_dgemm(cudaStream_t st, int m, int n, int k, double alpha, const double *A, int lda,
                const double *B, int ldb, double beta, double *C, int ldc);
 
