@@ -23,6 +23,8 @@ Contents, in the paper's order:
   * equation ordering                             (Appendix A)
   * linear Jacobian used by the preconditioner    (Appendix B, Eqs. PreA-PreD)
   * finite-difference Jacobian-vector product     (Eq. JvApprox)
+  * the exact Jacobian-vector product, by the
+    complex-step derivative of E                  (the derivative Eq. JvApprox approximates)
   * reference root-finders (dense FD-Newton for tiny meshes, Newton-GMRES
     with the linear-Jacobian preconditioner)      (Section 4)
 
@@ -84,6 +86,9 @@ def _lib():
                                                ctypes.c_double, ctypes.c_double] + [dp] * 8 + \
             [ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp, dp]
         lib.oracle_pairsum_targets.restype = None
+        lib.oracle_pairsum_cs.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_double] + [ctypes.c_void_p] * 9 + [dp]
+        lib.oracle_pairsum_cs.restype = None
         _LIB = lib
     return _LIB
 
@@ -133,8 +138,9 @@ def unpack(mesh: Mesh, u):
     """Split u per Eq. unknowns into phi_1[l], phi_x[l, k], zeta_1[l], zeta_x[l, k]."""
     N, M = mesh.N, mesh.M
     half = (N + 1) * M
-    P = np.asarray(u[:half], dtype=np.float64).reshape(M, N + 1)
-    Z = np.asarray(u[half:], dtype=np.float64).reshape(M, N + 1)
+    dt = np.complex128 if np.iscomplexobj(u) else np.float64   # complex: jvp_exact's step
+    P = np.asarray(u[:half], dtype=dt).reshape(M, N + 1)
+    Z = np.asarray(u[half:], dtype=dt).reshape(M, N + 1)
     return P[:, 0].copy(), P[:, 1:].copy(), Z[:, 0].copy(), Z[:, 1:].copy()
 
 
@@ -168,7 +174,8 @@ def spline_slope_y(mesh: Mesh, f):
     """d f / d y at the mesh nodes from the cubic spline through f[:, k] in y
     for every k (Section 3).  End conditions (R5): zero slope at y1 = 0, the
     even extension of the symmetric flow, and not-a-knot at y_M."""
-    f = np.asarray(f, dtype=np.float64)
+    f = np.asarray(f)
+    f = f if np.iscomplexobj(f) else f.astype(np.float64)   # complex for the complex step only
     cs = CubicSpline(mesh.y(), f, axis=0,
                      bc_type=((1, np.zeros(f.shape[1:])), "not-a-knot"))
     return cs(mesh.y(), 1)
@@ -214,9 +221,13 @@ def _G(A, B, C, s, t):
     D = 4AC - B^2 > 0.  Each term is zero where its prefactor s or t is zero
     (its limit there).  The asinh form is the logarithm form of the paper
     with one-variable terms dropped; they cancel in the four-corner sum."""
-    A, B, C, s, t = np.broadcast_arrays(*[np.asarray(v, dtype=np.float64) for v in (A, B, C, s, t)])
+    # (A, B, C are complex only under the complex step of jvp_exact; s, t are geometry)
+    dt = np.result_type(np.asarray(A), np.asarray(B), np.asarray(C), np.float64)
+    A, B, C = (np.asarray(v, dtype=dt) for v in (A, B, C))
+    s, t = (np.asarray(v, dtype=np.float64) for v in (s, t))
+    A, B, C, s, t = np.broadcast_arrays(A, B, C, s, t)
     sD = np.sqrt(4.0 * A * C - B * B)
-    out = np.zeros(s.shape)
+    out = np.zeros(s.shape, dtype=dt)
     ns, nt = s != 0.0, t != 0.0
     out[ns] += s[ns] / np.sqrt(C[ns]) * np.arcsinh((B[ns] * s[ns] + 2.0 * C[ns] * t[ns]) / (sD[ns] * np.abs(s[ns])))
     out[nt] += t[nt] / np.sqrt(A[nt]) * np.arcsinh((2.0 * A[nt] * s[nt] + B[nt] * t[nt]) / (sD[nt] * np.abs(t[nt])))
@@ -251,8 +262,19 @@ def free_surface_E1(F, phix, phiy, zetax, zetay, zeta):
 
 def integral_sum(mesh: Mesh, st):
     """The trapezoidal all-pairs sum of E2 (C, ``pairsum.c``); returns the
-    sum and the per-target sum of absolute term values, both [M, N-1]."""
+    sum and the per-target sum of absolute term values, both [M, N-1].
+    With complex mesh values (the complex step of jvp_exact) the sum is
+    complex and the second array sums |Im| of the terms."""
     N, M = mesh.N, mesh.M
+    if any(np.iscomplexobj(st[k]) for k in ("zeta", "zetax", "zetay", "g", "zeta_t", "zetax_t", "zetay_t", "g_t")):
+        cc = lambda a: np.ascontiguousarray(a, dtype=np.complex128)
+        arrs = [cc(st[k]) for k in ("zeta", "zetax", "zetay", "g", "zeta_t", "zetax_t", "zetay_t", "g_t")]
+        s = np.zeros((M, N - 1), dtype=np.complex128)
+        a = np.zeros((M, N - 1))
+        _lib().oracle_pairsum_cs(N, M, mesh.x1, mesh.dx, mesh.dy,
+                                 *[ctypes.c_void_p(x.ctypes.data) for x in arrs],
+                                 ctypes.c_void_p(s.ctypes.data), _p(a))
+        return s, a
     c = lambda a: np.ascontiguousarray(a, dtype=np.float64)
     zeta, zetax, zetay, g = c(st["zeta"]), c(st["zetax"]), c(st["zetay"]), c(st["g"])
     zt, zxt, zyt, gt = c(st["zeta_t"]), c(st["zetax_t"]), c(st["zetay_t"]), c(st["g_t"])
@@ -320,7 +342,7 @@ def residual_parts(mesh: Mesh, F: float, eps: float, u, pairs: bool = True):
     E6 = x1 * (zetax[:, 1] - zetax[:, 0]) / dx + n * zetax[:, 0]
     scale2 = Sabs + np.abs(2 * math.pi * st["g_t"]) + np.abs(src) + np.abs(zxt * I)
     return dict(E1=E1, E2=E2, E3=E3, E4=E4, E5=E5, E6=E6, I=I, src=src, S=S,
-                scale2=scale2, st=st)
+                scale2=scale2, st=st, Sabs=Sabs)
 
 
 def order(mesh: Mesh, E1, E2, E3, E4, E5, E6):
@@ -447,6 +469,27 @@ def jvp_fd(mesh, F, eps, u, v, Eu=None, h=None):
     if h is None:
         h = fd_step(u, v)
     return (residual(mesh, F, eps, u + h * v) - Eu) / h
+
+
+def jvp_exact(mesh, F, eps, u, v, h=1e-30):
+    """J(u) v of the discrete residual, exactly (to rounding): the directional
+    derivative d E(u + t v) / dt at t = 0, computed by the complex step
+    Im E(u + i h v) / h.  Every operation of E is analytic in u (the
+    trapezoid and spline are linear, the kernels and the closed form of I are
+    compositions of products, quotients, square roots and asinh), so no
+    difference is taken and h only needs to be tiny.  Returns (Jv, scale):
+    scale is, per E2 row, the sum of |d/dt| of the terms of the row (the
+    tolerance scale of the row), and |Jv| elsewhere."""
+    uc = np.asarray(u, dtype=np.float64) + 1j * h * np.asarray(v, dtype=np.float64)
+    p = residual_parts(mesh, F, eps, uc)
+    Jv = order(mesh, p["E1"], p["E2"], p["E3"], p["E4"], p["E5"], p["E6"]).imag / h
+    st = p["st"]
+    s2 = (p["Sabs"] + np.abs((2 * math.pi * st["g_t"]).imag) + np.abs(p["src"].imag)
+          + np.abs((st["zetax_t"] * p["I"]).imag)) / h
+    z = lambda e: np.zeros(e.shape)
+    scale = order(mesh, z(p["E1"]), s2, z(p["E3"]), z(p["E4"]), z(p["E5"]), z(p["E6"]))
+    scale = np.where(scale > 0, scale, np.abs(Jv))
+    return Jv, scale
 
 
 def jacobian_fd(mesh, F, eps, u, h=1e-6):

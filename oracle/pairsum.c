@@ -36,6 +36,7 @@
  * OpenMP when it is enabled at compile time.
  */
 #include <math.h>
+#include <complex.h>
 
 /* The three kernel values of one (source, target) pair.  Exposed so the
  * tests can pin each kernel against its geometric definition. */
@@ -127,4 +128,72 @@ void oracle_pairsum_targets(int N, int M, double x1, double dxm, double dym,
     for (int q = 0; q < nt; ++q)
         one_target(tidx[q], N, M, x1, dxm, dym, zeta, zetax, zetay, g, zeta_t,
                    zetax_t, zetay_t, g_t, &sum[q], &asum[q]);
+}
+
+/*
+ * Complex-step form of the same sum, for the exact directional derivative:
+ * every grid and target value is a complex number (arrays of interleaved
+ * re, im pairs, the layout of C99 double complex).  The kernels K1, K2, S2
+ * are analytic in every value, so for inputs u + i h v with h tiny,
+ * Im(sum) / h equals d sum(u + t v) / dt at t = 0 to rounding (the
+ * complex-step derivative; no subtractive cancellation).  aim[t] is the sum
+ * over sources of |Im| of the three terms, the scale of the derivative.
+ */
+static void one_target_cs(int t, int N, int M, double x1, double dxm, double dym,
+                          const double complex *zeta, const double complex *zetax,
+                          const double complex *zetay, const double complex *g,
+                          const double complex *zeta_t, const double complex *zetax_t,
+                          const double complex *zetay_t, const double complex *g_t,
+                          double complex *sum_out, double *aim_out)
+{
+    int k = t % (N - 1);
+    int l = t / (N - 1);
+    double xt = x1 + ((double)k + 0.5) * dxm;
+    double yt = (double)l * dym;
+    double complex zt = zeta_t[t], zxt = zetax_t[t], zyt = zetay_t[t], gt = g_t[t];
+    double complex A = 1.0 + zxt * zxt;
+    double complex B = 2.0 * zxt * zyt;
+    double complex C = 1.0 + zyt * zyt;
+    double complex s = 0.0;
+    double a = 0.0;
+    for (int j = 0; j < M; ++j) {
+        double yj = (double)j * dym;
+        double cj = (j == 0 || j == M - 1) ? 0.5 : 1.0;
+        for (int i = 0; i < N; ++i) {
+            double xi = x1 + (double)i * dxm;
+            double ci = (i == 0 || i == N - 1) ? 0.5 : 1.0;
+            double w = dxm * dym * ci * cj;
+            int p = j * N + i;
+            double dx = xi - xt, dy = yj - yt, dyp = yj + yt;
+            double complex dz = zeta[p] - zt;
+            double complex r1 = csqrt(dx * dx + dy * dy + dz * dz);
+            double complex r2 = csqrt(dx * dx + dyp * dyp + dz * dz);
+            double complex K1 = (dz - dx * zetax[p] - dy * zetay[p]) / (r1 * r1 * r1)
+                              + (dz - dx * zetax[p] - dyp * zetay[p]) / (r2 * r2 * r2);
+            double complex K2 = 1.0 / r1 + 1.0 / r2;
+            double complex S2 = 1.0 / csqrt(A * dx * dx + B * dx * dy + C * dy * dy)
+                              + 1.0 / csqrt(A * dx * dx - B * dx * dyp + C * dyp * dyp);
+            double complex t1 = w * (g[p] - gt) * K1;
+            double complex t2 = w * zetax[p] * K2;
+            double complex t3 = w * zxt * S2;
+            s += t1 + t2 - t3;
+            a += fabs(cimag(t1)) + fabs(cimag(t2)) + fabs(cimag(t3));
+        }
+    }
+    *sum_out = s;
+    *aim_out = a;
+}
+
+void oracle_pairsum_cs(int N, int M, double x1, double dxm, double dym,
+                       const double complex *zeta, const double complex *zetax,
+                       const double complex *zetay, const double complex *g,
+                       const double complex *zeta_t, const double complex *zetax_t,
+                       const double complex *zetay_t, const double complex *g_t,
+                       double complex *sum, double *aim)
+{
+    int T = (N - 1) * M;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int t = 0; t < T; ++t)
+        one_target_cs(t, N, M, x1, dxm, dym, zeta, zetax, zetay, g, zeta_t, zetax_t,
+                      zetay_t, g_t, &sum[t], &aim[t]);
 }

@@ -274,6 +274,64 @@ def test_fd_jvp_is_first_order():
     assert 1.8 < e1 / e2 < 2.2
 
 
+def test_exact_jvp_is_the_limit_of_fourth_order_differences():
+    """The complex-step J v against fourth-order central differences of the
+    real residual: the gap shrinks like h^4 (a factor ~10^4 per decade of h)
+    until the differences' own rounding (~eps_mach |E| / h) takes over, so it
+    is the derivative, not an approximation with an error of its own."""
+    spec = TINY
+    mesh = _mesh(spec)
+    u = W.random_state(spec, seed=10, amp=0.1)
+    v = np.random.default_rng(11).normal(size=u.size)
+    F, eps = 0.7, 0.3
+    Jv, scale = O.jvp_exact(mesh, F, eps, u, v)
+    E = lambda w: O.residual(mesh, F, eps, w)
+    gaps = []
+    for h in (1e-2, 1e-3, 1e-4):
+        ref = (8 * (E(u + h * v) - E(u - h * v)) - (E(u + 2 * h * v) - E(u - 2 * h * v))) / (12 * h)
+        gaps.append(np.abs(Jv - ref).max() / np.abs(Jv).max())
+    assert 3e3 < gaps[0] / gaps[1] < 3e4
+    assert gaps[2] < gaps[1] / 5 and gaps[2] < 1e-9
+    assert np.all(scale >= np.abs(Jv) * (1 - 1e-12))
+
+
+def test_exact_jvp_at_the_flat_state_is_the_appendix_B_jacobian():
+    """At the flat state with eps = 0 the exact Jacobian of E is the linear
+    Jacobian written case by case from Eqs. PreA-PreD (Appendix B)."""
+    for spec in (TINY, W.MeshSpec(12, 6, -3.0, 0.5, 0.45)):
+        mesh = _mesh(spec)
+        u0 = O.flat_guess(mesh)
+        P = O.jacobian_linear(mesh, 0.8)
+        for seed in (12, 13):
+            v = np.random.default_rng(seed).normal(size=u0.size)
+            Jv, _ = O.jvp_exact(mesh, 0.8, 0.0, u0, v)
+            assert np.abs(Jv - P @ v).max() <= 1e-13 * np.abs(P @ v).max()
+
+
+def test_exact_jvp_is_linear_in_v():
+    spec = TINY
+    mesh = _mesh(spec)
+    u = W.random_state(spec, seed=14, amp=0.1)
+    rng = np.random.default_rng(15)
+    v1, v2 = rng.normal(size=u.size), rng.normal(size=u.size)
+    J = lambda v: O.jvp_exact(mesh, 0.7, 0.3, u, v)[0]
+    a, b = J(v1), J(v2)
+    assert np.abs(J(2 * v1 - 3 * v2) - (2 * a - 3 * b)).max() <= 1e-13 * np.abs(a).max()
+
+
+def test_complex_step_leaves_the_real_residual_unchanged():
+    """The oracle's complex path (used only by jvp_exact) evaluated at a real
+    point gives the real residual."""
+    spec = TINY
+    mesh = _mesh(spec)
+    u = W.random_state(spec, seed=16, amp=0.1)
+    p = O.residual_parts(mesh, 0.7, 0.3, u.astype(np.complex128))
+    Ec = O.order(mesh, p["E1"], p["E2"], p["E3"], p["E4"], p["E5"], p["E6"])
+    Er = O.residual(mesh, 0.7, 0.3, u)
+    assert np.abs(Ec.imag).max() == 0.0
+    assert np.abs(Ec.real - Er).max() <= 1e-13 * max(1.0, np.abs(Er).max())
+
+
 def test_dense_newton_and_newton_gmres_reach_the_same_root():
     spec = TINY
     mesh = _mesh(spec)
