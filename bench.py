@@ -311,6 +311,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         e2e_ms.append(a.elapsed_time(b))
 
+    exact = exact_jvp_section(spec, F, eps, args, stream, flush, zeta_mixed) if rank == 0 else None
+
     batch = run_batch(args, stream, flush) if args.batch_steps > 0 else None
     serve = None
     if args.serve_requests > 0 and rank == 0:
@@ -382,12 +384,78 @@ def run_ours(args):
                 "unit": "solves/s", "h2d_bytes_per_step": ctx.n_unknowns * 8,
                 "d2h_bytes_per_step": spec.N * spec.M * 8},
         "gpu_launches": int(launches),
+        "exact_jvp": exact,
         "batch": batch,
         "serve": serve,
         "clocks": {"sm_mhz": cs["sm_mhz"], "sm_max_mhz": cs["sm_max_mhz"], "reasons": cs["reasons"]},
         "wall_s_timed": wall,
     }
     print(json.dumps(out), flush=True)
+
+
+TAN_FLOP_PER_PAIR = 88   # tangent pair: 12 add + 24 mul + 26 FMA (FMA = 2) + 4 rsqrt
+
+
+def exact_jvp_section(spec, F, eps, args, stream, flush, zeta_ref):
+    """The exact Jacobian-vector product (swj_jvp_exact) on the 181x61 workload:
+    time per product in FP32 and FP64 at a converged state, against one FP32
+    residual (what an FD product costs), and a mixed solve whose GMRES uses it."""
+    import numpy as np
+    import torch
+    from paper_1403_5044_b300 import swj
+    ctx = swj.Context.from_spec(spec, F, eps, solve_mode="mixed", block_bw=args.block_bw, stream=stream,
+                                jvp=swj.JVP_EXACT)
+    u = ctx.initial_guess_flat(ctx.vector())
+    for _ in range(args.warmup):
+        ctx.initial_guess_flat(u)
+        ctx.precond_setup()
+        st = ctx.solve(u)
+    ctx.sync()
+    t = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.initial_guess_flat(u)
+        ctx.precond_setup()
+        st = ctx.solve(u)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t.append(a.elapsed_time(b))
+    zeta = torch.empty(spec.N * spec.M, dtype=torch.float64, device="cuda")
+    ctx.unpack(u, zeta, None)
+    ctx.sync()
+    dz = float(np.abs(zeta.cpu().numpy() - zeta_ref).max())
+    v = torch.tensor(np.random.default_rng(5).normal(size=ctx.n_unknowns), device="cuda")
+    J, E = ctx.vector(), ctx.vector()
+
+    def per_call(fn, reps=20):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    ms32 = per_call(lambda: ctx.jvp_exact(u, v, J, swj.FP32))
+    ms64 = per_call(lambda: ctx.jvp_exact(u, v, J, swj.FP64), reps=5)
+    msr = per_call(lambda: ctx.residual(u, E, swj.FP32))
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    peak = sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    ctx.close()
+    return {"fp32_ms": ms32, "fp64_ms": ms64, "fp32_residual_ms": msr,
+            "fp32_tflops_whole_product": TAN_FLOP_PER_PAIR * spec.pairs / (ms32 * 1e-3) / 1e12,
+            "fp32_frac_whole_product": TAN_FLOP_PER_PAIR * spec.pairs / (ms32 * 1e-3) / 1e12 / peak,
+            "flop_per_pair": TAN_FLOP_PER_PAIR,
+            "mixed_solve": {"solves_per_s": 1e3 / (sum(t) / len(t)), "ms": sum(t) / len(t),
+                            "krylov_iters": st["krylov_iters"], "exact_jvps": st["exact_jvps"],
+                            "residual_evals": st["residual_evals"], "newton_iters": st["newton_iters"],
+                            "final_norm_inf_fp64": st["final_norm_inf_fp64"],
+                            "max_abs_dzeta_vs_fd_mixed": dz}}
 
 
 def run_batch(args, stream, flush):

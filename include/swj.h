@@ -100,7 +100,14 @@ typedef struct swj_opts {
     int    refine_precision; /* MIXED: all-pairs precision of the refinement          */
                            /* residuals: SWJ_FF (float-float, as accurate as FP64 and */
                            /* ~8x faster on this GPU) or SWJ_FP64 (SWJ_FF)            */
+    int    jvp;            /* Jacobian-vector products of GMRES: SWJ_JVP_FD (the      */
+                           /* difference quotient of Eq. JvApprox) or SWJ_JVP_EXACT   */
+                           /* (swj_jvp_exact, all-pairs part in the phase's precision)*/
+                           /* (SWJ_JVP_FD)                                            */
 } swj_opts;
+
+#define SWJ_JVP_FD    0
+#define SWJ_JVP_EXACT 1
 
 /* Counters and timings of one solve (KINSOL-style counters). */
 typedef struct swj_stats {
@@ -122,6 +129,7 @@ typedef struct swj_stats {
     int    pairs_per_residual_hi, pairs_per_residual_lo;  /* (N-1)M*NM as 2x31 bits */
     int    residual_evals_ff;    /* of which with the float-float all-pairs sum (the */
                                  /* right-hand side of the MIXED refinement)         */
+    int    exact_jvps;           /* GMRES iterations that used swj_jvp_exact (opts.jvp) */
 } swj_stats;
 
 typedef struct swj_ctx swj_ctx;
@@ -201,6 +209,17 @@ int swj_residual(swj_ctx *ctx, const double *u_dev, double *E_dev, int precision
  * with eps_mach of `precision`.  Async. */
 int swj_jvp(swj_ctx *ctx, const double *u_dev, const double *Eu_dev,
             const double *v_dev, double *Jv_dev, int precision);
+
+/* Jv_dev <- J(u) v exactly: the derivative d E(u + t v) / dt at t = 0, by
+ * forward-mode differentiation of every step of E (mesh step, per-target
+ * terms, the closed form of I, the all-pairs sum), the analytic counterpart
+ * of the difference quotient of Eq. JvApprox: no step size, no truncation
+ * error.  The all-pairs part is computed in `precision` (SWJ_FP64, or SWJ_FP32
+ * with Kahan compensation); everything else in FP64.  u_dev, v_dev, Jv_dev:
+ * device, count * 2(N+1)M doubles, Appendix A order; Jv_dev must not alias u
+ * or v.  Async.  SWJ_EINVAL for a null pointer or another precision. */
+int swj_jvp_exact(swj_ctx *ctx, const double *u_dev, const double *v_dev, double *Jv_dev,
+                  int precision);
 
 /* Build and factor the preconditioner P for the context's mesh, F and
  * block_bw: the linear Jacobian of Appendix B (Eqs. PreA-PreD plus the

@@ -20,10 +20,12 @@ constexpr double kPi = 3.14159265358979323846;
 
 // Warp per mesh row.  Rows 0..M-1 integrate phi_x - 1 from g_1 = phi_1 - x1
 // (so the result is g = phi - x exactly as the trapezoidal rule integrates
-// the constant 1 exactly); rows M..2M-1 integrate zeta_x from zeta_1.
+// the constant 1 exactly); rows M..2M-1 integrate zeta_x from zeta_1.  With
+// `tangent` the input is a direction v and the rule is applied without the
+// constants (the derivative of the map, which is affine in u).
 __global__ void k_integrate(int N, int M, int H, double x1, double dx,
                             const double *__restrict__ u, double *__restrict__ zeta,
-                            double *__restrict__ g, const int *__restrict__ act)
+                            double *__restrict__ g, const int *__restrict__ act, bool tangent = false)
 {
     const int inst = blockIdx.y;
     if (!SWJ_INST_ACTIVE(act, inst)) return;
@@ -37,8 +39,8 @@ __global__ void k_integrate(int N, int M, int H, double x1, double dx,
     int l = isz ? warp - M : warp;
     const double *row = u + (isz ? H : 0) + (size_t)l * (N + 1);
     double *out = (isz ? zeta : g) + (size_t)l * N;
-    double shift = isz ? 0.0 : 1.0;
-    double f1 = isz ? row[0] : row[0] - x1;
+    double shift = (isz || tangent) ? 0.0 : 1.0;
+    double f1 = (isz || tangent) ? row[0] : row[0] - x1;
     double hdx = 0.5 * dx;
     int per = (N + 31) / 32;
     int k0 = lane * per, k1 = min(k0 + per, N);
@@ -312,11 +314,27 @@ void swj_launch_mesh_step(swj_ctx *c, const double *u, double *E, const int *act
                                                          c->g, c->zetay, c->src64, c->src32, act);
 }
 
-void swj_launch_assemble(swj_ctx *c, double *E, int P, const int *act)
+void swj_launch_assemble(swj_ctx *c, double *E, int P, const int *act, const double *e2part)
 {
     SWJ_COUNT_LAUNCH();
     k_assemble<<<dim3(nblk(c->T, 256), c->nb), 256, 0, c->stream>>>(c->N, c->M, c->H, P, c->partial,
-                                                                     c->e2part, E, act);
+                                                                     e2part ? e2part : c->e2part, E, act);
+}
+
+// Tangent of the trapezoid and spline steps for a direction v: zeta', g',
+// zeta_y', g_y' into c->dnode ([4][nb][S]).
+void swj_launch_mesh_tangent(swj_ctx *c, const double *v, const int *act)
+{
+    const swj_mesh &m = c->mesh;
+    cudaStream_t st = c->stream;
+    const size_t NS = (size_t)c->nb * c->S;
+    double *dz = c->dnode, *dg = dz + NS, *dzy = dg + NS, *dgy = dzy + NS;
+    SWJ_COUNT_LAUNCH();
+    k_integrate<<<dim3(nblk(2L * c->M * 32, 256), c->nb), 256, 0, st>>>(c->N, c->M, c->H, m.x1, m.dx, v, dz,
+                                                                        dg, act, true);
+    SWJ_COUNT_LAUNCH();
+    k_spline<<<dim3(nblk(2L * c->N, 128), c->nb), 128, 0, st>>>(c->N, c->M, m.dy, c->spl_cp, c->spl_a,
+                                                                 c->spl_inv, dz, dg, dzy, dgy, act);
 }
 
 void swj_launch_flat(swj_ctx *c, double *u)

@@ -188,8 +188,11 @@ int arnoldi_device_step(swj_ctx *c, int j, const double *u, const double *Ebase,
     if (rc) return rc;
     SWJ_CUDA_TRY(cudaMemcpy2DAsync(Zj, zst * sizeof(double), c->u_try, ld * sizeof(double),
                                    ld * sizeof(double), nb, cudaMemcpyDeviceToDevice, s));
-    // w = J z_j (FD-JVP about (u, Ebase))
-    rc = swj_jvp_impl(c, u, Ebase, c->u_try, c->E_try, prec, c->opts.fd_h, act);
+    // w = J z_j: exact, or the FD-JVP about (u, Ebase)
+    if (c->opts.jvp == SWJ_JVP_EXACT)
+        rc = swj_jvp_exact_impl(c, u, c->u_try, c->E_try, prec == SWJ_FP64 ? SWJ_FP64 : SWJ_FP32, act);
+    else
+        rc = swj_jvp_impl(c, u, Ebase, c->u_try, c->E_try, prec, c->opts.fd_h, act);
     if (rc) return rc;
     SWJ_CUDA_TRY(cudaMemcpy2DAsync(w, vst * sizeof(double), c->E_try, ld * sizeof(double),
                                    ld * sizeof(double), nb, cudaMemcpyDeviceToDevice, s));
@@ -317,8 +320,13 @@ int gmres(swj_ctx *c, int kind, const double *u, const double *Ebase, int prec,
             rc = arnoldi_step(c, kind, j, u, Ebase, prec);
             if (rc) return rc;
             SWJ_CUDA_TRY(cudaStreamSynchronize(s));
-            count_residual(st, step, prec);
-            if (!Ebase) count_residual(st, step, prec);   // central difference: two residuals
+            if (c->opts.jvp == SWJ_JVP_EXACT) {
+                for (int i = 0; i < c->nb; ++i)
+                    if (step[i]) st[i].exact_jvps++;
+            } else {
+                count_residual(st, step, prec);
+                if (!Ebase) count_residual(st, step, prec);   // central difference: two residuals
+            }
             for (int i = 0; i < nb; ++i) {
                 if (!step[i]) continue;
                 if (st) { st[i].precond_applies++; st[i].krylov_iters++; }

@@ -27,6 +27,7 @@ bool valid_opts(const swj_opts *o)
     if (o->fd_h < 0.0 || !(o->mixed_tol_inf > 0.0) || !(o->refine_tol_inf > 0.0)) return false;
     if (o->autotune != 0 && o->autotune != 1) return false;
     if (o->refine_precision != SWJ_FF && o->refine_precision != SWJ_FP64) return false;
+    if (o->jvp != SWJ_JVP_FD && o->jvp != SWJ_JVP_EXACT) return false;
     return true;
 }
 
@@ -44,7 +45,8 @@ void free_all(swj_ctx *c)
     void *ptrs[] = {c->zeta, c->g, c->zetay, c->gy, c->spl_cp, c->spl_a, c->spl_inv, c->e2part,
                     c->Ival, c->src64, c->src32, c->tgt64_base, c->tgt32_base, c->partial,
                     c->u_tmp, c->E_tmp, c->u_tmp2, c->E_tmp2, c->E_cur, c->u_try, c->E_try, c->E_base32, c->du,
-                    c->rvec, c->dscal, c->red, c->V, c->Z, c->Fd, c->epsd, c->act_d};
+                    c->rvec, c->dscal, c->red, c->V, c->Z, c->Fd, c->epsd, c->act_d,
+                    c->dnode, c->tsrc64, c->tsrc32, c->ttgt64_base, c->ttgt32_base, c->de2part};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->hpin) cudaFreeHost(c->hpin);
@@ -82,6 +84,12 @@ int alloc_all(swj_ctx *c)
     rc |= dalloc(c, &c->Fd, nb);
     rc |= dalloc(c, &c->epsd, nb);
     rc |= dalloc(c, &c->act_d, nb);
+    rc |= dalloc(c, &c->dnode, 4 * nb * S);
+    rc |= dalloc(c, &c->tsrc64, nb * S);
+    rc |= dalloc(c, &c->tsrc32, nb * S);
+    rc |= dalloc(c, &c->ttgt64_base, 8 * nb * T);
+    rc |= dalloc(c, &c->ttgt32_base, 8 * nb * T);
+    rc |= dalloc(c, &c->de2part, nb * T);
     if (rc) return SWJ_ENOMEM;
     // each field of the target arrays holds nb blocks of T values
     const size_t NT = nb * T;
@@ -89,6 +97,10 @@ int alloc_all(swj_ctx *c)
     c->tgt64 = TgtArrays64{b, b + NT, b + 2 * NT, b + 3 * NT, b + 4 * NT, b + 5 * NT, b + 6 * NT, b + 7 * NT};
     float *f = c->tgt32_base;
     c->tgt32 = TgtArrays32{f, f + NT, f + 2 * NT, f + 3 * NT, f + 4 * NT, f + 5 * NT, f + 6 * NT, f + 7 * NT};
+    b = c->ttgt64_base;
+    c->ttgt64 = TgtArrays64{b, b + NT, b + 2 * NT, b + 3 * NT, b + 4 * NT, b + 5 * NT, b + 6 * NT, b + 7 * NT};
+    f = c->ttgt32_base;
+    c->ttgt32 = TgtArrays32{f, f + NT, f + 2 * NT, f + 3 * NT, f + 4 * NT, f + 5 * NT, f + 6 * NT, f + 7 * NT};
     c->plan64 = swj_pair_plan(c, SWJ_FP64);
     c->plan32 = swj_pair_plan(c, SWJ_FP32);
     c->planff = swj_pair_plan(c, SWJ_FF);
@@ -151,7 +163,10 @@ int ctx_bytes(const swj_mesh *mesh, int nb, int kry_m, size_t *out)
     size_t b = 4 * n * S * d + 3 * M * d + 2 * n * T * d + n * S * sizeof(SrcRec64) +
                n * S * sizeof(SrcRec32) + 8 * n * T * d + 8 * n * T * sizeof(float) + 2 * n * d +
                n * sizeof(int) + P * T * n * d + 10 * n * nu * d + n * SWJ_DS * d + n * SWJ_RED * d +
-               n * (size_t)(2 * kry_m + 1) * nu * d;
+               n * (size_t)(2 * kry_m + 1) * nu * d +
+               // exact-JVP tangents
+               4 * n * S * d + n * S * sizeof(SrcRec64) + n * S * sizeof(SrcRec32) + 8 * n * T * d +
+               8 * n * T * sizeof(float) + n * T * d;
     *out = b;
     return SWJ_OK;
 }
@@ -230,6 +245,7 @@ void swj_default_opts(swj_opts *o)
     o->verbose = 0;
     o->autotune = 1;
     o->refine_precision = SWJ_FF;
+    o->jvp = SWJ_JVP_FD;
 }
 
 int swj_create(swj_ctx **out, const swj_mesh *mesh, double F, double eps, const swj_opts *opts,
@@ -373,6 +389,13 @@ int swj_jvp(swj_ctx *c, const double *u, const double *Eu, const double *v, doub
     if (!c || !u || !Eu || !v || !Jv) return SWJ_EINVAL;
     if (precision != SWJ_FP64 && precision != SWJ_FP32) return SWJ_EINVAL;
     return swj_jvp_impl(c, u, Eu, v, Jv, precision, c->opts.fd_h, nullptr);
+}
+
+int swj_jvp_exact(swj_ctx *c, const double *u, const double *v, double *Jv, int precision)
+{
+    if (!c || !u || !v || !Jv || Jv == u || Jv == v) return SWJ_EINVAL;
+    if (precision != SWJ_FP64 && precision != SWJ_FP32) return SWJ_EINVAL;
+    return swj_jvp_exact_impl(c, u, v, Jv, precision, nullptr);
 }
 
 int swj_precond_setup(swj_ctx *c)

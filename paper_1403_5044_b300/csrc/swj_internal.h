@@ -135,6 +135,18 @@ struct swj_ctx {
     int pc_mc;                   // 1: the apply uses swj_band_sweep_mc
     double *pc_lt;               // set-up scratch: inv_i S_ij (j < i) of one block row, every instance
 
+    // exact JVP (jvp.cu): tangents of the node arrays [4][nb][S] (zeta, g,
+    // zeta_y, g_y), of the source records and target arrays (same layouts
+    // as the primal ones; x, y, w unused), and of the per-target part of E2
+    double *dnode;
+    SrcRec64 *tsrc64;
+    SrcRec32 *tsrc32;
+    double *ttgt64_base;
+    float *ttgt32_base;
+    TgtArrays64 ttgt64;
+    TgtArrays32 ttgt32;
+    double *de2part;
+
     size_t pc_bytes;             // device bytes of the preconditioner buffers
     size_t bytes;                // device bytes held (workspace + preconditioner)
     cudaEvent_t ev0, ev1;
@@ -160,7 +172,13 @@ inline int &swj_tuned_of(swj_ctx *c, int prec)
 // ---------------------------------------------------------------- launches
 // mesh.cu (act: device per-instance flags or nullptr for all)
 void swj_launch_mesh_step(swj_ctx *c, const double *u, double *E, const int *act);
-void swj_launch_assemble(swj_ctx *c, double *E, int P, const int *act);
+// E2 rows = e2part (c->e2part when null) - sum over the P source chunks
+void swj_launch_assemble(swj_ctx *c, double *E, int P, const int *act, const double *e2part = nullptr);
+void swj_launch_mesh_tangent(swj_ctx *c, const double *v, const int *act);
+// jvp.cu: Jv = J(u) v exactly (forward-mode derivative of E), all-pairs part in
+// `precision` (SWJ_FP64 or SWJ_FP32)
+int swj_jvp_exact_impl(swj_ctx *c, const double *u, const double *v, double *Jv, int precision,
+                       const int *act);
 void swj_spline_coeffs(int M, double *cp, double *a, double *inv);  // host helper
 void swj_launch_flat(swj_ctx *c, double *u);
 void swj_launch_unpack(swj_ctx *c, const double *u, double *zeta_out, double *phi_out);

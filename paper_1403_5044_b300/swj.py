@@ -19,6 +19,7 @@ OK, EINVAL, ENOMEM, ECUDA, ENOTCONV, ELINESEARCH, EGMRES, ENAN, ETIMEOUT, ESINGU
     0, -1, -2, -3, -4, -5, -6, -7, -8, -9, -10
 PENDING = 1
 FP64, FP32, FF = 0, 1, 2
+JVP_FD, JVP_EXACT = 0, 1
 SOLVE_FP64, SOLVE_MIXED = 0, 1
 
 
@@ -40,7 +41,8 @@ class Opts(ctypes.Structure):
                 ("eta_max", ctypes.c_double), ("eta_min", ctypes.c_double),
                 ("fd_h", ctypes.c_double), ("refine_max", ctypes.c_int),
                 ("mixed_tol_inf", ctypes.c_double), ("refine_tol_inf", ctypes.c_double),
-                ("verbose", ctypes.c_int), ("autotune", ctypes.c_int), ("refine_precision", ctypes.c_int)]
+                ("verbose", ctypes.c_int), ("autotune", ctypes.c_int), ("refine_precision", ctypes.c_int),
+                ("jvp", ctypes.c_int)]
 
 
 class ServerOpts(ctypes.Structure):
@@ -73,7 +75,7 @@ class Stats(ctypes.Structure):
                 ("final_norm_inf", ctypes.c_double), ("final_norm_inf_fp64", ctypes.c_double),
                 ("t_total_ms", ctypes.c_double), ("t_setup_ms", ctypes.c_double),
                 ("pairs_per_residual_hi", ctypes.c_int), ("pairs_per_residual_lo", ctypes.c_int),
-                ("residual_evals_ff", ctypes.c_int)]
+                ("residual_evals_ff", ctypes.c_int), ("exact_jvps", ctypes.c_int)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}
@@ -124,6 +126,7 @@ def lib():
             "swj_jvp": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_int]),
             "swj_precond_setup": (ctypes.c_int, [_vp]),
             "swj_precond_apply": (ctypes.c_int, [_vp, _vp, _vp]),
+            "swj_jvp_exact": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int]),
             "swj_precond_sweep_clusters": (ctypes.c_int, [_vp]),
             "swj_solve": (ctypes.c_int, [_vp, _vp, _vp]),
             "swj_unpack": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
@@ -262,6 +265,10 @@ class Context:
 
     def jvp(self, u, Eu, v, Jv, precision=FP64):
         _check(lib().swj_jvp(self._h, _ptr(u), _ptr(Eu), _ptr(v), _ptr(Jv), int(precision)), "swj_jvp")
+        return Jv
+
+    def jvp_exact(self, u, v, Jv, precision=FP64):
+        _check(lib().swj_jvp_exact(self._h, _ptr(u), _ptr(v), _ptr(Jv), int(precision)), "swj_jvp_exact")
         return Jv
 
     def precond_setup(self):
