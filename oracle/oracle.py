@@ -25,6 +25,8 @@ Contents, in the paper's order:
   * finite-difference Jacobian-vector product     (Eq. JvApprox)
   * the exact Jacobian-vector product, by the
     complex-step derivative of E                  (the derivative Eq. JvApprox approximates)
+  * the linear-problem initial guess and mesh
+    bootstrapping by resampling                   (Section 4.1, Section 2.3)
   * reference root-finders (dense FD-Newton for tiny meshes, Newton-GMRES
     with the linear-Jacobian preconditioner)      (Section 4)
 
@@ -490,6 +492,39 @@ def jvp_exact(mesh, F, eps, u, v, h=1e-30):
     scale = order(mesh, z(p["E1"]), s2, z(p["E3"]), z(p["E4"]), z(p["E5"]), z(p["E6"]))
     scale = np.where(scale > 0, scale, np.abs(Jv))
     return Jv, scale
+
+
+def linear_solution(mesh, F, eps, b=None):
+    """The solution of the linearised problem (Section 2.3, the weak-source
+    limit), offered as an initial guess in Section 4.1: one Newton step from
+    the flat state with the linear Jacobian of Appendix B,
+        u_L = u0 - J_lin^{-1} E(u0),
+    exact for the discretised linear problem when b is None (untruncated);
+    with a block bandwidth b the same step with the truncated matrix."""
+    u0 = flat_guess(mesh)
+    return u0 - np.linalg.solve(jacobian_linear(mesh, F, b), residual(mesh, F, eps, u0))
+
+
+def resample(src: Mesh, u_src, dst: Mesh):
+    """Mesh bootstrapping (Section 4.1 bootstraps in eps; the same idea across
+    meshes): the unknowns of ``dst`` from a solution on ``src`` by bilinear
+    interpolation of the source's node fields, coordinates clamped to the
+    source mesh.  phi_1 and zeta_1 come from g = phi - x and zeta at
+    (x1 of dst, y); phi_x and zeta_x from their node values."""
+    st = surface(src, u_src)
+    def bilinear(f, x, y):
+        fi = np.clip((x - src.x1) / src.dx, 0.0, src.N - 1)
+        fj = np.clip(y / src.dy, 0.0, src.M - 1)
+        i0 = np.minimum(np.floor(fi).astype(int), src.N - 2)
+        j0 = np.minimum(np.floor(fj).astype(int), src.M - 2)
+        a, b = fi - i0, fj - j0
+        return ((1 - a) * (1 - b) * f[j0, i0] + a * (1 - b) * f[j0, i0 + 1]
+                + (1 - a) * b * f[j0 + 1, i0] + a * b * f[j0 + 1, i0 + 1])
+    X, Y = np.meshgrid(dst.x(), dst.y())
+    x1 = np.full(dst.M, dst.x1)
+    phi1 = bilinear(st["g"], x1, dst.y()) + dst.x1
+    zeta1 = bilinear(st["zeta"], x1, dst.y())
+    return pack(dst, phi1, bilinear(st["phix"], X, Y), zeta1, bilinear(st["zetax"], X, Y))
 
 
 def jacobian_fd(mesh, F, eps, u, h=1e-6):

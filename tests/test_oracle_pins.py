@@ -332,6 +332,41 @@ def test_complex_step_leaves_the_real_residual_unchanged():
     assert np.abs(Ec.real - Er).max() <= 1e-13 * max(1.0, np.abs(Er).max())
 
 
+def test_linear_solution_is_the_weak_source_limit_and_solves_the_linear_system():
+    spec = W.MeshSpec(11, 5, -2.5, 0.5, 0.5)
+    mesh = _mesh(spec)
+    F, eps = 0.7, 0.02
+    uL = O.linear_solution(mesh, F, eps)
+    u0 = O.flat_guess(mesh)
+    J = O.jacobian_linear(mesh, F)
+    # the affine model of E about u0 with the linear Jacobian vanishes at u_L
+    assert np.abs(O.residual(mesh, F, eps, u0) + J @ (uL - u0)).max() < 1e-13
+    # and the nonlinear root is O(eps^2) away from it
+    u, _ = O.newton_dense(mesh, F, eps, u0, tol=1e-13)
+    assert np.abs(u - uL).max() < 5 * eps ** 2 * max(1.0, np.abs(uL - u0).max() / eps)
+
+
+def test_resample_onto_the_same_mesh_is_the_identity():
+    spec = W.MeshSpec(13, 7, -3.0, 0.5, 0.4)
+    mesh = _mesh(spec)
+    u = W.random_state(spec, seed=21, amp=0.1)
+    assert np.abs(O.resample(mesh, u, mesh) - u).max() <= 1e-14 * np.abs(u).max()
+
+
+def test_resample_onto_a_sub_mesh_picks_the_node_values():
+    """A mesh whose nodes are every other node of the source (same x1) gets
+    the source's node values: the trapezoid integral is not resampled, the
+    unknowns phi_x, zeta_x are the node values, phi_1, zeta_1 the first column."""
+    fine = W.MeshSpec(21, 9, -4.0, 0.25, 0.3)
+    coarse = W.MeshSpec(11, 5, -4.0, 0.5, 0.6)
+    u = W.random_state(fine, seed=22, amp=0.1)
+    mf, mc = _mesh(fine), _mesh(coarse)
+    got = O.resample(mf, u, mc)
+    p1, px, z1, zx = O.unpack(mf, u)
+    ref = O.pack(mc, p1[::2], px[::2, ::2], z1[::2], zx[::2, ::2])
+    assert np.abs(got - ref).max() <= 1e-14 * np.abs(ref).max()
+
+
 def test_dense_newton_and_newton_gmres_reach_the_same_root():
     spec = TINY
     mesh = _mesh(spec)
