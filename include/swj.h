@@ -193,6 +193,36 @@ size_t swj_footprint_bytes(const swj_mesh *mesh, int count, const swj_opts *opts
  * (phi_x)_{k,l} = 1, zeta_{1,l} = 0, (zeta_x)_{k,l} = 0.  Async. */
 int swj_initial_guess_flat(swj_ctx *ctx, double *u_dev);
 
+/* u_dev <- the solution of the linearised problem (Section 2.3, the weak-
+ * source limit), the other initial guess of Section 4.1:
+ * u0 - P^-1 E(u0), u0 the flat state, P the context's preconditioner (the
+ * linear Jacobian of Appendix B; with block_bw = 0 this is the exact solution
+ * of the discretised linear problem, with b > 0 its block-banded
+ * approximation).  E(u0) uses an FP64-accurate all-pairs sum (FP64, or the
+ * refinement precision in MIXED mode).  Builds P if needed.  Every instance
+ * of a batch.  u_dev: device, count * 2(N+1)M.  Synchronous when it builds P,
+ * else async; SWJ_ETIMEOUT as swj_sync. */
+int swj_initial_guess_linear(swj_ctx *ctx, double *u_dev);
+
+/* Bootstrapping in eps (Section 4.1): solve at eps_k = eps k / steps,
+ * k = 1..steps, each from the previous solution, starting from u_dev as
+ * given (e.g. the flat or linear guess); every instance of a batch scales
+ * its own eps.  F is unchanged, so the preconditioner is built once.  The
+ * context's eps is restored at return.  stats (optional, count entries)
+ * accumulate the counts and times of all steps and keep the final norms and
+ * status of the last one.  Returns the first failing step's status.
+ * Synchronous. */
+int swj_solve_continuation(swj_ctx *ctx, double *u_dev, int steps, swj_stats *stats);
+
+/* Mesh bootstrapping: u_dst (on dst's mesh) from u_src (a solution on src's
+ * mesh) by bilinear interpolation of src's node fields zeta, g = phi - x,
+ * zeta_x, phi_x at dst's nodes, coordinates clamped to src's mesh; phi_1 and
+ * zeta_1 from g and zeta at dst's x1.  Instance i of dst from instance i of
+ * src (equal counts).  src's scratch node arrays are used, so src must not
+ * be in use on another stream; runs on dst's stream and returns when done.
+ * src may equal dst (then u_dst must differ from u_src). */
+int swj_resample(swj_ctx *src, const double *u_src, swj_ctx *dst, double *u_dst);
+
 /* E_dev <- E(u_dev) (Section 3, Appendix A order), with the all-pairs sum in
  * `precision` (SWJ_FP64, SWJ_FP32 or SWJ_FF).  Steps: trapezoidal integration of
  * zeta and phi along x (Eq. zetaapprox), cubic-spline slopes along y

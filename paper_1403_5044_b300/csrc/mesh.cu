@@ -273,6 +273,48 @@ __global__ void k_surface(int N, int M, double dy, const double *zeta, const dou
     }
 }
 
+// Mesh bootstrapping: thread per unknown slot (l, k), k = 0..Nd, of the
+// destination mesh; bilinear interpolation of the source's node fields
+// (coordinates clamped to the source mesh).  k = 0: phi_1 = g(x1, y) + x1 and
+// zeta_1 = zeta(x1, y); k >= 1: phi_x and zeta_x at node k - 1.
+__global__ void k_resample(int Ns, int Ms, int Hs, double x1s, double dxs, double dys,
+                           const double *__restrict__ zeta_s, const double *__restrict__ g_s,
+                           const double *__restrict__ u_s, int Nd, int Md, int Hd, double x1d, double dxd,
+                           double dyd, double *__restrict__ u_d)
+{
+    const int inst = blockIdx.y;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= Hd) return;
+    zeta_s += (size_t)inst * Ns * Ms;
+    g_s += (size_t)inst * Ns * Ms;
+    u_s += (size_t)inst * 2 * Hs;
+    u_d += (size_t)inst * 2 * Hd;
+    const int l = e / (Nd + 1), k = e % (Nd + 1);
+    const double x = (k == 0) ? x1d : x1d + (double)(k - 1) * dxd;
+    const double y = (double)l * dyd;
+    const double fi = fmin(fmax((x - x1s) / dxs, 0.0), (double)(Ns - 1));
+    const double fj = fmin(fmax(y / dys, 0.0), (double)(Ms - 1));
+    const int i0 = min((int)floor(fi), Ns - 2), j0 = min((int)floor(fj), Ms - 2);
+    const double a = fi - i0, b = fj - j0;
+    const double w00 = (1.0 - a) * (1.0 - b), w01 = a * (1.0 - b), w10 = (1.0 - a) * b, w11 = a * b;
+    if (k == 0) {
+        auto bil = [&](const double *f) {
+            const double *r0 = f + (size_t)j0 * Ns + i0, *r1 = r0 + Ns;
+            return w00 * r0[0] + w01 * r0[1] + w10 * r1[0] + w11 * r1[1];
+        };
+        u_d[e] = bil(g_s) + x1d;
+        u_d[Hd + e] = bil(zeta_s);
+    } else {
+        // node field f[j][i] = u_s[base + j (Ns + 1) + 1 + i]
+        auto bil = [&](const double *base) {
+            const double *r0 = base + (size_t)j0 * (Ns + 1) + 1 + i0, *r1 = r0 + (Ns + 1);
+            return w00 * r0[0] + w01 * r0[1] + w10 * r1[0] + w11 * r1[1];
+        };
+        u_d[e] = bil(u_s);
+        u_d[Hd + e] = bil(u_s + Hs);
+    }
+}
+
 inline int nblk(long n, int b) { return (int)((n + b - 1) / b); }
 
 }  // namespace
@@ -360,4 +402,19 @@ void swj_launch_surface(swj_ctx *c, double *out)
     SWJ_COUNT_LAUNCH();
     k_surface<<<nblk(n, 256), 256, 0, c->stream>>>(c->N, c->M, c->mesh.dy, c->zeta, c->g, c->zetay,
                                                     c->gy, c->tgt64, c->Ival, out);
+}
+
+// u_dst (on dst's mesh) from u_src (on src's mesh), instance by instance, on
+// dst's stream; src's node arrays serve as scratch (src must be idle).
+void swj_launch_resample(swj_ctx *src, const double *u_src, swj_ctx *dst, double *u_dst)
+{
+    const swj_mesh &ms = src->mesh, &md = dst->mesh;
+    cudaStream_t st = dst->stream;
+    SWJ_COUNT_LAUNCH();
+    k_integrate<<<dim3(nblk(2L * src->M * 32, 256), src->nb), 256, 0, st>>>(src->N, src->M, src->H, ms.x1, ms.dx,
+                                                                            u_src, src->zeta, src->g, nullptr);
+    SWJ_COUNT_LAUNCH();
+    k_resample<<<dim3(nblk(dst->H, 256), dst->nb), 256, 0, st>>>(src->N, src->M, src->H, ms.x1, ms.dx, ms.dy,
+                                                                  src->zeta, src->g, u_src, dst->N, dst->M,
+                                                                  dst->H, md.x1, md.dx, md.dy, u_dst);
 }

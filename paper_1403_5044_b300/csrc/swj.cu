@@ -4,6 +4,7 @@
 #include <new>
 #include <stdlib.h>
 #include <string.h>
+#include <vector>
 
 std::atomic<unsigned long long> g_swj_launches{0};
 
@@ -373,6 +374,61 @@ int swj_initial_guess_flat(swj_ctx *c, double *u)
     if (!c || !u) return SWJ_EINVAL;
     swj_launch_flat(c, u);
     SWJ_CUDA_TRY(cudaGetLastError());
+    return SWJ_OK;
+}
+
+int swj_initial_guess_linear(swj_ctx *c, double *u)
+{
+    if (!c || !u) return SWJ_EINVAL;
+    // u0 - P^-1 E(u0), E with an FP64-accurate all-pairs sum
+    const int prec = (c->opts.solve_mode == SWJ_SOLVE_FP64) ? SWJ_FP64 : c->opts.refine_precision;
+    swj_launch_flat(c, u);
+    int rc = swj_residual_impl(c, u, c->E_try, prec, nullptr);
+    if (rc) return rc;
+    if (!c->pc_ready && (rc = swj_pc_setup(c)) != SWJ_OK) return rc;
+    if ((rc = swj_pc_apply(c, c->E_try, c->u_try, nullptr)) != SWJ_OK) return rc;
+    swj_baxpy(c->stream, c->nb, (int)c->nu, nullptr, 0, -1.0, c->u_try, u, c->nu, nullptr);
+    SWJ_CUDA_TRY(cudaGetLastError());
+    return swj_pc_status(c);
+}
+
+int swj_solve_continuation(swj_ctx *c, double *u, int steps, swj_stats *stats)
+{
+    if (!c || !u || steps < 1) return SWJ_EINVAL;
+    const int nb = c->nb;
+    std::vector<double> eps0(c->eps, c->eps + nb), F(c->F, c->F + nb), epsk(nb);
+    std::vector<swj_stats> acc(nb), one(nb);
+    memset((void *)acc.data(), 0, nb * sizeof(swj_stats));
+    int rc = SWJ_OK;
+    for (int k = 1; k <= steps && rc == SWJ_OK; ++k) {
+        for (int i = 0; i < nb; ++i) epsk[i] = eps0[i] * (double)k / (double)steps;
+        if ((rc = swj_batch_set_params(c, F.data(), epsk.data())) != SWJ_OK) break;   // F unchanged: P is kept
+        rc = swj_solve(c, u, one.data());
+        for (int i = 0; i < nb; ++i) {
+            swj_stats &a = acc[i], &o = one[i];
+            a.status = o.status;
+            a.newton_iters += o.newton_iters; a.refine_iters += o.refine_iters;
+            a.residual_evals += o.residual_evals; a.residual_evals_fp64 += o.residual_evals_fp64;
+            a.residual_evals_ff += o.residual_evals_ff; a.krylov_iters += o.krylov_iters;
+            a.precond_applies += o.precond_applies; a.line_search_cuts += o.line_search_cuts;
+            a.exact_jvps += o.exact_jvps;
+            a.final_norm_inf = o.final_norm_inf; a.final_norm_inf_fp64 = o.final_norm_inf_fp64;
+            a.t_total_ms += o.t_total_ms; a.t_setup_ms += o.t_setup_ms;
+            a.pairs_per_residual_hi = o.pairs_per_residual_hi; a.pairs_per_residual_lo = o.pairs_per_residual_lo;
+        }
+    }
+    const int rc2 = swj_batch_set_params(c, F.data(), eps0.data());
+    if (stats) memcpy(stats, acc.data(), nb * sizeof(swj_stats));
+    return rc ? rc : rc2;
+}
+
+int swj_resample(swj_ctx *src, const double *u_src, swj_ctx *dst, double *u_dst)
+{
+    if (!src || !dst || !u_src || !u_dst || src->nb != dst->nb || u_src == u_dst) return SWJ_EINVAL;
+    if (src != dst) SWJ_CUDA_TRY(cudaStreamSynchronize(src->stream));   // its node arrays are reused
+    swj_launch_resample(src, u_src, dst, u_dst);
+    SWJ_CUDA_TRY(cudaGetLastError());
+    if (src != dst) SWJ_CUDA_TRY(cudaStreamSynchronize(dst->stream));
     return SWJ_OK;
 }
 

@@ -175,6 +175,7 @@ void swj_launch_mesh_step(swj_ctx *c, const double *u, double *E, const int *act
 // E2 rows = e2part (c->e2part when null) - sum over the P source chunks
 void swj_launch_assemble(swj_ctx *c, double *E, int P, const int *act, const double *e2part = nullptr);
 void swj_launch_mesh_tangent(swj_ctx *c, const double *v, const int *act);
+void swj_launch_resample(swj_ctx *src, const double *u_src, swj_ctx *dst, double *u_dst);
 // jvp.cu: Jv = J(u) v exactly (forward-mode derivative of E), all-pairs part in
 // `precision` (SWJ_FP64 or SWJ_FP32)
 int swj_jvp_exact_impl(swj_ctx *c, const double *u, const double *v, double *Jv, int precision,

@@ -127,6 +127,9 @@ def lib():
             "swj_precond_setup": (ctypes.c_int, [_vp]),
             "swj_precond_apply": (ctypes.c_int, [_vp, _vp, _vp]),
             "swj_jvp_exact": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int]),
+            "swj_initial_guess_linear": (ctypes.c_int, [_vp, _vp]),
+            "swj_solve_continuation": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp]),
+            "swj_resample": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
             "swj_precond_sweep_clusters": (ctypes.c_int, [_vp]),
             "swj_solve": (ctypes.c_int, [_vp, _vp, _vp]),
             "swj_unpack": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
@@ -258,6 +261,24 @@ class Context:
     def initial_guess_flat(self, u):
         _check(lib().swj_initial_guess_flat(self._h, _ptr(u)), "swj_initial_guess_flat")
         return u
+
+    def initial_guess_linear(self, u):
+        _check(lib().swj_initial_guess_linear(self._h, _ptr(u)), "swj_initial_guess_linear")
+        return u
+
+    def resample_from(self, src, u_src, u):
+        """u (on this mesh) <- u_src, a solution on src's mesh (swj_resample)."""
+        _check(lib().swj_resample(src._h, _ptr(u_src), self._h, _ptr(u)), "swj_resample")
+        return u
+
+    def solve_continuation(self, u, steps, check=True):
+        st = Stats()
+        rc = lib().swj_solve_continuation(self._h, _ptr(u), int(steps), ctypes.cast(ctypes.byref(st), _vp))
+        if check:
+            _check(rc, "swj_solve_continuation")
+        d = st.as_dict()
+        d["rc"] = rc
+        return d
 
     def residual(self, u, E, precision=FP64):
         _check(lib().swj_residual(self._h, _ptr(u), _ptr(E), int(precision)), "swj_residual")
