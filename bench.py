@@ -93,6 +93,8 @@ def parse():
     ap.add_argument("--mesh", default="181x61",
                     help="--precond-only: mesh NxM on x in [-16,20], y in [0,12] (F = 0.7, eps = 0.3 "
                          "unless 181x61, the workload)")
+    ap.add_argument("--spectrum", action="store_true",
+                    help="spectral diagnostics of J P^-1 (41x21, F = 0.7, eps = 0.1, at the root) for several b")
     ap.add_argument("--precond-only", action="store_true",
                     help="build the preconditioner, apply it 10 times and solve once "
                          "(a small, fixed launch sequence for profilers)")
@@ -706,8 +708,36 @@ def run_precond_only(args):
                       "krylov_iters": st["krylov_iters"], "residual_evals": st["residual_evals"]}))
 
 
+def run_spectrum(args):
+    import torch
+    from paper_1403_5044_b300 import diagnostics as D
+    from paper_1403_5044_b300 import swj
+    from paper_1403_5044_b300 import workloads as W
+    spec, F, eps = W.MESH_41x21, 0.7, 0.1
+    with swj.Context.from_spec(spec, F, eps, solve_mode="fp64", block_bw=0) as ctx:
+        u = ctx.initial_guess_flat(ctx.vector())
+        ctx.solve(u)
+    for b in (1, 3, 5, 7, 11, 0):
+        with swj.Context.from_spec(spec, F, eps, solve_mode="fp64", block_bw=b) as ctx:
+            ctx.precond_setup()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            A = D.preconditioned_jacobian(ctx, u)
+            t1 = time.perf_counter()
+            import numpy as np
+            eigs = np.linalg.eigvals(A)
+            t2 = time.perf_counter()
+            print(json.dumps({"spectrum": True, "mesh": "41x21", "block_bw": b, "form_ms": (t1 - t0) * 1e3,
+                              "eig_ms": (t2 - t1) * 1e3, **D.clustering(eigs),
+                              "eigs_re_min": float(eigs.real.min()), "eigs_re_max": float(eigs.real.max()),
+                              "eigs_im_absmax": float(np.abs(eigs.imag).max())}), flush=True)
+
+
 def main():
     args = parse()
+    if args.spectrum:
+        run_spectrum(args)
+        return
     if args.large:
         if args.block_bw == BLOCK_BW:
             args.block_bw = 7

@@ -251,6 +251,16 @@ int swj_jvp(swj_ctx *ctx, const double *u_dev, const double *Eu_dev,
 int swj_jvp_exact(swj_ctx *ctx, const double *u_dev, const double *v_dev, double *Jv_dev,
                   int precision);
 
+/* Columns col0 .. col0 + ncols - 1 of the preconditioned Jacobian J(u) P^-1
+ * (the matrix whose spectrum Section 4.2 wants clustered; Figs. 2-3), for
+ * spectral diagnostics on small meshes: column j = swj_jvp_exact(u, P^-1 e_j)
+ * with the all-pairs part in `precision`.  out_dev: device, column-major,
+ * 2(N+1)M x ncols (leading dimension 2(N+1)M).  Single-instance contexts
+ * only.  Builds P if needed.  Synchronous.  SWJ_EINVAL for a batch context,
+ * a bad range or precision. */
+int swj_preconditioned_jacobian(swj_ctx *ctx, const double *u_dev, int col0, int ncols,
+                                double *out_dev, int precision);
+
 /* Build and factor the preconditioner P for the context's mesh, F and
  * block_bw: the linear Jacobian of Appendix B (Eqs. PreA-PreD plus the
  * radiation rows), its zeta-zeta block truncated to the block band, factored

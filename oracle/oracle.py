@@ -527,6 +527,14 @@ def resample(src: Mesh, u_src, dst: Mesh):
     return pack(dst, phi1, bilinear(st["phix"], X, Y), zeta1, bilinear(st["zetax"], X, Y))
 
 
+def preconditioned_jacobian(mesh, F, eps, u, b=None):
+    """J(u) P_b^-1 (Section 4.2), J exact column by column (jvp_exact) and
+    P_b the Appendix B Jacobian truncated to block bandwidth b."""
+    n = mesh.n_unknowns
+    J = np.column_stack([jvp_exact(mesh, F, eps, u, e)[0] for e in np.eye(n)])
+    return J @ np.linalg.inv(jacobian_linear(mesh, F, b))
+
+
 def jacobian_fd(mesh, F, eps, u, h=1e-6):
     """Dense Jacobian by central differences (tiny meshes only)."""
     n = u.size

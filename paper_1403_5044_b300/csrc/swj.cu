@@ -454,6 +454,25 @@ int swj_jvp_exact(swj_ctx *c, const double *u, const double *v, double *Jv, int 
     return swj_jvp_exact_impl(c, u, v, Jv, precision, nullptr);
 }
 
+int swj_preconditioned_jacobian(swj_ctx *c, const double *u, int col0, int ncols, double *out, int precision)
+{
+    if (!c || !u || !out || c->nb != 1) return SWJ_EINVAL;
+    if (precision != SWJ_FP64 && precision != SWJ_FP32) return SWJ_EINVAL;
+    if (col0 < 0 || ncols < 0 || (size_t)col0 + (size_t)ncols > c->nu) return SWJ_EINVAL;
+    int rc;
+    if (!c->pc_ready && (rc = swj_pc_setup(c)) != SWJ_OK) return rc;
+    const int n = (int)c->nu;
+    for (int j = 0; j < ncols; ++j) {
+        swj_bfill(c->stream, 1, n, 0.0, c->E_try, c->nu, nullptr);
+        swj_bfill(c->stream, 1, 1, 1.0, c->E_try + col0 + j, c->nu, nullptr);
+        if ((rc = swj_pc_apply(c, c->E_try, c->u_try, nullptr)) != SWJ_OK) return rc;
+        if ((rc = swj_jvp_exact_impl(c, u, c->u_try, out + (size_t)j * c->nu, precision, nullptr)) != SWJ_OK)
+            return rc;
+    }
+    SWJ_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return swj_pc_status(c);
+}
+
 int swj_precond_setup(swj_ctx *c)
 {
     if (!c) return SWJ_EINVAL;

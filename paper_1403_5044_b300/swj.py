@@ -130,6 +130,7 @@ def lib():
             "swj_initial_guess_linear": (ctypes.c_int, [_vp, _vp]),
             "swj_solve_continuation": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp]),
             "swj_resample": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+            "swj_preconditioned_jacobian": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int]),
             "swj_precond_sweep_clusters": (ctypes.c_int, [_vp]),
             "swj_solve": (ctypes.c_int, [_vp, _vp, _vp]),
             "swj_unpack": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
@@ -279,6 +280,14 @@ class Context:
         d = st.as_dict()
         d["rc"] = rc
         return d
+
+    def preconditioned_jacobian(self, u, out, col0=0, ncols=None, precision=FP64):
+        """Columns of J(u) P^-1 into `out` (a CUDA float64 tensor of
+        n_unknowns * ncols, column-major)."""
+        ncols = self.n_unknowns - col0 if ncols is None else ncols
+        _check(lib().swj_preconditioned_jacobian(self._h, _ptr(u), int(col0), int(ncols), _ptr(out), int(precision)),
+               "swj_preconditioned_jacobian")
+        return out
 
     def residual(self, u, E, precision=FP64):
         _check(lib().swj_residual(self._h, _ptr(u), _ptr(E), int(precision)), "swj_residual")

@@ -367,6 +367,25 @@ def test_resample_onto_a_sub_mesh_picks_the_node_values():
     assert np.abs(got - ref).max() <= 1e-14 * np.abs(ref).max()
 
 
+def test_preconditioned_jacobian_is_the_identity_at_the_linear_limit():
+    """At the flat state with eps = 0 the exact Jacobian is the untruncated
+    preconditioner, so J P^-1 = I and every eigenvalue is 1."""
+    mesh = _mesh(TINY)
+    A = O.preconditioned_jacobian(mesh, 0.7, 0.0, O.flat_guess(mesh))
+    assert np.abs(A - np.eye(A.shape[0])).max() < 1e-12
+
+
+def test_truncation_moves_the_spectrum_away_from_1():
+    """Block-banded P (b = 1) against the untruncated one at a nonlinear
+    state: the eigenvalues of J P^-1 spread further from 1."""
+    spec = W.MeshSpec(9, 7, -2.0, 0.5, 0.4)
+    mesh = _mesh(spec)
+    u = W.random_state(spec, seed=23, amp=0.05)
+    full = np.abs(np.linalg.eigvals(O.preconditioned_jacobian(mesh, 0.7, 0.2, u)) - 1).max()
+    band = np.abs(np.linalg.eigvals(O.preconditioned_jacobian(mesh, 0.7, 0.2, u, 1)) - 1).max()
+    assert band > full
+
+
 def test_dense_newton_and_newton_gmres_reach_the_same_root():
     spec = TINY
     mesh = _mesh(spec)
