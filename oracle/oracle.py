@@ -256,6 +256,20 @@ def I_S2(mesh: Mesh, A, B, C, xt, yt):
 # --------------------------------------------------------------------------
 # the residual
 # --------------------------------------------------------------------------
+def pressure(x, y):
+    """Applied surface pressure of the pressure-forcing variant (the
+    hovercraft-like forcing the Discussion names as the next configuration;
+    the paper gives no formula): the smooth bump with compact support
+    p = exp(2 + 1/(x^2 - 1) + 1/(y^2 - 1)) for |x| < 1 and |y| < 1, else 0,
+    equal to 1 at the centre."""
+    x, y = np.broadcast_arrays(np.asarray(x, dtype=np.float64), np.asarray(y, dtype=np.float64))
+    out = np.zeros(x.shape)
+    inside = (np.abs(x) < 1.0) & (np.abs(y) < 1.0)
+    xi, yi = x[inside], y[inside]
+    out[inside] = np.exp(2.0 + 1.0 / (xi * xi - 1.0) + 1.0 / (yi * yi - 1.0))
+    return out
+
+
 def free_surface_E1(F, phix, phiy, zetax, zetay, zeta):
     """Eq. freeSurfCond written as E1 = 0."""
     num = (1 + zetax ** 2) * phiy ** 2 + (1 + zetay ** 2) * phix ** 2 - 2 * zetax * zetay * phix * phiy
@@ -314,7 +328,7 @@ def residual_E2_at(mesh: Mesh, F: float, eps: float, u, targets):
     return E2, scale
 
 
-def residual_parts(mesh: Mesh, F: float, eps: float, u, pairs: bool = True):
+def residual_parts(mesh: Mesh, F: float, eps: float, u, pairs: bool = True, forcing: str = "source"):
     """Every row family of E(u) before ordering, plus the tolerance scale of
     each E2 row (sum of absolute values of its terms).  With pairs=False the
     all-pairs sum is skipped and E2 / scale2 are left as NaN (for sampled
@@ -327,12 +341,20 @@ def residual_parts(mesh: Mesh, F: float, eps: float, u, pairs: bool = True):
     B = 2 * zxt * zyt
     C = 1 + zyt ** 2
     I = I_S2(mesh, A, B, C, xt, yt)
-    src = eps / np.sqrt(xt ** 2 + yt ** 2 + (st["zeta_t"] + 1) ** 2)
+    if forcing == "source":
+        src = eps / np.sqrt(xt ** 2 + yt ** 2 + (st["zeta_t"] + 1) ** 2)
+    elif forcing == "pressure":
+        src = np.zeros(st["zeta_t"].shape)
+    else:
+        raise ValueError(forcing)
     if pairs:
         S, Sabs = integral_sum(mesh, st)
     else:
         S = Sabs = np.full(st["g_t"].shape, np.nan)
     E1 = free_surface_E1(F, st["phix_t"], st["phiy_t"], zxt, zyt, st["zeta_t"])
+    if forcing == "pressure":
+        # Bernoulli's equation with the applied pressure eps p on the surface
+        E1 = E1 + eps * pressure(xt, yt)
     # Eq. IntegroEqn with every term moved to one side, the second integral
     # split per the singularity subtraction (Section 3):
     E2 = 2 * math.pi * st["g_t"] + src - S - zxt * I
@@ -354,16 +376,16 @@ def order(mesh: Mesh, E1, E2, E3, E4, E5, E6):
     return np.concatenate([top.ravel(), bot.ravel()])
 
 
-def residual(mesh: Mesh, F: float, eps: float, u):
+def residual(mesh: Mesh, F: float, eps: float, u, forcing: str = "source"):
     """E(u) of Eq. nonlinearsys, length 2(N+1)M, Appendix A order."""
-    p = residual_parts(mesh, F, eps, u)
+    p = residual_parts(mesh, F, eps, u, forcing=forcing)
     return order(mesh, p["E1"], p["E2"], p["E3"], p["E4"], p["E5"], p["E6"])
 
 
-def residual_scale(mesh: Mesh, F: float, eps: float, u):
+def residual_scale(mesh: Mesh, F: float, eps: float, u, forcing: str = "source"):
     """Per-row magnitude that parity tolerances are relative to: for E2 rows
     the sum of absolute values of every term, for the other rows 1."""
-    p = residual_parts(mesh, F, eps, u)
+    p = residual_parts(mesh, F, eps, u, forcing=forcing)
     one = np.ones_like(p["E1"])
     r = np.ones(mesh.M)
     return order(mesh, one, p["scale2"], r, r, r, r)
@@ -463,17 +485,17 @@ def fd_step(u, v, eps_mach=np.finfo(np.float64).eps):
     return 0.0 if nv == 0 else math.sqrt(eps_mach) * max(1.0, np.linalg.norm(u)) / nv
 
 
-def jvp_fd(mesh, F, eps, u, v, Eu=None, h=None):
+def jvp_fd(mesh, F, eps, u, v, Eu=None, h=None, forcing="source"):
     """Eq. JvApprox (with P^{-1} v already applied by the caller):
     J v ~ (E(u + h v) - E(u)) / h."""
     if Eu is None:
-        Eu = residual(mesh, F, eps, u)
+        Eu = residual(mesh, F, eps, u, forcing=forcing)
     if h is None:
         h = fd_step(u, v)
-    return (residual(mesh, F, eps, u + h * v) - Eu) / h
+    return (residual(mesh, F, eps, u + h * v, forcing=forcing) - Eu) / h
 
 
-def jvp_exact(mesh, F, eps, u, v, h=1e-30):
+def jvp_exact(mesh, F, eps, u, v, h=1e-30, forcing="source"):
     """J(u) v of the discrete residual, exactly (to rounding): the directional
     derivative d E(u + t v) / dt at t = 0, computed by the complex step
     Im E(u + i h v) / h.  Every operation of E is analytic in u (the
@@ -483,7 +505,7 @@ def jvp_exact(mesh, F, eps, u, v, h=1e-30):
     scale is, per E2 row, the sum of |d/dt| of the terms of the row (the
     tolerance scale of the row), and |Jv| elsewhere."""
     uc = np.asarray(u, dtype=np.float64) + 1j * h * np.asarray(v, dtype=np.float64)
-    p = residual_parts(mesh, F, eps, uc)
+    p = residual_parts(mesh, F, eps, uc, forcing=forcing)
     Jv = order(mesh, p["E1"], p["E2"], p["E3"], p["E4"], p["E5"], p["E6"]).imag / h
     st = p["st"]
     s2 = (p["Sabs"] + np.abs((2 * math.pi * st["g_t"]).imag) + np.abs(p["src"].imag)
@@ -494,7 +516,7 @@ def jvp_exact(mesh, F, eps, u, v, h=1e-30):
     return Jv, scale
 
 
-def linear_solution(mesh, F, eps, b=None):
+def linear_solution(mesh, F, eps, b=None, forcing="source"):
     """The solution of the linearised problem (Section 2.3, the weak-source
     limit), offered as an initial guess in Section 4.1: one Newton step from
     the flat state with the linear Jacobian of Appendix B,
@@ -502,7 +524,7 @@ def linear_solution(mesh, F, eps, b=None):
     exact for the discretised linear problem when b is None (untruncated);
     with a block bandwidth b the same step with the truncated matrix."""
     u0 = flat_guess(mesh)
-    return u0 - np.linalg.solve(jacobian_linear(mesh, F, b), residual(mesh, F, eps, u0))
+    return u0 - np.linalg.solve(jacobian_linear(mesh, F, b), residual(mesh, F, eps, u0, forcing=forcing))
 
 
 def resample(src: Mesh, u_src, dst: Mesh):
@@ -535,30 +557,30 @@ def preconditioned_jacobian(mesh, F, eps, u, b=None):
     return J @ np.linalg.inv(jacobian_linear(mesh, F, b))
 
 
-def jacobian_fd(mesh, F, eps, u, h=1e-6):
+def jacobian_fd(mesh, F, eps, u, h=1e-6, forcing="source"):
     """Dense Jacobian by central differences (tiny meshes only)."""
     n = u.size
     J = np.empty((n, n))
     for j in range(n):
         e = np.zeros(n)
         e[j] = h
-        J[:, j] = (residual(mesh, F, eps, u + e) - residual(mesh, F, eps, u - e)) / (2 * h)
+        J[:, j] = (residual(mesh, F, eps, u + e, forcing=forcing) - residual(mesh, F, eps, u - e, forcing=forcing)) / (2 * h)
     return J
 
 
-def newton_dense(mesh, F, eps, u0, tol=1e-10, max_iter=50):
+def newton_dense(mesh, F, eps, u0, tol=1e-10, max_iter=50, forcing="source"):
     """Damped Newton (Eqs. newtonstep0, newtonstep) with a dense central-
     difference Jacobian and a halving line search on ||E||_2."""
     u = np.array(u0, dtype=np.float64)
-    E = residual(mesh, F, eps, u)
+    E = residual(mesh, F, eps, u, forcing=forcing)
     for it in range(max_iter):
         if np.max(np.abs(E)) < tol:
             return u, it
-        du = np.linalg.solve(jacobian_fd(mesh, F, eps, u), -E)
+        du = np.linalg.solve(jacobian_fd(mesh, F, eps, u, forcing=forcing), -E)
         lam = 1.0
         while True:
             un = u + lam * du
-            En = residual(mesh, F, eps, un)
+            En = residual(mesh, F, eps, un, forcing=forcing)
             if np.linalg.norm(En) <= (1 - 1e-4 * lam) * np.linalg.norm(E) or lam < 2 ** -10:
                 break
             lam *= 0.5
@@ -607,7 +629,7 @@ def gmres_right(apply_J, apply_Pinv, rhs, rtol, restart=30, max_iter=600):
     return x, total
 
 
-def newton_gmres(mesh, F, eps, u0, tol=1e-10, max_newton=50, b=None, eta=1e-4, restart=30):
+def newton_gmres(mesh, F, eps, u0, tol=1e-10, max_newton=50, b=None, eta=1e-4, restart=30, forcing="source"):
     """Damped inexact Newton with right-preconditioned GMRES and the linear-
     Jacobian preconditioner of Section 4.2 (dense LU of ``jacobian_linear``;
     small and mid-size meshes).  Returns (u, newton_iterations)."""
@@ -615,17 +637,17 @@ def newton_gmres(mesh, F, eps, u0, tol=1e-10, max_newton=50, b=None, eta=1e-4, r
     P = jacobian_linear(mesh, F, b)
     lu = sla.lu_factor(P)
     u = np.array(u0, dtype=np.float64)
-    E = residual(mesh, F, eps, u)
+    E = residual(mesh, F, eps, u, forcing=forcing)
     for it in range(max_newton):
         if np.max(np.abs(E)) < tol:
             return u, it
         Eu = E
-        du, _ = gmres_right(lambda z: jvp_fd(mesh, F, eps, u, z, Eu),
+        du, _ = gmres_right(lambda z: jvp_fd(mesh, F, eps, u, z, Eu, forcing=forcing),
                             lambda v: sla.lu_solve(lu, v), -E, eta, restart=restart)
         lam = 1.0
         while True:
             un = u + lam * du
-            En = residual(mesh, F, eps, un)
+            En = residual(mesh, F, eps, un, forcing=forcing)
             if np.linalg.norm(En) <= (1 - 1e-4 * lam) * np.linalg.norm(E) or lam < 2 ** -10:
                 break
             lam *= 0.5

@@ -386,6 +386,57 @@ def test_truncation_moves_the_spectrum_away_from_1():
     assert band > full
 
 
+def test_pressure_forcing_flat_state_residual_is_the_pressure_only():
+    """Pressure forcing: at the flat state every row vanishes except E1, which
+    is eps p(x*, y*) (the source term is absent from E2)."""
+    spec = W.MeshSpec(15, 7, -2.0, 0.3, 0.3)
+    mesh = _mesh(spec)
+    eps = 0.3
+    p = O.residual_parts(mesh, 0.7, eps, O.flat_guess(mesh), forcing="pressure")
+    xt, yt = mesh.x_star()[None, :], mesh.y()[:, None]
+    assert np.abs(p["E1"] - eps * O.pressure(xt, yt)).max() < 1e-15
+    assert np.abs(p["E2"]).max() < 1e-15
+    for k in ("E3", "E4", "E5", "E6"):
+        assert np.abs(p[k]).max() < 1e-15
+    # the bump is nonzero only inside the unit square around the origin
+    assert np.count_nonzero(p["E1"]) == np.count_nonzero((np.abs(xt) < 1) & (np.abs(yt) < 1) & (p["E1"] == p["E1"]))
+
+
+def test_pressure_forcing_weak_limit_is_the_linear_solution():
+    """As eps -> 0 the root under an applied pressure approaches the linear
+    one, u_L = u0 - J_lin^-1 E(u0): the difference is O(eps^2)."""
+    spec = W.MeshSpec(13, 5, -2.5, 0.4, 0.4)
+    mesh = _mesh(spec)
+    u0 = O.flat_guess(mesh)
+    errs = []
+    for eps in (0.04, 0.02, 0.01):
+        u, _ = O.newton_dense(mesh, 0.7, eps, u0, tol=1e-13, forcing="pressure")
+        uL = O.linear_solution(mesh, 0.7, eps, forcing="pressure")
+        errs.append(np.abs(u - uL).max())
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 3.6 < r1 < 4.4 and 3.8 < r2 < 4.2, errs
+
+
+def test_pressure_forcing_jacobian_differs_from_source_only_by_the_source_term():
+    """The two forcings give the same Jacobian up to the derivative of the
+    source term eps / r with respect to zeta* (complex step, exact)."""
+    spec = TINY
+    mesh = _mesh(spec)
+    u = W.random_state(spec, seed=24, amp=0.1)
+    v = np.random.default_rng(25).normal(size=u.size)
+    Js, _ = O.jvp_exact(mesh, 0.7, 0.3, u, v)
+    Jp, _ = O.jvp_exact(mesh, 0.7, 0.3, u, v, forcing="pressure")
+    st = O.surface(mesh, u)
+    dst = O.surface(mesh, v + 0 * u)     # the tangent of zeta* is the surface map of v without constants
+    xt, yt = mesh.x_star()[None, :], mesh.y()[:, None]
+    r2 = xt ** 2 + yt ** 2 + (st["zeta_t"] + 1) ** 2
+    # zeta is linear in u with no constant, so surface(v)["zeta_t"] is the tangent of zeta*
+    dsrc = -0.3 * (st["zeta_t"] + 1) * dst["zeta_t"] / r2 ** 1.5
+    z = np.zeros_like(dsrc)
+    diff = O.order(mesh, z, dsrc, z[:, 0], z[:, 0], z[:, 0], z[:, 0])
+    assert np.abs((Js - Jp) - diff).max() <= 1e-13 * np.abs(Js).max()
+
+
 def test_dense_newton_and_newton_gmres_reach_the_same_root():
     spec = TINY
     mesh = _mesh(spec)
