@@ -104,7 +104,15 @@ typedef struct swj_opts {
                            /* difference quotient of Eq. JvApprox) or SWJ_JVP_EXACT   */
                            /* (swj_jvp_exact, all-pairs part in the phase's precision)*/
                            /* (SWJ_JVP_FD)                                            */
+    int    forcing;        /* SWJ_FORCING_SOURCE: the submerged source of strength   */
+                           /* eps (Section 2); SWJ_FORCING_PRESSURE: an applied      */
+                           /* surface pressure eps p(x, y) in Bernoulli's condition, */
+                           /* p = exp(2 + 1/(x^2-1) + 1/(y^2-1)) on |x|, |y| < 1,    */
+                           /* else 0, and no source (SWJ_FORCING_SOURCE)             */
 } swj_opts;
+
+#define SWJ_FORCING_SOURCE   0
+#define SWJ_FORCING_PRESSURE 1
 
 #define SWJ_JVP_FD    0
 #define SWJ_JVP_EXACT 1

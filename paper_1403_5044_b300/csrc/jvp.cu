@@ -83,7 +83,7 @@ __device__ Dual I_S2(Dual A, Dual B, Dual C, int N, int M, int k, int l, double 
 // per-target part of E2', and the tangent target records.  Primal node arrays
 // and target records come from the mesh step on u that precedes it.
 __global__ void k_targets_tan(int N, int M, int H, double x1, double dx, double dy, const double *__restrict__ Fv,
-                              const double *__restrict__ epsv, double nrad, const double *__restrict__ u,
+                              const double *__restrict__ epsv, double nrad, int forcing, const double *__restrict__ u,
                               const double *__restrict__ v, const double *__restrict__ zeta,
                               const double *__restrict__ g, const double *__restrict__ zetay,
                               const double *__restrict__ gy, const double *__restrict__ dnode,
@@ -136,7 +136,8 @@ __global__ void k_targets_tan(int N, int M, int H, double x1, double dx, double 
     // source term eps / r, r^2 = x*^2 + y*^2 + (zeta* + 1)^2
     const double xt = x1 + ((double)k + 0.5) * dx, yt = (double)l * dy, zp1 = zs + 1.0;
     const double r2 = xt * xt + yt * yt + zp1 * zp1;
-    const double dsrc = -eps * zp1 * dzs / (r2 * sqrt(r2));
+    // (the applied pressure of the pressure forcing does not depend on u)
+    const double dsrc = (forcing == SWJ_FORCING_PRESSURE) ? 0.0 : -eps * zp1 * dzs / (r2 * sqrt(r2));
     de2part[ot + t] = 2.0 * kPi * dgs + dsrc - (dzx * Ival[ot + t] + zx * I.d);
     // tangent target records (units of L = dy, as the primal records)
     const size_t q = ot + t;
@@ -317,7 +318,8 @@ int swj_jvp_exact_impl(swj_ctx *c, const double *u, const double *v, double *Jv,
     swj_launch_mesh_tangent(c, v, act);
     SWJ_COUNT_LAUNCH();
     k_targets_tan<<<dim3(nblk(c->T, 128), nb), 128, 0, st>>>(
-        c->N, c->M, c->H, m.x1, m.dx, m.dy, c->Fd, c->epsd, m.n_rad, u, v, c->zeta, c->g, c->zetay, c->gy,
+        c->N, c->M, c->H, m.x1, m.dx, m.dy, c->Fd, c->epsd, m.n_rad, c->opts.forcing, u, v, c->zeta, c->g,
+        c->zetay, c->gy,
         c->dnode, c->Ival, Jv, c->de2part, c->ttgt64, c->ttgt32, act);
     SWJ_COUNT_LAUNCH();
     k_sources_tan<<<dim3(nblk(c->S, 256), nb), 256, 0, st>>>(c->N, c->M, c->H, m.dy, v, c->dnode, c->tsrc64,

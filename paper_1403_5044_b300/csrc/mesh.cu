@@ -108,9 +108,17 @@ __global__ void k_spline(int N, int M, double hy, const double *__restrict__ cp,
 }
 
 // Thread per half-mesh target t = l (N-1) + k.
+// Applied surface pressure of the pressure forcing: exp(2 + 1/(x^2-1) + 1/(y^2-1))
+// on |x|, |y| < 1, else 0 (1 at the centre; smooth, compact support).
+__device__ __forceinline__ double surface_pressure(double x, double y)
+{
+    if (!(fabs(x) < 1.0 && fabs(y) < 1.0)) return 0.0;
+    return exp(2.0 + 1.0 / (x * x - 1.0) + 1.0 / (y * y - 1.0));
+}
+
 __global__ void k_targets(int N, int M, int H, double x1, double dx, double dy,
                           const double *__restrict__ Fv, const double *__restrict__ epsv,
-                          double nrad, const double *__restrict__ u,
+                          double nrad, int forcing, const double *__restrict__ u,
                           const double *__restrict__ zeta, const double *__restrict__ g,
                           const double *__restrict__ zetay, const double *__restrict__ gy,
                           double *__restrict__ E, double *__restrict__ e2part,
@@ -149,7 +157,9 @@ __global__ void k_targets(int N, int M, int H, double x1, double dx, double dy,
     double yt = (double)l * dy;
     double I = swj_I_S2(A, B, C, N, M, k, l, dx, dy);
     double zp1 = zs + 1.0;
-    double src = eps / sqrt(xt * xt + yt * yt + zp1 * zp1);
+    double src = 0.0;
+    if (forcing == SWJ_FORCING_PRESSURE) E1 += eps * surface_pressure(xt, yt);
+    else src = eps / sqrt(xt * xt + yt * yt + zp1 * zp1);
     e2part[t] = 2.0 * kPi * gs + src - zx * I;
     Ival[t] = I;
     E[(size_t)l * (N + 1) + 2 + k] = E1;
@@ -348,7 +358,7 @@ void swj_launch_mesh_step(swj_ctx *c, const double *u, double *E, const int *act
                                                               c->gy, act);
     SWJ_COUNT_LAUNCH();
     k_targets<<<dim3(nblk(c->T, 128), nb), 128, 0, st>>>(c->N, c->M, c->H, m.x1, m.dx, m.dy, c->Fd,
-                                                          c->epsd, m.n_rad, u, c->zeta, c->g,
+                                                          c->epsd, m.n_rad, c->opts.forcing, u, c->zeta, c->g,
                                                           c->zetay, c->gy, E, c->e2part, c->Ival,
                                                           c->tgt64, c->tgt32, act);
     SWJ_COUNT_LAUNCH();

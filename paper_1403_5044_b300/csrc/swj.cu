@@ -29,6 +29,7 @@ bool valid_opts(const swj_opts *o)
     if (o->autotune != 0 && o->autotune != 1) return false;
     if (o->refine_precision != SWJ_FF && o->refine_precision != SWJ_FP64) return false;
     if (o->jvp != SWJ_JVP_FD && o->jvp != SWJ_JVP_EXACT) return false;
+    if (o->forcing != SWJ_FORCING_SOURCE && o->forcing != SWJ_FORCING_PRESSURE) return false;
     return true;
 }
 
@@ -247,6 +248,7 @@ void swj_default_opts(swj_opts *o)
     o->autotune = 1;
     o->refine_precision = SWJ_FF;
     o->jvp = SWJ_JVP_FD;
+    o->forcing = SWJ_FORCING_SOURCE;
 }
 
 int swj_create(swj_ctx **out, const swj_mesh *mesh, double F, double eps, const swj_opts *opts,
