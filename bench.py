@@ -93,6 +93,9 @@ def parse():
     ap.add_argument("--mesh", default="181x61",
                     help="--precond-only: mesh NxM on x in [-16,20], y in [0,12] (F = 0.7, eps = 0.3 "
                          "unless 181x61, the workload)")
+    ap.add_argument("--lu-products", type=int, default=None,
+                    help="block products of the band LU: 0 FP64 kernel, 1 bf16 slices on the tensor cores "
+                         "(default: the library's)")
     ap.add_argument("--spectrum", action="store_true",
                     help="spectral diagnostics of J P^-1 (41x21, F = 0.7, eps = 0.1, at the root) for several b")
     ap.add_argument("--precond-only", action="store_true",
@@ -676,7 +679,8 @@ def run_precond_only(args):
     if args.mesh != "181x61":
         N, M = (int(v) for v in args.mesh.split("x"))
         spec, F, eps = W.domain_mesh(N, M), 0.7, 0.3
-    with swj.Context.from_spec(spec, F, eps, solve_mode="mixed", block_bw=args.block_bw) as ctx:
+    kw = {} if args.lu_products is None else {"lu_products": args.lu_products}
+    with swj.Context.from_spec(spec, F, eps, solve_mode="mixed", block_bw=args.block_bw, **kw) as ctx:
         ctx.precond_setup()             # first use: module loading and kernel attributes
         ctx.sync()
         t0 = time.perf_counter()
@@ -703,6 +707,7 @@ def run_precond_only(args):
         st = ctx.solve(u)
         t3 = time.perf_counter()
     print(json.dumps({"precond_only": True, "mesh": args.mesh, "block_bw": args.block_bw,
+                      "lu_products": args.lu_products,
                       "setup_ms": (t1 - t0) * 1e3,
                       "apply_ms": apply_ms, "sweep_clusters": clusters, "solve_ms": (t3 - t2) * 1e3,
                       "krylov_iters": st["krylov_iters"], "residual_evals": st["residual_evals"]}))

@@ -109,7 +109,15 @@ typedef struct swj_opts {
                            /* surface pressure eps p(x, y) in Bernoulli's condition, */
                            /* p = exp(2 + 1/(x^2-1) + 1/(y^2-1)) on |x|, |y| < 1,    */
                            /* else 0, and no source (SWJ_FORCING_SOURCE)             */
+    int    lu_products;    /* block products of the band LU's bulk updates:          */
+                           /* SWJ_LU_FP64 (FP64 CUDA-core kernel) or SWJ_LU_SLICED    */
+                           /* (FP64-accurate: bf16 slices of each factor multiplied   */
+                           /* exactly on the tensor cores, Ozaki's splitting, summed */
+                           /* in FP64) (SWJ_LU_SLICED)                                */
 } swj_opts;
+
+#define SWJ_LU_FP64   0
+#define SWJ_LU_SLICED 1
 
 #define SWJ_FORCING_SOURCE   0
 #define SWJ_FORCING_PRESSURE 1

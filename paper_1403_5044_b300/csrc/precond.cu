@@ -305,6 +305,14 @@ void free_pc(swj_ctx *c)
     c->pc_ptrs_cap = 0;
     if (c->pc_mc_err) cudaFree(c->pc_mc_err);
     c->pc_mc_err = nullptr;
+    void *oz[] = {c->oz_sa, c->oz_sb, c->oz_ea, c->oz_eb, c->oz_P, c->oz_ptrs, c->oz_desc};
+    for (void *q : oz)
+        if (q) cudaFree(q);
+    c->oz_sa = c->oz_sb = nullptr;
+    c->oz_ea = c->oz_eb = nullptr;
+    c->oz_P = nullptr;
+    c->oz_ptrs = nullptr;
+    c->oz_desc = nullptr;
     c->pc_mc = 0;
     if (c->pc_chain) {
         cudaStreamSynchronize(c->pc_chain);
@@ -363,11 +371,53 @@ size_t pc_gemm_count(int M, int nb, int h)
     return np;
 }
 
+// ---- sliced (bf16 tensor-core) block products of the bulk stream (ozaki.cu)
+// Per step i and instance: the A factors split by rows (slot 0 = inv_i,
+// slot 1 + (j - i - 1) = S_ji, j = i+1..kmax), the B factors split by columns
+// (S_ik, k = i+2..kmax at [0, h-1); W_ik, k = i+1..kmax at [h, 2h); S_ij,
+// j < i, at [2h, 3h)), and the products of the groups Wb, B1, B2, L.
+struct OzLayout {
+    int np, beta, s;
+    size_t nsa, nsb;          // slice slots (A, B)
+    size_t maxP;              // block products per batched call
+    size_t nptr, nprod;       // split-list and product-list entries of all steps
+    size_t bytes_desc;        // descriptor buffer
+    size_t bytes;             // every buffer of the sliced path
+};
+
+constexpr size_t kOzPBytes = (size_t)256 << 20;   // slice products of one batched call
+
+size_t oz_align(size_t b) { return (b + 255) & ~(size_t)255; }
+
+OzLayout oz_layout(int n1, int M, int nb, int h)
+{
+    OzLayout L = {};
+    swj_ozaki_params(n1, &L.np, &L.beta, &L.s);
+    const size_t n2 = (size_t)L.np * L.np;
+    L.nsa = (size_t)nb * (h + 1);
+    L.nsb = (size_t)nb * 3 * h;
+    const size_t per = (size_t)L.s * n2 * sizeof(float);
+    size_t cap = kOzPBytes / per;
+    if (cap < 1) cap = 1;
+    const size_t most = (size_t)nb * h * h;
+    L.maxP = cap < most ? cap : most;
+    for (int i = 0; i < M; ++i) {
+        const size_t kr = (size_t)(i + h < M - 1 ? h : M - 1 - i), nt = (size_t)(i < h ? i : h);
+        L.nptr += (size_t)nb * ((1 + kr) + (kr > 0 ? kr - 1 : 0) + kr + nt);
+        L.nprod += (size_t)nb * ((kr > 0 ? kr - 1 : 0) + (kr > 0 ? kr * kr - 1 : 0) + nt);
+    }
+    L.bytes_desc = oz_align(L.nptr * sizeof(double *)) + oz_align(L.nptr * sizeof(int)) +
+                   oz_align(L.nprod * sizeof(OzProd));
+    L.bytes = L.nsa * L.s * n2 * 2 + L.nsb * L.s * n2 * 2 + (L.nsa + L.nsb) * L.np * sizeof(int) +
+              L.maxP * per + 3 * L.maxP * L.s * sizeof(void *) + L.bytes_desc;
+    return L;
+}
+
 }  // namespace
 
 void swj_pc_free(swj_ctx *c) { free_pc(c); }
 
-size_t swj_pc_bytes(int N, int M, int nb, int block_bw)
+size_t swj_pc_bytes(int N, int M, int nb, int block_bw, int lu_products)
 {
     const int n1 = N + 1, h = half_band(block_bw, M);
     size_t sz[kPcBufs], tot = 0;
@@ -376,6 +426,7 @@ size_t swj_pc_bytes(int N, int M, int nb, int block_bw)
     tot += (size_t)nb * M * sizeof(int);
     tot += 3 * pc_gemm_count(M, nb, h) * sizeof(double *);
     if (pc_mc_doubles(n1, M, nb, h)) tot += sizeof(int);
+    if (lu_products == SWJ_LU_SLICED && h > 0) tot += oz_layout(n1, M, nb, h).bytes;
     return tot;
 }
 
@@ -403,7 +454,8 @@ int swj_pc_setup(swj_ctx *c)
     const size_t n2 = (size_t)n1 * n1;
     const int nbs = 2 * h + 1;
     const bool gj_inplace = swj_gj_inplace(n1);
-    if (!c->pc_band || c->pc_h != h) {
+    const bool sliced = c->opts.lu_products == SWJ_LU_SLICED && h > 0;
+    if (!c->pc_band || c->pc_h != h || (c->oz_sa != nullptr) != sliced) {
         free_pc(c);
         c->pc_h = h;
         c->pc_nb = nbs;
@@ -436,6 +488,23 @@ int swj_pc_setup(swj_ctx *c)
             }
             c->pc_bytes += sizeof(int);
             c->bytes += sizeof(int);
+        }
+        if (sliced) {
+            const OzLayout L = oz_layout(n1, M, nb, h);
+            void **ozb[] = {&c->oz_sa, &c->oz_sb, (void **)&c->oz_ea, (void **)&c->oz_eb, (void **)&c->oz_P,
+                            (void **)&c->oz_ptrs, &c->oz_desc};
+            const size_t p2 = (size_t)L.np * L.np;
+            const size_t ozs[] = {L.nsa * L.s * p2 * 2, L.nsb * L.s * p2 * 2, L.nsa * L.np * sizeof(int),
+                                  L.nsb * L.np * sizeof(int), L.maxP * L.s * p2 * sizeof(float),
+                                  3 * L.maxP * L.s * sizeof(void *), L.bytes_desc};
+            for (int i = 0; i < 7; ++i) {
+                if (cudaMalloc(ozb[i], ozs[i]) != cudaSuccess) {
+                    free_pc(c);
+                    return SWJ_ENOMEM;
+                }
+                c->pc_bytes += ozs[i];
+                c->bytes += ozs[i];
+            }
         }
     }
     c->pc_ready = 0;
@@ -585,6 +654,75 @@ int swj_pc_setup(swj_ctx *c)
                                      cudaMemcpyHostToDevice, st));
         SWJ_CUDA_TRY(cudaStreamSynchronize(st));   // `all` must outlive the copy
         double **dA = c->pc_ptrs, **dB = c->pc_ptrs + np, **dC = c->pc_ptrs + 2 * np;
+        // the sliced path: split lists and product lists of every step (see OzLayout)
+        struct OzStep {
+            size_t a, wb, u, l, pwb, pb1, pb2, pl;
+            int na, nwb, nu, nl, cwb, cb1, cb2, cl;
+        };
+        std::vector<OzStep> zo(sliced ? M : 0);
+        OzLayout OL = {};
+        const double *const *zP = nullptr;
+        const int *zS = nullptr;
+        const OzProd *zQ = nullptr;
+        if (sliced) {
+            OL = oz_layout(n1, M, nb, h);
+            std::vector<const double *> zp;
+            std::vector<int> zs;
+            std::vector<OzProd> zq;
+            const int hs = h + 1, hb = 3 * h;
+            for (int i = 0; i < M; ++i) {
+                const int kmax = i + h < M - 1 ? i + h : M - 1, j0 = std::max(0, i - h);
+                OzStep &o = zo[i];
+                o.a = zp.size();
+                for (int q = 0; q < nb; ++q) {
+                    zp.push_back(blk(c, q, i, i)); zs.push_back(q * hs);
+                    for (int j = i + 1; j <= kmax; ++j) { zp.push_back(blk(c, q, j, i)); zs.push_back(q * hs + (j - i)); }
+                }
+                o.na = (int)(zp.size() - o.a);
+                o.wb = zp.size();
+                for (int q = 0; q < nb; ++q)
+                    for (int k = i + 2; k <= kmax; ++k) { zp.push_back(blk(c, q, i, k)); zs.push_back(q * hb + (k - i - 2)); }
+                o.nwb = (int)(zp.size() - o.wb);
+                o.u = zp.size();
+                for (int q = 0; q < nb; ++q)
+                    for (int k = i + 1; k <= kmax; ++k) { zp.push_back(wblk(c, q, i, k)); zs.push_back(q * hb + h + (k - i - 1)); }
+                o.nu = (int)(zp.size() - o.u);
+                o.l = zp.size();
+                for (int q = 0; q < nb; ++q)
+                    for (int j = j0; j < i; ++j) { zp.push_back(blk(c, q, i, j)); zs.push_back(q * hb + 2 * h + (j - j0)); }
+                o.nl = (int)(zp.size() - o.l);
+                o.pwb = zq.size();
+                for (int q = 0; q < nb; ++q)
+                    for (int k = i + 2; k <= kmax; ++k) zq.push_back({q * hs, q * hb + (k - i - 2), wblk(c, q, i, k), 0});
+                o.cwb = (int)(zq.size() - o.pwb);
+                for (int g = 0; g < 2; ++g) {
+                    (g ? o.pb2 : o.pb1) = zq.size();
+                    for (int q = 0; q < nb; ++q)
+                        for (int j = i + 1; j <= kmax; ++j)
+                            for (int k = i + 1; k <= kmax; ++k) {
+                                if (j == i + 1 && k == i + 1) continue;   // the chain's update
+                                if (chain_b1(i, j, k) != (g == 0)) continue;
+                                zq.push_back({q * hs + (j - i), q * hb + h + (k - i - 1), blk(c, q, j, k), 1});
+                            }
+                    (g ? o.cb2 : o.cb1) = (int)(zq.size() - (g ? o.pb2 : o.pb1));
+                }
+                o.pl = zq.size();
+                for (int q = 0; q < nb; ++q)
+                    for (int j = j0; j < i; ++j)
+                        zq.push_back({q * hs, q * hb + 2 * h + (j - j0), c->pc_lt + ((size_t)q * h + (j - j0)) * n2, 0});
+                o.cl = (int)(zq.size() - o.pl);
+            }
+            if (zp.size() != OL.nptr || zq.size() != OL.nprod) return SWJ_EINVAL;   // layout and lists disagree
+            char *base = (char *)c->oz_desc;
+            const size_t offS = oz_align(OL.nptr * sizeof(double *)), offQ = offS + oz_align(OL.nptr * sizeof(int));
+            SWJ_CUDA_TRY(cudaMemcpyAsync(base, zp.data(), zp.size() * sizeof(double *), cudaMemcpyHostToDevice, st));
+            SWJ_CUDA_TRY(cudaMemcpyAsync(base + offS, zs.data(), zs.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+            SWJ_CUDA_TRY(cudaMemcpyAsync(base + offQ, zq.data(), zq.size() * sizeof(OzProd), cudaMemcpyHostToDevice, st));
+            SWJ_CUDA_TRY(cudaStreamSynchronize(st));   // the host lists must outlive the copies
+            zP = (const double *const *)base;
+            zS = (const int *)(base + offS);
+            zQ = (const OzProd *)(base + offQ);
+        }
         // Look-ahead factorisation.  The chain stream (high priority) runs only
         // what the next diagonal block waits for: at step i it inverts S_ii,
         // forms W_{i,i+1} and applies the one update S_{i+1,i+1} -= S_{i+1,i}
@@ -645,6 +783,38 @@ int swj_pc_setup(swj_ctx *c)
             SWJ_CUDA_TRY(cudaEventRecord(evW[i % 4], sc));
             if ((rc = gemm(sc, i, gUc, -1.0, 1.0))) return rc;
             SWJ_CUDA_TRY(cudaStreamWaitEvent(sb, evW[i % 4], 0));
+            if (sliced) {
+                const OzStep &o = zo[i];
+                auto split = [&](bool rows, size_t off, int n_) {
+                    return swj_ozaki_split(sb, rows, n1, OL.np, OL.s, OL.beta, n_, zP + off, zS + off,
+                                           rows ? c->oz_sa : c->oz_sb, rows ? c->oz_ea : c->oz_eb);
+                };
+                auto prods = [&](size_t off, int n_, double alpha) {
+                    for (int c0 = 0; c0 < n_; c0 += (int)OL.maxP) {
+                        const int cc = std::min((int)OL.maxP, n_ - c0);
+                        const int r_ = swj_ozaki_products(&c->cublas, sb, n1, OL.np, OL.s, OL.beta, cc,
+                                                          zQ + off + c0, c->oz_sa, c->oz_ea, c->oz_sb, c->oz_eb,
+                                                          alpha, c->oz_P, c->oz_ptrs);
+                        if (r_) return r_;
+                    }
+                    return (int)SWJ_OK;
+                };
+                if ((rc = split(true, o.a, o.na)) || (rc = split(false, o.wb, o.nwb)) ||
+                    (rc = prods(o.pwb, o.cwb, 1.0)) || (rc = split(false, o.u, o.nu)) ||
+                    (rc = prods(o.pb1, o.cb1, -1.0)))
+                    return rc;
+                SWJ_CUDA_TRY(cudaEventRecord(evB1[i % 4], sb));
+                if ((rc = prods(o.pb2, o.cb2, -1.0)) || (rc = split(false, o.l, o.nl)) ||
+                    (rc = prods(o.pl, o.cl, 1.0)))
+                    return rc;
+                if (o.cl) {
+                    const int nt = std::min(i, h);
+                    SWJ_COUNT_LAUNCH();
+                    k_copy_blocks<<<dim3(64, nb), 256, 0, sb>>>((size_t)nt * n2, c->pc_lt, (size_t)h * n2,
+                                                                blk(c, 0, i, i - nt), bst);
+                }
+                continue;
+            }
             if ((rc = gemm(sb, i, gWb, 1.0, 0.0))) return rc;
             if ((rc = gemm(sb, i, gB1, -1.0, 1.0))) return rc;
             SWJ_CUDA_TRY(cudaEventRecord(evB1[i % 4], sb));

@@ -30,6 +30,7 @@ bool valid_opts(const swj_opts *o)
     if (o->refine_precision != SWJ_FF && o->refine_precision != SWJ_FP64) return false;
     if (o->jvp != SWJ_JVP_FD && o->jvp != SWJ_JVP_EXACT) return false;
     if (o->forcing != SWJ_FORCING_SOURCE && o->forcing != SWJ_FORCING_PRESSURE) return false;
+    if (o->lu_products != SWJ_LU_FP64 && o->lu_products != SWJ_LU_SLICED) return false;
     return true;
 }
 
@@ -57,6 +58,8 @@ void free_all(swj_ctx *c)
     free(c->eps);
     swj_graphs_free(c);
     swj_pc_free(c);
+    swj_cublas_destroy(c->cublas);
+    c->cublas = nullptr;
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
     if (c->tev) {
@@ -249,6 +252,7 @@ void swj_default_opts(swj_opts *o)
     o->refine_precision = SWJ_FF;
     o->jvp = SWJ_JVP_FD;
     o->forcing = SWJ_FORCING_SOURCE;
+    o->lu_products = SWJ_LU_SLICED;
 }
 
 int swj_create(swj_ctx **out, const swj_mesh *mesh, double F, double eps, const swj_opts *opts,
@@ -325,7 +329,9 @@ int swj_set_opts(swj_ctx *c, const swj_opts *o)
         c->bytes += (size_t)c->nb * (2 * c->kry_m + 1) * c->nu * sizeof(double);
     }
     if (o->fd_h != c->opts.fd_h) swj_graphs_free(c);
-    if (o->block_bw != c->opts.block_bw || o->solve_mode != c->opts.solve_mode) c->pc_ready = 0;
+    if (o->block_bw != c->opts.block_bw || o->solve_mode != c->opts.solve_mode ||
+        o->lu_products != c->opts.lu_products)
+        c->pc_ready = 0;
     c->opts = *o;
     return SWJ_OK;
 }
@@ -368,7 +374,7 @@ size_t swj_footprint_bytes(const swj_mesh *mesh, int count, const swj_opts *opts
     if (!valid_mesh(mesh) || count < 1 || !valid_opts(&o)) return 0;
     size_t b = 0;
     if (ctx_bytes(mesh, count, o.gmres_restart, &b) != SWJ_OK) return 0;
-    return b + swj_pc_bytes(mesh->N, mesh->M, count, o.block_bw);
+    return b + swj_pc_bytes(mesh->N, mesh->M, count, o.block_bw, o.lu_products);
 }
 
 int swj_initial_guess_flat(swj_ctx *c, double *u)

@@ -53,6 +53,14 @@ struct PairPlan {
     int v;        // compiled tile shape (index into the variant table)
 };
 
+// One FP64 block product of the sliced (tensor-core) path, ozaki.cu:
+// C = alpha A_slot(a) B_slot(b) (+ C when accumulate)
+struct OzProd {
+    int a, b;
+    double *C;
+    int accumulate;
+};
+
 // is instance `inst` active (act = device flags, or nullptr for all)
 #define SWJ_INST_ACTIVE(act, inst) ((act) == nullptr || (act)[inst] != 0)
 
@@ -134,6 +142,14 @@ struct swj_ctx {
     int *pc_mc_err;
     int pc_mc;                   // 1: the apply uses swj_band_sweep_mc
     double *pc_lt;               // set-up scratch: inv_i S_ij (j < i) of one block row, every instance
+    // sliced (bf16 tensor-core) block products of the band LU (lu_products = SWJ_LU_SLICED)
+    void *oz_sa, *oz_sb;         // bf16 slices of the A (row-split) and B (column-split) factors
+    int *oz_ea, *oz_eb;          // their row / column exponents
+    float *oz_P;                 // slice products of one batch of block products
+    void **oz_ptrs;              // pointer arrays of the batched GEMM
+    void *oz_desc;               // split lists and product lists of every step (device)
+    size_t oz_desc_cap;
+    void *cublas;                // cuBLAS handle (bf16 GEMMs)
 
     // exact JVP (jvp.cu): tangents of the node arrays [4][nb][S] (zeta, g,
     // zeta_y, g_y), of the source records and target arrays (same layouts
@@ -226,6 +242,18 @@ void swj_bcombine(cudaStream_t st, int nb, int n, int rows, const double *Z, siz
 void swj_dgemm_batched(cudaStream_t st, int m, int n, int k, double alpha,
                        const double *const *A, int lda, const double *const *B, int ldb,
                        double beta, double *const *C, int ldc, int batch, int tile = 64);   // tile 16, 32 or 64
+// ozaki.cu: FP64-accurate block products from bf16 slices (see there)
+// n: block size; np: n padded to a multiple of 8; beta bits per digit, s digits
+void swj_ozaki_params(int n, int *np, int *beta, int *s);
+// A factors (by_rows): slot layout [np][s][np] bf16 + [np] exponents;
+// B factors: [s][np][np] + [np]
+int swj_ozaki_split(cudaStream_t st, bool by_rows, int n, int np, int s, int beta, int count,
+                    const double *const *mats, const int *slots, void *slices, int *ex);
+// P: count * s * np^2 floats; ptrs: 3 * count * s pointers
+int swj_ozaki_products(void **handle, cudaStream_t st, int n, int np, int s, int beta, int count,
+                       const OzProd *prods, const void *sa, const int *ea, const void *sb, const int *eb,
+                       double alpha, float *P, void **ptrs);
+void swj_cublas_destroy(void *handle);
 void swj_dgemm(cudaStream_t st, int m, int n, int k, double alpha, const double *A, int lda,
                const double *B, int ldb, double beta, double *C, int ldc);
 
@@ -265,7 +293,7 @@ int swj_pc_apply(swj_ctx *c, const double *b, double *r, const int *act);
 int swj_pc_status(swj_ctx *c);   // SWJ_ETIMEOUT if a bounded wait of the apply gave up
 void swj_pc_free(swj_ctx *c);
 // device bytes the preconditioner of an nb-instance context holds after set-up
-size_t swj_pc_bytes(int N, int M, int nb, int block_bw);
+size_t swj_pc_bytes(int N, int M, int nb, int block_bw, int lu_products);
 
 // solver.cu
 int swj_residual_impl(swj_ctx *c, const double *u, double *E, int precision, const int *act);

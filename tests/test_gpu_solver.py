@@ -47,16 +47,18 @@ def test_jvp_matches_oracle_derivative():
                                     (W.MESH_41x21, 1),
                                     (W.MESH_41x21, 5),
                                     (W.MESH_41x21, 11)])
-def test_precond_apply_matches_linear_jacobian_solve(spec, b):
+@pytest.mark.parametrize("lu", [swj.LU_FP64, swj.LU_SLICED])
+def test_precond_apply_matches_linear_jacobian_solve(spec, b, lu):
     """r = P^-1 b from the Schur-complement block LU (Appendix C) equals a
     dense solve with the oracle's Appendix B matrix truncated to the same
-    block bandwidth."""
+    block bandwidth, with the band LU's block products in FP64 or from bf16
+    slices on the tensor cores."""
     F = 0.7
     m = omesh(spec)
     P = O.jacobian_linear(m, F, None if b == 0 else b)
     rhs = np.random.default_rng(b + spec.N).normal(size=m.n_unknowns)
     ref = np.linalg.solve(P, rhs)
-    with swj.Context.from_spec(spec, F, 0.1, solve_mode="fp64", block_bw=b) as ctx:
+    with swj.Context.from_spec(spec, F, 0.1, solve_mode="fp64", block_bw=b, lu_products=lu) as ctx:
         ctx.precond_setup()
         r = ctx.vector()
         ctx.precond_apply(dev(rhs), r)
@@ -93,6 +95,31 @@ def test_multi_cluster_sweep_equals_one_cluster_sweep(spec, b):
     hb = (spec.M - 1) if b == 0 else min((b - 1) // 2, spec.M - 1)
     assert h == hb, (h, hb)          # the device holds these few clusters at once
     assert np.array_equal(r1, rb[0]) and np.array_equal(r1, rb[1])
+
+
+@pytest.mark.parametrize("spec,b", [(W.MESH_41x21, 5), (W.SOLVE_181x61[0], 11), (W.SERVE_MESHES[3], 15)])
+def test_sliced_lu_products_agree_with_fp64_and_do_not_depend_on_the_batch(spec, b):
+    """The sliced block products are FP64-accurate (the applies agree with the
+    FP64 products to rounding) and exact slice by slice, so a batch of two
+    equals the single instance bit for bit."""
+    F = 0.75
+    rhs = np.random.default_rng(spec.N + b + 1).normal(size=spec.n_unknowns)
+    out = {}
+    for lu in (swj.LU_FP64, swj.LU_SLICED):
+        with swj.Context.from_spec(spec, F, 0.2, solve_mode="fp64", block_bw=b, lu_products=lu) as one:
+            r = one.vector()
+            one.precond_apply(dev(rhs), r)
+            one.sync()
+            out[lu] = r.cpu().numpy()
+    # both are FP64-accurate factorisations; their rounding differs, amplified by the conditioning of S
+    assert np.abs(out[swj.LU_SLICED] - out[swj.LU_FP64]).max() <= 1e-10 * np.abs(out[swj.LU_FP64]).max()
+    with swj.BatchContext.from_spec(spec, [F, F], [0.2, 0.2], solve_mode="fp64", block_bw=b,
+                                    lu_products=swj.LU_SLICED) as two:
+        rb = two.vector()
+        two.precond_apply(dev(np.concatenate([rhs, rhs])), rb)
+        two.sync()
+        rb = two.view(rb).cpu().numpy()
+    assert np.array_equal(rb[0], out[swj.LU_SLICED]) and np.array_equal(rb[1], out[swj.LU_SLICED])
 
 
 def gpu_solve(spec, F, eps, **kw):
