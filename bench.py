@@ -96,6 +96,8 @@ def parse():
     ap.add_argument("--lu-products", type=int, default=None,
                     help="block products of the band LU: 0 FP64 kernel, 1 bf16 slices on the tensor cores "
                          "(default: the library's)")
+    ap.add_argument("--jvp-only", action="store_true",
+                    help="exact Jacobian-vector products of the 181x61 workload only (FP32 and FP64, timed)")
     ap.add_argument("--spectrum", action="store_true",
                     help="spectral diagnostics of J P^-1 (41x21, F = 0.7, eps = 0.1, at the root) for several b")
     ap.add_argument("--precond-only", action="store_true",
@@ -713,6 +715,30 @@ def run_precond_only(args):
                       "krylov_iters": st["krylov_iters"], "residual_evals": st["residual_evals"]}))
 
 
+def run_jvp_only(args):
+    import numpy as np
+    import torch
+    from paper_1403_5044_b300 import swj
+    from paper_1403_5044_b300 import workloads as W
+    spec, F, eps = W.SOLVE_181x61
+    with swj.Context.from_spec(spec, F, eps) as ctx:
+        u = torch.tensor(W.random_state(spec, seed=1, amp=0.05), device="cuda")
+        v = torch.tensor(np.random.default_rng(2).normal(size=ctx.n_unknowns), device="cuda")
+        J = ctx.vector()
+        out = {"jvp_only": True, "workload": WORKLOAD, "pairs": spec.pairs}
+        for name, prec, reps in (("fp32", swj.FP32, args.steps), ("fp64", swj.FP64, max(1, args.steps // 10))):
+            ctx.jvp_exact(u, v, J, prec)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(reps):
+                ctx.jvp_exact(u, v, J, prec)
+            b.record()
+            torch.cuda.synchronize()
+            out[name + "_ms"] = a.elapsed_time(b) / reps
+    print(json.dumps(out), flush=True)
+
+
 def run_spectrum(args):
     import torch
     from paper_1403_5044_b300 import diagnostics as D
@@ -742,6 +768,9 @@ def main():
     args = parse()
     if args.spectrum:
         run_spectrum(args)
+        return
+    if args.jvp_only:
+        run_jvp_only(args)
         return
     if args.large:
         if args.block_bw == BLOCK_BW:
