@@ -12,9 +12,13 @@
 // shifts from the FP64 bit pattern); B the same by columns.  Then
 //   (A B)[r,c] = 2^(ea_r + eb_c) sum_d 2^(-beta (d+2)) T_d[r,c],
 //   T_d = sum_{p+q=d} a_p b_q = [a_0 .. a_d] [b_d; ..; b_0],
-// one GEMM with inner dimension (d+1) n per d (A's slices are stored
-// interleaved by row and B's in reverse order, so both operands are plain
-// strided matrices).  beta is chosen so that s n 2^(2 beta) <= 2^24: every
+// one GEMM per d, all with inner dimension s n: A's slices are stored
+// interleaved by row ([a_0 .. a_(s-1)] per row) and B's in reverse order
+// followed by s - 1 zero slices ([b_(s-1); ..; b_0; 0; ..; 0]), so that the s
+// rows of slices starting at b_d are [b_d; ..; b_0; 0..] and every T_d is a
+// plain strided product; the T_d of all products of a group are one batched
+// call (the zero slices cost tensor-core flops, not launches).  beta is
+// chosen so that s n 2^(2 beta) <= 2^24: every
 // partial sum of every T_d is an integer below 2^24, so a bf16 GEMM with FP32
 // accumulation (cuBLAS) computes it exactly whatever its summation order.
 // The T_d for d <= s - 1 are added in FP64, smallest first; the dropped terms
@@ -95,9 +99,10 @@ __global__ void k_oz_split_rows(int n, int np, int s, int beta, const double *co
     }
 }
 
-// Split by columns: slot slots[m] of sb, layout [slot][s][np][np] with digit q
-// at position s - 1 - q (reverse order); column exponents ex[slot][np].  Block
-// per (32-column strip, matrix): lanes over columns, warps over rows.
+// Split by columns: slot slots[m] of sb, layout [slot][2s-1][np][np] with digit
+// q at position s - 1 - q (reverse order; positions s .. 2s-2 stay zero);
+// column exponents ex[slot][np].  Block per (32-column strip, matrix): lanes
+// over columns, warps over rows.
 __global__ void k_oz_split_cols(int n, int np, int s, int beta, const double *const *mats, const int *slots,
                                 __nv_bfloat16 *sb, int *ex)
 {
@@ -120,7 +125,7 @@ __global__ void k_oz_split_cols(int n, int np, int s, int beta, const double *co
     const int e = (c < n) ? row_exponent(red[0][threadIdx.x & 31]) : 0;
     if (w == 0) ex[(size_t)slot * np + c] = e;
     const size_t n2 = (size_t)np * np;
-    __nv_bfloat16 *out = sb + (size_t)slot * s * n2 + c;
+    __nv_bfloat16 *out = sb + (size_t)slot * (2 * s - 1) * n2 + c;
     const int bits = s * beta;
     const unsigned mask = (1u << beta) - 1u;
     for (int r = w; r < np; r += nw) {
@@ -135,18 +140,18 @@ __global__ void k_oz_split_cols(int n, int np, int s, int beta, const double *co
 }
 
 // Pointer arrays of the GEMMs T_d of `count` products, d = 0..s-1: entry
-// d * count + t.  Row-major T = A' B' is the column-major T^T = B'^T A'^T, so
-// B' (rows (d+1) np, the slices q = d .. 0, i.e. stored positions s-1-d ..
-// s-1) comes first; A' is row-major with leading dimension s np.
+// t * s + d.  Row-major T = A' B' is the column-major T^T = B'^T A'^T, so B'
+// (s np rows from stored position s-1-d: b_d .. b_0 then zeros) comes first;
+// A' is row-major with leading dimension s np.
 __global__ void k_oz_ptrs(int count, int s, int np, const OzProd *__restrict__ prods, const __nv_bfloat16 *sa,
                           const __nv_bfloat16 *sb, float *P, const void **pA, const void **pB, void **pC)
 {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= count * s) return;
-    const int d = e / count, t = e % count;
+    const int t = e / s, d = e % s;
     const OzProd o = prods[t];
     const size_t n2 = (size_t)np * np;
-    pA[e] = sb + ((size_t)o.b * s + (s - 1 - d)) * n2;
+    pA[e] = sb + ((size_t)o.b * (2 * s - 1) + (s - 1 - d)) * n2;
     pB[e] = sa + (size_t)o.a * np * s * np;
     pC[e] = P + ((size_t)t * s + d) * n2;
 }
@@ -164,8 +169,10 @@ __global__ void k_oz_combine(int n, int np, int s, int beta, const OzProd *__res
     const int r = (int)(e / n), c = (int)(e % n);
     const size_t n2 = (size_t)np * np;
     const float *Pt = P + (size_t)t * s * n2 + (size_t)r * np + c;
+    // 2^(-beta (d+2)) built from its exponent bits (exact), one FMA per term
     double v = 0.0;
-    for (int d = s - 1; d >= 0; --d) v += ldexp((double)Pt[(size_t)d * n2], -beta * (d + 2));
+    for (int d = s - 1; d >= 0; --d)
+        v = fma((double)Pt[(size_t)d * n2], __longlong_as_double((long long)(1023 - beta * (d + 2)) << 52), v);
     v = ldexp(v, ea[(size_t)o.a * np + r] + eb[(size_t)o.b * np + c]);
     double *C = o.C + e;
     *C = o.accumulate ? fma(alpha, v, *C) : alpha * v;
@@ -218,14 +225,11 @@ int swj_ozaki_products(void **handle, cudaStream_t st, int n, int np, int s, int
     SWJ_COUNT_LAUNCH();
     k_oz_ptrs<<<nblk(nall, 256), 256, 0, st>>>(count, s, np, prods, sa, sb, P, pA, pB, pC);
     const float one = 1.0f, zero = 0.0f;
-    for (int d = 0; d < s; ++d) {
-        // T_d^T (np x np, column-major) = B'^T (np x (d+1) np) A'^T ((d+1) np x np)
-        if (cublasGemmBatchedEx(h, CUBLAS_OP_N, CUBLAS_OP_N, np, np, (d + 1) * np, &one, pA + (size_t)d * count,
-                                CUDA_R_16BF, np, pB + (size_t)d * count, CUDA_R_16BF, s * np, &zero,
-                                pC + (size_t)d * count, CUDA_R_32F, np, count, CUBLAS_COMPUTE_32F,
-                                CUBLAS_GEMM_DEFAULT) != CUBLAS_STATUS_SUCCESS)
-            return SWJ_ECUDA;
-    }
+    // every T_d^T (np x np, column-major) = B'^T (np x s np) A'^T (s np x np), one call
+    if (cublasGemmBatchedEx(h, CUBLAS_OP_N, CUBLAS_OP_N, np, np, s * np, &one, pA, CUDA_R_16BF, np, pB,
+                            CUDA_R_16BF, s * np, &zero, pC, CUDA_R_32F, np, nall, CUBLAS_COMPUTE_32F,
+                            CUBLAS_GEMM_DEFAULT) != CUBLAS_STATUS_SUCCESS)
+        return SWJ_ECUDA;
     SWJ_COUNT_LAUNCH();
     k_oz_combine<<<dim3(nblk((long)n * n, 256), count), 256, 0, st>>>(n, np, s, beta, prods, P, ea, eb, alpha);
     SWJ_CUDA_TRY(cudaGetLastError());

@@ -408,7 +408,7 @@ OzLayout oz_layout(int n1, int M, int nb, int h)
     }
     L.bytes_desc = oz_align(L.nptr * sizeof(double *)) + oz_align(L.nptr * sizeof(int)) +
                    oz_align(L.nprod * sizeof(OzProd));
-    L.bytes = L.nsa * L.s * n2 * 2 + L.nsb * L.s * n2 * 2 + (L.nsa + L.nsb) * L.np * sizeof(int) +
+    L.bytes = L.nsa * L.s * n2 * 2 + L.nsb * (2 * L.s - 1) * n2 * 2 + (L.nsa + L.nsb) * L.np * sizeof(int) +
               L.maxP * per + 3 * L.maxP * L.s * sizeof(void *) + L.bytes_desc;
     return L;
 }
@@ -494,7 +494,7 @@ int swj_pc_setup(swj_ctx *c)
             void **ozb[] = {&c->oz_sa, &c->oz_sb, (void **)&c->oz_ea, (void **)&c->oz_eb, (void **)&c->oz_P,
                             (void **)&c->oz_ptrs, &c->oz_desc};
             const size_t p2 = (size_t)L.np * L.np;
-            const size_t ozs[] = {L.nsa * L.s * p2 * 2, L.nsb * L.s * p2 * 2, L.nsa * L.np * sizeof(int),
+            const size_t ozs[] = {L.nsa * L.s * p2 * 2, L.nsb * (2 * L.s - 1) * p2 * 2, L.nsa * L.np * sizeof(int),
                                   L.nsb * L.np * sizeof(int), L.maxP * L.s * p2 * sizeof(float),
                                   3 * L.maxP * L.s * sizeof(void *), L.bytes_desc};
             for (int i = 0; i < 7; ++i) {
@@ -505,6 +505,8 @@ int swj_pc_setup(swj_ctx *c)
                 c->pc_bytes += ozs[i];
                 c->bytes += ozs[i];
             }
+            // the B slots' trailing s - 1 slices are zero padding, never written again
+            SWJ_CUDA_TRY(cudaMemsetAsync(c->oz_sb, 0, ozs[1], st));
         }
     }
     c->pc_ready = 0;
