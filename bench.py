@@ -109,15 +109,29 @@ def parse():
     return ap.parse_args()
 
 
-def dist_init(n):
+def dist_init(n, backend="nccl"):
+    """One process per GPU under torchrun (RANK, LOCAL_RANK, WORLD_SIZE and
+    MASTER_* from the environment); (0, 1, None) for a single process."""
     import torch
     if n <= 1 or "RANK" not in os.environ:
         return 0, 1, None
     import torch.distributed as dist
-    local = int(os.environ.get("LOCAL_RANK", 0))
-    torch.cuda.set_device(local)
-    dist.init_process_group("nccl")
+    if backend == "nccl":
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    dist.init_process_group(backend)
     return dist.get_rank(), dist.get_world_size(), dist
+
+
+def replica_rate(total_ms, solves_per_rank, world, dist, device="cuda"):
+    """Whole-job rate of `world` independent replicas (no data-path
+    collective; weak scaling): every rank's solves over the slowest rank's
+    time.  Returns (solves/s, max total ms)."""
+    import torch
+    if dist is not None:
+        t = torch.tensor([float(total_ms)], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return world * solves_per_rank / (total_ms / 1e3), total_ms
 
 
 class ClockSampler:
@@ -272,11 +286,7 @@ def run_ours(args):
     pair64_ms, pair64_n = ctx.pair_timing(swj.FP64)
     ctx.set_kernel_timing(False)
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    value, total_ms = replica_rate(sum(step_ms), args.steps, world, dist)
     ctx.unpack(u, zeta, None)
     ctx.sync()
     zeta_mixed = zeta.cpu().numpy()
@@ -305,6 +315,8 @@ def run_ours(args):
     u_host.copy_(torch.from_numpy(W.flat_state(spec)))
     z_host = torch.empty(spec.N * spec.M, dtype=torch.float64).pin_memory()
     e2e_ms = []
+    if dist:
+        dist.barrier()
     for k in range(args.steps):
         flush.fill_(float(k))
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -317,6 +329,7 @@ def run_ours(args):
         b.record(stream)
         torch.cuda.synchronize()
         e2e_ms.append(a.elapsed_time(b))
+    e2e_value, _ = replica_rate(sum(e2e_ms), args.steps, world, dist)
 
     exact = exact_jvp_section(spec, F, eps, args, stream, flush, zeta_mixed) if rank == 0 else None
 
@@ -328,7 +341,6 @@ def run_ours(args):
     if rank != 0:
         return
     n_solves = world * args.steps
-    value = n_solves / (total_ms / 1e3)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     pairs = spec.pairs
     avg_pair_ms = pair_ms / max(1, pair_n)
@@ -387,7 +399,7 @@ def run_ours(args):
                            "avg_launch_ms": pair64_ms / pair64_n, "launches_timed": pair64_n}
                           if pair64_n else None),
         "cpu_baseline": cpu,
-        "e2e": {"value": n_solves / (sum(e2e_ms) / 1e3) if world == 1 else args.steps / (sum(e2e_ms) / 1e3),
+        "e2e": {"value": e2e_value,
                 "unit": "solves/s", "h2d_bytes_per_step": ctx.n_unknowns * 8,
                 "d2h_bytes_per_step": spec.N * spec.M * 8},
         "gpu_launches": int(launches),
