@@ -114,10 +114,20 @@ typedef struct swj_opts {
                            /* (FP64-accurate: bf16 slices of each factor multiplied   */
                            /* exactly on the tensor cores, Ozaki's splitting, summed */
                            /* in FP64) (SWJ_LU_SLICED)                                */
+    int    lu_order;       /* elimination order of the band LU of a one-instance     */
+                           /* context: SWJ_LU_TOP_DOWN (block rows 0..M-1) or        */
+                           /* SWJ_LU_TWO_SIDED (the top half downwards and the bottom */
+                           /* half upwards at the same time, then the h block rows    */
+                           /* between them: the same factorisation of P up to         */
+                           /* rounding in about half the sequential steps); batched   */
+                           /* contexts always go top-down (SWJ_LU_TWO_SIDED)          */
 } swj_opts;
 
 #define SWJ_LU_FP64   0
 #define SWJ_LU_SLICED 1
+
+#define SWJ_LU_TOP_DOWN  0
+#define SWJ_LU_TWO_SIDED 1
 
 #define SWJ_FORCING_SOURCE   0
 #define SWJ_FORCING_PRESSURE 1

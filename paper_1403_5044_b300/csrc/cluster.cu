@@ -394,13 +394,11 @@ k_gj_pipe(int n, const double *in_base, size_t istride, double *out_base, size_t
 }
 
 // 16 CTAs per cluster where the device runs such clusters (a non-portable
-// size), else the portable 8.
-// (The kernel's dynamic shared-memory limit is raised to `smem` first: the
-// occupancy query fails for a size above the kernel's limit.)
+// size), else the portable 8.  The kernel's dynamic shared-memory limit must
+// already be at least `smem` (the occupancy query fails for a size above it).
 int cluster_ctas(const void *kernel, int threads, size_t smem)
 {
-    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
-        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
         cudaGetLastError();
         return 8;
     }
@@ -438,12 +436,16 @@ static int cluster_for(const void *kern, int threads, size_t smem)
     auto key = std::make_pair(kern, smem);
     auto it = g_cluster_cache.find(key);
     if (it != g_cluster_cache.end()) return it->second;
-    // the limit only grows: a smaller size queried later must not lower it
-    int cs = cluster_ctas(kern, threads, smem);
+    // The limit only grows, and is raised before the query: other host threads
+    // may be launching this kernel with a larger size meanwhile, and a launch
+    // above the kernel's limit at that moment fails.
     size_t &lim = g_smem_limit[kern];
-    if (smem > lim) lim = smem;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim);
-    cudaGetLastError();
+    if (smem > lim) {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess)
+            lim = smem;
+        cudaGetLastError();
+    }
+    int cs = cluster_ctas(kern, threads, smem);
     g_cluster_cache[key] = cs;
     return cs;
 }

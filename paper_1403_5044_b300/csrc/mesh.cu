@@ -13,6 +13,7 @@
 #include "swj_internal.h"
 #include "closed_form.cuh"
 #include <math.h>
+#include <cuda_pipeline.h>
 
 namespace {
 
@@ -62,19 +63,81 @@ __global__ void k_integrate(int N, int M, int H, double x1, double dx,
     }
 }
 
-// Thread per mesh column k (first N threads: zeta, next N: g).  Slopes m_j of
-// the cubic spline through f_0..f_{M-1} (uniform spacing h):
+// Slopes m_j of the cubic spline through f_0..f_{M-1} along y (uniform
+// spacing h), for every mesh column (columns 0..N-1: zeta, N..2N-1: g):
 //   m_0 = 0                                          (even extension at y = 0)
 //   m_{j-1} + 4 m_j + m_{j+1} = 3 (f_{j+1} - f_{j-1}) / h     (C2 continuity)
 //   2 m_{M-2} + m_{M-1} = (d_{M-3} + 5 d_{M-2}) / 2,  d_j = (f_{j+1} - f_j)/h
 // (the last row is the not-a-knot condition at y_{M-2} with m_{M-3}
 // eliminated through the row above it).  cp, a, inv are the forward-sweep
-// coefficients of this fixed matrix.
-__global__ void k_spline(int N, int M, double hy, const double *__restrict__ cp,
-                         const double *__restrict__ a, const double *__restrict__ inv,
-                         const double *__restrict__ zeta, const double *__restrict__ g,
-                         double *__restrict__ zetay, double *__restrict__ gy,
-                         const int *__restrict__ act)
+// coefficients of this fixed matrix (Thomas algorithm).
+//
+// Warp per 32 columns, a column per lane.  The warp first copies its columns
+// into shared memory (all M rows in flight at once: the sweeps are a chain of
+// M dependent steps, which must not also wait on memory), runs the forward
+// sweep there (m'_j overwrites f_j, which the sweep holds in registers by
+// then) and the backward sweep from there, writing each slope to global
+// memory as it is found (coalesced across the warp).
+constexpr int kSplineCols = 32;
+
+__global__ void __launch_bounds__(kSplineCols)
+k_spline(int N, int M, double hy, const double *__restrict__ cp,
+         const double *__restrict__ a, const double *__restrict__ inv,
+         const double *__restrict__ zeta, const double *__restrict__ g,
+         double *__restrict__ zetay, double *__restrict__ gy,
+         const int *__restrict__ act)
+{
+    const int inst = blockIdx.y;
+    if (!SWJ_INST_ACTIVE(act, inst)) return;
+    const size_t off = (size_t)inst * N * M;
+    zeta += off; g += off; zetay += off; gy += off;
+    extern __shared__ double sp[];
+    const int lane = threadIdx.x;
+    const int t = blockIdx.x * kSplineCols + lane;
+    if (t >= 2 * N) return;
+    const int k = t % N;
+    const double *f = (t < N ? zeta : g) + k;
+    double *m = (t < N ? zetay : gy) + k;
+    double *F = sp + lane;                      // row j of this column at F[j * kSplineCols]
+    for (int j = 0; j < M; ++j) __pipeline_memcpy_async(F + j * kSplineCols, f + (size_t)j * N, 8);
+    __pipeline_commit();
+    __pipeline_wait_prior(0);
+    const double rh = 1.0 / hy;
+    // right-hand side of the last row, before the sweep overwrites its inputs
+    const double d3 = (F[(M - 2) * kSplineCols] - F[(M - 3) * kSplineCols]) * rh;
+    const double d2 = (F[(M - 1) * kSplineCols] - F[(M - 2) * kSplineCols]) * rh;
+    const double dlast = 0.5 * (d3 + 5.0 * d2);
+    double dp = 0.0;
+    double fm = F[0], f0 = F[kSplineCols];      // f_{j-1}, f_j
+    for (int j = 1; j < M; ++j) {
+        double d;
+        if (j < M - 1) {
+            const double fp = F[(j + 1) * kSplineCols];
+            d = 3.0 * (fp - fm) * rh;
+            fm = f0;
+            f0 = fp;
+        } else {
+            d = dlast;
+        }
+        dp = (d - __ldg(a + j) * dp) * __ldg(inv + j);
+        F[j * kSplineCols] = dp;
+    }
+    double next = dp;
+    m[(size_t)(M - 1) * N] = next;
+    for (int j = M - 2; j >= 1; --j) {
+        next = F[j * kSplineCols] - __ldg(cp + j) * next;
+        m[(size_t)j * N] = next;
+    }
+    m[0] = 0.0;
+}
+
+// The same slopes, thread per column straight from global memory: for meshes
+// whose columns do not fit in shared memory.
+__global__ void k_spline_global(int N, int M, double hy, const double *__restrict__ cp,
+                                const double *__restrict__ a, const double *__restrict__ inv,
+                                const double *__restrict__ zeta, const double *__restrict__ g,
+                                double *__restrict__ zetay, double *__restrict__ gy,
+                                const int *__restrict__ act)
 {
     const int inst = blockIdx.y;
     if (!SWJ_INST_ACTIVE(act, inst)) return;
@@ -327,6 +390,26 @@ __global__ void k_resample(int Ns, int Ms, int Hs, double x1s, double dxs, doubl
 
 inline int nblk(long n, int b) { return (int)((n + b - 1) / b); }
 
+// Shared memory of k_spline: M rows of kSplineCols columns.  Up to 160 KB
+// (M <= 640) it runs; above, k_spline_global does.
+constexpr size_t kSplineSmemMax = 160 * 1024;
+
+void launch_spline(swj_ctx *c, cudaStream_t st, const double *f1, const double *f2, double *m1, double *m2,
+                   const int *act)
+{
+    const size_t smem = (size_t)c->M * kSplineCols * sizeof(double);
+    if (smem <= kSplineSmemMax) {
+        static const bool attr = cudaFuncSetAttribute(k_spline, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                      (int)kSplineSmemMax) == cudaSuccess;
+        (void)attr;
+        k_spline<<<dim3(nblk(2L * c->N, kSplineCols), c->nb), kSplineCols, smem, st>>>(
+            c->N, c->M, c->mesh.dy, c->spl_cp, c->spl_a, c->spl_inv, f1, f2, m1, m2, act);
+    } else {
+        k_spline_global<<<dim3(nblk(2L * c->N, 128), c->nb), 128, 0, st>>>(
+            c->N, c->M, c->mesh.dy, c->spl_cp, c->spl_a, c->spl_inv, f1, f2, m1, m2, act);
+    }
+}
+
 }  // namespace
 
 void swj_spline_coeffs(int M, double *cp, double *a, double *inv)
@@ -353,9 +436,7 @@ void swj_launch_mesh_step(swj_ctx *c, const double *u, double *E, const int *act
     k_integrate<<<dim3(nblk(2L * c->M * 32, 256), nb), 256, 0, st>>>(c->N, c->M, c->H, m.x1, m.dx, u,
                                                                      c->zeta, c->g, act);
     SWJ_COUNT_LAUNCH();
-    k_spline<<<dim3(nblk(2L * c->N, 128), nb), 128, 0, st>>>(c->N, c->M, m.dy, c->spl_cp, c->spl_a,
-                                                              c->spl_inv, c->zeta, c->g, c->zetay,
-                                                              c->gy, act);
+    launch_spline(c, st, c->zeta, c->g, c->zetay, c->gy, act);
     SWJ_COUNT_LAUNCH();
     k_targets<<<dim3(nblk(c->T, 128), nb), 128, 0, st>>>(c->N, c->M, c->H, m.x1, m.dx, m.dy, c->Fd,
                                                           c->epsd, m.n_rad, c->opts.forcing, u, c->zeta, c->g,
@@ -385,8 +466,7 @@ void swj_launch_mesh_tangent(swj_ctx *c, const double *v, const int *act)
     k_integrate<<<dim3(nblk(2L * c->M * 32, 256), c->nb), 256, 0, st>>>(c->N, c->M, c->H, m.x1, m.dx, v, dz,
                                                                         dg, act, true);
     SWJ_COUNT_LAUNCH();
-    k_spline<<<dim3(nblk(2L * c->N, 128), c->nb), 128, 0, st>>>(c->N, c->M, m.dy, c->spl_cp, c->spl_a,
-                                                                 c->spl_inv, dz, dg, dzy, dgy, act);
+    launch_spline(c, st, dz, dg, dzy, dgy, act);
 }
 
 void swj_launch_flat(swj_ctx *c, double *u)

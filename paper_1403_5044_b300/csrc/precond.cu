@@ -19,12 +19,24 @@
 // diagonal blocks, by the one block G = C A^-1 B.  S is factored by a block
 // LU that keeps the block band (no fill outside it), with partial pivoting
 // inside each diagonal block.  Step i inverts the updated pivot block
-// (inv_i), forms W_ik = inv_i S_ik for the blocks right of it, and updates
-// S_jk -= S_ji W_ik below it.  The blocks S_ji left of the diagonal are kept
-// as they are at their step, so the solve is
-//   forward   y_i = t_i - sum_{j<i} S_ij z_j,  z_i = inv_i y_i
-//   backward  x_i = z_i - sum_{k>i} W_ik x_k
-// (the L factor is S_ij inv_j, never formed).  Everything is FP64.
+// (inv_i), forms W_ik = inv_i S_ik for the blocks right of it, updates
+// S_jk -= S_ji W_ik below it and replaces the blocks left of the diagonal by
+// L_ij = inv_i S_ij, so the solve is
+//   forward   z_i = inv_i t_i - sum_{j<i} L_ij z_j
+//   backward  x_i = z_i - sum_{k>i} W_ik x_k.
+// Everything is FP64.
+//
+// Elimination order.  Top-down, the M steps form a chain (each diagonal block
+// waits for the update from the step before).  A one-instance context
+// instead eliminates the top mt block rows downwards and the bottom mb rows
+// upwards at the same time (mt + mb = M - h, mt - mb = 0 or 1), then the h
+// rows between them: the two halves do not couple (they are h + 1 rows
+// apart), each only updates the separator's blocks, and the separator's
+// Schur complement is D minus both halves' updates.  Both halves run as the
+// two instances of the batched code (the bottom one with its block order
+// reversed, padded to mt rows), so the chain has mt + h steps instead of M.
+// It is the same factorisation of S with the rows taken in another order;
+// the solve visits the halves, then the separator, in that order.
 //
 // Apply, r = P^-1 b, by the three stages of Appendix C:
 //   t2 = b2 - C A^-1 b1;  s2 = S^-1 t2;  r1 = A^-1 b1 - A^-1 B s2;  r2 = s2.
@@ -159,10 +171,50 @@ __global__ void k_diag_corr(int N, int M, int P, double dx, double dy,
     out[t] = 0.5 * s - 0.5 * I;
 }
 
-// D of one instance (the band of the zeta-zeta block of P; it does not depend
-// on F): block (l, m = l - h + slot).
+// Kernel values 1 / sqrt(ddx^2 + ddy^2) of D's entries: row di = i - k + N - 1
+// (ddx = (i - k + 1/2) dx, source column i, target k - 1/2), column dj = |ddy| / dy,
+// for di < 2N - 2, dj < 2M - 1.
+__global__ void k_k3_table(int N, int M, double dx, double dy, double *__restrict__ tab)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nj = 2 * M - 1;
+    if (e >= (2 * N - 2) * nj) return;
+    const int di = e / nj, dj = e % nj;
+    const int i = di, k = N - 1;   // any pair with i - k = di - (N - 1)
+    const double ddx = ((double)i - ((double)(k - 1) + 0.5)) * dx;
+    const double ddy = (double)dj * dy;
+    tab[e] = 1.0 / sqrt(ddx * ddx + ddy * ddy);
+}
+
+// Entry (r, c) of block (l, m) of D, the zeta-zeta block of P (block rows l, m
+// of the mesh; it does not depend on F); tab from k_k3_table.
+__device__ __forceinline__ double d_entry(int N, int M, int l, int m, int r, int c, double x1, double dx,
+                                          double dy, double nrad, const double *__restrict__ diag,
+                                          const double *__restrict__ tab)
+{
+    double v = 0.0;
+    if (r == 0) {                      // E5_l: x1 zeta_x,1 + n zeta_1
+        if (m == l) v = (c == 0) ? nrad : (c == 1 ? x1 : 0.0);
+    } else if (r == 1) {               // E6_l: x1 (zx_2 - zx_1)/dx + n zx_1
+        if (m == l) v = (c == 1) ? nrad - x1 / dx : (c == 2 ? x1 / dx : 0.0);
+    } else if (c >= 1) {               // E2_k,l versus (zeta_x)_{c, m}
+        int k = r - 1, i = c - 1;
+        double ci = (i == 0 || i == N - 1) ? 0.5 : 1.0;
+        double cj = (m == 0 || m == M - 1) ? 0.5 : 1.0;
+        double w = dx * dy * ci * cj;
+        // 1/|x - x'| + 1/|x - x'_image| at ddx = (i - k + 1/2) dx, ddy = (m - l) dy, (m + l) dy
+        const double *trow = tab + (size_t)(i - k + N - 1) * (2 * M - 1);
+        double K3 = trow[m > l ? m - l : l - m] + trow[m + l];
+        v = -w * K3;
+        if (m == l && (c == k || c == k + 1)) v += diag[(size_t)l * (N - 1) + (k - 1)];
+    }
+    return v;
+}
+
+// D of one instance (the band of D): block (l, m = l - h + slot).
 __global__ void k_fill_D(int N, int M, int h, double x1, double dx, double dy, double nrad,
-                         const double *__restrict__ diag, double *__restrict__ band)
+                         const double *__restrict__ diag, const double *__restrict__ tab,
+                         double *__restrict__ band)
 {
     const size_t n1 = N + 1, nb = 2 * h + 1;
     const size_t total = (size_t)M * nb * n1 * n1;
@@ -173,26 +225,133 @@ __global__ void k_fill_D(int N, int M, int h, double x1, double dx, double dy, d
         int slot = (int)((e / (n1 * n1)) % nb);
         int l = (int)(e / (n1 * n1 * nb));
         int m = l - h + slot;
+        band[e] = (m >= 0 && m < M) ? d_entry(N, M, l, m, r, c, x1, dx, dy, nrad, diag, tab) : 0.0;
+    }
+}
+
+// The two band instances of the two-sided order, S = D - G / F^2 on the
+// diagonal blocks: instance 0 row l is block row l (columns below Mv only);
+// instance 1 row l >= dB is block row M - 1 - (l - dB), the block order
+// reversed (its columns likewise), and rows and columns below dB are padding
+// (identity diagonal block, nothing else).
+__global__ void k_fill_S_two_sided(int N, int M, int h, int Mv, int dB, double x1, double dx, double dy,
+                                   double nrad, const double *__restrict__ diag, const double *__restrict__ tab,
+                                   const double *__restrict__ G1, const double *__restrict__ invF2,
+                                   double *__restrict__ band)
+{
+    const size_t n1 = N + 1, nb = 2 * h + 1, n2 = n1 * n1;
+    const size_t total = 2 * (size_t)Mv * nb * n2;
+    const double f = invF2[0];
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e % n1);
+        const int r = (int)((e / n1) % n1);
+        const int slot = (int)((e / n2) % nb);
+        const int l = (int)((e / (n2 * nb)) % Mv);
+        const int inst = (int)(e / (n2 * nb * Mv));
+        const int m = l - h + slot;
         double v = 0.0;
-        if (m >= 0 && m < M) {
-            if (r == 0) {                      // E5_l: x1 zeta_x,1 + n zeta_1
-                if (m == l) v = (c == 0) ? nrad : (c == 1 ? x1 : 0.0);
-            } else if (r == 1) {               // E6_l: x1 (zx_2 - zx_1)/dx + n zx_1
-                if (m == l) v = (c == 1) ? nrad - x1 / dx : (c == 2 ? x1 / dx : 0.0);
-            } else if (c >= 1) {               // E2_k,l versus (zeta_x)_{c, m}
-                int k = r - 1, i = c - 1;
-                double ci = (i == 0 || i == N - 1) ? 0.5 : 1.0;
-                double cj = (m == 0 || m == M - 1) ? 0.5 : 1.0;
-                double w = dx * dy * ci * cj;
-                double ddx = ((double)i - ((double)(k - 1) + 0.5)) * dx;
-                double ddy = (double)(m - l) * dy, ddyp = (double)(m + l) * dy;
-                double K3 = 1.0 / sqrt(ddx * ddx + ddy * ddy) + 1.0 / sqrt(ddx * ddx + ddyp * ddyp);
-                v = -w * K3;
-                if (m == l && (c == k || c == k + 1)) v += diag[(size_t)l * (N - 1) + (k - 1)];
+        if (m >= 0 && m < Mv) {
+            if (inst == 1 && (l < dB || m < dB)) {
+                v = (l == m && r == c) ? 1.0 : 0.0;
+            } else {
+                const int pl = inst == 0 ? l : M - 1 - (l - dB);
+                const int pm = inst == 0 ? m : M - 1 - (m - dB);
+                v = d_entry(N, M, pl, pm, r, c, x1, dx, dy, nrad, diag, tab);
+                if (pl == pm) v -= f * G1[(size_t)r * n1 + c];
             }
         }
         band[e] = v;
     }
+}
+
+// The h x h separator blocks of the two-sided order (block rows and columns
+// Mv-h..Mv-1 of band instance 0, Mv-1..Mv-h of instance 1).  mode 0:
+// sep0 <- instance 0's (D's, before any elimination); mode 1: instance 0's +=
+// instance 1's - sep0, i.e. D minus the Schur updates of both halves.
+__global__ void k_sep_blocks(int n1, int h, int Mv, double *__restrict__ band, size_t bst,
+                             double *__restrict__ sep0, int mode)
+{
+    const size_t n2 = (size_t)n1 * n1, nb = 2 * h + 1;
+    const size_t total = (size_t)h * h * n2;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const size_t rc = e % n2;
+        const int ab = (int)(e / n2), a = ab / h, b = ab % h;
+        double *t = band + ((size_t)(Mv - h + a) * nb + (b - a + h)) * n2 + rc;
+        if (mode == 0) {
+            sep0[e] = *t;
+        } else {
+            const double u = band[bst + ((size_t)(Mv - 1 - a) * nb + (a - b + h)) * n2 + rc];
+            *t = *t + (u - sep0[e]);
+        }
+    }
+}
+
+// Two-sided apply: tv = the right-hand side in the two band instances' row
+// orders (padding rows 0); x = the solution from them.
+__global__ void k_nd_scatter(int n1, int M, int Mv, int dB, const double *__restrict__ t, double *__restrict__ tv)
+{
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t per = (size_t)Mv * n1;
+    if (e >= 2 * per) return;
+    const int inst = (int)(e / per), l = (int)((e % per) / n1), k = (int)(e % n1);
+    tv[e] = inst == 0 ? t[(size_t)l * n1 + k] : (l < dB ? 0.0 : t[(size_t)(M - 1 - (l - dB)) * n1 + k]);
+}
+
+__global__ void k_nd_gather(int n1, int M, int Mv, int dB, const double *__restrict__ xv, double *__restrict__ x)
+{
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (size_t)M * n1) return;
+    const int l = (int)(e / n1), k = (int)(e % n1);
+    x[e] = l < Mv ? xv[(size_t)l * n1 + k] : xv[(size_t)Mv * n1 + (size_t)(M - 1 - l + dB) * n1 + k];
+}
+
+// y_a = sum_j S_{s,j} z_j over the bottom half's block rows j next to separator
+// row s (band instance 1 row Mv-1-a, the blocks left of its diagonal below
+// row Mv-h), a warp per (a, row).
+__global__ void k_sep_y(int n1, int h, int Mv, const double *__restrict__ bandB, const double *__restrict__ zB,
+                        double *__restrict__ y)
+{
+    const int warp = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (warp >= h * n1) return;
+    const size_t n2 = (size_t)n1 * n1, nb = 2 * h + 1;
+    const int a = warp / n1, r = warp % n1, rp = Mv - 1 - a;
+    double s = 0.0;
+    for (int d = h; d >= 1; --d) {
+        const int j = rp - d;
+        if (j < 0 || j >= Mv - h) continue;
+        const double *row = bandB + ((size_t)rp * nb + (h - d)) * n2 + (size_t)r * n1;
+        for (int k = lane; k < n1; k += 32) s = fma(row[k], zB[(size_t)j * n1 + k], s);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) y[(size_t)a * n1 + r] = s;
+}
+
+// p_s -= inv_s y_a for separator row s = Mv-h+a of band instance 0
+__global__ void k_sep_p(int n1, int h, int Mv, const double *__restrict__ bandT, const double *__restrict__ y,
+                        double *__restrict__ pT)
+{
+    const int warp = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (warp >= h * n1) return;
+    const size_t n2 = (size_t)n1 * n1, nb = 2 * h + 1;
+    const int a = warp / n1, r = warp % n1, l = Mv - h + a;
+    const double *row = bandT + ((size_t)l * nb + h) * n2 + (size_t)r * n1;
+    double s = 0.0;
+    for (int k = lane; k < n1; k += 32) s = fma(row[k], y[(size_t)a * n1 + k], s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) pT[(size_t)l * n1 + r] -= s;
+}
+
+// x of the separator rows, from band instance 0 into band instance 1
+__global__ void k_sep_x(int n1, int h, int Mv, double *__restrict__ xv)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= h * n1) return;
+    const int a = e / n1, k = e % n1;
+    xv[(size_t)Mv * n1 + (size_t)(Mv - 1 - a) * n1 + k] = xv[(size_t)(Mv - h + a) * n1 + k];
 }
 
 // dst[b] = src for instances b = 1..nb-1 (src is instance 0's band)
@@ -273,9 +432,10 @@ inline void rowdot(swj_ctx *c, const double *X, size_t xs, const double *Mat, do
 
 inline size_t band_stride(const swj_ctx *c)
 {
-    return (size_t)c->M * c->pc_nb * c->n1 * c->n1;
+    return (size_t)c->pc_M * c->pc_nb * c->n1 * c->n1;
 }
 
+// block (l, m) of band instance inst (rows and columns of that instance)
 inline double *blk(swj_ctx *c, int inst, int l, int m)
 {
     size_t n2 = (size_t)c->n1 * c->n1;
@@ -286,14 +446,15 @@ inline double *blk(swj_ctx *c, int inst, int l, int m)
 inline double *wblk(swj_ctx *c, int inst, int i, int k)
 {
     size_t n2 = (size_t)c->n1 * c->n1;
-    return c->pc_W + ((size_t)inst * c->M * c->pc_h + (size_t)i * c->pc_h + (k - i - 1)) * n2;
+    return c->pc_W + ((size_t)inst * c->pc_M * c->pc_h + (size_t)i * c->pc_h + (k - i - 1)) * n2;
 }
 
 void free_pc(swj_ctx *c)
 {
     double **bufs[] = {&c->pc_Ainv, &c->pc_AinvB1, &c->pc_CAinv, &c->pc_G1, &c->pc_A, &c->pc_B1,
                        &c->pc_C, &c->pc_invF2, &c->pc_band, &c->pc_W, &c->pc_sumK3, &c->pc_t1,
-                       &c->pc_t2, &c->pc_z, &c->pc_work, &c->pc_lt, &c->pc_mc_buf};
+                       &c->pc_t2, &c->pc_z, &c->pc_work, &c->pc_lt, &c->pc_mc_buf, &c->pc_nd_buf,
+                       &c->pc_k3};
     for (double **b : bufs) {
         if (*b) cudaFree(*b);
         *b = nullptr;
@@ -337,36 +498,63 @@ int half_band(int block_bw, int M)
     return h > M - 1 ? M - 1 : h;
 }
 
-// multi-cluster apply scratch (one instance, h >= 2): z [M][n1], then the term
-// slots cf, cb [M][h+1][n1] (0 where it does not apply)
-size_t pc_mc_doubles(int n1, int M, int nb, int h)
+// Layout of the band LU (see swj_ctx::pc_M): half bandwidth h, pc_nv band
+// instances of Mv block rows, the two-sided split.  Step i of the
+// factorisation runs on band instances 0..insts(i)-1.
+struct PcShape {
+    int h, Mv, nv, dB, split;
+    bool nd;
+    int insts(int i) const { return i < split ? nv : 1; }
+};
+
+PcShape pc_shape(int M, int nb, int h, int lu_order)
 {
-    return (nb == 1 && h >= 2) ? (size_t)M * n1 * (1 + 2 * (size_t)(h + 1)) : 0;
+    PcShape s = {h, M, nb, 0, M, false};
+    if (nb == 1 && h >= 1 && lu_order == SWJ_LU_TWO_SIDED && M - h >= 2) {
+        const int mt = (M - h + 1) / 2, mb = M - h - mt;
+        s.nd = true;
+        s.Mv = mt + h;
+        s.nv = 2;
+        s.dB = mt - mb;
+        s.split = mt;
+    }
+    return s;
 }
 
-constexpr int kPcBufs = 17;
+// multi-cluster apply scratch (h >= 2; one instance, or the two band instances of
+// the two-sided order): per band instance z [Mv][n1], then the term slots cf, cb
+// [Mv][h+1][n1] (0 where it does not apply)
+size_t pc_mc_doubles(int n1, const PcShape &sh)
+{
+    return (sh.h >= 2 && (sh.nd || sh.nv == 1)) ? (size_t)sh.nv * sh.Mv * n1 * (1 + 2 * (size_t)(sh.h + 1)) : 0;
+}
+
+constexpr int kPcBufs = 19;
 
 // doubles of each preconditioner buffer, in the order of free_pc's list
 // (0: not allocated)
-void pc_sizes(int n1, int M, int T, int H, int nb, int h, bool gj_inplace, size_t sz[kPcBufs])
+void pc_sizes(int n1, int M, int T, int H, int nb, const PcShape &sh, bool gj_inplace, size_t sz[kPcBufs])
 {
-    const size_t n2 = (size_t)n1 * n1;
-    const size_t work_blocks = gj_inplace ? 1 : (size_t)nb * (h == 0 ? M : 1);
+    const size_t n2 = (size_t)n1 * n1, h = sh.h, Mv = sh.Mv, nv = sh.nv;
+    const size_t work_blocks = gj_inplace ? 1 : nv * (h == 0 ? Mv : 1);
+    const size_t vz = std::max((size_t)nb * H, nv * Mv * n1);
+    const size_t nd = sh.nd ? 2 * nv * Mv * n1 + h * h * n2 + h * n1 : 0;
     const size_t v[kPcBufs] = {n2, n2, n2, n2, n2, n2, n2, (size_t)nb,
-                               (size_t)nb * M * (2 * h + 1) * n2, (size_t)nb * M * (h > 0 ? h : 1) * n2,
-                               (size_t)T, (size_t)nb * H, (size_t)nb * H, (size_t)nb * H, work_blocks * n2,
-                               (size_t)nb * h * n2, pc_mc_doubles(n1, M, nb, h)};
+                               nv * Mv * (2 * h + 1) * n2, nv * Mv * (h > 0 ? h : 1) * n2,
+                               (size_t)T, (size_t)nb * H, (size_t)nb * H, vz, work_blocks * n2,
+                               nv * h * n2, pc_mc_doubles(n1, sh), nd, (size_t)(2 * n1 - 4) * (2 * M - 1)};
     for (int i = 0; i < kPcBufs; ++i) sz[i] = v[i];
 }
 
 // block products of the band LU (pointer triples of the batched GEMMs)
-size_t pc_gemm_count(int M, int nb, int h)
+size_t pc_gemm_count(const PcShape &sh)
 {
+    const int h = sh.h, M = sh.Mv;
     if (h == 0) return 0;
     size_t np = 0;
     for (int i = 0; i < M; ++i) {
         size_t k = (size_t)(i + h < M - 1 ? h : M - 1 - i);
-        np += (size_t)nb * (k + k * k + (size_t)std::min(i, h));
+        np += (size_t)sh.insts(i) * (k + k * k + (size_t)std::min(i, h));
     }
     return np;
 }
@@ -389,9 +577,10 @@ constexpr size_t kOzPBytes = (size_t)256 << 20;   // slice products of one batch
 
 size_t oz_align(size_t b) { return (b + 255) & ~(size_t)255; }
 
-OzLayout oz_layout(int n1, int M, int nb, int h)
+OzLayout oz_layout(int n1, const PcShape &sh)
 {
     OzLayout L = {};
+    const int h = sh.h, M = sh.Mv, nb = sh.nv;
     swj_ozaki_params(n1, &L.np, &L.beta, &L.s);
     const size_t n2 = (size_t)L.np * L.np;
     L.nsa = (size_t)nb * (h + 1);
@@ -403,8 +592,9 @@ OzLayout oz_layout(int n1, int M, int nb, int h)
     L.maxP = cap < most ? cap : most;
     for (int i = 0; i < M; ++i) {
         const size_t kr = (size_t)(i + h < M - 1 ? h : M - 1 - i), nt = (size_t)(i < h ? i : h);
-        L.nptr += (size_t)nb * ((1 + kr) + (kr > 0 ? kr - 1 : 0) + kr + nt);
-        L.nprod += (size_t)nb * ((kr > 0 ? kr - 1 : 0) + (kr > 0 ? kr * kr - 1 : 0) + nt);
+        const size_t q = (size_t)sh.insts(i);
+        L.nptr += q * ((1 + kr) + (kr > 0 ? kr - 1 : 0) + kr + nt);
+        L.nprod += q * ((kr > 0 ? kr - 1 : 0) + (kr > 0 ? kr * kr - 1 : 0) + nt);
     }
     L.bytes_desc = oz_align(L.nptr * sizeof(double *)) + oz_align(L.nptr * sizeof(int)) +
                    oz_align(L.nprod * sizeof(OzProd));
@@ -417,24 +607,25 @@ OzLayout oz_layout(int n1, int M, int nb, int h)
 
 void swj_pc_free(swj_ctx *c) { free_pc(c); }
 
-size_t swj_pc_bytes(int N, int M, int nb, int block_bw, int lu_products)
+size_t swj_pc_bytes(int N, int M, int nb, int block_bw, int lu_products, int lu_order)
 {
-    const int n1 = N + 1, h = half_band(block_bw, M);
+    const int n1 = N + 1;
+    const PcShape sh = pc_shape(M, nb, half_band(block_bw, M), lu_order);
     size_t sz[kPcBufs], tot = 0;
-    pc_sizes(n1, M, (N - 1) * M, n1 * M, nb, h, swj_gj_inplace(n1), sz);
+    pc_sizes(n1, M, (N - 1) * M, n1 * M, nb, sh, swj_gj_inplace(n1), sz);
     for (size_t v : sz) tot += v * sizeof(double);
-    tot += (size_t)nb * M * sizeof(int);
-    tot += 3 * pc_gemm_count(M, nb, h) * sizeof(double *);
-    if (pc_mc_doubles(n1, M, nb, h)) tot += sizeof(int);
-    if (lu_products == SWJ_LU_SLICED && h > 0) tot += oz_layout(n1, M, nb, h).bytes;
+    tot += (size_t)sh.nv * sh.Mv * sizeof(int);
+    tot += 3 * pc_gemm_count(sh) * sizeof(double *);
+    if (pc_mc_doubles(n1, sh)) tot += sizeof(int);
+    if (lu_products == SWJ_LU_SLICED && sh.h > 0) tot += oz_layout(n1, sh).bytes;
     return tot;
 }
 
-// S x = pc_t2 on h clusters into x (one instance): p into pc_z, the scratch
-// and x set to "not yet written", then the sweep
+// S x = pc_t2 on h clusters into x (one instance, top-down order): p into
+// pc_z, the scratch and x set to "not yet written", then the sweep
 static int mc_solve(swj_ctx *c, double *x)
 {
-    const int M = c->M, n1 = c->n1, h = c->pc_h;
+    const int M = c->pc_M, n1 = c->n1, h = c->pc_h;
     const size_t mn = (size_t)M * n1;
     double *z = c->pc_mc_buf, *cf = z + mn, *cb = cf + mn * (h + 1);
     int rc = swj_block_p(c->stream, 1, n1, M, h, c->pc_band, band_stride(c), c->pc_t2, mn, c->pc_z, mn,
@@ -443,28 +634,102 @@ static int mc_solve(swj_ctx *c, double *x)
     return swj_band_sweep_mc(c->stream, n1, M, h, c->pc_band, c->pc_W, c->pc_z, z, x, cf, cb, c->pc_mc_err);
 }
 
+// S x = t for the two-sided order (one instance; t, x [M][n1]), on h clusters
+// per sweep (mc) or one.  With F = Mv - h block rows per half:
+//   1. t in both band instances' row orders, p = inv t for every row of both;
+//   2. the bottom half's forward recurrence (instance 1, rows 0..F-1);
+//   3. each separator row's p loses inv_s sum_j S_sj z_j over the bottom rows
+//      j next to it (those blocks of instance 1, left as they were at the
+//      bottom half's steps);
+//   4. both recurrences of instance 0 (top half, then the separator rows last
+//      forward and first backward);
+//   5. the separator's x into instance 1, the bottom half's backward
+//      recurrence from row F-1 (its rows above are the separator's);
+//   6. x from both instances.
+static int nd_solve(swj_ctx *c, const double *t, double *x, bool mc)
+{
+    const int n1 = c->n1, Mv = c->pc_M, h = c->pc_h, M = c->M, F = Mv - h;
+    const size_t per = (size_t)Mv * n1, n2 = (size_t)n1 * n1, bst = band_stride(c), wst = (size_t)Mv * h * n2;
+    cudaStream_t st = c->stream;
+    double *tv = c->pc_nd_buf, *xv = tv + 2 * per, *y = xv + 2 * per + (size_t)h * h * n2;
+    const double *bandT = c->pc_band, *bandB = c->pc_band + bst, *WT = c->pc_W, *WB = c->pc_W + wst;
+    double *pz = c->pc_z;   // p of both band instances (the one-cluster sweep turns it into z)
+    const int nw = nblk((long)h * n1 * 32, 256);
+    SWJ_COUNT_LAUNCH();
+    k_nd_scatter<<<nblk((long)(2 * per), 256), 256, 0, st>>>(n1, M, Mv, c->pc_dB, t, tv);
+    int rc;
+    if (mc) {
+        const size_t pm = per * (1 + 2 * (size_t)(h + 1));   // z, cf, cb of one band instance
+        double *zT = c->pc_mc_buf, *zB = zT + pm;
+        double *cfT = zT + per, *cbT = cfT + per * (h + 1), *cfB = zB + per, *cbB = cfB + per * (h + 1);
+        if ((rc = swj_block_p(st, 2, n1, Mv, h, c->pc_band, bst, tv, per, pz, per, nullptr, c->pc_mc_buf, 2 * pm,
+                              xv, 2 * per)))
+            return rc;
+        if ((rc = swj_band_sweep_mc(st, n1, Mv, h, bandB, WB, pz + per, zB, xv + per, cfB, cbB, c->pc_mc_err,
+                                    false, F, -1)))
+            return rc;
+        SWJ_COUNT_LAUNCH();
+        k_sep_y<<<nw, 256, 0, st>>>(n1, h, Mv, bandB, zB, y);
+        SWJ_COUNT_LAUNCH();
+        k_sep_p<<<nw, 256, 0, st>>>(n1, h, Mv, bandT, y, pz);
+        if ((rc = swj_band_sweep_mc(st, n1, Mv, h, bandT, WT, pz, zT, xv, cfT, cbT, c->pc_mc_err))) return rc;
+        SWJ_COUNT_LAUNCH();
+        k_sep_x<<<nblk((long)h * n1, 256), 256, 0, st>>>(n1, h, Mv, xv);
+        if ((rc = swj_band_sweep_mc(st, n1, Mv, h, bandB, WB, zB, zB, xv + per, cfB, cbB, c->pc_mc_err, false, 0,
+                                    F - 1)))
+            return rc;
+    } else {
+        if ((rc = swj_block_p(st, 2, n1, Mv, h, c->pc_band, bst, tv, per, pz, per, nullptr))) return rc;
+        if ((rc = swj_band_sweep_cluster(st, 1, n1, Mv, h, bandB, bst, WB, wst, pz + per, per, xv + per, per,
+                                         nullptr, false, F, -1)))
+            return rc;
+        SWJ_COUNT_LAUNCH();
+        k_sep_y<<<nw, 256, 0, st>>>(n1, h, Mv, bandB, pz + per, y);
+        SWJ_COUNT_LAUNCH();
+        k_sep_p<<<nw, 256, 0, st>>>(n1, h, Mv, bandT, y, pz);
+        if ((rc = swj_band_sweep_cluster(st, 1, n1, Mv, h, bandT, bst, WT, wst, pz, per, xv, per, nullptr)))
+            return rc;
+        SWJ_COUNT_LAUNCH();
+        k_sep_x<<<nblk((long)h * n1, 256), 256, 0, st>>>(n1, h, Mv, xv);
+        if ((rc = swj_band_sweep_cluster(st, 1, n1, Mv, h, bandB, bst, WB, wst, pz + per, per, xv + per, per,
+                                         nullptr, false, 0, F - 1)))
+            return rc;
+    }
+    SWJ_COUNT_LAUNCH();
+    k_nd_gather<<<nblk((long)M * n1, 256), 256, 0, st>>>(n1, M, Mv, c->pc_dB, xv, x);
+    SWJ_CUDA_TRY(cudaGetLastError());
+    return SWJ_OK;
+}
+
 int swj_pc_setup(swj_ctx *c)
 {
     const int N = c->N, M = c->M, n1 = c->n1, nb = c->nb;
     const swj_mesh &m = c->mesh;
     cudaStream_t st = c->stream;
     const int h = half_band(c->opts.block_bw, M);
+    const PcShape sh = pc_shape(M, nb, h, c->opts.lu_order);
+    const int Mv = sh.Mv, nv = sh.nv;
     // the band sweep stages h vectors of n1 doubles in shared memory
     if ((size_t)(h + 1) * n1 * sizeof(double) > 200 * 1024) return SWJ_EINVAL;
     const size_t n2 = (size_t)n1 * n1;
     const int nbs = 2 * h + 1;
     const bool gj_inplace = swj_gj_inplace(n1);
     const bool sliced = c->opts.lu_products == SWJ_LU_SLICED && h > 0;
-    if (!c->pc_band || c->pc_h != h || (c->oz_sa != nullptr) != sliced) {
+    if (!c->pc_band || c->pc_h != h || (c->oz_sa != nullptr) != sliced || c->pc_nd != (int)sh.nd) {
         free_pc(c);
         c->pc_h = h;
         c->pc_nb = nbs;
+        c->pc_nd = sh.nd;
+        c->pc_M = Mv;
+        c->pc_nv = nv;
+        c->pc_dB = sh.dB;
+        c->pc_split = sh.split;
         size_t sz[kPcBufs];
-        pc_sizes(n1, M, c->T, c->H, nb, h, gj_inplace, sz);
+        pc_sizes(n1, M, c->T, c->H, nb, sh, gj_inplace, sz);
         double **bufs[] = {&c->pc_Ainv, &c->pc_AinvB1, &c->pc_CAinv, &c->pc_G1, &c->pc_A,
                            &c->pc_B1, &c->pc_C, &c->pc_invF2, &c->pc_band, &c->pc_W,
                            &c->pc_sumK3, &c->pc_t1, &c->pc_t2, &c->pc_z, &c->pc_work,
-                           &c->pc_lt, &c->pc_mc_buf};
+                           &c->pc_lt, &c->pc_mc_buf, &c->pc_nd_buf, &c->pc_k3};
         static_assert(sizeof(bufs) / sizeof(bufs[0]) == kPcBufs, "buffer list");
         for (int i = 0; i < kPcBufs; ++i) {
             if (!sz[i]) continue;
@@ -475,12 +740,12 @@ int swj_pc_setup(swj_ctx *c)
             c->pc_bytes += sz[i] * sizeof(double);
             c->bytes += sz[i] * sizeof(double);
         }
-        if (cudaMalloc(&c->pc_info, (size_t)nb * M * sizeof(int)) != cudaSuccess) {
+        if (cudaMalloc(&c->pc_info, (size_t)nv * Mv * sizeof(int)) != cudaSuccess) {
             free_pc(c);
             return SWJ_ENOMEM;
         }
-        c->pc_bytes += (size_t)nb * M * sizeof(int);
-        c->bytes += (size_t)nb * M * sizeof(int);
+        c->pc_bytes += (size_t)nv * Mv * sizeof(int);
+        c->bytes += (size_t)nv * Mv * sizeof(int);
         if (c->pc_mc_buf) {
             if (cudaMalloc(&c->pc_mc_err, sizeof(int)) != cudaSuccess) {
                 free_pc(c);
@@ -490,7 +755,7 @@ int swj_pc_setup(swj_ctx *c)
             c->bytes += sizeof(int);
         }
         if (sliced) {
-            const OzLayout L = oz_layout(n1, M, nb, h);
+            const OzLayout L = oz_layout(n1, sh);
             void **ozb[] = {&c->oz_sa, &c->oz_sb, (void **)&c->oz_ea, (void **)&c->oz_eb, (void **)&c->oz_P,
                             (void **)&c->oz_ptrs, &c->oz_desc};
             const size_t p2 = (size_t)L.np * L.np;
@@ -551,18 +816,30 @@ int swj_pc_setup(swj_ctx *c)
     k_diag_corr<<<nblk(c->T, 256), 256, 0, st>>>(N, M, pl.P, m.dx, m.dy, c->partial, c->pc_sumK3);
     // --- band of S for every instance: D (shared) minus G / F^2 on the diagonal blocks
     const size_t bst = band_stride(c);
+    double *sep0 = sh.nd ? c->pc_nd_buf + 2 * (size_t)nv * Mv * n1 : nullptr;   // D's separator blocks
     SWJ_COUNT_LAUNCH();
-    k_fill_D<<<4 * c->num_sms, 256, 0, st>>>(N, M, h, m.x1, m.dx, m.dy, m.n_rad, c->pc_sumK3,
-                                             c->pc_band);
-    if (nb > 1) {
+    k_k3_table<<<nblk((long)(2 * N - 2) * (2 * M - 1), 256), 256, 0, st>>>(N, M, m.dx, m.dy, c->pc_k3);
+    if (sh.nd) {
         SWJ_COUNT_LAUNCH();
-        k_replicate<<<dim3(2 * c->num_sms, nb - 1), 256, 0, st>>>(bst, c->pc_band, c->pc_band, bst);
+        k_fill_S_two_sided<<<4 * c->num_sms, 256, 0, st>>>(N, M, h, Mv, sh.dB, m.x1, m.dx, m.dy, m.n_rad,
+                                                            c->pc_sumK3, c->pc_k3, c->pc_G1, c->pc_invF2,
+                                                            c->pc_band);
+        SWJ_COUNT_LAUNCH();
+        k_sep_blocks<<<2 * c->num_sms, 256, 0, st>>>(n1, h, Mv, c->pc_band, bst, sep0, 0);
+    } else {
+        SWJ_COUNT_LAUNCH();
+        k_fill_D<<<4 * c->num_sms, 256, 0, st>>>(N, M, h, m.x1, m.dx, m.dy, m.n_rad, c->pc_sumK3, c->pc_k3,
+                                                 c->pc_band);
+        if (nb > 1) {
+            SWJ_COUNT_LAUNCH();
+            k_replicate<<<dim3(2 * c->num_sms, nb - 1), 256, 0, st>>>(bst, c->pc_band, c->pc_band, bst);
+        }
+        SWJ_COUNT_LAUNCH();
+        k_sub_G<<<dim3(nblk((long)M * n2, 256) < 4096 ? nblk((long)M * n2, 256) : 4096, nb), 256, 0, st>>>(
+            n1, M, h, c->pc_G1, c->pc_invF2, c->pc_band, bst);
     }
-    SWJ_COUNT_LAUNCH();
-    k_sub_G<<<dim3(nblk((long)M * n2, 256) < 4096 ? nblk((long)M * n2, 256) : 4096, nb), 256, 0, st>>>(
-        n1, M, h, c->pc_G1, c->pc_invF2, c->pc_band, bst);
-    // --- block LU of every instance, step by step
-    SWJ_CUDA_TRY(cudaMemsetAsync(c->pc_info, 0, (size_t)nb * M * sizeof(int), st));
+    // --- block LU of every band instance, step by step
+    SWJ_CUDA_TRY(cudaMemsetAsync(c->pc_info, 0, (size_t)nv * Mv * sizeof(int), st));
     int rc;
     if (h == 0) {
         // all M diagonal blocks of all instances are independent
@@ -586,7 +863,7 @@ int swj_pc_setup(swj_ctx *c)
         enum { gWc, gUc, gWb, gB1, gB2, gL, kGroups };
         std::vector<const double *> PA, PB;
         std::vector<double *> PC;
-        std::vector<int> off((size_t)M * kGroups), cnt((size_t)M * kGroups);
+        std::vector<int> off((size_t)Mv * kGroups), cnt((size_t)Mv * kGroups);
         auto begin = [&](int i, int g) { off[(size_t)i * kGroups + g] = (int)PA.size(); };
         auto end = [&](int i, int g) {
             cnt[(size_t)i * kGroups + g] = (int)PA.size() - off[(size_t)i * kGroups + g];
@@ -598,23 +875,23 @@ int swj_pc_setup(swj_ctx *c)
             return (j == i + 1 && k == i + 1) || (j == i + 1 && k == i + 2) || (j == i + 2 && k == i + 1) ||
                    (j == i + 2 && k == i + 2);
         };
-        for (int i = 0; i < M; ++i) {
-            const int kmax = i + h < M - 1 ? i + h : M - 1;
+        for (int i = 0; i < Mv; ++i) {
+            const int kmax = i + h < Mv - 1 ? i + h : Mv - 1;
             begin(i, gWc);
-            for (int q = 0; q < nb; ++q)
+            for (int q = 0; q < sh.insts(i); ++q)
                 if (kmax >= i + 1) add(blk(c, q, i, i), blk(c, q, i, i + 1), wblk(c, q, i, i + 1));
             end(i, gWc);
             begin(i, gUc);
-            for (int q = 0; q < nb; ++q)
+            for (int q = 0; q < sh.insts(i); ++q)
                 if (kmax >= i + 1) add(blk(c, q, i + 1, i), wblk(c, q, i, i + 1), blk(c, q, i + 1, i + 1));
             end(i, gUc);
             begin(i, gWb);
-            for (int q = 0; q < nb; ++q)
+            for (int q = 0; q < sh.insts(i); ++q)
                 for (int k = i + 2; k <= kmax; ++k) add(blk(c, q, i, i), blk(c, q, i, k), wblk(c, q, i, k));
             end(i, gWb);
             for (int g : {gB1, gB2}) {
                 begin(i, g);
-                for (int q = 0; q < nb; ++q)
+                for (int q = 0; q < sh.insts(i); ++q)
                     for (int j = i + 1; j <= kmax; ++j)
                         for (int k = i + 1; k <= kmax; ++k) {
                             if (j == i + 1 && k == i + 1) continue;   // Uc
@@ -625,7 +902,7 @@ int swj_pc_setup(swj_ctx *c)
             }
             const int j0 = std::max(0, i - h);
             begin(i, gL);
-            for (int q = 0; q < nb; ++q)
+            for (int q = 0; q < sh.insts(i); ++q)
                 for (int j = j0; j < i; ++j)
                     add(blk(c, q, i, i), blk(c, q, i, j), c->pc_lt + ((size_t)q * h + (j - j0)) * n2);
             end(i, gL);
@@ -661,45 +938,45 @@ int swj_pc_setup(swj_ctx *c)
             size_t a, wb, u, l, pwb, pb1, pb2, pl;
             int na, nwb, nu, nl, cwb, cb1, cb2, cl;
         };
-        std::vector<OzStep> zo(sliced ? M : 0);
+        std::vector<OzStep> zo(sliced ? Mv : 0);
         OzLayout OL = {};
         const double *const *zP = nullptr;
         const int *zS = nullptr;
         const OzProd *zQ = nullptr;
         if (sliced) {
-            OL = oz_layout(n1, M, nb, h);
+            OL = oz_layout(n1, sh);
             std::vector<const double *> zp;
             std::vector<int> zs;
             std::vector<OzProd> zq;
             const int hs = h + 1, hb = 3 * h;
-            for (int i = 0; i < M; ++i) {
-                const int kmax = i + h < M - 1 ? i + h : M - 1, j0 = std::max(0, i - h);
+            for (int i = 0; i < Mv; ++i) {
+                const int kmax = i + h < Mv - 1 ? i + h : Mv - 1, j0 = std::max(0, i - h);
                 OzStep &o = zo[i];
                 o.a = zp.size();
-                for (int q = 0; q < nb; ++q) {
+                for (int q = 0; q < sh.insts(i); ++q) {
                     zp.push_back(blk(c, q, i, i)); zs.push_back(q * hs);
                     for (int j = i + 1; j <= kmax; ++j) { zp.push_back(blk(c, q, j, i)); zs.push_back(q * hs + (j - i)); }
                 }
                 o.na = (int)(zp.size() - o.a);
                 o.wb = zp.size();
-                for (int q = 0; q < nb; ++q)
+                for (int q = 0; q < sh.insts(i); ++q)
                     for (int k = i + 2; k <= kmax; ++k) { zp.push_back(blk(c, q, i, k)); zs.push_back(q * hb + (k - i - 2)); }
                 o.nwb = (int)(zp.size() - o.wb);
                 o.u = zp.size();
-                for (int q = 0; q < nb; ++q)
+                for (int q = 0; q < sh.insts(i); ++q)
                     for (int k = i + 1; k <= kmax; ++k) { zp.push_back(wblk(c, q, i, k)); zs.push_back(q * hb + h + (k - i - 1)); }
                 o.nu = (int)(zp.size() - o.u);
                 o.l = zp.size();
-                for (int q = 0; q < nb; ++q)
+                for (int q = 0; q < sh.insts(i); ++q)
                     for (int j = j0; j < i; ++j) { zp.push_back(blk(c, q, i, j)); zs.push_back(q * hb + 2 * h + (j - j0)); }
                 o.nl = (int)(zp.size() - o.l);
                 o.pwb = zq.size();
-                for (int q = 0; q < nb; ++q)
+                for (int q = 0; q < sh.insts(i); ++q)
                     for (int k = i + 2; k <= kmax; ++k) zq.push_back({q * hs, q * hb + (k - i - 2), wblk(c, q, i, k), 0});
                 o.cwb = (int)(zq.size() - o.pwb);
                 for (int g = 0; g < 2; ++g) {
                     (g ? o.pb2 : o.pb1) = zq.size();
-                    for (int q = 0; q < nb; ++q)
+                    for (int q = 0; q < sh.insts(i); ++q)
                         for (int j = i + 1; j <= kmax; ++j)
                             for (int k = i + 1; k <= kmax; ++k) {
                                 if (j == i + 1 && k == i + 1) continue;   // the chain's update
@@ -709,7 +986,7 @@ int swj_pc_setup(swj_ctx *c)
                     (g ? o.cb2 : o.cb1) = (int)(zq.size() - (g ? o.pb2 : o.pb1));
                 }
                 o.pl = zq.size();
-                for (int q = 0; q < nb; ++q)
+                for (int q = 0; q < sh.insts(i); ++q)
                     for (int j = j0; j < i; ++j)
                         zq.push_back({q * hs, q * hb + 2 * h + (j - j0), c->pc_lt + ((size_t)q * h + (j - j0)) * n2, 0});
                 o.cl = (int)(zq.size() - o.pl);
@@ -767,17 +1044,22 @@ int swj_pc_setup(swj_ctx *c)
                               (const double *const *)(dB + o), n1, beta, dC + o, n1, n, tile_for(n));
             return SWJ_OK;
         };
+        // steps [i0, i1) of the factorisation on both streams, joined into st at the end
+        auto run_steps = [&](int i0, int i1) -> int {
+        if (i0 >= i1) return SWJ_OK;
+        int rc = SWJ_OK;
         SWJ_CUDA_TRY(cudaEventRecord(evStart, st));
         SWJ_CUDA_TRY(cudaStreamWaitEvent(sc, evStart, 0));
         SWJ_CUDA_TRY(cudaStreamWaitEvent(sb, evStart, 0));
-        for (int i = 0; i < M; ++i) {
+        for (int i = i0; i < i1; ++i) {
             double *diag0 = blk(c, 0, i, i);
+            const int nq = sh.insts(i);
             if (gj_inplace) {
-                rc = swj_gj_inverse_cluster(sc, n1, nb, diag0, bst, diag0, bst, c->pc_info + (size_t)i * nb);
+                rc = swj_gj_inverse_cluster(sc, n1, nq, diag0, bst, diag0, bst, c->pc_info + (size_t)i * nv);
             } else {
                 SWJ_COUNT_LAUNCH();
-                k_copy_blocks<<<dim3(64, nb), 256, 0, sc>>>(n2, diag0, bst, c->pc_work, n2);
-                rc = swj_gj_inverse_cluster(sc, n1, nb, c->pc_work, n2, diag0, bst, c->pc_info + (size_t)i * nb);
+                k_copy_blocks<<<dim3(64, nq), 256, 0, sc>>>(n2, diag0, bst, c->pc_work, n2);
+                rc = swj_gj_inverse_cluster(sc, n1, nq, c->pc_work, n2, diag0, bst, c->pc_info + (size_t)i * nv);
             }
             if (rc) return rc;
             if (i >= 1) SWJ_CUDA_TRY(cudaStreamWaitEvent(sc, evB1[(i - 1) % 4], 0));
@@ -812,7 +1094,7 @@ int swj_pc_setup(swj_ctx *c)
                 if (o.cl) {
                     const int nt = std::min(i, h);
                     SWJ_COUNT_LAUNCH();
-                    k_copy_blocks<<<dim3(64, nb), 256, 0, sb>>>((size_t)nt * n2, c->pc_lt, (size_t)h * n2,
+                    k_copy_blocks<<<dim3(64, nq), 256, 0, sb>>>((size_t)nt * n2, c->pc_lt, (size_t)h * n2,
                                                                 blk(c, 0, i, i - nt), bst);
                 }
                 continue;
@@ -825,7 +1107,7 @@ int swj_pc_setup(swj_ctx *c)
                 if ((rc = gemm(sb, i, gL, 1.0, 0.0))) return rc;
                 const int nt = std::min(i, h);
                 SWJ_COUNT_LAUNCH();
-                k_copy_blocks<<<dim3(64, nb), 256, 0, sb>>>((size_t)nt * n2, c->pc_lt, (size_t)h * n2,
+                k_copy_blocks<<<dim3(64, nq), 256, 0, sb>>>((size_t)nt * n2, c->pc_lt, (size_t)h * n2,
                                                             blk(c, 0, i, i - nt), bst);
             }
         }
@@ -833,8 +1115,20 @@ int swj_pc_setup(swj_ctx *c)
         SWJ_CUDA_TRY(cudaStreamWaitEvent(st, evEnd, 0));
         SWJ_CUDA_TRY(cudaEventRecord(evEnd, sc));
         SWJ_CUDA_TRY(cudaStreamWaitEvent(st, evEnd, 0));
+        return SWJ_OK;
+        };
+        // Two-sided order: both halves first (steps 0..split-1 of both band
+        // instances), then the separator blocks of instance 0 become D minus the
+        // Schur updates of both halves, then instance 0 alone eliminates the
+        // separator rows.  Top-down: split = Mv, one phase.
+        if ((rc = run_steps(0, sh.split))) return rc;
+        if (sh.nd) {
+            SWJ_COUNT_LAUNCH();
+            k_sep_blocks<<<2 * c->num_sms, 256, 0, st>>>(n1, h, Mv, c->pc_band, bst, sep0, 1);
+        }
+        if ((rc = run_steps(sh.split, Mv))) return rc;
     }
-    std::vector<int> info((size_t)nb * M);
+    std::vector<int> info((size_t)nv * Mv);
     SWJ_CUDA_TRY(cudaMemcpyAsync(info.data(), c->pc_info, info.size() * sizeof(int),
                                  cudaMemcpyDeviceToHost, st));
     SWJ_CUDA_TRY(cudaStreamSynchronize(st));
@@ -843,21 +1137,21 @@ int swj_pc_setup(swj_ctx *c)
         if (info[i] < 0) return SWJ_ETIMEOUT;
         else if (info[i] != 0) return SWJ_ESINGULAR;
     if (h > 0) {
-        int rc = swj_band_sweep_cluster(st, nb, n1, M, h, c->pc_band, band_stride(c), c->pc_W,
-                                        (size_t)M * h * n2, c->pc_z, (size_t)c->H, c->pc_t2, (size_t)c->H,
-                                        nullptr, true);
+        int rc = swj_band_sweep_cluster(st, nv, n1, Mv, h, c->pc_band, band_stride(c), c->pc_W,
+                                        (size_t)Mv * h * n2, c->pc_z, (size_t)Mv * n1, c->pc_t2,
+                                        (size_t)Mv * n1, nullptr, true);
         if (rc) return rc;
     }
     // one instance: the multi-cluster apply where the device holds its h
     // clusters, after one trial solve (of t = 0) shows that the launch forms
     // them
     c->pc_mc = 0;
-    if (c->pc_mc_buf && swj_band_sweep_mc(st, n1, M, h, c->pc_band, c->pc_W, nullptr, nullptr, nullptr,
+    if (c->pc_mc_buf && swj_band_sweep_mc(st, n1, Mv, h, c->pc_band, c->pc_W, nullptr, nullptr, nullptr,
                                           nullptr, nullptr, nullptr, true) == SWJ_OK) {
         SWJ_CUDA_TRY(cudaMemsetAsync(c->pc_t2, 0, (size_t)c->H * sizeof(double), st));
         SWJ_CUDA_TRY(cudaMemsetAsync(c->pc_mc_err, 0, sizeof(int), st));
         c->pc_mc = 1;
-        int rc = mc_solve(c, c->pc_t1);
+        int rc = sh.nd ? nd_solve(c, c->pc_t2, c->pc_t1, true) : mc_solve(c, c->pc_t1);
         int err = 1;
         if (rc == SWJ_OK) {
             SWJ_CUDA_TRY(cudaMemcpyAsync(&err, c->pc_mc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -896,10 +1190,14 @@ int swj_pc_apply(swj_ctx *c, const double *b, double *r, const int *act)
     // s2 = S^-1 t2 into r2 (= r + H of every instance)
     int rc = SWJ_EINVAL;
     if (c->pc_mc) {
-        rc = mc_solve(c, r + H);
-        if (rc) c->pc_mc = 0;   // the launch was refused: one cluster from now on
+        rc = c->pc_nd ? nd_solve(c, t2, r + H, true) : mc_solve(c, r + H);
+        if (rc == SWJ_EINVAL) c->pc_mc = 0;   // the launch was refused: one cluster from now on
+        else if (rc) return rc;
     }
-    if (rc) {
+    if (rc && c->pc_nd) {
+        rc = nd_solve(c, t2, r + H, false);
+        if (rc) return rc;
+    } else if (rc) {
         rc = swj_block_p(st, nb, n1, M, h, c->pc_band, band_stride(c), t2, H, h ? c->pc_z : r + H,
                          h ? H : nu, act);
         if (rc) return rc;

@@ -231,12 +231,19 @@ int arnoldi_step(swj_ctx *c, int kind, int j, const double *u, const double *Eba
         }
         int rc = arnoldi_device_step(c, j, u, Ebase, prec);
         cudaError_t e = cudaStreamEndCapture(c->stream, &g);
-        if (rc || e != cudaSuccess || !g) {
+        if (e != cudaSuccess || !g) {
+            // The capture was invalidated, e.g. by a device-wide synchronisation
+            // from another host thread (cudaFree of another context in a
+            // server) while it ran; the errors the step met came from that.
+            // Nothing was executed: run the step now, capture it next time.
             cudaGetLastError();
             if (g) cudaGraphDestroy(g);
-            c->graphs_enabled = 0;
-            if (rc) return rc;
             return arnoldi_device_step(c, j, u, Ebase, prec);
+        }
+        if (rc) {
+            cudaGraphDestroy(g);
+            c->graphs_enabled = 0;
+            return rc;
         }
         if (cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) {
             cudaGetLastError();

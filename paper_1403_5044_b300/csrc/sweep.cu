@@ -193,12 +193,15 @@ k_block_p(int n1, int M, int h, const double *__restrict__ band, size_t bs, cons
 // One cluster per instance runs both recurrences; z holds p on entry and z
 // on exit, x receives the solution.  Each CTA computes a slice of the rows of
 // every block step (a warp per row); the vectors a step reads are staged in
-// shared memory after the cluster barrier that ends the previous step.
+// shared memory after the cluster barrier that ends the previous step.  The
+// forward recurrence runs over block rows 1..F-1 (z_0 = p_0), the backward
+// one from row Bs down to 0; rows of x above Bs are inputs (F = M and
+// Bs = M - 1 for the whole band).
 template <int KC>
 __global__ void __launch_bounds__(kSweepThreads)
 k_band_sweep(int n1, int M, int h, const double *__restrict__ band, size_t band_stride,
              const double *__restrict__ W, size_t w_stride, double *z, size_t zs, double *x, size_t xs,
-             const int *__restrict__ act)
+             const int *__restrict__ act, int F, int Bs)
 {
     cg::cluster_group cl = cg::this_cluster();
     const int ncta = (int)cl.num_blocks();
@@ -215,7 +218,7 @@ k_band_sweep(int n1, int M, int h, const double *__restrict__ band, size_t band_
     const int r0 = min(n1, rank * rows), r1 = min(n1, r0 + rows);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     extern __shared__ double vs[];   // up to h staged vectors of n1
-    for (int i = 1; i < M; ++i) {
+    for (int i = 1; i < F; ++i) {
         const int nt = min(i, h);
         // vs[d - 1] = z_{i-d}
         for (int e = threadIdx.x; e < nt * n1; e += blockDim.x) vs[e] = z[(size_t)(i - 1 - e / n1) * n1 + e % n1];
@@ -228,7 +231,7 @@ k_band_sweep(int n1, int M, int h, const double *__restrict__ band, size_t band_
         }
         cl.sync();
     }
-    for (int i = M - 1; i >= 0; --i) {
+    for (int i = Bs; i >= 0; --i) {
         const int nt = min(M - 1 - i, h);
         // vs[e - 1] = x_{i+e}
         for (int e = threadIdx.x; e < nt * n1; e += blockDim.x) vs[e] = x[(size_t)(i + 1 + e / n1) * n1 + e % n1];
@@ -261,11 +264,14 @@ k_band_sweep(int n1, int M, int h, const double *__restrict__ band, size_t band_
 // cooperative, so all clusters are resident at once; a poll that runs out
 // sets *err = 1 (as does a barrier wait that runs out), and a launch whose
 // clusters are not of cs CTAs, each with one to two rows per warp, sets
-// *err = 2 and returns at once.
+// *err = 2 and returns at once.  As in k_band_sweep, the forward recurrence
+// covers rows 0..F-1 and the backward one rows Bs..0, the rows of x above Bs
+// being inputs (set before the launch); a launch with F = 0 reads z from p.
 template <int KC>
 __global__ void __launch_bounds__(kSweepThreads)
 k_band_sweep_mc(int n1, int M, int h, const double *__restrict__ band, const double *__restrict__ W,
-                const double *__restrict__ p, double *z, double *x, double *cf, double *cb, int cs, int *err)
+                const double *__restrict__ p, double *z, double *x, double *cf, double *cb, int cs, int *err,
+                int F, int Bs)
 {
     cg::cluster_group cl = cg::this_cluster();
     const int ncta = (int)cl.num_blocks();
@@ -361,17 +367,17 @@ k_band_sweep_mc(int n1, int M, int h, const double *__restrict__ band, const dou
         // ---- forward: step i reads L_{i,i-1} from rb[i & 1] and prefetches
         //      L_{i+1,i} into the other buffer
         read_terms(cf, 0, 0, cur[0], cur[1]);
-        for (int i = 0; i < M; ++i) {
+        for (int i = 0; i < F; ++i) {
             const int nd = min(h, i);   // terms c_{i,2..nd}
             __syncthreads();            // every warp is done with step i - 1 (rb, zs)
             if (threadIdx.x == 0) mbar_expect(&mbz[i & 1], n1 * (int)sizeof(double));
-            if (i + 1 < M) prefetch((i + 1) & 1, band + ((size_t)(i + 1) * nbk + (h - 1)) * n2);
+            if (i + 1 < F) prefetch((i + 1) & 1, band + ((size_t)(i + 1) * nbk + (h - 1)) * n2);
             __pipeline_commit();
             __pipeline_wait_prior(1);
             __syncthreads();
             if (i > 0) wait_bar(&mbz[(i - 1) & 1], ((i - 1) >> 1) & 1);
             double nxt[2] = {0.0, 0.0};
-            if (i + 1 < M) read_terms(cf, i + 1, min(h, i + 1), nxt[0], nxt[1]);
+            if (i + 1 < F) read_terms(cf, i + 1, min(h, i + 1), nxt[0], nxt[1]);
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
                 const int rr = warp + q * nw;
@@ -390,12 +396,20 @@ k_band_sweep_mc(int n1, int M, int h, const double *__restrict__ band, const dou
             cur[0] = nxt[0];
             cur[1] = nxt[1];
         }
-        // ---- backward: step t = M - 1 - i reads W_{i,i+1} from rb[t & 1] and
-        //      prefetches W_{i-1,i} into the other buffer
+        // ---- backward: step t = Bs - i reads W_{i,i+1} from rb[t & 1] and
+        //      prefetches W_{i-1,i} into the other buffer.  When the rows above
+        //      Bs are inputs, x_{Bs+1} is staged in vx[1] and W_{Bs,Bs+1} in
+        //      rb[0] before the first step.
         __syncthreads();
-        read_terms(cb, M - 1, 0, cur[0], cur[1]);
-        for (int i = M - 1; i >= 0; --i) {
-            const int t = M - 1 - i;
+        const bool preset = Bs >= 0 && Bs < M - 1;
+        if (preset) {
+            for (int e = threadIdx.x; e < n1; e += blockDim.x) vx[n1 + e] = x[(size_t)(Bs + 1) * n1 + e];
+            prefetch(0, W + ((size_t)Bs * h) * n2);
+            __pipeline_commit();
+        }
+        if (Bs >= 0) read_terms(cb, Bs, min(h, M - 1 - Bs), cur[0], cur[1]);
+        for (int i = Bs; i >= 0; --i) {
+            const int t = Bs - i;
             const int ne = min(h, M - 1 - i);   // terms b_{i,2..ne}
             __syncthreads();
             if (threadIdx.x == 0) mbar_expect(&mbx[t & 1], n1 * (int)sizeof(double));
@@ -412,7 +426,8 @@ k_band_sweep_mc(int n1, int M, int h, const double *__restrict__ band, const dou
                 if (q >= rpw || rr >= nr) break;
                 const int r = r0 + rr;
                 double v = zs[(size_t)i * rows + rr];
-                if (t > 0) v -= block_dot<KC>(rb + ((size_t)(t & 1) * rows + rr) * n1, vx + (size_t)((t - 1) & 1) * n1, n1, lane);
+                if (t > 0 || preset)
+                    v -= block_dot<KC>(rb + ((size_t)(t & 1) * rows + rr) * n1, vx + (size_t)((t - 1) & 1) * n1, n1, lane);
                 if (lane >= 2 && lane <= ne) cur[q] = poll(cb + ((size_t)i * hs + lane) * n1 + r, cur[q]);
                 for (int e = 2; e <= ne; ++e) v -= __shfl_sync(0xffffffffu, cur[q], e);
                 if (lane == 0) st_relaxed(x + (size_t)i * n1 + r, v);
@@ -424,17 +439,17 @@ k_band_sweep_mc(int n1, int M, int h, const double *__restrict__ band, const dou
         __pipeline_wait_prior(0);
         // the last vectors were sent but not read: wait for them, so that no
         // store into this CTA's shared memory is in flight when it exits
-        wait_bar(&mbz[(M - 1) & 1], ((M - 1) >> 1) & 1);
-        wait_bar(&mbx[(M - 1) & 1], ((M - 1) >> 1) & 1);
+        if (F > 0) wait_bar(&mbz[(F - 1) & 1], ((F - 1) >> 1) & 1);
+        if (Bs >= 0) wait_bar(&mbx[Bs & 1], (Bs >> 1) & 1);
         cl.sync();
     } else {
         const int d = cid + 1;   // 2..h
         // forward terms c_{j+d,d} = L_{j+d,j} z_j (slot h - d of block row j + d)
-        if (d < M) prefetch(0, band + ((size_t)d * nbk + (h - d)) * n2);
+        if (d < F) prefetch(0, band + ((size_t)d * nbk + (h - d)) * n2);
         __pipeline_commit();
-        for (int j = 0; j + d < M; ++j) {
+        for (int j = 0; j + d < F; ++j) {
             const int buf = j & 1;
-            if (j + 1 + d < M) prefetch(buf ^ 1, band + ((size_t)(j + 1 + d) * nbk + (h - d)) * n2);
+            if (j + 1 + d < F) prefetch(buf ^ 1, band + ((size_t)(j + 1 + d) * nbk + (h - d)) * n2);
             __pipeline_commit();
             for (int e = threadIdx.x; e < n1; e += blockDim.x) vz[e] = poll(z + (size_t)j * n1 + e, ld_relaxed(z + (size_t)j * n1 + e));
             __pipeline_wait_prior(1);
@@ -447,10 +462,11 @@ k_band_sweep_mc(int n1, int M, int h, const double *__restrict__ band, const dou
         }
         __pipeline_wait_prior(0);
         __syncthreads();
-        // backward terms b_{k-d,d} = W_{k-d,k} x_k, k = M-1 down to d
-        if (M - 1 - d >= 0) prefetch(0, W + ((size_t)(M - 1 - d) * h + (d - 1)) * n2);
+        // backward terms b_{k-d,d} = W_{k-d,k} x_k for the rows k - d <= Bs
+        const int k0 = min(M - 1, Bs + d);
+        if (k0 - d >= 0) prefetch(0, W + ((size_t)(k0 - d) * h + (d - 1)) * n2);
         __pipeline_commit();
-        for (int k = M - 1, t = 0; k - d >= 0; --k, ++t) {
+        for (int k = k0, t = 0; k - d >= 0; --k, ++t) {
             const int buf = t & 1;
             if (k - 1 - d >= 0) prefetch(buf ^ 1, W + ((size_t)(k - 1 - d) * h + (d - 1)) * n2);
             __pipeline_commit();
@@ -481,7 +497,7 @@ size_t mc_smem_bytes(int n1, int M, int cs)
 template <int KC>
 static int launch_sweep(cudaStream_t st, int nb, int n1, int M, int h, const double *band, size_t bs,
                         const double *W, size_t ws, double *z, size_t zs, double *x, size_t xs,
-                        const int *act, bool prepare)
+                        const int *act, bool prepare, int F, int Bs)
 {
     const size_t smem = (size_t)(h > 0 ? h : 1) * n1 * sizeof(double);
     const int cs = swj_cluster_for((const void *)k_band_sweep<KC>, kSweepThreads, smem);
@@ -499,7 +515,7 @@ static int launch_sweep(cudaStream_t st, int nb, int n1, int M, int h, const dou
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     SWJ_COUNT_LAUNCH();
-    SWJ_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_band_sweep<KC>, n1, M, h, band, bs, W, ws, z, zs, x, xs, act));
+    SWJ_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_band_sweep<KC>, n1, M, h, band, bs, W, ws, z, zs, x, xs, act, F, Bs));
     return SWJ_OK;
 }
 
@@ -512,7 +528,7 @@ static std::map<std::tuple<const void *, int, int, int>, std::pair<int, size_t>>
 template <int KC>
 static int launch_sweep_mc(cudaStream_t st, int n1, int M, int h, const double *band, const double *W,
                            const double *p, double *z, double *x, double *cf, double *cb, int *err,
-                           bool prepare)
+                           bool prepare, int F, int Bs)
 {
     const void *kern = (const void *)k_band_sweep_mc<KC>;
     int cs;
@@ -573,10 +589,19 @@ static int launch_sweep_mc(cudaStream_t st, int n1, int M, int h, const double *
     cfg.attrs = attr;
     cfg.numAttrs = 2;
     SWJ_COUNT_LAUNCH();
-    if (cudaLaunchKernelEx(&cfg, k_band_sweep_mc<KC>, n1, M, h, band, W, p, z, x, cf, cb, cs, err) !=
-        cudaSuccess) {
-        cudaGetLastError();   // e.g. no cooperative launch with clusters: the caller falls back
-        return SWJ_EINVAL;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_band_sweep_mc<KC>, n1, M, h, band, W, p, z, x, cf, cb, cs,
+                                             err, F, Bs);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        // a stream capture that another host thread invalidated is not a refusal
+        // of this launch (SWJ_ECUDA: the caller's capture logic retries); any
+        // other error, e.g. no cooperative launch with clusters: the caller falls back
+        const bool capture = e == cudaErrorStreamCaptureUnsupported || e == cudaErrorStreamCaptureInvalidated ||
+                             e == cudaErrorStreamCaptureMerge || e == cudaErrorStreamCaptureUnmatched ||
+                             e == cudaErrorStreamCaptureUnjoined || e == cudaErrorStreamCaptureIsolation ||
+                             e == cudaErrorStreamCaptureImplicit || e == cudaErrorCapturedEvent ||
+                             e == cudaErrorStreamCaptureWrongThread;
+        return capture ? SWJ_ECUDA : SWJ_EINVAL;
     }
     return SWJ_OK;
 }
@@ -617,14 +642,19 @@ int swj_block_p(cudaStream_t st, int nb, int n1, int M, int h, const double *ban
 
 int swj_band_sweep_cluster(cudaStream_t st, int nb, int n1, int M, int h, const double *band, size_t bs,
                            const double *W, size_t ws, double *z, size_t zs, double *x, size_t xs,
-                           const int *act, bool prepare)
+                           const int *act, bool prepare, int F, int Bs)
 {
-    SWJ_KC_DISPATCH((launch_sweep<K>(st, nb, n1, M, h, band, bs, W, ws, z, zs, x, xs, act, prepare)));
+    if (F < 0) F = M;
+    if (Bs < -1 || Bs >= M) Bs = M - 1;
+    SWJ_KC_DISPATCH((launch_sweep<K>(st, nb, n1, M, h, band, bs, W, ws, z, zs, x, xs, act, prepare, F, Bs)));
 }
 
 int swj_band_sweep_mc(cudaStream_t st, int n1, int M, int h, const double *band, const double *W,
-                      const double *p, double *z, double *x, double *cf, double *cb, int *err, bool prepare)
+                      const double *p, double *z, double *x, double *cf, double *cb, int *err, bool prepare,
+                      int F, int Bs)
 {
     if (h < 2 || M < 2) return SWJ_EINVAL;
-    SWJ_KC_DISPATCH((launch_sweep_mc<K>(st, n1, M, h, band, W, p, z, x, cf, cb, err, prepare)));
+    if (F < 0) F = M;
+    if (Bs < -1 || Bs >= M) Bs = M - 1;
+    SWJ_KC_DISPATCH((launch_sweep_mc<K>(st, n1, M, h, band, W, p, z, x, cf, cb, err, prepare, F, Bs)));
 }

@@ -31,6 +31,7 @@ bool valid_opts(const swj_opts *o)
     if (o->jvp != SWJ_JVP_FD && o->jvp != SWJ_JVP_EXACT) return false;
     if (o->forcing != SWJ_FORCING_SOURCE && o->forcing != SWJ_FORCING_PRESSURE) return false;
     if (o->lu_products != SWJ_LU_FP64 && o->lu_products != SWJ_LU_SLICED) return false;
+    if (o->lu_order != SWJ_LU_TOP_DOWN && o->lu_order != SWJ_LU_TWO_SIDED) return false;
     return true;
 }
 
@@ -253,6 +254,7 @@ void swj_default_opts(swj_opts *o)
     o->jvp = SWJ_JVP_FD;
     o->forcing = SWJ_FORCING_SOURCE;
     o->lu_products = SWJ_LU_SLICED;
+    o->lu_order = SWJ_LU_TWO_SIDED;
 }
 
 int swj_create(swj_ctx **out, const swj_mesh *mesh, double F, double eps, const swj_opts *opts,
@@ -330,7 +332,7 @@ int swj_set_opts(swj_ctx *c, const swj_opts *o)
     }
     if (o->fd_h != c->opts.fd_h) swj_graphs_free(c);
     if (o->block_bw != c->opts.block_bw || o->solve_mode != c->opts.solve_mode ||
-        o->lu_products != c->opts.lu_products)
+        o->lu_products != c->opts.lu_products || o->lu_order != c->opts.lu_order)
         c->pc_ready = 0;
     c->opts = *o;
     return SWJ_OK;
@@ -374,7 +376,7 @@ size_t swj_footprint_bytes(const swj_mesh *mesh, int count, const swj_opts *opts
     if (!valid_mesh(mesh) || count < 1 || !valid_opts(&o)) return 0;
     size_t b = 0;
     if (ctx_bytes(mesh, count, o.gmres_restart, &b) != SWJ_OK) return 0;
-    return b + swj_pc_bytes(mesh->N, mesh->M, count, o.block_bw, o.lu_products);
+    return b + swj_pc_bytes(mesh->N, mesh->M, count, o.block_bw, o.lu_products, o.lu_order);
 }
 
 int swj_initial_guess_flat(swj_ctx *c, double *u)

@@ -125,10 +125,20 @@ struct swj_ctx {
     int pc_ready, pc_h, pc_nb;   // built flag, block half bandwidth, blocks per band row
     double *pc_Ainv, *pc_AinvB1, *pc_CAinv, *pc_G1, *pc_A, *pc_B1, *pc_C;   // (n1 x n1), "1" = at F = 1
     double *pc_invF2;            // [nb] 1 / F^2 (scales B, G, A^-1 B)
-    double *pc_band;             // [nb][M][2h+1][n1][n1]
-    double *pc_W;                // [nb][M][h][n1][n1]  W_ik = inv_i S_ik
+    // Block rows of the factors: pc_nv band instances of pc_M block rows.  Top-down
+    // order: pc_nv = nb, pc_M = M.  Two-sided order (pc_nd, one instance, M - h = mt + mb
+    // with mt = mb or mb + 1): band instance 0 holds block rows 0..mt+h-1 (the top half
+    // and the h separator rows), instance 1 holds rows M-1 down to mt (the bottom half
+    // and the separator rows, reversed) after pc_dB = mt - mb padding rows; pc_split = mt
+    // is the first step that instance 0 takes alone (pc_M when top-down).
+    int pc_nd, pc_M, pc_nv, pc_dB, pc_split;
+    double *pc_band;             // [pc_nv][pc_M][2h+1][n1][n1]
+    double *pc_W;                // [pc_nv][pc_M][h][n1][n1]  W_ik = inv_i S_ik
     double *pc_sumK3;            // [T] PreD correction (flat-state sums; F-independent)
-    int *pc_info;                // [nb][M] status of the block inverses
+    int *pc_info;                // [pc_nv][pc_M] status of the block inverses
+    double *pc_k3;               // [2N-2][2M-1] kernel values of D's entries (set-up scratch)
+    double *pc_nd_buf;           // two-sided apply: right-hand sides and solutions [2][pc_M][n1],
+                                 // separator blocks of D [h][h][n1][n1], separator sums [h][n1]
     double **pc_ptrs;            // device pointer arrays for batched block GEMMs
     int pc_ptrs_cap;
     double *pc_t1, *pc_t2, *pc_z;   // apply temporaries [nb][H]
@@ -274,18 +284,23 @@ int swj_block_p(cudaStream_t st, int nb, int n1, int M, int h, const double *ban
                 double *fill1 = nullptr, size_t nfill1 = 0, double *fill2 = nullptr, size_t nfill2 = 0);
 // One cluster per instance: z (p on entry) -> z, then x.  prepare = true only
 // settles the kernel's attributes (no launch); call it once before any launch
-// that may be captured into a graph.
+// that may be captured into a graph.  The forward recurrence covers block rows
+// 0..F-1 and the backward one rows Bs..0 (the rows of x above Bs are inputs);
+// F = -1, Bs = -2: the whole band.
 int swj_band_sweep_cluster(cudaStream_t st, int nb, int n1, int M, int h, const double *band,
                            size_t band_stride, const double *W, size_t w_stride, double *z, size_t zs,
-                           double *x, size_t xs, const int *act, bool prepare = false);
+                           double *x, size_t xs, const int *act, bool prepare = false, int F = -1,
+                           int Bs = -2);
 // One instance on h clusters (a critical one and h - 1 helpers, cooperative
 // launch): p -> z -> x.  z, x and cf, cb ([M][h+1][n1]) must hold the "not yet
-// written" pattern (swj_block_p's fill); err: set to 1 when a poll gave up, 2
-// when the launch did not form clusters of the expected size.  SWJ_EINVAL when
-// h < 2 or the device cannot hold h clusters at once (nothing launched).
+// written" pattern (swj_block_p's fill) where the launch writes them; err: set
+// to 1 when a poll gave up, 2 when the launch did not form clusters of the
+// expected size.  SWJ_EINVAL when h < 2 or the device cannot hold h clusters
+// at once (nothing launched).  F, Bs as for swj_band_sweep_cluster (with F = 0
+// the backward recurrence reads z from p).
 int swj_band_sweep_mc(cudaStream_t st, int n1, int M, int h, const double *band, const double *W,
                       const double *p, double *z, double *x, double *cf, double *cb, int *err,
-                      bool prepare = false);
+                      bool prepare = false, int F = -1, int Bs = -2);
 
 // precond.cu
 int swj_pc_setup(swj_ctx *c);
@@ -293,7 +308,7 @@ int swj_pc_apply(swj_ctx *c, const double *b, double *r, const int *act);
 int swj_pc_status(swj_ctx *c);   // SWJ_ETIMEOUT if a bounded wait of the apply gave up
 void swj_pc_free(swj_ctx *c);
 // device bytes the preconditioner of an nb-instance context holds after set-up
-size_t swj_pc_bytes(int N, int M, int nb, int block_bw, int lu_products);
+size_t swj_pc_bytes(int N, int M, int nb, int block_bw, int lu_products, int lu_order);
 
 // solver.cu
 int swj_residual_impl(swj_ctx *c, const double *u, double *E, int precision, const int *act);

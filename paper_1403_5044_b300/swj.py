@@ -22,6 +22,7 @@ FP64, FP32, FF = 0, 1, 2
 JVP_FD, JVP_EXACT = 0, 1
 FORCING_SOURCE, FORCING_PRESSURE = 0, 1
 LU_FP64, LU_SLICED = 0, 1
+LU_TOP_DOWN, LU_TWO_SIDED = 0, 1
 SOLVE_FP64, SOLVE_MIXED = 0, 1
 
 
@@ -45,7 +46,7 @@ class Opts(ctypes.Structure):
                 ("mixed_tol_inf", ctypes.c_double), ("refine_tol_inf", ctypes.c_double),
                 ("verbose", ctypes.c_int), ("autotune", ctypes.c_int), ("refine_precision", ctypes.c_int),
                 ("jvp", ctypes.c_int), ("forcing", ctypes.c_int),
-                ("lu_products", ctypes.c_int)]
+                ("lu_products", ctypes.c_int), ("lu_order", ctypes.c_int)]
 
 
 class ServerOpts(ctypes.Structure):

@@ -68,7 +68,8 @@ def test_batch_jvp_and_precond_match_single_instances():
         Jb = ctx.view(Jb).cpu().numpy()
         Rb = ctx.view(Rb).cpu().numpy()
     for i in range(len(F)):
-        with swj.Context.from_spec(spec, F[i], eps[i], solve_mode="fp64", block_bw=3) as one:
+        with swj.Context.from_spec(spec, F[i], eps[i], solve_mode="fp64", block_bw=3,
+                                   lu_order=swj.LU_TOP_DOWN) as one:
             u, v = dev(us[i]), dev(vs[i])
             E, J, R = one.vector(), one.vector(), one.vector()
             one.residual(u, E, swj.FP64)

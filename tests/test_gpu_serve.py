@@ -54,7 +54,12 @@ def test_served_mix_equals_each_request_alone():
         assert o["rc"] == swj.OK, (spec, F, eps, o["rc"])
         rc, z = solve_alone(spec, F, eps)
         assert rc == swj.OK
-        assert np.abs(o["zeta"] - z).max() <= 1e-10, (spec.N, F, eps)
+        # a request served in a group of two or more runs in a batched context,
+        # whose band LU goes top-down, and alone two-sided: the same P^-1 up to
+        # rounding, so the two solves stop at different points of the
+        # ||E||_inf < 1e-9 ball around the root
+        tol = 1e-10 if o["group_size"] == 1 else 1e-8
+        assert np.abs(o["zeta"] - z).max() <= tol, (spec.N, F, eps, o["group_size"])
         assert np.abs(o["zeta"]).max() < F ** 2 / 2
 
 

@@ -48,17 +48,21 @@ def test_jvp_matches_oracle_derivative():
                                     (W.MESH_41x21, 5),
                                     (W.MESH_41x21, 11)])
 @pytest.mark.parametrize("lu", [swj.LU_FP64, swj.LU_SLICED])
-def test_precond_apply_matches_linear_jacobian_solve(spec, b, lu):
+@pytest.mark.parametrize("order", [swj.LU_TOP_DOWN, swj.LU_TWO_SIDED])
+def test_precond_apply_matches_linear_jacobian_solve(spec, b, lu, order):
     """r = P^-1 b from the Schur-complement block LU (Appendix C) equals a
     dense solve with the oracle's Appendix B matrix truncated to the same
     block bandwidth, with the band LU's block products in FP64 or from bf16
-    slices on the tensor cores."""
+    slices on the tensor cores, eliminated top-down or from both ends (the
+    9x5 mesh with b = 5 has halves of unequal length, the two-sided b = 3
+    cases run the one-cluster substitution)."""
     F = 0.7
     m = omesh(spec)
     P = O.jacobian_linear(m, F, None if b == 0 else b)
     rhs = np.random.default_rng(b + spec.N).normal(size=m.n_unknowns)
     ref = np.linalg.solve(P, rhs)
-    with swj.Context.from_spec(spec, F, 0.1, solve_mode="fp64", block_bw=b, lu_products=lu) as ctx:
+    with swj.Context.from_spec(spec, F, 0.1, solve_mode="fp64", block_bw=b, lu_products=lu,
+                               lu_order=order) as ctx:
         ctx.precond_setup()
         r = ctx.vector()
         ctx.precond_apply(dev(rhs), r)
@@ -75,10 +79,11 @@ def test_precond_apply_matches_linear_jacobian_solve(spec, b, lu):
 def test_multi_cluster_sweep_equals_one_cluster_sweep(spec, b):
     """A single-instance context spreads the block substitution over h
     clusters; a batch runs it on one cluster per instance.  Both subtract the
-    same block products in the same order, so the applies agree bit for bit."""
+    same block products in the same order, so the applies agree bit for bit
+    (top-down order for both: batches always eliminate top-down)."""
     F = 0.75
     rhs = np.random.default_rng(spec.N + b).normal(size=spec.n_unknowns)
-    with swj.Context.from_spec(spec, F, 0.2, solve_mode="fp64", block_bw=b) as one:
+    with swj.Context.from_spec(spec, F, 0.2, solve_mode="fp64", block_bw=b, lu_order=swj.LU_TOP_DOWN) as one:
         one.precond_setup()
         h = one.sweep_clusters()
         r1 = one.vector()
@@ -106,7 +111,8 @@ def test_sliced_lu_products_agree_with_fp64_and_do_not_depend_on_the_batch(spec,
     rhs = np.random.default_rng(spec.N + b + 1).normal(size=spec.n_unknowns)
     out = {}
     for lu in (swj.LU_FP64, swj.LU_SLICED):
-        with swj.Context.from_spec(spec, F, 0.2, solve_mode="fp64", block_bw=b, lu_products=lu) as one:
+        with swj.Context.from_spec(spec, F, 0.2, solve_mode="fp64", block_bw=b, lu_products=lu,
+                                   lu_order=swj.LU_TOP_DOWN) as one:
             r = one.vector()
             one.precond_apply(dev(rhs), r)
             one.sync()
@@ -120,6 +126,28 @@ def test_sliced_lu_products_agree_with_fp64_and_do_not_depend_on_the_batch(spec,
         two.sync()
         rb = two.view(rb).cpu().numpy()
     assert np.array_equal(rb[0], out[swj.LU_SLICED]) and np.array_equal(rb[1], out[swj.LU_SLICED])
+
+
+@pytest.mark.parametrize("spec,b", [(W.MESH_41x21, 11), (W.SERVE_MESHES[1], 11), (W.SOLVE_181x61[0], 11),
+                                    (W.SOLVE_181x61[0], 9), (W.SERVE_MESHES[3], 15)])
+def test_two_sided_factorisation_equals_top_down(spec, b):
+    """Eliminating the two halves of the band from both ends and the h block
+    rows between them last factors the same matrix: the applies agree with the
+    top-down factorisation to rounding (amplified by the conditioning of S),
+    and the two-sided substitution runs on the h clusters of the single-
+    instance sweep.  (181x61 with b = 9 has halves of unequal length.)"""
+    F = 0.75
+    rhs = np.random.default_rng(spec.N + b + 2).normal(size=spec.n_unknowns)
+    out = {}
+    for order in (swj.LU_TOP_DOWN, swj.LU_TWO_SIDED):
+        with swj.Context.from_spec(spec, F, 0.2, solve_mode="fp64", block_bw=b, lu_order=order) as one:
+            r = one.vector()
+            one.precond_apply(dev(rhs), r)
+            one.sync()
+            assert one.sweep_clusters() == (b - 1) // 2
+            out[order] = r.cpu().numpy()
+    ref = out[swj.LU_TOP_DOWN]
+    assert np.abs(out[swj.LU_TWO_SIDED] - ref).max() <= 1e-10 * np.abs(ref).max()
 
 
 def gpu_solve(spec, F, eps, **kw):
