@@ -65,7 +65,7 @@ PROFILED_TRAFFIC = {
     "k_pairs_x2r<2,256,3,1,1>": 717751,
     "k_pairs_x2r<3,128,2,1,1>": 723639,
 }
-BLOCK_BW = 11          # block bandwidth of the mixed solves (fastest measured at 181x61)
+BLOCK_BW = 15          # block bandwidth of the mixed solves (fastest measured at 181x61)
 FP64_BLOCK_BW = 15     # the FP64 solve's own fastest block bandwidth
 
 

@@ -79,7 +79,7 @@ typedef struct swj_opts {
     int    solve_mode;     /* SWJ_SOLVE_FP64 | SWJ_SOLVE_MIXED (MIXED)               */
     int    block_bw;       /* preconditioner block bandwidth b: odd >= 1, 0 for the  */
                            /* untruncated linear Jacobian (Section 4.2), or -1: by  */
-                           /* mesh, 11 for M <= 64 block rows, else 15 (-1)         */
+                           /* mesh, 11 for M <= 48 block rows, else 15 (-1)         */
     int    gmres_restart;  /* GMRES restart length m (30)                            */
     int    max_newton;     /* Newton iteration cap (60)                              */
     int    max_krylov;     /* GMRES iterations per Newton step (300)                 */

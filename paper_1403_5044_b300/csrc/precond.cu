@@ -489,11 +489,11 @@ void free_pc(swj_ctx *c)
 }
 
 // block half bandwidth of the option block_bw (0 = the whole matrix, -1 = by
-// mesh: b = 11 up to 64 block rows, 15 above, the fastest set-up + solve
+// mesh: b = 11 up to 48 block rows, 15 above, the fastest set-up + solve
 // measured on the 61x21, 121x41, 181x61 and 361x121 meshes)
 int half_band(int block_bw, int M)
 {
-    if (block_bw < 0) block_bw = (M <= 64) ? 11 : 15;
+    if (block_bw < 0) block_bw = (M <= 48) ? 11 : 15;
     int h = (block_bw == 0) ? M - 1 : (block_bw - 1) / 2;
     return h > M - 1 ? M - 1 : h;
 }
@@ -634,63 +634,85 @@ static int mc_solve(swj_ctx *c, double *x)
     return swj_band_sweep_mc(c->stream, n1, M, h, c->pc_band, c->pc_W, c->pc_z, z, x, cf, cb, c->pc_mc_err);
 }
 
-// S x = t for the two-sided order (one instance; t, x [M][n1]), on h clusters
-// per sweep (mc) or one.  With F = Mv - h block rows per half:
+// S x = t for the two-sided order (one instance; t, x [M][n1]).  With
+// F = Mv - h block rows per half:
 //   1. t in both band instances' row orders, p = inv t for every row of both;
-//   2. the bottom half's forward recurrence (instance 1, rows 0..F-1);
+//   2. the forward recurrence of both halves (rows 0..F-1 of both instances);
 //   3. each separator row's p loses inv_s sum_j S_sj z_j over the bottom rows
 //      j next to it (those blocks of instance 1, left as they were at the
 //      bottom half's steps);
-//   4. both recurrences of instance 0 (top half, then the separator rows last
-//      forward and first backward);
-//   5. the separator's x into instance 1, the bottom half's backward
-//      recurrence from row F-1 (its rows above are the separator's);
+//   4. the separator rows of instance 0: forward, then backward;
+//   5. the separator's x into instance 1, the backward recurrence of both
+//      halves (rows F-1..0 of both instances, the rows above given);
 //   6. x from both instances.
-static int nd_solve(swj_ctx *c, const double *t, double *x, bool mc)
+// mode 2: steps 2 and 5 each one multi-cluster launch for both instances (a
+// critical cluster each, shared helpers); mode 1: multi-cluster launches for
+// one instance at a time (bottom forward, the whole of instance 0, bottom
+// backward); mode 0: the same order with one cluster per launch.
+static int nd_solve(swj_ctx *c, const double *t, double *x, int mode)
 {
     const int n1 = c->n1, Mv = c->pc_M, h = c->pc_h, M = c->M, F = Mv - h;
     const size_t per = (size_t)Mv * n1, n2 = (size_t)n1 * n1, bst = band_stride(c), wst = (size_t)Mv * h * n2;
+    const size_t sst = per * (h + 1);   // term slots of one band instance
     cudaStream_t st = c->stream;
     double *tv = c->pc_nd_buf, *xv = tv + 2 * per, *y = xv + 2 * per + (size_t)h * h * n2;
     const double *bandT = c->pc_band, *bandB = c->pc_band + bst, *WT = c->pc_W, *WB = c->pc_W + wst;
     double *pz = c->pc_z;   // p of both band instances (the one-cluster sweep turns it into z)
     const int nw = nblk((long)h * n1 * 32, 256);
+    int *err = c->pc_mc_err;
     SWJ_COUNT_LAUNCH();
     k_nd_scatter<<<nblk((long)(2 * per), 256), 256, 0, st>>>(n1, M, Mv, c->pc_dB, t, tv);
     int rc;
-    if (mc) {
-        const size_t pm = per * (1 + 2 * (size_t)(h + 1));   // z, cf, cb of one band instance
-        double *zT = c->pc_mc_buf, *zB = zT + pm;
-        double *cfT = zT + per, *cbT = cfT + per * (h + 1), *cfB = zB + per, *cbB = cfB + per * (h + 1);
-        if ((rc = swj_block_p(st, 2, n1, Mv, h, c->pc_band, bst, tv, per, pz, per, nullptr, c->pc_mc_buf, 2 * pm,
-                              xv, 2 * per)))
-            return rc;
-        if ((rc = swj_band_sweep_mc(st, n1, Mv, h, bandB, WB, pz + per, zB, xv + per, cfB, cbB, c->pc_mc_err,
-                                    false, F, -1)))
-            return rc;
+    auto sep_p = [&](const double *zB) {
         SWJ_COUNT_LAUNCH();
         k_sep_y<<<nw, 256, 0, st>>>(n1, h, Mv, bandB, zB, y);
         SWJ_COUNT_LAUNCH();
         k_sep_p<<<nw, 256, 0, st>>>(n1, h, Mv, bandT, y, pz);
-        if ((rc = swj_band_sweep_mc(st, n1, Mv, h, bandT, WT, pz, zT, xv, cfT, cbT, c->pc_mc_err))) return rc;
+    };
+    auto sep_x = [&]() {
         SWJ_COUNT_LAUNCH();
         k_sep_x<<<nblk((long)h * n1, 256), 256, 0, st>>>(n1, h, Mv, xv);
-        if ((rc = swj_band_sweep_mc(st, n1, Mv, h, bandB, WB, zB, zB, xv + per, cfB, cbB, c->pc_mc_err, false, 0,
-                                    F - 1)))
+    };
+    if (mode > 0) {
+        // multi-cluster scratch: z of both instances, then cf of both, then cb of both
+        double *zv = c->pc_mc_buf, *cf = zv + 2 * per, *cb = cf + 2 * sst;
+        if ((rc = swj_block_p(st, 2, n1, Mv, h, c->pc_band, bst, tv, per, pz, per, nullptr, c->pc_mc_buf,
+                              2 * (per + 2 * sst), xv, 2 * per)))
             return rc;
+        if (mode == 2) {
+            if ((rc = swj_band_sweep_mc_ranges(st, n1, Mv, h, 2, c->pc_band, bst, c->pc_W, wst, pz, zv, xv, per, cf,
+                                               cb, sst, err, false, 0, F, -1, 0)))
+                return rc;
+            sep_p(zv + per);
+            if ((rc = swj_band_sweep_mc_ranges(st, n1, Mv, h, 1, bandT, 0, WT, 0, pz, zv, xv, 0, cf, cb, 0, err,
+                                               false, F, Mv, Mv - 1, F)))
+                return rc;
+            sep_x();
+            if ((rc = swj_band_sweep_mc_ranges(st, n1, Mv, h, 2, c->pc_band, bst, c->pc_W, wst, zv, zv, xv, per, cf,
+                                               cb, sst, err, false, 0, 0, F - 1, 0)))
+                return rc;
+        } else {
+            if ((rc = swj_band_sweep_mc_ranges(st, n1, Mv, h, 1, bandB, 0, WB, 0, pz + per, zv + per, xv + per, 0,
+                                               cf + sst, cb + sst, 0, err, false, 0, F, -1, 0)))
+                return rc;
+            sep_p(zv + per);
+            if ((rc = swj_band_sweep_mc_ranges(st, n1, Mv, h, 1, bandT, 0, WT, 0, pz, zv, xv, 0, cf, cb, 0, err,
+                                               false, 0, Mv, Mv - 1, 0)))
+                return rc;
+            sep_x();
+            if ((rc = swj_band_sweep_mc_ranges(st, n1, Mv, h, 1, bandB, 0, WB, 0, zv + per, zv + per, xv + per, 0,
+                                               cf + sst, cb + sst, 0, err, false, 0, 0, F - 1, 0)))
+                return rc;
+        }
     } else {
         if ((rc = swj_block_p(st, 2, n1, Mv, h, c->pc_band, bst, tv, per, pz, per, nullptr))) return rc;
         if ((rc = swj_band_sweep_cluster(st, 1, n1, Mv, h, bandB, bst, WB, wst, pz + per, per, xv + per, per,
                                          nullptr, false, F, -1)))
             return rc;
-        SWJ_COUNT_LAUNCH();
-        k_sep_y<<<nw, 256, 0, st>>>(n1, h, Mv, bandB, pz + per, y);
-        SWJ_COUNT_LAUNCH();
-        k_sep_p<<<nw, 256, 0, st>>>(n1, h, Mv, bandT, y, pz);
+        sep_p(pz + per);
         if ((rc = swj_band_sweep_cluster(st, 1, n1, Mv, h, bandT, bst, WT, wst, pz, per, xv, per, nullptr)))
             return rc;
-        SWJ_COUNT_LAUNCH();
-        k_sep_x<<<nblk((long)h * n1, 256), 256, 0, st>>>(n1, h, Mv, xv);
+        sep_x();
         if ((rc = swj_band_sweep_cluster(st, 1, n1, Mv, h, bandB, bst, WB, wst, pz + per, per, xv + per, per,
                                          nullptr, false, 0, F - 1)))
             return rc;
@@ -1145,19 +1167,26 @@ int swj_pc_setup(swj_ctx *c)
     // one instance: the multi-cluster apply where the device holds its h
     // clusters, after one trial solve (of t = 0) shows that the launch forms
     // them
+    //  (two-sided order: both halves at once where ni + h - 1 = h + 1 clusters fit,
+    //  else one half at a time)
     c->pc_mc = 0;
     if (c->pc_mc_buf && swj_band_sweep_mc(st, n1, Mv, h, c->pc_band, c->pc_W, nullptr, nullptr, nullptr,
                                           nullptr, nullptr, nullptr, true) == SWJ_OK) {
-        SWJ_CUDA_TRY(cudaMemsetAsync(c->pc_t2, 0, (size_t)c->H * sizeof(double), st));
-        SWJ_CUDA_TRY(cudaMemsetAsync(c->pc_mc_err, 0, sizeof(int), st));
-        c->pc_mc = 1;
-        int rc = sh.nd ? nd_solve(c, c->pc_t2, c->pc_t1, true) : mc_solve(c, c->pc_t1);
-        int err = 1;
-        if (rc == SWJ_OK) {
-            SWJ_CUDA_TRY(cudaMemcpyAsync(&err, c->pc_mc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
-            SWJ_CUDA_TRY(cudaStreamSynchronize(st));
+        int best = 1;
+        if (sh.nd && swj_band_sweep_mc_ranges(st, n1, Mv, h, 2, nullptr, 0, nullptr, 0, nullptr, nullptr, nullptr,
+                                              0, nullptr, nullptr, 0, nullptr, true, 0, 0, -1, 0) == SWJ_OK)
+            best = 2;
+        for (int mode = best; mode >= 1 && !c->pc_mc; --mode) {
+            SWJ_CUDA_TRY(cudaMemsetAsync(c->pc_t2, 0, (size_t)c->H * sizeof(double), st));
+            SWJ_CUDA_TRY(cudaMemsetAsync(c->pc_mc_err, 0, sizeof(int), st));
+            int rc = sh.nd ? nd_solve(c, c->pc_t2, c->pc_t1, mode) : mc_solve(c, c->pc_t1);
+            int err = 1;
+            if (rc == SWJ_OK) {
+                SWJ_CUDA_TRY(cudaMemcpyAsync(&err, c->pc_mc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+                SWJ_CUDA_TRY(cudaStreamSynchronize(st));
+            }
+            if (rc == SWJ_OK && err == 0) c->pc_mc = mode;
         }
-        c->pc_mc = (rc == SWJ_OK && err == 0);
         SWJ_CUDA_TRY(cudaMemsetAsync(c->pc_mc_err, 0, sizeof(int), st));
     }
     c->pc_ready = 1;
@@ -1190,12 +1219,12 @@ int swj_pc_apply(swj_ctx *c, const double *b, double *r, const int *act)
     // s2 = S^-1 t2 into r2 (= r + H of every instance)
     int rc = SWJ_EINVAL;
     if (c->pc_mc) {
-        rc = c->pc_nd ? nd_solve(c, t2, r + H, true) : mc_solve(c, r + H);
+        rc = c->pc_nd ? nd_solve(c, t2, r + H, c->pc_mc) : mc_solve(c, r + H);
         if (rc == SWJ_EINVAL) c->pc_mc = 0;   // the launch was refused: one cluster from now on
         else if (rc) return rc;
     }
     if (rc && c->pc_nd) {
-        rc = nd_solve(c, t2, r + H, false);
+        rc = nd_solve(c, t2, r + H, 0);
         if (rc) return rc;
     } else if (rc) {
         rc = swj_block_p(st, nb, n1, M, h, c->pc_band, band_stride(c), t2, H, h ? c->pc_z : r + H,

@@ -245,37 +245,43 @@ k_band_sweep(int n1, int M, int h, const double *__restrict__ band, size_t band_
     }
 }
 
-// The same recurrences for one instance on h clusters.  Cluster 0 (critical)
-// keeps only the product with the block next to the diagonal:
+// The same recurrences for ni instances (1 or 2) on ni + hsets (h - 1)
+// clusters.  Cluster q < ni (critical for instance q) keeps only the product
+// with the block next to the diagonal:
 //   forward   z_i = p_i - L_{i,i-1} z_{i-1} - sum_{d>=2} c_{i,d}
 //   backward  x_i = z_i - W_{i,i+1} x_{i+1} - sum_{e>=2} b_{i,e}
-// and cluster d-1 (d = 2..h) computes the older terms as soon as their
-// vector exists: c_{j+d,d} = L_{j+d,j} z_j and b_{k-d,d} = W_{k-d,k} x_k.
-// Nothing is signalled apart from the values themselves: z, x and the term
-// slots cf, cb ([M][h+1][n1], slots 2..h used) are set to kUnset before the
-// launch, producers store each value once (relaxed, 8 bytes, single-copy
-// atomic) and consumers poll it until it is set.  In cluster 0 each CTA owns
-// a slice of rows (at least one), takes the next step's block rows into
-// shared memory with cp.async while the current step runs, keeps p and then
-// its z rows in shared memory, reads the helpers' terms one step ahead, and
-// sends every new element of z_i / x_i into the shared memory of all CTAs of
-// the cluster by st.async, whose arrival each CTA awaits on an mbarrier (no
-// cluster barrier per step).  The helpers are independent CTAs.  The launch is
-// cooperative, so all clusters are resident at once; a poll that runs out
-// sets *err = 1 (as does a barrier wait that runs out), and a launch whose
-// clusters are not of cs CTAs, each with one to two rows per warp, sets
-// *err = 2 and returns at once.  As in k_band_sweep, the forward recurrence
-// covers rows 0..F-1 and the backward one rows Bs..0, the rows of x above Bs
-// being inputs (set before the launch); a launch with F = 0 reads z from p.
+// and the helper clusters compute the older terms as soon as their vector
+// exists: c_{j+d,d} = L_{j+d,j} z_j and b_{k-d,d} = W_{k-d,k} x_k, one helper
+// per d = 2..h for every instance (hsets = 1) or for each instance (hsets =
+// ni).  Nothing is signalled apart from the values
+// themselves: z, x and the term slots cf, cb ([M][h+1][n1], slots 2..h used)
+// are set to kUnset before the launch where it writes them, producers store
+// each value once (relaxed, 8 bytes, single-copy atomic) and consumers poll it
+// until it is set.  In a critical cluster each CTA owns a slice of rows (at
+// least one), takes the next step's block rows into shared memory with
+// cp.async while the current step runs, keeps p and then its z rows in shared
+// memory, reads the helpers' terms one step ahead, and sends every new
+// element of z_i / x_i into the shared memory of all CTAs of the cluster by
+// st.async, whose arrival each CTA awaits on an mbarrier (no cluster barrier
+// per step).  The helpers are independent CTAs.  The launch is cooperative,
+// so all clusters are resident at once; a poll that runs out sets *err = 1
+// (as does a barrier wait that runs out), and a launch whose clusters are not
+// of cs CTAs, each with one to two rows per warp, sets *err = 2 and returns
+// at once.  The forward recurrence covers rows F0..F1-1 and the backward one
+// rows B1 down to B0; the rows of z below F0 and of x above B1 are inputs
+// (set before the launch), and zs starts from p (pass z as p for a launch
+// without forward rows).  Instance q's band, W, vectors and term slots are at
+// q bst, q wst, q vst, q sst.
 template <int KC>
 __global__ void __launch_bounds__(kSweepThreads)
-k_band_sweep_mc(int n1, int M, int h, const double *__restrict__ band, const double *__restrict__ W,
-                const double *__restrict__ p, double *z, double *x, double *cf, double *cb, int cs, int *err,
-                int F, int Bs)
+k_band_sweep_mc(int n1, int M, int h, int ni, int hsets, const double *__restrict__ band, size_t bst,
+                const double *__restrict__ W, size_t wst, const double *__restrict__ p, double *z, double *x,
+                size_t vst, double *cf, double *cb, size_t sst, int cs, int *err, int F0, int F1, int B1,
+                int B0)
 {
     cg::cluster_group cl = cg::this_cluster();
     const int ncta = (int)cl.num_blocks();
-    if (ncta != cs || (int)gridDim.x != cs * h || (cs - 1) * ((n1 + cs - 1) / cs) >= n1 ||
+    if (ncta != cs || (int)gridDim.x != cs * (ni + hsets * (h - 1)) || (cs - 1) * ((n1 + cs - 1) / cs) >= n1 ||
         (n1 + cs - 1) / cs > 2 * (kSweepThreads / 32)) {   // the same decision in every CTA
         if (threadIdx.x == 0) atomicExch(err, 2);
         return;
@@ -320,15 +326,26 @@ k_band_sweep_mc(int n1, int M, int h, const double *__restrict__ band, const dou
         }
         return v;
     };
-    if (cid == 0) {
+    if (cid < ni) {
+        // critical cluster of instance cid
+        band += (size_t)cid * bst;
+        W += (size_t)cid * wst;
+        p += (size_t)cid * vst;
+        z += (size_t)cid * vst;
+        x += (size_t)cid * vst;
+        cf += (size_t)cid * sst;
+        cb += (size_t)cid * sst;
         // Exchange inside the cluster: element r of z_i (x_i) goes from the CTA
-        // that owns row r to vz[i & 1][r] (vx[t & 1][r], t = M - 1 - i) of every
-        // CTA by st.async, which completes mbz[i & 1] (mbx[t & 1]) there; each
-        // CTA arms that barrier for n1 * 8 bytes at the start of the step and
-        // waits on it (the use count >> 1 gives the phase) before reading the
-        // vector.  A buffer is rewritten two steps later, only after every CTA
-        // produced its rows of the step in between, i.e. after every reader
-        // of the buffer has finished with it.
+        // that owns row r to vz[t & 1][r] (vx[t & 1][r]) of every CTA, t the
+        // step's index in its recurrence (i - F0, B1 - i), by st.async, which
+        // completes mbz[t & 1] (mbx[t & 1]) there; each CTA arms that barrier
+        // for n1 * 8 bytes at the start of the step and waits on it (the use
+        // count >> 1 gives the phase) before reading the vector.  A buffer is
+        // rewritten two steps later, only after every CTA produced its rows of
+        // the step in between, i.e. after every reader of the buffer has
+        // finished with it.  An input vector next to the first step (z_{F0-1},
+        // x_{B1+1}) is staged in buffer 1 directly, with the first step's
+        // block rows in rb[0].
         const int rpw = (nr + nw - 1) / nw;   // rows per warp (<= 2, checked at launch)
         if (threadIdx.x == 0) {
             for (int q = 0; q < 2; ++q) {
@@ -364,69 +381,75 @@ k_band_sweep_mc(int n1, int M, int h, const double *__restrict__ band, const dou
                 if (warp + nw < nr) o1 = ld_relaxed(a + warp + nw);
             }
         };
-        // ---- forward: step i reads L_{i,i-1} from rb[i & 1] and prefetches
-        //      L_{i+1,i} into the other buffer
-        read_terms(cf, 0, 0, cur[0], cur[1]);
-        for (int i = 0; i < F; ++i) {
+        // ---- forward: step t = i - F0 reads L_{i,i-1} from rb[t & 1] and
+        //      prefetches L_{i+1,i} into the other buffer
+        const bool fpre = F0 > 0 && F1 > F0;
+        if (fpre) {
+            for (int e = threadIdx.x; e < n1; e += blockDim.x) vz[n1 + e] = z[(size_t)(F0 - 1) * n1 + e];
+            prefetch(0, band + ((size_t)F0 * nbk + (h - 1)) * n2);
+            __pipeline_commit();
+        }
+        if (F1 > F0) read_terms(cf, F0, min(h, F0), cur[0], cur[1]);
+        for (int i = F0; i < F1; ++i) {
+            const int t = i - F0;
             const int nd = min(h, i);   // terms c_{i,2..nd}
-            __syncthreads();            // every warp is done with step i - 1 (rb, zs)
-            if (threadIdx.x == 0) mbar_expect(&mbz[i & 1], n1 * (int)sizeof(double));
-            if (i + 1 < F) prefetch((i + 1) & 1, band + ((size_t)(i + 1) * nbk + (h - 1)) * n2);
+            __syncthreads();            // every warp is done with step t - 1 (rb, zs)
+            if (threadIdx.x == 0) mbar_expect(&mbz[t & 1], n1 * (int)sizeof(double));
+            if (i + 1 < F1) prefetch((t + 1) & 1, band + ((size_t)(i + 1) * nbk + (h - 1)) * n2);
             __pipeline_commit();
             __pipeline_wait_prior(1);
             __syncthreads();
-            if (i > 0) wait_bar(&mbz[(i - 1) & 1], ((i - 1) >> 1) & 1);
+            if (t > 0) wait_bar(&mbz[(t - 1) & 1], ((t - 1) >> 1) & 1);
             double nxt[2] = {0.0, 0.0};
-            if (i + 1 < F) read_terms(cf, i + 1, min(h, i + 1), nxt[0], nxt[1]);
+            if (i + 1 < F1) read_terms(cf, i + 1, min(h, i + 1), nxt[0], nxt[1]);
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
                 const int rr = warp + q * nw;
                 if (q >= rpw || rr >= nr) break;
                 const int r = r0 + rr;
                 double v = zs[(size_t)i * rows + rr];
-                if (i > 0) v -= block_dot<KC>(rb + ((size_t)(i & 1) * rows + rr) * n1, vz + (size_t)((i - 1) & 1) * n1, n1, lane);
+                if (t > 0 || fpre)
+                    v -= block_dot<KC>(rb + ((size_t)(t & 1) * rows + rr) * n1, vz + (size_t)((t - 1) & 1) * n1, n1, lane);
                 if (lane >= 2 && lane <= nd) cur[q] = poll(cf + ((size_t)i * hs + lane) * n1 + r, cur[q]);
                 for (int d = 2; d <= nd; ++d) v -= __shfl_sync(0xffffffffu, cur[q], d);
                 if (lane == 0) {
                     st_relaxed(z + (size_t)i * n1 + r, v);
                     zs[(size_t)i * rows + rr] = v;
                 }
-                send(vz + (size_t)(i & 1) * n1, &mbz[i & 1], r, v);
+                send(vz + (size_t)(t & 1) * n1, &mbz[t & 1], r, v);
             }
             cur[0] = nxt[0];
             cur[1] = nxt[1];
         }
-        // ---- backward: step t = Bs - i reads W_{i,i+1} from rb[t & 1] and
-        //      prefetches W_{i-1,i} into the other buffer.  When the rows above
-        //      Bs are inputs, x_{Bs+1} is staged in vx[1] and W_{Bs,Bs+1} in
-        //      rb[0] before the first step.
+        // ---- backward: step t = B1 - i reads W_{i,i+1} from rb[t & 1] and
+        //      prefetches W_{i-1,i} into the other buffer
         __syncthreads();
-        const bool preset = Bs >= 0 && Bs < M - 1;
-        if (preset) {
-            for (int e = threadIdx.x; e < n1; e += blockDim.x) vx[n1 + e] = x[(size_t)(Bs + 1) * n1 + e];
-            prefetch(0, W + ((size_t)Bs * h) * n2);
+        const bool bpre = B1 >= B0 && B1 < M - 1;
+        if (bpre) {
+            for (int e = threadIdx.x; e < n1; e += blockDim.x) vx[n1 + e] = x[(size_t)(B1 + 1) * n1 + e];
+            prefetch(0, W + ((size_t)B1 * h) * n2);
             __pipeline_commit();
         }
-        if (Bs >= 0) read_terms(cb, Bs, min(h, M - 1 - Bs), cur[0], cur[1]);
-        for (int i = Bs; i >= 0; --i) {
-            const int t = Bs - i;
+        if (B1 >= B0) read_terms(cb, B1, min(h, M - 1 - B1), cur[0], cur[1]);
+        for (int i = B1; i >= B0; --i) {
+            const int t = B1 - i;
             const int ne = min(h, M - 1 - i);   // terms b_{i,2..ne}
             __syncthreads();
             if (threadIdx.x == 0) mbar_expect(&mbx[t & 1], n1 * (int)sizeof(double));
-            if (i >= 1) prefetch((t + 1) & 1, W + ((size_t)(i - 1) * h) * n2);
+            if (i - 1 >= B0) prefetch((t + 1) & 1, W + ((size_t)(i - 1) * h) * n2);
             __pipeline_commit();
             __pipeline_wait_prior(1);
             __syncthreads();
             if (t > 0) wait_bar(&mbx[(t - 1) & 1], ((t - 1) >> 1) & 1);
             double nxt[2] = {0.0, 0.0};
-            if (i >= 1) read_terms(cb, i - 1, min(h, M - i), nxt[0], nxt[1]);
+            if (i - 1 >= B0) read_terms(cb, i - 1, min(h, M - i), nxt[0], nxt[1]);
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
                 const int rr = warp + q * nw;
                 if (q >= rpw || rr >= nr) break;
                 const int r = r0 + rr;
                 double v = zs[(size_t)i * rows + rr];
-                if (t > 0 || preset)
+                if (t > 0 || bpre)
                     v -= block_dot<KC>(rb + ((size_t)(t & 1) * rows + rr) * n1, vx + (size_t)((t - 1) & 1) * n1, n1, lane);
                 if (lane >= 2 && lane <= ne) cur[q] = poll(cb + ((size_t)i * hs + lane) * n1 + r, cur[q]);
                 for (int e = 2; e <= ne; ++e) v -= __shfl_sync(0xffffffffu, cur[q], e);
@@ -439,43 +462,66 @@ k_band_sweep_mc(int n1, int M, int h, const double *__restrict__ band, const dou
         __pipeline_wait_prior(0);
         // the last vectors were sent but not read: wait for them, so that no
         // store into this CTA's shared memory is in flight when it exits
-        if (F > 0) wait_bar(&mbz[(F - 1) & 1], ((F - 1) >> 1) & 1);
-        if (Bs >= 0) wait_bar(&mbx[Bs & 1], (Bs >> 1) & 1);
+        if (F1 > F0) {
+            const int tl = F1 - 1 - F0;
+            wait_bar(&mbz[tl & 1], (tl >> 1) & 1);
+        }
+        if (B1 >= B0) {
+            const int tl = B1 - B0;
+            wait_bar(&mbx[tl & 1], (tl >> 1) & 1);
+        }
         cl.sync();
     } else {
-        const int d = cid + 1;   // 2..h
+        const int hid = cid - ni, d = hid % (h - 1) + 2;   // d = 2..h
+        // the instances of this helper: all (q = q0 + 0..nq-1), or one
+        const int q0 = hsets == 1 ? 0 : hid / (h - 1), nq = hsets == 1 ? ni : 1;
         // forward terms c_{j+d,d} = L_{j+d,j} z_j (slot h - d of block row j + d)
-        if (d < F) prefetch(0, band + ((size_t)d * nbk + (h - d)) * n2);
+        // for the rows j + d in [F0, F1), instance by instance within a step:
+        // item w = (j - j0) nq + (q - q0), the next item's block rows prefetched
+        const int j0 = max(0, F0 - d), nf = max(0, F1 - d - j0) * nq;
+        auto fblk = [&](int w) {
+            const int j = j0 + w / nq, q = q0 + w % nq;
+            return band + (size_t)q * bst + ((size_t)(j + d) * nbk + (h - d)) * n2;
+        };
+        if (nf > 0) prefetch(0, fblk(0));
         __pipeline_commit();
-        for (int j = 0; j + d < F; ++j) {
-            const int buf = j & 1;
-            if (j + 1 + d < F) prefetch(buf ^ 1, band + ((size_t)(j + 1 + d) * nbk + (h - d)) * n2);
+        for (int w = 0; w < nf; ++w) {
+            const int j = j0 + w / nq, q = q0 + w % nq, buf = w & 1;
+            if (w + 1 < nf) prefetch(buf ^ 1, fblk(w + 1));
             __pipeline_commit();
-            for (int e = threadIdx.x; e < n1; e += blockDim.x) vz[e] = poll(z + (size_t)j * n1 + e, ld_relaxed(z + (size_t)j * n1 + e));
+            const double *zq = z + (size_t)q * vst + (size_t)j * n1;
+            for (int e = threadIdx.x; e < n1; e += blockDim.x) vz[e] = poll(zq + e, ld_relaxed(zq + e));
             __pipeline_wait_prior(1);
             __syncthreads();
+            double *cq = cf + (size_t)q * sst + ((size_t)(j + d) * hs + d) * n1 + r0;
             for (int rr = warp; rr < nr; rr += nw) {
                 const double s = block_dot<KC>(rb + ((size_t)buf * rows + rr) * n1, vz, n1, lane);
-                if (lane == 0) st_relaxed(cf + ((size_t)(j + d) * hs + d) * n1 + r0 + rr, s);
+                if (lane == 0) st_relaxed(cq + rr, s);
             }
             __syncthreads();
         }
         __pipeline_wait_prior(0);
         __syncthreads();
-        // backward terms b_{k-d,d} = W_{k-d,k} x_k for the rows k - d <= Bs
-        const int k0 = min(M - 1, Bs + d);
-        if (k0 - d >= 0) prefetch(0, W + ((size_t)(k0 - d) * h + (d - 1)) * n2);
+        // backward terms b_{k-d,d} = W_{k-d,k} x_k for the rows k - d in [B0, B1]
+        const int k0 = min(M - 1, B1 + d), nbw = max(0, k0 - d - B0 + 1) * nq;
+        auto bblk = [&](int w) {
+            const int k = k0 - w / nq, q = q0 + w % nq;
+            return W + (size_t)q * wst + ((size_t)(k - d) * h + (d - 1)) * n2;
+        };
+        if (nbw > 0) prefetch(0, bblk(0));
         __pipeline_commit();
-        for (int k = k0, t = 0; k - d >= 0; --k, ++t) {
-            const int buf = t & 1;
-            if (k - 1 - d >= 0) prefetch(buf ^ 1, W + ((size_t)(k - 1 - d) * h + (d - 1)) * n2);
+        for (int w = 0; w < nbw; ++w) {
+            const int k = k0 - w / nq, q = q0 + w % nq, buf = w & 1;
+            if (w + 1 < nbw) prefetch(buf ^ 1, bblk(w + 1));
             __pipeline_commit();
-            for (int e = threadIdx.x; e < n1; e += blockDim.x) vz[e] = poll(x + (size_t)k * n1 + e, ld_relaxed(x + (size_t)k * n1 + e));
+            const double *xq = x + (size_t)q * vst + (size_t)k * n1;
+            for (int e = threadIdx.x; e < n1; e += blockDim.x) vz[e] = poll(xq + e, ld_relaxed(xq + e));
             __pipeline_wait_prior(1);
             __syncthreads();
+            double *bq = cb + (size_t)q * sst + ((size_t)(k - d) * hs + d) * n1 + r0;
             for (int rr = warp; rr < nr; rr += nw) {
                 const double s = block_dot<KC>(rb + ((size_t)buf * rows + rr) * n1, vz, n1, lane);
-                if (lane == 0) st_relaxed(cb + ((size_t)(k - d) * hs + d) * n1 + r0 + rr, s);
+                if (lane == 0) st_relaxed(bq + rr, s);
             }
             __syncthreads();
         }
@@ -519,63 +565,72 @@ static int launch_sweep(cudaStream_t st, int nb, int n1, int M, int h, const dou
     return SWJ_OK;
 }
 
-// Cluster size and shared memory of the multi-cluster sweep per (kernel, n1,
-// M, h): 16 CTAs, else 8, where h such clusters fit on the device at once
-// (0: the multi-cluster sweep does not apply).
+// Cluster size, shared memory and helper sets of the multi-cluster sweep per
+// (kernel, n1, M, h, ni): 16 CTAs, else 12, else 8, with a helper set per
+// instance where ni h such clusters fit on the device at once, else one shared
+// set where ni + h - 1 fit (cs = 0: the multi-cluster sweep does not apply).
+struct McPick {
+    int cs, hsets;
+    size_t smem;
+};
 static std::mutex g_mc_mutex;
-static std::map<std::tuple<const void *, int, int, int>, std::pair<int, size_t>> g_mc_cache;
+static std::map<std::tuple<const void *, int, int, int, int>, McPick> g_mc_cache;
 
 template <int KC>
-static int launch_sweep_mc(cudaStream_t st, int n1, int M, int h, const double *band, const double *W,
-                           const double *p, double *z, double *x, double *cf, double *cb, int *err,
-                           bool prepare, int F, int Bs)
+static int launch_sweep_mc(cudaStream_t st, int n1, int M, int h, int ni, const double *band, size_t bst,
+                           const double *W, size_t wst, const double *p, double *z, double *x, size_t vst,
+                           double *cf, double *cb, size_t sst, int *err, bool prepare, int F0, int F1, int B1,
+                           int B0)
 {
     const void *kern = (const void *)k_band_sweep_mc<KC>;
-    int cs;
-    size_t smem;
+    McPick pick = {0, 1, 0};
     {
         std::lock_guard<std::mutex> lock(g_mc_mutex);
-        auto key = std::make_tuple(kern, n1, M, h);
+        auto key = std::make_tuple(kern, n1, M, h, ni);
         auto it = g_mc_cache.find(key);
         if (it == g_mc_cache.end()) {
-            std::pair<int, size_t> pick(0, 0);
-            for (int c0 : {16, 8}) {
-                // as many CTAs as it takes to give each the same number of rows
-                // (every CTA owns at least one row: the exchange relies on it),
-                // at most two rows per warp
-                const int rows = (n1 + c0 - 1) / c0, c = (n1 + rows - 1) / rows;
-                if (rows > 2 * (kSweepThreads / 32)) continue;
-                const size_t sm = mc_smem_bytes(n1, M, c);
-                if (sm > 220 * 1024) continue;
-                swj_cluster_for(kern, kSweepThreads, sm);   // raises the kernel's limit to sm
-                cudaLaunchConfig_t q = {};
-                q.gridDim = dim3(c * h);
-                q.blockDim = dim3(kSweepThreads);
-                q.dynamicSmemBytes = sm;
-                cudaLaunchAttribute qa[1];
-                qa[0].id = cudaLaunchAttributeClusterDimension;
-                qa[0].val.clusterDim.x = c;
-                qa[0].val.clusterDim.y = 1;
-                qa[0].val.clusterDim.z = 1;
-                q.attrs = qa;
-                q.numAttrs = 1;
-                int ncl = 0;
-                if (cudaOccupancyMaxActiveClusters(&ncl, kern, &q) != cudaSuccess) ncl = 0;
-                cudaGetLastError();
-                if (ncl >= h) {
-                    pick = std::make_pair(c, sm);
-                    break;
+            const int hs_try[2] = {ni, 1};
+            for (int hi = 0; hi < (ni > 1 ? 2 : 1) && !pick.cs; ++hi) {
+                const int hs = hs_try[hi], ncl_need = ni + hs * (h - 1);
+                for (int c0 : {16, 12, 8}) {
+                    // as many CTAs as it takes to give each the same number of rows
+                    // (every CTA owns at least one row: the exchange relies on it),
+                    // at most two rows per warp
+                    const int rows = (n1 + c0 - 1) / c0, c = (n1 + rows - 1) / rows;
+                    if (rows > 2 * (kSweepThreads / 32)) continue;
+                    const size_t sm = mc_smem_bytes(n1, M, c);
+                    if (sm > 220 * 1024) continue;
+                    swj_cluster_for(kern, kSweepThreads, sm);   // raises the kernel's limit to sm
+                    cudaLaunchConfig_t q = {};
+                    q.gridDim = dim3(c * ncl_need);
+                    q.blockDim = dim3(kSweepThreads);
+                    q.dynamicSmemBytes = sm;
+                    cudaLaunchAttribute qa[1];
+                    qa[0].id = cudaLaunchAttributeClusterDimension;
+                    qa[0].val.clusterDim.x = c;
+                    qa[0].val.clusterDim.y = 1;
+                    qa[0].val.clusterDim.z = 1;
+                    q.attrs = qa;
+                    q.numAttrs = 1;
+                    int ncl = 0;
+                    if (cudaOccupancyMaxActiveClusters(&ncl, kern, &q) != cudaSuccess) ncl = 0;
+                    cudaGetLastError();
+                    if (ncl >= ncl_need) {
+                        pick = {c, hs, sm};
+                        break;
+                    }
                 }
             }
             it = g_mc_cache.emplace(key, pick).first;
         }
-        cs = it->second.first;
-        smem = it->second.second;
+        pick = it->second;
     }
+    const int cs = pick.cs, hsets = pick.hsets;
+    const size_t smem = pick.smem;
     if (!cs) return SWJ_EINVAL;
     if (prepare) return SWJ_OK;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(cs * h);
+    cfg.gridDim = dim3(cs * (ni + hsets * (h - 1)));
     cfg.blockDim = dim3(kSweepThreads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
@@ -589,8 +644,8 @@ static int launch_sweep_mc(cudaStream_t st, int n1, int M, int h, const double *
     cfg.attrs = attr;
     cfg.numAttrs = 2;
     SWJ_COUNT_LAUNCH();
-    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_band_sweep_mc<KC>, n1, M, h, band, W, p, z, x, cf, cb, cs,
-                                             err, F, Bs);
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_band_sweep_mc<KC>, n1, M, h, ni, hsets, band, bst, W, wst, p,
+                                             z, x, vst, cf, cb, sst, cs, err, F0, F1, B1, B0);
     if (e != cudaSuccess) {
         cudaGetLastError();
         // a stream capture that another host thread invalidated is not a refusal
@@ -650,11 +705,19 @@ int swj_band_sweep_cluster(cudaStream_t st, int nb, int n1, int M, int h, const 
 }
 
 int swj_band_sweep_mc(cudaStream_t st, int n1, int M, int h, const double *band, const double *W,
-                      const double *p, double *z, double *x, double *cf, double *cb, int *err, bool prepare,
-                      int F, int Bs)
+                      const double *p, double *z, double *x, double *cf, double *cb, int *err, bool prepare)
 {
     if (h < 2 || M < 2) return SWJ_EINVAL;
-    if (F < 0) F = M;
-    if (Bs < -1 || Bs >= M) Bs = M - 1;
-    SWJ_KC_DISPATCH((launch_sweep_mc<K>(st, n1, M, h, band, W, p, z, x, cf, cb, err, prepare, F, Bs)));
+    SWJ_KC_DISPATCH((launch_sweep_mc<K>(st, n1, M, h, 1, band, 0, W, 0, p, z, x, 0, cf, cb, 0, err, prepare, 0, M,
+                                        M - 1, 0)));
+}
+
+int swj_band_sweep_mc_ranges(cudaStream_t st, int n1, int M, int h, int ni, const double *band, size_t bst,
+                             const double *W, size_t wst, const double *p, double *z, double *x, size_t vst,
+                             double *cf, double *cb, size_t sst, int *err, bool prepare, int F0, int F1, int B1,
+                             int B0)
+{
+    if (h < 2 || M < 2 || ni < 1 || ni > 2 || F0 < 0 || F1 > M || B1 >= M || B0 < 0) return SWJ_EINVAL;
+    SWJ_KC_DISPATCH((launch_sweep_mc<K>(st, n1, M, h, ni, band, bst, W, wst, p, z, x, vst, cf, cb, sst, err, prepare,
+                                        F0, F1, B1, B0)));
 }

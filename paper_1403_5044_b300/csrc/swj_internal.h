@@ -150,7 +150,8 @@ struct swj_ctx {
     // multi-cluster apply (one instance): z, then the term slots cf, cb, and the error word
     double *pc_mc_buf;
     int *pc_mc_err;
-    int pc_mc;                   // 1: the apply uses swj_band_sweep_mc
+    int pc_mc;                   // apply on h clusters: 0 no, 1 one instance (or half) per launch, 2 both
+                                 // halves of the two-sided order in one launch
     double *pc_lt;               // set-up scratch: inv_i S_ij (j < i) of one block row, every instance
     // sliced (bf16 tensor-core) block products of the band LU (lu_products = SWJ_LU_SLICED)
     void *oz_sa, *oz_sb;         // bf16 slices of the A (row-split) and B (column-split) factors
@@ -296,11 +297,21 @@ int swj_band_sweep_cluster(cudaStream_t st, int nb, int n1, int M, int h, const 
 // written" pattern (swj_block_p's fill) where the launch writes them; err: set
 // to 1 when a poll gave up, 2 when the launch did not form clusters of the
 // expected size.  SWJ_EINVAL when h < 2 or the device cannot hold h clusters
-// at once (nothing launched).  F, Bs as for swj_band_sweep_cluster (with F = 0
-// the backward recurrence reads z from p).
+// at once (nothing launched).
 int swj_band_sweep_mc(cudaStream_t st, int n1, int M, int h, const double *band, const double *W,
                       const double *p, double *z, double *x, double *cf, double *cb, int *err,
-                      bool prepare = false, int F = -1, int Bs = -2);
+                      bool prepare = false);
+// The same for ni = 1 or 2 instances at once (instance q's band, W, vectors and
+// term slots at q bst, q wst, q vst, q sst; one critical cluster each, the h - 1
+// helper clusters shared) over forward rows F0..F1-1 and backward rows B1 down to
+// B0: the rows of z below F0 and of x above B1 are inputs, zs starts from p (pass
+// z as p for a launch without forward rows).  SWJ_EINVAL when the device cannot
+// hold ni + h - 1 clusters at once (nothing launched); SWJ_ECUDA when the launch
+// met an invalidated stream capture.
+int swj_band_sweep_mc_ranges(cudaStream_t st, int n1, int M, int h, int ni, const double *band, size_t bst,
+                             const double *W, size_t wst, const double *p, double *z, double *x, size_t vst,
+                             double *cf, double *cb, size_t sst, int *err, bool prepare, int F0, int F1, int B1,
+                             int B0);
 
 // precond.cu
 int swj_pc_setup(swj_ctx *c);
