@@ -191,6 +191,20 @@ __device__ __forceinline__ unsigned ld_acquire_cluster(const unsigned *local_wor
     return v;
 }
 
+// (key, index) of the warp's largest 64-bit key, the smallest index among
+// equal keys, in every lane: three warp reductions (high word, low word among
+// the lanes with the largest high word, index among the lanes with the
+// largest key) instead of a shuffle tree.  Indices are non-negative.
+__device__ __forceinline__ void warp_argmax(unsigned long long &key, int &idx)
+{
+    const unsigned hi = (unsigned)(key >> 32), lo = (unsigned)key;
+    const unsigned mhi = __reduce_max_sync(0xffffffffu, hi);
+    const unsigned mlo = __reduce_max_sync(0xffffffffu, hi == mhi ? lo : 0u);
+    const bool top = hi == mhi && lo == mlo;
+    idx = (int)__reduce_min_sync(0xffffffffu, top ? (unsigned)idx : 0xffffffffu);
+    key = ((unsigned long long)mhi << 32) | mlo;
+}
+
 // Iterations of a flag wait before the kernel gives up (far above any real
 // wait: a step takes a few microseconds).
 constexpr long long kGJSpinLimit = 1ll << 26;
@@ -282,23 +296,13 @@ k_gj_pipe(int n, const double *in_base, size_t istride, double *out_base, size_t
                     (unsigned long long)__double_as_longlong(fabs(A[(size_t)i * ws + kk]));
                 if (kv > bk || (kv == bk && i < bi)) { bk = kv; bi = i; }
             }
-#pragma unroll
-            for (int sft = 16; sft > 0; sft >>= 1) {
-                const unsigned long long ok = __shfl_xor_sync(0xffffffffu, bk, sft);
-                const int oi = __shfl_xor_sync(0xffffffffu, bi, sft);
-                if (ok > bk || (ok == bk && oi < bi)) { bk = ok; bi = oi; }
-            }
+            warp_argmax(bk, bi);
             if ((tid & 31) == 0) { red_k[tid >> 5] = bk; red_i[tid >> 5] = bi; }
             __syncthreads();
             if (tid < 32) {
                 unsigned long long kv = (tid < nth / 32) ? red_k[tid] : 0ull;
                 int ii = (tid < nth / 32) ? red_i[tid] : n;
-#pragma unroll
-                for (int sft = 16; sft > 0; sft >>= 1) {
-                    const unsigned long long ok = __shfl_xor_sync(0xffffffffu, kv, sft);
-                    const int oi = __shfl_xor_sync(0xffffffffu, ii, sft);
-                    if (ok > kv || (ok == kv && oi < ii)) { kv = ok; ii = oi; }
-                }
+                warp_argmax(kv, ii);
                 if (tid == 0) {
                     const double pv = (ii < n) ? A[(size_t)ii * ws + kk] : 0.0;
                     const bool good = ii < n && pv != 0.0 && isfinite(pv);

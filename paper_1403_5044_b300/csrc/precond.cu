@@ -48,6 +48,7 @@
 #include "closed_form.cuh"
 #include <vector>
 #include <string.h>
+#include <cuda_pipeline.h>
 
 namespace {
 
@@ -93,8 +94,10 @@ __global__ void k_build_ABC(int N, double x1, double dx, double nrad, double F,
     C[e] = cc;
 }
 
-// Forward-sweep coefficients c'_r of the tridiagonal block A (one thread).
-__global__ void k_tri_coef(int n1, const double *__restrict__ A, double *__restrict__ cp)
+// Forward-sweep coefficients of the tridiagonal block A (one thread): c'_r,
+// the sub-diagonal a_r and 1 / den_r, den_r = b_r - a_r c'_{r-1} (Thomas
+// algorithm), at coef[r], coef[n1 + r], coef[2 n1 + r].
+__global__ void k_tri_coef(int n1, const double *__restrict__ A, double *__restrict__ coef)
 {
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
     double prev = 0.0;
@@ -102,33 +105,51 @@ __global__ void k_tri_coef(int n1, const double *__restrict__ A, double *__restr
         double sub = r > 0 ? A[r * n1 + r - 1] : 0.0;
         double dia = A[r * n1 + r];
         double sup = r + 1 < n1 ? A[r * n1 + r + 1] : 0.0;
-        double den = dia - sub * prev;
-        prev = sup / den;
-        cp[r] = prev;
+        double rd = 1.0 / (dia - sub * prev);
+        prev = sup * rd;
+        coef[r] = prev;
+        coef[n1 + r] = sub;
+        coef[2 * n1 + r] = rd;
     }
 }
 
-// X = A^-1 Rhs for all ncol columns (Thomas algorithm, one thread per column;
-// Rhs == nullptr means the identity).  X and Rhs are n1 x ncol row-major.
-__global__ void k_tri_cols(int n1, int ncol, const double *__restrict__ A,
-                           const double *__restrict__ cp, const double *Rhs, double *X)
+// X = A^-1 Rhs for all ncol columns (Rhs == nullptr means the identity); X and
+// Rhs are n1 x ncol row-major.  A column per thread, blockDim.x columns per
+// block: the block's columns are copied into shared memory first (all rows
+// in flight), both sweeps run there, and X is written as it is found.
+__global__ void k_tri_cols(int n1, int ncol, const double *__restrict__ coef, const double *Rhs, double *X)
 {
-    int col = blockIdx.x * blockDim.x + threadIdx.x;
+    extern __shared__ double sc[];
+    const int nc = blockDim.x, lane = threadIdx.x;
+    const int col = blockIdx.x * nc + lane;
     if (col >= ncol) return;
+    const double *cp = coef, *sub = coef + n1, *rden = coef + 2 * n1;
+    double *Y = sc + lane;   // row r of this column at Y[r * nc]
+    if (Rhs) {
+        for (int r = 0; r < n1; ++r) __pipeline_memcpy_async(Y + (size_t)r * nc, Rhs + (size_t)r * ncol + col, 8);
+        __pipeline_commit();
+        __pipeline_wait_prior(0);
+    } else {
+        for (int r = 0; r < n1; ++r) Y[(size_t)r * nc] = (r == col) ? 1.0 : 0.0;
+    }
     double dprev = 0.0;
     for (int r = 0; r < n1; ++r) {
-        double sub = r > 0 ? A[r * n1 + r - 1] : 0.0;
-        double dia = A[r * n1 + r];
-        double den = dia - sub * (r > 0 ? cp[r - 1] : 0.0);
-        double d = Rhs ? Rhs[(size_t)r * ncol + col] : (r == col ? 1.0 : 0.0);
-        dprev = (d - sub * dprev) / den;
-        X[(size_t)r * ncol + col] = dprev;
+        dprev = (Y[(size_t)r * nc] - sub[r] * dprev) * rden[r];
+        Y[(size_t)r * nc] = dprev;
     }
-    double next = X[(size_t)(n1 - 1) * ncol + col];
+    double next = dprev;
+    X[(size_t)(n1 - 1) * ncol + col] = next;
     for (int r = n1 - 2; r >= 0; --r) {
-        next = X[(size_t)r * ncol + col] - cp[r] * next;
+        next = Y[(size_t)r * nc] - cp[r] * next;
         X[(size_t)r * ncol + col] = next;
     }
+}
+
+// columns per block of k_tri_cols: 32 while they fit in 160 KB of shared memory
+inline int tri_cols_per_block(int n1)
+{
+    const int fit = (int)((160 * 1024) / ((size_t)n1 * sizeof(double)));
+    return fit >= 32 ? 32 : (fit < 1 ? 1 : fit);
 }
 
 // Records of the flat state (zeta = 0, g = 0, zeta_x = 1 at the sources,
@@ -449,8 +470,13 @@ inline double *wblk(swj_ctx *c, int inst, int i, int k)
     return c->pc_W + ((size_t)inst * c->pc_M * c->pc_h + (size_t)i * c->pc_h + (k - i - 1)) * n2;
 }
 
+void delete_plan(void *plan);
+
 void free_pc(swj_ctx *c)
 {
+    delete_plan(c->pc_plan);
+    c->pc_plan = nullptr;
+    c->pc_mc_ok = 0;
     double **bufs[] = {&c->pc_Ainv, &c->pc_AinvB1, &c->pc_CAinv, &c->pc_G1, &c->pc_A, &c->pc_B1,
                        &c->pc_C, &c->pc_invF2, &c->pc_band, &c->pc_W, &c->pc_sumK3, &c->pc_t1,
                        &c->pc_t2, &c->pc_z, &c->pc_work, &c->pc_lt, &c->pc_mc_buf, &c->pc_nd_buf,
@@ -602,6 +628,26 @@ OzLayout oz_layout(int n1, const PcShape &sh)
               L.maxP * per + 3 * L.maxP * L.s * sizeof(void *) + L.bytes_desc;
     return L;
 }
+
+// One step's entries in the sliced path's split and product lists.
+struct OzStep {
+    size_t a, wb, u, l, pwb, pb1, pb2, pl;
+    int na, nwb, nu, nl, cwb, cb1, cb2, cl;
+};
+
+// The band LU's host-side plan, built once per allocation of the buffers (the
+// lists hold device addresses of blocks, fixed until the buffers are freed):
+// per step and group the offset and count into the pointer triples of the
+// batched FP64 products (uploaded to pc_ptrs), and the sliced path's split and
+// product lists (uploaded to oz_desc).
+struct PcPlan {
+    int np = 0;
+    std::vector<int> off, cnt;
+    std::vector<OzStep> zo;
+    OzLayout OL = {};
+};
+
+void delete_plan(void *plan) { delete (PcPlan *)plan; }
 
 }  // namespace
 
@@ -804,13 +850,20 @@ int swj_pc_setup(swj_ctx *c)
     SWJ_COUNT_LAUNCH();
     k_build_ABC<<<nblk((long)n2, 256), 256, 0, st>>>(N, m.x1, m.dx, m.n_rad, 1.0, c->pc_A,
                                                      c->pc_B1, c->pc_C);
-    double *cpv = c->pc_t1;   // n1 scratch
+    double *cpv = c->pc_t1;   // 3 n1 scratch (pc_t1 holds M n1, M >= 3)
     SWJ_COUNT_LAUNCH();
     k_tri_coef<<<1, 1, 0, st>>>(n1, c->pc_A, cpv);
-    SWJ_COUNT_LAUNCH();
-    k_tri_cols<<<nblk(n1, 128), 128, 0, st>>>(n1, n1, c->pc_A, cpv, nullptr, c->pc_Ainv);
-    SWJ_COUNT_LAUNCH();
-    k_tri_cols<<<nblk(n1, 128), 128, 0, st>>>(n1, n1, c->pc_A, cpv, c->pc_B1, c->pc_AinvB1);
+    {
+        const int tc = tri_cols_per_block(n1);
+        const size_t tsm = (size_t)tc * n1 * sizeof(double);
+        static const bool tri_attr = cudaFuncSetAttribute(k_tri_cols, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                          160 * 1024) == cudaSuccess;
+        if (!tri_attr) cudaGetLastError();
+        SWJ_COUNT_LAUNCH();
+        k_tri_cols<<<nblk(n1, tc), tc, tsm, st>>>(n1, n1, cpv, nullptr, c->pc_Ainv);
+        SWJ_COUNT_LAUNCH();
+        k_tri_cols<<<nblk(n1, tc), tc, tsm, st>>>(n1, n1, cpv, c->pc_B1, c->pc_AinvB1);
+    }
     swj_dgemm(st, n1, n1, n1, 1.0, c->pc_C, n1, c->pc_Ainv, n1, 0.0, c->pc_CAinv, n1);
     swj_dgemm(st, n1, n1, n1, 1.0, c->pc_C, n1, c->pc_AinvB1, n1, 0.0, c->pc_G1, n1);
     // --- PreD diagonal correction: trapezoid sum of w K3 and I of the flat surface
@@ -883,19 +936,24 @@ int swj_pc_setup(swj_ctx *c)
         //   B2  S_jk -= S_ji W_ik for the other j, k = i+1..kmax
         //   L   L_ij = inv_i S_ij, j = i-h..i-1, into the scratch pc_lt
         enum { gWc, gUc, gWb, gB1, gB2, gL, kGroups };
+        auto chain_b1 = [&](int i, int j, int k) {
+            return (j == i + 1 && k == i + 1) || (j == i + 1 && k == i + 2) || (j == i + 2 && k == i + 1) ||
+                   (j == i + 2 && k == i + 2);
+        };
+        if (!c->pc_plan) {
+        PcPlan *plan = new PcPlan();
+        c->pc_plan = plan;
         std::vector<const double *> PA, PB;
         std::vector<double *> PC;
-        std::vector<int> off((size_t)Mv * kGroups), cnt((size_t)Mv * kGroups);
+        std::vector<int> &off = plan->off, &cnt = plan->cnt;
+        off.assign((size_t)Mv * kGroups, 0);
+        cnt.assign((size_t)Mv * kGroups, 0);
         auto begin = [&](int i, int g) { off[(size_t)i * kGroups + g] = (int)PA.size(); };
         auto end = [&](int i, int g) {
             cnt[(size_t)i * kGroups + g] = (int)PA.size() - off[(size_t)i * kGroups + g];
         };
         auto add = [&](const double *a, const double *b, double *cc) {
             PA.push_back(a); PB.push_back(b); PC.push_back(cc);
-        };
-        auto chain_b1 = [&](int i, int j, int k) {
-            return (j == i + 1 && k == i + 1) || (j == i + 1 && k == i + 2) || (j == i + 2 && k == i + 1) ||
-                   (j == i + 2 && k == i + 2);
         };
         for (int i = 0; i < Mv; ++i) {
             const int kmax = i + h < Mv - 1 ? i + h : Mv - 1;
@@ -929,7 +987,8 @@ int swj_pc_setup(swj_ctx *c)
                     add(blk(c, q, i, i), blk(c, q, i, j), c->pc_lt + ((size_t)q * h + (j - j0)) * n2);
             end(i, gL);
         }
-        int np = (int)PA.size();
+        const int np = (int)PA.size();
+        plan->np = np;
         if (c->pc_ptrs_cap < np) {
             if (c->pc_ptrs) {
                 cudaFree(c->pc_ptrs);
@@ -954,18 +1013,11 @@ int swj_pc_setup(swj_ctx *c)
         SWJ_CUDA_TRY(cudaMemcpyAsync(c->pc_ptrs, all.data(), all.size() * sizeof(double *),
                                      cudaMemcpyHostToDevice, st));
         SWJ_CUDA_TRY(cudaStreamSynchronize(st));   // `all` must outlive the copy
-        double **dA = c->pc_ptrs, **dB = c->pc_ptrs + np, **dC = c->pc_ptrs + 2 * np;
         // the sliced path: split lists and product lists of every step (see OzLayout)
-        struct OzStep {
-            size_t a, wb, u, l, pwb, pb1, pb2, pl;
-            int na, nwb, nu, nl, cwb, cb1, cb2, cl;
-        };
-        std::vector<OzStep> zo(sliced ? Mv : 0);
-        OzLayout OL = {};
-        const double *const *zP = nullptr;
-        const int *zS = nullptr;
-        const OzProd *zQ = nullptr;
+        std::vector<OzStep> &zo = plan->zo;
+        zo.assign(sliced ? Mv : 0, OzStep{});
         if (sliced) {
+            OzLayout &OL = plan->OL;
             OL = oz_layout(n1, sh);
             std::vector<const double *> zp;
             std::vector<int> zs;
@@ -1020,6 +1072,20 @@ int swj_pc_setup(swj_ctx *c)
             SWJ_CUDA_TRY(cudaMemcpyAsync(base + offS, zs.data(), zs.size() * sizeof(int), cudaMemcpyHostToDevice, st));
             SWJ_CUDA_TRY(cudaMemcpyAsync(base + offQ, zq.data(), zq.size() * sizeof(OzProd), cudaMemcpyHostToDevice, st));
             SWJ_CUDA_TRY(cudaStreamSynchronize(st));   // the host lists must outlive the copies
+        }
+        }
+        const PcPlan &PL = *(const PcPlan *)c->pc_plan;
+        const std::vector<int> &off = PL.off, &cnt = PL.cnt;
+        const std::vector<OzStep> &zo = PL.zo;
+        const OzLayout &OL = PL.OL;
+        const int np = PL.np;
+        double **dA = c->pc_ptrs, **dB = c->pc_ptrs + np, **dC = c->pc_ptrs + 2 * np;
+        const double *const *zP = nullptr;
+        const int *zS = nullptr;
+        const OzProd *zQ = nullptr;
+        if (sliced) {
+            char *base = (char *)c->oz_desc;
+            const size_t offS = oz_align(OL.nptr * sizeof(double *)), offQ = offS + oz_align(OL.nptr * sizeof(int));
             zP = (const double *const *)base;
             zS = (const int *)(base + offS);
             zQ = (const OzProd *)(base + offQ);
@@ -1169,9 +1235,11 @@ int swj_pc_setup(swj_ctx *c)
     // them
     //  (two-sided order: both halves at once where ni + h - 1 = h + 1 clusters fit,
     //  else one half at a time)
-    c->pc_mc = 0;
-    if (c->pc_mc_buf && swj_band_sweep_mc(st, n1, Mv, h, c->pc_band, c->pc_W, nullptr, nullptr, nullptr,
-                                          nullptr, nullptr, nullptr, true) == SWJ_OK) {
+    //  (settled once per allocation of the buffers: pc_mc_ok = mode + 1)
+    c->pc_mc = c->pc_mc_ok ? c->pc_mc_ok - 1 : 0;
+    if (!c->pc_mc_ok && c->pc_mc_buf &&
+        swj_band_sweep_mc(st, n1, Mv, h, c->pc_band, c->pc_W, nullptr, nullptr, nullptr, nullptr, nullptr,
+                          nullptr, true) == SWJ_OK) {
         int best = 1;
         if (sh.nd && swj_band_sweep_mc_ranges(st, n1, Mv, h, 2, nullptr, 0, nullptr, 0, nullptr, nullptr, nullptr,
                                               0, nullptr, nullptr, 0, nullptr, true, 0, 0, -1, 0) == SWJ_OK)
@@ -1189,6 +1257,7 @@ int swj_pc_setup(swj_ctx *c)
         }
         SWJ_CUDA_TRY(cudaMemsetAsync(c->pc_mc_err, 0, sizeof(int), st));
     }
+    c->pc_mc_ok = c->pc_mc + 1;
     c->pc_ready = 1;
     return SWJ_OK;
 }
