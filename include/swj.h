@@ -64,7 +64,8 @@ extern "C" {
 #define SWJ_SOLVE_FP64  0  /* Newton-GMRES with the FP64 residual throughout       */
 #define SWJ_SOLVE_MIXED 1  /* FP32 residual inside Newton/GMRES, then FP64         */
                            /* residual refinement steps (Newton on the FP64        */
-                           /* residual with FP32 Jacobian-vector products)         */
+                           /* residual with exact Jacobian-vector products whose   */
+                           /* all-pairs part is FP32, as swj_jvp_exact)            */
 
 /* Mesh (Section 3).  N >= 4 points in x, M >= 3 in y; dx, dy > 0; y1 = 0.
  * n_rad is the decay rate n of the radiation condition (0.05 in Section 3). */

@@ -21,10 +21,10 @@
 // chosen so that s n 2^(2 beta) <= 2^24: every
 // partial sum of every T_d is an integer below 2^24, so a bf16 GEMM with FP32
 // accumulation (cuBLAS) computes it exactly whatever its summation order.
-// The T_d for d <= s - 1 are added in FP64, smallest first; the dropped terms
-// and the digit truncation are below n 2^(-56) of |A_r,:| |B_:,c|, the size
-// of FP64's own rounding of the dot product, and the result does not depend
-// on how the products are batched.  Matrices are padded with zeros to a
+// The T_d for d <= s - 1 are summed exactly in integer arithmetic and rounded
+// to FP64 once; the dropped terms and the digit truncation are below
+// n 2^(-56) of |A_r,:| |B_:,c|, the size of FP64's own rounding of the dot
+// product, and the result does not depend on how the products are batched.  Matrices are padded with zeros to a
 // multiple of 8 (16-byte rows for the tensor-core kernels).
 #include "swj_internal.h"
 #include <cublas_v2.h>
@@ -156,8 +156,12 @@ __global__ void k_oz_ptrs(int count, int s, int np, const OzProd *__restrict__ p
     pC[e] = P + ((size_t)t * s + d) * n2;
 }
 
-// C_t = alpha 2^(ea_r + eb_c) sum_d 2^(-beta (d+2)) T_d[r, c] (+ C_t), d from s - 1
-// down (smallest terms first).  Thread per element of the n x n block.
+// C_t = alpha 2^(ea_r + eb_c) sum_d 2^(-beta (d+2)) T_d[r, c] (+ C_t).  Every
+// T_d[r, c] is an integer below 2^24 in magnitude, so the sum is the integer
+// S = sum_d T_d 2^(beta (s-1-d)) (below 2^80) times 2^(-beta (s+1)): it is
+// accumulated exactly in 128-bit two's complement with integer operations
+// (B300's FP64 pipe, two FMAs per clock per SM, would bound it otherwise) and
+// rounded to FP64 once.  Thread per element of the n x n block.
 __global__ void k_oz_combine(int n, int np, int s, int beta, const OzProd *__restrict__ prods,
                              const float *__restrict__ P, const int *__restrict__ ea, const int *__restrict__ eb,
                              double alpha)
@@ -169,13 +173,21 @@ __global__ void k_oz_combine(int n, int np, int s, int beta, const OzProd *__res
     const int r = (int)(e / n), c = (int)(e % n);
     const size_t n2 = (size_t)np * np;
     const float *Pt = P + (size_t)t * s * n2 + (size_t)r * np + c;
-    // 2^(-beta (d+2)) built from its exponent bits (exact), one FMA per term
-    double v = 0.0;
-    for (int d = s - 1; d >= 0; --d)
-        v = fma((double)Pt[(size_t)d * n2], __longlong_as_double((long long)(1023 - beta * (d + 2)) << 52), v);
-    v = ldexp(v, ea[(size_t)o.a * np + r] + eb[(size_t)o.b * np + c]);
+    long long hi = 0;
+    unsigned long long lo = 0;
+    for (int d = 0; d < s; ++d) {
+        const long long q = (long long)__float2int_rn(Pt[(size_t)d * n2]);   // exact: |T_d| < 2^24
+        const int sh = beta * (s - 1 - d);                                  // 0 <= sh < 64
+        const unsigned long long tl = (unsigned long long)q << sh;           // low word of q 2^sh
+        const long long th = sh ? (q >> (64 - sh)) : (q >> 63);             // high word (sign-extended)
+        lo += tl;
+        hi += th + (lo < tl ? 1 : 0);
+    }
+    // |hi| < 2^16 is exact in FP64; one rounding of lo, one of the sum
+    double v = fma((double)hi, 18446744073709551616.0, (double)lo);
+    v = ldexp(v, ea[(size_t)o.a * np + r] + eb[(size_t)o.b * np + c] - beta * (s + 1));
     double *C = o.C + e;
-    *C = o.accumulate ? fma(alpha, v, *C) : alpha * v;
+    *C = o.accumulate ? fma(alpha, v, C[0]) : alpha * v;
 }
 
 inline int nblk(long n, int b) { return (int)((n + b - 1) / b); }
@@ -209,21 +221,25 @@ int swj_ozaki_split(cudaStream_t st, bool by_rows, int n, int np, int s, int bet
 
 int swj_ozaki_products(void **handle, cudaStream_t st, int n, int np, int s, int beta, int count,
                        const OzProd *prods, const void *sa_, const int *ea, const void *sb_, const int *eb,
-                       double alpha, float *P, void **ptrs)
+                       double alpha, float *P, void **ptrs, int mode)
 {
     if (count <= 0) return SWJ_OK;
     const __nv_bfloat16 *sa = (const __nv_bfloat16 *)sa_, *sb = (const __nv_bfloat16 *)sb_;
+    const int nall = count * s;
+    const void **pA = (const void **)ptrs, **pB = pA + nall;
+    void **pC = ptrs + 2 * (size_t)nall;
+    if (mode != SWJ_OZ_USE_PTRS) {
+        SWJ_COUNT_LAUNCH();
+        k_oz_ptrs<<<nblk(nall, 256), 256, 0, st>>>(count, s, np, prods, sa, sb, P, pA, pB, pC);
+        SWJ_CUDA_TRY(cudaGetLastError());
+        if (mode == SWJ_OZ_FILL_PTRS) return SWJ_OK;
+    }
     cublasHandle_t h = (cublasHandle_t)*handle;
     if (!h) {
         if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) return SWJ_ECUDA;
         *handle = h;
     }
     if (cublasSetStream(h, st) != CUBLAS_STATUS_SUCCESS) return SWJ_ECUDA;
-    const int nall = count * s;
-    const void **pA = (const void **)ptrs, **pB = pA + nall;
-    void **pC = ptrs + 2 * (size_t)nall;
-    SWJ_COUNT_LAUNCH();
-    k_oz_ptrs<<<nblk(nall, 256), 256, 0, st>>>(count, s, np, prods, sa, sb, P, pA, pB, pC);
     const float one = 1.0f, zero = 0.0f;
     // every T_d^T (np x np, column-major) = B'^T (np x s np) A'^T (s np x np), one call
     if (cublasGemmBatchedEx(h, CUBLAS_OP_N, CUBLAS_OP_N, np, np, s * np, &one, pA, CUDA_R_16BF, np, pB,

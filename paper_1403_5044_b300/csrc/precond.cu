@@ -625,7 +625,7 @@ OzLayout oz_layout(int n1, const PcShape &sh)
     L.bytes_desc = oz_align(L.nptr * sizeof(double *)) + oz_align(L.nptr * sizeof(int)) +
                    oz_align(L.nprod * sizeof(OzProd));
     L.bytes = L.nsa * L.s * n2 * 2 + L.nsb * (2 * L.s - 1) * n2 * 2 + (L.nsa + L.nsb) * L.np * sizeof(int) +
-              L.maxP * per + 3 * L.maxP * L.s * sizeof(void *) + L.bytes_desc;
+              L.maxP * per + 3 * L.nprod * L.s * sizeof(void *) + L.bytes_desc;
     return L;
 }
 
@@ -829,7 +829,7 @@ int swj_pc_setup(swj_ctx *c)
             const size_t p2 = (size_t)L.np * L.np;
             const size_t ozs[] = {L.nsa * L.s * p2 * 2, L.nsb * (2 * L.s - 1) * p2 * 2, L.nsa * L.np * sizeof(int),
                                   L.nsb * L.np * sizeof(int), L.maxP * L.s * p2 * sizeof(float),
-                                  3 * L.maxP * L.s * sizeof(void *), L.bytes_desc};
+                                  3 * L.nprod * L.s * sizeof(void *), L.bytes_desc};
             for (int i = 0; i < 7; ++i) {
                 if (cudaMalloc(ozb[i], ozs[i]) != cudaSuccess) {
                     free_pc(c);
@@ -1032,22 +1032,30 @@ int swj_pc_setup(swj_ctx *c)
                     for (int j = i + 1; j <= kmax; ++j) { zp.push_back(blk(c, q, j, i)); zs.push_back(q * hs + (j - i)); }
                 }
                 o.na = (int)(zp.size() - o.a);
+                // the factors right (S_ik, k >= i + 2) and left (S_ij, j < i) of the
+                // diagonal, one split; their products with inv_i, one batched call
                 o.wb = zp.size();
                 for (int q = 0; q < sh.insts(i); ++q)
                     for (int k = i + 2; k <= kmax; ++k) { zp.push_back(blk(c, q, i, k)); zs.push_back(q * hb + (k - i - 2)); }
                 o.nwb = (int)(zp.size() - o.wb);
-                o.u = zp.size();
-                for (int q = 0; q < sh.insts(i); ++q)
-                    for (int k = i + 1; k <= kmax; ++k) { zp.push_back(wblk(c, q, i, k)); zs.push_back(q * hb + h + (k - i - 1)); }
-                o.nu = (int)(zp.size() - o.u);
                 o.l = zp.size();
                 for (int q = 0; q < sh.insts(i); ++q)
                     for (int j = j0; j < i; ++j) { zp.push_back(blk(c, q, i, j)); zs.push_back(q * hb + 2 * h + (j - j0)); }
                 o.nl = (int)(zp.size() - o.l);
+                o.u = zp.size();
+                for (int q = 0; q < sh.insts(i); ++q)
+                    for (int k = i + 1; k <= kmax; ++k) { zp.push_back(wblk(c, q, i, k)); zs.push_back(q * hb + h + (k - i - 1)); }
+                o.nu = (int)(zp.size() - o.u);
                 o.pwb = zq.size();
                 for (int q = 0; q < sh.insts(i); ++q)
                     for (int k = i + 2; k <= kmax; ++k) zq.push_back({q * hs, q * hb + (k - i - 2), wblk(c, q, i, k), 0});
                 o.cwb = (int)(zq.size() - o.pwb);
+                // L_ij = inv_i S_ij straight into the band: S_ij was split above, the
+                // product reads only the slices
+                o.pl = zq.size();
+                for (int q = 0; q < sh.insts(i); ++q)
+                    for (int j = j0; j < i; ++j) zq.push_back({q * hs, q * hb + 2 * h + (j - j0), blk(c, q, i, j), 0});
+                o.cl = (int)(zq.size() - o.pl);
                 for (int g = 0; g < 2; ++g) {
                     (g ? o.pb2 : o.pb1) = zq.size();
                     for (int q = 0; q < sh.insts(i); ++q)
@@ -1059,11 +1067,6 @@ int swj_pc_setup(swj_ctx *c)
                             }
                     (g ? o.cb2 : o.cb1) = (int)(zq.size() - (g ? o.pb2 : o.pb1));
                 }
-                o.pl = zq.size();
-                for (int q = 0; q < sh.insts(i); ++q)
-                    for (int j = j0; j < i; ++j)
-                        zq.push_back({q * hs, q * hb + 2 * h + (j - j0), c->pc_lt + ((size_t)q * h + (j - j0)) * n2, 0});
-                o.cl = (int)(zq.size() - o.pl);
             }
             if (zp.size() != OL.nptr || zq.size() != OL.nprod) return SWJ_EINVAL;   // layout and lists disagree
             char *base = (char *)c->oz_desc;
@@ -1072,6 +1075,23 @@ int swj_pc_setup(swj_ctx *c)
             SWJ_CUDA_TRY(cudaMemcpyAsync(base + offS, zs.data(), zs.size() * sizeof(int), cudaMemcpyHostToDevice, st));
             SWJ_CUDA_TRY(cudaMemcpyAsync(base + offQ, zq.data(), zq.size() * sizeof(OzProd), cudaMemcpyHostToDevice, st));
             SWJ_CUDA_TRY(cudaStreamSynchronize(st));   // the host lists must outlive the copies
+            // the batched GEMMs' pointer arrays of every call of every step, once:
+            // the call at product-list offset g uses oz_ptrs + 3 s g
+            const OzProd *dq = (const OzProd *)(base + offQ);
+            for (int i = 0; i < Mv; ++i) {
+                const OzStep &o = zo[i];
+                const size_t goff[3] = {o.pwb, o.pb1, o.pb2};
+                const int gcnt[3] = {o.cwb + o.cl, o.cb1, o.cb2};
+                for (int g = 0; g < 3; ++g)
+                    for (int c0 = 0; c0 < gcnt[g]; c0 += (int)OL.maxP) {
+                        const int cc = std::min((int)OL.maxP, gcnt[g] - c0);
+                        const size_t g0 = goff[g] + c0;
+                        const int r_ = swj_ozaki_products(&c->cublas, st, n1, OL.np, OL.s, OL.beta, cc, dq + g0,
+                                                          c->oz_sa, c->oz_ea, c->oz_sb, c->oz_eb, 1.0, c->oz_P,
+                                                          c->oz_ptrs + 3 * (size_t)OL.s * g0, SWJ_OZ_FILL_PTRS);
+                        if (r_) return r_;
+                    }
+            }
         }
         }
         const PcPlan &PL = *(const PcPlan *)c->pc_plan;
@@ -1097,7 +1117,8 @@ int swj_pc_setup(swj_ctx *c)
         // other W_ik, first the three updates step i + 1 of the chain reads
         // (B1, event evB1), then all the others (B2), then replaces block row
         // i's left blocks by L_ij = inv_i S_ij (the forward substitution's
-        // factors; nothing of the set-up reads them after step i - 1).  The
+        // factors; nothing of the set-up reads them after step i - 1; the
+        // sliced path forms them with the W_ik, in one batched call).  The
         // chain waits for B1 of step i - 1 before W_{i,i+1}; every other
         // update a chain product reads was enqueued on the bulk stream before
         // that B1.  Every block receives its updates in the order of the steps,
@@ -1166,25 +1187,19 @@ int swj_pc_setup(swj_ctx *c)
                         const int cc = std::min((int)OL.maxP, n_ - c0);
                         const int r_ = swj_ozaki_products(&c->cublas, sb, n1, OL.np, OL.s, OL.beta, cc,
                                                           zQ + off + c0, c->oz_sa, c->oz_ea, c->oz_sb, c->oz_eb,
-                                                          alpha, c->oz_P, c->oz_ptrs);
+                                                          alpha, c->oz_P, c->oz_ptrs + 3 * (size_t)OL.s * (off + c0),
+                                                          SWJ_OZ_USE_PTRS);
                         if (r_) return r_;
                     }
                     return (int)SWJ_OK;
                 };
-                if ((rc = split(true, o.a, o.na)) || (rc = split(false, o.wb, o.nwb)) ||
-                    (rc = prods(o.pwb, o.cwb, 1.0)) || (rc = split(false, o.u, o.nu)) ||
+                // (the plan lists S_ij, j < i, right after S_ik and L_ij right after W_ik)
+                if ((rc = split(true, o.a, o.na)) || (rc = split(false, o.wb, o.nwb + o.nl)) ||
+                    (rc = prods(o.pwb, o.cwb + o.cl, 1.0)) || (rc = split(false, o.u, o.nu)) ||
                     (rc = prods(o.pb1, o.cb1, -1.0)))
                     return rc;
                 SWJ_CUDA_TRY(cudaEventRecord(evB1[i % 4], sb));
-                if ((rc = prods(o.pb2, o.cb2, -1.0)) || (rc = split(false, o.l, o.nl)) ||
-                    (rc = prods(o.pl, o.cl, 1.0)))
-                    return rc;
-                if (o.cl) {
-                    const int nt = std::min(i, h);
-                    SWJ_COUNT_LAUNCH();
-                    k_copy_blocks<<<dim3(64, nq), 256, 0, sb>>>((size_t)nt * n2, c->pc_lt, (size_t)h * n2,
-                                                                blk(c, 0, i, i - nt), bst);
-                }
+                if ((rc = prods(o.pb2, o.cb2, -1.0))) return rc;
                 continue;
             }
             if ((rc = gemm(sb, i, gWb, 1.0, 0.0))) return rc;

@@ -188,8 +188,12 @@ int arnoldi_device_step(swj_ctx *c, int j, const double *u, const double *Ebase,
     if (rc) return rc;
     SWJ_CUDA_TRY(cudaMemcpy2DAsync(Zj, zst * sizeof(double), c->u_try, ld * sizeof(double),
                                    ld * sizeof(double), nb, cudaMemcpyDeviceToDevice, s));
-    // w = J z_j: exact, or the FD-JVP about (u, Ebase)
-    if (c->opts.jvp == SWJ_JVP_EXACT)
+    // w = J z_j: exact, or the FD-JVP about (u, Ebase).  Refinement steps
+    // (Ebase == nullptr) take the exact product in FP32: a central difference
+    // of FP32 residuals costs as much (two residuals against one tangent) and
+    // is ~100 times less accurate, which leaves one refinement step just short
+    // of the FP64 tolerance.
+    if (c->opts.jvp == SWJ_JVP_EXACT || !Ebase)
         rc = swj_jvp_exact_impl(c, u, c->u_try, c->E_try, prec == SWJ_FP64 ? SWJ_FP64 : SWJ_FP32, act);
     else
         rc = swj_jvp_impl(c, u, Ebase, c->u_try, c->E_try, prec, c->opts.fd_h, act);
@@ -327,12 +331,11 @@ int gmres(swj_ctx *c, int kind, const double *u, const double *Ebase, int prec,
             rc = arnoldi_step(c, kind, j, u, Ebase, prec);
             if (rc) return rc;
             SWJ_CUDA_TRY(cudaStreamSynchronize(s));
-            if (c->opts.jvp == SWJ_JVP_EXACT) {
-                for (int i = 0; i < c->nb; ++i)
+            if (c->opts.jvp == SWJ_JVP_EXACT || !Ebase) {
+                for (int i = 0; st && i < c->nb; ++i)
                     if (step[i]) st[i].exact_jvps++;
             } else {
                 count_residual(st, step, prec);
-                if (!Ebase) count_residual(st, step, prec);   // central difference: two residuals
             }
             for (int i = 0; i < nb; ++i) {
                 if (!step[i]) continue;
@@ -441,9 +444,9 @@ int gmres(swj_ctx *c, int kind, const double *u, const double *Ebase, int prec,
     return SWJ_OK;
 }
 
-// GMRES tolerance of the refinement steps: their central-difference FP32 JVPs
-// are accurate to ~1e-5 relative, so one step can contract the FP64 residual
-// by about that much
+// GMRES tolerance of the refinement steps: their JVPs (exact, FP32 all-pairs
+// part) are accurate to ~1e-7 relative, so one step contracts the FP64
+// residual by about this factor
 constexpr double kRefineEta = 1e-4;
 
 struct Phase {
@@ -478,7 +481,7 @@ int newton_phase(swj_ctx *c, double *u, int prec, double tol, int max_it, Phase 
         if (!any) break;
         rc = set_mask(c, on);
         if (rc) return rc;
-        // refinement: central-difference FP32 JVPs (no FP32 base residual needed)
+        // refinement: exact JVPs with the FP32 all-pairs tangent (no FP32 base residual needed)
         const double *Ebase = refine ? nullptr : c->E_cur;
         const int jprec = refine ? SWJ_FP32 : prec;
         swj_bscale(s, nb, n, nullptr, 0, -1.0, 0, c->E_cur, c->rvec, ld, c->act_d);

@@ -262,10 +262,14 @@ void swj_ozaki_params(int n, int *np, int *beta, int *s);
 // B factors: [s][np][np] + [np]
 int swj_ozaki_split(cudaStream_t st, bool by_rows, int n, int np, int s, int beta, int count,
                     const double *const *mats, const int *slots, void *slices, int *ex);
-// P: count * s * np^2 floats; ptrs: 3 * count * s pointers
+// P: count * s * np^2 floats; ptrs: 3 * count * s pointers (the batched GEMM's
+// A, B, C arrays).  mode: SWJ_OZ_ALL fills ptrs, multiplies and combines;
+// SWJ_OZ_FILL_PTRS only fills ptrs (they depend on prods, sa, sb and P only);
+// SWJ_OZ_USE_PTRS multiplies and combines with ptrs filled before.
+enum { SWJ_OZ_ALL = 0, SWJ_OZ_FILL_PTRS = 1, SWJ_OZ_USE_PTRS = 2 };
 int swj_ozaki_products(void **handle, cudaStream_t st, int n, int np, int s, int beta, int count,
                        const OzProd *prods, const void *sa, const int *ea, const void *sb, const int *eb,
-                       double alpha, float *P, void **ptrs);
+                       double alpha, float *P, void **ptrs, int mode = SWJ_OZ_ALL);
 void swj_cublas_destroy(void *handle);
 void swj_dgemm(cudaStream_t st, int m, int n, int k, double alpha, const double *A, int lda,
                const double *B, int ldb, double beta, double *C, int ldc);
