@@ -150,7 +150,8 @@ k_gj_cluster(int n, double *work_base, size_t wstride, double *out_base, size_t 
 template <int WM>
 __device__ __forceinline__ void gj_eliminate(double *A, int ws, int n, int nc, int k, int kk_own,
                                              const double *__restrict__ col_k,
-                                             const double *__restrict__ rowk, int tid, int nth)
+                                             const double *__restrict__ rowk, int tid, int nth,
+                                             int skip = -1)
 {
     double r[WM];
 #pragma unroll
@@ -160,15 +161,15 @@ __device__ __forceinline__ void gj_eliminate(double *A, int ws, int n, int nc, i
         if (i == k) {
 #pragma unroll
             for (int jj = 0; jj < WM; ++jj)
-                if (jj < nc) Ai[jj] = r[jj];
+                if (jj < nc && jj != skip) Ai[jj] = r[jj];
         } else {
             const double m = col_k[i];
             double v[WM];
 #pragma unroll
-            for (int jj = 0; jj < WM; ++jj) v[jj] = (jj < nc && jj != kk_own) ? Ai[jj] : 0.0;
+            for (int jj = 0; jj < WM; ++jj) v[jj] = (jj < nc && jj != kk_own && jj != skip) ? Ai[jj] : 0.0;
 #pragma unroll
             for (int jj = 0; jj < WM; ++jj)
-                if (jj < nc) Ai[jj] = fma(-m, r[jj], v[jj]);
+                if (jj < nc && jj != skip) Ai[jj] = fma(-m, r[jj], v[jj]);
         }
     }
 }
@@ -397,6 +398,186 @@ k_gj_pipe(int n, const double *in_base, size_t istride, double *out_base, size_t
     cl.sync();
 }
 
+// The same inverse with the columns dealt round-robin (column j on CTA
+// j mod ncta) and a one-step look-ahead: the owner of step k + 1 applies step
+// k to its pivot column k + 1 first, searches the pivot of step k + 1 there,
+// records and publishes it, and only then applies step k to its other
+// columns.  Consecutive steps thus belong to different CTAs, and the chain of
+// publications runs through one column update, one search and one
+// publication per step instead of a whole slice's elimination.  Records,
+// flags, failure and timeout handling are those of k_gj_pipe (a CTA's record
+// for its step k sits in slot k / ncta of its record array); the elimination
+// of every element is the same sequence of operations, so the result is
+// that of k_gj_pipe bit for bit.
+template <int WM>
+__global__ void __launch_bounds__(kGJThreads)
+k_gj_rr(int n, const double *in_base, size_t istride, double *out_base, size_t ostride, int *info)
+{
+    cg::cluster_group cl = cg::this_cluster();
+    const int ncta = (int)cl.num_blocks();
+    const int rank = (int)cl.block_rank();
+    const int mat = blockIdx.x / ncta;
+    const double *in = in_base + (size_t)mat * istride;
+    double *out = out_base + (size_t)mat * ostride;
+    const int w = (n + ncta - 1) / ncta;
+    const int ws = w | 1;                       // odd row stride: conflict-free row-per-thread access
+    const int nc = rank < n ? (n - 1 - rank) / ncta + 1 : 0;   // local columns j = rank + jj ncta
+    extern __shared__ double sm[];
+    double *A = sm;                             // n x w slice (row-major, stride ws)
+    const int rs = n + 2;
+    double *rec = A + (size_t)n * ws;           // w x rs: records of this CTA's steps
+    double *lrec = rec + (size_t)w * rs;        // 2 x rs: copies of other owners' records (by step parity)
+    double *rowk = lrec + 2 * (size_t)rs;       // w
+    int *piv = (int *)(rowk + w);               // n
+    int *sigma = piv + n;                       // n
+    int *ctl = sigma + n;                       // [0] step status, [2..3] prefetch counts by parity
+    unsigned *flag = (unsigned *)(ctl + 4);     // published step count (written by the owners)
+    __shared__ unsigned long long red_k[kGJThreads / 32];
+    __shared__ int red_i[kGJThreads / 32];
+    const int tid = threadIdx.x, nth = blockDim.x;
+    for (int e = tid; e < n * nc; e += nth) {
+        const int i = e / nc, jj = e - i * nc;
+        A[(size_t)i * ws + jj] = in[(size_t)i * n + rank + jj * ncta];
+    }
+    if (tid == 0) {
+        *flag = 0u;
+        ctl[0] = ctl[1] = ctl[2] = ctl[3] = 0;
+    }
+    cl.sync();                                  // flags initialised before any remote store
+    const int npre = 64;
+    const bool prefetch = n <= nth - npre;
+    const bool pre_thread = prefetch && tid >= nth - npre;
+    // record and publish step s of this CTA from its (up to date) local column
+    // s / ncta: pivot = the largest |a_is|, rows s..n-1, first index on ties;
+    // returns the failure code (0, or s + 1 for a zero or non-finite pivot)
+    auto make_record = [&](int s) -> int {
+        const int kk = s / ncta;
+        double *r = rec + (size_t)kk * rs;
+        unsigned long long bk = 0ull;
+        int bi = n;
+        for (int i = s + tid; i < n; i += nth) {
+            const unsigned long long kv = (unsigned long long)__double_as_longlong(fabs(A[(size_t)i * ws + kk]));
+            if (kv > bk || (kv == bk && i < bi)) { bk = kv; bi = i; }
+        }
+        warp_argmax(bk, bi);
+        if ((tid & 31) == 0) { red_k[tid >> 5] = bk; red_i[tid >> 5] = bi; }
+        __syncthreads();
+        if (tid < 32) {
+            unsigned long long kv = (tid < nth / 32) ? red_k[tid] : 0ull;
+            int ii = (tid < nth / 32) ? red_i[tid] : n;
+            warp_argmax(kv, ii);
+            if (tid == 0) {
+                const double pv = (ii < n) ? A[(size_t)ii * ws + kk] : 0.0;
+                const bool good = ii < n && pv != 0.0 && isfinite(pv);
+                ctl[0] = good ? 0 : s + 1;
+                r[s] = pv;
+                r[n] = good ? 1.0 / pv : 0.0;        // one division per step
+                r[n + 1] = (double)(good ? ii : s);
+            }
+        }
+        __syncthreads();
+        const int f = ctl[0];
+        if (!f) {
+            // multipliers after the interchange of rows s and p (values before it)
+            const int p = (int)r[n + 1];
+            for (int i = tid; i < n; i += nth)
+                if (i != s) r[i] = (i == p) ? A[(size_t)s * ws + kk] : A[(size_t)i * ws + kk];
+        }
+        __syncthreads();
+        if (tid < ncta && tid != rank) max_release_cluster(flag, tid, f ? (unsigned)(n + f) : (unsigned)(s + 1));
+        return f;
+    };
+    int fail = 0;
+    if (rank == 0 && n > 0) fail = make_record(0);
+    for (int k = 0; k < n && !fail; ++k) {
+        const int o = k % ncta, kk = k / ncta;
+        const int nk = k + 1, no = nk % ncta;   // the next step and its owner
+        auto prefetch_next = [&]() {
+            if (!pre_thread || nk >= n || no == rank) return;
+            long long it = 0;
+            unsigned v;
+            while ((v = ld_acquire_cluster(flag)) < (unsigned)(nk + 1)) {
+                if (++it > kGJSpinLimit) break;
+            }
+            if (v < (unsigned)(nk + 1) || v > (unsigned)n) return;   // left to the next step
+            const double *orec = cl.map_shared_rank(rec + (size_t)(nk / ncta) * rs, no);
+            double *dst = lrec + (size_t)(nk & 1) * rs;
+            for (int i = tid - (nth - npre); i < rs; i += npre) dst[i] = orec[i];
+            atomicAdd(&ctl[2 + (nk & 1)], 1);
+        };
+        const double *r;
+        if (rank == o) {
+            r = rec + (size_t)kk * rs;
+        } else {
+            double *lr = lrec + (size_t)(k & 1) * rs;
+            if (!(prefetch && ctl[2 + (k & 1)] == npre)) {
+                long long it = 0;
+                unsigned v;
+                while ((v = ld_acquire_cluster(flag)) < (unsigned)(k + 1)) {
+                    if (++it > kGJSpinLimit) break;
+                }
+                int st = 0;
+                if (v < (unsigned)(k + 1)) st = -1;                      // timed out
+                else if (v > (unsigned)n) st = (int)(v - (unsigned)n);    // the owner's pivot failed
+                if (!st) {
+                    const double *orec = cl.map_shared_rank(rec + (size_t)kk * rs, o);
+                    for (int i = tid; i < rs; i += nth) lr[i] = orec[i];
+                }
+                if (__syncthreads_or(st != 0)) { fail = st ? st : -1; break; }
+            }
+            r = lr;
+        }
+        const int p = (int)r[n + 1];
+        const double rp = r[n];
+        const int kk_own = (rank == o) ? kk : -1;
+        if (tid == 0) piv[k] = p;
+        // scaled pivot row and the interchange of rows k and p, every local column
+        for (int jj = tid; jj < nc; jj += nth) {
+            const double a = A[(size_t)p * ws + jj];
+            rowk[jj] = (jj == kk_own) ? rp : a * rp;
+            if (p != k) A[(size_t)p * ws + jj] = A[(size_t)k * ws + jj];
+        }
+        __syncthreads();
+        if (tid == 0 && rank != o) ctl[2 + (k & 1)] = 0;
+        if (nk < n && no == rank) {
+            // look-ahead: step k on the pivot column of step k + 1, then its record
+            const int kk2 = nk / ncta;
+            const double rk = rowk[kk2];
+            for (int i = tid; i < n; i += nth) {
+                double *a = A + (size_t)i * ws + kk2;
+                *a = (i == k) ? rk : fma(-r[i], rk, *a);
+            }
+            __syncthreads();
+            const int f = make_record(nk);
+            if (f) { fail = f; break; }
+            if (!pre_thread) gj_eliminate<WM>(A, ws, n, nc, k, kk_own, r, rowk, tid, nth, kk2);
+        } else {
+            if (pre_thread) prefetch_next();
+            else gj_eliminate<WM>(A, ws, n, nc, k, kk_own, r, rowk, tid, nth);
+        }
+        __syncthreads();
+    }
+    // every CTA keeps its shared memory until all have read what they need
+    cl.sync();
+    if (!fail) {
+        if (tid == 0) {
+            for (int j = 0; j < n; ++j) sigma[j] = j;
+            for (int k = n - 1; k >= 0; --k) {
+                int p = piv[k];
+                int t = sigma[k]; sigma[k] = sigma[p]; sigma[p] = t;
+            }
+            for (int j = 0; j < n; ++j) piv[sigma[j]] = j;
+        }
+        __syncthreads();
+        for (int e = tid; e < n * nc; e += nth) {
+            const int i = e / nc, jj = e - i * nc;
+            out[(size_t)i * n + piv[rank + jj * ncta]] = A[(size_t)i * ws + jj];
+        }
+    }
+    if (rank == 0 && tid == 0) info[mat] = fail;
+    cl.sync();
+}
+
 // 16 CTAs per cluster where the device runs such clusters (a non-portable
 // size), else the portable 8.  The kernel's dynamic shared-memory limit must
 // already be at least `smem` (the occupancy query fails for a size above it).
@@ -463,13 +644,17 @@ size_t gj_smem_bytes(int n, int cs)
 
 
 // Instances of the blocked Gauss-Jordan kernel by maximum slice width.
+// Up to 12 columns per CTA the panel kernel is faster (its owner's steps need
+// no exchange; measured set-up 181x61: 20.1 ms against 21.7 with k_gj_rr), from
+// 16 on the round-robin one (361x121: 149 against 162 ms: a panel owner's
+// elimination of its wider slice is on the critical path every step).
 static const void *gj_blocked_kernel(int w)
 {
     if (w <= 8) return (const void *)k_gj_pipe<8>;
     if (w <= 12) return (const void *)k_gj_pipe<12>;
-    if (w <= 16) return (const void *)k_gj_pipe<16>;
-    if (w <= 24) return (const void *)k_gj_pipe<24>;
-    return (const void *)k_gj_pipe<32>;
+    if (w <= 16) return (const void *)k_gj_rr<16>;
+    if (w <= 24) return (const void *)k_gj_rr<24>;
+    return (const void *)k_gj_rr<32>;
 }
 
 // Cluster size of the blocked kernel for n x n blocks (0: it does not apply).
