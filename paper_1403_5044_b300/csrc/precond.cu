@@ -476,7 +476,6 @@ void free_pc(swj_ctx *c)
 {
     delete_plan(c->pc_plan);
     c->pc_plan = nullptr;
-    c->pc_mc_ok = 0;
     double **bufs[] = {&c->pc_Ainv, &c->pc_AinvB1, &c->pc_CAinv, &c->pc_G1, &c->pc_A, &c->pc_B1,
                        &c->pc_C, &c->pc_invF2, &c->pc_band, &c->pc_W, &c->pc_sumK3, &c->pc_t1,
                        &c->pc_t2, &c->pc_z, &c->pc_work, &c->pc_lt, &c->pc_mc_buf, &c->pc_nd_buf,
@@ -1250,29 +1249,32 @@ int swj_pc_setup(swj_ctx *c)
     // them
     //  (two-sided order: both halves at once where ni + h - 1 = h + 1 clusters fit,
     //  else one half at a time)
-    //  (settled once per allocation of the buffers: pc_mc_ok = mode + 1)
-    c->pc_mc = c->pc_mc_ok ? c->pc_mc_ok - 1 : 0;
-    if (!c->pc_mc_ok && c->pc_mc_buf &&
-        swj_band_sweep_mc(st, n1, Mv, h, c->pc_band, c->pc_W, nullptr, nullptr, nullptr, nullptr, nullptr,
-                          nullptr, true) == SWJ_OK) {
+    //  (a launch with empty row ranges only checks that the clusters form; it
+    //  runs at every set-up, since a profiler that replays launches one by one
+    //  may break them up at any time)
+    c->pc_mc = 0;
+    if (c->pc_mc_buf && swj_band_sweep_mc(st, n1, Mv, h, c->pc_band, c->pc_W, nullptr, nullptr, nullptr, nullptr,
+                                          nullptr, nullptr, true) == SWJ_OK) {
         int best = 1;
         if (sh.nd && swj_band_sweep_mc_ranges(st, n1, Mv, h, 2, nullptr, 0, nullptr, 0, nullptr, nullptr, nullptr,
                                               0, nullptr, nullptr, 0, nullptr, true, 0, 0, -1, 0) == SWJ_OK)
             best = 2;
+        const size_t per = (size_t)Mv * n1, sst = per * (h + 1);
+        double *zv = c->pc_mc_buf, *cf = zv + nv * per, *cb = cf + nv * sst;
         for (int mode = best; mode >= 1 && !c->pc_mc; --mode) {
-            SWJ_CUDA_TRY(cudaMemsetAsync(c->pc_t2, 0, (size_t)c->H * sizeof(double), st));
+            const int ni = mode == 2 ? 2 : 1;
             SWJ_CUDA_TRY(cudaMemsetAsync(c->pc_mc_err, 0, sizeof(int), st));
-            int rc = sh.nd ? nd_solve(c, c->pc_t2, c->pc_t1, mode) : mc_solve(c, c->pc_t1);
+            int rc = swj_band_sweep_mc_ranges(st, n1, Mv, h, ni, c->pc_band, bst, c->pc_W, (size_t)Mv * h * n2,
+                                              c->pc_z, zv, zv, per, cf, cb, sst, c->pc_mc_err, false, 0, 0, -1, 0);
             int err = 1;
             if (rc == SWJ_OK) {
                 SWJ_CUDA_TRY(cudaMemcpyAsync(&err, c->pc_mc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
                 SWJ_CUDA_TRY(cudaStreamSynchronize(st));
             }
-            if (rc == SWJ_OK && err == 0) c->pc_mc = mode;
+            if (rc == SWJ_OK && err == 0) c->pc_mc = sh.nd ? mode : 1;
         }
         SWJ_CUDA_TRY(cudaMemsetAsync(c->pc_mc_err, 0, sizeof(int), st));
     }
-    c->pc_mc_ok = c->pc_mc + 1;
     c->pc_ready = 1;
     return SWJ_OK;
 }

@@ -141,7 +141,6 @@ struct swj_ctx {
                                  // separator blocks of D [h][h][n1][n1], separator sums [h][n1]
     double **pc_ptrs;            // device pointer arrays for batched block GEMMs
     void *pc_plan;               // host plan of the band LU's block products (precond.cu)
-    int pc_mc_ok;                // 0: not settled yet, else the apply mode + 1 the set-up settled
     int pc_ptrs_cap;
     double *pc_t1, *pc_t2, *pc_z;   // apply temporaries [nb][H]
     double *pc_work;             // Gauss-Jordan work copies [nb][(h == 0 ? M : 1)][n1][n1]
