@@ -727,6 +727,206 @@ k_pairs_ff(int T_, int S_, int chunk, int N, const SrcRec64 *__restrict__ src, T
     }
 }
 
+// ------------------------------------------------------- float-float, packed
+// The same float-float arithmetic on two targets at once: every value of a
+// target pair is an ff2 (the hi and lo floats of both targets, each a float2)
+// and every error-free transformation is the packed instruction
+// (__fadd2_rn, __fmul2_rn, __ffma2_rn: one rounding per lane, as the scalar
+// intrinsics), so each lane computes what k_pairs_ff computes for its target
+// over the same sources, with half the FP32 instructions (the source chunking
+// follows from the kernel's occupancy, as for every variant).  Subtractions
+// are an FMA with -1 (exact product, one rounding).
+struct ff2 {
+    float2 h, l;
+};
+
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+
+__device__ __forceinline__ ff2 ff2_fast2(float2 a, float2 b)
+{
+    const float2 s = __fadd2_rn(a, b);
+    return {s, sub2(b, sub2(s, a))};
+}
+
+__device__ __forceinline__ ff2 ff2_two_sum(float2 a, float2 b)
+{
+    const float2 s = __fadd2_rn(a, b);
+    const float2 bb = sub2(s, a);
+    return {s, __fadd2_rn(sub2(a, sub2(s, bb)), sub2(b, bb))};
+}
+
+__device__ __forceinline__ ff2 ff2_add(ff2 a, ff2 b)
+{
+    const ff2 s = ff2_two_sum(a.h, b.h);
+    return ff2_fast2(s.h, __fadd2_rn(s.l, __fadd2_rn(a.l, b.l)));
+}
+
+__device__ __forceinline__ ff2 ff2_addf(ff2 a, float2 b)   // b exact
+{
+    const ff2 s = ff2_two_sum(a.h, b);
+    return ff2_fast2(s.h, __fadd2_rn(s.l, a.l));
+}
+
+__device__ __forceinline__ ff2 ff2_add_acc(ff2 a, ff2 b)
+{
+    const ff2 s = ff2_two_sum(a.h, b.h);
+    const ff2 t = ff2_two_sum(a.l, b.l);
+    const ff2 u = ff2_fast2(s.h, __fadd2_rn(s.l, t.h));
+    return ff2_fast2(u.h, __fadd2_rn(u.l, t.l));
+}
+
+__device__ __forceinline__ ff2 ff2_neg(ff2 a)
+{
+    return {make_float2(-a.h.x, -a.h.y), make_float2(-a.l.x, -a.l.y)};
+}
+
+__device__ __forceinline__ ff2 ff2_mul(ff2 a, ff2 b)
+{
+    const float2 p = __fmul2_rn(a.h, b.h);
+    float2 e = __ffma2_rn(a.h, b.h, make_float2(-p.x, -p.y));
+    e = __ffma2_rn(a.h, b.l, e);
+    e = __ffma2_rn(a.l, b.h, e);
+    return ff2_fast2(p, e);
+}
+
+__device__ __forceinline__ ff2 ff2_mulf(ff2 a, float2 b)   // b exact
+{
+    const float2 p = __fmul2_rn(a.h, b);
+    float2 e = __ffma2_rn(a.h, b, make_float2(-p.x, -p.y));
+    e = __ffma2_rn(a.l, b, e);
+    return ff2_fast2(p, e);
+}
+
+__device__ __forceinline__ ff2 ff2_rsqrt(ff2 x)
+{
+    const float2 y = make_float2(rsqrt_ftz(x.h.x), rsqrt_ftz(x.h.y));
+    const ff2 t = ff2_mulf(ff2_mulf(x, y), y);
+    const float2 r = sub2(sub2(make_float2(1.f, 1.f), t.h), t.l);
+    return ff2_fast2(y, __fmul2_rn(__fmul2_rn(make_float2(0.5f, 0.5f), y), r));
+}
+
+__device__ __forceinline__ ff2 ff2_bc(ff v) { return {make_float2(v.h, v.h), make_float2(v.l, v.l)}; }
+
+// source record of the packed kernel: every field broadcast to both lanes
+struct __align__(16) SrcFF2 {
+    ff2 x, z, zx, zy, g, w, zxw;
+};
+
+// RP packed pairs of targets per thread (target 2m + h of the thread is
+// tb + (2m + h) 128, in lane h of pair m); otherwise k_pairs_ff.
+template <int RP>
+__global__ void __launch_bounds__(128)
+k_pairs_ff2(int T_, int S_, int chunk, int N, const SrcRec64 *__restrict__ src, TgtArrays64 tg,
+            double *__restrict__ partial, const int *__restrict__ act)
+{
+    constexpr int TILE = 128;
+    const int inst = blockIdx.z;
+    if (!SWJ_INST_ACTIVE(act, inst)) return;
+    {
+        const size_t ot = (size_t)inst * T_;
+        src += (size_t)inst * S_;
+        tg.x += ot; tg.y += ot; tg.zeta += ot; tg.g += ot; tg.zxw += ot; tg.A += ot; tg.B += ot; tg.C += ot;
+        partial += (size_t)inst * gridDim.y * T_;
+    }
+    __shared__ SrcFF2 sh[TILE];
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int s0 = blockIdx.y * chunk;
+    const int s1 = min(S_, s0 + chunk);
+    ff2 ntx[RP], ntz[RP], ntg[RP], ntzw[RP], A[RP], B[RP], C[RP], sum[RP];
+    float2 ty[RP], dy[RP], mdyp[RP], dy2[RP], dyp2[RP];
+    ff2 Bdy[RP], mBdyp[RP], Cdy2[RP], Cdyp2[RP];
+    const int tb = blockIdx.x * 2 * RP * nth + tid;
+    auto pair = [&](const double *a, int ta, int tc, bool neg) {
+        const ff u = ff_from(neg ? -a[ta] : a[ta]), v = ff_from(neg ? -a[tc] : a[tc]);
+        return ff2{make_float2(u.h, v.h), make_float2(u.l, v.l)};
+    };
+#pragma unroll
+    for (int m = 0; m < RP; ++m) {
+        const int ta = min(tb + 2 * m * nth, T_ - 1), tc = min(tb + (2 * m + 1) * nth, T_ - 1);
+        ntx[m] = pair(tg.x, ta, tc, true); ntz[m] = pair(tg.zeta, ta, tc, true);
+        ntg[m] = pair(tg.g, ta, tc, true); ntzw[m] = pair(tg.zxw, ta, tc, true);
+        A[m] = pair(tg.A, ta, tc, false); B[m] = pair(tg.B, ta, tc, false); C[m] = pair(tg.C, ta, tc, false);
+        ty[m] = make_float2((float)tg.y[ta], (float)tg.y[tc]);
+        sum[m] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    }
+    int row = -1;
+    for (int base = s0; base < s1; base += TILE) {
+        const int nt = min(TILE, s1 - base);
+        __syncthreads();
+        for (int i = tid; i < nt; i += nth) {
+            const SrcRec64 q = src[base + i];
+            SrcFF2 r;
+            r.x = ff2_bc(ff_from(q.x)); r.z = ff2_bc(ff_from(q.zeta)); r.zx = ff2_bc(ff_from(q.zx));
+            r.zy = ff2_bc(ff_from(q.zy)); r.g = ff2_bc(ff_from(q.g)); r.w = ff2_bc(ff_from(q.w));
+            r.zxw = ff2_bc(ff_from(q.zxw));
+            sh[i] = r;
+        }
+        __syncthreads();
+        int j = base / N;
+        int row_end = (j + 1) * N - base;
+        for (int sb = 0; sb < nt; sb += kSub) {
+            const int se = min(sb + kSub, nt);
+            ff2 loc[RP];
+#pragma unroll
+            for (int m = 0; m < RP; ++m) loc[m] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+            int s = sb;
+            while (s < se) {
+                while (s >= row_end) { ++j; row_end += N; }
+                if (j != row) {
+                    row = j;
+#pragma unroll
+                    for (int m = 0; m < RP; ++m) {
+                        dy[m] = make_float2((float)j - ty[m].x, (float)j - ty[m].y);        // exact (integers)
+                        mdyp[m] = make_float2(-(float)j - ty[m].x, -(float)j - ty[m].y);    // -(y_j + y*)
+                        dy2[m] = make_float2(dy[m].x * dy[m].x, dy[m].y * dy[m].y);
+                        dyp2[m] = make_float2(mdyp[m].x * mdyp[m].x, mdyp[m].y * mdyp[m].y);
+                        Bdy[m] = ff2_mulf(B[m], dy[m]);
+                        mBdyp[m] = ff2_mulf(B[m], mdyp[m]);
+                        Cdy2[m] = ff2_mulf(C[m], dy2[m]);
+                        Cdyp2[m] = ff2_mulf(C[m], dyp2[m]);
+                    }
+                }
+                const int send = min(se, row_end);
+#pragma unroll 1
+                for (; s < send; ++s) {
+                    const SrcFF2 q = sh[s];
+#pragma unroll
+                    for (int m = 0; m < RP; ++m) {
+                        const ff2 p = ff2_add(q.x, ntx[m]);
+                        const ff2 dz = ff2_add(q.z, ntz[m]);
+                        const ff2 bs = ff2_add(ff2_mul(p, p), ff2_mul(dz, dz));
+                        const ff2 r1s = ff2_addf(bs, dy2[m]);
+                        const ff2 r2s = ff2_addf(bs, dyp2[m]);
+                        const ff2 nc = ff2_add(dz, ff2_neg(ff2_mul(p, q.zx)));
+                        const ff2 n1 = ff2_add(nc, ff2_neg(ff2_mulf(q.zy, dy[m])));
+                        const ff2 n2 = ff2_add(nc, ff2_mulf(q.zy, mdyp[m]));
+                        const ff2 i1 = ff2_rsqrt(r1s), i2 = ff2_rsqrt(r2s);
+                        const ff2 i1c = ff2_mul(ff2_mul(i1, i1), i1), i2c = ff2_mul(ff2_mul(i2, i2), i2);
+                        const ff2 K1 = ff2_add(ff2_mul(n1, i1c), ff2_mul(n2, i2c));
+                        const ff2 K2 = ff2_add(i1, i2);
+                        const ff2 Ap = ff2_mul(A[m], p);
+                        const ff2 Q1 = ff2_add(ff2_mul(ff2_add(Ap, Bdy[m]), p), Cdy2[m]);
+                        const ff2 Q2 = ff2_add(ff2_mul(ff2_add(Ap, mBdyp[m]), p), Cdyp2[m]);
+                        const ff2 S2 = ff2_add(ff2_rsqrt(Q1), ff2_rsqrt(Q2));
+                        const ff2 f = ff2_add(q.g, ntg[m]);
+                        const ff2 inner =
+                            ff2_add(ff2_add(ff2_mul(q.zxw, K2), ff2_mul(f, K1)), ff2_mul(ntzw[m], S2));
+                        loc[m] = ff2_add(loc[m], ff2_mul(q.w, inner));
+                    }
+                }
+            }
+#pragma unroll
+            for (int m = 0; m < RP; ++m) sum[m] = ff2_add_acc(sum[m], loc[m]);
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < RP; ++m) {
+        const int ta = tb + 2 * m * nth, tc = tb + (2 * m + 1) * nth;
+        if (ta < T_) partial[(size_t)blockIdx.y * T_ + ta] = (double)sum[m].h.x + (double)sum[m].l.x;
+        if (tc < T_) partial[(size_t)blockIdx.y * T_ + tc] = (double)sum[m].h.y + (double)sum[m].l.y;
+    }
+}
+
 // Source-chunk count P for (tiles) target tiles: (tiles x P) blocks should fill
 // whole waves of `slots` resident blocks; chunks keep at least 64 sources.
 PairPlan make_plan(int T, int S, int slots, int tpb, int R, int v)
@@ -789,6 +989,14 @@ void launch_ff(dim3 g, cudaStream_t st, int T_, int S_, int chunk, int N, const 
                                      partial, act);
 }
 
+template <int RP>
+void launch_ff2(dim3 g, cudaStream_t st, int T_, int S_, int chunk, int N, const void *src,
+                const void *tg, double *partial, const int *act)
+{
+    k_pairs_ff2<RP><<<g, 128, 0, st>>>(T_, S_, chunk, N, (const SrcRec64 *)src, *(const TgtArrays64 *)tg,
+                                       partial, act);
+}
+
 template <int R>
 void launch_r64(dim3 g, cudaStream_t st, int T_, int S_, int chunk, int N, const void *src,
                 const void *tg, double *partial, const int *act)
@@ -846,9 +1054,11 @@ const PairVariant kVar64[] = {
     {(const void *)k_pairs_s<double, 4>, 128, 4, ScalarLaunch<double, 4, 128>::go, "k_pairs_s<double,4>"},
 };
 const PairVariant kVarFF[] = {
+    {(const void *)k_pairs_ff2<1>, 128, 2, launch_ff2<1>, "k_pairs_ff2<1>"},
     {(const void *)k_pairs_ff<2>, 128, 2, launch_ff<2>, "k_pairs_ff<2>"},
     {(const void *)k_pairs_ff<1>, 128, 1, launch_ff<1>, "k_pairs_ff<1>"},
     {(const void *)k_pairs_ff<4>, 128, 4, launch_ff<4>, "k_pairs_ff<4>"},
+    {(const void *)k_pairs_ff2<2>, 128, 4, launch_ff2<2>, "k_pairs_ff2<2>"},
 };
 constexpr int kNVar32 = sizeof(kVar32) / sizeof(kVar32[0]);
 constexpr int kNVar64 = sizeof(kVar64) / sizeof(kVar64[0]);
