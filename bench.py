@@ -789,7 +789,7 @@ def main():
         return
     if args.large:
         if args.block_bw == BLOCK_BW:
-            args.block_bw = 7
+            args.block_bw = -1   # the library's rule: 15 at 241 block rows
         run_large(args)
     elif args.serve:
         if args.serve_requests == 64:
