@@ -196,6 +196,143 @@ template <> struct TanCfg<float> { static constexpr int tile = 256; static const
 template <> struct TanCfg<double> { static constexpr int tile = 128; static constexpr bool kahan = false; };
 constexpr int kTanSub = 64;   // sources per compensated sub-tile
 
+// FP32 tangent pair sum on packed instructions: RP pairs of targets per
+// thread (target 2m + h of the thread is tb + (2m + h) 128, in lane h of pair
+// m), each formula of k_pairs_tan<float> as paired FFMA2/FMUL2/FADD2 with the
+// source values broadcast to both lanes (negated copies where a formula
+// subtracts them); the reciprocal square roots stay scalar.
+struct __align__(16) TanX2 {
+    float2 x, y, z, nzx, nzy, g, w, zxw, nzxw, dz, ndzx, ndzy, dg, dzxw;
+};
+
+__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 rsq2(float2 v) { return make_float2(rsq(v.x), rsq(v.y)); }
+
+template <int RP>
+__global__ void __launch_bounds__(128)
+k_pairs_tan_x2(int T_, int S_, int chunk, const SrcRecS<float> *__restrict__ src,
+               const SrcRecS<float> *__restrict__ dsrc, TgtArraysS<float> tg, TgtArraysS<float> dtg,
+               double *__restrict__ partial, const int *__restrict__ act)
+{
+    constexpr int TILE = 256;
+    const int inst = blockIdx.z;
+    if (!SWJ_INST_ACTIVE(act, inst)) return;
+    {
+        const size_t ot = (size_t)inst * T_;
+        src += (size_t)inst * S_;
+        dsrc += (size_t)inst * S_;
+        tg.x += ot; tg.y += ot; tg.zeta += ot; tg.g += ot; tg.zxw += ot; tg.A += ot; tg.B += ot; tg.C += ot;
+        dtg.zeta += ot; dtg.g += ot; dtg.zxw += ot; dtg.A += ot; dtg.B += ot; dtg.C += ot;
+        partial += (size_t)inst * gridDim.y * T_;
+    }
+    __shared__ TanX2 sh[TILE];
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int s0 = blockIdx.y * chunk, s1 = min(S_, s0 + chunk);
+    float2 ntx[RP], nty[RP], ty[RP], ntz[RP], ndtz[RP], ntg[RP], ndtg[RP], ntzw[RP], ndtzw[RP];
+    float2 A[RP], B[RP], nB[RP], C[RP], dA[RP], dB[RP], ndB[RP], dC[RP], sum[RP], comp[RP];
+    const int tb = blockIdx.x * 2 * RP * nth + tid;
+#pragma unroll
+    for (int m = 0; m < RP; ++m) {
+        const int ta = min(tb + 2 * m * nth, T_ - 1), tc = min(tb + (2 * m + 1) * nth, T_ - 1);
+        ntx[m] = make_float2(-tg.x[ta], -tg.x[tc]);
+        ty[m] = make_float2(tg.y[ta], tg.y[tc]);
+        nty[m] = make_float2(-tg.y[ta], -tg.y[tc]);
+        ntz[m] = make_float2(-tg.zeta[ta], -tg.zeta[tc]);
+        ndtz[m] = make_float2(-dtg.zeta[ta], -dtg.zeta[tc]);
+        ntg[m] = make_float2(-tg.g[ta], -tg.g[tc]);
+        ndtg[m] = make_float2(-dtg.g[ta], -dtg.g[tc]);
+        ntzw[m] = make_float2(-tg.zxw[ta], -tg.zxw[tc]);
+        ndtzw[m] = make_float2(-dtg.zxw[ta], -dtg.zxw[tc]);
+        A[m] = make_float2(tg.A[ta], tg.A[tc]);
+        B[m] = make_float2(tg.B[ta], tg.B[tc]);
+        nB[m] = make_float2(-tg.B[ta], -tg.B[tc]);
+        C[m] = make_float2(tg.C[ta], tg.C[tc]);
+        dA[m] = make_float2(dtg.A[ta], dtg.A[tc]);
+        dB[m] = make_float2(dtg.B[ta], dtg.B[tc]);
+        ndB[m] = make_float2(-dtg.B[ta], -dtg.B[tc]);
+        dC[m] = make_float2(dtg.C[ta], dtg.C[tc]);
+        sum[m] = bc2(0.f);
+        comp[m] = bc2(0.f);
+    }
+    const float2 m1 = bc2(-1.f), m3 = bc2(-3.f), mh = bc2(-0.5f);
+    for (int base = s0; base < s1; base += TILE) {
+        const int nt = min(TILE, s1 - base);
+        __syncthreads();
+        for (int i = tid; i < nt; i += nth) {
+            const SrcRecS<float> q = src[base + i], d = dsrc[base + i];
+            TanX2 r;
+            r.x = bc2(q.x); r.y = bc2(q.y); r.z = bc2(q.zeta); r.nzx = bc2(-q.zx); r.nzy = bc2(-q.zy);
+            r.g = bc2(q.g); r.w = bc2(q.w); r.zxw = bc2(q.zxw); r.nzxw = bc2(-q.zxw);
+            r.dz = bc2(d.zeta); r.ndzx = bc2(-d.zx); r.ndzy = bc2(-d.zy); r.dg = bc2(d.g); r.dzxw = bc2(d.zxw);
+            sh[i] = r;
+        }
+        __syncthreads();
+        for (int sb = 0; sb < nt; sb += kTanSub) {
+            const int se = min(sb + kTanSub, nt);
+            float2 loc[RP];
+#pragma unroll
+            for (int m = 0; m < RP; ++m) loc[m] = bc2(0.f);
+            for (int s = sb; s < se; ++s) {
+                const TanX2 q = sh[s];
+#pragma unroll
+                for (int m = 0; m < RP; ++m) {
+                    const float2 p = __fadd2_rn(q.x, ntx[m]);
+                    const float2 qq = __fadd2_rn(q.y, nty[m]), qp = __fadd2_rn(q.y, ty[m]);
+                    const float2 dz = __fadd2_rn(q.z, ntz[m]), ddz = __fadd2_rn(q.dz, ndtz[m]);
+                    const float2 p2 = __fmul2_rn(p, p);
+                    const float2 bs = __ffma2_rn(dz, dz, p2);
+                    const float2 r1s = __ffma2_rn(qq, qq, bs), r2s = __ffma2_rn(qp, qp, bs);
+                    const float2 nc = __ffma2_rn(p, q.nzx, dz);
+                    const float2 n1 = __ffma2_rn(qq, q.nzy, nc), n2 = __ffma2_rn(qp, q.nzy, nc);
+                    const float2 dnc = __ffma2_rn(p, q.ndzx, ddz);
+                    const float2 dn1 = __ffma2_rn(qq, q.ndzy, dnc), dn2 = __ffma2_rn(qp, q.ndzy, dnc);
+                    const float2 i1 = rsq2(r1s), i2 = rsq2(r2s);
+                    const float2 i1s = __fmul2_rn(i1, i1), i2s = __fmul2_rn(i2, i2);
+                    const float2 i1c = __fmul2_rn(i1s, i1), i2c = __fmul2_rn(i2s, i2);
+                    const float2 e = __fmul2_rn(dz, ddz);
+                    const float2 a1 = __fmul2_rn(n1, i1c), a2 = __fmul2_rn(n2, i2c);
+                    const float2 K1 = __fadd2_rn(a1, a2);
+                    const float2 dK1 = __ffma2_rn(__fmul2_rn(m3, e), __ffma2_rn(a1, i1s, __fmul2_rn(a2, i2s)),
+                                                  __ffma2_rn(dn1, i1c, __fmul2_rn(dn2, i2c)));
+                    const float2 K2 = __fadd2_rn(i1, i2);
+                    const float2 eK = __fmul2_rn(e, __fadd2_rn(i1c, i2c));   // -dK2
+                    const float2 Ap2 = __fmul2_rn(A[m], p2), Bp = __fmul2_rn(B[m], p), nBp = __fmul2_rn(nB[m], p);
+                    const float2 dAp2 = __fmul2_rn(dA[m], p2), dBp = __fmul2_rn(dB[m], p),
+                                 ndBp = __fmul2_rn(ndB[m], p);
+                    const float2 Q1 = __ffma2_rn(__ffma2_rn(C[m], qq, Bp), qq, Ap2);
+                    const float2 Q2 = __ffma2_rn(__ffma2_rn(C[m], qp, nBp), qp, Ap2);
+                    const float2 dQ1 = __ffma2_rn(__ffma2_rn(dC[m], qq, dBp), qq, dAp2);
+                    const float2 dQ2 = __ffma2_rn(__ffma2_rn(dC[m], qp, ndBp), qp, dAp2);
+                    const float2 j1 = rsq2(Q1), j2 = rsq2(Q2);
+                    const float2 S2 = __fadd2_rn(j1, j2);
+                    const float2 j1c = __fmul2_rn(__fmul2_rn(j1, j1), j1), j2c = __fmul2_rn(__fmul2_rn(j2, j2), j2);
+                    const float2 dS2 = __fmul2_rn(mh, __ffma2_rn(j1c, dQ1, __fmul2_rn(j2c, dQ2)));
+                    const float2 f = __fadd2_rn(q.g, ntg[m]), df = __fadd2_rn(q.dg, ndtg[m]);
+                    float2 inner = __ffma2_rn(q.dzxw, K2, __fmul2_rn(q.nzxw, eK));
+                    inner = __ffma2_rn(df, K1, inner);
+                    inner = __ffma2_rn(f, dK1, inner);
+                    inner = __ffma2_rn(ndtzw[m], S2, inner);
+                    inner = __ffma2_rn(ntzw[m], dS2, inner);
+                    loc[m] = __ffma2_rn(q.w, inner, loc[m]);
+                }
+            }
+#pragma unroll
+            for (int m = 0; m < RP; ++m) {
+                const float2 y = __ffma2_rn(comp[m], m1, loc[m]);
+                const float2 t2 = __fadd2_rn(sum[m], y);
+                comp[m] = __ffma2_rn(y, m1, __ffma2_rn(sum[m], m1, t2));
+                sum[m] = t2;
+            }
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < RP; ++m) {
+        const int ta = tb + 2 * m * nth, tc = tb + (2 * m + 1) * nth;
+        if (ta < T_) partial[(size_t)blockIdx.y * T_ + ta] = (double)sum[m].x - (double)comp[m].x;
+        if (tc < T_) partial[(size_t)blockIdx.y * T_ + tc] = (double)sum[m].y - (double)comp[m].y;
+    }
+}
+
 // The sum over sources of the pair tangents above, per target and source
 // chunk (grid: target tiles x chunks x instances; R targets per thread in
 // registers, sources with their tangents through shared memory).
@@ -335,8 +472,8 @@ int swj_jvp_exact_impl(swj_ctx *c, const double *u, const double *v, double *Jv,
                                                       c->ttgt64, c->partial, act);
     } else {
         if (pl.R != 4 || pl.tpb != 128) return SWJ_EINVAL;
-        k_pairs_tan<float, 4><<<grid, 128, 0, st>>>(c->T, c->S, pl.chunk, c->src32, c->tsrc32, c->tgt32,
-                                                     c->ttgt32, c->partial, act);
+        k_pairs_tan_x2<2><<<grid, 128, 0, st>>>(c->T, c->S, pl.chunk, c->src32, c->tsrc32, c->tgt32,
+                                                 c->ttgt32, c->partial, act);
     }
     swj_launch_assemble(c, Jv, pl.P, act, c->de2part);
     SWJ_CUDA_TRY(cudaGetLastError());
