@@ -146,30 +146,59 @@ k_gj_cluster(int n, double *work_base, size_t wstride, double *out_base, size_t 
 // One elimination step on a CTA's slice (rows over threads, WM >= nc columns
 // per row held in registers): row k <- rowk, every other row i <- row i -
 // col_k[i] rowk, with the pivot column's own entry (local index kk_own, or
-// -1 if it is not in this slice) starting from zero.
+// -1 if it is not in this slice) starting from zero.  Only the local columns
+// lo..nc-1 other than `skip` are touched.
 template <int WM>
 __device__ __forceinline__ void gj_eliminate(double *A, int ws, int n, int nc, int k, int kk_own,
                                              const double *__restrict__ col_k,
                                              const double *__restrict__ rowk, int tid, int nth,
-                                             int skip = -1)
+                                             int skip = -1, int lo = 0)
 {
     double r[WM];
 #pragma unroll
-    for (int jj = 0; jj < WM; ++jj) r[jj] = (jj < nc) ? rowk[jj] : 0.0;
+    for (int jj = 0; jj < WM; ++jj) r[jj] = (jj >= lo && jj < nc) ? rowk[jj] : 0.0;
     for (int i = tid; i < n; i += nth) {
         double *Ai = A + (size_t)i * ws;
         if (i == k) {
 #pragma unroll
             for (int jj = 0; jj < WM; ++jj)
-                if (jj < nc && jj != skip) Ai[jj] = r[jj];
+                if (jj >= lo && jj < nc && jj != skip) Ai[jj] = r[jj];
         } else {
             const double m = col_k[i];
             double v[WM];
 #pragma unroll
-            for (int jj = 0; jj < WM; ++jj) v[jj] = (jj < nc && jj != kk_own && jj != skip) ? Ai[jj] : 0.0;
+            for (int jj = 0; jj < WM; ++jj)
+                v[jj] = (jj >= lo && jj < nc && jj != kk_own && jj != skip) ? Ai[jj] : 0.0;
 #pragma unroll
             for (int jj = 0; jj < WM; ++jj)
-                if (jj < nc && jj != skip) Ai[jj] = fma(-m, r[jj], v[jj]);
+                if (jj >= lo && jj < nc && jj != skip) Ai[jj] = fma(-m, r[jj], v[jj]);
+        }
+    }
+}
+
+// The same step on the local columns lo..hi-1 only, with a loop over just
+// those columns: each FP64 instruction of a warp occupies its SM sub-partition
+// for ~64 cycles on B300, predicated off or not, so a slice's unrolled
+// register loop costs WM FMAs per row however few columns are live.  Same
+// arithmetic per element as gj_eliminate (no pivot column among lo..hi-1).
+__device__ __forceinline__ void gj_eliminate_cols(double *A, int ws, int n, int k, int lo, int hi,
+                                                  const double *__restrict__ col_k,
+                                                  const double *__restrict__ rowk, int tid, int nth)
+{
+    if (lo >= hi) return;
+    for (int i = tid; i < n; i += nth) {
+        double *Ai = A + (size_t)i * ws;
+        if (i == k) {
+            for (int jj = lo; jj < hi; ++jj) Ai[jj] = rowk[jj];
+        } else {
+            const double m = col_k[i];
+            int jj = lo;
+            for (; jj + 1 < hi; jj += 2) {
+                const double a0 = Ai[jj], a1 = Ai[jj + 1];
+                Ai[jj] = fma(-m, rowk[jj], a0);
+                Ai[jj + 1] = fma(-m, rowk[jj + 1], a1);
+            }
+            if (jj < hi) Ai[jj] = fma(-m, rowk[jj], Ai[jj]);
         }
     }
 }
@@ -215,8 +244,12 @@ constexpr long long kGJSpinLimit = 1ll << 26;
 // steps k = 0..n-1 are owned by the CTA holding column k.  The owner searches
 // the pivot in its (up to date) column, records the step (pivot row, the
 // multiplier column after the interchange, the reciprocal pivot) in its own
-// shared memory, raises a release flag in every other CTA and eliminates its
-// slice; it goes on to its next step at once.  Every other CTA waits for the
+// shared memory, raises a release flag in every other CTA and eliminates the
+// columns of its slice right of the pivot; it goes on to its next step at
+// once, and applies its panel's steps to the rest of its slice after the
+// panel (column by column the same operations in the same order, so the
+// result is that of eliminating the whole slice at every step).  Every other
+// CTA waits for the
 // flag of step k (acquire), reads the step from the owner's shared memory and
 // applies it to its slice.  Steps are applied in order everywhere, so the
 // arithmetic is that of the unblocked elimination; no CTA waits for the
@@ -288,31 +321,30 @@ k_gj_pipe(int n, const double *in_base, size_t istride, double *out_base, size_t
             atomicAdd(&ctl[2 + (nk & 1)], 1);
         };
         if (rank == o) {
-            // pivot: the largest |a_ik|, rows k..n-1 of local column kk, first index
-            // on ties (non-negative doubles order as their bit patterns)
-            unsigned long long bk = 0ull;
-            int bi = n;
-            for (int i = k + tid; i < n; i += nth) {
-                const unsigned long long kv =
-                    (unsigned long long)__double_as_longlong(fabs(A[(size_t)i * ws + kk]));
-                if (kv > bk || (kv == bk && i < bi)) { bk = kv; bi = i; }
-            }
-            warp_argmax(bk, bi);
-            if ((tid & 31) == 0) { red_k[tid >> 5] = bk; red_i[tid >> 5] = bi; }
-            __syncthreads();
+            // pivot: the largest |a_ik|, rows k..n-1 of local column kk, first index on
+            // ties (non-negative doubles order as their bit patterns), searched by one
+            // warp; a zero or non-finite pivot is told by its bit pattern and the pivot
+            // row travels as the integer bits of a double: B300 takes 60-400 cycles for
+            // each dependent FP64 compare, conversion or division, and these steps are
+            // the kernel's critical path
             if (tid < 32) {
-                unsigned long long kv = (tid < nth / 32) ? red_k[tid] : 0ull;
-                int ii = (tid < nth / 32) ? red_i[tid] : n;
-                warp_argmax(kv, ii);
+                unsigned long long bk = 0ull;
+                int bi = n;
+                for (int i = k + tid; i < n; i += 32) {
+                    const unsigned long long kv =
+                        (unsigned long long)__double_as_longlong(A[(size_t)i * ws + kk]) & 0x7FFFFFFFFFFFFFFFull;
+                    if (kv > bk || (kv == bk && i < bi)) { bk = kv; bi = i; }
+                }
+                warp_argmax(bk, bi);
                 if (tid == 0) {
-                    const double pv = (ii < n) ? A[(size_t)ii * ws + kk] : 0.0;
-                    const bool good = ii < n && pv != 0.0 && isfinite(pv);
-                    piv[k] = good ? ii : k;
+                    const double pv = (bi < n) ? A[(size_t)bi * ws + kk] : 0.0;
+                    const bool good = bi < n && bk != 0ull && (bk >> 52) < 0x7FFull;
+                    piv[k] = good ? bi : k;
                     ctl[0] = good ? 0 : k + 1;
                     double *r = rec + (size_t)kk * rs;
                     r[k] = pv;
                     r[n] = good ? 1.0 / pv : 0.0;        // one division per step
-                    r[n + 1] = (double)(good ? ii : k);
+                    r[n + 1] = __longlong_as_double((long long)(good ? bi : k));
                 }
             }
             __syncthreads();
@@ -321,23 +353,48 @@ k_gj_pipe(int n, const double *in_base, size_t istride, double *out_base, size_t
             double *r = rec + (size_t)kk * rs;
             const double rp = r[n];
             if (!f) {
-                // interchange rows k and p, scaled pivot row, multipliers (pre-interchange
-                // values: row k is not written in this phase, row p only by its own column)
-                for (int jj = tid; jj < nc; jj += nth) {
+                // interchange rows k and p and scale the pivot row in the columns right of
+                // the pivot; multipliers (pre-interchange values: row k is not written in
+                // this phase, and the pivot column not at all)
+                for (int jj = kk + 1 + tid; jj < nc; jj += nth) {
                     const double v = A[(size_t)p * ws + jj];
-                    rowk[jj] = (jj == kk) ? rp : v * rp;
+                    rowk[jj] = v * rp;
                     if (p != k) A[(size_t)p * ws + jj] = A[(size_t)k * ws + jj];
                 }
                 for (int i = tid; i < n; i += nth)
                     if (i != k) r[i] = (i == p) ? A[(size_t)k * ws + kk] : A[(size_t)i * ws + kk];
             }
             __syncthreads();
-            // publish step k (or the failure) to every other CTA
-            if (tid < ncta && tid != rank) max_release_cluster(flag, tid, f ? (unsigned)(n + f) : (unsigned)(k + 1));
+            // publish step k (or the failure) to every other CTA, from the last warp: its
+            // remote release takes ~800 cycles, which the elimination of the other warps
+            // hides (the last warp prefetches, it eliminates no rows)
+            const int pl = tid - (nth - 32);
+            if (pl >= 0 && pl < ncta && pl != rank) max_release_cluster(flag, pl, f ? (unsigned)(n + f) : (unsigned)(k + 1));
             if (f) { fail = f; break; }
+            // Within its panel the owner eliminates only the columns right of the pivot,
+            // which its next searches read; the pivot column and those left of it get
+            // the panel's steps after the panel, each column still in step order.
             if (pre_thread) prefetch_next();
-            else gj_eliminate<WM>(A, ws, n, nc, k, kk, r, rowk, tid, nth);
+            else gj_eliminate_cols(A, ws, n, k, kk + 1, nc, r, rowk, tid, nth);
             __syncthreads();
+            if (kk == nc - 1) {
+                const int k0 = k - kk;
+                for (int ks = 0; ks <= kk; ++ks) {
+                    // step k0 + ks on local columns 0..ks (ks: its own pivot column)
+                    const int s = k0 + ks;
+                    const double *rs_ = rec + (size_t)ks * rs;
+                    const int ps = (int)__double_as_longlong(rs_[n + 1]);
+                    const double rps = rs_[n];
+                    for (int jj = tid; jj <= ks; jj += nth) {
+                        const double v = A[(size_t)ps * ws + jj];
+                        rowk[jj] = (jj == ks) ? rps : v * rps;
+                        if (ps != s && jj != ks) A[(size_t)ps * ws + jj] = A[(size_t)s * ws + jj];
+                    }
+                    __syncthreads();
+                    gj_eliminate<WM>(A, ws, n, ks + 1, s, ks, rs_, rowk, tid, nth);
+                    __syncthreads();
+                }
+            }
         } else {
             double *lr = lrec + (size_t)(k & 1) * rs;
             if (!(prefetch && ctl[2 + (k & 1)] == npre)) {
@@ -358,7 +415,7 @@ k_gj_pipe(int n, const double *in_base, size_t istride, double *out_base, size_t
                 // the CTA stops if any thread timed out or saw the owner's failure
                 if (__syncthreads_or(st != 0)) { fail = st ? st : -1; break; }
             }
-            const int p = (int)lr[n + 1];
+            const int p = (int)__double_as_longlong(lr[n + 1]);
             const double rp = lr[n];
             if (tid == 0) piv[k] = p;
             for (int jj = tid; jj < nc; jj += nth) {
