@@ -283,8 +283,6 @@ k_gj_pipe(int n, const double *in_base, size_t istride, double *out_base, size_t
     int *sigma = piv + n;                       // n
     int *ctl = sigma + n;                       // [0] step status, [2..3] prefetch counts by parity
     unsigned *flag = (unsigned *)(ctl + 4);     // published step count (written by the owners)
-    __shared__ unsigned long long red_k[kGJThreads / 32];
-    __shared__ int red_i[kGJThreads / 32];
     const int tid = threadIdx.x, nth = blockDim.x;
     for (int e = tid; e < n * nc; e += nth) {
         const int i = e / nc, jj = e - i * nc;
@@ -303,6 +301,7 @@ k_gj_pipe(int n, const double *in_base, size_t istride, double *out_base, size_t
     const bool prefetch = n <= nth - npre;
     const bool pre_thread = prefetch && tid >= nth - npre;
     int fail = 0;
+    bool ahead = false;                         // this step's pivot already searched
     for (int k = 0; k < n && !fail; ++k) {
         const int o = k / w, kk = k - o * w;
         const int nk = k + 1, no = nk / w;      // the next step and its owner
@@ -320,33 +319,35 @@ k_gj_pipe(int n, const double *in_base, size_t istride, double *out_base, size_t
             for (int i = tid - (nth - npre); i < rs; i += npre) dst[i] = orec[i];
             atomicAdd(&ctl[2 + (nk & 1)], 1);
         };
-        if (rank == o) {
-            // pivot: the largest |a_ik|, rows k..n-1 of local column kk, first index on
-            // ties (non-negative doubles order as their bit patterns), searched by one
-            // warp; a zero or non-finite pivot is told by its bit pattern and the pivot
-            // row travels as the integer bits of a double: B300 takes 60-400 cycles for
-            // each dependent FP64 compare, conversion or division, and these steps are
-            // the kernel's critical path
-            if (tid < 32) {
-                unsigned long long bk = 0ull;
-                int bi = n;
-                for (int i = k + tid; i < n; i += 32) {
-                    const unsigned long long kv =
-                        (unsigned long long)__double_as_longlong(A[(size_t)i * ws + kk]) & 0x7FFFFFFFFFFFFFFFull;
-                    if (kv > bk || (kv == bk && i < bi)) { bk = kv; bi = i; }
-                }
-                warp_argmax(bk, bi);
-                if (tid == 0) {
-                    const double pv = (bi < n) ? A[(size_t)bi * ws + kk] : 0.0;
-                    const bool good = bi < n && bk != 0ull && (bk >> 52) < 0x7FFull;
-                    piv[k] = good ? bi : k;
-                    ctl[0] = good ? 0 : k + 1;
-                    double *r = rec + (size_t)kk * rs;
-                    r[k] = pv;
-                    r[n] = good ? 1.0 / pv : 0.0;        // one division per step
-                    r[n + 1] = __longlong_as_double((long long)(good ? bi : k));
-                }
+        // pivot of step ks in local column kks (warp 0 of the owner): the largest
+        // |a_ik|, rows ks..n-1, first index on ties (non-negative doubles order as
+        // their bit patterns); a zero or non-finite pivot is told by its bit pattern
+        // and the pivot row travels as the integer bits of a double: B300 takes
+        // 60-400 cycles for each dependent FP64 compare, conversion or division, and
+        // these steps are the kernel's critical path
+        auto search = [&](int ks, int kks) {
+            unsigned long long bk = 0ull;
+            int bi = n;
+            for (int i = ks + tid; i < n; i += 32) {
+                const unsigned long long kv =
+                    (unsigned long long)__double_as_longlong(A[(size_t)i * ws + kks]) & 0x7FFFFFFFFFFFFFFFull;
+                if (kv > bk || (kv == bk && i < bi)) { bk = kv; bi = i; }
             }
+            warp_argmax(bk, bi);
+            if (tid == 0) {
+                const double pv = (bi < n) ? A[(size_t)bi * ws + kks] : 0.0;
+                const bool good = bi < n && bk != 0ull && (bk >> 52) < 0x7FFull;
+                piv[ks] = good ? bi : ks;
+                ctl[0] = good ? 0 : ks + 1;
+                double *r = rec + (size_t)kks * rs;
+                r[ks] = pv;
+                r[n] = good ? 1.0 / pv : 0.0;        // one division per step
+                r[n + 1] = __longlong_as_double((long long)(good ? bi : ks));
+            }
+        };
+        if (rank == o) {
+            // (searched at the end of the previous step when that was this panel's too)
+            if (!ahead && tid < 32) search(k, kk);
             __syncthreads();
             const int f = ctl[0];
             const int p = piv[k];
@@ -373,9 +374,19 @@ k_gj_pipe(int n, const double *in_base, size_t istride, double *out_base, size_t
             if (f) { fail = f; break; }
             // Within its panel the owner eliminates only the columns right of the pivot,
             // which its next searches read; the pivot column and those left of it get
-            // the panel's steps after the panel, each column still in step order.
-            if (pre_thread) prefetch_next();
-            else gj_eliminate_cols(A, ws, n, k, kk + 1, nc, r, rowk, tid, nth);
+            // the panel's steps after the panel, each column still in step order.  The
+            // next pivot column comes first, then warp 0 searches the next step's pivot
+            // while the other warps eliminate the remaining columns (rows over them).
+            if (kk + 1 < nc) {
+                if (tid >= 32) gj_eliminate_cols(A, ws, n, k, kk + 1, kk + 2, r, rowk, tid - 32, nth - 32);
+                __syncthreads();
+                if (tid < 32) search(k + 1, kk + 1);
+                else gj_eliminate_cols(A, ws, n, k, kk + 2, nc, r, rowk, tid - 32, nth - 32);
+                ahead = true;
+            } else {
+                if (pre_thread) prefetch_next();
+                ahead = false;
+            }
             __syncthreads();
             if (kk == nc - 1) {
                 const int k0 = k - kk;
@@ -385,13 +396,16 @@ k_gj_pipe(int n, const double *in_base, size_t istride, double *out_base, size_t
                     const double *rs_ = rec + (size_t)ks * rs;
                     const int ps = (int)__double_as_longlong(rs_[n + 1]);
                     const double rps = rs_[n];
-                    for (int jj = tid; jj <= ks; jj += nth) {
+                    for (int jj = tid; jj < ks; jj += nth) {
                         const double v = A[(size_t)ps * ws + jj];
-                        rowk[jj] = (jj == ks) ? rps : v * rps;
-                        if (ps != s && jj != ks) A[(size_t)ps * ws + jj] = A[(size_t)s * ws + jj];
+                        rowk[jj] = v * rps;
+                        if (ps != s) A[(size_t)ps * ws + jj] = A[(size_t)s * ws + jj];
                     }
                     __syncthreads();
-                    gj_eliminate<WM>(A, ws, n, ks + 1, s, ks, rs_, rowk, tid, nth);
+                    gj_eliminate_cols(A, ws, n, s, 0, ks, rs_, rowk, tid, nth);
+                    // the pivot column itself (entries from zero, as in gj_eliminate)
+                    for (int i = tid; i < n; i += nth)
+                        A[(size_t)i * ws + ks] = (i == s) ? rps : fma(-rs_[i], rps, 0.0);
                     __syncthreads();
                 }
             }
