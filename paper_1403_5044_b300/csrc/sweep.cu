@@ -10,10 +10,14 @@
 //   z_i = p_i - sum_{d=1..h} L_{i,i-d} z_{i-d}              (forward, i = 0..M-1)
 //   x_i = z_i - sum_{e=1..h} W_{i,i+e} x_{i+e}              (backward, i = M-1..0)
 // Only the forward and backward recurrences are sequential.  Every block
-// product is a set of row dots computed by block_dot (one warp per row, one
-// fixed order of operations), and every recurrence subtracts them nearest
-// block first, so the single-cluster and the multi-cluster sweeps below
-// return identical bits.
+// product is a set of row dots (one warp per row, one fixed order of
+// operations).  A recurrence row keeps the nearest block's dot as 32 lane
+// partials, adds the farther blocks' finished dots into lanes 2, 3, ... (the
+// block at distance d into lane d), sums the lanes with one butterfly and
+// subtracts the sum: on B300 every FP64 instruction of a warp holds its SM
+// sub-partition for ~64 cycles, so one butterfly instead of a subtraction per
+// block matters on the sequential path.  The single-cluster and the
+// multi-cluster sweeps below do exactly this and return identical bits.
 #include "swj_internal.h"
 #include <map>
 #include <mutex>
@@ -101,7 +105,7 @@ __device__ __forceinline__ double warp_sum(double a)
 // columns l, l + 32, ... with FMAs in that order, then a butterfly sum; every
 // lane returns the result.
 template <int KC>
-__device__ __forceinline__ double block_dot(const double *row, const double *v, int n1, int lane)
+__device__ __forceinline__ double block_dot_partial(const double *row, const double *v, int n1, int lane)
 {
     double x[KC];
 #pragma unroll
@@ -115,7 +119,13 @@ __device__ __forceinline__ double block_dot(const double *row, const double *v, 
         const int c = lane + 32 * k;
         if (c < n1) a = fma(x[k], v[c], a);
     }
-    return warp_sum(a);
+    return a;
+}
+
+template <int KC>
+__device__ __forceinline__ double block_dot(const double *row, const double *v, int n1, int lane)
+{
+    return warp_sum(block_dot_partial<KC>(row, v, n1, lane));
 }
 
 // Two dots at once (the loads of both in flight together), each with exactly
@@ -144,23 +154,29 @@ __device__ __forceinline__ void block_dot2(const double *row0, const double *v0,
     s1 = warp_sum(a1);
 }
 
-// v - sum_{q=0..nt-1} dot(row q, vector q), subtracted in the order q = 0, 1, ...
-// Rows at base + q bstride (global memory; bstride may be negative), vectors
-// at vs + q n1 (shared).
+// v - sum_{q=0..nt-1} dot(row q, vector q) in the recurrences' order: the
+// lane partials of dot 0, dot q (q >= 1, finished) added into lane q + 1, one
+// butterfly, one subtraction.  Rows at base + q bstride (global memory;
+// bstride may be negative), vectors at vs + q n1 (shared).
 template <int KC>
 __device__ __forceinline__ double sub_dots(double v, const double *base, long long bstride, const double *vs,
                                            int nt, int n1, int lane)
 {
-    int q = 0;
+    if (nt == 0) return v - warp_sum(0.0);
+    double a = block_dot_partial<KC>(base, vs, n1, lane);
+    int q = 1;
     for (; q + 1 < nt; q += 2) {
         double s0, s1;
         block_dot2<KC>(base + q * bstride, vs + (size_t)q * n1, base + (q + 1) * bstride,
                        vs + (size_t)(q + 1) * n1, n1, lane, s0, s1);
-        v -= s0;
-        v -= s1;
+        if (lane == q + 1) a += s0;
+        if (lane == q + 2) a += s1;
     }
-    if (q < nt) v -= block_dot<KC>(base + q * bstride, vs + (size_t)q * n1, n1, lane);
-    return v;
+    if (q < nt) {
+        const double s0 = block_dot<KC>(base + q * bstride, vs + (size_t)q * n1, n1, lane);
+        if (lane == q + 1) a += s0;
+    }
+    return v - warp_sum(a);
 }
 
 // p_i = inv_i t_i for every block row of every active instance (one warp per
@@ -407,11 +423,11 @@ k_band_sweep_mc(int n1, int M, int h, int ni, int hsets, const double *__restric
                 const int rr = warp + q * nw;
                 if (q >= rpw || rr >= nr) break;
                 const int r = r0 + rr;
-                double v = zs[(size_t)i * rows + rr];
+                double a = 0.0;
                 if (t > 0 || fpre)
-                    v -= block_dot<KC>(rb + ((size_t)(t & 1) * rows + rr) * n1, vz + (size_t)((t - 1) & 1) * n1, n1, lane);
-                if (lane >= 2 && lane <= nd) cur[q] = poll(cf + ((size_t)i * hs + lane) * n1 + r, cur[q]);
-                for (int d = 2; d <= nd; ++d) v -= __shfl_sync(0xffffffffu, cur[q], d);
+                    a = block_dot_partial<KC>(rb + ((size_t)(t & 1) * rows + rr) * n1, vz + (size_t)((t - 1) & 1) * n1, n1, lane);
+                if (lane >= 2 && lane <= nd) a += (cur[q] = poll(cf + ((size_t)i * hs + lane) * n1 + r, cur[q]));
+                const double v = zs[(size_t)i * rows + rr] - warp_sum(a);
                 if (lane == 0) {
                     st_relaxed(z + (size_t)i * n1 + r, v);
                     zs[(size_t)i * rows + rr] = v;
@@ -448,11 +464,11 @@ k_band_sweep_mc(int n1, int M, int h, int ni, int hsets, const double *__restric
                 const int rr = warp + q * nw;
                 if (q >= rpw || rr >= nr) break;
                 const int r = r0 + rr;
-                double v = zs[(size_t)i * rows + rr];
+                double a = 0.0;
                 if (t > 0 || bpre)
-                    v -= block_dot<KC>(rb + ((size_t)(t & 1) * rows + rr) * n1, vx + (size_t)((t - 1) & 1) * n1, n1, lane);
-                if (lane >= 2 && lane <= ne) cur[q] = poll(cb + ((size_t)i * hs + lane) * n1 + r, cur[q]);
-                for (int e = 2; e <= ne; ++e) v -= __shfl_sync(0xffffffffu, cur[q], e);
+                    a = block_dot_partial<KC>(rb + ((size_t)(t & 1) * rows + rr) * n1, vx + (size_t)((t - 1) & 1) * n1, n1, lane);
+                if (lane >= 2 && lane <= ne) a += (cur[q] = poll(cb + ((size_t)i * hs + lane) * n1 + r, cur[q]));
+                const double v = zs[(size_t)i * rows + rr] - warp_sum(a);
                 if (lane == 0) st_relaxed(x + (size_t)i * n1 + r, v);
                 send(vx + (size_t)(t & 1) * n1, &mbx[t & 1], r, v);
             }
