@@ -203,6 +203,29 @@ __device__ __forceinline__ void gj_eliminate_cols(double *A, int ws, int n, int 
     }
 }
 
+// One row's share of a step: the cnt columns at Ai (rowk entries at rk), W >=
+// cnt held in registers; the pivot row takes rowk, the others subtract m rowk
+// (the arithmetic of gj_eliminate with fewer index tests per row).
+template <int W>
+__device__ __forceinline__ void gj_elim_row(double *Ai, bool pivot_row, double m, const double *rk, int cnt)
+{
+    double r[W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) r[j] = (j < cnt) ? rk[j] : 0.0;
+    if (pivot_row) {
+#pragma unroll
+        for (int j = 0; j < W; ++j)
+            if (j < cnt) Ai[j] = r[j];
+    } else {
+        double v[W];
+#pragma unroll
+        for (int j = 0; j < W; ++j) v[j] = (j < cnt) ? Ai[j] : 0.0;
+#pragma unroll
+        for (int j = 0; j < W; ++j)
+            if (j < cnt) Ai[j] = fma(-m, r[j], v[j]);
+    }
+}
+
 // Flag helpers for the pipelined Gauss-Jordan kernel: a release max-update of
 // a word in another CTA's shared memory (a max, not a store: updates from two
 // successive owners may land in either order, the flag must never go back)
@@ -442,7 +465,12 @@ k_gj_pipe(int n, const double *in_base, size_t istride, double *out_base, size_t
             // buffer is free again for the step after next
             if (tid == 0) ctl[2 + (k & 1)] = 0;
             if (pre_thread) prefetch_next();
-            else gj_eliminate<WM>(A, ws, n, nc, k, -1, lr, rowk, tid, nth);
+            else if (n <= nth - npre) {
+                // one row per thread (all rows fit the non-prefetching warps)
+                if (tid < n) gj_elim_row<WM>(A + (size_t)tid * ws, tid == k, tid == k ? 0.0 : lr[tid], rowk, nc);
+            } else {
+                gj_eliminate<WM>(A, ws, n, nc, k, -1, lr, rowk, tid, nth);
+            }
             __syncthreads();
         }
     }
