@@ -531,8 +531,6 @@ k_gj_rr(int n, const double *in_base, size_t istride, double *out_base, size_t o
     int *sigma = piv + n;                       // n
     int *ctl = sigma + n;                       // [0] step status, [2..3] prefetch counts by parity
     unsigned *flag = (unsigned *)(ctl + 4);     // published step count (written by the owners)
-    __shared__ unsigned long long red_k[kGJThreads / 32];
-    __shared__ int red_i[kGJThreads / 32];
     const int tid = threadIdx.x, nth = blockDim.x;
     for (int e = tid; e < n * nc; e += nth) {
         const int i = e / nc, jj = e - i * nc;
@@ -552,33 +550,31 @@ k_gj_rr(int n, const double *in_base, size_t istride, double *out_base, size_t o
     auto make_record = [&](int s) -> int {
         const int kk = s / ncta;
         double *r = rec + (size_t)kk * rs;
-        unsigned long long bk = 0ull;
-        int bi = n;
-        for (int i = s + tid; i < n; i += nth) {
-            const unsigned long long kv = (unsigned long long)__double_as_longlong(fabs(A[(size_t)i * ws + kk]));
-            if (kv > bk || (kv == bk && i < bi)) { bk = kv; bi = i; }
-        }
-        warp_argmax(bk, bi);
-        if ((tid & 31) == 0) { red_k[tid >> 5] = bk; red_i[tid >> 5] = bi; }
-        __syncthreads();
+        // (one warp, one level; tests on the bit pattern and the pivot row as
+        // integer bits, as in k_gj_pipe)
         if (tid < 32) {
-            unsigned long long kv = (tid < nth / 32) ? red_k[tid] : 0ull;
-            int ii = (tid < nth / 32) ? red_i[tid] : n;
-            warp_argmax(kv, ii);
+            unsigned long long bk = 0ull;
+            int bi = n;
+            for (int i = s + tid; i < n; i += 32) {
+                const unsigned long long kv =
+                    (unsigned long long)__double_as_longlong(A[(size_t)i * ws + kk]) & 0x7FFFFFFFFFFFFFFFull;
+                if (kv > bk || (kv == bk && i < bi)) { bk = kv; bi = i; }
+            }
+            warp_argmax(bk, bi);
             if (tid == 0) {
-                const double pv = (ii < n) ? A[(size_t)ii * ws + kk] : 0.0;
-                const bool good = ii < n && pv != 0.0 && isfinite(pv);
+                const double pv = (bi < n) ? A[(size_t)bi * ws + kk] : 0.0;
+                const bool good = bi < n && bk != 0ull && (bk >> 52) < 0x7FFull;
                 ctl[0] = good ? 0 : s + 1;
                 r[s] = pv;
                 r[n] = good ? 1.0 / pv : 0.0;        // one division per step
-                r[n + 1] = (double)(good ? ii : s);
+                r[n + 1] = __longlong_as_double((long long)(good ? bi : s));
             }
         }
         __syncthreads();
         const int f = ctl[0];
         if (!f) {
             // multipliers after the interchange of rows s and p (values before it)
-            const int p = (int)r[n + 1];
+            const int p = (int)__double_as_longlong(r[n + 1]);
             for (int i = tid; i < n; i += nth)
                 if (i != s) r[i] = (i == p) ? A[(size_t)s * ws + kk] : A[(size_t)i * ws + kk];
         }
@@ -626,7 +622,7 @@ k_gj_rr(int n, const double *in_base, size_t istride, double *out_base, size_t o
             }
             r = lr;
         }
-        const int p = (int)r[n + 1];
+        const int p = (int)__double_as_longlong(r[n + 1]);
         const double rp = r[n];
         const int kk_own = (rank == o) ? kk : -1;
         if (tid == 0) piv[k] = p;
