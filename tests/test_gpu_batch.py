@@ -144,6 +144,21 @@ def test_batch_64x121x41_mixed_matches_fp64():
     dz = np.abs(z["mixed"] - z["fp64"]).reshape(len(F), -1).max(axis=1)
     assert dz.max() <= 1e-6, dz.max()
     assert all(np.abs(z["fp64"][i]).max() < F[i] ** 2 / 2 for i in range(len(F)))
+    # sampled instances against the oracle's own roots, stored by
+    # tests/golden/make_roots.py (||E||_inf ~ 2e-14)
+    import importlib.util
+    import os
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    sp = importlib.util.spec_from_file_location("make_roots", os.path.join(here, "make_roots.py"))
+    mod = importlib.util.module_from_spec(sp)
+    sp.loader.exec_module(mod)
+    for head, zo, _ in mod.load(os.path.join(here, "oracle_root_121x41_batch.txt")):
+        i = int(head["label"])
+        assert (head["F"], head["eps"]) == (F[i], eps[i])
+        zm = np.asarray(z["mixed"][i]).reshape(spec.M, spec.N)
+        z6 = np.asarray(z["fp64"][i]).reshape(spec.M, spec.N)
+        assert np.abs(z6 - zo).max() <= 1e-8, (i, np.abs(z6 - zo).max())
+        assert np.abs(zm - zo).max() <= 1e-6, (i, np.abs(zm - zo).max())
 
 
 def test_batch_instance_matches_oracle_root():

@@ -199,6 +199,37 @@ def test_181x61_mixed_and_fp64_solves_agree_and_are_oracle_roots():
     assert z64.max() < F ** 2 / 2
 
 
+def _stored_root(name):
+    import importlib.util
+    import os
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    spec_ = importlib.util.spec_from_file_location("make_roots", os.path.join(here, "make_roots.py"))
+    mod = importlib.util.module_from_spec(spec_)
+    spec_.loader.exec_module(mod)
+    return mod.load(os.path.join(here, name))
+
+
+def test_181x61_solves_match_the_stored_oracle_root():
+    """The 181x61 workload against the oracle's own Newton-GMRES root
+    (tests/golden/oracle_root_181x61.txt, ||E||_inf ~ 6e-14): max|d zeta| and
+    max|d phi| <= 1e-8 for the FP64 solve, <= 1e-6 for the mixed solve."""
+    spec, F, eps = W.SOLVE_181x61
+    head, zo, po = _stored_root("oracle_root_181x61.txt")[0]
+    assert (head["N"], head["M"], head["F"], head["eps"]) == (spec.N, spec.M, F, eps)
+    for mode, tol in (("fp64", 1e-8), ("mixed", 1e-6)):
+        with swj.Context.from_spec(spec, F, eps, solve_mode=mode, block_bw=15) as ctx:
+            u = ctx.initial_guess_flat(ctx.vector())
+            st = ctx.solve(u)
+            zeta = torch.empty(spec.N * spec.M, dtype=torch.float64, device="cuda")
+            phi = torch.empty_like(zeta)
+            ctx.unpack(u, zeta, phi)
+            ctx.sync()
+        assert st["rc"] == 0, st
+        dz = np.abs(zeta.cpu().numpy().reshape(spec.M, spec.N) - zo).max()
+        dp = np.abs(phi.cpu().numpy().reshape(spec.M, spec.N) - po).max()
+        assert dz <= tol and dp <= tol, (mode, dz, dp)
+
+
 def test_refinement_precisions_reach_the_same_root():
     """MIXED solves refined with float-float and with FP64 residuals: the same
     FP64 root (the float-float sum is as accurate as FP64), both roots of the
