@@ -5,7 +5,15 @@ F = 0.7, eps = 0.4, flat initial guess, GMRES restart 30.  One step is one
 complete solve: preconditioner set-up, Newton-GMRES with the FP32 all-pairs
 residual, and the FP64 residual refinement down to ||E_fp64||_inf < 1e-9
 (the mixed-precision solve).  The plain FP64 solve of the same workload is
-timed beside it and every mixed result is compared with it (max |d zeta|).
+timed beside it and every mixed result is compared with it and with the
+stored oracle root (max |d zeta|, max |d phi|).
+
+After the timed steps the default run also reports, outside the headline:
+the exact-JVP solve; the 64 x 121x41 batch (mixed and FP64, sampled
+instances against stored oracle roots); the serving workload (mixed: 256
+Poisson requests at the saturated rate, 1.0x and 0.5x of it; FP64, about 37x
+slower per request: 16 requests at its saturated rate and 1.0x); and one
+721x241 solve (eps = 0.8) with its root refined further on FP64 residuals.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -38,33 +46,12 @@ SM_MAX_MHZ = 2032.0
 # default options (measured on the GPU path); the reference arm converts the
 # oracle's residual time into solves/s with it
 RESIDUALS_PER_SOLVE = 21
-# DRAM bytes (read + write) per launch of a pair-kernel shape, from the ncu capture
-# summarised in profiles/k_pairs_fp32_181x61.md (null for a shape not captured)
-PROFILED_TRAFFIC = {
-    "k_pairs_s<float,4>": 727589,
-    "k_pairs_x2<1,256,4>": 721664,
-    "k_pairs_x2<2,128,1>": 724882,
-    "k_pairs_x2<2,128,5>": 740498,
-    "k_pairs_x2<2,128,6>": 722213,
-    "k_pairs_x2<2,256,1>": 716178,
-    "k_pairs_x2<2,256,3>": 719726,
-    "k_pairs_x2<3,128,1>": 731173,
-    "k_pairs_x2<3,256,2>": 723712,
-    "k_pairs_x2<4,128,1>": 724699,
-    "k_pairs_x2<4,64,1>": 724151,
-    "k_pairs_x2r<1,128,8,1,2>": 721335,
-    "k_pairs_x2r<1,256,3,1,2>": 719177,
-    "k_pairs_x2r<1,256,4,1,1>": 716983,
-    "k_pairs_x2r<1,256,4,1,2>": 716946,
-    "k_pairs_x2r<1,256,5,1,1>": 717897,
-    "k_pairs_x2r<2,128,4,0,2>": 917285,
-    "k_pairs_x2r<2,128,4,1,1>": 723127,
-    "k_pairs_x2r<2,256,2,0,1>": 723163,
-    "k_pairs_x2r<2,256,2,0,2>": 720201,
-    "k_pairs_x2r<2,256,2,1,1>": 728864,
-    "k_pairs_x2r<2,256,3,1,1>": 717751,
-    "k_pairs_x2r<3,128,2,1,1>": 723639,
-}
+# committed ncu summary of the FP32 all-pairs kernel's DRAM traffic per tile shape
+# (its header records the hash of the kernel source it was captured from)
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_pairs_fp32_traffic_181x61.txt")
+KERNEL_SOURCE = os.path.join(ROOT, "paper_1403_5044_b300", "csrc", "pairs.cu")
+ORACLE_ROOT_181x61 = os.path.join(ROOT, "tests", "golden", "oracle_root_181x61.txt")
+ORACLE_ROOT_BATCH = os.path.join(ROOT, "tests", "golden", "oracle_root_121x41_batch.txt")
 BLOCK_BW = 15          # block bandwidth of the mixed solves (fastest measured at 181x61)
 FP64_BLOCK_BW = 15     # the FP64 solve's own fastest block bandwidth
 
@@ -79,8 +66,14 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--fp64-block-bw", type=int, default=FP64_BLOCK_BW)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--serve-requests", type=int, default=64,
-                    help="requests of the serving sample in the default run (0 = skip it)")
+    ap.add_argument("--serve-requests", type=int, default=None,
+                    help="requests per rate point of the mixed serving block (default 256, 2000 with --serve; "
+                         "0 = skip it)")
+    ap.add_argument("--serve-requests-fp64", type=int, default=None,
+                    help="requests per rate point of the FP64 serving block (default 16, 64 with --serve; "
+                         "0 = skip it)")
+    ap.add_argument("--large-steps", type=int, default=1,
+                    help="721x241 solves in the default run (0 = skip them)")
     ap.add_argument("--serve", action="store_true",
                     help="only the serving workload: 2000 Poisson requests per rate, rates swept over "
                          "{0.25, 0.5, 0.75, 1.0, 1.25} x the measured saturated rate, mixed and FP64")
@@ -187,6 +180,67 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def source_hash(path):
+    """First 16 hex digits of the SHA-256 of a file (identifies a kernel build)."""
+    import hashlib
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def measured_traffic(shape):
+    """DRAM bytes (read + write) per launch of one tile shape of the FP32
+    all-pairs kernel, from the committed ncu summary: lines
+    '<shape> <bytes>' under a header 'source_sha256_16 <hash>'.  None when
+    the shape was not captured or the kernel source changed since."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            lines = [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
+    except OSError:
+        return None, "no traffic summary"
+    table = {ln[0]: ln[1] for ln in lines if len(ln) == 2}
+    if table.get("source_sha256_16") != source_hash(KERNEL_SOURCE):
+        return None, "kernel source changed since the ncu capture"
+    if shape not in table:
+        return None, "shape not in the ncu capture"
+    return int(table[shape]), "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch of this shape"
+
+
+def load_roots(path):
+    """Stored oracle roots: list of (header dict, zeta [M][N], phi [M][N] or
+    None when the file holds zeta alone)."""
+    import numpy as np
+    blocks = []
+    with open(path) as f:
+        for line in f:
+            if line.startswith("# instance"):
+                head, rest = line[2:].split(":", 1)
+                words = rest.split()
+                N, M = (int(v) for v in words[1].split("x"))
+                kv = {k: float(v) for k, v in (w.split("=") for w in words[2:])}
+                blocks.append({"label": head.split()[1], "N": N, "M": M, **kv, "rows": []})
+            elif line.startswith("# newton_iterations") and blocks:
+                blocks[-1].update({k: float(v) for k, v in (t.split("=") for t in line[2:].split())})
+            elif not line.startswith("#") and line.strip():
+                blocks[-1]["rows"].append([float(v) for v in line.split()])
+    out = []
+    for b in blocks:
+        a = np.array(b.pop("rows")).reshape(b["M"] * b["N"], -1)
+        out.append((b, a[:, 0].reshape(b["M"], b["N"]),
+                    a[:, 1].reshape(b["M"], b["N"]) if a.shape[1] > 1 else None))
+    return out
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.startswith("model name"):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
 def cpu_oracle_residual_rate(seconds):
     """Time the oracle's full FP64 residual of the workload on the host cores;
     returns (seconds per residual, evaluations, cores)."""
@@ -220,8 +274,9 @@ def run_reference(args):
     per = per[args.warmup:]
     t_res = sum(per) / len(per)
     solves_s = 1.0 / (t_res * RESIDUALS_PER_SOLVE)
-    sample = ("each step: one full oracle FP64 residual of the 181x61 workload (%d pairs) on %d host "
-              "threads; solves/s = 1 / (t_residual x %d residual evaluations per solve)"
+    sample = ("a projection, not a timed solve: each step times one full oracle FP64 residual of the "
+              "181x61 workload (%d pairs) on %d host threads; solves/s = 1 / (t_residual x %d residual "
+              "evaluations per solve); the oracle's own LU and Krylov work is not counted"
               % (spec.pairs, cores, RESIDUALS_PER_SOLVE))
     out = {"impl": "reference", "metric": METRIC, "value": solves_s, "unit": "solves/s",
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -229,7 +284,7 @@ def run_reference(args):
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": WORKLOAD, "impl": "CPU oracle (numpy + plain C, OpenMP)"},
            "cpu_baseline": {"value": solves_s, "unit": "solves/s", "cores": cores, "kind": "oracle",
-                            "sample": sample},
+                            "sample": sample, "cpu_model": cpu_model()},
            "e2e": {"value": solves_s, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
            "residual_pairs_per_s": spec.pairs / t_res}
     print(json.dumps(out), flush=True)
@@ -286,13 +341,15 @@ def run_ours(args):
     launches = swj.kernel_launches() - launches0
     pair_ms, pair_n = ctx.pair_timing(swj.FP32)
     pair_name = swj.pair_variant_name(swj.FP32, ctx.pair_config(swj.FP32)[0])
+    traffic, traffic_note = measured_traffic(pair_name)
     pair64_ms, pair64_n = ctx.pair_timing(swj.FP64)
     ctx.set_kernel_timing(False)
     step_ms = [a.elapsed_time(b) for a, b in ev]
     value, total_ms = replica_rate(sum(step_ms), args.steps, world, dist)
-    ctx.unpack(u, zeta, None)
+    phi = torch.empty_like(zeta)
+    ctx.unpack(u, zeta, phi)
     ctx.sync()
-    zeta_mixed = zeta.cpu().numpy()
+    zeta_mixed, phi_mixed = zeta.cpu().numpy(), phi.cpu().numpy()
 
     # ---- plain FP64 solve of the same workload (reference for max|dzeta| and its own rate)
     ctx64 = swj.Context.from_spec(spec, F, eps, solve_mode="fp64", block_bw=args.fp64_block_bw, stream=stream)
@@ -309,9 +366,20 @@ def run_ours(args):
         b.record(stream)
         torch.cuda.synchronize()
         t64.append(a.elapsed_time(b))
-    ctx64.unpack(u64, zeta, None)
+    ctx64.unpack(u64, zeta, phi)
     ctx64.sync()
-    dzeta = float(np.abs(zeta_mixed - zeta.cpu().numpy()).max())
+    zeta64, phi64 = zeta.cpu().numpy(), phi.cpu().numpy()
+    dzeta = float(np.abs(zeta_mixed - zeta64).max())
+    vs_oracle = None
+    if os.path.exists(ORACLE_ROOT_181x61):
+        head, zo, po = load_roots(ORACLE_ROOT_181x61)[0]
+        zo, po = zo.ravel(), po.ravel()
+        vs_oracle = {"root": "oracle Newton-GMRES root, ||E||_inf %.1e (stored, written by the oracle only)"
+                             % head["final_norm_inf"],
+                     "max_abs_dzeta_mixed": float(np.abs(zeta_mixed - zo).max()),
+                     "max_abs_dphi_mixed": float(np.abs(phi_mixed - po).max()),
+                     "max_abs_dzeta_fp64": float(np.abs(zeta64 - zo).max()),
+                     "max_abs_dphi_fp64": float(np.abs(phi64 - po).max())}
 
     # ---- end to end through the public API with host buffers
     u_host = torch.empty(ctx.n_unknowns, dtype=torch.float64).pin_memory()
@@ -338,8 +406,13 @@ def run_ours(args):
 
     batch = run_batch(args, stream, flush) if args.batch_steps > 0 else None
     serve = None
-    if args.serve_requests > 0 and rank == 0:
-        serve = {"mixed": serve_point("mixed", args.serve_requests, 1.0)}
+    if rank == 0 and (args.serve_requests > 0 or args.serve_requests_fp64 > 0):
+        serve = {"workload": SERVE_WORKLOAD}
+        if args.serve_requests > 0:
+            serve["mixed"] = serve_block("mixed", args.serve_requests, [1.0, 0.5])
+        if args.serve_requests_fp64 > 0:
+            serve["fp64"] = serve_block("fp64", args.serve_requests_fp64, [1.0])
+    large = large_section(args) if (rank == 0 and args.large_steps > 0) else None
 
     if rank != 0:
         return
@@ -357,10 +430,11 @@ def run_ours(args):
         dt, n, cores = cpu_oracle_residual_rate(args.cpu_seconds)
         res_per_solve = mean([s["residual_evals"] for s in stats])
         cpu = {"value": 1.0 / (dt * st64["residual_evals"]), "unit": "solves/s", "cores": cores, "kind": "oracle",
-               "sample": "%d full oracle FP64 residuals of the 181x61 workload (%.2f s each, %.3e pairs/s); "
-                         "solves/s = 1 / (t_residual x %d residual evaluations of the FP64 solve)"
+               "sample": "a projection, not a timed solve: %d full oracle FP64 residuals of the 181x61 workload "
+                         "were timed (%.2f s each, %.3e pairs/s) and solves/s = 1 / (t_residual x %d residual "
+                         "evaluations of the FP64 solve); the oracle's own LU and Krylov work is not counted"
                          % (n, dt, pairs / dt, st64["residual_evals"]),
-               "residual_pairs_per_s": pairs / dt}
+               "cpu_model": cpu_model(), "residual_pairs_per_s": pairs / dt}
     out = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -370,8 +444,9 @@ def run_ours(args):
                    "block_bw": args.block_bw, "gmres_restart": 30, "solve": "mixed",
                    "refine_tol_inf": 1e-9, "l2": "flushed (256 MB write) before every step, outside the step time",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "latency_ms": {"p50": statistics.median(step_ms), "p99": float(np.percentile(step_ms, 99)),
-                       "mean": mean(step_ms)},
+        "latency_ms": serve_latency(serve),
+        "solve_ms": {"p50": statistics.median(step_ms), "p99": float(np.percentile(step_ms, 99)),
+                     "mean": mean(step_ms)},
         "solve_stats": {k: s0[k] for k in ("newton_iters", "refine_iters", "residual_evals", "residual_evals_fp64",
                                            "krylov_iters", "precond_applies", "final_norm_inf_fp64", "t_setup_ms")},
         "fp64_solve": {"value": 1e3 / mean(t64), "unit": "solves/s", "ms": mean(t64),
@@ -379,6 +454,7 @@ def run_ours(args):
                        "residual_evals": st64["residual_evals"], "krylov_iters": st64["krylov_iters"],
                        "final_norm_inf": st64["final_norm_inf"]},
         "max_abs_dzeta_mixed_vs_fp64": dzeta,
+        "vs_oracle_root": vs_oracle,
         "speedup_mixed_vs_fp64": value / (1e3 / mean(t64)),
         "residual_pairs_per_s": {"fp32_kernel": pairs / (avg_pair_ms * 1e-3),
                                  "fp64_kernel": pairs / (pair64_ms / max(1, pair64_n) * 1e-3) if pair64_n else None},
@@ -390,7 +466,8 @@ def run_ours(args):
                      "avg_launch_ms": avg_pair_ms, "launches_timed": pair_n,
                      "frac_at_measured_clock": (achieved / (sms * FP32_LANES_PER_SM * 2 * cs["sm_mhz"] * 1e6 / 1e12)
                                                 if cs["sm_mhz"] else None),
-                     "traffic": PROFILED_TRAFFIC.get(pair_name)},
+                     "traffic": traffic, "traffic_source": traffic_note,
+                     "algorithmic_bytes_per_launch": spec.N * spec.M * 32 + (spec.N - 1) * spec.M * 32},
         "roofline_fp64": ({"bound": "alu", "kernel": swj.pair_variant_name(swj.FP64, ctx.pair_config(swj.FP64)[0])
                            + " (FP64 all-pairs sum of the refinement residuals)",
                            "achieved": FLOP_PER_PAIR * pairs / (pair64_ms / pair64_n * 1e-3) / 1e12,
@@ -409,10 +486,20 @@ def run_ours(args):
         "exact_jvp": exact,
         "batch": batch,
         "serve": serve,
+        "large": large,
         "clocks": {"sm_mhz": cs["sm_mhz"], "sm_max_mhz": cs["sm_max_mhz"], "reasons": cs["reasons"]},
         "wall_s_timed": wall,
     }
     print(json.dumps(out), flush=True)
+
+
+def serve_latency(serve):
+    """Headline latency: the mixed serving block at 1.0 x its saturated rate."""
+    if not serve or "mixed" not in serve:
+        return None
+    pt = [p for p in serve["mixed"]["points"] if p["rate_factor"] == 1.0][0]
+    return {**pt["latency_ms"], "source": "serving workload, mixed, %d requests at 1.0 x the saturated rate"
+            % pt["requests"]}
 
 
 TAN_FLOP_PER_PAIR = 88   # tangent pair: 12 add + 24 mul + 26 FMA (FMA = 2) + 4 rsqrt
@@ -528,6 +615,13 @@ def run_batch(args, stream, flush):
                      "effective_pairs_per_s": sum(res) * spec.pairs / (sum(ms) / len(ms) / 1e3)}
         ctx.close()
     out["max_abs_dzeta_mixed_vs_fp64"] = float(np.abs(zeta["mixed"] - zeta["fp64"]).max())
+    if os.path.exists(ORACLE_ROOT_BATCH):
+        roots = load_roots(ORACLE_ROOT_BATCH)
+        idx = [int(h["label"]) for h, _, _ in roots]
+        zo = np.stack([z.ravel() for _, z, _ in roots])
+        out["vs_oracle_root"] = {"instances": idx,
+                                 "max_abs_dzeta_mixed": float(np.abs(zeta["mixed"][idx] - zo).max()),
+                                 "max_abs_dzeta_fp64": float(np.abs(zeta["fp64"][idx] - zo).max())}
     out["speedup_mixed_vs_fp64"] = out["mixed"]["solves_per_s"] / out["fp64"]["solves_per_s"]
     return out
 
@@ -536,52 +630,62 @@ SERVE_WORKLOAD = ("requests on meshes drawn uniformly from {61x21, 121x41, 181x6
                   "x in [-16,20], y in [0,12]; F ~ U[0.5,1], eps ~ U[0.05,0.5]; Poisson arrivals (seed 1403_5045)")
 
 
-def serve_point(mode, count, rate_factor, sat=None):
-    """One point of the serving workload: measure the saturated rate (all
-    `count` requests submitted at once) unless given, then replay `count`
-    Poisson arrivals at rate_factor x that rate.  Latency is submit -> result
-    on the host, measured inside the server."""
+def _serve_summary(reqs, res, rate_factor, offered, span):
     import numpy as np
     from paper_1403_5044_b300 import swj
-    from paper_1403_5044_b300 import workloads as W
-    reqs = W.serve_requests(count=count)
-    kw = dict(max_active=4, max_group=8, block_bw=-1, solve_mode=mode)   # block bandwidth by mesh
-    with swj.Server(**kw) as srv:
-        # warm-up: one request per mesh (creates the kept contexts' first graphs)
-        for m in W.SERVE_MESHES:
-            srv.poll(srv.submit(m, 0.75, 0.25), wait=True)
-        if sat is None:
-            t0 = time.perf_counter()
-            ids = [srv.submit(m, F, eps) for _, m, F, eps in reqs]
-            srv.drain()
-            sat = count / (time.perf_counter() - t0)
-            for i in ids:
-                srv.poll(i, wait=True)
-        rate = rate_factor * sat
-        arrivals = np.array([t for t, *_ in reqs])
-        arrivals = arrivals / arrivals[-1] * (count / rate)      # rescale the stream to `rate`
-        ids = []
-        t0 = time.perf_counter()
-        for (t, m, F, eps), ta in zip(reqs, arrivals):
-            dt = ta - (time.perf_counter() - t0)
-            if dt > 0:
-                time.sleep(dt)
-            ids.append(srv.submit(m, F, eps))
-        srv.drain()
-        span = time.perf_counter() - t0
-        res = [srv.poll(i, wait=True) for i in ids]
-        info = srv.info()
     lat = np.array([r["latency_ms"] for r in res])
     ok = sum(1 for r in res if r["rc"] == swj.OK)
     by_mesh = {}
     for (t, m, F, eps), r in zip(reqs, res):
         by_mesh.setdefault("%dx%d" % (m.N, m.M), []).append(r["latency_ms"])
-    return {"requests": count, "rate_factor": rate_factor, "saturated_solves_per_s": sat,
-            "offered_solves_per_s": rate, "solves_per_s": count / span, "converged": ok,
+    return {"rate_factor": rate_factor, "offered_solves_per_s": offered, "solves_per_s": len(res) / span,
+            "requests": len(res), "converged": ok, "not_converged": len(res) - ok,
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                           "mean": float(lat.mean())},
+                           "mean": float(lat.mean()), "max": float(lat.max())},
             "p50_ms_by_mesh": {k: float(np.median(v)) for k, v in sorted(by_mesh.items())},
-            "mean_group": float(np.mean([r["group_size"] for r in res])),
+            "mean_group": float(np.mean([r["group_size"] for r in res]))}
+
+
+def serve_block(mode, count, rate_factors):
+    """The serving workload in one precision: `count` requests of the Poisson
+    stream (seed 1403_5045) first all submitted at once (the saturated rate,
+    itself a latency point), then replayed at rate_factor x that rate for each
+    factor.  Latency is submit -> result on the host, measured inside the
+    server; requests that did not converge are counted, never dropped."""
+    import numpy as np
+    from paper_1403_5044_b300 import swj
+    from paper_1403_5044_b300 import workloads as W
+    reqs = W.serve_requests(count=count)
+    kw = dict(max_active=4, max_group=8, block_bw=-1, solve_mode=mode)   # block bandwidth by mesh
+    points = []
+    with swj.Server(**kw) as srv:
+        # warm-up: one request per mesh (creates the kept contexts' first graphs)
+        for m in W.SERVE_MESHES:
+            srv.poll(srv.submit(m, 0.75, 0.25), wait=True)
+        t0 = time.perf_counter()
+        ids = [srv.submit(m, F, eps) for _, m, F, eps in reqs]
+        srv.drain()
+        span = time.perf_counter() - t0
+        res = [srv.poll(i, wait=True) for i in ids]
+        sat = count / span
+        points.append(_serve_summary(reqs, res, "saturated", None, span))
+        arrivals = np.array([t for t, *_ in reqs])
+        for f in rate_factors:
+            rate = f * sat
+            ta_all = arrivals / arrivals[-1] * (count / rate)      # rescale the stream to `rate`
+            ids = []
+            t0 = time.perf_counter()
+            for (t, m, F, eps), ta in zip(reqs, ta_all):
+                dt = ta - (time.perf_counter() - t0)
+                if dt > 0:
+                    time.sleep(dt)
+                ids.append(srv.submit(m, F, eps))
+            srv.drain()
+            span = time.perf_counter() - t0
+            res = [srv.poll(i, wait=True) for i in ids]
+            points.append(_serve_summary(reqs, res, f, rate, span))
+        info = srv.info()
+    return {"requests_per_point": count, "saturated_solves_per_s": sat, "points": points,
             "peak_active": info["peak_active"], "peak_bytes_held": info["peak_bytes_held"],
             "contexts_created": info["contexts_created"], "contexts_reused": info["contexts_reused"]}
 
@@ -590,39 +694,39 @@ def run_serve(args):
     import torch
     torch.cuda.set_device(0)
     rates = [float(r) for r in args.serve_rates.split(",")]
-    out = {"serve": True, "workload": SERVE_WORKLOAD, "points": {}}
+    out = {"serve": True, "workload": SERVE_WORKLOAD}
+    counts = {"mixed": args.serve_requests, "fp64": args.serve_requests_fp64}
     for mode in ("mixed", "fp64"):
-        sat = None
-        pts = []
-        for f in rates:
-            p = serve_point(mode, args.serve_requests, f, sat)
-            sat = p["saturated_solves_per_s"]
-            pts.append(p)
-            print(json.dumps({"mode": mode, **p}), flush=True)
-        out["points"][mode] = pts
+        if counts[mode] > 0:
+            out[mode] = serve_block(mode, counts[mode], rates)
+            print(json.dumps({"mode": mode, **out[mode]}), flush=True)
     print(json.dumps(out), flush=True)
 
 
-def run_large(args):
-    """The 721x241 workload: F = 0.7, eps = 0.8 (a steep, near-limiting wave),
-    mixed precision with FP64 GMRES/LU and a float-float refinement, from the
-    flat guess; falls back to eps-continuation 0.2, 0.4, 0.6, 0.8 (Section 5)
-    if the direct solve fails."""
+def large_section(args):
+    """The 721x241 workload (F = 0.7, eps = 0.8, a steep near-limiting wave):
+    one mixed solve from the flat guess (FP32 Newton-GMRES, FP64 GMRES/LU,
+    float-float refinement), its counters, the plain FP64 residual at its
+    root, the crest against the limiting height F^2/2, and max|dzeta|
+    against the same root refined further with FP64 residuals
+    (refine_precision = FP64) down to ||E_fp64||_inf < 1e-11."""
+    import numpy as np
     import torch
     from paper_1403_5044_b300 import swj
     from paper_1403_5044_b300 import workloads as W
     spec, F, eps = W.SOLVE_721x241
-    out = {"large": True, "workload": "ship-wave solve 721x241, F=0.7, eps=0.8 (x in [-16,20], y in [0,12], dx=dy=0.05)",
-           "pairs_per_residual": spec.pairs, "block_bw": args.block_bw}
-    with swj.Context.from_spec(spec, F, eps, solve_mode="mixed", block_bw=args.block_bw) as ctx:
+    out = {"workload": "ship-wave solve 721x241, F=0.7, eps=0.8 (x in [-16,20], y in [0,12], dx=dy=0.05)",
+           "pairs_per_residual": spec.pairs}
+    with swj.Context.from_spec(spec, F, eps, solve_mode="mixed", block_bw=-1) as ctx:
         u = ctx.initial_guess_flat(ctx.vector())
         out["workspace_bytes"] = ctx.workspace_bytes()
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
         ctx.precond_setup()
         ctx.sync()
         out["setup_s"] = time.perf_counter() - t0
-        path = [eps]
         st = ctx.solve(u, check=False)
+        path = [eps]
         if st["rc"] != swj.OK:
             path = [0.2, 0.4, 0.6, 0.8]
             ctx.initial_guess_flat(u)
@@ -631,17 +735,42 @@ def run_large(args):
                 st = ctx.solve(u, check=False)
                 if st["rc"] != swj.OK:
                     break
+        ctx.sync()
         out["total_s"] = time.perf_counter() - t0
         out["eps_path"] = path
         out["solve_stats"] = {k: st[k] for k in ("rc", "newton_iters", "refine_iters", "residual_evals",
                                                  "residual_evals_ff", "krylov_iters", "final_norm_inf_fp64",
                                                  "t_total_ms")}
-        z = torch.empty(spec.N * spec.M, dtype=torch.float64, device="cuda")
+        E = ctx.vector()
+        ctx.residual(u, E, swj.FP64)
+        z, zr = (torch.empty(spec.N * spec.M, dtype=torch.float64, device="cuda") for _ in range(2))
         ctx.unpack(u, z, None)
         ctx.sync()
+        out["fp64_residual_norm_inf_at_root"] = float(E.abs().max().item())
         out["max_zeta"] = float(z.max().item())
         out["crest_bound_F2_over_2"] = F * F / 2
-    print(json.dumps(out), flush=True)
+        # the same root refined with FP64 residuals (FP32 phase skipped)
+        o = swj.default_opts(solve_mode="mixed", block_bw=-1, refine_precision=swj.FP64,
+                             refine_tol_inf=1e-11, mixed_tol_inf=1e300)
+        ctx.set_opts(o)
+        u2 = u.clone()
+        t1 = time.perf_counter()
+        st2 = ctx.solve(u2, check=False)
+        ctx.unpack(u2, zr, None)
+        ctx.sync()
+        out["fp64_refined"] = {"rc": st2["rc"], "refine_iters": st2["refine_iters"],
+                               "residual_evals_fp64": st2["residual_evals_fp64"],
+                               "final_norm_inf_fp64": st2["final_norm_inf_fp64"],
+                               "seconds": time.perf_counter() - t1,
+                               "max_abs_dzeta_vs_mixed": float((z - zr).abs().max().item())}
+    return out
+
+
+def run_large(args):
+    """Only the 721x241 workload (see large_section)."""
+    import torch
+    torch.cuda.set_device(0)
+    print(json.dumps({"large": True, **large_section(args)}), flush=True)
 
 
 def run_residual_only(args):
@@ -781,6 +910,10 @@ def run_spectrum(args):
 
 def main():
     args = parse()
+    if args.serve_requests is None:
+        args.serve_requests = 2000 if args.serve else 256
+    if args.serve_requests_fp64 is None:
+        args.serve_requests_fp64 = 64 if args.serve else 16
     if args.spectrum:
         run_spectrum(args)
         return
@@ -788,12 +921,8 @@ def main():
         run_jvp_only(args)
         return
     if args.large:
-        if args.block_bw == BLOCK_BW:
-            args.block_bw = -1   # the library's rule: 15 at 241 block rows
         run_large(args)
     elif args.serve:
-        if args.serve_requests == 64:
-            args.serve_requests = 2000
         run_serve(args)
     elif args.precond_only:
         run_precond_only(args)
