@@ -122,6 +122,12 @@ typedef struct swj_opts {
                            /* between them: the same factorisation of P up to         */
                            /* rounding in about half the sequential steps); batched   */
                            /* contexts always go top-down (SWJ_LU_TWO_SIDED)          */
+    int    wait_limit;     /* iterations after which a bounded device-side wait of    */
+                           /* the preconditioner gives up and reports SWJ_ETIMEOUT    */
+                           /* (the Gauss-Jordan chain's flag waits in the set-up, the */
+                           /* multi-cluster substitution's polls in the apply); 0:    */
+                           /* the built-in limits, 2^26 and 2^21 (about a second     */
+                           /* each) (0)                                               */
 } swj_opts;
 
 #define SWJ_LU_FP64   0
@@ -426,17 +432,36 @@ const char *swj_strerror(int status);
 /* Library version string. */
 const char *swj_version(void);
 
+/* ---- test hooks ---- */
+
+/* Test hook for the failure path of the bounded device waits: with
+ * SWJ_TEST_WITHHOLD_HELPERS set, the multi-cluster substitution of
+ * swj_precond_apply is launched without its helper clusters, so the terms the
+ * critical clusters poll for are never written; every poll gives up after
+ * opts.wait_limit iterations, the kernel returns, and the apply reports
+ * SWJ_ETIMEOUT (its result is then meaningless).  Nothing faults, traps or
+ * waits without bound.  hooks = 0 restores normal launches; the next
+ * swj_precond_setup clears the timeout status.  Applies only to contexts whose
+ * apply runs on several clusters (swj_sweep_clusters > 1).  Returns SWJ_OK or
+ * SWJ_EINVAL. */
+#define SWJ_TEST_WITHHOLD_HELPERS 1
+int swj_set_test_hooks(swj_ctx *ctx, int hooks);
+
 /* ---- residual without allocation ---- */
 
 /* Bytes of the device array that swj_residual_noalloc works in. */
 #define SWJ_NOALLOC_SCRATCH_BYTES (16u << 20)
 
-/* E_dev <- E(u_dev) exactly as swj_residual computes it (same kernels,
- * precision SWJ_FP64 or SWJ_FP32), for callers that cannot allocate device
- * memory: no context, no cudaMalloc, cudaFree or allocating library call.
- * The paper has no counterpart; it exists for hosts such as a serving loop
- * with a fixed latency budget (cudaMalloc/cudaFree synchronise the whole
- * device) or a framework that budgets all device memory up front.
+/* E_dev <- E(u_dev) as swj_residual computes it with default options (source
+ * forcing; precision SWJ_FP64 or SWJ_FP32, the same kernels), for callers
+ * that cannot allocate device memory: no context, no cudaMalloc, cudaFree or
+ * allocating library call.  The paper has no counterpart; it exists for hosts
+ * such as a serving loop with a fixed latency budget (cudaMalloc/cudaFree
+ * synchronise the whole device) or a framework that budgets all device memory
+ * up front.  The result equals swj_residual's within the residual parity
+ * tolerance (10^-12 of the row scale in FP64, 2*10^-6 in FP32); it can differ
+ * in the last bits where the scratch forces fewer source chunks than the
+ * context's launch plan, which changes the summation order.
  *
  * Work is queued on `stream` (a cudaStream_t, NULL = legacy default) of the
  * current device; the call returns before it finishes.  u_dev and E_dev are
@@ -444,13 +469,15 @@ const char *swj_version(void);
  *
  * Scratch: one file-scope device array of SWJ_NOALLOC_SCRATCH_BYTES (16 MiB)
  * per GPU that loads the library, held until the process exits.  A mesh
- * needs about 128 NM + 112 (N-1)M bytes plus 8 (N-1)M per source chunk
- * (meshes up to about 361 x 121 fit); larger meshes return SWJ_ESIZE before
- * any work is queued.  The first call on each device looks up the array's
- * device address (cudaGetSymbolAddress, with that device current): make that
- * first call before any stream capture.  All calls on a device share the
- * array and leave their data in it; nothing needs clearing between calls, but
- * calls that overlap on the GPU race on it, so serialise them.
+ * needs about 128 NM + 120 (N-1)M bytes plus 8 (N-1)M per source chunk (at
+ * least one): 361 x 121 fits (with fewer chunks than a context uses), and
+ * with N = 361 the largest that fits is 361 x 187 (one chunk).  A mesh that does not fit returns SWJ_ESIZE before any work is
+ * queued.  The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current): make that first call
+ * before any stream capture.  All calls on a device share the array and leave
+ * their data in it; nothing needs clearing between calls (every byte a call
+ * reads it wrote first), but calls that overlap on the GPU race on it, so
+ * serialise them.
  * Returns SWJ_OK, SWJ_EINVAL (bad argument), SWJ_ESIZE or SWJ_ECUDA. */
 int swj_residual_noalloc(const swj_mesh *mesh, double F, double eps, const double *u_dev,
                          double *E_dev, int precision, void *stream);

@@ -258,9 +258,24 @@ __device__ __forceinline__ void warp_argmax(unsigned long long &key, int &idx)
     key = ((unsigned long long)mhi << 32) | mlo;
 }
 
-// Iterations of a flag wait before the kernel gives up (far above any real
-// wait: a step takes a few microseconds).
-constexpr long long kGJSpinLimit = 1ll << 26;
+// Status of a block from every CTA's own (read from their shared memory
+// after a cluster barrier): the smallest failing pivot step (+1) any CTA saw,
+// else -1 if a wait of any CTA timed out, else 0.
+__device__ int gj_cluster_status(cg::cluster_group &cl, int *own, int ncta)
+{
+    int s = 0;
+    bool timeout = false;
+    for (int q = 0; q < ncta; ++q) {
+        const int f = *cl.map_shared_rank(own, q);
+        if (f < 0) timeout = true;
+        else if (f > 0 && (s == 0 || f < s)) s = f;
+    }
+    return s ? s : (timeout ? -1 : 0);
+}
+
+// A flag wait gives up after spin_limit iterations (a kernel argument:
+// opts.wait_limit, else kSwjSpinLimit = 2^26, far above any real wait: a step
+// takes a few microseconds).
 
 // Pipelined Gauss-Jordan inverse with partial (row) pivoting, one n x n block
 // per cluster, each CTA's column slice (n x w) in shared memory.  The pivot
@@ -278,12 +293,15 @@ constexpr long long kGJSpinLimit = 1ll << 26;
 // arithmetic is that of the unblocked elimination; no CTA waits for the
 // slower ones except a new panel owner, which must have applied every earlier
 // step first.  A failed pivot is published as a flag above n; a flag wait that
-// runs past kGJSpinLimit ends the kernel with info = -1.  Every CTA loads its
+// runs past spin_limit ends the kernel with info = -1 (every CTA's status is
+// combined: a CTA that stops on a timeout while the others finish still
+// fails the block).  Every CTA loads its
 // slice before the first barrier and writes the (column-permuted) inverse
 // after the last, so `in` and `out` may alias.
 template <int WM>
 __global__ void __launch_bounds__(kGJThreads)
-k_gj_pipe(int n, const double *in_base, size_t istride, double *out_base, size_t ostride, int *info)
+k_gj_pipe(int n, const double *in_base, size_t istride, double *out_base, size_t ostride, int *info,
+          long long spin_limit)
 {
     cg::cluster_group cl = cg::this_cluster();
     const int ncta = (int)cl.num_blocks();
@@ -334,7 +352,7 @@ k_gj_pipe(int n, const double *in_base, size_t istride, double *out_base, size_t
             long long it = 0;
             unsigned v;
             while ((v = ld_acquire_cluster(flag)) < (unsigned)(nk + 1)) {
-                if (++it > kGJSpinLimit) break;
+                if (++it > spin_limit) break;
             }
             if (v < (unsigned)(nk + 1) || v > (unsigned)n) return;   // left to the next step
             const double *orec = cl.map_shared_rank(rec + (size_t)(nk - no * w) * rs, no);
@@ -440,7 +458,7 @@ k_gj_pipe(int n, const double *in_base, size_t istride, double *out_base, size_t
                 long long it = 0;
                 unsigned v;
                 while ((v = ld_acquire_cluster(flag)) < (unsigned)(k + 1)) {
-                    if (++it > kGJSpinLimit) break;
+                    if (++it > spin_limit) break;
                 }
                 int st = 0;
                 if (v < (unsigned)(k + 1)) st = -1;                      // timed out
@@ -474,7 +492,9 @@ k_gj_pipe(int n, const double *in_base, size_t istride, double *out_base, size_t
             __syncthreads();
         }
     }
-    // every CTA keeps its shared memory until all have read what they need
+    // every CTA keeps its shared memory until all have read what they need;
+    // ctl[1] holds this CTA's status for rank 0
+    if (tid == 0) ctl[1] = fail;
     cl.sync();
     if (!fail) {
         if (tid == 0) {
@@ -491,9 +511,7 @@ k_gj_pipe(int n, const double *in_base, size_t istride, double *out_base, size_t
             out[(size_t)i * n + piv[c0 + jj]] = A[(size_t)i * ws + jj];
         }
     }
-    // status of the block: the first failing step (+1), -1 for a timeout, 0 for success;
-    // CTAs that stopped for different reasons agree on failure, rank 0 reports
-    if (rank == 0 && tid == 0) info[mat] = fail;
+    if (rank == 0 && tid == 0) info[mat] = gj_cluster_status(cl, ctl + 1, ncta);
     cl.sync();
 }
 
@@ -510,7 +528,8 @@ k_gj_pipe(int n, const double *in_base, size_t istride, double *out_base, size_t
 // that of k_gj_pipe bit for bit.
 template <int WM>
 __global__ void __launch_bounds__(kGJThreads)
-k_gj_rr(int n, const double *in_base, size_t istride, double *out_base, size_t ostride, int *info)
+k_gj_rr(int n, const double *in_base, size_t istride, double *out_base, size_t ostride, int *info,
+        long long spin_limit)
 {
     cg::cluster_group cl = cg::this_cluster();
     const int ncta = (int)cl.num_blocks();
@@ -592,7 +611,7 @@ k_gj_rr(int n, const double *in_base, size_t istride, double *out_base, size_t o
             long long it = 0;
             unsigned v;
             while ((v = ld_acquire_cluster(flag)) < (unsigned)(nk + 1)) {
-                if (++it > kGJSpinLimit) break;
+                if (++it > spin_limit) break;
             }
             if (v < (unsigned)(nk + 1) || v > (unsigned)n) return;   // left to the next step
             const double *orec = cl.map_shared_rank(rec + (size_t)(nk / ncta) * rs, no);
@@ -609,7 +628,7 @@ k_gj_rr(int n, const double *in_base, size_t istride, double *out_base, size_t o
                 long long it = 0;
                 unsigned v;
                 while ((v = ld_acquire_cluster(flag)) < (unsigned)(k + 1)) {
-                    if (++it > kGJSpinLimit) break;
+                    if (++it > spin_limit) break;
                 }
                 int st = 0;
                 if (v < (unsigned)(k + 1)) st = -1;                      // timed out
@@ -652,7 +671,9 @@ k_gj_rr(int n, const double *in_base, size_t istride, double *out_base, size_t o
         }
         __syncthreads();
     }
-    // every CTA keeps its shared memory until all have read what they need
+    // every CTA keeps its shared memory until all have read what they need;
+    // ctl[1] holds this CTA's status for rank 0
+    if (tid == 0) ctl[1] = fail;
     cl.sync();
     if (!fail) {
         if (tid == 0) {
@@ -669,7 +690,7 @@ k_gj_rr(int n, const double *in_base, size_t istride, double *out_base, size_t o
             out[(size_t)i * n + piv[rank + jj * ncta]] = A[(size_t)i * ws + jj];
         }
     }
-    if (rank == 0 && tid == 0) info[mat] = fail;
+    if (rank == 0 && tid == 0) info[mat] = gj_cluster_status(cl, ctl + 1, ncta);
     cl.sync();
 }
 
@@ -775,7 +796,7 @@ static int gj_blocked_cluster(int n)
 bool swj_gj_inplace(int n) { return gj_blocked_cluster(n) > 0; }
 
 int swj_gj_inverse_cluster(cudaStream_t st, int n, int count, double *work, size_t wstride,
-                           double *out, size_t ostride, int *info)
+                           double *out, size_t ostride, int *info, long long spin_limit)
 {
     const int csb = gj_blocked_cluster(n);
     const bool use_smem = csb > 0;
@@ -808,7 +829,8 @@ int swj_gj_inverse_cluster(cudaStream_t st, int n, int count, double *work, size
     cfg.numAttrs = 1;
     SWJ_COUNT_LAUNCH();
     const double *win = work;
-    void *args[] = {(void *)&n, (void *)&win, (void *)&wstride, (void *)&out, (void *)&ostride, (void *)&info};
+    void *args[] = {(void *)&n,    (void *)&win,  (void *)&wstride,   (void *)&out,
+                    (void *)&ostride, (void *)&info, (void *)&spin_limit};
     if (use_smem) SWJ_CUDA_TRY(cudaLaunchKernelExC(&cfg, kern, args));
     else SWJ_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_gj_cluster, n, work, wstride, out, ostride, info));
     return SWJ_OK;

@@ -6,9 +6,12 @@
 // (cudaMalloc and cudaFree synchronise the whole device and stall every other
 // stream) or an embedding framework that budgets all device memory up front
 // and forbids allocation after start-up.  For them this entry point computes
-// exactly what swj_residual computes, with the same kernels, but takes its
-// scratch (mesh-step arrays, pair records, per-chunk partial sums) from one
-// file-scope device array instead of a context's cudaMalloc'ed workspace.
+// what swj_residual computes with default options (source forcing), with the
+// same kernels, but takes its scratch (mesh-step arrays, pair records,
+// per-chunk partial sums) from one file-scope device array instead of a
+// context's cudaMalloc'ed workspace.  When the partial sums of the context's
+// launch plan do not fit, it uses fewer source chunks: the result then agrees
+// with swj_residual to the residual's rounding, not bit for bit.
 //
 // * The array is SWJ_NOALLOC_SCRATCH_BYTES (16 MiB) and lives on every GPU
 //   that loads the library until the process exits.
@@ -69,6 +72,8 @@ __global__ void k_na_setup(int M, double *cp, double *a, double *inv, double *Fd
     }
 }
 
+inline long long na_round(long long bytes) { return (bytes + 255) & ~255LL; }
+
 struct Carver {
     unsigned char *base;
     size_t off, cap;
@@ -76,7 +81,7 @@ struct Carver {
     {
         size_t o = off;
         off = (off + bytes + 255) & ~(size_t)255;
-        return (off <= cap) ? base + o : nullptr;
+        return (off <= cap) ? base + o : nullptr;   // o is a multiple of 256
     }
 };
 
@@ -91,10 +96,12 @@ extern "C" int swj_residual_noalloc(const swj_mesh *mesh, double F, double eps, 
     if (!(F > 0.0) || !(eps >= 0.0)) return SWJ_EINVAL;
     if (precision != SWJ_FP64 && precision != SWJ_FP32) return SWJ_EINVAL;
     const long long S = (long long)mesh->N * mesh->M, T = (long long)(mesh->N - 1) * mesh->M;
-    // fixed part of the scratch; the partial sums need at least one chunk (P = 1)
-    const long long need = 4 * S * 8 + 3LL * mesh->M * 8 + 2 * T * 8 + S * (long long)sizeof(SrcRec64) +
-                           S * (long long)sizeof(SrcRec32) + 8 * T * 8 + 8 * T * 4 + T * 8 + 15 * 256;
-    if (need > (long long)SWJ_NOALLOC_SCRATCH_BYTES) return SWJ_ESIZE;
+    // every piece the scratch holds, each rounded up to 256 bytes as the
+    // carver takes it; the partial sums need at least one chunk (P = 1)
+    const long long fixed = 4 * na_round(S * 8) + 3 * na_round((long long)mesh->M * 8) + 2 * na_round(T * 8) +
+                            na_round(S * (long long)sizeof(SrcRec64)) + na_round(S * (long long)sizeof(SrcRec32)) +
+                            na_round(8 * T * 8) + na_round(8 * T * 4) + 2 * na_round(8);
+    if (fixed + na_round(T * 8) > (long long)SWJ_NOALLOC_SCRATCH_BYTES) return SWJ_ESIZE;
 
     void *base = nullptr;
     int rc = na_base(&base);
@@ -135,8 +142,12 @@ extern "C" int swj_residual_noalloc(const swj_mesh *mesh, double F, double eps, 
                                 t64 + 6 * T, t64 + 7 * T};
     c.tgt32 = TgtArrays32{t32, t32 + T, t32 + 2 * T, t32 + 3 * T, t32 + 4 * T, t32 + 5 * T,
                           t32 + 6 * T, t32 + 7 * T};
+    c.Fd = (double *)cv.take(8);
+    c.epsd = (double *)cv.take(8);
+    if (!c.epsd) return SWJ_ESIZE;
     // the launch plan of the context path, with fewer source chunks if the
-    // partial sums would not fit the rest of the scratch
+    // partial sums would not fit the rest of the scratch (the pair sum is then
+    // added in another order: the same value to rounding, not bit for bit)
     PairPlan pl = swj_pair_plan(&c, precision);
     long long maxP = (long long)(cv.cap - cv.off) / (T * 8);
     if (maxP < 1) return SWJ_ESIZE;
@@ -145,9 +156,7 @@ extern "C" int swj_residual_noalloc(const swj_mesh *mesh, double F, double eps, 
         pl.P = (int)((S + pl.chunk - 1) / pl.chunk);
     }
     c.partial = (double *)cv.take((size_t)pl.P * T * 8);
-    c.Fd = (double *)cv.take(8);
-    c.epsd = (double *)cv.take(8);
-    if (!c.partial || !c.epsd) return SWJ_ESIZE;
+    if (!c.partial) return SWJ_ESIZE;
 
     SWJ_COUNT_LAUNCH();
     k_na_setup<<<1, 1, 0, c.stream>>>(c.M, c.spl_cp, c.spl_a, c.spl_inv, c.Fd, c.epsd, F, eps);

@@ -676,7 +676,8 @@ static int mc_solve(swj_ctx *c, double *x)
     int rc = swj_block_p(c->stream, 1, n1, M, h, c->pc_band, band_stride(c), c->pc_t2, mn, c->pc_z, mn,
                          nullptr, c->pc_mc_buf, mn * (1 + 2 * (size_t)(h + 1)), x, mn);
     if (rc) return rc;
-    return swj_band_sweep_mc(c->stream, n1, M, h, c->pc_band, c->pc_W, c->pc_z, z, x, cf, cb, c->pc_mc_err);
+    return swj_band_sweep_mc(c->stream, n1, M, h, c->pc_band, c->pc_W, c->pc_z, z, x, cf, cb, c->pc_mc_err, false,
+                             swj_waits(c, true));
 }
 
 // S x = t for the two-sided order (one instance; t, x [M][n1]).  With
@@ -705,6 +706,7 @@ static int nd_solve(swj_ctx *c, const double *t, double *x, int mode)
     double *pz = c->pc_z;   // p of both band instances (the one-cluster sweep turns it into z)
     const int nw = nblk((long)h * n1 * 32, 256);
     int *err = c->pc_mc_err;
+    const SwjWaits wt = swj_waits(c, true);
     SWJ_COUNT_LAUNCH();
     k_nd_scatter<<<nblk((long)(2 * per), 256), 256, 0, st>>>(n1, M, Mv, c->pc_dB, t, tv);
     int rc;
@@ -918,11 +920,13 @@ int swj_pc_setup(swj_ctx *c)
     if (h == 0) {
         // all M diagonal blocks of all instances are independent
         if (gj_inplace) {
-            rc = swj_gj_inverse_cluster(st, n1, nb * M, c->pc_band, n2, c->pc_band, n2, c->pc_info);
+            rc = swj_gj_inverse_cluster(st, n1, nb * M, c->pc_band, n2, c->pc_band, n2, c->pc_info,
+                                        swj_waits(c, false).spin_limit);
         } else {
             SWJ_CUDA_TRY(cudaMemcpyAsync(c->pc_work, c->pc_band, (size_t)nb * M * n2 * sizeof(double),
                                          cudaMemcpyDeviceToDevice, st));
-            rc = swj_gj_inverse_cluster(st, n1, nb * M, c->pc_work, n2, c->pc_band, n2, c->pc_info);
+            rc = swj_gj_inverse_cluster(st, n1, nb * M, c->pc_work, n2, c->pc_band, n2, c->pc_info,
+                                        swj_waits(c, false).spin_limit);
         }
         if (rc) return rc;
     } else {
@@ -1163,11 +1167,13 @@ int swj_pc_setup(swj_ctx *c)
             double *diag0 = blk(c, 0, i, i);
             const int nq = sh.insts(i);
             if (gj_inplace) {
-                rc = swj_gj_inverse_cluster(sc, n1, nq, diag0, bst, diag0, bst, c->pc_info + (size_t)i * nv);
+                rc = swj_gj_inverse_cluster(sc, n1, nq, diag0, bst, diag0, bst, c->pc_info + (size_t)i * nv,
+                                            swj_waits(c, false).spin_limit);
             } else {
                 SWJ_COUNT_LAUNCH();
                 k_copy_blocks<<<dim3(64, nq), 256, 0, sc>>>(n2, diag0, bst, c->pc_work, n2);
-                rc = swj_gj_inverse_cluster(sc, n1, nq, c->pc_work, n2, diag0, bst, c->pc_info + (size_t)i * nv);
+                rc = swj_gj_inverse_cluster(sc, n1, nq, c->pc_work, n2, diag0, bst, c->pc_info + (size_t)i * nv,
+                                            swj_waits(c, false).spin_limit);
             }
             if (rc) return rc;
             if (i >= 1) SWJ_CUDA_TRY(cudaStreamWaitEvent(sc, evB1[(i - 1) % 4], 0));
@@ -1265,7 +1271,8 @@ int swj_pc_setup(swj_ctx *c)
             const int ni = mode == 2 ? 2 : 1;
             SWJ_CUDA_TRY(cudaMemsetAsync(c->pc_mc_err, 0, sizeof(int), st));
             int rc = swj_band_sweep_mc_ranges(st, n1, Mv, h, ni, c->pc_band, bst, c->pc_W, (size_t)Mv * h * n2,
-                                              c->pc_z, zv, zv, per, cf, cb, sst, c->pc_mc_err, false, 0, 0, -1, 0);
+                                              c->pc_z, zv, zv, per, cf, cb, sst, c->pc_mc_err, false, 0, 0, -1, 0,
+                                              swj_waits(c, false));
             int err = 1;
             if (rc == SWJ_OK) {
                 SWJ_CUDA_TRY(cudaMemcpyAsync(&err, c->pc_mc_err, sizeof(int), cudaMemcpyDeviceToHost, st));

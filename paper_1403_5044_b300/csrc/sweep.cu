@@ -36,9 +36,9 @@ constexpr int kSweepThreads = 512;
 // result is always quiet), so a consumer polls a value until it differs.
 constexpr unsigned long long kUnset = 0x7FF4DEAD7FF4DEADull;
 
-// a poll that has not seen its value after this many reads gives up (about a
-// second at L2 latency) and reports through the error word
-constexpr int kPollLimit = 1 << 21;
+// a poll that has not seen its value after poll_limit reads (a kernel
+// argument; kSwjPollLimit = 2^21 by default, about a second at L2 latency)
+// gives up and reports through the error word
 
 __device__ __forceinline__ double ld_relaxed(const double *p)
 {
@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(kSweepThreads)
 k_band_sweep_mc(int n1, int M, int h, int ni, int hsets, const double *__restrict__ band, size_t bst,
                 const double *__restrict__ W, size_t wst, const double *__restrict__ p, double *z, double *x,
                 size_t vst, double *cf, double *cb, size_t sst, int cs, int *err, int F0, int F1, int B1,
-                int B0)
+                int B0, int poll_limit)
 {
     cg::cluster_group cl = cg::this_cluster();
     const int ncta = (int)cl.num_blocks();
@@ -334,7 +334,7 @@ k_band_sweep_mc(int n1, int M, int h, int ni, int hsets, const double *__restric
         if (unset(v) && !*(volatile int *)&bad) {
             int it = 0;
             while (unset(v = ld_relaxed(a)))
-                if (++it > kPollLimit || *(volatile int *)&bad) {
+                if (++it > poll_limit || *(volatile int *)&bad) {
                     bad = 1;
                     atomicExch(err, 1);
                     break;
@@ -374,11 +374,16 @@ k_band_sweep_mc(int n1, int M, int h, int ni, int hsets, const double *__restric
         for (int e = threadIdx.x; e < M * nr; e += blockDim.x)
             zs[(size_t)(e / nr) * rows + e % nr] = p[(size_t)(e / nr) * n1 + r0 + e % nr];
         cl.sync();
+        // The exchange inside the cluster goes on after a poll of another
+        // cluster's value gave up (every CTA still sends its rows each step),
+        // so these waits are not skipped then: a barrier is re-armed only
+        // after its previous phase completed, and no CTA leaves while values
+        // sent to it are in flight.  They wait on this cluster alone, so
+        // their bound is the built-in one, not poll_limit.
         auto wait_bar = [&](uint64_t *mb, int parity) {
-            if (*(volatile int *)&bad) return;
             int it = 0;
             while (!mbar_test(mb, parity))
-                if (++it > kPollLimit) {
+                if (++it > kSwjPollLimit) {
                     bad = 1;
                     atomicExch(err, 1);
                     return;
@@ -596,7 +601,7 @@ template <int KC>
 static int launch_sweep_mc(cudaStream_t st, int n1, int M, int h, int ni, const double *band, size_t bst,
                            const double *W, size_t wst, const double *p, double *z, double *x, size_t vst,
                            double *cf, double *cb, size_t sst, int *err, bool prepare, int F0, int F1, int B1,
-                           int B0)
+                           int B0, SwjWaits waits)
 {
     const void *kern = (const void *)k_band_sweep_mc<KC>;
     McPick pick = {0, 1, 0};
@@ -641,7 +646,10 @@ static int launch_sweep_mc(cudaStream_t st, int n1, int M, int h, int ni, const 
         }
         pick = it->second;
     }
-    const int cs = pick.cs, hsets = pick.hsets;
+    const int cs = pick.cs;
+    // test hook: no helper clusters, so nobody writes the terms the critical
+    // clusters poll for (every poll runs out after waits.poll_limit reads)
+    const int hsets = waits.no_helpers ? 0 : pick.hsets;
     const size_t smem = pick.smem;
     if (!cs) return SWJ_EINVAL;
     if (prepare) return SWJ_OK;
@@ -661,7 +669,8 @@ static int launch_sweep_mc(cudaStream_t st, int n1, int M, int h, int ni, const 
     cfg.numAttrs = 2;
     SWJ_COUNT_LAUNCH();
     const cudaError_t e = cudaLaunchKernelEx(&cfg, k_band_sweep_mc<KC>, n1, M, h, ni, hsets, band, bst, W, wst, p,
-                                             z, x, vst, cf, cb, sst, cs, err, F0, F1, B1, B0);
+                                             z, x, vst, cf, cb, sst, cs, err, F0, F1, B1, B0,
+                                             waits.poll_limit);
     if (e != cudaSuccess) {
         cudaGetLastError();
         // a stream capture that another host thread invalidated is not a refusal
@@ -721,19 +730,20 @@ int swj_band_sweep_cluster(cudaStream_t st, int nb, int n1, int M, int h, const 
 }
 
 int swj_band_sweep_mc(cudaStream_t st, int n1, int M, int h, const double *band, const double *W,
-                      const double *p, double *z, double *x, double *cf, double *cb, int *err, bool prepare)
+                      const double *p, double *z, double *x, double *cf, double *cb, int *err, bool prepare,
+                      SwjWaits waits)
 {
     if (h < 2 || M < 2) return SWJ_EINVAL;
     SWJ_KC_DISPATCH((launch_sweep_mc<K>(st, n1, M, h, 1, band, 0, W, 0, p, z, x, 0, cf, cb, 0, err, prepare, 0, M,
-                                        M - 1, 0)));
+                                        M - 1, 0, waits)));
 }
 
 int swj_band_sweep_mc_ranges(cudaStream_t st, int n1, int M, int h, int ni, const double *band, size_t bst,
                              const double *W, size_t wst, const double *p, double *z, double *x, size_t vst,
                              double *cf, double *cb, size_t sst, int *err, bool prepare, int F0, int F1, int B1,
-                             int B0)
+                             int B0, SwjWaits waits)
 {
     if (h < 2 || M < 2 || ni < 1 || ni > 2 || F0 < 0 || F1 > M || B1 >= M || B0 < 0) return SWJ_EINVAL;
     SWJ_KC_DISPATCH((launch_sweep_mc<K>(st, n1, M, h, ni, band, bst, W, wst, p, z, x, vst, cf, cb, sst, err, prepare,
-                                        F0, F1, B1, B0)));
+                                        F0, F1, B1, B0, waits)));
 }

@@ -32,6 +32,7 @@ bool valid_opts(const swj_opts *o)
     if (o->forcing != SWJ_FORCING_SOURCE && o->forcing != SWJ_FORCING_PRESSURE) return false;
     if (o->lu_products != SWJ_LU_FP64 && o->lu_products != SWJ_LU_SLICED) return false;
     if (o->lu_order != SWJ_LU_TOP_DOWN && o->lu_order != SWJ_LU_TWO_SIDED) return false;
+    if (o->wait_limit < 0) return false;
     return true;
 }
 
@@ -255,6 +256,14 @@ void swj_default_opts(swj_opts *o)
     o->forcing = SWJ_FORCING_SOURCE;
     o->lu_products = SWJ_LU_SLICED;
     o->lu_order = SWJ_LU_TWO_SIDED;
+    o->wait_limit = 0;
+}
+
+int swj_set_test_hooks(swj_ctx *c, int hooks)
+{
+    if (!c || (hooks & ~SWJ_TEST_WITHHOLD_HELPERS)) return SWJ_EINVAL;
+    c->test_hooks = hooks;
+    return SWJ_OK;
 }
 
 int swj_create(swj_ctx **out, const swj_mesh *mesh, double F, double eps, const swj_opts *opts,

@@ -152,6 +152,7 @@ struct swj_ctx {
     double *pc_mc_buf;
     int *pc_mc_err;
     int pc_mc;                   // apply on h clusters: 0 no, 1 one instance (or half) per launch, 2 both
+    int test_hooks;              // SWJ_TEST_* flags (swj_set_test_hooks)
                                  // halves of the two-sided order in one launch
     double *pc_lt;               // set-up scratch: inv_i S_ij (j < i) of one block row, every instance
     // sliced (bf16 tensor-core) block products of the band LU (lu_products = SWJ_LU_SLICED)
@@ -275,8 +276,26 @@ void swj_dgemm(cudaStream_t st, int m, int n, int k, double alpha, const double 
 
 // cluster.cu
 bool swj_gj_inplace(int n);
+// Limits of the bounded device waits of the preconditioner kernels, from
+// opts.wait_limit (0: the built-in ones), and whether the multi-cluster
+// substitution is launched without its helper clusters (test hook).
+struct SwjWaits {
+    long long spin_limit;   // Gauss-Jordan flag waits
+    int poll_limit;         // multi-cluster substitution: polls of another cluster's values
+    int no_helpers;
+};
+constexpr long long kSwjSpinLimit = 1ll << 26;
+constexpr int kSwjPollLimit = 1 << 21;
+inline SwjWaits swj_waits(const swj_ctx *c, bool hooks)
+{
+    const int w = c->opts.wait_limit;
+    return SwjWaits{w > 0 ? (long long)w : kSwjSpinLimit, w > 0 ? w : kSwjPollLimit,
+                    hooks && (c->test_hooks & SWJ_TEST_WITHHOLD_HELPERS) ? 1 : 0};
+}
+inline SwjWaits swj_default_waits() { return SwjWaits{kSwjSpinLimit, kSwjPollLimit, 0}; }
+
 int swj_gj_inverse_cluster(cudaStream_t st, int n, int count, double *work, size_t wstride,
-                           double *out, size_t ostride, int *info);
+                           double *out, size_t ostride, int *info, long long spin_limit = kSwjSpinLimit);
 // cluster size (16, else 8) for `kern` with `smem` bytes of dynamic shared
 // memory per CTA; raises the kernel's shared-memory limit to `smem`
 int swj_cluster_for(const void *kern, int threads, size_t smem);
@@ -305,7 +324,7 @@ int swj_band_sweep_cluster(cudaStream_t st, int nb, int n1, int M, int h, const 
 // at once (nothing launched).
 int swj_band_sweep_mc(cudaStream_t st, int n1, int M, int h, const double *band, const double *W,
                       const double *p, double *z, double *x, double *cf, double *cb, int *err,
-                      bool prepare = false);
+                      bool prepare = false, SwjWaits waits = swj_default_waits());
 // The same for ni = 1 or 2 instances at once (instance q's band, W, vectors and
 // term slots at q bst, q wst, q vst, q sst; one critical cluster each, the h - 1
 // helper clusters shared) over forward rows F0..F1-1 and backward rows B1 down to
@@ -316,7 +335,7 @@ int swj_band_sweep_mc(cudaStream_t st, int n1, int M, int h, const double *band,
 int swj_band_sweep_mc_ranges(cudaStream_t st, int n1, int M, int h, int ni, const double *band, size_t bst,
                              const double *W, size_t wst, const double *p, double *z, double *x, size_t vst,
                              double *cf, double *cb, size_t sst, int *err, bool prepare, int F0, int F1, int B1,
-                             int B0);
+                             int B0, SwjWaits waits = swj_default_waits());
 
 // precond.cu
 int swj_pc_setup(swj_ctx *c);

@@ -24,6 +24,7 @@ FORCING_SOURCE, FORCING_PRESSURE = 0, 1
 LU_FP64, LU_SLICED = 0, 1
 LU_TOP_DOWN, LU_TWO_SIDED = 0, 1
 SOLVE_FP64, SOLVE_MIXED = 0, 1
+TEST_WITHHOLD_HELPERS = 1
 
 
 class SwjError(RuntimeError):
@@ -46,7 +47,7 @@ class Opts(ctypes.Structure):
                 ("mixed_tol_inf", ctypes.c_double), ("refine_tol_inf", ctypes.c_double),
                 ("verbose", ctypes.c_int), ("autotune", ctypes.c_int), ("refine_precision", ctypes.c_int),
                 ("jvp", ctypes.c_int), ("forcing", ctypes.c_int),
-                ("lu_products", ctypes.c_int), ("lu_order", ctypes.c_int)]
+                ("lu_products", ctypes.c_int), ("lu_order", ctypes.c_int), ("wait_limit", ctypes.c_int)]
 
 
 class ServerOpts(ctypes.Structure):
@@ -124,6 +125,7 @@ def lib():
             "swj_server_destroy": (None, [_vp]),
             "swj_set_params": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double]),
             "swj_set_opts": (ctypes.c_int, [_vp, P(Opts)]),
+            "swj_set_test_hooks": (ctypes.c_int, [_vp, ctypes.c_int]),
             "swj_workspace_bytes": (ctypes.c_size_t, [_vp]),
             "swj_initial_guess_flat": (ctypes.c_int, [_vp, _vp]),
             "swj_residual": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int]),
@@ -314,6 +316,11 @@ class Context:
 
     def sweep_clusters(self):
         return int(lib().swj_precond_sweep_clusters(self._h))
+
+    def set_test_hooks(self, hooks):
+        """swj_set_test_hooks: TEST_WITHHOLD_HELPERS makes the multi-cluster
+        apply's bounded polls run out (for testing the timeout path)."""
+        _check(lib().swj_set_test_hooks(self._h, int(hooks)), "swj_set_test_hooks")
 
     def solve(self, u, check=True):
         st = Stats()

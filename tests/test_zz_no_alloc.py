@@ -35,7 +35,13 @@ def oracle_scale(spec, F, eps, u):
     return np.maximum(1.0, O.residual_scale(m, F, eps, u))
 
 
-@pytest.mark.parametrize("spec,F,eps", [W.SOLVE_41x21, W.SOLVE_181x61])
+# 41x21 and 181x61 keep the context's launch plan; at 361x121 (the largest
+# serving mesh) and 494x85 the partial sums of that plan do not fit and fewer
+# source chunks are used, filling the scratch; 361x187 is the largest mesh
+# with N = 361 that fits at all (one chunk).
+@pytest.mark.parametrize("spec,F,eps", [W.SOLVE_41x21, W.SOLVE_181x61, (W.domain_mesh(361, 121), 0.7, 0.3),
+                                        (W.domain_mesh(494, 85), 0.8, 0.2),
+                                        (W.domain_mesh(361, 187), 0.6, 0.25)])
 def test_noalloc_residual_matches_swj_residual_on_two_calls(spec, F, eps):
     f = noalloc_fn()
     u = W.random_state(spec, seed=17, amp=0.06)
@@ -57,9 +63,9 @@ def test_noalloc_residual_matches_swj_residual_on_two_calls(spec, F, eps):
                 assert err <= TOL[prec], (prec, call, err)
 
 
-def test_noalloc_rejects_a_mesh_larger_than_its_scratch():
+@pytest.mark.parametrize("spec", [W.domain_mesh(361, 188), W.MESH_721x241])
+def test_noalloc_rejects_a_mesh_larger_than_its_scratch(spec):
     f = noalloc_fn()
-    spec = W.MESH_721x241
     mesh = swj.Mesh(spec.N, spec.M, spec.x1, spec.dx, spec.dy, spec.n_rad)
     u = torch.zeros(spec.n_unknowns, dtype=torch.float64, device="cuda")
     E = torch.zeros_like(u)
