@@ -45,7 +45,7 @@ def build(force=False, verbose=False):
         objs.append(obj)
     tmp = OUT + ".tmp%d" % os.getpid()
     subprocess.check_call([NVCC, "-shared", "-gencode", "arch=compute_103a,code=sm_103a",
-                           "-o", tmp] + objs + ["-lcudart", "-lcublas"])
+                           "-o", tmp] + objs + ["-lcudart"])
     os.replace(tmp, OUT)
     return OUT
 

@@ -11,23 +11,20 @@
 // fixed-point magnitude truncated after s beta >= 56 bits, taken with integer
 // shifts from the FP64 bit pattern); B the same by columns.  Then
 //   (A B)[r,c] = 2^(ea_r + eb_c) sum_d 2^(-beta (d+2)) T_d[r,c],
-//   T_d = sum_{p+q=d} a_p b_q = [a_0 .. a_d] [b_d; ..; b_0],
-// one GEMM per d, all with inner dimension s n: A's slices are stored
-// interleaved by row ([a_0 .. a_(s-1)] per row) and B's in reverse order
-// followed by s - 1 zero slices ([b_(s-1); ..; b_0; 0; ..; 0]), so that the s
-// rows of slices starting at b_d are [b_d; ..; b_0; 0..] and every T_d is a
-// plain strided product; the T_d of all products of a group are one batched
-// call (the zero slices cost tensor-core flops, not launches).  beta is
-// chosen so that s n 2^(2 beta) <= 2^24: every
-// partial sum of every T_d is an integer below 2^24, so a bf16 GEMM with FP32
-// accumulation (cuBLAS) computes it exactly whatever its summation order.
-// The T_d for d <= s - 1 are summed exactly in integer arithmetic and rounded
-// to FP64 once; the dropped terms and the digit truncation are below
-// n 2^(-56) of |A_r,:| |B_:,c|, the size of FP64's own rounding of the dot
-// product, and the result does not depend on how the products are batched.  Matrices are padded with zeros to a
-// multiple of 8 (16-byte rows for the tensor-core kernels).
+//   T_d = sum_{p+q=d} a_p b_q,
+// formed on the tensor cores by this library's tcgen05 kernel (umma.cu).
+// Both factors' slices are stored K-major with one shape,
+// [slot][row][digit][np]: row r of A's slot holds a_0[r, :] .. a_(s-1)[r, :],
+// row c of B's slot holds column c of b_0 .. b_(s-1).  beta is chosen so
+// that s n 2^(2 beta) <= 2^24: every partial sum of every T_d is an integer
+// below 2^24, so bf16 products with FP32 accumulation compute it exactly
+// whatever the summation order.  The T_d for d <= s - 1 are summed exactly in
+// integer arithmetic and rounded to FP64 once; the dropped terms and the
+// digit truncation are below n 2^(-56) of |A_r,:| |B_:,c|, the size of FP64's
+// own rounding of the dot product, and the result does not depend on how the
+// products are batched.  Matrices are padded with zeros to a multiple of 8
+// (16-byte digit rows for the tensor-memory-access loads).
 #include "swj_internal.h"
-#include <cublas_v2.h>
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -99,61 +96,57 @@ __global__ void k_oz_split_rows(int n, int np, int s, int beta, const double *co
     }
 }
 
-// Split by columns: slot slots[m] of sb, layout [slot][2s-1][np][np] with digit
-// q at position s - 1 - q (reverse order; positions s .. 2s-2 stay zero);
-// column exponents ex[slot][np].  Block per (32-column strip, matrix): lanes
-// over columns, warps over rows.
+// Split by columns: slot slots[m] of sb, layout [slot][np columns][s][np rows]
+// (column c, digit q, row r: K-major, the layout of the A slices), digits
+// with the entry's sign; column exponents ex[slot][np].  Block per (32-column
+// strip, matrix), 256 threads: the column maxima with lanes over columns and
+// warps over rows (coalesced reads), then 32 x 32 tiles through shared
+// memory, written with lanes over rows (64-byte runs per column and digit).
 __global__ void k_oz_split_cols(int n, int np, int s, int beta, const double *const *mats, const int *slots,
                                 __nv_bfloat16 *sb, int *ex)
 {
-    const int c = blockIdx.x * 32 + (threadIdx.x & 31), w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int c0 = blockIdx.x * 32, lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int m = blockIdx.y;
     const double *A = mats[m];
     const int slot = slots[m];
     __shared__ double red[32][33];
+    __shared__ int ec[32];
+    const int c = c0 + lane;
     double mx = 0.0;
     if (c < n)
         for (int r = w; r < n; r += nw) mx = fmax(mx, fabs(A[(size_t)r * n + c]));
-    red[w][threadIdx.x & 31] = mx;
+    red[w][lane] = mx;
     __syncthreads();
     if (w == 0) {
-        for (int q = 1; q < nw; ++q) mx = fmax(mx, red[q][threadIdx.x & 31]);
-        red[0][threadIdx.x & 31] = mx;
+        for (int q = 1; q < nw; ++q) mx = fmax(mx, red[q][lane]);
+        const int e = (c < n) ? row_exponent(mx) : 0;
+        ec[lane] = e;
+        if (c < np) ex[(size_t)slot * np + c] = e;
     }
-    __syncthreads();
-    if (c >= np) return;
-    const int e = (c < n) ? row_exponent(red[0][threadIdx.x & 31]) : 0;
-    if (w == 0) ex[(size_t)slot * np + c] = e;
-    const size_t n2 = (size_t)np * np;
-    __nv_bfloat16 *out = sb + (size_t)slot * (2 * s - 1) * n2 + c;
     const int bits = s * beta;
     const unsigned mask = (1u << beta) - 1u;
-    for (int r = w; r < np; r += nw) {
-        const double x = (c < n && r < n) ? A[(size_t)r * n + c] : 0.0;
-        const unsigned long long X = fixed_bits(x, e, bits);
-        const float sg = (x < 0.0) ? -1.f : 1.f;
-        for (int q = 0; q < s; ++q) {
-            const unsigned dgt = (unsigned)(X >> (beta * (s - 1 - q))) & mask;
-            out[(size_t)(s - 1 - q) * n2 + (size_t)r * np] = __float2bfloat16(sg * (float)dgt);
+    const size_t rowlen = (size_t)s * np;
+    __nv_bfloat16 *out = sb + (size_t)slot * np * rowlen;
+    for (int r0 = 0; r0 < np; r0 += 32) {
+        __syncthreads();   // ec written; the previous tile consumed
+        for (int rr = w; rr < 32; rr += nw) {
+            const int r = r0 + rr;
+            red[rr][lane] = (r < n && c < n) ? A[(size_t)r * n + c] : 0.0;
+        }
+        __syncthreads();
+        const int r = r0 + lane;
+        for (int cc = w; cc < 32; cc += nw) {
+            if (c0 + cc >= np || r >= np) continue;
+            const double x = red[lane][cc];
+            const unsigned long long X = fixed_bits(x, ec[cc], bits);
+            const float sg = (x < 0.0) ? -1.f : 1.f;
+            __nv_bfloat16 *o = out + (size_t)(c0 + cc) * rowlen + r;
+            for (int q = 0; q < s; ++q) {
+                const unsigned dgt = (unsigned)(X >> (beta * (s - 1 - q))) & mask;
+                o[(size_t)q * np] = __float2bfloat16(sg * (float)dgt);   // exact: dgt < 2^8
+            }
         }
     }
-}
-
-// Pointer arrays of the GEMMs T_d of `count` products, d = 0..s-1: entry
-// t * s + d.  Row-major T = A' B' is the column-major T^T = B'^T A'^T, so B'
-// (s np rows from stored position s-1-d: b_d .. b_0 then zeros) comes first;
-// A' is row-major with leading dimension s np.
-__global__ void k_oz_ptrs(int count, int s, int np, const OzProd *__restrict__ prods, const __nv_bfloat16 *sa,
-                          const __nv_bfloat16 *sb, float *P, const void **pA, const void **pB, void **pC)
-{
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= count * s) return;
-    const int t = e / s, d = e % s;
-    const OzProd o = prods[t];
-    const size_t n2 = (size_t)np * np;
-    pA[e] = sb + ((size_t)o.b * (2 * s - 1) + (s - 1 - d)) * n2;
-    pB[e] = sa + (size_t)o.a * np * s * np;
-    pC[e] = P + ((size_t)t * s + d) * n2;
 }
 
 // C_t = alpha 2^(ea_r + eb_c) sum_d 2^(-beta (d+2)) T_d[r, c] (+ C_t).  Every
@@ -219,40 +212,16 @@ int swj_ozaki_split(cudaStream_t st, bool by_rows, int n, int np, int s, int bet
     return SWJ_OK;
 }
 
-int swj_ozaki_products(void **handle, cudaStream_t st, int n, int np, int s, int beta, int count,
-                       const OzProd *prods, const void *sa_, const int *ea, const void *sb_, const int *eb,
-                       double alpha, float *P, void **ptrs, int mode)
+int swj_ozaki_products(cudaStream_t st, int n, int np, int s, int beta, int count, const OzProd *prods,
+                       const void *sa, size_t nsa, const int *ea, const void *sb, size_t nsb, const int *eb,
+                       double alpha, float *P, int *err)
 {
     if (count <= 0) return SWJ_OK;
-    const __nv_bfloat16 *sa = (const __nv_bfloat16 *)sa_, *sb = (const __nv_bfloat16 *)sb_;
-    const int nall = count * s;
-    const void **pA = (const void **)ptrs, **pB = pA + nall;
-    void **pC = ptrs + 2 * (size_t)nall;
-    if (mode != SWJ_OZ_USE_PTRS) {
-        SWJ_COUNT_LAUNCH();
-        k_oz_ptrs<<<nblk(nall, 256), 256, 0, st>>>(count, s, np, prods, sa, sb, P, pA, pB, pC);
-        SWJ_CUDA_TRY(cudaGetLastError());
-        if (mode == SWJ_OZ_FILL_PTRS) return SWJ_OK;
-    }
-    cublasHandle_t h = (cublasHandle_t)*handle;
-    if (!h) {
-        if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) return SWJ_ECUDA;
-        *handle = h;
-    }
-    if (cublasSetStream(h, st) != CUBLAS_STATUS_SUCCESS) return SWJ_ECUDA;
-    const float one = 1.0f, zero = 0.0f;
-    // every T_d^T (np x np, column-major) = B'^T (np x s np) A'^T (s np x np), one call
-    if (cublasGemmBatchedEx(h, CUBLAS_OP_N, CUBLAS_OP_N, np, np, s * np, &one, pA, CUDA_R_16BF, np, pB,
-                            CUDA_R_16BF, s * np, &zero, pC, CUDA_R_32F, np, nall, CUBLAS_COMPUTE_32F,
-                            CUBLAS_GEMM_DEFAULT) != CUBLAS_STATUS_SUCCESS)
-        return SWJ_ECUDA;
+    int rc = swj_oz_gemm(st, np, s, count, prods, sa, nsa, sb, nsb, P, err);
+    if (rc) return rc;
     SWJ_COUNT_LAUNCH();
     k_oz_combine<<<dim3(nblk((long)n * n, 256), count), 256, 0, st>>>(n, np, s, beta, prods, P, ea, eb, alpha);
     SWJ_CUDA_TRY(cudaGetLastError());
     return SWJ_OK;
 }
 
-void swj_cublas_destroy(void *handle)
-{
-    if (handle) cublasDestroy((cublasHandle_t)handle);
-}

@@ -491,13 +491,13 @@ void free_pc(swj_ctx *c)
     c->pc_ptrs_cap = 0;
     if (c->pc_mc_err) cudaFree(c->pc_mc_err);
     c->pc_mc_err = nullptr;
-    void *oz[] = {c->oz_sa, c->oz_sb, c->oz_ea, c->oz_eb, c->oz_P, c->oz_ptrs, c->oz_desc};
+    void *oz[] = {c->oz_sa, c->oz_sb, c->oz_ea, c->oz_eb, c->oz_P, c->oz_err, c->oz_desc};
     for (void *q : oz)
         if (q) cudaFree(q);
     c->oz_sa = c->oz_sb = nullptr;
     c->oz_ea = c->oz_eb = nullptr;
     c->oz_P = nullptr;
-    c->oz_ptrs = nullptr;
+    c->oz_err = nullptr;
     c->oz_desc = nullptr;
     c->pc_mc = 0;
     if (c->pc_chain) {
@@ -623,8 +623,8 @@ OzLayout oz_layout(int n1, const PcShape &sh)
     }
     L.bytes_desc = oz_align(L.nptr * sizeof(double *)) + oz_align(L.nptr * sizeof(int)) +
                    oz_align(L.nprod * sizeof(OzProd));
-    L.bytes = L.nsa * L.s * n2 * 2 + L.nsb * (2 * L.s - 1) * n2 * 2 + (L.nsa + L.nsb) * L.np * sizeof(int) +
-              L.maxP * per + 3 * L.nprod * L.s * sizeof(void *) + L.bytes_desc;
+    L.bytes = (L.nsa + L.nsb) * L.s * n2 * 2 + (L.nsa + L.nsb) * L.np * sizeof(int) + L.maxP * per + sizeof(int) +
+              L.bytes_desc;
     return L;
 }
 
@@ -728,27 +728,27 @@ static int nd_solve(swj_ctx *c, const double *t, double *x, int mode)
             return rc;
         if (mode == 2) {
             if ((rc = swj_band_sweep_mc_ranges(st, n1, Mv, h, 2, c->pc_band, bst, c->pc_W, wst, pz, zv, xv, per, cf,
-                                               cb, sst, err, false, 0, F, -1, 0)))
+                                               cb, sst, err, false, 0, F, -1, 0, wt)))
                 return rc;
             sep_p(zv + per);
             if ((rc = swj_band_sweep_mc_ranges(st, n1, Mv, h, 1, bandT, 0, WT, 0, pz, zv, xv, 0, cf, cb, 0, err,
-                                               false, F, Mv, Mv - 1, F)))
+                                               false, F, Mv, Mv - 1, F, wt)))
                 return rc;
             sep_x();
             if ((rc = swj_band_sweep_mc_ranges(st, n1, Mv, h, 2, c->pc_band, bst, c->pc_W, wst, zv, zv, xv, per, cf,
-                                               cb, sst, err, false, 0, 0, F - 1, 0)))
+                                               cb, sst, err, false, 0, 0, F - 1, 0, wt)))
                 return rc;
         } else {
             if ((rc = swj_band_sweep_mc_ranges(st, n1, Mv, h, 1, bandB, 0, WB, 0, pz + per, zv + per, xv + per, 0,
-                                               cf + sst, cb + sst, 0, err, false, 0, F, -1, 0)))
+                                               cf + sst, cb + sst, 0, err, false, 0, F, -1, 0, wt)))
                 return rc;
             sep_p(zv + per);
             if ((rc = swj_band_sweep_mc_ranges(st, n1, Mv, h, 1, bandT, 0, WT, 0, pz, zv, xv, 0, cf, cb, 0, err,
-                                               false, 0, Mv, Mv - 1, 0)))
+                                               false, 0, Mv, Mv - 1, 0, wt)))
                 return rc;
             sep_x();
             if ((rc = swj_band_sweep_mc_ranges(st, n1, Mv, h, 1, bandB, 0, WB, 0, zv + per, zv + per, xv + per, 0,
-                                               cf + sst, cb + sst, 0, err, false, 0, 0, F - 1, 0)))
+                                               cf + sst, cb + sst, 0, err, false, 0, 0, F - 1, 0, wt)))
                 return rc;
         }
     } else {
@@ -826,11 +826,11 @@ int swj_pc_setup(swj_ctx *c)
         if (sliced) {
             const OzLayout L = oz_layout(n1, sh);
             void **ozb[] = {&c->oz_sa, &c->oz_sb, (void **)&c->oz_ea, (void **)&c->oz_eb, (void **)&c->oz_P,
-                            (void **)&c->oz_ptrs, &c->oz_desc};
+                            (void **)&c->oz_err, &c->oz_desc};
             const size_t p2 = (size_t)L.np * L.np;
-            const size_t ozs[] = {L.nsa * L.s * p2 * 2, L.nsb * (2 * L.s - 1) * p2 * 2, L.nsa * L.np * sizeof(int),
-                                  L.nsb * L.np * sizeof(int), L.maxP * L.s * p2 * sizeof(float),
-                                  3 * L.nprod * L.s * sizeof(void *), L.bytes_desc};
+            const size_t ozs[] = {L.nsa * L.s * p2 * 2, L.nsb * L.s * p2 * 2, L.nsa * L.np * sizeof(int),
+                                  L.nsb * L.np * sizeof(int), L.maxP * L.s * p2 * sizeof(float), sizeof(int),
+                                  L.bytes_desc};
             for (int i = 0; i < 7; ++i) {
                 if (cudaMalloc(ozb[i], ozs[i]) != cudaSuccess) {
                     free_pc(c);
@@ -839,8 +839,6 @@ int swj_pc_setup(swj_ctx *c)
                 c->pc_bytes += ozs[i];
                 c->bytes += ozs[i];
             }
-            // the B slots' trailing s - 1 slices are zero padding, never written again
-            SWJ_CUDA_TRY(cudaMemsetAsync(c->oz_sb, 0, ozs[1], st));
         }
     }
     c->pc_ready = 0;
@@ -1078,23 +1076,6 @@ int swj_pc_setup(swj_ctx *c)
             SWJ_CUDA_TRY(cudaMemcpyAsync(base + offS, zs.data(), zs.size() * sizeof(int), cudaMemcpyHostToDevice, st));
             SWJ_CUDA_TRY(cudaMemcpyAsync(base + offQ, zq.data(), zq.size() * sizeof(OzProd), cudaMemcpyHostToDevice, st));
             SWJ_CUDA_TRY(cudaStreamSynchronize(st));   // the host lists must outlive the copies
-            // the batched GEMMs' pointer arrays of every call of every step, once:
-            // the call at product-list offset g uses oz_ptrs + 3 s g
-            const OzProd *dq = (const OzProd *)(base + offQ);
-            for (int i = 0; i < Mv; ++i) {
-                const OzStep &o = zo[i];
-                const size_t goff[3] = {o.pwb, o.pb1, o.pb2};
-                const int gcnt[3] = {o.cwb + o.cl, o.cb1, o.cb2};
-                for (int g = 0; g < 3; ++g)
-                    for (int c0 = 0; c0 < gcnt[g]; c0 += (int)OL.maxP) {
-                        const int cc = std::min((int)OL.maxP, gcnt[g] - c0);
-                        const size_t g0 = goff[g] + c0;
-                        const int r_ = swj_ozaki_products(&c->cublas, st, n1, OL.np, OL.s, OL.beta, cc, dq + g0,
-                                                          c->oz_sa, c->oz_ea, c->oz_sb, c->oz_eb, 1.0, c->oz_P,
-                                                          c->oz_ptrs + 3 * (size_t)OL.s * g0, SWJ_OZ_FILL_PTRS);
-                        if (r_) return r_;
-                    }
-            }
         }
         }
         const PcPlan &PL = *(const PcPlan *)c->pc_plan;
@@ -1156,6 +1137,8 @@ int swj_pc_setup(swj_ctx *c)
                               (const double *const *)(dB + o), n1, beta, dC + o, n1, n, tile_for(n));
             return SWJ_OK;
         };
+        // a bounded wait of the slice GEMM that runs out sets oz_err (checked at the end)
+        if (sliced) SWJ_CUDA_TRY(cudaMemsetAsync(c->oz_err, 0, sizeof(int), st));
         // steps [i0, i1) of the factorisation on both streams, joined into st at the end
         auto run_steps = [&](int i0, int i1) -> int {
         if (i0 >= i1) return SWJ_OK;
@@ -1190,10 +1173,9 @@ int swj_pc_setup(swj_ctx *c)
                 auto prods = [&](size_t off, int n_, double alpha) {
                     for (int c0 = 0; c0 < n_; c0 += (int)OL.maxP) {
                         const int cc = std::min((int)OL.maxP, n_ - c0);
-                        const int r_ = swj_ozaki_products(&c->cublas, sb, n1, OL.np, OL.s, OL.beta, cc,
-                                                          zQ + off + c0, c->oz_sa, c->oz_ea, c->oz_sb, c->oz_eb,
-                                                          alpha, c->oz_P, c->oz_ptrs + 3 * (size_t)OL.s * (off + c0),
-                                                          SWJ_OZ_USE_PTRS);
+                        const int r_ = swj_ozaki_products(sb, n1, OL.np, OL.s, OL.beta, cc, zQ + off + c0,
+                                                          c->oz_sa, OL.nsa, c->oz_ea, c->oz_sb, OL.nsb, c->oz_eb,
+                                                          alpha, c->oz_P, c->oz_err);
                         if (r_) return r_;
                     }
                     return (int)SWJ_OK;
@@ -1239,8 +1221,11 @@ int swj_pc_setup(swj_ctx *c)
     std::vector<int> info((size_t)nv * Mv);
     SWJ_CUDA_TRY(cudaMemcpyAsync(info.data(), c->pc_info, info.size() * sizeof(int),
                                  cudaMemcpyDeviceToHost, st));
+    int oz_err = 0;
+    if (c->oz_err) SWJ_CUDA_TRY(cudaMemcpyAsync(&oz_err, c->oz_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     SWJ_CUDA_TRY(cudaStreamSynchronize(st));
     SWJ_CUDA_TRY(cudaGetLastError());
+    if (oz_err) return SWJ_ETIMEOUT;
     for (size_t i = 0; i < info.size(); ++i)
         if (info[i] < 0) return SWJ_ETIMEOUT;
         else if (info[i] != 0) return SWJ_ESINGULAR;

@@ -60,8 +60,6 @@ void free_all(swj_ctx *c)
     free(c->eps);
     swj_graphs_free(c);
     swj_pc_free(c);
-    swj_cublas_destroy(c->cublas);
-    c->cublas = nullptr;
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
     if (c->tev) {

@@ -159,10 +159,9 @@ struct swj_ctx {
     void *oz_sa, *oz_sb;         // bf16 slices of the A (row-split) and B (column-split) factors
     int *oz_ea, *oz_eb;          // their row / column exponents
     float *oz_P;                 // slice products of one batch of block products
-    void **oz_ptrs;              // pointer arrays of the batched GEMM
+    int *oz_err;                 // set by the slice GEMM when a bounded wait ran out
     void *oz_desc;               // split lists and product lists of every step (device)
     size_t oz_desc_cap;
-    void *cublas;                // cuBLAS handle (bf16 GEMMs)
 
     // exact JVP (jvp.cu): tangents of the node arrays [4][nb][S] (zeta, g,
     // zeta_y, g_y), of the source records and target arrays (same layouts
@@ -258,19 +257,21 @@ void swj_dgemm_batched(cudaStream_t st, int m, int n, int k, double alpha,
 // ozaki.cu: FP64-accurate block products from bf16 slices (see there)
 // n: block size; np: n padded to a multiple of 8; beta bits per digit, s digits
 void swj_ozaki_params(int n, int *np, int *beta, int *s);
-// A factors (by_rows): slot layout [np][s][np] bf16 + [np] exponents;
-// B factors: [s][np][np] + [np]
+// Slot layout of both factors, K-major: [np rows (A) or columns (B)][s][np]
+// bf16, plus [np] row or column exponents
 int swj_ozaki_split(cudaStream_t st, bool by_rows, int n, int np, int s, int beta, int count,
                     const double *const *mats, const int *slots, void *slices, int *ex);
-// P: count * s * np^2 floats; ptrs: 3 * count * s pointers (the batched GEMM's
-// A, B, C arrays).  mode: SWJ_OZ_ALL fills ptrs, multiplies and combines;
-// SWJ_OZ_FILL_PTRS only fills ptrs (they depend on prods, sa, sb and P only);
-// SWJ_OZ_USE_PTRS multiplies and combines with ptrs filled before.
-enum { SWJ_OZ_ALL = 0, SWJ_OZ_FILL_PTRS = 1, SWJ_OZ_USE_PTRS = 2 };
-int swj_ozaki_products(void **handle, cudaStream_t st, int n, int np, int s, int beta, int count,
-                       const OzProd *prods, const void *sa, const int *ea, const void *sb, const int *eb,
-                       double alpha, float *P, void **ptrs, int mode = SWJ_OZ_ALL);
-void swj_cublas_destroy(void *handle);
+// the count block products prods (device list): T_d of every product on the
+// tensor cores into P (count * s * np^2 floats), then the exact combine into
+// each C; err (device word) is set if a bounded wait of the GEMM ran out
+int swj_ozaki_products(cudaStream_t st, int n, int np, int s, int beta, int count, const OzProd *prods,
+                       const void *sa, size_t nsa, const int *ea, const void *sb, size_t nsb, const int *eb,
+                       double alpha, float *P, int *err);
+// umma.cu: T_d = sum_{p <= d} a_p b_(d-p) of every product and digit level d
+// (tcgen05 bf16 MMAs, FP32 accumulators; exact for the sliced operands);
+// nsa, nsb: slots in sa, sb
+int swj_oz_gemm(cudaStream_t st, int np, int s, int count, const OzProd *prods, const void *sa, size_t nsa,
+                const void *sb, size_t nsb, float *P, int *err);
 void swj_dgemm(cudaStream_t st, int m, int n, int k, double alpha, const double *A, int lda,
                const double *B, int ldb, double beta, double *C, int ldc);
 
