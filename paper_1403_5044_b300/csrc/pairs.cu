@@ -1021,7 +1021,9 @@ void launch_x2(dim3 g, cudaStream_t st, int T_, int S_, int chunk, int, const vo
                                           *(const TgtArrays32 *)tg, partial, act);
 }
 
-// Compiled tile shapes; index 0 of each table is the untuned default.
+// Compiled tile shapes; index 0 of each table is the untuned default.  Only
+// shapes that compile without register spills are candidates (a spilling
+// shape reads and writes its spill slots through the memory system).
 const PairVariant kVar32[] = {
     {(const void *)k_pairs_s<float, 4>, 128, 4, ScalarLaunch<float, 4, 128>::go, "k_pairs_s<float,4>"},
     {(const void *)k_pairs_x2<2, 128, 1>, 128, 4, launch_x2<2, 128, 1>, "k_pairs_x2<2,128,1>"},
@@ -1029,23 +1031,15 @@ const PairVariant kVar32[] = {
     {(const void *)k_pairs_x2<4, 128, 1>, 128, 8, launch_x2<4, 128, 1>, "k_pairs_x2<4,128,1>"},
     {(const void *)k_pairs_x2<2, 256, 1>, 256, 4, launch_x2<2, 256, 1>, "k_pairs_x2<2,256,1>"},
     {(const void *)k_pairs_x2<4, 64, 1>, 64, 8, launch_x2<4, 64, 1>, "k_pairs_x2<4,64,1>"},
-    {(const void *)k_pairs_x2<2, 256, 3>, 256, 4, launch_x2<2, 256, 3>, "k_pairs_x2<2,256,3>"},
-    {(const void *)k_pairs_x2<2, 128, 5>, 128, 4, launch_x2<2, 128, 5>, "k_pairs_x2<2,128,5>"},
-    {(const void *)k_pairs_x2<2, 128, 6>, 128, 4, launch_x2<2, 128, 6>, "k_pairs_x2<2,128,6>"},
     {(const void *)k_pairs_x2<3, 256, 2>, 256, 6, launch_x2<3, 256, 2>, "k_pairs_x2<3,256,2>"},
     {(const void *)k_pairs_x2<1, 256, 4>, 256, 2, launch_x2<1, 256, 4>, "k_pairs_x2<1,256,4>"},
     {(const void *)k_pairs_x2r<2, 256, 2, false, 1>, 256, 4, launch_x2r<2, 256, 2, false, 1>, "k_pairs_x2r<2,256,2,0,1>"},
     {(const void *)k_pairs_x2r<2, 256, 2, true, 1>, 256, 4, launch_x2r<2, 256, 2, true, 1>, "k_pairs_x2r<2,256,2,1,1>"},
-    {(const void *)k_pairs_x2r<2, 256, 3, true, 1>, 256, 4, launch_x2r<2, 256, 3, true, 1>, "k_pairs_x2r<2,256,3,1,1>"},
-    {(const void *)k_pairs_x2r<2, 128, 4, true, 1>, 128, 4, launch_x2r<2, 128, 4, true, 1>, "k_pairs_x2r<2,128,4,1,1>"},
     {(const void *)k_pairs_x2r<3, 128, 2, true, 1>, 128, 6, launch_x2r<3, 128, 2, true, 1>, "k_pairs_x2r<3,128,2,1,1>"},
     {(const void *)k_pairs_x2r<1, 256, 4, true, 1>, 256, 2, launch_x2r<1, 256, 4, true, 1>, "k_pairs_x2r<1,256,4,1,1>"},
-    {(const void *)k_pairs_x2r<1, 256, 5, true, 1>, 256, 2, launch_x2r<1, 256, 5, true, 1>, "k_pairs_x2r<1,256,5,1,1>"},
     {(const void *)k_pairs_x2r<1, 256, 4, true, 2>, 256, 2, launch_x2r<1, 256, 4, true, 2>, "k_pairs_x2r<1,256,4,1,2>"},
     {(const void *)k_pairs_x2r<1, 256, 3, true, 2>, 256, 2, launch_x2r<1, 256, 3, true, 2>, "k_pairs_x2r<1,256,3,1,2>"},
-    {(const void *)k_pairs_x2r<2, 128, 4, false, 2>, 128, 4, launch_x2r<2, 128, 4, false, 2>, "k_pairs_x2r<2,128,4,0,2>"},
     {(const void *)k_pairs_x2r<2, 256, 2, false, 2>, 256, 4, launch_x2r<2, 256, 2, false, 2>, "k_pairs_x2r<2,256,2,0,2>"},
-    {(const void *)k_pairs_x2r<1, 128, 8, true, 2>, 128, 2, launch_x2r<1, 128, 8, true, 2>, "k_pairs_x2r<1,128,8,1,2>"},
 };
 const PairVariant kVar64[] = {
     {(const void *)k_pairs_r64<2>, 128, 2, launch_r64<2>, "k_pairs_r64<2>"},
