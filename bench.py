@@ -77,7 +77,10 @@ def parse():
     ap.add_argument("--serve", action="store_true",
                     help="only the serving workload: 2000 Poisson requests per rate, rates swept over "
                          "{0.25, 0.5, 0.75, 1.0, 1.25} x the measured saturated rate, mixed and FP64")
-    ap.add_argument("--serve-rates", default="0.25,0.5,0.75,1.0,1.25")
+    ap.add_argument("--serve-rates", default="0.25,0.5,0.75,1.0,1.25",
+                    help="--serve: rate factors of the mixed block (x its saturated rate)")
+    ap.add_argument("--serve-rates-fp64", default="0.5,1.0",
+                    help="--serve: rate factors of the FP64 block (x its own saturated rate)")
     ap.add_argument("--large", action="store_true",
                     help="only the 721x241 workload (F = 0.7, eps = 0.8): one mixed solve from the flat "
                          "guess, reported with its counters (minutes)")
@@ -381,7 +384,9 @@ def run_ours(args):
                      "max_abs_dzeta_fp64": float(np.abs(zeta64 - zo).max()),
                      "max_abs_dphi_fp64": float(np.abs(phi64 - po).max())}
 
-    # ---- end to end through the public API with host buffers
+    # ---- end to end through the C ABI with host buffers: swj_solve_host copies the
+    # pinned host initial guess in, rebuilds the preconditioner, solves, and copies
+    # the surface zeta back to pinned host memory, all inside the timed region
     u_host = torch.empty(ctx.n_unknowns, dtype=torch.float64).pin_memory()
     u_host.copy_(torch.from_numpy(W.flat_state(spec)))
     z_host = torch.empty(spec.N * spec.M, dtype=torch.float64).pin_memory()
@@ -392,14 +397,11 @@ def run_ours(args):
         flush.fill_(float(k))
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        u.copy_(u_host, non_blocking=True)
-        ctx.precond_setup()
-        ctx.solve(u)
-        ctx.unpack(u, zeta, None)
-        z_host.copy_(zeta, non_blocking=True)
+        ctx.solve_host(u_host, True, None, z_host, None)
         b.record(stream)
         torch.cuda.synchronize()
         e2e_ms.append(a.elapsed_time(b))
+    e2e_dz = float(np.abs(z_host.numpy() - zeta_mixed).max())
     e2e_value, _ = replica_rate(sum(e2e_ms), args.steps, world, dist)
 
     exact = exact_jvp_section(spec, F, eps, args, stream, flush, zeta_mixed) if rank == 0 else None
@@ -481,7 +483,9 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value,
                 "unit": "solves/s", "h2d_bytes_per_step": ctx.n_unknowns * 8,
-                "d2h_bytes_per_step": spec.N * spec.M * 8},
+                "d2h_bytes_per_step": spec.N * spec.M * 8,
+                "call": "swj_solve_host (C ABI, pinned host buffers in and out, preconditioner rebuilt)",
+                "max_abs_dzeta_vs_device_solve": e2e_dz},
         "gpu_launches": int(launches),
         "exact_jvp": exact,
         "batch": batch,
@@ -693,12 +697,13 @@ def serve_block(mode, count, rate_factors):
 def run_serve(args):
     import torch
     torch.cuda.set_device(0)
-    rates = [float(r) for r in args.serve_rates.split(",")]
+    rates = {"mixed": [float(r) for r in args.serve_rates.split(",")],
+             "fp64": [float(r) for r in args.serve_rates_fp64.split(",")]}
     out = {"serve": True, "workload": SERVE_WORKLOAD}
     counts = {"mixed": args.serve_requests, "fp64": args.serve_requests_fp64}
     for mode in ("mixed", "fp64"):
         if counts[mode] > 0:
-            out[mode] = serve_block(mode, counts[mode], rates)
+            out[mode] = serve_block(mode, counts[mode], rates[mode])
             print(json.dumps({"mode": mode, **out[mode]}), flush=True)
     print(json.dumps(out), flush=True)
 

@@ -320,6 +320,21 @@ int swj_precond_sweep_clusters(const swj_ctx *ctx);
  * else SWJ_ENOTCONV / SWJ_ELINESEARCH / SWJ_ENAN.  Synchronous. */
 int swj_solve(swj_ctx *ctx, double *u_dev_inout, swj_stats *stats);
 
+/* The whole solve from and to HOST memory, for callers whose data live on the
+ * host: u0_host (2(N+1)M doubles; pinned host memory copies fastest, pageable
+ * works) is copied to the device as the initial guess; with setup != 0 the
+ * preconditioner is rebuilt first (with setup = 0 it is built only if the
+ * context has none); then the solve of swj_solve runs, and the result is
+ * copied back: u_host the final iterate (may be NULL; may alias u0_host),
+ * zeta_host and phi_host the surface and potential at the nodes ([M][N]
+ * row-major, x fastest; either may be NULL).  The first call allocates the
+ * context's device staging, 2(N+1)M + 2NM doubles, counted by
+ * swj_workspace_bytes.  Single-instance contexts only (SWJ_EINVAL for a
+ * batch).  Synchronous.  Returns swj_solve's status, or SWJ_EINVAL /
+ * SWJ_ENOMEM / SWJ_ECUDA / a set-up status. */
+int swj_solve_host(swj_ctx *ctx, const double *u0_host, int setup, double *u_host, double *zeta_host,
+                   double *phi_host, swj_stats *stats);
+
 /* zeta_dev, phi_dev <- zeta and phi on the mesh ([M][N] row-major, index
  * (l-1) N + (k-1)) rebuilt from u by Eq. zetaapprox.  Either may be NULL.
  * Async. */

@@ -51,7 +51,7 @@ void free_all(swj_ctx *c)
                     c->Ival, c->src64, c->src32, c->tgt64_base, c->tgt32_base, c->partial,
                     c->u_tmp, c->E_tmp, c->u_tmp2, c->E_tmp2, c->E_cur, c->u_try, c->E_try, c->E_base32, c->du,
                     c->rvec, c->dscal, c->red, c->V, c->Z, c->Fd, c->epsd, c->act_d,
-                    c->dnode, c->tsrc64, c->tsrc32, c->ttgt64_base, c->ttgt32_base, c->de2part};
+                    c->dnode, c->tsrc64, c->tsrc32, c->ttgt64_base, c->ttgt32_base, c->de2part, c->hs_buf};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->hpin) cudaFreeHost(c->hpin);
@@ -519,6 +519,36 @@ int swj_solve(swj_ctx *c, double *u, swj_stats *st)
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return SWJ_ECUDA;
     return rc;
+}
+
+int swj_solve_host(swj_ctx *c, const double *u0_host, int setup, double *u_host, double *zeta_host,
+                   double *phi_host, swj_stats *st)
+{
+    if (!c || !u0_host || c->nb != 1) return SWJ_EINVAL;
+    const size_t nu = (size_t)c->nu, S = (size_t)c->S;
+    if (!c->hs_buf) {
+        const size_t b = (nu + 2 * S) * sizeof(double);
+        if (cudaMalloc(&c->hs_buf, b) != cudaSuccess) {
+            c->hs_buf = nullptr;
+            return SWJ_ENOMEM;
+        }
+        c->bytes += b;
+    }
+    double *u = c->hs_buf, *z = u + nu, *p = z + S;
+    SWJ_CUDA_TRY(cudaMemcpyAsync(u, u0_host, nu * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    if (setup || !c->pc_ready) {
+        const int rc = swj_pc_setup(c);
+        if (rc) return rc;
+    }
+    const int src = swj_solve_impl(c, u, st);
+    if (src == SWJ_ECUDA) return src;
+    if (zeta_host || phi_host) swj_launch_unpack(c, u, zeta_host ? z : nullptr, phi_host ? p : nullptr);
+    if (zeta_host) SWJ_CUDA_TRY(cudaMemcpyAsync(zeta_host, z, S * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (phi_host) SWJ_CUDA_TRY(cudaMemcpyAsync(phi_host, p, S * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (u_host) SWJ_CUDA_TRY(cudaMemcpyAsync(u_host, u, nu * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    SWJ_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    SWJ_CUDA_TRY(cudaGetLastError());
+    return src;
 }
 
 int swj_unpack(swj_ctx *c, const double *u, double *zeta, double *phi)

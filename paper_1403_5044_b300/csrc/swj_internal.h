@@ -104,6 +104,7 @@ struct swj_ctx {
 
     // JVP / solver temporaries, [nb][nu]
     double *u_tmp, *E_tmp;           // JVP: u + h v and E(u + h v)
+    double *hs_buf;                  // swj_solve_host staging: u [nu], zeta [S], phi [S] (first call)
     double *u_tmp2, *E_tmp2;         // central-difference JVP: u - h v and E(u - h v)
     double *E_cur, *u_try, *E_try;   // Newton: current residual, line-search trial
     double *E_base32;                // MIXED refinement: FP32 residual at u (JVP base)

@@ -125,6 +125,7 @@ def lib():
             "swj_server_destroy": (None, [_vp]),
             "swj_set_params": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double]),
             "swj_set_opts": (ctypes.c_int, [_vp, P(Opts)]),
+            "swj_solve_host": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, _vp, _vp, P(Stats)]),
             "swj_set_test_hooks": (ctypes.c_int, [_vp, ctypes.c_int]),
             "swj_workspace_bytes": (ctypes.c_size_t, [_vp]),
             "swj_initial_guess_flat": (ctypes.c_int, [_vp, _vp]),
@@ -202,6 +203,20 @@ def _ptr(t):
     if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
         raise ValueError("expected a contiguous CUDA float64 tensor")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _host_ptr(a):
+    """Address of a contiguous float64 host buffer (numpy array or CPU torch tensor), or None."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if a.is_cuda or str(a.dtype) != "torch.float64" or not a.is_contiguous():
+            raise ValueError("expected a contiguous float64 CPU tensor")
+        return _vp(a.data_ptr())
+    import numpy as np
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]):
+        raise ValueError("expected a contiguous float64 numpy array")
+    return _vp(a.ctypes.data)
 
 
 def _check(rc, what):
@@ -327,6 +342,18 @@ class Context:
         rc = lib().swj_solve(self._h, _ptr(u), ctypes.cast(ctypes.byref(st), _vp))
         if check:
             _check(rc, "swj_solve")
+        d = st.as_dict()
+        d["rc"] = rc
+        return d
+
+    def solve_host(self, u0_host, setup=True, u_host=None, zeta_host=None, phi_host=None, check=True):
+        """swj_solve_host: the solve from and to host buffers (contiguous
+        float64 numpy arrays or CPU torch tensors, pinned or not)."""
+        st = Stats()
+        rc = lib().swj_solve_host(self._h, _host_ptr(u0_host), int(bool(setup)), _host_ptr(u_host),
+                                  _host_ptr(zeta_host), _host_ptr(phi_host), ctypes.byref(st))
+        if check:
+            _check(rc, "swj_solve_host")
         d = st.as_dict()
         d["rc"] = rc
         return d

@@ -230,6 +230,37 @@ def test_181x61_solves_match_the_stored_oracle_root():
         assert dz <= tol and dp <= tol, (mode, dz, dp)
 
 
+def test_solve_from_host_buffers_equals_the_device_solve():
+    """swj_solve_host (host u in, host u / zeta / phi out, preconditioner
+    rebuilt) gives the device-pointer solve's results bit for bit, from pinned
+    and from pageable host memory, and rejects a batch context."""
+    spec, F, eps = W.SOLVE_41x21
+    with swj.Context.from_spec(spec, F, eps, solve_mode="mixed", block_bw=5) as ctx:
+        u = ctx.initial_guess_flat(ctx.vector())
+        ctx.precond_setup()
+        st = ctx.solve(u)
+        zeta = torch.empty(spec.N * spec.M, dtype=torch.float64, device="cuda")
+        phi = torch.empty_like(zeta)
+        ctx.unpack(u, zeta, phi)
+        ctx.sync()
+        ref = (u.cpu().numpy(), zeta.cpu().numpy(), phi.cpu().numpy())
+        u0 = W.flat_state(spec)
+        for pinned in (True, False):
+            uh = torch.from_numpy(u0.copy())
+            zh = torch.empty(spec.N * spec.M, dtype=torch.float64)
+            ph = torch.empty_like(zh)
+            if pinned:
+                uh, zh, ph = uh.pin_memory(), zh.pin_memory(), ph.pin_memory()
+            sh = ctx.solve_host(uh, True, uh, zh, ph)
+            assert sh["rc"] == 0 and sh["newton_iters"] == st["newton_iters"]
+            assert np.array_equal(uh.numpy(), ref[0])
+            assert np.array_equal(zh.numpy(), ref[1]) and np.array_equal(ph.numpy(), ref[2])
+    with swj.BatchContext.from_spec(spec, [0.7, 0.8], [0.1, 0.1]) as b:
+        rc = swj.lib().swj_solve_host(b._h, swj._host_ptr(np.zeros(2 * spec.n_unknowns)), 1, None, None, None,
+                                      None)
+        assert rc == swj.EINVAL
+
+
 def test_refinement_precisions_reach_the_same_root():
     """MIXED solves refined with float-float and with FP64 residuals: the same
     FP64 root (the float-float sum is as accurate as FP64), both roots of the
