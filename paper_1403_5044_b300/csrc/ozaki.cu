@@ -99,7 +99,8 @@ __global__ void k_oz_split_rows(int n, int np, int s, int beta, const double *co
 // Split by columns: slot slots[m] of sb, layout [slot][np columns][s][np rows]
 // (column c, digit q, row r: K-major, the layout of the A slices), digits
 // with the entry's sign; column exponents ex[slot][np].  Block per (32-column
-// strip, matrix), 256 threads: the column maxima with lanes over columns and
+// strip, matrix), up to 32 warps (the launch uses 32: a set-up call splits few
+// matrices, so the blocks are few): the column maxima with lanes over columns and
 // warps over rows (coalesced reads), then 32 x 32 tiles through shared
 // memory, written with lanes over rows (64-byte runs per column and digit).
 __global__ void k_oz_split_cols(int n, int np, int s, int beta, const double *const *mats, const int *slots,
@@ -207,7 +208,7 @@ int swj_ozaki_split(cudaStream_t st, bool by_rows, int n, int np, int s, int bet
     __nv_bfloat16 *sl = (__nv_bfloat16 *)slices;
     SWJ_COUNT_LAUNCH();
     if (by_rows) k_oz_split_rows<<<dim3(np, count), 128, 0, st>>>(n, np, s, beta, mats, slots, sl, ex);
-    else k_oz_split_cols<<<dim3(nblk(np, 32), count), 256, 0, st>>>(n, np, s, beta, mats, slots, sl, ex);
+    else k_oz_split_cols<<<dim3(nblk(np, 32), count), 1024, 0, st>>>(n, np, s, beta, mats, slots, sl, ex);
     SWJ_CUDA_TRY(cudaGetLastError());
     return SWJ_OK;
 }
