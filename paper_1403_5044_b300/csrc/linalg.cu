@@ -332,8 +332,10 @@ void swj_dgemm(cudaStream_t st, int m, int n, int k, double alpha, const double 
                const double *B, int ldb, double beta, double *C, int ldc)
 {
     if (m <= 0 || n <= 0) return;
-    dim3 grid(nblk(n, 32), nblk(m, 32), 1);
+    // 16 x 16 output tiles: a single product of a few hundred rows must spread
+    // over the SMs (the arithmetic of an element is the same for every tile)
+    dim3 grid(nblk(n, 16), nblk(m, 16), 1);
     SWJ_COUNT_LAUNCH();
-    k_dgemm<32><<<grid, 256, 0, st>>>(m, n, k, alpha, nullptr, A, lda, nullptr, B, ldb, beta,
+    k_dgemm<16><<<grid, 256, 0, st>>>(m, n, k, alpha, nullptr, A, lda, nullptr, B, ldb, beta,
                                       nullptr, C, ldc);
 }

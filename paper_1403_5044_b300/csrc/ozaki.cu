@@ -25,6 +25,7 @@
 // products are batched.  Matrices are padded with zeros to a multiple of 8
 // (16-byte digit rows for the tensor-memory-access loads).
 #include "swj_internal.h"
+#include "oz_round.cuh"
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -44,11 +45,33 @@ __device__ __forceinline__ unsigned long long fixed_bits(double x, int e, int bi
     return -sh >= 64 ? 0ull : (m >> -sh);
 }
 
-__device__ __forceinline__ int row_exponent(double mx)
+// The magnitude and sign of x from its bit pattern.  B300 runs FP64
+// comparisons and min/max on its FP64 pipe (two lanes per clock per SM), so the
+// splits order magnitudes as integers: for finite doubles the order of
+// |x|'s bit patterns is the order of |x|.
+__device__ __forceinline__ unsigned long long mag_bits(double x)
 {
-    int e = 0;
-    if (mx > 0.0) frexp(mx, &e);   // mx = f 2^e, f in [1/2, 1): every |x| < 2^e
-    return e;
+    return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b)
+{
+    return a > b ? a : b;
+}
+// x < 0 (false for -0)
+__device__ __forceinline__ bool negative(double x)
+{
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    return (u >> 63) && (u << 1);
+}
+
+// e with |x| = f 2^e, f in [1/2, 1) (frexp's exponent) for the magnitude with
+// bit pattern a; 0 for zero.  Every entry of the row is then below 2^e.
+__device__ __forceinline__ int row_exponent(unsigned long long a)
+{
+    if (a == 0) return 0;
+    const int E = (int)(a >> 52);
+    if (E) return E - 1022;           // normal: [2^(E-1023), 2^(E-1022))
+    return (64 - __clzll(a)) - 1074;  // subnormal: a 2^-1074
 }
 
 // Split row-major n x n FP64 matrices mats[m] by rows: slot slots[m] of sa,
@@ -67,17 +90,17 @@ __global__ void k_oz_split_rows(int n, int np, int s, int beta, const double *co
         return;
     }
     const double *row = mats[m] + (size_t)r * n;
-    __shared__ double red[32];
-    double mx = 0.0;
-    for (int j = threadIdx.x; j < n; j += blockDim.x) mx = fmax(mx, fabs(row[j]));
+    __shared__ unsigned long long red[32];
+    unsigned long long mx = 0;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) mx = umax64(mx, mag_bits(row[j]));
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    for (int o = 16; o > 0; o >>= 1) mx = umax64(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
     __syncthreads();
     if (threadIdx.x < 32) {
-        double v = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+        unsigned long long v = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0ull;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+        for (int o = 16; o > 0; o >>= 1) v = umax64(v, __shfl_xor_sync(0xffffffffu, v, o));
         if (threadIdx.x == 0) red[0] = v;
     }
     __syncthreads();
@@ -88,7 +111,7 @@ __global__ void k_oz_split_rows(int n, int np, int s, int beta, const double *co
     for (int j = threadIdx.x; j < np; j += blockDim.x) {
         const double x = (j < n) ? row[j] : 0.0;
         const unsigned long long X = fixed_bits(x, e, bits);
-        const float sg = (x < 0.0) ? -1.f : 1.f;
+        const float sg = negative(x) ? -1.f : 1.f;
         for (int p = 0; p < s; ++p) {
             const unsigned dgt = (unsigned)(X >> (beta * (s - 1 - p))) & mask;
             out[(size_t)p * np + j] = __float2bfloat16(sg * (float)dgt);   // exact: dgt < 2^8
@@ -111,15 +134,16 @@ __global__ void k_oz_split_cols(int n, int np, int s, int beta, const double *co
     const double *A = mats[m];
     const int slot = slots[m];
     __shared__ double red[32][33];
+    __shared__ unsigned long long mred[32][32];
     __shared__ int ec[32];
     const int c = c0 + lane;
-    double mx = 0.0;
+    unsigned long long mx = 0;
     if (c < n)
-        for (int r = w; r < n; r += nw) mx = fmax(mx, fabs(A[(size_t)r * n + c]));
-    red[w][lane] = mx;
+        for (int r = w; r < n; r += nw) mx = umax64(mx, mag_bits(A[(size_t)r * n + c]));
+    mred[w][lane] = mx;
     __syncthreads();
     if (w == 0) {
-        for (int q = 1; q < nw; ++q) mx = fmax(mx, red[q][lane]);
+        for (int q = 1; q < nw; ++q) mx = umax64(mx, mred[q][lane]);
         const int e = (c < n) ? row_exponent(mx) : 0;
         ec[lane] = e;
         if (c < np) ex[(size_t)slot * np + c] = e;
@@ -140,7 +164,7 @@ __global__ void k_oz_split_cols(int n, int np, int s, int beta, const double *co
             if (c0 + cc >= np || r >= np) continue;
             const double x = red[lane][cc];
             const unsigned long long X = fixed_bits(x, ec[cc], bits);
-            const float sg = (x < 0.0) ? -1.f : 1.f;
+            const float sg = negative(x) ? -1.f : 1.f;
             __nv_bfloat16 *o = out + (size_t)(c0 + cc) * rowlen + r;
             for (int q = 0; q < s; ++q) {
                 const unsigned dgt = (unsigned)(X >> (beta * (s - 1 - q))) & mask;
@@ -155,32 +179,39 @@ __global__ void k_oz_split_cols(int n, int np, int s, int beta, const double *co
 // S = sum_d T_d 2^(beta (s-1-d)) (below 2^80) times 2^(-beta (s+1)): it is
 // accumulated exactly in 128-bit two's complement with integer operations
 // (B300's FP64 pipe, two FMAs per clock per SM, would bound it otherwise) and
-// rounded to FP64 once.  Thread per element of the n x n block.
+// rounded to FP64 (the low word to 53 bits, then the sum; oz_round.cuh).
+// Thread per element of the n x n block.
+// block (32, 8) over 32 columns x 8 rows of the n x n block, grid.z = product
+template <int S_, int B_>
 __global__ void k_oz_combine(int n, int np, int s, int beta, const OzProd *__restrict__ prods,
                              const float *__restrict__ P, const int *__restrict__ ea, const int *__restrict__ eb,
                              double alpha)
 {
-    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= (size_t)n * n) return;
-    const int t = blockIdx.y;
+    const int c = blockIdx.x * 32 + threadIdx.x, r = blockIdx.y * 8 + threadIdx.y;
+    if (r >= n || c >= n) return;
+    const int t = blockIdx.z;
     const OzProd o = prods[t];
-    const int r = (int)(e / n), c = (int)(e % n);
     const size_t n2 = (size_t)np * np;
     const float *Pt = P + (size_t)t * s * n2 + (size_t)r * np + c;
-    long long hi = 0;
-    unsigned long long lo = 0;
-    for (int d = 0; d < s; ++d) {
-        const long long q = (long long)__float2int_rn(Pt[(size_t)d * n2]);   // exact: |T_d| < 2^24
-        const int sh = beta * (s - 1 - d);                                  // 0 <= sh < 64
-        const unsigned long long tl = (unsigned long long)q << sh;           // low word of q 2^sh
-        const long long th = sh ? (q >> (64 - sh)) : (q >> 63);             // high word (sign-extended)
-        lo += tl;
-        hi += th + (lo < tl ? 1 : 0);
+    int64_t hi;
+    uint64_t lo;
+    if constexpr (S_ > 0) {
+        int32_t q[S_];
+#pragma unroll
+        for (int d = 0; d < S_; ++d) q[d] = __float2int_rn(Pt[(size_t)d * n2]);   // exact: |T_d| < 2^24
+        oz_horner<S_, B_>(q, hi, lo);
+    } else {
+        int32_t q[16];
+        for (int d = 0; d < s; ++d) q[d] = __float2int_rn(Pt[(size_t)d * n2]);
+        oz_sum_any(q, s, beta, hi, lo);
     }
-    // |hi| < 2^16 is exact in FP64; one rounding of lo, one of the sum
-    double v = fma((double)hi, 18446744073709551616.0, (double)lo);
-    v = ldexp(v, ea[(size_t)o.a * np + r] + eb[(size_t)o.b * np + c] - beta * (s + 1));
-    double *C = o.C + e;
+    // the double nearest to hi 2^64 + RN(lo), scaled: bit pattern from integer
+    // operations (oz_round.cuh), ldexp only outside the normal range
+    const int e2 = ea[(size_t)o.a * np + r] + eb[(size_t)o.b * np + c] - beta * (s + 1);
+    bool fb;
+    double v = __longlong_as_double((long long)oz_round_bits(hi, lo, e2, &fb));
+    if (fb) v = ldexp(v, e2);
+    double *C = o.C + (size_t)r * n + c;
     *C = o.accumulate ? fma(alpha, v, C[0]) : alpha * v;
 }
 
@@ -218,10 +249,16 @@ int swj_ozaki_products(cudaStream_t st, int n, int np, int s, int beta, int coun
                        double alpha, float *P, int *err)
 {
     if (count <= 0) return SWJ_OK;
+    if (s < 1 || s > 16) return SWJ_EINVAL;
     int rc = swj_oz_gemm(st, np, s, count, prods, sa, nsa, sb, nsb, P, err);
     if (rc) return rc;
     SWJ_COUNT_LAUNCH();
-    k_oz_combine<<<dim3(nblk((long)n * n, 256), count), 256, 0, st>>>(n, np, s, beta, prods, P, ea, eb, alpha);
+    const dim3 grid(nblk(n, 32), nblk(n, 8), count), block(32, 8);
+    if (s == 10 && beta == 6) k_oz_combine<10, 6><<<grid, block, 0, st>>>(n, np, s, beta, prods, P, ea, eb, alpha);
+    else if (s == 8 && beta == 7) k_oz_combine<8, 7><<<grid, block, 0, st>>>(n, np, s, beta, prods, P, ea, eb, alpha);
+    else if (s == 12 && beta == 5) k_oz_combine<12, 5><<<grid, block, 0, st>>>(n, np, s, beta, prods, P, ea, eb, alpha);
+    else if (s == 7 && beta == 8) k_oz_combine<7, 8><<<grid, block, 0, st>>>(n, np, s, beta, prods, P, ea, eb, alpha);
+    else k_oz_combine<0, 0><<<grid, block, 0, st>>>(n, np, s, beta, prods, P, ea, eb, alpha);
     SWJ_CUDA_TRY(cudaGetLastError());
     return SWJ_OK;
 }

@@ -99,12 +99,21 @@ __global__ void k_build_ABC(int N, double x1, double dx, double nrad, double F,
 // algorithm), at coef[r], coef[n1 + r], coef[2 n1 + r].
 __global__ void k_tri_coef(int n1, const double *__restrict__ A, double *__restrict__ coef)
 {
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    // the three diagonals into shared memory at once, then the recurrence on
+    // one thread (a dependent division per row)
+    extern __shared__ double dg[];   // sub, dia, sup: 3 n1
+    for (int r = threadIdx.x; r < n1; r += blockDim.x) {
+        dg[r] = r > 0 ? A[r * n1 + r - 1] : 0.0;
+        dg[n1 + r] = A[r * n1 + r];
+        dg[2 * n1 + r] = r + 1 < n1 ? A[r * n1 + r + 1] : 0.0;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
     double prev = 0.0;
     for (int r = 0; r < n1; ++r) {
-        double sub = r > 0 ? A[r * n1 + r - 1] : 0.0;
-        double dia = A[r * n1 + r];
-        double sup = r + 1 < n1 ? A[r * n1 + r + 1] : 0.0;
+        double sub = dg[r];
+        double dia = dg[n1 + r];
+        double sup = dg[2 * n1 + r];
         double rd = 1.0 / (dia - sub * prev);
         prev = sup * rd;
         coef[r] = prev;
@@ -117,9 +126,13 @@ __global__ void k_tri_coef(int n1, const double *__restrict__ A, double *__restr
 // Rhs are n1 x ncol row-major.  A column per thread, blockDim.x columns per
 // block: the block's columns are copied into shared memory first (all rows
 // in flight), both sweeps run there, and X is written as it is found.
-__global__ void k_tri_cols(int n1, int ncol, const double *__restrict__ coef, const double *Rhs, double *X)
+// blockIdx.y selects (Rhs0, X0) or (Rhs1, X1): two systems in one launch.
+__global__ void k_tri_cols(int n1, int ncol, const double *__restrict__ coef, const double *Rhs0, double *X0,
+                           const double *Rhs1, double *X1)
 {
     extern __shared__ double sc[];
+    const double *Rhs = blockIdx.y ? Rhs1 : Rhs0;
+    double *X = blockIdx.y ? X1 : X0;
     const int nc = blockDim.x, lane = threadIdx.x;
     const int col = blockIdx.x * nc + lane;
     if (col >= ncol) return;
@@ -178,18 +191,28 @@ __global__ void k_flat_records(int N, int M, double dx, double dy, SrcRecS<T> *s
     }
 }
 
-// diag[t] = (1/2) sum_s w K3 - (1/2) I_flat, the PreD correction of target t.
-__global__ void k_diag_corr(int N, int M, int P, double dx, double dy,
-                            const double *__restrict__ partial, double *__restrict__ out)
+// I of the flat surface at every target (the closed form of the S2 integral
+// with A = C = 1, B = 0), into out[t]; k_diag_corr completes it in place.
+__global__ void k_flat_I(int N, int M, double dx, double dy, double *__restrict__ out)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    int Tn = (N - 1) * M;
+    if (t >= Tn) return;
+    int k = t % (N - 1), l = t / (N - 1);
+    out[t] = swj_I_S2(1.0, 0.0, 1.0, N, M, k, l, dx, dy);
+}
+
+// diag[t] = (1/2) sum_s w K3 - (1/2) I_flat, the PreD correction of target t
+// (I_flat read from diag[t], written there by k_flat_I).
+__global__ void k_diag_corr(int N, int M, int P, const double *__restrict__ partial, double *__restrict__ diag)
 {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     int Tn = (N - 1) * M;
     if (t >= Tn) return;
     double s = 0.0;
     for (int p = 0; p < P; ++p) s += partial[(size_t)p * Tn + t];
-    int k = t % (N - 1), l = t / (N - 1);
-    double I = swj_I_S2(1.0, 0.0, 1.0, N, M, k, l, dx, dy);
-    out[t] = 0.5 * s - 0.5 * I;
+    double I = diag[t];
+    diag[t] = 0.5 * s - 0.5 * I;
 }
 
 // Kernel values 1 / sqrt(ddx^2 + ddy^2) of D's entries: row di = i - k + N - 1
@@ -207,82 +230,117 @@ __global__ void k_k3_table(int N, int M, double dx, double dy, double *__restric
     tab[e] = 1.0 / sqrt(ddx * ddx + ddy * ddy);
 }
 
-// Entry (r, c) of block (l, m) of D, the zeta-zeta block of P (block rows l, m
-// of the mesh; it does not depend on F); tab from k_k3_table.
-__device__ __forceinline__ double d_entry(int N, int M, int l, int m, int r, int c, double x1, double dx,
-                                          double dy, double nrad, const double *__restrict__ diag,
-                                          const double *__restrict__ tab)
+// Block (l, m) of D, the zeta-zeta block of P (block rows l, m of the mesh; it
+// does not depend on F), row-major n1 x n1 at `out`; tab from k_k3_table.
+//   row 0 (E5_l: x1 zeta_x,1 + n zeta_1) and row 1 (E6_l: x1 (zx_2 - zx_1)/dx +
+//   n zx_1) on the diagonal block only;
+//   row r = k + 1 >= 2, column c = i + 1 >= 1 (E2_k,l versus (zeta_x)_{i, m}):
+//   -w K3 with w = dx dy ci cj (trapezoid weight of source (i, m)) and K3 =
+//   1/|x - x'| + 1/|x - x'_image| at ddx = (i - k + 1/2) dx, ddy = (m - l) dy,
+//   (m + l) dy, plus the PreD correction diag at columns k and k + 1 of the
+//   diagonal block.
+// -w K3 depends on the column only through i - k and ci, so the block first
+// tabulates it (V[ci][i - k + N - 1], 2 (2N - 2) values, dynamic shared
+// memory) and every entry is then a look-up: each value is formed by the same
+// operations as entry by entry, and B300's FP64 pipe (two FMAs per clock per
+// SM) does 45x less work.  With G1 != nullptr the diagonal block also gets
+// -f G1 (S = D - G / F^2).  The calling CTA's threads all take part.
+__device__ __forceinline__ void d_block(int N, int M, int l, int m, double x1, double dx, double dy, double nrad,
+                                        const double *__restrict__ diag, const double *__restrict__ tab,
+                                        const double *__restrict__ G1, double f, double *__restrict__ out,
+                                        double *V)
 {
-    double v = 0.0;
-    if (r == 0) {                      // E5_l: x1 zeta_x,1 + n zeta_1
-        if (m == l) v = (c == 0) ? nrad : (c == 1 ? x1 : 0.0);
-    } else if (r == 1) {               // E6_l: x1 (zx_2 - zx_1)/dx + n zx_1
-        if (m == l) v = (c == 1) ? nrad - x1 / dx : (c == 2 ? x1 / dx : 0.0);
-    } else if (c >= 1) {               // E2_k,l versus (zeta_x)_{c, m}
-        int k = r - 1, i = c - 1;
-        double ci = (i == 0 || i == N - 1) ? 0.5 : 1.0;
-        double cj = (m == 0 || m == M - 1) ? 0.5 : 1.0;
-        double w = dx * dy * ci * cj;
-        // 1/|x - x'| + 1/|x - x'_image| at ddx = (i - k + 1/2) dx, ddy = (m - l) dy, (m + l) dy
-        const double *trow = tab + (size_t)(i - k + N - 1) * (2 * M - 1);
-        double K3 = trow[m > l ? m - l : l - m] + trow[m + l];
-        v = -w * K3;
-        if (m == l && (c == k || c == k + 1)) v += diag[(size_t)l * (N - 1) + (k - 1)];
+    const int n1 = N + 1, nd = 2 * N - 2;
+    const double cj = (m == 0 || m == M - 1) ? 0.5 : 1.0;
+    const int ja = m > l ? m - l : l - m, jb = m + l;
+    for (int q = threadIdx.x; q < 2 * nd; q += blockDim.x) {
+        const int cs = q >= nd, di = q - cs * nd;
+        const double ci = cs ? 0.5 : 1.0;
+        const double w = dx * dy * ci * cj;
+        const double *trow = tab + (size_t)di * (2 * M - 1);
+        const double K3 = trow[ja] + trow[jb];
+        V[q] = -w * K3;
     }
-    return v;
+    __syncthreads();
+    // Off the diagonal block every entry is a look-up (no FP64 instruction: B300
+    // issues a predicated-off one at full cost); the diagonal block also
+    // takes the E5/E6 rows, the PreD correction and -f G1.
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (m != l) {
+        for (int r = warp; r < n1; r += nw) {
+            double *orow = out + (size_t)r * n1;
+            for (int c = lane; c < n1; c += 32) {
+                const int cs = (c == 1 || c == N) ? 1 : 0;   // ci = 1/2 at the end columns i = 0, N - 1
+                orow[c] = (r >= 2 && c >= 1) ? V[cs * nd + (c - r + N - 1)] : 0.0;
+            }
+        }
+        return;
+    }
+    for (int r = warp; r < n1; r += nw) {
+        double *orow = out + (size_t)r * n1;
+        const double dg = r >= 2 ? diag[(size_t)l * (N - 1) + (r - 2)] : 0.0;
+        for (int c = lane; c < n1; c += 32) {
+            double v = 0.0;
+            if (r == 0) {
+                v = (c == 0) ? nrad : (c == 1 ? x1 : 0.0);
+            } else if (r == 1) {
+                v = (c == 1) ? nrad - x1 / dx : (c == 2 ? x1 / dx : 0.0);
+            } else if (c >= 1) {
+                const int cs = (c == 1 || c == N) ? 1 : 0;
+                v = V[cs * nd + (c - r + N - 1)];
+                if (c == r - 1 || c == r) v += dg;
+            }
+            if (G1) v -= f * G1[(size_t)r * n1 + c];
+            orow[c] = v;
+        }
+    }
 }
 
-// D of one instance (the band of D): block (l, m = l - h + slot).
+// zero (or identity) n1 x n1 block
+__device__ __forceinline__ void const_block(int n1, bool identity, double *__restrict__ out)
+{
+    const size_t n2 = (size_t)n1 * n1;
+    for (size_t e = threadIdx.x; e < n2; e += blockDim.x) out[e] = (identity && e % (n1 + 1) == 0) ? 1.0 : 0.0;
+}
+
+// D of one instance (the band of D): block (l, m = l - h + slot), a CTA per
+// block, blockIdx.x = l (2h + 1) + slot.
 __global__ void k_fill_D(int N, int M, int h, double x1, double dx, double dy, double nrad,
                          const double *__restrict__ diag, const double *__restrict__ tab,
                          double *__restrict__ band)
 {
-    const size_t n1 = N + 1, nb = 2 * h + 1;
-    const size_t total = (size_t)M * nb * n1 * n1;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
-         e += (size_t)gridDim.x * blockDim.x) {
-        int c = (int)(e % n1);
-        int r = (int)((e / n1) % n1);
-        int slot = (int)((e / (n1 * n1)) % nb);
-        int l = (int)(e / (n1 * n1 * nb));
-        int m = l - h + slot;
-        band[e] = (m >= 0 && m < M) ? d_entry(N, M, l, m, r, c, x1, dx, dy, nrad, diag, tab) : 0.0;
-    }
+    extern __shared__ double V[];
+    const int n1 = N + 1, nb = 2 * h + 1;
+    const int slot = blockIdx.x % nb, l = blockIdx.x / nb, m = l - h + slot;
+    double *out = band + (size_t)blockIdx.x * n1 * n1;
+    if (m >= 0 && m < M) d_block(N, M, l, m, x1, dx, dy, nrad, diag, tab, nullptr, 0.0, out, V);
+    else const_block(n1, false, out);
 }
 
 // The two band instances of the two-sided order, S = D - G / F^2 on the
 // diagonal blocks: instance 0 row l is block row l (columns below Mv only);
 // instance 1 row l >= dB is block row M - 1 - (l - dB), the block order
 // reversed (its columns likewise), and rows and columns below dB are padding
-// (identity diagonal block, nothing else).
+// (identity diagonal block, nothing else).  A CTA per block, blockIdx.x =
+// (instance Mv + l) (2h + 1) + slot.
 __global__ void k_fill_S_two_sided(int N, int M, int h, int Mv, int dB, double x1, double dx, double dy,
                                    double nrad, const double *__restrict__ diag, const double *__restrict__ tab,
                                    const double *__restrict__ G1, const double *__restrict__ invF2,
                                    double *__restrict__ band)
 {
-    const size_t n1 = N + 1, nb = 2 * h + 1, n2 = n1 * n1;
-    const size_t total = 2 * (size_t)Mv * nb * n2;
-    const double f = invF2[0];
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
-         e += (size_t)gridDim.x * blockDim.x) {
-        const int c = (int)(e % n1);
-        const int r = (int)((e / n1) % n1);
-        const int slot = (int)((e / n2) % nb);
-        const int l = (int)((e / (n2 * nb)) % Mv);
-        const int inst = (int)(e / (n2 * nb * Mv));
-        const int m = l - h + slot;
-        double v = 0.0;
-        if (m >= 0 && m < Mv) {
-            if (inst == 1 && (l < dB || m < dB)) {
-                v = (l == m && r == c) ? 1.0 : 0.0;
-            } else {
-                const int pl = inst == 0 ? l : M - 1 - (l - dB);
-                const int pm = inst == 0 ? m : M - 1 - (m - dB);
-                v = d_entry(N, M, pl, pm, r, c, x1, dx, dy, nrad, diag, tab);
-                if (pl == pm) v -= f * G1[(size_t)r * n1 + c];
-            }
-        }
-        band[e] = v;
+    extern __shared__ double V[];
+    const int n1 = N + 1, nb = 2 * h + 1;
+    const int slot = blockIdx.x % nb, l = (blockIdx.x / nb) % Mv, inst = blockIdx.x / (nb * Mv);
+    const int m = l - h + slot;
+    double *out = band + (size_t)blockIdx.x * n1 * n1;
+    if (m < 0 || m >= Mv) {
+        const_block(n1, false, out);
+    } else if (inst == 1 && (l < dB || m < dB)) {
+        const_block(n1, l == m, out);
+    } else {
+        const int pl = inst == 0 ? l : M - 1 - (l - dB);
+        const int pm = inst == 0 ? m : M - 1 - (m - dB);
+        d_block(N, M, pl, pm, x1, dx, dy, nrad, diag, tab, G1, invF2[0], out, V);
     }
 }
 
@@ -842,16 +900,31 @@ int swj_pc_setup(swj_ctx *c)
         }
     }
     c->pc_ready = 0;
+    if (!c->pc_chain) {
+        int lo = 0, hi = 0;
+        cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        SWJ_CUDA_TRY(cudaStreamCreateWithPriority(&c->pc_chain, cudaStreamNonBlocking, hi));
+        SWJ_CUDA_TRY(cudaStreamCreateWithPriority(&c->pc_bulk, cudaStreamNonBlocking, lo));
+        for (cudaEvent_t &e : c->pc_ev) SWJ_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    // Two independent branches, joined before the band is filled: on the side
+    // stream A, B (at F = 1), C, A^-1, A^-1 B, C A^-1, G = C A^-1 B (Appendix
+    // C), the K3 table and I of the flat surface; on the context's stream the
+    // trapezoid sum of w K3 of the flat surface (the pair kernel).
+    cudaStream_t sa = c->pc_chain;
+    cudaEvent_t evFork = c->pc_ev[10], evJoin = c->pc_ev[11];
+    SWJ_CUDA_TRY(cudaEventRecord(evFork, st));
+    SWJ_CUDA_TRY(cudaStreamWaitEvent(sa, evFork, 0));
     std::vector<double> invF2(nb);
     for (int i = 0; i < nb; ++i) invF2[i] = 1.0 / (c->F[i] * c->F[i]);
     SWJ_CUDA_TRY(cudaMemcpyAsync(c->pc_invF2, invF2.data(), nb * sizeof(double), cudaMemcpyHostToDevice, st));
     // --- repeated blocks A, B (at F = 1), C and their products (Appendix C)
     SWJ_COUNT_LAUNCH();
-    k_build_ABC<<<nblk((long)n2, 256), 256, 0, st>>>(N, m.x1, m.dx, m.n_rad, 1.0, c->pc_A,
+    k_build_ABC<<<nblk((long)n2, 256), 256, 0, sa>>>(N, m.x1, m.dx, m.n_rad, 1.0, c->pc_A,
                                                      c->pc_B1, c->pc_C);
     double *cpv = c->pc_t1;   // 3 n1 scratch (pc_t1 holds M n1, M >= 3)
     SWJ_COUNT_LAUNCH();
-    k_tri_coef<<<1, 1, 0, st>>>(n1, c->pc_A, cpv);
+    k_tri_coef<<<1, 256, 3 * (size_t)n1 * sizeof(double), sa>>>(n1, c->pc_A, cpv);
     {
         const int tc = tri_cols_per_block(n1);
         const size_t tsm = (size_t)tc * n1 * sizeof(double);
@@ -859,12 +932,16 @@ int swj_pc_setup(swj_ctx *c)
                                                           160 * 1024) == cudaSuccess;
         if (!tri_attr) cudaGetLastError();
         SWJ_COUNT_LAUNCH();
-        k_tri_cols<<<nblk(n1, tc), tc, tsm, st>>>(n1, n1, cpv, nullptr, c->pc_Ainv);
-        SWJ_COUNT_LAUNCH();
-        k_tri_cols<<<nblk(n1, tc), tc, tsm, st>>>(n1, n1, cpv, c->pc_B1, c->pc_AinvB1);
+        k_tri_cols<<<dim3(nblk(n1, tc), 2), tc, tsm, sa>>>(n1, n1, cpv, nullptr, c->pc_Ainv, c->pc_B1,
+                                                          c->pc_AinvB1);
     }
-    swj_dgemm(st, n1, n1, n1, 1.0, c->pc_C, n1, c->pc_Ainv, n1, 0.0, c->pc_CAinv, n1);
-    swj_dgemm(st, n1, n1, n1, 1.0, c->pc_C, n1, c->pc_AinvB1, n1, 0.0, c->pc_G1, n1);
+    swj_dgemm(sa, n1, n1, n1, 1.0, c->pc_C, n1, c->pc_Ainv, n1, 0.0, c->pc_CAinv, n1);
+    swj_dgemm(sa, n1, n1, n1, 1.0, c->pc_C, n1, c->pc_AinvB1, n1, 0.0, c->pc_G1, n1);
+    SWJ_COUNT_LAUNCH();
+    k_k3_table<<<nblk((long)(2 * N - 2) * (2 * M - 1), 256), 256, 0, sa>>>(N, M, m.dx, m.dy, c->pc_k3);
+    SWJ_COUNT_LAUNCH();
+    k_flat_I<<<nblk(c->T, 128), 128, 0, sa>>>(N, M, m.dx, m.dy, c->pc_sumK3);
+    SWJ_CUDA_TRY(cudaEventRecord(evJoin, sa));
     // --- PreD diagonal correction: trapezoid sum of w K3 and I of the flat surface
     //     (instance 0's record buffers serve as scratch; every residual rewrites them)
     int prec = (c->opts.solve_mode == SWJ_SOLVE_FP64) ? SWJ_FP64 : SWJ_FP32;
@@ -886,24 +963,28 @@ int swj_pc_setup(swj_ctx *c)
         k_flat_records<float><<<nblk(ne, 256), 256, 0, st>>>(N, M, m.dx, m.dy, c->src32, c->tgt32);
         swj_launch_pairs32(c, pl, act0);
     }
+    SWJ_CUDA_TRY(cudaStreamWaitEvent(st, evJoin, 0));
     SWJ_COUNT_LAUNCH();
-    k_diag_corr<<<nblk(c->T, 256), 256, 0, st>>>(N, M, pl.P, m.dx, m.dy, c->partial, c->pc_sumK3);
+    k_diag_corr<<<nblk(c->T, 256), 256, 0, st>>>(N, M, pl.P, c->partial, c->pc_sumK3);
     // --- band of S for every instance: D (shared) minus G / F^2 on the diagonal blocks
     const size_t bst = band_stride(c);
     double *sep0 = sh.nd ? c->pc_nd_buf + 2 * (size_t)nv * Mv * n1 : nullptr;   // D's separator blocks
-    SWJ_COUNT_LAUNCH();
-    k_k3_table<<<nblk((long)(2 * N - 2) * (2 * M - 1), 256), 256, 0, st>>>(N, M, m.dx, m.dy, c->pc_k3);
+    const size_t vsm = (size_t)2 * (2 * N - 2) * sizeof(double);   // the fill kernels' value table
+    if (vsm > 48 * 1024) {                                           // N > 1537
+        SWJ_CUDA_TRY(cudaFuncSetAttribute(k_fill_D, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsm));
+        SWJ_CUDA_TRY(cudaFuncSetAttribute(k_fill_S_two_sided, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsm));
+    }
     if (sh.nd) {
         SWJ_COUNT_LAUNCH();
-        k_fill_S_two_sided<<<4 * c->num_sms, 256, 0, st>>>(N, M, h, Mv, sh.dB, m.x1, m.dx, m.dy, m.n_rad,
+        k_fill_S_two_sided<<<2 * Mv * nbs, 256, vsm, st>>>(N, M, h, Mv, sh.dB, m.x1, m.dx, m.dy, m.n_rad,
                                                             c->pc_sumK3, c->pc_k3, c->pc_G1, c->pc_invF2,
                                                             c->pc_band);
         SWJ_COUNT_LAUNCH();
         k_sep_blocks<<<2 * c->num_sms, 256, 0, st>>>(n1, h, Mv, c->pc_band, bst, sep0, 0);
     } else {
         SWJ_COUNT_LAUNCH();
-        k_fill_D<<<4 * c->num_sms, 256, 0, st>>>(N, M, h, m.x1, m.dx, m.dy, m.n_rad, c->pc_sumK3, c->pc_k3,
-                                                 c->pc_band);
+        k_fill_D<<<M * nbs, 256, vsm, st>>>(N, M, h, m.x1, m.dx, m.dy, m.n_rad, c->pc_sumK3, c->pc_k3,
+                                            c->pc_band);
         if (nb > 1) {
             SWJ_COUNT_LAUNCH();
             k_replicate<<<dim3(2 * c->num_sms, nb - 1), 256, 0, st>>>(bst, c->pc_band, c->pc_band, bst);
@@ -1109,13 +1190,6 @@ int swj_pc_setup(swj_ctx *c)
         // so the factors do not depend on timing.  Events: evW[i % 4] after
         // W_{i,i+1}, evB1[i % 4] after B1 of step i (rings of 4: a wait is
         // always enqueued before its event is recorded again).
-        if (!c->pc_chain) {
-            int lo = 0, hi = 0;
-            cudaDeviceGetStreamPriorityRange(&lo, &hi);
-            SWJ_CUDA_TRY(cudaStreamCreateWithPriority(&c->pc_chain, cudaStreamNonBlocking, hi));
-            SWJ_CUDA_TRY(cudaStreamCreateWithPriority(&c->pc_bulk, cudaStreamNonBlocking, lo));
-            for (cudaEvent_t &e : c->pc_ev) SWJ_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-        }
         cudaStream_t sc = c->pc_chain, sb = c->pc_bulk;
         cudaEvent_t *evW = c->pc_ev, *evB1 = c->pc_ev + 4, evStart = c->pc_ev[8], evEnd = c->pc_ev[9];
         // Output tile of a batched product launch: the largest of 64, 32, 16 that

@@ -148,7 +148,7 @@ struct swj_ctx {
     // look-ahead factorisation: the critical chain (Gauss-Jordan, W, next block row)
     // on a high-priority stream, the other Schur updates on a low-priority one
     cudaStream_t pc_chain, pc_bulk;
-    cudaEvent_t pc_ev[10];
+    cudaEvent_t pc_ev[12];
     // multi-cluster apply (one instance): z, then the term slots cf, cb, and the error word
     double *pc_mc_buf;
     int *pc_mc_err;
