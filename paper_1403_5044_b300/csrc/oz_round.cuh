@@ -105,7 +105,7 @@ OZ_HD uint64_t oz_round_bits(int64_t hi, uint64_t lo, int e2, bool *fallback)
 }
 
 // S = sum_d q_d 2^(beta (s-1-d)) as 128-bit two's complement hi 2^64 + lo, for
-// |q_d| < 2^24 (the digit-level products T_d) and s beta < 128.
+// |q_d| < 2^25 (the digit-level products T_d, below 2^24) and s beta < 100.
 OZ_HD void oz_sum_any(const int32_t *q, int s, int beta, int64_t &hi, uint64_t &lo)
 {
     hi = 0;
@@ -132,8 +132,8 @@ OZ_HD void oz_sum_any(const int32_t *q, int s, int beta, int64_t &hi, uint64_t &
 
 // The same sum for fixed (S_, B_) as two int64 Horner sums: the high digits H =
 // sum_{d < SH} q_d 2^(B_ (SH-1-d)) and the low digits L (the other S_ - SH),
-// S = H 2^(B_ (S_ - SH)) + L.  Each half stays below 2^(25 + B_ (SH - 1)) <
-// 2^62, and the shifts are constants.
+// S = H 2^(B_ (S_ - SH)) + L.  For |q_d| < 2^25 each half stays below
+// 2^(26 + B_ (SH - 1)) < 2^63, and the shifts are constants.
 template <int S_, int B_>
 OZ_HD void oz_horner(const int32_t *q, int64_t &hi, uint64_t &lo)
 {

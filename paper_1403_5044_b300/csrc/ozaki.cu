@@ -28,6 +28,8 @@
 #include "oz_round.cuh"
 #include <cuda_bf16.h>
 #include <math.h>
+#include <algorithm>
+#include <cmath>
 
 namespace {
 
@@ -181,7 +183,8 @@ __global__ void k_oz_split_cols(int n, int np, int s, int beta, const double *co
 // (B300's FP64 pipe, two FMAs per clock per SM, would bound it otherwise) and
 // rounded to FP64 (the low word to 53 bits, then the sum; oz_round.cuh).
 // Thread per element of the n x n block.
-// block (32, 8) over 32 columns x 8 rows of the n x n block, grid.z = product
+// block (32, 8) over 32 columns x 8 rows of the n x n block, grid.z = product;
+// P holds T_d of levels d = 0..s-1 (the scheme's outputs) of every product.
 template <int S_, int B_>
 __global__ void k_oz_combine(int n, int np, int s, int beta, const OzProd *__restrict__ prods,
                              const float *__restrict__ P, const int *__restrict__ ea, const int *__restrict__ eb,
@@ -219,17 +222,31 @@ inline int nblk(long n, int b) { return (int)((n + b - 1) / b); }
 
 }  // namespace
 
-void swj_ozaki_params(int n, int *np, int *beta, int *s)
+// The digit scheme for n x n products: the largest beta (digits up to
+// 2^beta - 1 <= 255 are exact in bf16) with s n 2^(2 beta) <= 2^24 for s =
+// ceil(56 / beta) digits, so every row (column) keeps s beta >= 56 bits of its
+// fixed-point magnitude and a whole digit level sums exactly in one FP32
+// accumulator: output o is level d = o (digits p = 0..d).  (Measured at n =
+// 182: beta = 7 with levels split over two accumulators, 36 instead of 55
+// digit products, took as long per set-up: the GEMM's CTAs are bound by
+// latency, not by their MMAs, and the extra outputs cost the combine.)
+void swj_ozaki_scheme(int n, OzScheme *z)
 {
-    // largest beta with s n 2^(2 beta) <= 2^24 for s = ceil(56 / beta) digits
     int b = 8;
     for (; b > 1; --b) {
         const int sl = (56 + b - 1) / b;
         if (log2((double)sl * n) + 2.0 * b <= 24.0) break;
     }
-    *beta = b;
-    *s = (56 + b - 1) / b;
-    *np = (n + 7) / 8 * 8;
+    z->np = (n + 7) / 8 * 8;
+    z->beta = b;
+    z->s = (56 + b - 1) / b;
+    z->nout = z->s < kOzMaxOut ? z->s : kOzMaxOut;
+    for (int d = 0; d < z->nout; ++d) {
+        z->d[d] = (unsigned char)d;
+        z->p0[d] = 0;
+        z->p1[d] = (unsigned char)d;
+        z->order[d] = (unsigned char)(z->nout - 1 - d);   // the longest level first
+    }
 }
 
 int swj_ozaki_split(cudaStream_t st, bool by_rows, int n, int np, int s, int beta, int count,
@@ -244,22 +261,24 @@ int swj_ozaki_split(cudaStream_t st, bool by_rows, int n, int np, int s, int bet
     return SWJ_OK;
 }
 
-int swj_ozaki_products(cudaStream_t st, int n, int np, int s, int beta, int count, const OzProd *prods,
+int swj_ozaki_products(cudaStream_t st, int n, const OzScheme &z, int count, const OzProd *prods,
                        const void *sa, size_t nsa, const int *ea, const void *sb, size_t nsb, const int *eb,
                        double alpha, float *P, int *err)
 {
     if (count <= 0) return SWJ_OK;
-    if (s < 1 || s > 16) return SWJ_EINVAL;
-    int rc = swj_oz_gemm(st, np, s, count, prods, sa, nsa, sb, nsb, P, err);
+    const int np = z.np, s = z.s, beta = z.beta;
+    if (s < 1 || s > 16 || z.nout != s) return SWJ_EINVAL;
+    int rc = swj_oz_gemm(st, z, count, prods, sa, nsa, sb, nsb, P, err);
     if (rc) return rc;
     SWJ_COUNT_LAUNCH();
     const dim3 grid(nblk(n, 32), nblk(n, 8), count), block(32, 8);
-    if (s == 10 && beta == 6) k_oz_combine<10, 6><<<grid, block, 0, st>>>(n, np, s, beta, prods, P, ea, eb, alpha);
-    else if (s == 8 && beta == 7) k_oz_combine<8, 7><<<grid, block, 0, st>>>(n, np, s, beta, prods, P, ea, eb, alpha);
-    else if (s == 12 && beta == 5) k_oz_combine<12, 5><<<grid, block, 0, st>>>(n, np, s, beta, prods, P, ea, eb, alpha);
-    else if (s == 7 && beta == 8) k_oz_combine<7, 8><<<grid, block, 0, st>>>(n, np, s, beta, prods, P, ea, eb, alpha);
-    else k_oz_combine<0, 0><<<grid, block, 0, st>>>(n, np, s, beta, prods, P, ea, eb, alpha);
+#define SWJ_OZ_COMBINE(S_, B_) k_oz_combine<S_, B_><<<grid, block, 0, st>>>(n, np, s, beta, prods, P, ea, eb, alpha)
+    if (s == 10 && beta == 6) SWJ_OZ_COMBINE(10, 6);
+    else if (s == 8 && beta == 7) SWJ_OZ_COMBINE(8, 7);
+    else if (s == 12 && beta == 5) SWJ_OZ_COMBINE(12, 5);
+    else if (s == 7 && beta == 8) SWJ_OZ_COMBINE(7, 8);
+    else SWJ_OZ_COMBINE(0, 0);
+#undef SWJ_OZ_COMBINE
     SWJ_CUDA_TRY(cudaGetLastError());
     return SWJ_OK;
 }
-

@@ -648,6 +648,7 @@ size_t pc_gemm_count(const PcShape &sh)
 // (S_ik, k = i+2..kmax at [0, h-1); W_ik, k = i+1..kmax at [h, 2h); S_ij,
 // j < i, at [2h, 3h)), and the products of the groups Wb, B1, B2, L.
 struct OzLayout {
+    OzScheme z;
     int np, beta, s;
     size_t nsa, nsb;          // slice slots (A, B)
     size_t maxP;              // block products per batched call
@@ -664,11 +665,14 @@ OzLayout oz_layout(int n1, const PcShape &sh)
 {
     OzLayout L = {};
     const int h = sh.h, M = sh.Mv, nb = sh.nv;
-    swj_ozaki_params(n1, &L.np, &L.beta, &L.s);
+    swj_ozaki_scheme(n1, &L.z);
+    L.np = L.z.np;
+    L.beta = L.z.beta;
+    L.s = L.z.s;
     const size_t n2 = (size_t)L.np * L.np;
     L.nsa = (size_t)nb * (h + 1);
     L.nsb = (size_t)nb * 3 * h;
-    const size_t per = (size_t)L.s * n2 * sizeof(float);
+    const size_t per = (size_t)L.z.nout * n2 * sizeof(float);   // the outputs of one block product
     size_t cap = kOzPBytes / per;
     if (cap < 1) cap = 1;
     const size_t most = (size_t)nb * h * h;
@@ -887,7 +891,7 @@ int swj_pc_setup(swj_ctx *c)
                             (void **)&c->oz_err, &c->oz_desc};
             const size_t p2 = (size_t)L.np * L.np;
             const size_t ozs[] = {L.nsa * L.s * p2 * 2, L.nsb * L.s * p2 * 2, L.nsa * L.np * sizeof(int),
-                                  L.nsb * L.np * sizeof(int), L.maxP * L.s * p2 * sizeof(float), sizeof(int),
+                                  L.nsb * L.np * sizeof(int), L.maxP * L.z.nout * p2 * sizeof(float), sizeof(int),
                                   L.bytes_desc};
             for (int i = 0; i < 7; ++i) {
                 if (cudaMalloc(ozb[i], ozs[i]) != cudaSuccess) {
@@ -1247,7 +1251,7 @@ int swj_pc_setup(swj_ctx *c)
                 auto prods = [&](size_t off, int n_, double alpha) {
                     for (int c0 = 0; c0 < n_; c0 += (int)OL.maxP) {
                         const int cc = std::min((int)OL.maxP, n_ - c0);
-                        const int r_ = swj_ozaki_products(sb, n1, OL.np, OL.s, OL.beta, cc, zQ + off + c0,
+                        const int r_ = swj_ozaki_products(sb, n1, OL.z, cc, zQ + off + c0,
                                                           c->oz_sa, OL.nsa, c->oz_ea, c->oz_sb, OL.nsb, c->oz_eb,
                                                           alpha, c->oz_P, c->oz_err);
                         if (r_) return r_;

@@ -255,23 +255,31 @@ void swj_bcombine(cudaStream_t st, int nb, int n, int rows, const double *Z, siz
 void swj_dgemm_batched(cudaStream_t st, int m, int n, int k, double alpha,
                        const double *const *A, int lda, const double *const *B, int ldb,
                        double beta, double *const *C, int ldc, int batch, int tile = 64);   // tile 16, 32 or 64
-// ozaki.cu: FP64-accurate block products from bf16 slices (see there)
-// n: block size; np: n padded to a multiple of 8; beta bits per digit, s digits
-void swj_ozaki_params(int n, int *np, int *beta, int *s);
+// ozaki.cu: FP64-accurate block products from bf16 slices (see there).
+// The digit scheme of n x n products: np = n padded to a multiple of 8, s
+// digits of beta bits; the GEMM's nout outputs of one block product, output
+// o summing a_p b_(d-p) over p in [p0[o], p1[o]] (T_d of level d = o: p0 = 0,
+// p1 = d); order[] lists the outputs by decreasing length (the GEMM's tile
+// order).
+constexpr int kOzMaxOut = 16;
+struct OzScheme {
+    int np, beta, s, nout;
+    unsigned char d[kOzMaxOut], p0[kOzMaxOut], p1[kOzMaxOut], order[kOzMaxOut];
+};
+void swj_ozaki_scheme(int n, OzScheme *z);
 // Slot layout of both factors, K-major: [np rows (A) or columns (B)][s][np]
 // bf16, plus [np] row or column exponents
 int swj_ozaki_split(cudaStream_t st, bool by_rows, int n, int np, int s, int beta, int count,
                     const double *const *mats, const int *slots, void *slices, int *ex);
-// the count block products prods (device list): T_d of every product on the
-// tensor cores into P (count * s * np^2 floats), then the exact combine into
-// each C; err (device word) is set if a bounded wait of the GEMM ran out
-int swj_ozaki_products(cudaStream_t st, int n, int np, int s, int beta, int count, const OzProd *prods,
+// the count block products prods (device list): the T_d of every product on
+// the tensor cores into P (count * s * np^2 floats), then the exact combine
+// into each C; err (device word) is set if a bounded wait of the GEMM ran out
+int swj_ozaki_products(cudaStream_t st, int n, const OzScheme &z, int count, const OzProd *prods,
                        const void *sa, size_t nsa, const int *ea, const void *sb, size_t nsb, const int *eb,
                        double alpha, float *P, int *err);
-// umma.cu: T_d = sum_{p <= d} a_p b_(d-p) of every product and digit level d
-// (tcgen05 bf16 MMAs, FP32 accumulators; exact for the sliced operands);
-// nsa, nsb: slots in sa, sb
-int swj_oz_gemm(cudaStream_t st, int np, int s, int count, const OzProd *prods, const void *sa, size_t nsa,
+// umma.cu: the outputs of every product (tcgen05 bf16 MMAs, FP32
+// accumulators; exact for the sliced operands); nsa, nsb: slots in sa, sb
+int swj_oz_gemm(cudaStream_t st, const OzScheme &z, int count, const OzProd *prods, const void *sa, size_t nsa,
                 const void *sb, size_t nsb, float *P, int *err);
 void swj_dgemm(cudaStream_t st, int m, int n, int k, double alpha, const double *A, int lda,
                const double *B, int ldb, double beta, double *C, int ldc);

@@ -4,25 +4,30 @@
 // tensor memory.
 //
 // For block product t (A = slices of slot a, B = slices of slot b, s digits of
-// beta bits each) and digit level d the kernel forms
-//     T_d = sum_{p=0..d} a_p b_(d-p)          (np x np, FP32)
+// beta bits each) and output o of the digit scheme (level d, digits p0..p1;
+// OzScheme) the kernel forms
+//     T_o = sum_{p=p0..p1} a_p b_(d-p)        (np x np, FP32)
+// (the outputs of level d together make T_d = sum_{p=0..d} a_p b_(d-p)).
 // Both operands are stored K-major with the same shape [slot][row][digit][np]:
 // row r of A holds a_0[r, :] .. a_(s-1)[r, :]; row c of B holds column c of
-// b_0 .. b_(s-1).  T_d[r, c] is then the dot product of A's row r over digits
-// 0..d with B's row c over digits d..0, so the zero products a_p b_q with
-// p + q > d are never formed.  Every partial sum is an integer below 2^24
-// (beta is chosen for that), so FP32 accumulation is exact in any order and
-// the result equals any other exact evaluation bit for bit.
+// b_0 .. b_(s-1).  T_o[r, c] is then the dot product of A's row r over digits
+// p0..p1 with B's row c over digits d-p0..d-p1, so the zero products a_p b_q
+// with p + q > d are never formed.  Every partial sum is an integer below
+// 2^24 (beta and the outputs' length are chosen for that), so FP32
+// accumulation is exact in any order and the result equals any other exact
+// evaluation bit for bit.
 //
-// One CTA per output tile (t, d, 128-row tile, tn-column tile): M = 128 x
+// One CTA per output tile (t, o, 128-row tile, tn-column tile): M = 128 x
 // N = tn x K = 16 MMAs, tn = np split into equal parts of at most 192, rounded
 // up to 16 (TMA fills rows and columns past np with zeros); K runs over digit
 // p and 64-element chunks of it.  Warp 0 lane 0 issues the
-// TMA loads into a four-stage ring, warp 1 lane 0 issues the MMAs (one
+// TMA loads into a two-stage ring (81 KB of shared memory, 256 tensor-memory
+// columns: two CTAs per SM, so one CTA's prologue and epilogue overlap the
+// other's MMAs), warp 1 lane 0 issues the MMAs (one
 // tcgen05.commit frees each stage), warp 2 owns the tensor-memory allocation,
 // and all four warps read the accumulator back (tcgen05.ld, one warp per 32
-// rows) and store the np x np tile of T_d.  Tiles run heaviest digit level
-// first.  Every mbarrier wait is bounded: a wait that runs out sets *err and
+// rows) and store the np x np tile of T_o.  Tiles run longest output first.
+// Every mbarrier wait is bounded: a wait that runs out sets *err and
 // the CTA skips the rest of its work, still waiting (bounded) for its own TMA
 // loads and MMAs in flight before it frees its tensor memory and exits.
 #include "swj_internal.h"
@@ -33,7 +38,7 @@
 
 namespace {
 
-constexpr int kTM = 128, kTN = 192, kTK = 64, kStages = 4, kThreads = 128;
+constexpr int kTM = 128, kTN = 192, kTK = 64, kStages = 2, kThreads = 128;
 constexpr int kABytes = kTM * kTK * 2;            // one stage of A: 128 rows x 128 B
 constexpr int kBBytes = kTN * kTK * 2;            // room for B: up to 192 rows x 128 B
 constexpr int kStageBytes = kABytes + kBBytes;
@@ -137,10 +142,10 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, 2)
 k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-          const OzProd *__restrict__ prods, int count, int s, int np, int tn, int mtiles, int ntiles, int kch,
-          float *__restrict__ P, int *err)
+          const OzProd *__restrict__ prods, int count, const __grid_constant__ OzScheme z, int tn, int mtiles,
+          int ntiles, int kch, float *__restrict__ P, int *err)
 {
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full[kStages], empty[kStages], accb;
@@ -148,12 +153,13 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     __shared__ int bad;
     unsigned char *ring = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // tile order: digit level d = s-1 first (the most chunks), then t, row tile, column tile
-    const int per = count * mtiles * ntiles;
-    const int d = s - 1 - (int)blockIdx.x / per;
+    // tile order: the longest outputs first (z.order), then t, row tile, column tile
+    const int per = count * mtiles * ntiles, np = z.np;
+    const int oi = z.order[(int)blockIdx.x / per];
+    const int d = z.d[oi], p0 = z.p0[oi];
     const int rem = (int)blockIdx.x % per;
     const int t = rem / (mtiles * ntiles), mt = (rem / ntiles) % mtiles, nt = rem % ntiles;
-    const int nk = kch * (d + 1);   // K chunks: digits p = 0..d, kch 64-element chunks each
+    const int nk = kch * (z.p1[oi] - p0 + 1);   // K chunks: digits p = p0..p1, kch 64-element chunks each
     const int stage_tx = kABytes + tn * kTK * 2;
     if (threadIdx.x == 0) {
         for (int i = 0; i < kStages; ++i) {
@@ -190,7 +196,7 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
             }
             if (*(volatile int *)&bad) break;
             unsigned char *sa = ring + (size_t)st * kStageBytes, *sb = sa + kABytes;
-            const int p = kc / kch, jc = kc - kch * p;
+            const int pp = kc / kch, jc = kc - kch * pp, p = p0 + pp;
             mbar_expect_tx(&full[st], stage_tx);
             tma_load_4d(sa, &tmA, &full[st], kTK * jc, p, kTM * mt, o.a);
             tma_load_4d(sb, &tmB, &full[st], kTK * jc, d - p, tn * nt, o.b);
@@ -222,7 +228,7 @@ k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     tc_fence_after();
     if (ok && !*(volatile int *)&bad) {
         const int r = kTM * mt + 32 * warp + lane, cb = tn * nt, ce = min(np, cb + tn);
-        float *row = P + ((size_t)(t * s + d) * np + r) * np;
+        float *row = P + ((size_t)(t * z.nout + oi) * np + r) * np;
         const uint32_t tl = tmem + ((uint32_t)(32 * warp) << 16);
         for (int c0 = cb; c0 < ce; c0 += 16) {
             float v[16];
@@ -290,10 +296,12 @@ int slice_map(CUtensorMap *out, const void *base, int np, int s, size_t nslots, 
 
 }  // namespace
 
-int swj_oz_gemm(cudaStream_t st, int np, int s, int count, const OzProd *prods, const void *sa, size_t nsa,
+int swj_oz_gemm(cudaStream_t st, const OzScheme &z, int count, const OzProd *prods, const void *sa, size_t nsa,
                 const void *sb, size_t nsb, float *P, int *err)
 {
     if (count <= 0) return SWJ_OK;
+    const int np = z.np, s = z.s;
+    if (z.nout < 1 || z.nout > kOzMaxOut) return SWJ_EINVAL;
     // np a multiple of 8 (16-byte digit rows for TMA), 16-byte aligned slices
     if (np < 8 || np % 8 || s < 1 || ((uintptr_t)sa | (uintptr_t)sb) % 16) return SWJ_EINVAL;
     const int ntiles = (np + kTN - 1) / kTN;
@@ -309,8 +317,8 @@ int swj_oz_gemm(cudaStream_t st, int np, int s, int count, const OzProd *prods, 
         attr = true;
     }
     SWJ_COUNT_LAUNCH();
-    k_oz_gemm<<<count * s * mtiles * ntiles, kThreads, kSmemBytes, st>>>(mA, mB, prods, count, s, np, tn, mtiles,
-                                                                         ntiles, kch, P, err);
+    k_oz_gemm<<<count * z.nout * mtiles * ntiles, kThreads, kSmemBytes, st>>>(mA, mB, prods, count, z, tn, mtiles,
+                                                                              ntiles, kch, P, err);
     SWJ_CUDA_TRY(cudaGetLastError());
     return SWJ_OK;
 }

@@ -125,12 +125,12 @@ def test_digit_sums_are_the_exact_integer(prog):
     rows = []
     for s, beta in ((10, 6), (8, 7), (12, 5), (7, 8), (14, 4)):
         for k in range(400):
-            lim = 2 ** 24 - 1 if k % 4 else 2 ** int(rng.integers(1, 24))
+            lim = 2 ** 25 - 1 if k % 4 else 2 ** int(rng.integers(1, 25))
             q = [int(v) for v in rng.integers(-lim, lim + 1, size=s)]
             if k == 0:
-                q = [2 ** 24 - 1] * s
+                q = [2 ** 25 - 1] * s
             elif k == 1:
-                q = [-(2 ** 24 - 1)] * s
+                q = [-(2 ** 25 - 1)] * s
             rows.append((s, beta, q))
     inp = "".join("%d %d %s\n" % (s, b, " ".join(map(str, q))) for s, b, q in rows)
     out = subprocess.run([prog, "sums"], input=inp, capture_output=True, text=True, check=True).stdout.split("\n")
