@@ -128,6 +128,14 @@ typedef struct swj_opts {
                            /* multi-cluster substitution's polls in the apply); 0:    */
                            /* the built-in limits, 2^26 and 2^21 (about a second     */
                            /* each) (0)                                               */
+    int    sm_partition;   /* 1: the band LU of a two-sided one-instance context runs */
+                           /* its Gauss-Jordan chain on a partition of 32 SMs and the */
+                           /* bulk block products on the other SMs (two CUDA green    */
+                           /* contexts of the device, created at the first set-up),   */
+                           /* so that neither slows the other; where the device or    */
+                           /* driver offers no such partition the set-up runs         */
+                           /* unpartitioned.  The factors do not change.  0: every    */
+                           /* kernel may run on every SM (1)                          */
 } swj_opts;
 
 #define SWJ_LU_FP64   0
@@ -311,6 +319,11 @@ int swj_precond_apply(swj_ctx *ctx, const double *b_dev, double *r_dev);
  * h - 1 helper clusters, 1 for one cluster per instance, 0 before the
  * preconditioner is built.  Both give identical results. */
 int swj_precond_sweep_clusters(const swj_ctx *ctx);
+
+/* SMs of the partition the set-up's Gauss-Jordan chain ran on
+ * (opts.sm_partition: 32 on B300; the bulk block products ran on the other
+ * SMs), 0 when the last set-up ran unpartitioned or none has run yet. */
+int swj_precond_chain_sms(const swj_ctx *ctx);
 
 /* Solve E(u) = 0 by damped inexact Newton (Section 4.1) with right-
  * preconditioned restarted GMRES and FD Jacobian-vector products

@@ -795,26 +795,64 @@ static int gj_blocked_cluster(int n)
 // blocks (then input and output may be the same block)
 bool swj_gj_inplace(int n) { return gj_blocked_cluster(n) > 0; }
 
-int swj_gj_inverse_cluster(cudaStream_t st, int n, int count, double *work, size_t wstride,
-                           double *out, size_t ostride, int *info, long long spin_limit)
+// The kernel, cluster size and shared memory of the Gauss-Jordan launch for
+// n x n blocks; min_smem raises the shared memory (the kernel does not use the
+// rest), e.g. to keep one CTA per SM.
+static void gj_launch_shape(int n, size_t min_smem, const void **kern, int *cs, size_t *smem, bool *blocked)
 {
     const int csb = gj_blocked_cluster(n);
-    const bool use_smem = csb > 0;
-    int cs;
-    size_t smem;
-    const void *kern;
-    if (use_smem) {
-        cs = csb;
-        smem = gj_smem_bytes(n, cs);
-        kern = gj_blocked_kernel((n + cs - 1) / cs);
+    *blocked = csb > 0;
+    if (*blocked) {
+        *cs = csb;
+        *smem = gj_smem_bytes(n, csb);
+        *kern = gj_blocked_kernel((n + csb - 1) / csb);
     } else {
         std::lock_guard<std::mutex> lock(g_attr_mutex);
-        kern = (const void *)k_gj_cluster;
-        cs = cluster_for(kern, kGJThreads, 64 * 1024);
-        const int w = (n + cs - 1) / cs;
-        smem = (size_t)(2 * n + w) * sizeof(double) + (size_t)(2 * n + 4) * sizeof(int);
-        cluster_for(kern, kGJThreads, smem);
+        *kern = (const void *)k_gj_cluster;
+        *cs = cluster_for(*kern, kGJThreads, 64 * 1024);
+        const int w = (n + *cs - 1) / *cs;
+        *smem = (size_t)(2 * n + w) * sizeof(double) + (size_t)(2 * n + 4) * sizeof(int);
+        cluster_for(*kern, kGJThreads, *smem);
     }
+    if (min_smem > *smem) {
+        std::lock_guard<std::mutex> lock(g_attr_mutex);
+        *smem = min_smem;
+        cluster_for(*kern, kGJThreads, *smem);   // raises the kernel's limit
+    }
+}
+
+int swj_gj_cluster_capacity(int n, size_t min_smem)
+{
+    const void *kern;
+    int cs;
+    size_t smem;
+    bool blocked;
+    gj_launch_shape(n, min_smem, &kern, &cs, &smem, &blocked);
+    cudaLaunchConfig_t q = {};
+    q.gridDim = dim3(cs);
+    q.blockDim = dim3(kGJThreads);
+    q.dynamicSmemBytes = smem;
+    cudaLaunchAttribute qa[1];
+    qa[0].id = cudaLaunchAttributeClusterDimension;
+    qa[0].val.clusterDim.x = cs;
+    qa[0].val.clusterDim.y = 1;
+    qa[0].val.clusterDim.z = 1;
+    q.attrs = qa;
+    q.numAttrs = 1;
+    int ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, kern, &q) != cudaSuccess) ncl = 0;
+    cudaGetLastError();
+    return ncl;
+}
+
+int swj_gj_inverse_cluster(cudaStream_t st, int n, int count, double *work, size_t wstride,
+                           double *out, size_t ostride, int *info, long long spin_limit, size_t min_smem)
+{
+    const void *kern;
+    int cs;
+    size_t smem;
+    bool use_smem;
+    gj_launch_shape(n, min_smem, &kern, &cs, &smem, &use_smem);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cs * count);
     cfg.blockDim = dim3(kGJThreads);

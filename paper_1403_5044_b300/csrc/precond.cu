@@ -44,6 +44,7 @@
 // M x (N+1) matrix of per-row vectors with one (N+1)^2 block, computed as
 // row-by-row dot products (one warp per output) so that all SMs share it.
 #include "swj_internal.h"
+#include <cuda.h>
 #include <algorithm>
 #include "closed_form.cuh"
 #include <vector>
@@ -528,6 +529,131 @@ inline double *wblk(swj_ctx *c, int inst, int i, int k)
     return c->pc_W + ((size_t)inst * c->pc_M * c->pc_h + (size_t)i * c->pc_h + (k - i - 1)) * n2;
 }
 
+// ---- SM partitions of the band LU (opts.sm_partition) -------------------------
+// Two CUDA green contexts of the device: 32 SMs that hold the Gauss-Jordan
+// chain's clusters, the other SMs for the bulk block products.  Unpartitioned,
+// the bulk kernels share the chain's SMs and slow each pivot step of the
+// latency-bound chain.  The driver functions come through the runtime's
+// entry-point query (the library links only the runtime).
+typedef CUresult (*PfnDevGet)(CUdevice *, int);
+typedef CUresult (*PfnGetRes)(CUdevice, CUdevResource *, CUdevResourceType);
+typedef CUresult (*PfnSplit)(CUdevResource *, unsigned int *, const CUdevResource *, CUdevResource *, unsigned int,
+                             unsigned int);
+typedef CUresult (*PfnDesc)(CUdevResourceDesc *, CUdevResource *, unsigned int);
+typedef CUresult (*PfnGcCreate)(CUgreenCtx *, CUdevResourceDesc, CUdevice, unsigned int);
+typedef CUresult (*PfnGcDestroy)(CUgreenCtx);
+typedef CUresult (*PfnGcStream)(CUstream *, CUgreenCtx, unsigned int, int);
+typedef CUresult (*PfnCtxFromGc)(CUcontext *, CUgreenCtx);
+typedef CUresult (*PfnCtxPush)(CUcontext);
+typedef CUresult (*PfnCtxPop)(CUcontext *);
+struct GreenApi {
+    PfnDevGet dev_get = nullptr;
+    PfnGetRes get_res = nullptr;
+    PfnSplit split = nullptr;
+    PfnDesc desc = nullptr;
+    PfnGcCreate create = nullptr;
+    PfnGcDestroy destroy = nullptr;
+    PfnGcStream stream = nullptr;
+    PfnCtxFromGc ctx_of = nullptr;
+    PfnCtxPush push = nullptr;
+    PfnCtxPop pop = nullptr;
+    bool ok = false;
+};
+const GreenApi &green_api()
+{
+    static GreenApi g = [] {
+        GreenApi a;
+        auto get = [](const char *name, void **fn) {
+            cudaDriverEntryPointQueryResult q;
+            return cudaGetDriverEntryPointByVersion(name, fn, 12080, cudaEnableDefault, &q) == cudaSuccess &&
+                   q == cudaDriverEntryPointSuccess && *fn;
+        };
+        a.ok = get("cuDeviceGet", (void **)&a.dev_get) && get("cuDeviceGetDevResource", (void **)&a.get_res) &&
+               get("cuDevSmResourceSplitByCount", (void **)&a.split) &&
+               get("cuDevResourceGenerateDesc", (void **)&a.desc) && get("cuGreenCtxCreate", (void **)&a.create) &&
+               get("cuGreenCtxDestroy", (void **)&a.destroy) && get("cuGreenCtxStreamCreate", (void **)&a.stream) &&
+               get("cuCtxFromGreenCtx", (void **)&a.ctx_of) && get("cuCtxPushCurrent", (void **)&a.push) &&
+               get("cuCtxPopCurrent", (void **)&a.pop);
+        cudaGetLastError();
+        return a;
+    }();
+    return g;
+}
+constexpr unsigned kChainSMs = 32;
+constexpr size_t kGJOneCtaSmem = 116 * 1024;   // above half an SM's shared memory: one CTA per SM
+
+void free_partitions(swj_ctx *c)
+{
+    if (c->pc_gchain) cudaStreamDestroy(c->pc_gchain);
+    if (c->pc_gbulk) cudaStreamDestroy(c->pc_gbulk);
+    c->pc_gchain = c->pc_gbulk = nullptr;
+    const GreenApi &g = green_api();
+    for (void *&h : c->pc_gctx) {
+        if (h && g.ok) g.destroy((CUgreenCtx)h);
+        h = nullptr;
+    }
+    cudaGetLastError();
+    c->pc_green = 0;
+}
+
+// Create the partitions (once per context): the smallest chain partition of
+// 32, 40 or 48 SMs whose SMs hold the chain's nv clusters of n1 x n1 blocks at
+// once at one CTA per SM (a partition's SMs need not form whole GPCs), the
+// rest of the device for the bulk work.  True if that worked.
+bool pc_partitions(swj_ctx *c, int n1, int nv)
+{
+    if (c->pc_green) return c->pc_green > 0;
+    c->pc_green = -1;
+    const GreenApi &g = green_api();
+    if (!g.ok) return false;
+    int ord = 0, lo = 0, hi = 0;
+    CUdevice dev;
+    CUdevResource all;
+    if (cudaGetDevice(&ord) != cudaSuccess || g.dev_get(&dev, ord) != CUDA_SUCCESS ||
+        g.get_res(dev, &all, CU_DEV_RESOURCE_TYPE_SM) != CUDA_SUCCESS) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    for (unsigned int want : {32u, 40u, 48u}) {
+        CUdevResource grp[1], rest;
+        unsigned int ng = 1;
+        CUdevResourceDesc dc, db;
+        CUgreenCtx gc = nullptr, gb = nullptr;
+        CUstream sc = nullptr, sb = nullptr;
+        bool ok = g.split(grp, &ng, &all, &rest, CU_DEV_SM_RESOURCE_SPLIT_MAX_POTENTIAL_CLUSTER_SIZE, want) ==
+                      CUDA_SUCCESS &&
+                  ng == 1 && grp[0].sm.smCount >= want && rest.sm.smCount >= 2 * want &&
+                  g.desc(&dc, grp, 1) == CUDA_SUCCESS && g.desc(&db, &rest, 1) == CUDA_SUCCESS &&
+                  g.create(&gc, dc, dev, CU_GREEN_CTX_DEFAULT_STREAM) == CUDA_SUCCESS &&
+                  g.create(&gb, db, dev, CU_GREEN_CTX_DEFAULT_STREAM) == CUDA_SUCCESS &&
+                  g.stream(&sc, gc, CU_STREAM_NON_BLOCKING, hi) == CUDA_SUCCESS &&
+                  g.stream(&sb, gb, CU_STREAM_NON_BLOCKING, lo) == CUDA_SUCCESS;
+        c->pc_gctx[0] = gc;
+        c->pc_gctx[1] = gb;
+        c->pc_gchain = (cudaStream_t)sc;
+        c->pc_gbulk = (cudaStream_t)sb;
+        if (ok) {
+            CUcontext cc = nullptr, popped = nullptr;
+            int ncl = 0;
+            if (g.ctx_of(&cc, gc) == CUDA_SUCCESS && g.push(cc) == CUDA_SUCCESS) {
+                ncl = swj_gj_cluster_capacity(n1, kGJOneCtaSmem);
+                g.pop(&popped);
+            }
+            ok = ncl >= nv;
+        }
+        cudaGetLastError();
+        if (ok) {
+            c->pc_green = 1;
+            c->pc_gsms = (int)grp[0].sm.smCount;
+            return true;
+        }
+        free_partitions(c);
+    }
+    c->pc_green = -1;
+    return false;
+}
+
 void delete_plan(void *plan);
 
 void free_pc(swj_ctx *c)
@@ -566,6 +692,9 @@ void free_pc(swj_ctx *c)
         cudaStreamDestroy(c->pc_bulk);
         c->pc_chain = c->pc_bulk = nullptr;
     }
+    if (c->pc_gchain) cudaStreamSynchronize(c->pc_gchain);
+    if (c->pc_gbulk) cudaStreamSynchronize(c->pc_gbulk);
+    free_partitions(c);
     c->pc_ready = 0;
     c->bytes -= c->pc_bytes;
     c->pc_bytes = 0;
@@ -904,6 +1033,7 @@ int swj_pc_setup(swj_ctx *c)
         }
     }
     c->pc_ready = 0;
+    c->pc_chain_sms = 0;
     if (!c->pc_chain) {
         int lo = 0, hi = 0;
         cudaDeviceGetStreamPriorityRange(&lo, &hi);
@@ -1194,8 +1324,17 @@ int swj_pc_setup(swj_ctx *c)
         // so the factors do not depend on timing.  Events: evW[i % 4] after
         // W_{i,i+1}, evB1[i % 4] after B1 of step i (rings of 4: a wait is
         // always enqueued before its event is recorded again).
-        cudaStream_t sc = c->pc_chain, sb = c->pc_bulk;
-        cudaEvent_t *evW = c->pc_ev, *evB1 = c->pc_ev + 4, evStart = c->pc_ev[8], evEnd = c->pc_ev[9];
+        // With SM partitions (two-sided order, opts.sm_partition) the Gauss-Jordan
+        // launches run on the chain partition's stream sg at one CTA per SM, the
+        // bulk work on the other partition's stream; the chain's two FP64 block
+        // products stay on sc, which may use every SM (evG: the inverse of step i
+        // is done; evU: the update of S_{i+1,i+1} is done).
+        const bool part = c->opts.sm_partition && sh.nd && pc_partitions(c, n1, nv);
+        c->pc_chain_sms = part ? c->pc_gsms : 0;
+        cudaStream_t sc = c->pc_chain, sb = part ? c->pc_gbulk : c->pc_bulk, sg = part ? c->pc_gchain : sc;
+        const size_t gj_smem = part ? kGJOneCtaSmem : 0;
+        cudaEvent_t *evW = c->pc_ev, *evB1 = c->pc_ev + 4, evStart = c->pc_ev[8], evEnd = c->pc_ev[9],
+                    *evG = c->pc_ev + 12, *evU = c->pc_ev + 16;
         // Output tile of a batched product launch: the largest of 64, 32, 16 that
         // still gives every SM a few CTAs.  One CTA of a 64-wide tile runs for
         // ~0.2 ms on B300's FP64 pipe (two FMAs per clock per SM), so a launch of
@@ -1224,23 +1363,30 @@ int swj_pc_setup(swj_ctx *c)
         SWJ_CUDA_TRY(cudaEventRecord(evStart, st));
         SWJ_CUDA_TRY(cudaStreamWaitEvent(sc, evStart, 0));
         SWJ_CUDA_TRY(cudaStreamWaitEvent(sb, evStart, 0));
+        if (part) SWJ_CUDA_TRY(cudaStreamWaitEvent(sg, evStart, 0));
         for (int i = i0; i < i1; ++i) {
             double *diag0 = blk(c, 0, i, i);
             const int nq = sh.insts(i);
+            if (part && i > i0) SWJ_CUDA_TRY(cudaStreamWaitEvent(sg, evU[(i - 1) % 4], 0));
             if (gj_inplace) {
-                rc = swj_gj_inverse_cluster(sc, n1, nq, diag0, bst, diag0, bst, c->pc_info + (size_t)i * nv,
-                                            swj_waits(c, false).spin_limit);
+                rc = swj_gj_inverse_cluster(sg, n1, nq, diag0, bst, diag0, bst, c->pc_info + (size_t)i * nv,
+                                            swj_waits(c, false).spin_limit, gj_smem);
             } else {
                 SWJ_COUNT_LAUNCH();
-                k_copy_blocks<<<dim3(64, nq), 256, 0, sc>>>(n2, diag0, bst, c->pc_work, n2);
-                rc = swj_gj_inverse_cluster(sc, n1, nq, c->pc_work, n2, diag0, bst, c->pc_info + (size_t)i * nv,
-                                            swj_waits(c, false).spin_limit);
+                k_copy_blocks<<<dim3(64, nq), 256, 0, sg>>>(n2, diag0, bst, c->pc_work, n2);
+                rc = swj_gj_inverse_cluster(sg, n1, nq, c->pc_work, n2, diag0, bst, c->pc_info + (size_t)i * nv,
+                                            swj_waits(c, false).spin_limit, gj_smem);
             }
             if (rc) return rc;
+            if (part) {
+                SWJ_CUDA_TRY(cudaEventRecord(evG[i % 4], sg));
+                SWJ_CUDA_TRY(cudaStreamWaitEvent(sc, evG[i % 4], 0));
+            }
             if (i >= 1) SWJ_CUDA_TRY(cudaStreamWaitEvent(sc, evB1[(i - 1) % 4], 0));
             if ((rc = gemm(sc, i, gWc, 1.0, 0.0))) return rc;
             SWJ_CUDA_TRY(cudaEventRecord(evW[i % 4], sc));
             if ((rc = gemm(sc, i, gUc, -1.0, 1.0))) return rc;
+            if (part) SWJ_CUDA_TRY(cudaEventRecord(evU[i % 4], sc));
             SWJ_CUDA_TRY(cudaStreamWaitEvent(sb, evW[i % 4], 0));
             if (sliced) {
                 const OzStep &o = zo[i];
@@ -1283,6 +1429,10 @@ int swj_pc_setup(swj_ctx *c)
         SWJ_CUDA_TRY(cudaStreamWaitEvent(st, evEnd, 0));
         SWJ_CUDA_TRY(cudaEventRecord(evEnd, sc));
         SWJ_CUDA_TRY(cudaStreamWaitEvent(st, evEnd, 0));
+        if (part) {
+            SWJ_CUDA_TRY(cudaEventRecord(evEnd, sg));
+            SWJ_CUDA_TRY(cudaStreamWaitEvent(st, evEnd, 0));
+        }
         return SWJ_OK;
         };
         // Two-sided order: both halves first (steps 0..split-1 of both band

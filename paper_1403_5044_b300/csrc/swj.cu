@@ -33,6 +33,7 @@ bool valid_opts(const swj_opts *o)
     if (o->lu_products != SWJ_LU_FP64 && o->lu_products != SWJ_LU_SLICED) return false;
     if (o->lu_order != SWJ_LU_TOP_DOWN && o->lu_order != SWJ_LU_TWO_SIDED) return false;
     if (o->wait_limit < 0) return false;
+    if (o->sm_partition != 0 && o->sm_partition != 1) return false;
     return true;
 }
 
@@ -255,6 +256,7 @@ void swj_default_opts(swj_opts *o)
     o->lu_products = SWJ_LU_SLICED;
     o->lu_order = SWJ_LU_TWO_SIDED;
     o->wait_limit = 0;
+    o->sm_partition = 1;
 }
 
 int swj_set_test_hooks(swj_ctx *c, int hooks)
@@ -500,6 +502,12 @@ int swj_precond_sweep_clusters(const swj_ctx *c)
 {
     if (!c || !c->pc_ready) return 0;
     return c->pc_mc ? c->pc_h : 1;
+}
+
+int swj_precond_chain_sms(const swj_ctx *c)
+{
+    if (!c || !c->pc_ready) return 0;
+    return c->pc_chain_sms;
 }
 
 int swj_precond_apply(swj_ctx *c, const double *b, double *r)

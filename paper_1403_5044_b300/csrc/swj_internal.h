@@ -148,7 +148,15 @@ struct swj_ctx {
     // look-ahead factorisation: the critical chain (Gauss-Jordan, W, next block row)
     // on a high-priority stream, the other Schur updates on a low-priority one
     cudaStream_t pc_chain, pc_bulk;
-    cudaEvent_t pc_ev[12];
+    cudaEvent_t pc_ev[20];
+    // SM partitions of the set-up's band LU (opts.sm_partition): green contexts
+    // (CUgreenCtx) for the Gauss-Jordan chain and the bulk products, a stream in
+    // each; pc_green 1 in use, -1 unavailable, 0 not tried
+    void *pc_gctx[2];
+    cudaStream_t pc_gchain, pc_gbulk;
+    int pc_green;
+    int pc_gsms;                 // SMs of the chain partition
+    int pc_chain_sms;            // SMs of the chain partition the last set-up used (0: none)
     // multi-cluster apply (one instance): z, then the term slots cf, cb, and the error word
     double *pc_mc_buf;
     int *pc_mc_err;
@@ -304,8 +312,14 @@ inline SwjWaits swj_waits(const swj_ctx *c, bool hooks)
 }
 inline SwjWaits swj_default_waits() { return SwjWaits{kSwjSpinLimit, kSwjPollLimit, 0}; }
 
+// min_smem: shared memory per CTA at least (the kernel ignores the rest; the
+// set-up's SM partition asks for one CTA per SM)
 int swj_gj_inverse_cluster(cudaStream_t st, int n, int count, double *work, size_t wstride,
-                           double *out, size_t ostride, int *info, long long spin_limit = kSwjSpinLimit);
+                           double *out, size_t ostride, int *info, long long spin_limit = kSwjSpinLimit,
+                           size_t min_smem = 0);
+// clusters of the Gauss-Jordan launch for n x n blocks (with min_smem) that the
+// current context's SMs hold at once
+int swj_gj_cluster_capacity(int n, size_t min_smem);
 // cluster size (16, else 8) for `kern` with `smem` bytes of dynamic shared
 // memory per CTA; raises the kernel's shared-memory limit to `smem`
 int swj_cluster_for(const void *kern, int threads, size_t smem);

@@ -47,7 +47,8 @@ class Opts(ctypes.Structure):
                 ("mixed_tol_inf", ctypes.c_double), ("refine_tol_inf", ctypes.c_double),
                 ("verbose", ctypes.c_int), ("autotune", ctypes.c_int), ("refine_precision", ctypes.c_int),
                 ("jvp", ctypes.c_int), ("forcing", ctypes.c_int),
-                ("lu_products", ctypes.c_int), ("lu_order", ctypes.c_int), ("wait_limit", ctypes.c_int)]
+                ("lu_products", ctypes.c_int), ("lu_order", ctypes.c_int), ("wait_limit", ctypes.c_int),
+                ("sm_partition", ctypes.c_int)]
 
 
 class ServerOpts(ctypes.Structure):
@@ -139,6 +140,7 @@ def lib():
             "swj_resample": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
             "swj_preconditioned_jacobian": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int]),
             "swj_precond_sweep_clusters": (ctypes.c_int, [_vp]),
+            "swj_precond_chain_sms": (ctypes.c_int, [_vp]),
             "swj_solve": (ctypes.c_int, [_vp, _vp, _vp]),
             "swj_unpack": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
             "swj_surface": (ctypes.c_int, [_vp, _vp, _vp]),
@@ -331,6 +333,9 @@ class Context:
 
     def sweep_clusters(self):
         return int(lib().swj_precond_sweep_clusters(self._h))
+
+    def chain_sms(self):
+        return int(lib().swj_precond_chain_sms(self._h))
 
     def set_test_hooks(self, hooks):
         """swj_set_test_hooks: TEST_WITHHOLD_HELPERS makes the multi-cluster

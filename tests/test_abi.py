@@ -31,7 +31,7 @@ def test_default_opts(lib):
     assert o.solve_mode == swj.SOLVE_MIXED and o.gmres_restart == 30 and o.ftol_inf == 1e-10
     assert o.block_bw == -1 and o.autotune == 1 and o.refine_precision == swj.FF
     assert o.jvp == swj.JVP_FD and o.forcing == swj.FORCING_SOURCE and o.lu_products == swj.LU_SLICED
-    assert o.lu_order == swj.LU_TWO_SIDED
+    assert o.lu_order == swj.LU_TWO_SIDED and o.wait_limit == 0 and o.sm_partition == 1
 
 
 @pytest.mark.parametrize("N,M,dx,dy", [(3, 5, 0.5, 0.5), (10, 2, 0.5, 0.5), (10, 5, 0.0, 0.5), (10, 5, 0.5, -1.0)])
@@ -48,7 +48,8 @@ def test_create_rejects_bad_mesh_without_touching_the_gpu(lib, N, M, dx, dy):
                                          ("jvp", 2), ("jvp", -1),
                                          ("forcing", 2), ("forcing", -1),
                                          ("lu_products", 2), ("lu_products", -1),
-                                         ("lu_order", 2), ("lu_order", -1)])
+                                         ("lu_order", 2), ("lu_order", -1),
+                                         ("wait_limit", -1), ("sm_partition", 2), ("sm_partition", -1)])
 def test_create_rejects_bad_options(lib, field, value):
     h = ctypes.c_void_p()
     mesh = swj.Mesh(9, 5, -2.0, 0.5, 0.4, 0.05)

@@ -128,6 +128,29 @@ def test_sliced_lu_products_agree_with_fp64_and_do_not_depend_on_the_batch(spec,
     assert np.array_equal(rb[0], out[swj.LU_SLICED]) and np.array_equal(rb[1], out[swj.LU_SLICED])
 
 
+@pytest.mark.parametrize("spec,b", [(W.SOLVE_181x61[0], 15), (W.SERVE_MESHES[1], 11)])
+def test_sm_partitioned_setup_gives_the_same_factors(spec, b):
+    """With opts.sm_partition the two-sided set-up runs its Gauss-Jordan chain
+    on a 32-SM green context and the bulk products on the other SMs; every
+    block still receives the same updates in the same order, so the apply is
+    bit-identical to the unpartitioned set-up's (and to a second partitioned
+    set-up on the same context)."""
+    rhs = np.random.default_rng(spec.N + b + 3).normal(size=spec.n_unknowns)
+    out, sms = {}, {}
+    for part in (0, 1):
+        with swj.Context.from_spec(spec, 0.75, 0.2, solve_mode="mixed", block_bw=b, sm_partition=part) as ctx:
+            for rep in range(2):
+                ctx.precond_setup()
+                r = ctx.vector()
+                ctx.precond_apply(dev(rhs), r)
+                ctx.sync()
+                out[part, rep] = r.cpu().numpy()
+            sms[part] = ctx.chain_sms()
+    assert sms[0] == 0 and sms[1] in (0, 32, 40, 48), sms   # 0: the device offered no partition
+    assert np.array_equal(out[1, 0], out[0, 0]) and np.array_equal(out[1, 1], out[0, 0])
+    assert np.array_equal(out[0, 1], out[0, 0])
+
+
 @pytest.mark.parametrize("spec,b", [(W.MESH_41x21, 11), (W.SERVE_MESHES[1], 11), (W.SOLVE_181x61[0], 11),
                                     (W.SOLVE_181x61[0], 9), (W.SERVE_MESHES[3], 15)])
 def test_two_sided_factorisation_equals_top_down(spec, b):
