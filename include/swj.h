@@ -133,9 +133,12 @@ typedef struct swj_opts {
                            /* bulk block products on the other SMs (two CUDA green    */
                            /* contexts of the device, created at the first set-up),   */
                            /* so that neither slows the other; where the device or    */
-                           /* driver offers no such partition the set-up runs         */
-                           /* unpartitioned.  The factors do not change.  0: every    */
-                           /* kernel may run on every SM (1)                          */
+                           /* driver offers no such partition, or a tool is injected  */
+                           /* into the process (CUDA_INJECTION64_PATH or Nsight's     */
+                           /* injection variables set: profilers, sanitizers), the    */
+                           /* set-up runs unpartitioned.  The                         */
+                           /* factors do not change.  0: every kernel may run on      */
+                           /* every SM (1)                                            */
 } swj_opts;
 
 #define SWJ_LU_FP64   0

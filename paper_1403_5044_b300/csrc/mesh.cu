@@ -72,15 +72,19 @@ __global__ void k_integrate(int N, int M, int H, double x1, double dx,
 // eliminated through the row above it).  cp, a, inv are the forward-sweep
 // coefficients of this fixed matrix (Thomas algorithm).
 //
-// Warp per 32 columns, a column per lane.  The warp first copies its columns
-// into shared memory (all M rows in flight at once: the sweeps are a chain of
-// M dependent steps, which must not also wait on memory), runs the forward
-// sweep there (m'_j overwrites f_j, which the sweep holds in registers by
-// then) and the backward sweep from there, writing each slope to global
-// memory as it is found (coalesced across the warp).
-constexpr int kSplineCols = 32;
+// 32 columns per block, a column per lane of each of its four warps.  The
+// warps first copy the columns into shared memory (all M rows in flight at
+// once) and form the right-hand sides d_j of every row there, rows dealt over
+// the four warps: B300 issues FP64 at 0.5 lanes per clock per SM
+// sub-partition, so this off-chain work spreads over four sub-partitions.
+// Warp 0 then runs the forward sweep (the chain of M dependent steps, now
+// only its own two FP64 operations per step; m'_j overwrites d_j) and the
+// backward sweep, writing each slope to global memory as it is found
+// (coalesced across the warp).  The operations per value are those of the
+// one-warp form, so the slopes are the same bit for bit.
+constexpr int kSplineCols = 32, kSplineWarps = 4;
 
-__global__ void __launch_bounds__(kSplineCols)
+__global__ void __launch_bounds__(kSplineCols * kSplineWarps)
 k_spline(int N, int M, double hy, const double *__restrict__ cp,
          const double *__restrict__ a, const double *__restrict__ inv,
          const double *__restrict__ zeta, const double *__restrict__ g,
@@ -92,40 +96,44 @@ k_spline(int N, int M, double hy, const double *__restrict__ cp,
     const size_t off = (size_t)inst * N * M;
     zeta += off; g += off; zetay += off; gy += off;
     extern __shared__ double sp[];
-    const int lane = threadIdx.x;
+    const int lane = threadIdx.x & (kSplineCols - 1), w = threadIdx.x / kSplineCols;
     const int t = blockIdx.x * kSplineCols + lane;
-    if (t >= 2 * N) return;
-    const int k = t % N;
+    const bool live = t < 2 * N;
+    const int k = live ? t % N : 0;
     const double *f = (t < N ? zeta : g) + k;
-    double *m = (t < N ? zetay : gy) + k;
-    double *F = sp + lane;                      // row j of this column at F[j * kSplineCols]
-    for (int j = 0; j < M; ++j) __pipeline_memcpy_async(F + j * kSplineCols, f + (size_t)j * N, 8);
+    double *F = sp + lane;                      // f_j of this column at F[j * kSplineCols]
+    double *D = sp + (size_t)M * kSplineCols + lane;   // d_j, then m'_j
+    if (live)
+        for (int j = w; j < M; j += kSplineWarps) __pipeline_memcpy_async(F + j * kSplineCols, f + (size_t)j * N, 8);
     __pipeline_commit();
     __pipeline_wait_prior(0);
+    __syncthreads();
     const double rh = 1.0 / hy;
-    // right-hand side of the last row, before the sweep overwrites its inputs
-    const double d3 = (F[(M - 2) * kSplineCols] - F[(M - 3) * kSplineCols]) * rh;
-    const double d2 = (F[(M - 1) * kSplineCols] - F[(M - 2) * kSplineCols]) * rh;
-    const double dlast = 0.5 * (d3 + 5.0 * d2);
-    double dp = 0.0;
-    double fm = F[0], f0 = F[kSplineCols];      // f_{j-1}, f_j
-    for (int j = 1; j < M; ++j) {
-        double d;
-        if (j < M - 1) {
-            const double fp = F[(j + 1) * kSplineCols];
-            d = 3.0 * (fp - fm) * rh;
-            fm = f0;
-            f0 = fp;
-        } else {
-            d = dlast;
+    if (live) {
+        for (int j = 1 + w; j < M; j += kSplineWarps) {
+            double d;
+            if (j < M - 1) {
+                d = 3.0 * (F[(j + 1) * kSplineCols] - F[(j - 1) * kSplineCols]) * rh;
+            } else {
+                const double d3 = (F[(M - 2) * kSplineCols] - F[(M - 3) * kSplineCols]) * rh;
+                const double d2 = (F[(M - 1) * kSplineCols] - F[(M - 2) * kSplineCols]) * rh;
+                d = 0.5 * (d3 + 5.0 * d2);
+            }
+            D[j * kSplineCols] = d;
         }
-        dp = (d - __ldg(a + j) * dp) * __ldg(inv + j);
-        F[j * kSplineCols] = dp;
+    }
+    __syncthreads();
+    if (w != 0 || !live) return;
+    double *m = (t < N ? zetay : gy) + k;
+    double dp = 0.0;
+    for (int j = 1; j < M; ++j) {
+        dp = (D[j * kSplineCols] - __ldg(a + j) * dp) * __ldg(inv + j);
+        D[j * kSplineCols] = dp;
     }
     double next = dp;
     m[(size_t)(M - 1) * N] = next;
     for (int j = M - 2; j >= 1; --j) {
-        next = F[j * kSplineCols] - __ldg(cp + j) * next;
+        next = D[j * kSplineCols] - __ldg(cp + j) * next;
         m[(size_t)j * N] = next;
     }
     m[0] = 0.0;
@@ -390,19 +398,19 @@ __global__ void k_resample(int Ns, int Ms, int Hs, double x1s, double dxs, doubl
 
 inline int nblk(long n, int b) { return (int)((n + b - 1) / b); }
 
-// Shared memory of k_spline: M rows of kSplineCols columns.  Up to 160 KB
-// (M <= 640) it runs; above, k_spline_global does.
+// Shared memory of k_spline: two arrays of M rows of kSplineCols columns.  Up
+// to 160 KB (M <= 320) it runs; above, k_spline_global does.
 constexpr size_t kSplineSmemMax = 160 * 1024;
 
 void launch_spline(swj_ctx *c, cudaStream_t st, const double *f1, const double *f2, double *m1, double *m2,
                    const int *act)
 {
-    const size_t smem = (size_t)c->M * kSplineCols * sizeof(double);
+    const size_t smem = 2 * (size_t)c->M * kSplineCols * sizeof(double);
     if (smem <= kSplineSmemMax) {
         static const bool attr = cudaFuncSetAttribute(k_spline, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                       (int)kSplineSmemMax) == cudaSuccess;
         (void)attr;
-        k_spline<<<dim3(nblk(2L * c->N, kSplineCols), c->nb), kSplineCols, smem, st>>>(
+        k_spline<<<dim3(nblk(2L * c->N, kSplineCols), c->nb), kSplineCols * kSplineWarps, smem, st>>>(
             c->N, c->M, c->mesh.dy, c->spl_cp, c->spl_a, c->spl_inv, f1, f2, m1, m2, act);
     } else {
         k_spline_global<<<dim3(nblk(2L * c->N, 128), c->nb), 128, 0, st>>>(

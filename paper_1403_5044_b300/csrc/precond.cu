@@ -49,6 +49,7 @@
 #include "closed_form.cuh"
 #include <vector>
 #include <string.h>
+#include <stdlib.h>
 #include <cuda_pipeline.h>
 
 namespace {
@@ -604,6 +605,15 @@ bool pc_partitions(swj_ctx *c, int n1, int nv)
 {
     if (c->pc_green) return c->pc_green > 0;
     c->pc_green = -1;
+    // a tool injected into the process (a profiler, a sanitizer) may not follow
+    // green contexts (Nsight Compute fails to prepare the chain's launches): the
+    // set-up then runs unpartitioned (the factors are the same).  The tools
+    // announce themselves through their injection variables.
+    for (const char *var : {"CUDA_INJECTION64_PATH", "NV_NSIGHT_INJECTION_TRANSPORT_TYPE",
+                            "NV_COMPUTE_PROFILER_PERFWORKS_DIR"}) {
+        const char *v = getenv(var);
+        if (v && *v) return false;
+    }
     const GreenApi &g = green_api();
     if (!g.ok) return false;
     int ord = 0, lo = 0, hi = 0;
