@@ -454,7 +454,7 @@ int swj_jvp_exact_impl(swj_ctx *c, const double *u, const double *v, double *Jv,
     swj_launch_mesh_step(c, u, c->E_tmp, act);
     swj_launch_mesh_tangent(c, v, act);
     SWJ_COUNT_LAUNCH();
-    k_targets_tan<<<dim3(nblk(c->T, 128), nb), 128, 0, st>>>(
+    k_targets_tan<<<dim3(nblk(c->T, kFp64Block), nb), kFp64Block, 0, st>>>(
         c->N, c->M, c->H, m.x1, m.dx, m.dy, c->Fd, c->epsd, m.n_rad, c->opts.forcing, u, v, c->zeta, c->g,
         c->zetay, c->gy,
         c->dnode, c->Ival, Jv, c->de2part, c->ttgt64, c->ttgt32, act);

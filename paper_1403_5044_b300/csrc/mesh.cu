@@ -441,12 +441,12 @@ void swj_launch_mesh_step(swj_ctx *c, const double *u, double *E, const int *act
     cudaStream_t st = c->stream;
     const int nb = c->nb;
     SWJ_COUNT_LAUNCH();
-    k_integrate<<<dim3(nblk(2L * c->M * 32, 256), nb), 256, 0, st>>>(c->N, c->M, c->H, m.x1, m.dx, u,
+    k_integrate<<<dim3(nblk(2L * c->M * 32, kFp64Block), nb), kFp64Block, 0, st>>>(c->N, c->M, c->H, m.x1, m.dx, u,
                                                                      c->zeta, c->g, act);
     SWJ_COUNT_LAUNCH();
     launch_spline(c, st, c->zeta, c->g, c->zetay, c->gy, act);
     SWJ_COUNT_LAUNCH();
-    k_targets<<<dim3(nblk(c->T, 128), nb), 128, 0, st>>>(c->N, c->M, c->H, m.x1, m.dx, m.dy, c->Fd,
+    k_targets<<<dim3(nblk(c->T, kFp64Block), nb), kFp64Block, 0, st>>>(c->N, c->M, c->H, m.x1, m.dx, m.dy, c->Fd,
                                                           c->epsd, m.n_rad, c->opts.forcing, u, c->zeta, c->g,
                                                           c->zetay, c->gy, E, c->e2part, c->Ival,
                                                           c->tgt64, c->tgt32, act);
@@ -458,7 +458,7 @@ void swj_launch_mesh_step(swj_ctx *c, const double *u, double *E, const int *act
 void swj_launch_assemble(swj_ctx *c, double *E, int P, const int *act, const double *e2part)
 {
     SWJ_COUNT_LAUNCH();
-    k_assemble<<<dim3(nblk(c->T, 256), c->nb), 256, 0, c->stream>>>(c->N, c->M, c->H, P, c->partial,
+    k_assemble<<<dim3(nblk(c->T, kFp64Block), c->nb), kFp64Block, 0, c->stream>>>(c->N, c->M, c->H, P, c->partial,
                                                                      e2part ? e2part : c->e2part, E, act);
 }
 
@@ -471,7 +471,7 @@ void swj_launch_mesh_tangent(swj_ctx *c, const double *v, const int *act)
     const size_t NS = (size_t)c->nb * c->S;
     double *dz = c->dnode, *dg = dz + NS, *dzy = dg + NS, *dgy = dzy + NS;
     SWJ_COUNT_LAUNCH();
-    k_integrate<<<dim3(nblk(2L * c->M * 32, 256), c->nb), 256, 0, st>>>(c->N, c->M, c->H, m.x1, m.dx, v, dz,
+    k_integrate<<<dim3(nblk(2L * c->M * 32, kFp64Block), c->nb), kFp64Block, 0, st>>>(c->N, c->M, c->H, m.x1, m.dx, v, dz,
                                                                         dg, act, true);
     SWJ_COUNT_LAUNCH();
     launch_spline(c, st, dz, dg, dzy, dgy, act);
@@ -487,7 +487,7 @@ void swj_launch_unpack(swj_ctx *c, const double *u, double *zo, double *po)
 {
     const swj_mesh &m = c->mesh;
     SWJ_COUNT_LAUNCH();
-    k_integrate<<<dim3(nblk(2L * c->M * 32, 256), c->nb), 256, 0, c->stream>>>(
+    k_integrate<<<dim3(nblk(2L * c->M * 32, kFp64Block), c->nb), kFp64Block, 0, c->stream>>>(
         c->N, c->M, c->H, m.x1, m.dx, u, c->zeta, c->g, nullptr);
     SWJ_COUNT_LAUNCH();
     k_unpack<<<dim3(nblk(c->S, 256), c->nb), 256, 0, c->stream>>>(c->N, c->M, m.x1, m.dx, c->zeta,
@@ -509,7 +509,7 @@ void swj_launch_resample(swj_ctx *src, const double *u_src, swj_ctx *dst, double
     const swj_mesh &ms = src->mesh, &md = dst->mesh;
     cudaStream_t st = dst->stream;
     SWJ_COUNT_LAUNCH();
-    k_integrate<<<dim3(nblk(2L * src->M * 32, 256), src->nb), 256, 0, st>>>(src->N, src->M, src->H, ms.x1, ms.dx,
+    k_integrate<<<dim3(nblk(2L * src->M * 32, kFp64Block), src->nb), kFp64Block, 0, st>>>(src->N, src->M, src->H, ms.x1, ms.dx,
                                                                             u_src, src->zeta, src->g, nullptr);
     SWJ_COUNT_LAUNCH();
     k_resample<<<dim3(nblk(dst->H, 256), dst->nb), 256, 0, st>>>(src->N, src->M, src->H, ms.x1, ms.dx, ms.dy,

@@ -1084,7 +1084,7 @@ int swj_pc_setup(swj_ctx *c)
     SWJ_COUNT_LAUNCH();
     k_k3_table<<<nblk((long)(2 * N - 2) * (2 * M - 1), 256), 256, 0, sa>>>(N, M, m.dx, m.dy, c->pc_k3);
     SWJ_COUNT_LAUNCH();
-    k_flat_I<<<nblk(c->T, 128), 128, 0, sa>>>(N, M, m.dx, m.dy, c->pc_sumK3);
+    k_flat_I<<<nblk(c->T, kFp64Block), kFp64Block, 0, sa>>>(N, M, m.dx, m.dy, c->pc_sumK3);
     SWJ_CUDA_TRY(cudaEventRecord(evJoin, sa));
     // --- PreD diagonal correction: trapezoid sum of w K3 and I of the flat surface
     //     (instance 0's record buffers serve as scratch; every residual rewrites them)
@@ -1109,7 +1109,7 @@ int swj_pc_setup(swj_ctx *c)
     }
     SWJ_CUDA_TRY(cudaStreamWaitEvent(st, evJoin, 0));
     SWJ_COUNT_LAUNCH();
-    k_diag_corr<<<nblk(c->T, 256), 256, 0, st>>>(N, M, pl.P, c->partial, c->pc_sumK3);
+    k_diag_corr<<<nblk(c->T, kFp64Block), kFp64Block, 0, st>>>(N, M, pl.P, c->partial, c->pc_sumK3);
     // --- band of S for every instance: D (shared) minus G / F^2 on the diagonal blocks
     const size_t bst = band_stride(c);
     double *sep0 = sh.nd ? c->pc_nd_buf + 2 * (size_t)nv * Mv * n1 : nullptr;   // D's separator blocks

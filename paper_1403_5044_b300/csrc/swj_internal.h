@@ -263,6 +263,13 @@ void swj_bcombine(cudaStream_t st, int nb, int n, int rows, const double *Z, siz
 void swj_dgemm_batched(cudaStream_t st, int m, int n, int k, double alpha,
                        const double *const *A, int lda, const double *const *B, int ldb,
                        double beta, double *const *C, int ldc, int batch, int tile = 64);   // tile 16, 32 or 64
+// Block size of the thread-per-item kernels that run long chains of FP64
+// instructions (the per-target closed forms, the residual assembly, the row
+// integrations): one-warp blocks spread their few warps over every SM instead
+// of a few SMs' sub-partitions (181x61: 344 target warps on 148 SMs rather than
+// 86).  Each FP64 warp instruction holds its sub-partition for 64 cycles, so a
+// warp's own chain bounds these kernels (targets 57 -> 54.5 us).
+constexpr int kFp64Block = 32;
 // ozaki.cu: FP64-accurate block products from bf16 slices (see there).
 // The digit scheme of n x n products: np = n padded to a multiple of 8, s
 // digits of beta bits; the GEMM's nout outputs of one block product, output
