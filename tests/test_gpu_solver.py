@@ -151,6 +151,28 @@ def test_sm_partitioned_setup_gives_the_same_factors(spec, b):
     assert np.array_equal(out[0, 1], out[0, 0])
 
 
+def test_sm_partitions_stay_off_under_an_injected_tool(monkeypatch):
+    """A profiler injected into the process announces itself through its
+    injection variables; the set-up then runs unpartitioned (Nsight Compute
+    cannot prepare launches on a green context), with the same factors."""
+    spec = W.SERVE_MESHES[1]
+    rhs = np.random.default_rng(5).normal(size=spec.n_unknowns)
+    out = []
+    for tool in (None, "NV_COMPUTE_PROFILER_PERFWORKS_DIR", "CUDA_INJECTION64_PATH"):
+        if tool:
+            monkeypatch.setenv(tool, "/nonexistent/tool")
+        with swj.Context.from_spec(spec, 0.75, 0.2, solve_mode="mixed", block_bw=11) as ctx:
+            ctx.precond_setup()
+            r = ctx.vector()
+            ctx.precond_apply(dev(rhs), r)
+            ctx.sync()
+            out.append((ctx.chain_sms(), r.cpu().numpy()))
+        if tool:
+            monkeypatch.delenv(tool)
+    assert out[1][0] == 0 and out[2][0] == 0
+    assert np.array_equal(out[1][1], out[0][1]) and np.array_equal(out[2][1], out[0][1])
+
+
 @pytest.mark.parametrize("spec,b", [(W.MESH_41x21, 11), (W.SERVE_MESHES[1], 11), (W.SOLVE_181x61[0], 11),
                                     (W.SOLVE_181x61[0], 9), (W.SERVE_MESHES[3], 15)])
 def test_two_sided_factorisation_equals_top_down(spec, b):
