@@ -396,6 +396,10 @@ def run_ours(args):
     u_host = torch.empty(ctx.n_unknowns, dtype=torch.float64).pin_memory()
     u_host.copy_(torch.from_numpy(W.flat_state(spec)))
     z_host = torch.empty(spec.N * spec.M, dtype=torch.float64).pin_memory()
+    # untimed warm-up through the same call (its first use allocates the staging buffer)
+    for _ in range(max(1, min(args.warmup, 2))):
+        ctx.solve_host(u_host, True, None, z_host, None)
+    torch.cuda.synchronize()
     e2e_ms = []
     if dist:
         dist.barrier()
@@ -492,6 +496,7 @@ def run_ours(args):
                 "unit": "solves/s", "h2d_bytes_per_step": ctx.n_unknowns * 8,
                 "d2h_bytes_per_step": spec.N * spec.M * 8,
                 "call": "swj_solve_host (C ABI, pinned host buffers in and out, preconditioner rebuilt)",
+                "ms": {"p50": statistics.median(e2e_ms), "max": max(e2e_ms), "min": min(e2e_ms)},
                 "max_abs_dzeta_vs_device_solve": e2e_dz},
         "gpu_launches": int(launches),
         "exact_jvp": exact,
