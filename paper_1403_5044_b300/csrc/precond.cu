@@ -539,8 +539,9 @@ inline double *wblk(swj_ctx *c, int inst, int i, int k)
 }
 
 // ---- SM partitions of the band LU (opts.sm_partition) -------------------------
-// Two CUDA green contexts of the device: 32 SMs that hold the Gauss-Jordan
-// chain's clusters, the other SMs for the bulk block products.  Unpartitioned,
+// Two CUDA green contexts of the device: 32 to 48 SMs (40 on B300) that hold
+// the Gauss-Jordan chain's clusters, the other SMs for the bulk block products
+// (pc_partitions).  Unpartitioned,
 // the bulk kernels share the chain's SMs and slow each pivot step of the
 // latency-bound chain.  The driver functions come through the runtime's
 // entry-point query (the library links only the runtime).
@@ -588,7 +589,6 @@ const GreenApi &green_api()
     }();
     return g;
 }
-constexpr unsigned kChainSMs = 32;
 constexpr size_t kGJOneCtaSmem = 116 * 1024;   // above half an SM's shared memory: one CTA per SM
 
 void free_partitions(swj_ctx *c)
